@@ -1,0 +1,316 @@
+"""Pins of the CPU oracle against things other than itself.
+
+* hand-derived golden fixtures (tests/golden/*.json, each with its citation
+  and the derivation of every expected value);
+* the exact-integer dt_max against independent big-integer arithmetic and
+  against ceil() in extended precision on random distances;
+* an independent all-pairs brute force (no sort, no window, pure Python)
+  on tiny random slices with forced ties and coincidences;
+* closed forms on pure Poisson background: the accidental floor-coincidence
+  seed rate and the mean causal count;
+* recovery of every injected muon track that fires on its own hits;
+* invariance of the triggers under a different partition of the run.
+"""
+import glob
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workload
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+GEOMETRIES = {"nemo32": workload.nemo_tower, "km3it84": workload.km3_tower, "array2688": workload.tower_array}
+
+
+def _tuples(a, fields):
+    return [tuple(int(x[f]) for f in fields) for x in a]
+
+
+SEED_F = ("t", "pmt", "charge", "count")
+WIN_F = ("lo", "hi", "n_hits", "n_triggers")
+
+
+# ------------------------------------------------------------------ golden
+
+@pytest.mark.parametrize("path", sorted(glob.glob(os.path.join(GOLDEN, "*.json"))), ids=os.path.basename)
+def test_golden_fixture(path, params):
+    fx = json.load(open(path))
+    det = GEOMETRIES[fx["geometry"]]()
+    par = dict(params)
+    par.update(fx["params"])
+    hits = np.zeros(len(fx["hits"]), oracle.HIT_DTYPE)
+    for i, (t, p, q) in enumerate(fx["hits"]):
+        hits[i] = (t, p, q, 0)
+    res = oracle.run(det.xyz_mm, det.floor_id, par, hits, fx["slices"])
+    for r, exp in zip(res, fx["expected"]):
+        assert _tuples(r.seeds, SEED_F) == [tuple(x) for x in exp["seeds"]]
+        assert _tuples(r.triggers, SEED_F) == [tuple(x) for x in exp["triggers"]]
+        assert _tuples(r.windows, WIN_F) == [tuple(x) for x in exp["windows"]]
+
+
+# ------------------------------------------------------------------ dt_max
+
+def _k_exact(d2, n_num=6900, n_den=1499):
+    """Smallest k with k * n_den * 1000 >= n_num * sqrt(d2): integer square
+    root on Python big integers (independent of the oracle's search)."""
+    M = n_den * 1000
+    X = n_num * n_num * d2
+    r = math.isqrt(X)
+    if r * r == X:
+        return (r + M - 1) // M
+    return r // M + 1
+
+
+def test_dtmax_worked_values():
+    # distances in mm, expected dt_max by hand: 20 + ceil(d[m] * 1.38 / 0.2998)
+    cases = {
+        0: 20,                                   # same point
+        6000 ** 2: 48,                           # across a 6 m bar: ceil(27.62) = 28
+        40000 ** 2: 205,                         # one floor straight up: ceil(184.12) = 185
+        1618 * 10 ** 6: 206,                     # rotated adjacent floor, sqrt(1618) m
+        80000 ** 2: 389,                         # two floors up: ceil(368.25)
+        14990 ** 2: 89,                          # 14.99 m: exactly 69, ceil of an integer
+        14990 ** 2 + 1: 90,                      # a hair more: 70
+        3000 ** 2 + 3000 ** 2 + 280000 ** 2: 1310,   # NEMO tower's longest pair
+        3000 ** 2 + 3000 ** 2 + 520000 ** 2: 2414,   # KM3Net-It tower's longest pair
+        633000 ** 2 + 273000 ** 2 + 520000 ** 2: 3995,  # array corner to corner
+    }
+    for d2, want in cases.items():
+        assert oracle.dtmax_pair(d2) == want, d2
+        assert 20 + _k_exact(d2) == want
+
+
+def test_dtmax_tables_match_geometry(params):
+    for make, want_max in ((workload.nemo_tower, 1310), (workload.km3_tower, 2414)):
+        det = make()
+        dt = oracle.dtmax(det.xyz_mm, params)
+        assert dt.max() == want_max
+        assert np.array_equal(dt, dt.T)
+        assert np.all(np.diag(dt) == 20)
+
+
+def test_dtmax_random_against_bigint_and_longdouble(params):
+    rng = np.random.Generator(np.random.PCG64(7))
+    xyz = rng.integers(-600_000, 600_000, size=(700, 3)).astype(np.int32)
+    xyz[:50, 2] = 0
+    xyz[50:100] = xyz[0]          # co-located PMTs
+    dt = oracle.dtmax(xyz, params).astype(np.int64)
+    d = xyz[:, None, :].astype(np.int64) - xyz[None, :, :].astype(np.int64)
+    d2 = (d * d).sum(-1)
+    # extended precision ceil, skipping values within 1e-9 of an integer
+    x = np.sqrt(d2.astype(np.longdouble)) * np.longdouble(6900) / np.longdouble(1499000)
+    c = np.ceil(x)
+    ok = np.abs(x - np.round(x)) > 1e-9
+    assert np.array_equal(dt[ok], 20 + c[ok].astype(np.int64))
+    # the rest (and a sample of all) against the big-integer root
+    idx = np.argwhere(~ok).tolist() + rng.integers(0, 700, size=(2000, 2)).tolist()
+    for i, j in idx:
+        assert dt[i, j] == 20 + _k_exact(int(d2[i, j])), (i, j)
+
+
+# ------------------------------------------------------ all-pairs brute force
+
+def _brute(det, par, hits, t0s):
+    """Plain definition over every pair, no ordering and no window."""
+    P = det.n_pmt
+    xyz = det.xyz_mm.astype(np.int64)
+    floor = det.floor_id
+    W = par["corr_window_ns"]
+
+    def dtm(a, b):
+        dd = xyz[a] - xyz[b]
+        return par["tol_ns"] + _k_exact(int((dd * dd).sum()), par["n_num"], par["n_den"])
+
+    cache = {}
+    H = [(int(h["t"]), int(h["pmt"]), int(h["charge"])) for h in hits]
+    out = []
+    for t0 in t0s:
+        seeds = []
+        for (ts, ps, qs) in H:
+            if not (t0 <= ts < t0 + par["slice_ns"]):
+                continue
+            seed = qs >= par["q_seed_adc"]
+            if not seed:
+                seed = any(pj != ps and floor[pj] == floor[ps] and abs(tj - ts) <= par["floor_tau_ns"]
+                           for (tj, pj, qj) in H)
+            if not seed:
+                continue
+            c = 0
+            for (tj, pj, qj) in H:
+                key = (ps, pj)
+                if key not in cache:
+                    cache[key] = dtm(ps, pj)
+                if abs(tj - ts) <= min(cache[key], W):
+                    c += 1
+            seeds.append((ts, ps, qs, c))
+        seeds.sort()
+        trig = [s for s in seeds if s[3] >= par["threshold"]]
+        wins = []
+        h = par["win_half_ns"]
+        for s in sorted(trig):
+            lo, hi = s[0] - h, s[0] + h
+            if wins and lo <= wins[-1][1] + 1:
+                wins[-1][1] = max(wins[-1][1], hi)
+                wins[-1][3] += 1
+            else:
+                wins.append([lo, hi, 0, 1])
+        for w in wins:
+            w[2] = sum(1 for (tj, _, _) in H if w[0] <= tj <= w[1])
+        out.append((seeds, trig, [tuple(w) for w in wins]))
+    return out
+
+
+@pytest.mark.parametrize("case", range(6))
+def test_oracle_matches_all_pairs_bruteforce(case, params):
+    rng = np.random.Generator(np.random.PCG64(100 + case))
+    det = [workload.nemo_tower, workload.km3_tower][case % 2]()
+    par = dict(params)
+    par["slice_ns"] = 20_000
+    par["threshold"] = int(rng.integers(1, 6))
+    par["q_seed_adc"] = int(rng.choice([300, 150, 65535]))
+    if case == 5:
+        par["corr_window_ns"] = 400          # make the clamp bind on a tower
+        par["win_half_ns"] = 500
+    n = int(rng.integers(150, 320))
+    t0s = [1_000_000, 1_020_000]
+    t = rng.integers(1_000_000 - 3000, 1_040_000 + 3000, n)
+    # forced near-coincidences and exact ties
+    t[: n // 4] = t[n // 4: 2 * (n // 4)] + rng.integers(-25, 26, n // 4)
+    t[-10:] = t[-20:-10]
+    hits = np.zeros(n, oracle.HIT_DTYPE)
+    hits["t"] = t
+    hits["pmt"] = rng.integers(0, det.n_pmt, n)
+    hits["charge"] = rng.integers(1, 400, n)
+    got = oracle.run(det.xyz_mm, det.floor_id, par, hits, t0s)
+    want = _brute(det, par, hits, t0s)
+    for r, (seeds, trig, wins) in zip(got, want):
+        assert _tuples(r.seeds, SEED_F) == seeds
+        assert _tuples(r.triggers, SEED_F) == trig
+        assert _tuples(r.windows, WIN_F) == wins
+
+
+def test_merge_is_lexicographic_sort():
+    rng = np.random.Generator(np.random.PCG64(3))
+    h = np.zeros(5000, oracle.HIT_DTYPE)
+    h["t"] = rng.integers(0, 300, 5000)
+    h["pmt"] = rng.integers(0, 8, 5000)
+    h["charge"] = rng.integers(0, 4, 5000)
+    h["reserved"] = np.arange(5000)
+    m = oracle.merge(h)
+    order = np.lexsort((h["reserved"], h["charge"], h["pmt"], h["t"]))
+    assert np.array_equal(m, h[order])
+
+
+# ------------------------------------------------------------ closed forms
+
+def test_accidental_floor_coincidence_rate(params):
+    """Pure Poisson background, no charge seeds: a hit is a seed iff one of
+    the other PMTs of its floor has a hit within +-tau.  For rates R_b the
+    chance is 1 - exp(-sum_b R_b (2 tau + 1 ns)) (integer-ns times), the
+    paper's 2 R^2 tau accidental rate per PMT pair at first order."""
+    det = workload.nemo_tower()
+    par = dict(params)
+    par["q_seed_adc"] = 65535
+    n_slices, rate = 50, 50e3
+    S = par["slice_ns"]
+    t_org = workload.T_ORIGIN_NS
+    st = workload.gen_stream(det, t_org - 3000, t_org + n_slices * S + 3000, rate, seed=11, stream=77)
+    t0s = [t_org + k * S for k in range(n_slices)]
+    res = oracle.run(det.xyz_mm, det.floor_id, par, st.hits, t0s)
+    obs = sum(len(r.seeds) for r in res)
+    tau = par["floor_tau_ns"]
+    lam = 3 * rate * (2 * tau + 1) * 1e-9           # three floor mates per PMT on NEMO
+    n_hits = int(np.count_nonzero((st.hits["t"] >= t0s[0]) & (st.hits["t"] < t0s[-1] + S)))
+    expect = n_hits * (1 - math.exp(-lam))
+    sigma = math.sqrt(2 * expect)                    # seeds come in pairs
+    assert abs(obs - expect) < 4 * sigma, (obs, expect, sigma)
+    # without the +1 ns of integer time the expectation moves by > 4 sigma
+    wrong = n_hits * (1 - math.exp(-3 * rate * 2 * tau * 1e-9))
+    assert abs(wrong - expect) > 4 * sigma
+
+
+def test_mean_causal_count_closed_form(params):
+    """Every hit a seed (q_seed = 0), threshold 0: on Poisson background
+    E[c(s) - 1] = sum_j R_j (2 min(dt_max[p_s][j], W) + 1 ns)."""
+    det = workload.tower_array(nx=8, ny=2)            # 16 towers: 1344 PMTs, far pairs beyond 3 us
+    par = dict(params)
+    par.update(q_seed_adc=0, threshold=0, slice_ns=200_000)
+    rate = 55e3
+    n_slices = 150
+    t_org = workload.T_ORIGIN_NS
+    S = par["slice_ns"]
+    st = workload.gen_stream(det, t_org - 3000, t_org + n_slices * S + 3000, rate, seed=5, stream=9)
+    t0s = [t_org + k * S for k in range(n_slices)]
+    res = oracle.run(det.xyz_mm, det.floor_id, par, st.hits, t0s)
+    dt = np.minimum(oracle.dtmax(det.xyz_mm, par).astype(np.float64), par["corr_window_ns"])
+    per_pmt = (rate * (2 * dt + 1) * 1e-9).sum(1)    # expected c-1 for a seed on PMT p
+    means, expects = [], []
+    for r in res:
+        c = r.seeds["count"].astype(np.float64) - 1
+        means.append(c.mean())
+        expects.append(per_pmt[r.seeds["pmt"]].mean())
+    means, expects = np.array(means), np.array(expects)
+    err = means.std(ddof=1) / math.sqrt(len(means))
+    assert abs(means.mean() - expects.mean()) < 4 * err + 1e-9, (means.mean(), expects.mean(), err)
+    # a count that left out the seed itself would sit 1 lower: resolved
+    assert abs(means.mean() + 1 - expects.mean()) > 4 * err, err
+
+
+# ------------------------------------------------------ injection recovery
+
+@pytest.mark.parametrize("cfg", ["nemo", "km3"])
+def test_injected_tracks_above_threshold_are_recovered(cfg, params):
+    wl = workload.CONFIGS[cfg]()
+    det = wl.detectors[0]
+    full = wl.runs[0]
+    t0s = wl.run_slices[0]
+    res = oracle.run(det.xyz_mm, det.floor_id, params, full.hits, t0s)
+    trig = {}
+    for r in res:
+        for x in r.triggers:
+            trig[(int(x["t"]), int(x["pmt"]), int(x["charge"]))] = int(x["count"])
+    wins = np.concatenate([r.windows for r in res])
+    tracks = np.unique(full.hits["reserved"][full.hits["reserved"] > 0])
+    n_above = 0
+    for m in tracks:
+        own = full.hits[full.hits["reserved"] == m]
+        alone = oracle.run(det.xyz_mm, det.floor_id, params, own, t0s)
+        for r in alone:
+            for x in r.triggers:
+                n_above += 1
+                key = (int(x["t"]), int(x["pmt"]), int(x["charge"]))
+                assert key in trig, (m, key)
+                assert trig[key] >= int(x["count"])
+                inside = (wins["lo"] <= x["t"] - params["win_half_ns"]) & (wins["hi"] >= x["t"] + params["win_half_ns"])
+                assert inside.any()
+    assert n_above > 0
+
+
+# ------------------------------------------------------------- invariance
+
+def test_trigger_list_independent_of_slicing(params):
+    wl = workload.cfg_km3()
+    det = wl.detectors[0]
+    full = wl.runs[0]
+    a = oracle.run(det.xyz_mm, det.floor_id, params, full.hits, wl.run_slices[0])
+    par2 = dict(params)
+    par2["slice_ns"] = params["slice_ns"] // 4
+    t0 = wl.run_slices[0][0]
+    b = oracle.run(det.xyz_mm, det.floor_id, par2, full.hits,
+                   [t0 + k * par2["slice_ns"] for k in range(4 * len(wl.run_slices[0]))])
+    ta = np.concatenate([r.triggers for r in a])
+    tb = np.concatenate([r.triggers for r in b])
+    sa = np.concatenate([r.seeds for r in a])
+    sb = np.concatenate([r.seeds for r in b])
+    assert np.array_equal(ta, tb)
+    assert np.array_equal(sa, sb)
+    # shuffling the input does not change anything
+    perm = np.random.Generator(np.random.PCG64(1)).permutation(len(full.hits))
+    c = oracle.run(det.xyz_mm, det.floor_id, params, full.hits[perm], wl.run_slices[0])
+    for x, y in zip(a, c):
+        assert np.array_equal(x.triggers, y.triggers)
+        assert np.array_equal(x.windows, y.windows)
