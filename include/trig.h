@@ -1,0 +1,249 @@
+/*
+ * trig.h -- C ABI of the GB300 online muon trigger (arXiv 1411.3968).
+ *
+ * The method ("Muon trigger strategy" and "Sorting and triggering in GPU"):
+ * every 200 ms time slice of merged PMT hits of a detector is scanned for
+ * seed hits (charge over threshold, or two hits on one floor within a few
+ * ns); each seed counts the hits causally related to it,
+ *     c(s) = #{ j : |t_j - t_s| <= min(dt_max[p_s][p_j], W) },
+ * with dt_max the light travel time between the two PMTs plus a tolerance
+ * and W the 3 us correlation interval; the seed fires when c(s) reaches the
+ * threshold, and the 6 us windows centred on the fired seeds (+-3 us, the
+ * data sent to the Event Manager, "DAQ system of NEMO Phase II") are merged
+ * and returned.
+ *
+ * Two faces:
+ *   - the engine (trig_create / trig_submit_slice / trig_poll / trig_destroy):
+ *     host buffers in, host results out; slices from all detectors are
+ *     batched continuously on one GPU;
+ *   - the device batch call (trig_batch_run): device buffers in and out, the
+ *     caller owns all memory, one launch sequence for many slices.
+ *
+ * All functions return TRIG_OK (0) or a negative TRIG_E* code and never
+ * throw.  trig_last_error() gives a message for the calling thread's last
+ * failure.  Pointers marked "device" must be CUDA device (or managed)
+ * memory of the current device; "host" pointers are ordinary host memory.
+ */
+#ifndef TRIG_H
+#define TRIG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ----------------------------------------------------------------- codes */
+#define TRIG_OK          0
+#define TRIG_EINVAL     (-1)  /* bad argument or malformed input slice          */
+#define TRIG_ENOMEM     (-2)  /* host or device allocation failed               */
+#define TRIG_EAGAIN     (-3)  /* admission full (submit) / nothing ready (poll) */
+#define TRIG_ETIMEOUT   (-4)  /* a bounded wait ran out                         */
+#define TRIG_EDEVICE    (-5)  /* CUDA error                                     */
+#define TRIG_ECAPACITY  (-6)  /* output capacity or tile capacity exceeded      */
+
+/* Slice status bits reported by the device (trig_slice_stats.flags). */
+#define TRIG_FLAG_BAD_PMT      0x01u  /* hit.pmt >= n_pmt or outside its CSR row  */
+#define TRIG_FLAG_UNSORTED     0x02u  /* a PMT stream is not time-ordered         */
+#define TRIG_FLAG_OUT_OF_RANGE 0x04u  /* hit outside [t0 - halo, t0 + S + halo)   */
+#define TRIG_FLAG_TILE_FULL    0x08u  /* > tile capacity hits inside one 1 ns core
+                                         plus its halo; results incomplete       */
+#define TRIG_FLAG_TRIG_FULL    0x10u  /* more triggers than trig_cap             */
+#define TRIG_FLAG_WIN_FULL     0x20u  /* more windows than win_cap               */
+#define TRIG_FLAG_TIMEOUT      0x40u  /* a bounded device wait gave up            */
+
+/* ----------------------------------------------------------------- types */
+
+/* One PMT hit, 16 bytes: the fixed-size GPU hit record of "CPU-GPU" (charge,
+ * time, DU identification).  `reserved` is carried but never read. */
+typedef struct {
+    int64_t t_ns;       /* hit time, integer ns                       */
+    uint16_t pmt;       /* PMT (detection unit) index, < n_pmt         */
+    uint16_t charge;    /* ADC counts (1 pe = 100 in the workloads)    */
+    uint32_t reserved;
+} trig_hit;
+
+/* Detector description, copied by trig_create.  Two PMTs are on the same
+ * floor iff their floor_id values are equal (ids need not be dense).
+ * Coordinates must lie within +-1e8 mm; 1 <= n_pmt <= 4096. */
+typedef struct {
+    uint32_t n_pmt;
+    const int32_t *xyz_mm;      /* host, 3 * n_pmt: x, y, z of PMT p       */
+    const uint32_t *floor_id;   /* host, n_pmt                              */
+    const uint32_t *tower_id;   /* host, n_pmt, informational (may be NULL) */
+} trig_geometry;
+
+/* Trigger constants.  The paper names the primitives (QTRIG charge
+ * threshold, floor coincidence, 3 us correlation interval, +-3 us tagging)
+ * but leaves their values open; the workloads use
+ * {300, 20, 20, 6900, 1499, 3000, 4, 3000, 200000000}. */
+typedef struct {
+    uint32_t q_seed_adc;        /* charge seed: charge >= q_seed_adc                */
+    uint32_t floor_tau_ns;      /* floor coincidence: |t_i - t_j| <= tau            */
+    uint32_t tol_ns;            /* dt_max = tol + ceil(d * n_num / (n_den * 1000))  */
+    uint32_t n_num, n_den;      /*   for d in mm: n_num/n_den ns per metre          */
+    uint32_t corr_window_ns;    /* W: the causal test uses min(dt_max, W)           */
+    uint32_t threshold;         /* fire when c(s) >= threshold                      */
+    uint32_t win_half_ns;       /* event window [t - h, t + h], merged when touching */
+    int64_t slice_ns;           /* a slice owns [t0, t0 + slice_ns)                 */
+} trig_params;
+
+/* A fired seed: its hit and causal count c(s). 16 bytes. */
+typedef struct {
+    int64_t t_ns;
+    uint16_t pmt;
+    uint16_t charge;
+    uint32_t count;
+} trig_trigger;
+
+/* A merged event window [lo_ns, hi_ns] (inclusive), the number of hits of
+ * the slice submission inside it and the number of triggers it merged. */
+typedef struct {
+    int64_t lo_ns, hi_ns;
+    uint64_t n_hits;
+    uint64_t n_triggers;
+} trig_window;
+
+/* Per-slice counters written by the device. status is TRIG_OK,
+ * TRIG_EINVAL (input flags), TRIG_ECAPACITY or TRIG_ETIMEOUT. */
+typedef struct {
+    int32_t status;
+    uint32_t flags;             /* TRIG_FLAG_* bits                          */
+    uint64_t n_hits;            /* hits submitted (owned range and halos)    */
+    uint64_t n_seeds;
+    uint64_t n_triggers;        /* may exceed trig_cap (then TRIG_FLAG_TRIG_FULL) */
+    uint64_t n_windows;         /* may exceed win_cap  (then TRIG_FLAG_WIN_FULL)  */
+} trig_slice_stats;
+
+typedef struct trig_detector trig_detector;
+
+/* Engine result of one slice; owned by the library until trig_result_free. */
+typedef struct {
+    uint64_t slice_id;
+    int64_t t0_ns;
+    int32_t status;             /* TRIG_OK or a TRIG_E* code      */
+    uint32_t flags;             /* TRIG_FLAG_* bits               */
+    uint64_t n_hits, n_seeds, n_triggers, n_windows;
+    trig_trigger *triggers;     /* n_triggers entries, (t, pmt, charge) order */
+    trig_window *windows;       /* n_windows entries, time order              */
+    int64_t latency_ns;         /* submit -> result ready (host clock)        */
+} trig_result;
+
+/* ------------------------------------------------------------- detectors */
+
+/* Creates a detector: copies the geometry and parameters, builds the exact
+ * integer causality table dt_max on the device ("Muon trigger strategy":
+ * the time-space correlation) and keeps it resident until trig_destroy.
+ * EINVAL on n_pmt outside [1, 4096], NULL pointers, n_den == 0,
+ * slice_ns <= 0 or coordinates beyond +-1e8 mm; ENOMEM / EDEVICE on CUDA
+ * failures.  The detector is bound to the CUDA device current at creation. */
+int trig_create(const trig_geometry *geometry, const trig_params *params, trig_detector **out);
+
+/* Drains the detector's in-flight slices, then frees it.  Results not yet
+ * polled are discarded.  NULL is accepted. */
+int trig_destroy(trig_detector *det);
+
+/* Copies the exact (unclamped) dt_max table into host memory dt_out
+ * (n_pmt * n_pmt int32, row p_s, column p_j). */
+int trig_detector_dtmax(const trig_detector *det, int32_t *dt_out);
+
+/* Halo the detector needs around each slice: hits in
+ * [t0 - halo, t0 + slice_ns + halo) are accepted and used; halo =
+ * max(corr_window_ns, win_half_ns, floor_tau_ns). */
+int64_t trig_detector_halo_ns(const trig_detector *det);
+
+/* ---------------------------------------------------------------- engine */
+
+/* Submits one slice (host memory).  hits are grouped by PMT (CSR):
+ * hits[pmt_off[p] .. pmt_off[p+1]) are PMT p's hits in non-decreasing time;
+ * pmt_off has n_pmt + 1 entries, pmt_off[0] == 0, and pmt_off[n_pmt] is the
+ * hit count (< 2^32).  The producer includes the halos: every hit in
+ * [t0 - halo, t0 + slice_ns + halo) that the detector recorded (the paper's
+ * "proceeds on first hits of the next time slice", "Preparation in CPU").
+ * Seeds are only those in [t0, t0 + slice_ns).  The hits are copied before
+ * the call returns.  EINVAL on malformed offsets; EAGAIN when the engine's
+ * staging memory is full (poll, then retry).  Malformed hit records (bad
+ * pmt, unsorted streams, out-of-range times) are detected on the device and
+ * reported through the result's status (EINVAL) and flags. */
+int trig_submit_slice(trig_detector *det, int64_t slice_t0_ns, const trig_hit *hits, const uint64_t *pmt_off,
+                      int is_continuation, uint64_t *slice_id_out);
+
+/* Returns the detector's oldest unreturned result (slices complete in
+ * submission order per detector).  Waits up to timeout_ms (0: do not wait,
+ * < 0: wait without limit); EAGAIN if nothing is ready in time. */
+int trig_poll(trig_detector *det, int timeout_ms, trig_result **out);
+
+void trig_result_free(trig_result *res);
+
+/* Engine policy: 0 = plain (every slice is its own launch sequence),
+ * 1 = batched (pending slices of all detectors share one launch, replayed
+ * from a CUDA graph).  Default 1. */
+int trig_engine_set_mode(int mode);
+
+/* Engine counters since start: batches launched, slices completed. */
+int trig_engine_stats(uint64_t *batches, uint64_t *slices);
+
+/* Message of the calling thread's last failure ("" if none). */
+const char *trig_last_error(void);
+
+/* ------------------------------------------------------- device batches */
+
+/* One slice for trig_batch_run.  All buffers are device memory owned by the
+ * caller.  hits must be 16-byte aligned.  Layout and halo rules as for
+ * trig_submit_slice.  Outputs: up to trig_cap triggers and win_cap windows;
+ * a window bound that can never overflow is
+ *   win_cap >= (slice_ns + 2 * win_half_ns) / (2 * win_half_ns + 2) + 1. */
+typedef struct {
+    const trig_detector *det;
+    const trig_hit *hits;          /* device */
+    const uint64_t *pmt_off;       /* device, n_pmt + 1 */
+    uint64_t n_hits;               /* == pmt_off[n_pmt]  */
+    int64_t t0_ns;
+    trig_trigger *triggers;        /* device, trig_cap entries */
+    uint64_t trig_cap;
+    trig_window *windows;          /* device, win_cap entries  */
+    uint64_t win_cap;
+    trig_slice_stats *stats;       /* device, one entry        */
+} trig_slice_dev;
+
+/* Scratch bytes trig_batch_run needs for these slices (0 on bad input). */
+size_t trig_batch_scratch_bytes(const trig_slice_dev *slices, uint32_t n_slices);
+
+/* Runs the whole hot path for n_slices slices on `stream` (a cudaStream_t,
+ * NULL for the legacy default stream): the k-way merge of the PMT streams,
+ * seed selection, causal counting, stream compaction of the fired seeds and
+ * the window merge.  Asynchronous: results are valid once the stream
+ * reaches this point.  `scratch` is device memory of at least
+ * trig_batch_scratch_bytes(), 256-byte aligned; it must not be used by
+ * anything else until the work completes.  flags: TRIG_RUN_GRAPH replays
+ * the launch sequence from a cached CUDA graph (one per stream and scratch
+ * pointer).  EINVAL on bad arguments (nothing is launched). */
+#define TRIG_RUN_GRAPH 0x1u
+int trig_batch_run(const trig_slice_dev *slices, uint32_t n_slices, void *scratch, size_t scratch_bytes,
+                   void *stream, uint32_t flags);
+
+/* Row-level view of one slice for verification: writes the owned hits in
+ * merged (t, pmt, charge) order to merged_out (device, n_hits entries; the
+ * owned hits start at index 0) and, for each of them, its causal count if
+ * it is a seed or 0xFFFFFFFF if not, to seedcnt_out (device, n_hits
+ * entries).  *n_owned_out (host) receives the number of owned hits.  Runs
+ * the same kernels as trig_batch_run and synchronises the stream. */
+int trig_slice_rows(const trig_slice_dev *slice, trig_hit *merged_out, uint32_t *seedcnt_out,
+                    uint64_t *n_owned_out, void *scratch, size_t scratch_bytes, void *stream);
+
+/* Device launch configuration of the tile kernel: tile capacity (hits per
+ * shared-memory tile including halos) and target fill fraction (percent)
+ * used to choose the tile width.  cap must be 2048, 4096 or 8192;
+ * fill_pct in [10, 95].  Applies to later runs in this process. */
+int trig_set_tile_config(uint32_t cap, uint32_t fill_pct);
+int trig_get_tile_config(uint32_t *cap, uint32_t *fill_pct);
+
+/* Kernel launches issued by trig_batch_run per call (graph replays count
+ * their kernels). */
+uint64_t trig_kernel_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TRIG_H */

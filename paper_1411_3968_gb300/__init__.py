@@ -1,0 +1,11 @@
+"""GB300-native online muon trigger for underwater neutrino telescopes
+(arXiv 1411.3968): C ABI in include/trig.h, sm_103a kernels in csrc/,
+Python binding in _lib.  PyTorch (optional) is used only by callers for
+device memory and streams; see runner.py."""
+from ._lib import (  # noqa: F401
+    HIT_DTYPE, STATS_DTYPE, TRIGGER_DTYPE, WINDOW_DTYPE, Detector, Result, TrigError,
+    TRIG_OK, TRIG_EINVAL, TRIG_ENOMEM, TRIG_EAGAIN, TRIG_ETIMEOUT, TRIG_EDEVICE, TRIG_ECAPACITY,
+    TRIG_RUN_GRAPH, load, trig_batch_run, trig_batch_scratch_bytes, trig_create, trig_destroy,
+    trig_engine_set_mode, trig_engine_stats, trig_get_tile_config, trig_kernel_launch_count, trig_last_error,
+    trig_poll, trig_set_tile_config, trig_slice_rows, trig_submit_slice, win_cap_for,
+)

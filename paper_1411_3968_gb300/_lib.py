@@ -1,0 +1,285 @@
+"""ctypes binding of libtrig.so (include/trig.h).  Argument marshalling only:
+every step of the trigger runs in the library's CUDA kernels.  There is no
+CPU fallback; loading fails loudly if the library is missing."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtrig.so")
+
+TRIG_OK = 0
+TRIG_EINVAL = -1
+TRIG_ENOMEM = -2
+TRIG_EAGAIN = -3
+TRIG_ETIMEOUT = -4
+TRIG_EDEVICE = -5
+TRIG_ECAPACITY = -6
+
+TRIG_FLAG_BAD_PMT = 0x01
+TRIG_FLAG_UNSORTED = 0x02
+TRIG_FLAG_OUT_OF_RANGE = 0x04
+TRIG_FLAG_TILE_FULL = 0x08
+TRIG_FLAG_TRIG_FULL = 0x10
+TRIG_FLAG_WIN_FULL = 0x20
+TRIG_FLAG_TIMEOUT = 0x40
+
+TRIG_RUN_GRAPH = 0x1
+
+HIT_DTYPE = np.dtype([("t", "<i8"), ("pmt", "<u2"), ("charge", "<u2"), ("reserved", "<u4")])
+TRIGGER_DTYPE = np.dtype([("t", "<i8"), ("pmt", "<u2"), ("charge", "<u2"), ("count", "<u4")])
+WINDOW_DTYPE = np.dtype([("lo", "<i8"), ("hi", "<i8"), ("n_hits", "<u8"), ("n_triggers", "<u8")])
+STATS_DTYPE = np.dtype([("status", "<i4"), ("flags", "<u4"), ("n_hits", "<u8"), ("n_seeds", "<u8"),
+                        ("n_triggers", "<u8"), ("n_windows", "<u8")])
+
+# symbols declared in include/trig.h
+EXPORTS = [
+    "trig_create", "trig_destroy", "trig_detector_dtmax", "trig_detector_halo_ns", "trig_submit_slice",
+    "trig_poll", "trig_result_free", "trig_engine_set_mode", "trig_engine_stats", "trig_last_error",
+    "trig_batch_scratch_bytes", "trig_batch_run", "trig_slice_rows", "trig_set_tile_config",
+    "trig_get_tile_config", "trig_kernel_launch_count",
+]
+
+
+class TrigError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"trig error {code}: {msg}")
+        self.code = code
+
+
+class trig_geometry(ctypes.Structure):
+    _fields_ = [("n_pmt", ctypes.c_uint32), ("xyz_mm", ctypes.c_void_p), ("floor_id", ctypes.c_void_p),
+                ("tower_id", ctypes.c_void_p)]
+
+
+class trig_params(ctypes.Structure):
+    _fields_ = [("q_seed_adc", ctypes.c_uint32), ("floor_tau_ns", ctypes.c_uint32), ("tol_ns", ctypes.c_uint32),
+                ("n_num", ctypes.c_uint32), ("n_den", ctypes.c_uint32), ("corr_window_ns", ctypes.c_uint32),
+                ("threshold", ctypes.c_uint32), ("win_half_ns", ctypes.c_uint32), ("slice_ns", ctypes.c_int64)]
+
+
+class trig_result(ctypes.Structure):
+    _fields_ = [("slice_id", ctypes.c_uint64), ("t0_ns", ctypes.c_int64), ("status", ctypes.c_int32),
+                ("flags", ctypes.c_uint32), ("n_hits", ctypes.c_uint64), ("n_seeds", ctypes.c_uint64),
+                ("n_triggers", ctypes.c_uint64), ("n_windows", ctypes.c_uint64), ("triggers", ctypes.c_void_p),
+                ("windows", ctypes.c_void_p), ("latency_ns", ctypes.c_int64)]
+
+
+class trig_slice_dev(ctypes.Structure):
+    _fields_ = [("det", ctypes.c_void_p), ("hits", ctypes.c_void_p), ("pmt_off", ctypes.c_void_p),
+                ("n_hits", ctypes.c_uint64), ("t0_ns", ctypes.c_int64), ("triggers", ctypes.c_void_p),
+                ("trig_cap", ctypes.c_uint64), ("windows", ctypes.c_void_p), ("win_cap", ctypes.c_uint64),
+                ("stats", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libtrig.so (built by __graft_entry__.build() or build.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise ImportError(f"libtrig.so not built at {p}; run __graft_entry__.build()")
+    lib = ctypes.CDLL(p)
+    c = ctypes
+    sig = {
+        "trig_create": (c.c_int, [c.POINTER(trig_geometry), c.POINTER(trig_params), c.POINTER(c.c_void_p)]),
+        "trig_destroy": (c.c_int, [c.c_void_p]),
+        "trig_detector_dtmax": (c.c_int, [c.c_void_p, c.c_void_p]),
+        "trig_detector_halo_ns": (c.c_int64, [c.c_void_p]),
+        "trig_submit_slice": (c.c_int, [c.c_void_p, c.c_int64, c.c_void_p, c.c_void_p, c.c_int,
+                                        c.POINTER(c.c_uint64)]),
+        "trig_poll": (c.c_int, [c.c_void_p, c.c_int, c.POINTER(c.POINTER(trig_result))]),
+        "trig_result_free": (None, [c.POINTER(trig_result)]),
+        "trig_engine_set_mode": (c.c_int, [c.c_int]),
+        "trig_engine_stats": (c.c_int, [c.POINTER(c.c_uint64), c.POINTER(c.c_uint64)]),
+        "trig_last_error": (c.c_char_p, []),
+        "trig_batch_scratch_bytes": (c.c_size_t, [c.POINTER(trig_slice_dev), c.c_uint32]),
+        "trig_batch_run": (c.c_int, [c.POINTER(trig_slice_dev), c.c_uint32, c.c_void_p, c.c_size_t, c.c_void_p,
+                                     c.c_uint32]),
+        "trig_slice_rows": (c.c_int, [c.POINTER(trig_slice_dev), c.c_void_p, c.c_void_p, c.POINTER(c.c_uint64),
+                                      c.c_void_p, c.c_size_t, c.c_void_p]),
+        "trig_set_tile_config": (c.c_int, [c.c_uint32, c.c_uint32]),
+        "trig_get_tile_config": (c.c_int, [c.POINTER(c.c_uint32), c.POINTER(c.c_uint32)]),
+        "trig_kernel_launch_count": (c.c_uint64, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc):
+    if rc != TRIG_OK:
+        raise TrigError(rc, load().trig_last_error().decode())
+    return rc
+
+
+def trig_last_error() -> str:
+    return load().trig_last_error().decode()
+
+
+# ------------------------------------------------------------------ detectors
+
+class Detector:
+    """Owns a trig_detector handle."""
+
+    def __init__(self, xyz_mm, floor_id, params: dict, tower_id=None):
+        lib = load()
+        self.xyz = np.ascontiguousarray(xyz_mm, np.int32).reshape(-1, 3)
+        self.floor_id = np.ascontiguousarray(floor_id, np.uint32)
+        self.tower_id = None if tower_id is None else np.ascontiguousarray(tower_id, np.uint32)
+        self.n_pmt = self.xyz.shape[0]
+        self.params = dict(params)
+        g = trig_geometry(self.n_pmt, self.xyz.ctypes.data, self.floor_id.ctypes.data,
+                          None if self.tower_id is None else self.tower_id.ctypes.data)
+        p = trig_params(*(int(params[f]) for f, _ in trig_params._fields_))
+        h = ctypes.c_void_p()
+        _check(lib.trig_create(ctypes.byref(g), ctypes.byref(p), ctypes.byref(h)))
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            load().trig_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def halo_ns(self) -> int:
+        return int(load().trig_detector_halo_ns(self.handle))
+
+    def dtmax(self) -> np.ndarray:
+        out = np.empty((self.n_pmt, self.n_pmt), np.int32)
+        _check(load().trig_detector_dtmax(self.handle, out.ctypes.data))
+        return out
+
+
+def trig_create(xyz_mm, floor_id, params, tower_id=None) -> Detector:
+    return Detector(xyz_mm, floor_id, params, tower_id)
+
+
+def trig_destroy(det: Detector) -> None:
+    det.close()
+
+
+# --------------------------------------------------------------------- engine
+
+def trig_submit_slice(det: Detector, t0: int, hits: np.ndarray, pmt_off: np.ndarray, is_continuation: int = 0) -> int:
+    h = np.ascontiguousarray(hits, HIT_DTYPE)
+    o = np.ascontiguousarray(pmt_off, np.uint64)
+    sid = ctypes.c_uint64()
+    rc = load().trig_submit_slice(det.handle, int(t0), h.ctypes.data if len(h) else None, o.ctypes.data,
+                                  int(is_continuation), ctypes.byref(sid))
+    _check(rc)
+    return int(sid.value)
+
+
+class Result:
+    def __init__(self, r: trig_result):
+        self.slice_id = int(r.slice_id)
+        self.t0 = int(r.t0_ns)
+        self.status = int(r.status)
+        self.flags = int(r.flags)
+        self.n_hits = int(r.n_hits)
+        self.n_seeds = int(r.n_seeds)
+        self.latency_ns = int(r.latency_ns)
+        self.triggers = _copy(r.triggers, r.n_triggers, TRIGGER_DTYPE)
+        self.windows = _copy(r.windows, r.n_windows, WINDOW_DTYPE)
+
+
+def _copy(ptr, n, dtype):
+    n = int(n)
+    if n == 0 or not ptr:
+        return np.empty(0, dtype)
+    buf = (ctypes.c_char * (n * dtype.itemsize)).from_address(ptr)
+    return np.frombuffer(buf, dtype).copy()
+
+
+def trig_poll(det: Detector, timeout_ms: int = -1) -> Result | None:
+    lib = load()
+    out = ctypes.POINTER(trig_result)()
+    rc = lib.trig_poll(det.handle, int(timeout_ms), ctypes.byref(out))
+    if rc == TRIG_EAGAIN:
+        return None
+    _check(rc)
+    try:
+        return Result(out.contents)
+    finally:
+        lib.trig_result_free(out)
+
+
+def trig_engine_set_mode(mode: int) -> None:
+    _check(load().trig_engine_set_mode(int(mode)))
+
+
+def trig_engine_stats() -> tuple[int, int]:
+    b, s = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(load().trig_engine_stats(ctypes.byref(b), ctypes.byref(s)))
+    return int(b.value), int(s.value)
+
+
+def trig_set_tile_config(cap: int, fill_pct: int) -> None:
+    _check(load().trig_set_tile_config(int(cap), int(fill_pct)))
+
+
+def trig_get_tile_config() -> tuple[int, int]:
+    c, f = ctypes.c_uint32(), ctypes.c_uint32()
+    _check(load().trig_get_tile_config(ctypes.byref(c), ctypes.byref(f)))
+    return int(c.value), int(f.value)
+
+
+def trig_kernel_launch_count() -> int:
+    return int(load().trig_kernel_launch_count())
+
+
+# ------------------------------------------------------------- device batches
+
+def slice_dev(det: Detector, hits_ptr: int, pmt_off_ptr: int, n_hits: int, t0: int, trig_ptr: int, trig_cap: int,
+              win_ptr: int, win_cap: int, stats_ptr: int) -> trig_slice_dev:
+    return trig_slice_dev(det.handle.value, hits_ptr, pmt_off_ptr, n_hits, t0, trig_ptr, trig_cap, win_ptr, win_cap,
+                          stats_ptr)
+
+
+def _array(slices):
+    arr = (trig_slice_dev * len(slices))(*slices)
+    return arr
+
+
+def trig_batch_scratch_bytes(slices) -> int:
+    arr = _array(slices)
+    n = load().trig_batch_scratch_bytes(arr, len(slices))
+    if n == 0:
+        raise TrigError(TRIG_EINVAL, trig_last_error())
+    return int(n)
+
+
+def trig_batch_run(slices, scratch_ptr: int, scratch_bytes: int, stream_ptr: int = 0, flags: int = 0) -> None:
+    arr = _array(slices)
+    _check(load().trig_batch_run(arr, len(slices), scratch_ptr, scratch_bytes, stream_ptr or None, flags))
+
+
+def trig_slice_rows(s: trig_slice_dev, merged_ptr: int, seedcnt_ptr: int, scratch_ptr: int, scratch_bytes: int,
+                    stream_ptr: int = 0) -> int:
+    n = ctypes.c_uint64()
+    _check(load().trig_slice_rows(ctypes.byref(s), merged_ptr, seedcnt_ptr, ctypes.byref(n), scratch_ptr,
+                                  scratch_bytes, stream_ptr or None))
+    return int(n.value)
+
+
+def win_cap_for(params: dict) -> int:
+    """A window capacity that can never overflow for one slice."""
+    h = int(params["win_half_ns"])
+    return (int(params["slice_ns"]) + 2 * h) // (2 * h + 2) + 2

@@ -1,0 +1,981 @@
+// trig_engine.cpp -- host runtime behind trig.h: detectors, batch planning,
+// CUDA-graph replay and the continuously batching slice engine.
+//
+// Serving model (the paper's TGPU, "CPU-GPU"): slices of several detectors
+// arrive on the host; each submission is copied into pinned staging memory
+// and queued; a worker thread forms batches from whatever is pending,
+// admits a batch when a slot (stream + device arena) is free and the device
+// has the memory, copies it to the GPU, runs the whole trigger for all its
+// slices in one launch sequence, and hands results back per detector in
+// submission order.  Up to kSlots batches are in flight, so copies of one
+// batch overlap the kernels of another.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "trig_internal.h"
+
+using namespace trig;
+
+// ---------------------------------------------------------------- errors
+
+static thread_local std::string g_last_error;
+
+static int fail(int code, const std::string &msg)
+{
+    g_last_error = msg;
+    return code;
+}
+
+static int cuda_fail(cudaError_t e, const char *what)
+{
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    (void)cudaGetLastError();
+    return fail(e == cudaErrorMemoryAllocation ? TRIG_ENOMEM : TRIG_EDEVICE, m);
+}
+
+extern "C" const char *trig_last_error(void) { return g_last_error.c_str(); }
+
+static std::atomic<uint64_t> g_launches{0};
+extern "C" uint64_t trig_kernel_launch_count(void) { return g_launches.load(); }
+
+static std::mutex g_cfg_mu;
+static TileConfig g_cfg{4096, 60};
+
+extern "C" int trig_set_tile_config(uint32_t cap, uint32_t fill_pct)
+{
+    if ((cap != 2048 && cap != 4096) || fill_pct < 10 || fill_pct > 95)
+        return fail(TRIG_EINVAL, "trig_set_tile_config: cap must be 2048 or 4096, fill_pct in [10, 95]");
+    std::lock_guard<std::mutex> lk(g_cfg_mu);
+    g_cfg = TileConfig{cap, fill_pct};
+    return TRIG_OK;
+}
+
+extern "C" int trig_get_tile_config(uint32_t *cap, uint32_t *fill_pct)
+{
+    std::lock_guard<std::mutex> lk(g_cfg_mu);
+    if (cap) *cap = g_cfg.cap;
+    if (fill_pct) *fill_pct = g_cfg.fill_pct;
+    return TRIG_OK;
+}
+
+static TileConfig current_cfg()
+{
+    std::lock_guard<std::mutex> lk(g_cfg_mu);
+    return g_cfg;
+}
+
+// ------------------------------------------------------------- detectors
+
+struct DetQueue;
+
+struct trig_detector {
+    uint32_t n_pmt = 0;
+    trig_params par{};
+    int device = 0;
+    uint32_t tile_halo = 0;       // max(max_q min(dt_max, W), tau)
+    int64_t in_halo = 0;          // accepted halo around a slice
+    std::vector<int32_t> xyz;
+    std::vector<uint32_t> floor_id;
+    DetDev dev{};
+    int32_t *d_xyz = nullptr;
+    std::shared_ptr<DetQueue> q;
+};
+
+static void free_det_dev(trig_detector *d)
+{
+    cudaFree(d->dev.dt);
+    cudaFree(d->dev.dt_exact);
+    cudaFree(d->dev.floor);
+    cudaFree(d->dev.dmax_row);
+    cudaFree(d->d_xyz);
+    d->dev = DetDev{};
+    d->d_xyz = nullptr;
+}
+
+static int check_params(const trig_params *p)
+{
+    if (!p) return fail(TRIG_EINVAL, "params is NULL");
+    if (p->n_den == 0 || p->n_num == 0) return fail(TRIG_EINVAL, "n_num and n_den must be positive");
+    if (p->slice_ns <= 0 || p->slice_ns > ((int64_t)1 << 40)) return fail(TRIG_EINVAL, "slice_ns out of range");
+    if (p->corr_window_ns > 60000 || p->win_half_ns > 60000 || p->floor_tau_ns > 60000)
+        return fail(TRIG_EINVAL, "corr_window_ns, win_half_ns and floor_tau_ns must be <= 60000");
+    if (p->q_seed_adc > 65536) return fail(TRIG_EINVAL, "q_seed_adc > 65536");
+    return TRIG_OK;
+}
+
+extern "C" int trig_create(const trig_geometry *g, const trig_params *params, trig_detector **out)
+{
+    if (!out) return fail(TRIG_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!g || !g->xyz_mm || !g->floor_id) return fail(TRIG_EINVAL, "geometry or its arrays are NULL");
+    if (g->n_pmt < 1 || g->n_pmt > kMaxPmt) return fail(TRIG_EINVAL, "n_pmt must be in [1, 4096]");
+    int rc = check_params(params);
+    if (rc) return rc;
+    const uint32_t P = g->n_pmt;
+    for (uint32_t i = 0; i < 3 * P; ++i)
+        if (g->xyz_mm[i] > 100000000 || g->xyz_mm[i] < -100000000)
+            return fail(TRIG_EINVAL, "coordinates must lie within +-1e8 mm");
+
+    std::unique_ptr<trig_detector> d(new trig_detector());
+    d->n_pmt = P;
+    d->par = *params;
+    cudaGetDevice(&d->device);
+    d->xyz.assign(g->xyz_mm, g->xyz_mm + 3 * P);
+    d->floor_id.assign(g->floor_id, g->floor_id + P);
+    // dense floor indices
+    std::vector<uint16_t> floor_dense(P);
+    {
+        std::map<uint32_t, uint16_t> ids;
+        for (uint32_t p = 0; p < P; ++p) {
+            auto it = ids.find(g->floor_id[p]);
+            if (it == ids.end()) it = ids.emplace(g->floor_id[p], (uint16_t)ids.size()).first;
+            floor_dense[p] = it->second;
+        }
+    }
+    const size_t PP = (size_t)P * P;
+    cudaError_t e;
+    if ((e = cudaMalloc(&d->dev.dt, PP * 2)) || (e = cudaMalloc(&d->dev.dt_exact, PP * 4)) ||
+        (e = cudaMalloc(&d->dev.floor, (size_t)P * 2)) || (e = cudaMalloc(&d->dev.dmax_row, (size_t)P * 2)) ||
+        (e = cudaMalloc(&d->d_xyz, (size_t)3 * P * 4))) {
+        free_det_dev(d.get());
+        return cuda_fail(e, "trig_create: cudaMalloc");
+    }
+    cudaStream_t st;
+    if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking))) {
+        free_det_dev(d.get());
+        return cuda_fail(e, "trig_create: stream");
+    }
+    std::vector<uint16_t> dmax(P);
+    e = cudaMemcpyAsync(d->d_xyz, g->xyz_mm, (size_t)3 * P * 4, cudaMemcpyHostToDevice, st);
+    if (!e) e = cudaMemcpyAsync(d->dev.floor, floor_dense.data(), (size_t)P * 2, cudaMemcpyHostToDevice, st);
+    if (!e)
+        e = launch_dtmax(d->d_xyz, P, params->tol_ns, params->n_num, params->n_den, params->corr_window_ns,
+                         d->dev.dt_exact, d->dev.dt, d->dev.dmax_row, st);
+    if (!e) e = cudaMemcpyAsync(dmax.data(), d->dev.dmax_row, (size_t)P * 2, cudaMemcpyDeviceToHost, st);
+    if (!e) e = cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+    if (e) {
+        free_det_dev(d.get());
+        return cuda_fail(e, "trig_create: building dt_max");
+    }
+    uint32_t H = params->floor_tau_ns;
+    for (uint16_t v : dmax) H = std::max<uint32_t>(H, v);
+    d->tile_halo = H;
+    d->in_halo = std::max<int64_t>({(int64_t)params->corr_window_ns, (int64_t)params->win_half_ns,
+                                    (int64_t)params->floor_tau_ns});
+    *out = d.release();
+    return TRIG_OK;
+}
+
+extern "C" int64_t trig_detector_halo_ns(const trig_detector *d) { return d ? d->in_halo : -1; }
+
+extern "C" int trig_detector_dtmax(const trig_detector *d, int32_t *dt_out)
+{
+    if (!d || !dt_out) return fail(TRIG_EINVAL, "NULL argument");
+    cudaError_t e = cudaMemcpy(dt_out, d->dev.dt_exact, (size_t)d->n_pmt * d->n_pmt * 4, cudaMemcpyDeviceToHost);
+    if (e) return cuda_fail(e, "trig_detector_dtmax");
+    return TRIG_OK;
+}
+
+// ------------------------------------------------------------ batch plan
+
+static inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Plan {
+    BatchHeader hdr{};
+    std::vector<SliceDesc> desc;
+    size_t bytes = 0;
+    uint32_t max_pmt = 0;
+    bool smem_dt = true;
+};
+
+// Tile width W = 2^k ns: the largest power of two for which a tile plus its
+// two halos is expected to hold about fill% of the tile capacity.
+static uint32_t choose_wshift(const trig_detector *det, uint64_t n_hits, const TileConfig &cfg)
+{
+    const double span = (double)det->par.slice_ns + 2.0 * (double)det->in_halo;
+    const double rate = n_hits > 0 ? (double)n_hits / span : 1e-9;       // hits per ns
+    const double target = (double)cfg.cap * cfg.fill_pct / 100.0;
+    double w = target / rate - 2.0 * det->tile_halo;
+    uint32_t ws = 10;
+    while (ws < 30 && (double)((int64_t)1 << (ws + 1)) <= w) ++ws;
+    return ws;
+}
+
+static int make_plan(const trig_slice_dev *sl, uint32_t n, uintptr_t base, const TileConfig &cfg, Plan &pl,
+                     bool rows)
+{
+    if (!sl || n == 0) return fail(TRIG_EINVAL, "no slices");
+    pl.desc.assign(n, SliceDesc{});
+    size_t off = align256(sizeof(BatchHeader));
+    const size_t desc_off = off;
+    off += align256(sizeof(SliceDesc) * n);
+    uint32_t items = 0, chunks = 0;
+    pl.max_pmt = 0;
+    pl.smem_dt = true;
+    for (uint32_t s = 0; s < n; ++s) {
+        const trig_slice_dev &x = sl[s];
+        const trig_detector *det = x.det;
+        if (!det) return fail(TRIG_EINVAL, "slice without detector");
+        if (!x.pmt_off || !x.stats || (x.n_hits && !x.hits)) return fail(TRIG_EINVAL, "slice buffers are NULL");
+        if (x.n_hits > kMaxSliceHits) return fail(TRIG_EINVAL, "slice has too many hits (limit 2^32 - 16)");
+        if (((uintptr_t)x.hits & 15u) != 0) return fail(TRIG_EINVAL, "hits must be 16-byte aligned");
+        if ((x.trig_cap && !x.triggers) || (x.win_cap && !x.windows)) return fail(TRIG_EINVAL, "outputs are NULL");
+        if (x.t0_ns < -((int64_t)1 << 61) || x.t0_ns > ((int64_t)1 << 61)) return fail(TRIG_EINVAL, "t0 out of range");
+        SliceDesc &d = pl.desc[s];
+        const uint32_t P = det->n_pmt;
+        pl.max_pmt = std::max(pl.max_pmt, P);
+        if (P > kSmemDtMaxPmt) pl.smem_dt = false;
+        d.hits = x.hits;
+        d.pmt_off = x.pmt_off;
+        d.dt = det->dev.dt;
+        d.floor = det->dev.floor;
+        d.dmax_row = det->dev.dmax_row;
+        d.n_pmt = P;
+        d.halo = det->tile_halo;
+        d.q_seed = det->par.q_seed_adc;
+        d.tau = det->par.floor_tau_ns;
+        d.threshold = det->par.threshold;
+        d.win_half = det->par.win_half_ns;
+        d.t0 = x.t0_ns;
+        d.slice_ns = det->par.slice_ns;
+        d.in_lo = x.t0_ns - det->in_halo;
+        d.in_hi = x.t0_ns + det->par.slice_ns + det->in_halo;
+        d.n_hits = x.n_hits;
+        d.wshift = choose_wshift(det, x.n_hits, cfg);
+        const int64_t W = (int64_t)1 << d.wshift;
+        const uint64_t ng = x.n_hits ? (uint64_t)((det->par.slice_ns + W - 1) / W) : 0;
+        if (ng > 0x3fffffffu) return fail(TRIG_EINVAL, "too many tiles");
+        d.n_tiles = (uint32_t)ng;
+        d.item0 = items;
+        d.chunk0 = chunks;
+        items += d.n_tiles;
+        chunks += (uint32_t)((x.n_hits + kChunkHits - 1) / kChunkHits);
+        const size_t eb = (size_t)d.n_tiles * P * 4;
+        d.e_lo = reinterpret_cast<uint32_t *>(base + off);
+        off += align256(eb);
+        d.e_hi = reinterpret_cast<uint32_t *>(base + off);
+        off += align256(eb);
+        d.tile_nfired = reinterpret_cast<uint32_t *>(base + off);
+        off += align256((size_t)d.n_tiles * 4);
+        d.tile_rank = reinterpret_cast<uint32_t *>(base + off);
+        off += align256((size_t)d.n_tiles * 4);
+        d.tile_out = reinterpret_cast<uint32_t *>(base + off);
+        off += align256((size_t)d.n_tiles * 4);
+        d.stage = reinterpret_cast<trig_trigger *>(base + off);
+        off += align256((size_t)x.n_hits * sizeof(trig_trigger));
+        d.triggers = x.triggers;
+        d.trig_cap = x.trig_cap;
+        d.windows = x.windows;
+        d.win_cap = x.win_cap;
+        d.stats = x.stats;
+        d.dbg_merged = nullptr;
+        d.dbg_seedcnt = nullptr;
+        d.dbg_rank0 = 0;
+    }
+    (void)rows;
+    pl.hdr.n_slices = n;
+    pl.hdr.n_items = items;
+    pl.hdr.n_chunks = chunks;
+    pl.bytes = off;
+    (void)desc_off;
+    return TRIG_OK;
+}
+
+extern "C" size_t trig_batch_scratch_bytes(const trig_slice_dev *slices, uint32_t n_slices)
+{
+    Plan pl;
+    if (make_plan(slices, n_slices, 0, current_cfg(), pl, false)) return 0;
+    return pl.bytes;
+}
+
+static void pack_plan(const Plan &pl, std::vector<unsigned char> &buf)
+{
+    const size_t desc_off = align256(sizeof(BatchHeader));
+    buf.assign(desc_off + sizeof(SliceDesc) * pl.desc.size(), 0);
+    std::memcpy(buf.data(), &pl.hdr, sizeof(BatchHeader));
+    std::memcpy(buf.data() + desc_off, pl.desc.data(), sizeof(SliceDesc) * pl.desc.size());
+}
+
+// ------------------------------------------------------------ graph cache
+
+struct GraphKey {
+    cudaStream_t stream;
+    uintptr_t scratch;
+    uint32_t n_slices, max_pmt, cap, fill;
+    bool smem_dt;
+    bool operator<(const GraphKey &o) const
+    {
+        return std::tie(stream, scratch, n_slices, max_pmt, cap, fill, smem_dt) <
+               std::tie(o.stream, o.scratch, o.n_slices, o.max_pmt, o.cap, o.fill, o.smem_dt);
+    }
+};
+
+struct GraphEntry {
+    cudaGraphExec_t exec = nullptr;
+    unsigned char *pinned = nullptr;     // header + descriptors, copied by the graph's first node
+    size_t bytes = 0;
+    cudaEvent_t done = nullptr;          // last replay finished reading `pinned`
+    bool launched = false;
+};
+
+static std::mutex g_graph_mu;
+static std::map<GraphKey, GraphEntry> g_graphs;
+
+static int run_graph(const Plan &pl, void *scratch, cudaStream_t st, const TileConfig &cfg)
+{
+    GraphKey key{st, (uintptr_t)scratch, pl.hdr.n_slices, pl.max_pmt, cfg.cap, cfg.fill_pct, pl.smem_dt};
+    std::vector<unsigned char> host;
+    pack_plan(pl, host);
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    GraphEntry &ge = g_graphs[key];
+    cudaError_t e;
+    if (!ge.exec) {
+        if ((e = cudaMallocHost(&ge.pinned, host.size()))) return cuda_fail(e, "graph: pinned descriptors");
+        ge.bytes = host.size();
+        if ((e = cudaEventCreateWithFlags(&ge.done, cudaEventDisableTiming))) return cuda_fail(e, "graph: event");
+        std::memcpy(ge.pinned, host.data(), host.size());
+        // capture on a private stream (the caller's may be the legacy default
+        // stream, which cannot capture); replays go to the caller's stream
+        cudaGraph_t graph;
+        cudaStream_t cap;
+        if ((e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking))) return cuda_fail(e, "graph: stream");
+        if ((e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal))) {
+            cudaStreamDestroy(cap);
+            return cuda_fail(e, "graph: capture");
+        }
+        uint64_t nl = 0;
+        cudaError_t ce = cudaMemcpyAsync(scratch, ge.pinned, host.size(), cudaMemcpyHostToDevice, cap);
+        if (!ce)
+            ce = launch_batch(reinterpret_cast<BatchHeader *>(scratch),
+                              reinterpret_cast<SliceDesc *>((char *)scratch + align256(sizeof(BatchHeader))),
+                              pl.hdr.n_slices, pl.max_pmt, pl.smem_dt, cfg, cap, &nl, false);
+        e = cudaStreamEndCapture(cap, &graph);
+        cudaStreamDestroy(cap);
+        if (ce) return cuda_fail(ce, "graph: capture launch");
+        if (e) return cuda_fail(e, "graph: end capture");
+        e = cudaGraphInstantiate(&ge.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e) { ge.exec = nullptr; return cuda_fail(e, "graph: instantiate"); }
+    } else {
+        if (ge.launched && (e = cudaEventSynchronize(ge.done))) return cuda_fail(e, "graph: wait previous");
+        std::memcpy(ge.pinned, host.data(), host.size());
+    }
+    if ((e = cudaGraphLaunch(ge.exec, st))) return cuda_fail(e, "graph: launch");
+    if ((e = cudaEventRecord(ge.done, st))) return cuda_fail(e, "graph: record");
+    ge.launched = true;
+    g_launches += 7;
+    return TRIG_OK;
+}
+
+static int run_plan(const Plan &pl, void *scratch, size_t scratch_bytes, cudaStream_t st, uint32_t flags,
+                    const TileConfig &cfg, bool rows)
+{
+    if (!scratch || ((uintptr_t)scratch & 255u)) return fail(TRIG_EINVAL, "scratch must be 256-byte aligned device memory");
+    if (scratch_bytes < pl.bytes) return fail(TRIG_EINVAL, "scratch too small (see trig_batch_scratch_bytes)");
+    if ((flags & TRIG_RUN_GRAPH) && !rows) return run_graph(pl, scratch, st, cfg);
+    std::vector<unsigned char> host;
+    pack_plan(pl, host);
+    cudaError_t e = cudaMemcpyAsync(scratch, host.data(), host.size(), cudaMemcpyHostToDevice, st);
+    if (e) return cuda_fail(e, "copy descriptors");
+    uint64_t nl = 0;
+    e = launch_batch(reinterpret_cast<BatchHeader *>(scratch),
+                     reinterpret_cast<SliceDesc *>((char *)scratch + align256(sizeof(BatchHeader))), pl.hdr.n_slices,
+                     pl.max_pmt, pl.smem_dt, cfg, st, &nl, rows);
+    g_launches += nl;
+    if (e) return cuda_fail(e, "launch");
+    return TRIG_OK;
+}
+
+extern "C" int trig_batch_run(const trig_slice_dev *slices, uint32_t n_slices, void *scratch, size_t scratch_bytes,
+                              void *stream, uint32_t flags)
+{
+    const TileConfig cfg = current_cfg();
+    Plan pl;
+    int rc = make_plan(slices, n_slices, (uintptr_t)scratch, cfg, pl, false);
+    if (rc) return rc;
+    return run_plan(pl, scratch, scratch_bytes, (cudaStream_t)stream, flags, cfg, false);
+}
+
+extern "C" int trig_slice_rows(const trig_slice_dev *slice, trig_hit *merged_out, uint32_t *seedcnt_out,
+                               uint64_t *n_owned_out, void *scratch, size_t scratch_bytes, void *stream)
+{
+    if (!slice || !merged_out || !seedcnt_out || !n_owned_out) return fail(TRIG_EINVAL, "NULL argument");
+    const TileConfig cfg = current_cfg();
+    Plan pl;
+    int rc = make_plan(slice, 1, (uintptr_t)scratch, cfg, pl, true);
+    if (rc) return rc;
+    pl.desc[0].dbg_merged = merged_out;
+    pl.desc[0].dbg_seedcnt = seedcnt_out;
+    cudaStream_t st = (cudaStream_t)stream;
+    rc = run_plan(pl, scratch, scratch_bytes, st, 0, cfg, true);
+    if (rc) return rc;
+    SliceDesc back;
+    cudaError_t e = cudaMemcpyAsync(&back, (char *)scratch + align256(sizeof(BatchHeader)), sizeof(SliceDesc),
+                                    cudaMemcpyDeviceToHost, st);
+    if (!e) e = cudaStreamSynchronize(st);
+    if (e) return cuda_fail(e, "trig_slice_rows");
+    // k_rank0 stored the merged ranks of t0 and t0 + S
+    *n_owned_out = back.dbg_rank1 - back.dbg_rank0;
+    return TRIG_OK;
+}
+
+// ================================================================ engine
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Pending {
+    trig_detector *det = nullptr;
+    std::shared_ptr<DetQueue> q;
+    uint64_t id = 0;
+    int64_t t0 = 0;
+    unsigned char *pinned = nullptr;     // hits then pmt_off
+    size_t pinned_bytes = 0;
+    uint64_t n_hits = 0;
+    Clock::time_point t_submit;
+};
+
+struct PinnedPool {
+    std::mutex mu;
+    std::multimap<size_t, unsigned char *> free_blocks;
+    size_t used = 0, limit = (size_t)24 << 30;
+    unsigned char *get(size_t bytes, size_t *got)
+    {
+        size_t cls = 1;
+        while (cls < bytes) cls <<= 1;
+        if (cls < 4096) cls = 4096;
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = free_blocks.find(cls);
+        if (it != free_blocks.end()) {
+            unsigned char *p = it->second;
+            free_blocks.erase(it);
+            *got = cls;
+            return p;
+        }
+        if (used + cls > limit) {
+            // drop idle blocks of other sizes first
+            for (auto f = free_blocks.begin(); f != free_blocks.end() && used + cls > limit;) {
+                cudaFreeHost(f->second);
+                used -= f->first;
+                f = free_blocks.erase(f);
+            }
+            if (used + cls > limit) return nullptr;
+        }
+        void *p = nullptr;
+        if (cudaMallocHost(&p, cls) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return nullptr;
+        }
+        used += cls;
+        *got = cls;
+        return static_cast<unsigned char *>(p);
+    }
+    void put(unsigned char *p, size_t cls)
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        free_blocks.emplace(cls, p);
+    }
+};
+
+}  // namespace
+
+struct DetQueue {
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<uint64_t> order;                    // submitted ids, oldest first
+    std::map<uint64_t, trig_result *> done;
+    uint64_t in_flight = 0;
+};
+
+namespace {
+
+struct Slot {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev_stats = nullptr, ev_done = nullptr;
+    void *arena = nullptr;
+    size_t arena_bytes = 0;
+    unsigned char *bounce = nullptr;                // pinned: stats + outputs
+    size_t bounce_bytes = 0;
+    int state = 0;                                  // 0 idle, 1 computing, 2 copying back
+    std::vector<Pending> slices;
+    std::vector<size_t> out_off;                    // per slice offset into bounce
+    std::vector<trig_slice_dev> dev;
+    std::vector<uint64_t> trig_n, win_n;
+};
+
+constexpr int kSlots = 3;
+constexpr uint32_t kMaxBatchSlices = 256;
+
+struct Engine {
+    int device = 0;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<Pending> pending;
+    Slot slots[kSlots];
+    PinnedPool pool;
+    std::thread worker;
+    bool stop = false;
+    int mode = 1;
+    std::atomic<uint64_t> next_id{1};
+    std::atomic<uint64_t> batches{0}, completed{0};
+    bool started = false;
+    std::string fatal;
+
+    int start()
+    {
+        cudaGetDevice(&device);
+        for (auto &s : slots) {
+            cudaError_t e;
+            if ((e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking)) ||
+                (e = cudaEventCreateWithFlags(&s.ev_stats, cudaEventDisableTiming)) ||
+                (e = cudaEventCreateWithFlags(&s.ev_done, cudaEventDisableTiming)))
+                return cuda_fail(e, "engine start");
+        }
+        worker = std::thread([this] { run(); });
+        started = true;
+        return TRIG_OK;
+    }
+
+    void shutdown()
+    {
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            stop = true;
+        }
+        cv.notify_all();
+        if (worker.joinable()) worker.join();
+    }
+
+    void run();
+    bool launch_batch_on(Slot &s, std::vector<Pending> &batch);
+    void collect_stats(Slot &s);
+    void finish(Slot &s);
+};
+
+Engine *g_engine = nullptr;
+std::mutex g_engine_mu;
+
+void engine_atexit()
+{
+    std::lock_guard<std::mutex> lk(g_engine_mu);
+    if (g_engine) g_engine->shutdown();
+}
+
+Engine *engine()
+{
+    std::lock_guard<std::mutex> lk(g_engine_mu);
+    if (!g_engine) {
+        Engine *e = new Engine();
+        if (e->start()) {
+            delete e;
+            return nullptr;
+        }
+        g_engine = e;
+        std::atexit(engine_atexit);
+    }
+    return g_engine;
+}
+
+uint64_t win_cap_for(const trig_detector *det)
+{
+    const int64_t h = det->par.win_half_ns;
+    return (uint64_t)((det->par.slice_ns + 2 * h) / (2 * h + 2)) + 2;
+}
+
+// Device footprint of a batch in one arena: inputs, outputs, stats, scratch.
+struct ArenaLayout {
+    size_t bytes = 0;
+    std::vector<size_t> hits, offs, trig, win, stats;
+    size_t scratch = 0, scratch_bytes = 0;
+};
+
+}  // namespace
+
+bool Engine::launch_batch_on(Slot &s, std::vector<Pending> &batch)
+{
+    // layout of the arena
+    const uint32_t n = (uint32_t)batch.size();
+    std::vector<trig_slice_dev> dev(n);
+    ArenaLayout L;
+    size_t off = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+        const Pending &p = batch[i];
+        const uint32_t P = p.det->n_pmt;
+        L.hits.push_back(off);
+        off += align256(p.n_hits * sizeof(trig_hit));
+        L.offs.push_back(off);
+        off += align256((size_t)(P + 1) * 8);
+        L.trig.push_back(off);
+        off += align256(std::max<uint64_t>(p.n_hits, 1) * sizeof(trig_trigger));
+        L.win.push_back(off);
+        off += align256(win_cap_for(p.det) * sizeof(trig_window));
+        L.stats.push_back(off);
+        off += align256(sizeof(trig_slice_stats));
+        dev[i].det = p.det;
+        dev[i].n_hits = p.n_hits;
+        dev[i].t0_ns = p.t0;
+        dev[i].trig_cap = std::max<uint64_t>(p.n_hits, 1);
+        dev[i].win_cap = win_cap_for(p.det);
+        // temporary non-null pointers for planning (real ones set below)
+        dev[i].hits = reinterpret_cast<const trig_hit *>(256);
+        dev[i].pmt_off = reinterpret_cast<const uint64_t *>(256);
+        dev[i].triggers = reinterpret_cast<trig_trigger *>(256);
+        dev[i].windows = reinterpret_cast<trig_window *>(256);
+        dev[i].stats = reinterpret_cast<trig_slice_stats *>(256);
+    }
+    L.scratch = off;
+    L.scratch_bytes = trig_batch_scratch_bytes(dev.data(), n);
+    if (!L.scratch_bytes) {
+        fatal = g_last_error;
+        return false;
+    }
+    L.bytes = off + align256(L.scratch_bytes);
+    // grow the arena when needed, admitting by free device memory
+    if (s.arena_bytes < L.bytes) {
+        size_t free_b = 0, total_b = 0;
+        cudaMemGetInfo(&free_b, &total_b);
+        if (L.bytes + s.arena_bytes > free_b + ((size_t)256 << 20) * 0) {
+            if (s.arena && L.bytes <= free_b + s.arena_bytes) {
+                // fits after releasing the old arena
+            } else if (L.bytes > free_b + s.arena_bytes) {
+                return false;   // not now: wait for other slots to finish
+            }
+        }
+        if (s.arena) cudaFree(s.arena);
+        s.arena = nullptr;
+        s.arena_bytes = 0;
+        size_t want = L.bytes + L.bytes / 4;
+        if (cudaMalloc(&s.arena, want) != cudaSuccess) {
+            (void)cudaGetLastError();
+            if (cudaMalloc(&s.arena, L.bytes) != cudaSuccess) {
+                (void)cudaGetLastError();
+                return false;
+            }
+            want = L.bytes;
+        }
+        s.arena_bytes = want;
+    }
+    char *A = static_cast<char *>(s.arena);
+    size_t bounce_need = 0;
+    s.out_off.assign(n, 0);
+    for (uint32_t i = 0; i < n; ++i) {
+        dev[i].hits = reinterpret_cast<const trig_hit *>(A + L.hits[i]);
+        dev[i].pmt_off = reinterpret_cast<const uint64_t *>(A + L.offs[i]);
+        dev[i].triggers = reinterpret_cast<trig_trigger *>(A + L.trig[i]);
+        dev[i].windows = reinterpret_cast<trig_window *>(A + L.win[i]);
+        dev[i].stats = reinterpret_cast<trig_slice_stats *>(A + L.stats[i]);
+        s.out_off[i] = bounce_need;
+        bounce_need += align256(dev[i].trig_cap * sizeof(trig_trigger)) + align256(dev[i].win_cap * sizeof(trig_window));
+    }
+    const size_t stats_off = bounce_need;
+    bounce_need += align256(n * sizeof(trig_slice_stats));
+    if (s.bounce_bytes < bounce_need) {
+        if (s.bounce) cudaFreeHost(s.bounce);
+        s.bounce = nullptr;
+        s.bounce_bytes = 0;
+        void *p = nullptr;
+        if (cudaMallocHost(&p, bounce_need) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return false;
+        }
+        s.bounce = static_cast<unsigned char *>(p);
+        s.bounce_bytes = bounce_need;
+    }
+    // copies in, run, stats back
+    cudaError_t e = cudaSuccess;
+    for (uint32_t i = 0; i < n && !e; ++i) {
+        const Pending &p = batch[i];
+        if (p.n_hits)
+            e = cudaMemcpyAsync((void *)dev[i].hits, p.pinned, p.n_hits * sizeof(trig_hit), cudaMemcpyHostToDevice,
+                                s.stream);
+        if (!e)
+            e = cudaMemcpyAsync((void *)dev[i].pmt_off, p.pinned + p.n_hits * sizeof(trig_hit),
+                                (size_t)(p.det->n_pmt + 1) * 8, cudaMemcpyHostToDevice, s.stream);
+    }
+    if (e) {
+        fatal = cudaGetErrorString(e);
+        (void)cudaGetLastError();
+        return false;
+    }
+    const uint32_t flags = (mode == 1) ? TRIG_RUN_GRAPH : 0u;
+    int rc = trig_batch_run(dev.data(), n, A + L.scratch, L.scratch_bytes, s.stream, flags);
+    if (rc) {
+        fatal = g_last_error;
+        return false;
+    }
+    for (uint32_t i = 0; i < n && !e; ++i)
+        e = cudaMemcpyAsync(s.bounce + stats_off + i * sizeof(trig_slice_stats), dev[i].stats,
+                            sizeof(trig_slice_stats), cudaMemcpyDeviceToHost, s.stream);
+    if (!e) e = cudaEventRecord(s.ev_stats, s.stream);
+    if (e) {
+        fatal = cudaGetErrorString(e);
+        (void)cudaGetLastError();
+        return false;
+    }
+    s.slices = std::move(batch);
+    s.dev = std::move(dev);
+    s.state = 1;
+    s.trig_n.assign(n, 0);
+    s.win_n.assign(n, 0);
+    s.out_off.push_back(stats_off);   // last entry: stats
+    batches++;
+    return true;
+}
+
+void Engine::collect_stats(Slot &s)
+{
+    const uint32_t n = (uint32_t)s.slices.size();
+    const size_t stats_off = s.out_off[n];
+    const trig_slice_stats *st = reinterpret_cast<const trig_slice_stats *>(s.bounce + stats_off);
+    cudaError_t e = cudaSuccess;
+    for (uint32_t i = 0; i < n && !e; ++i) {
+        uint64_t nt = std::min<uint64_t>(st[i].n_triggers, s.dev[i].trig_cap);
+        uint64_t nw = std::min<uint64_t>(st[i].n_windows, s.dev[i].win_cap);
+        s.trig_n[i] = nt;
+        s.win_n[i] = nw;
+        unsigned char *dst = s.bounce + s.out_off[i];
+        if (nt) e = cudaMemcpyAsync(dst, s.dev[i].triggers, nt * sizeof(trig_trigger), cudaMemcpyDeviceToHost, s.stream);
+        if (!e && nw)
+            e = cudaMemcpyAsync(dst + align256(s.dev[i].trig_cap * sizeof(trig_trigger)), s.dev[i].windows,
+                                nw * sizeof(trig_window), cudaMemcpyDeviceToHost, s.stream);
+    }
+    if (!e) e = cudaEventRecord(s.ev_done, s.stream);
+    if (e) {
+        fatal = cudaGetErrorString(e);
+        (void)cudaGetLastError();
+    }
+    s.state = 2;
+}
+
+void Engine::finish(Slot &s)
+{
+    const uint32_t n = (uint32_t)s.slices.size();
+    const size_t stats_off = s.out_off[n];
+    const trig_slice_stats *st = reinterpret_cast<const trig_slice_stats *>(s.bounce + stats_off);
+    const auto now = Clock::now();
+    for (uint32_t i = 0; i < n; ++i) {
+        Pending &p = s.slices[i];
+        trig_result *r = static_cast<trig_result *>(std::calloc(1, sizeof(trig_result)));
+        if (r) {
+            r->slice_id = p.id;
+            r->t0_ns = p.t0;
+            r->status = st[i].status;
+            r->flags = st[i].flags;
+            r->n_hits = st[i].n_hits;
+            r->n_seeds = st[i].n_seeds;
+            r->n_triggers = s.trig_n[i];
+            r->n_windows = s.win_n[i];
+            if (r->n_triggers) {
+                r->triggers = static_cast<trig_trigger *>(std::malloc(r->n_triggers * sizeof(trig_trigger)));
+                if (r->triggers) std::memcpy(r->triggers, s.bounce + s.out_off[i], r->n_triggers * sizeof(trig_trigger));
+            }
+            if (r->n_windows) {
+                r->windows = static_cast<trig_window *>(std::malloc(r->n_windows * sizeof(trig_window)));
+                if (r->windows)
+                    std::memcpy(r->windows, s.bounce + s.out_off[i] + align256(s.dev[i].trig_cap * sizeof(trig_trigger)),
+                                r->n_windows * sizeof(trig_window));
+            }
+            if ((r->n_triggers && !r->triggers) || (r->n_windows && !r->windows)) r->status = TRIG_ENOMEM;
+            r->latency_ns = std::chrono::duration_cast<std::chrono::nanoseconds>(now - p.t_submit).count();
+        }
+        pool.put(p.pinned, p.pinned_bytes);
+        {
+            std::lock_guard<std::mutex> lk(p.q->mu);
+            p.q->done[p.id] = r;
+            p.q->in_flight--;
+        }
+        p.q->cv.notify_all();
+        completed++;
+    }
+    s.slices.clear();
+    s.state = 0;
+}
+
+void Engine::run()
+{
+    cudaSetDevice(device);
+    std::unique_lock<std::mutex> lk(mu);
+    for (;;) {
+        bool busy = false;
+        for (auto &s : slots) busy |= s.state != 0;
+        if (stop && !busy && pending.empty()) break;
+        if (!busy && pending.empty()) {
+            cv.wait(lk);
+            continue;
+        }
+        // progress in-flight slots
+        lk.unlock();
+        for (auto &s : slots) {
+            if (s.state == 1 && cudaEventQuery(s.ev_stats) == cudaSuccess) collect_stats(s);
+            if (s.state == 2 && cudaEventQuery(s.ev_done) == cudaSuccess) finish(s);
+        }
+        (void)cudaGetLastError();
+        lk.lock();
+        // admit a new batch into an idle slot
+        bool launched = false;
+        if (!pending.empty()) {
+            for (auto &s : slots) {
+                if (s.state != 0) continue;
+                std::vector<Pending> batch;
+                const uint32_t take = (mode == 1) ? kMaxBatchSlices : 1u;
+                while (!pending.empty() && batch.size() < take) {
+                    batch.push_back(std::move(pending.front()));
+                    pending.pop_front();
+                }
+                lk.unlock();
+                bool ok = launch_batch_on(s, batch);
+                lk.lock();
+                if (!ok) {
+                    bool others = false;
+                    for (auto &o : slots) others |= o.state != 0;
+                    if (others && fatal.empty()) {
+                        // admission refused for now (memory): put back, retry later
+                        for (auto it = batch.rbegin(); it != batch.rend(); ++it) pending.push_front(std::move(*it));
+                    } else {
+                        // cannot run at all: fail these slices
+                        for (auto &p : batch) {
+                            trig_result *r = static_cast<trig_result *>(std::calloc(1, sizeof(trig_result)));
+                            if (r) {
+                                r->slice_id = p.id;
+                                r->t0_ns = p.t0;
+                                r->status = fatal.empty() ? TRIG_ENOMEM : TRIG_EDEVICE;
+                            }
+                            pool.put(p.pinned, p.pinned_bytes);
+                            std::lock_guard<std::mutex> ql(p.q->mu);
+                            p.q->done[p.id] = r;
+                            p.q->in_flight--;
+                            p.q->cv.notify_all();
+                        }
+                        fatal.clear();
+                    }
+                    break;
+                }
+                launched = true;
+                break;
+            }
+        }
+        if (!launched) cv.wait_for(lk, std::chrono::microseconds(20));
+    }
+}
+
+extern "C" int trig_engine_set_mode(int mode)
+{
+    if (mode != 0 && mode != 1) return fail(TRIG_EINVAL, "mode must be 0 (plain) or 1 (batched)");
+    Engine *e = engine();
+    if (!e) return TRIG_EDEVICE;
+    std::lock_guard<std::mutex> lk(e->mu);
+    e->mode = mode;
+    return TRIG_OK;
+}
+
+extern "C" int trig_engine_stats(uint64_t *batches, uint64_t *slices)
+{
+    Engine *e = engine();
+    if (!e) return TRIG_EDEVICE;
+    if (batches) *batches = e->batches.load();
+    if (slices) *slices = e->completed.load();
+    return TRIG_OK;
+}
+
+extern "C" int trig_submit_slice(trig_detector *det, int64_t t0, const trig_hit *hits, const uint64_t *pmt_off,
+                                 int is_continuation, uint64_t *slice_id_out)
+{
+    if (!det || !pmt_off) return fail(TRIG_EINVAL, "NULL argument");
+    if (is_continuation) return fail(TRIG_EINVAL, "is_continuation: submissions carry their own halos");
+    const uint32_t P = det->n_pmt;
+    if (pmt_off[0] != 0) return fail(TRIG_EINVAL, "pmt_off[0] must be 0");
+    for (uint32_t p = 0; p < P; ++p)
+        if (pmt_off[p + 1] < pmt_off[p]) return fail(TRIG_EINVAL, "pmt_off must be non-decreasing");
+    const uint64_t n = pmt_off[P];
+    if (n && !hits) return fail(TRIG_EINVAL, "hits is NULL");
+    if (n > kMaxSliceHits) return fail(TRIG_EINVAL, "too many hits in one slice");
+    Engine *e = engine();
+    if (!e) return fail(TRIG_EDEVICE, "engine failed to start: " + g_last_error);
+    Pending p;
+    p.det = det;
+    if (!det->q) det->q = std::make_shared<DetQueue>();
+    p.q = det->q;
+    p.t0 = t0;
+    p.n_hits = n;
+    const size_t bytes = n * sizeof(trig_hit) + (size_t)(P + 1) * 8;
+    p.pinned = e->pool.get(bytes, &p.pinned_bytes);
+    if (!p.pinned) return fail(TRIG_EAGAIN, "staging memory full; poll results and retry");
+    if (n) std::memcpy(p.pinned, hits, n * sizeof(trig_hit));
+    std::memcpy(p.pinned + n * sizeof(trig_hit), pmt_off, (size_t)(P + 1) * 8);
+    p.t_submit = Clock::now();
+    p.id = e->next_id++;
+    {
+        std::lock_guard<std::mutex> lk(p.q->mu);
+        p.q->order.push_back(p.id);
+        p.q->in_flight++;
+    }
+    if (slice_id_out) *slice_id_out = p.id;
+    {
+        std::lock_guard<std::mutex> lk(e->mu);
+        e->pending.push_back(std::move(p));
+    }
+    e->cv.notify_all();
+    return TRIG_OK;
+}
+
+extern "C" int trig_poll(trig_detector *det, int timeout_ms, trig_result **out)
+{
+    if (!det || !out) return fail(TRIG_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (!det->q) return fail(TRIG_EAGAIN, "nothing submitted");
+    DetQueue &q = *det->q;
+    std::unique_lock<std::mutex> lk(q.mu);
+    auto ready = [&] { return !q.order.empty() && q.done.count(q.order.front()); };
+    if (!ready()) {
+        if (timeout_ms == 0) return fail(TRIG_EAGAIN, "no result ready");
+        if (timeout_ms < 0) q.cv.wait(lk, ready);
+        else if (!q.cv.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready))
+            return fail(TRIG_EAGAIN, "no result ready");
+    }
+    uint64_t id = q.order.front();
+    q.order.pop_front();
+    *out = q.done[id];
+    q.done.erase(id);
+    if (!*out) return fail(TRIG_ENOMEM, "result allocation failed");
+    return TRIG_OK;
+}
+
+extern "C" void trig_result_free(trig_result *r)
+{
+    if (!r) return;
+    std::free(r->triggers);
+    std::free(r->windows);
+    std::free(r);
+}
+
+extern "C" int trig_destroy(trig_detector *det)
+{
+    if (!det) return TRIG_OK;
+    if (det->q) {
+        std::unique_lock<std::mutex> lk(det->q->mu);
+        det->q->cv.wait(lk, [&] { return det->q->in_flight == 0; });
+        for (auto &kv : det->q->done) trig_result_free(kv.second);
+        det->q->done.clear();
+    }
+    cudaDeviceSynchronize();
+    free_det_dev(det);
+    delete det;
+    return TRIG_OK;
+}

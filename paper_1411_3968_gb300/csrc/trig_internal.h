@@ -1,0 +1,91 @@
+// trig_internal.h -- structures shared by the sm_103a kernels (trig_kernels.cu)
+// and the host runtime (trig_engine.cpp).  Not part of the public ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "trig.h"
+
+namespace trig {
+
+// Limits of this implementation.
+constexpr uint32_t kMaxPmt = 4096;          // PMTs per detector
+constexpr uint32_t kSmemDtMaxPmt = 96;      // dt table lives in shared memory up to this P
+constexpr uint64_t kMaxSliceHits = 0xFFFFFFF0ull;
+
+// Detector tables resident on the device (owned by trig_detector).
+struct DetDev {
+    uint16_t *dt;         // [P*P] min(dt_max, W), row p_s
+    int32_t *dt_exact;    // [P*P] exact dt_max
+    uint16_t *floor;      // [P] dense floor index
+    uint16_t *dmax_row;   // [P] max_q min(dt_max[p][q], W)
+};
+
+// Per-slice descriptor in device scratch, written by the host each run.
+struct SliceDesc {
+    const trig_hit *hits;
+    const uint64_t *pmt_off;
+    const uint16_t *dt;
+    const uint16_t *floor;
+    const uint16_t *dmax_row;
+    uint32_t n_pmt;
+    uint32_t halo;          // tile halo H = max(max dmax_row, floor_tau)
+    uint32_t q_seed;
+    uint32_t tau;
+    uint32_t threshold;
+    uint32_t win_half;
+    int64_t t0;
+    int64_t slice_ns;
+    int64_t in_lo, in_hi;   // accepted hit times [in_lo, in_hi)
+    uint64_t n_hits;
+    uint32_t wshift;        // tile width W = 1 << wshift
+    uint32_t n_tiles;       // NG
+    uint32_t item0;         // first work item (tile) of this slice
+    uint32_t chunk0;        // first structure-pass chunk of this slice
+    uint32_t *e_lo;         // [NG][P] first hit index with t >= B_g - H
+    uint32_t *e_hi;         // [NG][P] first hit index with t >= B_{g+1} + H
+    trig_trigger *stage;    // [n_hits] fired seeds at their merged rank
+    uint32_t *tile_nfired;  // [NG]
+    uint32_t *tile_rank;    // [NG] merged rank of the tile's first core hit
+    uint32_t *tile_out;     // [NG] exclusive prefix of tile_nfired
+    trig_trigger *triggers;
+    uint64_t trig_cap;
+    trig_window *windows;
+    uint64_t win_cap;
+    trig_slice_stats *stats;
+    trig_hit *dbg_merged;   // optional row outputs, indexed by merged rank - rank(t0)
+    uint32_t *dbg_seedcnt;
+    uint64_t dbg_rank0;     // merged rank of the first owned hit (row outputs only)
+    uint64_t dbg_rank1;     // merged rank of the first hit after the owned range
+};
+
+struct BatchHeader {
+    uint32_t n_slices;
+    uint32_t n_items;       // total tiles
+    uint32_t n_chunks;      // total structure-pass chunks
+    uint32_t err;
+    uint32_t queue;         // tile work queue head
+    uint32_t pad[3];
+};
+
+constexpr uint32_t kChunkHits = 4096;       // structure-pass chunk
+
+// Kernel launch helpers implemented in trig_kernels.cu.
+cudaError_t launch_dtmax(const int32_t *xyz, uint32_t n_pmt, uint32_t tol, uint32_t n_num, uint32_t n_den,
+                         uint32_t corr, int32_t *dt_exact, uint16_t *dt, uint16_t *dmax_row, cudaStream_t st);
+
+struct TileConfig {
+    uint32_t cap;       // hits per shared-memory tile
+    uint32_t fill_pct;  // target fill of a tile (percent of cap)
+};
+
+// Enqueues the batch pipeline; header/desc already copied to device scratch.
+cudaError_t launch_batch(BatchHeader *d_hdr, SliceDesc *d_desc, uint32_t n_slices, uint32_t max_pmt,
+                         bool any_smem_dt, const TileConfig &cfg, cudaStream_t st, uint64_t *launches,
+                         bool rows);
+
+int device_sm_count();
+
+}  // namespace trig

@@ -1,0 +1,95 @@
+"""Device-resident batches: PyTorch holds the device memory and the stream,
+libtrig.so does all the work (trig_batch_run / trig_slice_rows)."""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import HIT_DTYPE, STATS_DTYPE, TRIGGER_DTYPE, WINDOW_DTYPE
+
+
+def _dev_bytes(nbytes: int, device) -> torch.Tensor:
+    # 256-byte aligned allocation (the caching allocator aligns to >= 512 B)
+    return torch.empty(max(int(nbytes), 16), dtype=torch.uint8, device=device)
+
+
+def _to_dev(a: np.ndarray, device) -> torch.Tensor:
+    t = torch.from_numpy(np.ascontiguousarray(a).view(np.uint8).reshape(-1))
+    out = _dev_bytes(t.numel(), device)
+    if t.numel():
+        out[: t.numel()].copy_(t)
+    return out
+
+
+@dataclass
+class SliceIn:
+    det: "_lib.Detector"
+    t0: int
+    hits: np.ndarray        # HIT_DTYPE, grouped by PMT
+    pmt_off: np.ndarray     # uint64, n_pmt + 1
+
+
+class DeviceBatch:
+    """Inputs resident in HBM, outputs and scratch pre-allocated; run()
+    enqueues the whole hot path for all slices on the current stream."""
+
+    def __init__(self, slices: list[SliceIn], device="cuda", trig_cap: int | None = None):
+        self.slices = slices
+        self.device = torch.device(device)
+        self.hits = [_to_dev(s.hits, self.device) for s in slices]
+        self.offs = [_to_dev(np.asarray(s.pmt_off, np.uint64), self.device) for s in slices]
+        self.trig_cap = [max(1, len(s.hits) if trig_cap is None else trig_cap) for s in slices]
+        self.win_cap = [_lib.win_cap_for(s.det.params) for s in slices]
+        self.trig = [_dev_bytes(c * TRIGGER_DTYPE.itemsize, self.device) for c in self.trig_cap]
+        self.win = [_dev_bytes(c * WINDOW_DTYPE.itemsize, self.device) for c in self.win_cap]
+        self.stats = _dev_bytes(len(slices) * STATS_DTYPE.itemsize, self.device)
+        self.descs = []
+        for i, s in enumerate(slices):
+            self.descs.append(_lib.slice_dev(s.det, self.hits[i].data_ptr(), self.offs[i].data_ptr(), len(s.hits),
+                                             int(s.t0), self.trig[i].data_ptr(), self.trig_cap[i],
+                                             self.win[i].data_ptr(), self.win_cap[i],
+                                             self.stats.data_ptr() + i * STATS_DTYPE.itemsize))
+        self.scratch_bytes = _lib.trig_batch_scratch_bytes(self.descs)
+        self.scratch = _dev_bytes(self.scratch_bytes + 256, self.device)
+        self.n_hits = sum(len(s.hits) for s in slices)
+        self.input_bytes = sum(s.hits.nbytes + np.asarray(s.pmt_off).nbytes for s in slices)
+
+    def run(self, graph: bool = False, stream=None) -> None:
+        st = stream if stream is not None else torch.cuda.current_stream(self.device)
+        _lib.trig_batch_run(self.descs, self.scratch.data_ptr(), self.scratch_bytes, st.cuda_stream,
+                            _lib.TRIG_RUN_GRAPH if graph else 0)
+
+    def run_each(self, stream=None) -> None:
+        """Plain per-slice launches: one launch sequence per slice."""
+        st = stream if stream is not None else torch.cuda.current_stream(self.device)
+        for d in self.descs:
+            _lib.trig_batch_run([d], self.scratch.data_ptr(), self.scratch_bytes, st.cuda_stream, 0)
+
+    def results(self):
+        torch.cuda.synchronize(self.device)
+        stats = np.frombuffer(self.stats.cpu().numpy().tobytes()[: len(self.slices) * STATS_DTYPE.itemsize],
+                              STATS_DTYPE).copy()
+        out = []
+        for i in range(len(self.slices)):
+            nt = min(int(stats[i]["n_triggers"]), self.trig_cap[i])
+            nw = min(int(stats[i]["n_windows"]), self.win_cap[i])
+            trig = np.frombuffer(self.trig[i][: nt * TRIGGER_DTYPE.itemsize].cpu().numpy().tobytes(), TRIGGER_DTYPE)
+            win = np.frombuffer(self.win[i][: nw * WINDOW_DTYPE.itemsize].cpu().numpy().tobytes(), WINDOW_DTYPE)
+            out.append((stats[i], trig.copy(), win.copy()))
+        return out
+
+    def rows(self, i: int):
+        """Merged owned hits of slice i and their seed counts (0xFFFFFFFF: not a seed)."""
+        s = self.slices[i]
+        n = max(len(s.hits), 1)
+        merged = _dev_bytes(n * HIT_DTYPE.itemsize, self.device)
+        seedcnt = _dev_bytes(n * 4, self.device)
+        st = torch.cuda.current_stream(self.device)
+        n_owned = _lib.trig_slice_rows(self.descs[i], merged.data_ptr(), seedcnt.data_ptr(), self.scratch.data_ptr(),
+                                       self.scratch_bytes, st.cuda_stream)
+        m = np.frombuffer(merged[: n_owned * HIT_DTYPE.itemsize].cpu().numpy().tobytes(), HIT_DTYPE).copy()
+        c = np.frombuffer(seedcnt[: n_owned * 4].cpu().numpy().tobytes(), np.uint32).copy()
+        return m, c

@@ -1,0 +1,339 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Timestamps and dt_max are integer ns, so trigger lists, counts and windows
+must match bit-exactly; the merged order and seed counts are compared row by
+row.  Inputs are seeded synthetic workloads (workload/) and hand-built
+slices at every boundary of the trigger rule.
+"""
+import glob
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workload
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+GEOM = {"nemo32": workload.nemo_tower, "km3it84": workload.km3_tower, "array2688": workload.tower_array}
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import torch
+    import paper_1411_3968_gb300 as p
+    from paper_1411_3968_gb300 import build
+    build.build()
+    p.load()
+    torch.cuda.init()
+    return p
+
+
+def _det(pkg, geom, par):
+    return pkg.Detector(geom.xyz_mm, geom.floor_id, par)
+
+
+def _run(pkg, det, subs, graph=False, each=False):
+    from paper_1411_3968_gb300.runner import DeviceBatch, SliceIn
+    b = DeviceBatch([SliceIn(det if not isinstance(det, list) else det[i], t0, s.hits, s.pmt_off)
+                     for i, (t0, s) in enumerate(subs)])
+    if each:
+        b.run_each()
+    else:
+        b.run(graph=graph)
+    return b, b.results()
+
+
+def _assert_same(res, ref, ctx=""):
+    stats, trig, win = res
+    assert int(stats["status"]) == 0, (ctx, stats)
+    assert int(stats["n_seeds"]) == len(ref.seeds), ctx
+    assert len(trig) == len(ref.triggers), (ctx, len(trig), len(ref.triggers))
+    for f in ("t", "pmt", "charge", "count"):
+        assert np.array_equal(trig[f], ref.triggers[f]), (ctx, f)
+    assert len(win) == len(ref.windows), ctx
+    for f in ("lo", "hi", "n_hits", "n_triggers"):
+        assert np.array_equal(win[f], ref.windows[f]), (ctx, f)
+
+
+def _subs_from_run(full, t0s, slice_ns, halo=3000):
+    return [(t0, workload.cut(full, t0 - halo, t0 + slice_ns + halo)) for t0 in t0s]
+
+
+def _stream_from_hits(hits, n_pmt):
+    h = np.sort(hits, order=["pmt", "t", "charge"], kind="stable")
+    off = np.zeros(n_pmt + 1, np.uint64)
+    np.cumsum(np.bincount(h["pmt"], minlength=n_pmt), out=off[1:])
+    return workload.Stream(h, off)
+
+
+# --------------------------------------------------------------------- dt_max
+
+@pytest.mark.parametrize("name", ["nemo32", "km3it84", "array2688"])
+def test_dtmax_table_bit_exact(pkg, params, name):
+    g = GEOM[name]()
+    d = _det(pkg, g, params)
+    assert np.array_equal(d.dtmax(), oracle.dtmax(g.xyz_mm, params))
+    d.close()
+
+
+def test_dtmax_random_geometry(pkg, params):
+    rng = np.random.Generator(np.random.PCG64(12))
+    xyz = rng.integers(-2_000_000, 2_000_000, size=(600, 3)).astype(np.int32)
+    xyz[100:120] = xyz[0]
+    fl = np.arange(600, dtype=np.uint32)
+    for par in (params, dict(params, n_num=1, n_den=1, tol_ns=0), dict(params, n_num=9999, n_den=7, tol_ns=3)):
+        d = pkg.Detector(xyz, fl, par)
+        assert np.array_equal(d.dtmax(), oracle.dtmax(xyz, par))
+        d.close()
+
+
+# --------------------------------------------------------------------- golden
+
+@pytest.mark.parametrize("path", sorted(glob.glob(os.path.join(GOLDEN, "*.json"))), ids=os.path.basename)
+def test_golden_fixtures_on_gpu(pkg, params, path):
+    fx = json.load(open(path))
+    g = GEOM[fx["geometry"]]()
+    par = dict(params)
+    par.update(fx["params"])
+    hits = np.zeros(len(fx["hits"]), workload.HIT_DTYPE)
+    for i, (t, p, q) in enumerate(fx["hits"]):
+        hits[i] = (t, p, q, 0)
+    full = _stream_from_hits(hits, g.n_pmt)
+    d = _det(pkg, g, par)
+    _, res = _run(pkg, d, _subs_from_run(full, fx["slices"], par["slice_ns"]))
+    ref = oracle.run(g.xyz_mm, g.floor_id, par, hits, fx["slices"])
+    for r, o, exp in zip(res, ref, fx["expected"]):
+        _assert_same(r, o, path)
+        assert [tuple(int(x[f]) for f in ("t", "pmt", "charge", "count")) for x in r[1]] == \
+            [tuple(x) for x in exp["triggers"]]
+    d.close()
+
+
+# --------------------------------------------------------------- random tiny
+
+@pytest.mark.parametrize("case", range(8))
+def test_random_dense_slices(pkg, params, case):
+    rng = np.random.Generator(np.random.PCG64(500 + case))
+    g = [workload.nemo_tower, workload.km3_tower][case % 2]()
+    par = dict(params)
+    par["slice_ns"] = int(rng.choice([20_000, 100_000, 1_000_000]))
+    par["threshold"] = int(rng.integers(1, 7))
+    par["q_seed_adc"] = int(rng.choice([300, 150, 65535]))
+    if case >= 6:
+        par.update(corr_window_ns=700, win_half_ns=int(rng.integers(0, 2000)), floor_tau_ns=int(rng.integers(0, 60)))
+    t0 = 5_000_000
+    n = int(rng.integers(200, 4000))
+    t = rng.integers(t0 - 3000, t0 + 2 * par["slice_ns"] + 3000, n)
+    t[: n // 4] = t[n // 4: 2 * (n // 4)] + rng.integers(-30, 31, n // 4)
+    t[-20:] = t[-40:-20]
+    hits = np.zeros(n, workload.HIT_DTYPE)
+    hits["t"] = t
+    hits["pmt"] = rng.integers(0, g.n_pmt, n)
+    hits["charge"] = rng.integers(1, 500, n)
+    t0s = [t0, t0 + par["slice_ns"]]
+    full = _stream_from_hits(hits, g.n_pmt)
+    halo = max(par["corr_window_ns"], par["win_half_ns"], par["floor_tau_ns"])
+    d = _det(pkg, g, par)
+    _, res = _run(pkg, d, _subs_from_run(full, t0s, par["slice_ns"], halo))
+    ref = oracle.run(g.xyz_mm, g.floor_id, par, hits, t0s)
+    for k, (r, o) in enumerate(zip(res, ref)):
+        _assert_same(r, o, f"case {case} slice {k}")
+    d.close()
+
+
+# ------------------------------------------------------------------ configs
+
+def test_nemo_config(pkg, params):
+    wl = workload.cfg_nemo()
+    g = wl.detectors[0]
+    d = _det(pkg, g, params)
+    b, res = _run(pkg, d, [(s.t0, s.stream) for s in wl.submissions])
+    ref = oracle.run(g.xyz_mm, g.floor_id, params, wl.runs[0].hits, wl.run_slices[0])
+    _assert_same(res[0], ref[0], "nemo")
+    # row level: merged order (k-way merge), seeds and their counts
+    merged, seedcnt = b.rows(0)
+    own = wl.runs[0].hits
+    own = own[(own["t"] >= wl.run_slices[0][0]) & (own["t"] < wl.run_slices[0][0] + params["slice_ns"])]
+    om = oracle.merge(own)
+    for f in ("t", "pmt", "charge"):
+        assert np.array_equal(merged[f], om[f]), f
+    is_seed = seedcnt != 0xFFFFFFFF
+    assert is_seed.sum() == len(ref[0].seeds)
+    assert np.array_equal(merged["t"][is_seed], ref[0].seeds["t"])
+    assert np.array_equal(seedcnt[is_seed], ref[0].seeds["count"])
+    d.close()
+
+
+def test_km3_config_five_slices_with_bursts(pkg, params):
+    wl = workload.cfg_km3()
+    g = wl.detectors[0]
+    d = _det(pkg, g, params)
+    subs = [(s.t0, s.stream) for s in wl.submissions]
+    _, res = _run(pkg, d, subs)
+    ref = oracle.run(g.xyz_mm, g.floor_id, params, wl.runs[0].hits, wl.run_slices[0])
+    for k in range(len(subs)):
+        _assert_same(res[k], ref[k], f"km3 slice {k}")
+    # plain per-slice launches and the graph replay give the same
+    _, res_each = _run(pkg, d, subs, each=True)
+    _, res_graph = _run(pkg, d, subs, graph=True)
+    for k in range(len(subs)):
+        _assert_same(res_each[k], ref[k], f"km3 each {k}")
+        _assert_same(res_graph[k], ref[k], f"km3 graph {k}")
+    d.close()
+
+
+def test_scaled_array_config(pkg, params):
+    wl = workload.cfg_scaled()
+    g = wl.detectors[0]
+    d = _det(pkg, g, params)
+    _, res = _run(pkg, d, [(s.t0, s.stream) for s in wl.submissions])
+    ref = oracle.run(g.xyz_mm, g.floor_id, params, wl.runs[0].hits, wl.run_slices[0])
+    _assert_same(res[0], ref[0], "scaled")
+    d.close()
+
+
+def test_batched_config_sampled(pkg, params):
+    """All 64 slices in one launch; 8 of them checked in full against the
+    oracle, the rest by invariants (status, monotone counts, windows)."""
+    wl = workload.cfg_batched()
+    dets = [_det(pkg, g, params) for g in wl.detectors]
+    subs = [(s.t0, s.stream) for s in wl.submissions]
+    from paper_1411_3968_gb300.runner import DeviceBatch, SliceIn
+    b = DeviceBatch([SliceIn(dets[s.det_index], s.t0, s.stream.hits, s.stream.pmt_off) for s in wl.submissions])
+    b.run(graph=True)
+    res = b.results()
+    pick = [0, 7, 13, 21, 30, 42, 55, 63]
+    for k in pick:
+        s = wl.submissions[k]
+        g = wl.detectors[s.det_index]
+        ref = oracle.run(g.xyz_mm, g.floor_id, params, s.stream.hits, [s.t0])[0]
+        _assert_same(res[k], ref, f"batched slice {k}")
+    for k, (stats, trig, win) in enumerate(res):
+        assert int(stats["status"]) == 0
+        assert np.all(np.diff(trig["t"]) >= 0)
+        assert np.all(trig["count"] >= params["threshold"])
+        assert int(win["n_triggers"].sum()) == len(trig)
+        assert np.all(win["lo"][1:] > win["hi"][:-1] + 1)
+    for d in dets:
+        d.close()
+
+
+# ---------------------------------------------------------- tiles and edges
+
+def test_result_independent_of_tile_configuration(pkg, params):
+    wl = workload.cfg_km3()
+    g = wl.detectors[0]
+    d = _det(pkg, g, params)
+    subs = [(s.t0, s.stream) for s in wl.submissions[:2]]
+    ref = oracle.run(g.xyz_mm, g.floor_id, params, wl.runs[0].hits, wl.run_slices[0][:2])
+    old = pkg.trig_get_tile_config()
+    try:
+        for cap, fill in ((2048, 30), (2048, 90), (4096, 15), (4096, 60), (4096, 95)):
+            pkg.trig_set_tile_config(cap, fill)
+            _, res = _run(pkg, d, subs)
+            for k in range(2):
+                _assert_same(res[k], ref[k], f"cap {cap} fill {fill} slice {k}")
+    finally:
+        pkg.trig_set_tile_config(*old)
+    d.close()
+
+
+def test_dense_burst_takes_split_path(pkg, params):
+    """A burst far above the tile's planned density: tiles overflow and
+    are split; results stay exact."""
+    g = workload.nemo_tower()
+    par = dict(params, slice_ns=2_000_000)
+    t0 = workload.T_ORIGIN_NS
+    st = workload.gen_stream(g, t0 - 3000, t0 + par["slice_ns"] + 3000, 50e3, seed=3, stream=1)
+    rng = np.random.Generator(np.random.PCG64(9))
+    burst = np.zeros(30_000, workload.HIT_DTYPE)
+    burst["t"] = rng.integers(t0 + 700_000, t0 + 760_000, len(burst))
+    burst["pmt"] = rng.integers(0, 32, len(burst))
+    burst["charge"] = rng.integers(50, 400, len(burst))
+    hits = np.concatenate([st.hits, burst])
+    full = _stream_from_hits(hits, g.n_pmt)
+    d = _det(pkg, g, par)
+    _, res = _run(pkg, d, [(t0, full)])
+    ref = oracle.run(g.xyz_mm, g.floor_id, par, hits, [t0])
+    _assert_same(res[0], ref[0], "burst")
+    d.close()
+
+
+def test_degenerate_single_ns_pileup_reports_capacity(pkg, params):
+    g = workload.nemo_tower()
+    par = dict(params, slice_ns=1_000_000)
+    t0 = 10_000_000
+    hits = np.zeros(6000, workload.HIT_DTYPE)
+    hits["t"] = t0 + 5000
+    hits["pmt"] = np.arange(6000) % 32
+    hits["charge"] = 100
+    full = _stream_from_hits(hits, g.n_pmt)
+    d = _det(pkg, g, par)
+    _, res = _run(pkg, d, [(t0, full)])
+    stats = res[0][0]
+    assert int(stats["status"]) == pkg.TRIG_ECAPACITY
+    assert int(stats["flags"]) & 0x08
+    d.close()
+
+
+def test_edge_cases_empty_and_single(pkg, params):
+    g = workload.nemo_tower()
+    d = _det(pkg, g, params)
+    t0 = 10_000_000
+    empty = workload.Stream(np.zeros(0, workload.HIT_DTYPE), np.zeros(33, np.uint64))
+    one = np.zeros(1, workload.HIT_DTYPE)
+    one["t"], one["pmt"], one["charge"] = t0, 5, 500
+    only_halo = np.zeros(2, workload.HIT_DTYPE)
+    only_halo["t"], only_halo["pmt"], only_halo["charge"] = [t0 - 100, t0 - 90], [0, 1], 100
+    subs = [(t0, empty), (t0, _stream_from_hits(one, 32)), (t0, _stream_from_hits(only_halo, 32))]
+    _, res = _run(pkg, [d, d, d], subs)
+    assert int(res[0][0]["status"]) == 0 and len(res[0][1]) == 0 and int(res[0][0]["n_seeds"]) == 0
+    assert int(res[1][0]["n_seeds"]) == 1 and len(res[1][1]) == 0
+    assert int(res[2][0]["n_seeds"]) == 0 and len(res[2][1]) == 0
+    d.close()
+
+
+def test_malformed_input_is_flagged(pkg, params):
+    g = workload.nemo_tower()
+    d = _det(pkg, g, params)
+    t0 = 10_000_000
+    h = np.zeros(3, workload.HIT_DTYPE)
+    h["t"] = [t0 + 10, t0 + 5, t0 + 20]
+    h["pmt"] = [3, 3, 3]
+    off = np.zeros(33, np.uint64)
+    off[4:] = 3
+    unsorted = workload.Stream(h, off)
+    h2 = h.copy()
+    h2["t"] = [t0, t0 + 1, t0 + 2]
+    h2["pmt"] = [3, 7, 3]
+    wrong_row = workload.Stream(h2, off)
+    h3 = h2.copy()
+    h3["pmt"] = 3
+    h3["t"] = [t0, t0 + 1, t0 + params["slice_ns"] + 3000]
+    out_of_range = workload.Stream(h3, off)
+    _, res = _run(pkg, [d, d, d], [(t0, unsorted), (t0, wrong_row), (t0, out_of_range)])
+    assert int(res[0][0]["status"]) == pkg.TRIG_EINVAL and int(res[0][0]["flags"]) & 0x02
+    assert int(res[1][0]["status"]) == pkg.TRIG_EINVAL and int(res[1][0]["flags"]) & 0x01
+    assert int(res[2][0]["status"]) == pkg.TRIG_EINVAL and int(res[2][0]["flags"]) & 0x04
+    d.close()
+
+
+def test_output_capacity_flag(pkg, params):
+    wl = workload.cfg_nemo()
+    g = wl.detectors[0]
+    d = _det(pkg, g, params)
+    from paper_1411_3968_gb300.runner import DeviceBatch, SliceIn
+    s = wl.submissions[0]
+    b = DeviceBatch([SliceIn(d, s.t0, s.stream.hits, s.stream.pmt_off)], trig_cap=10)
+    b.run()
+    stats, trig, win = b.results()[0]
+    ref = oracle.run(g.xyz_mm, g.floor_id, params, wl.runs[0].hits, wl.run_slices[0])[0]
+    assert int(stats["status"]) == pkg.TRIG_ECAPACITY
+    assert int(stats["n_triggers"]) == len(ref.triggers)
+    assert len(trig) == 10
+    assert np.array_equal(trig["t"], ref.triggers["t"][:10])
+    d.close()
