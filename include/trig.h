@@ -220,6 +220,7 @@ size_t trig_batch_scratch_bytes(const trig_slice_dev *slices, uint32_t n_slices)
  * the launch sequence from a cached CUDA graph (one per stream and scratch
  * pointer).  EINVAL on bad arguments (nothing is launched). */
 #define TRIG_RUN_GRAPH 0x1u
+#define TRIG_RUN_TIMED 0x2u   /* record CUDA events around each kernel (not with GRAPH) */
 int trig_batch_run(const trig_slice_dev *slices, uint32_t n_slices, void *scratch, size_t scratch_bytes,
                    void *stream, uint32_t flags);
 
@@ -239,9 +240,16 @@ int trig_slice_rows(const trig_slice_dev *slice, trig_hit *merged_out, uint32_t 
 int trig_set_tile_config(uint32_t cap, uint32_t fill_pct);
 int trig_get_tile_config(uint32_t *cap, uint32_t *fill_pct);
 
-/* Kernel launches issued by trig_batch_run per call (graph replays count
+/* Kernel launches issued by trig_batch_run so far (graph replays count
  * their kernels). */
 uint64_t trig_kernel_launch_count(void);
+
+/* Average device time per kernel of the pipeline over the runs made with
+ * TRIG_RUN_TIMED since the previous call (waits for their events), in the
+ * launch order k_prep, k_bounds, k_tile, k_scan, k_copy, k_windows,
+ * k_status.  avg_ms[i] and names[i] (static strings) for i < max_kernels;
+ * returns the number of kernels (7) and the number of runs in *n_runs. */
+int trig_kernel_times(double *avg_ms, const char **names, uint32_t max_kernels, uint32_t *n_runs);
 
 #ifdef __cplusplus
 }

@@ -28,6 +28,7 @@ TRIG_FLAG_WIN_FULL = 0x20
 TRIG_FLAG_TIMEOUT = 0x40
 
 TRIG_RUN_GRAPH = 0x1
+TRIG_RUN_TIMED = 0x2
 
 HIT_DTYPE = np.dtype([("t", "<i8"), ("pmt", "<u2"), ("charge", "<u2"), ("reserved", "<u4")])
 TRIGGER_DTYPE = np.dtype([("t", "<i8"), ("pmt", "<u2"), ("charge", "<u2"), ("count", "<u4")])
@@ -40,7 +41,7 @@ EXPORTS = [
     "trig_create", "trig_destroy", "trig_detector_dtmax", "trig_detector_halo_ns", "trig_submit_slice",
     "trig_poll", "trig_result_free", "trig_engine_set_mode", "trig_engine_stats", "trig_last_error",
     "trig_batch_scratch_bytes", "trig_batch_run", "trig_slice_rows", "trig_set_tile_config",
-    "trig_get_tile_config", "trig_kernel_launch_count",
+    "trig_get_tile_config", "trig_kernel_launch_count", "trig_kernel_times",
 ]
 
 
@@ -108,6 +109,8 @@ def load(path: str | None = None):
         "trig_set_tile_config": (c.c_int, [c.c_uint32, c.c_uint32]),
         "trig_get_tile_config": (c.c_int, [c.POINTER(c.c_uint32), c.POINTER(c.c_uint32)]),
         "trig_kernel_launch_count": (c.c_uint64, []),
+        "trig_kernel_times": (c.c_int, [c.POINTER(c.c_double), c.POINTER(c.c_char_p), c.c_uint32,
+                                        c.POINTER(c.c_uint32)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -243,6 +246,17 @@ def trig_get_tile_config() -> tuple[int, int]:
 
 def trig_kernel_launch_count() -> int:
     return int(load().trig_kernel_launch_count())
+
+
+def trig_kernel_times() -> tuple[dict, int]:
+    """Average ms per pipeline kernel over the TIMED runs since the last call."""
+    ms = (ctypes.c_double * 16)()
+    names = (ctypes.c_char_p * 16)()
+    nr = ctypes.c_uint32()
+    k = load().trig_kernel_times(ms, names, 16, ctypes.byref(nr))
+    if k < 0:
+        _check(k)
+    return {names[i].decode(): float(ms[i]) for i in range(k)}, int(nr.value)
 
 
 # ------------------------------------------------------------- device batches

@@ -81,7 +81,13 @@ static TileConfig current_cfg()
 
 // ------------------------------------------------------------- detectors
 
-struct DetQueue;
+struct DetQueue {
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<uint64_t> order;                    // submitted ids, oldest first
+    std::map<uint64_t, trig_result *> done;
+    uint64_t in_flight = 0;
+};
 
 struct trig_detector {
     uint32_t n_pmt = 0;
@@ -178,6 +184,7 @@ extern "C" int trig_create(const trig_geometry *g, const trig_params *params, tr
     d->tile_halo = H;
     d->in_halo = std::max<int64_t>({(int64_t)params->corr_window_ns, (int64_t)params->win_half_ns,
                                     (int64_t)params->floor_tau_ns});
+    d->q = std::make_shared<DetQueue>();
     *out = d.release();
     return TRIG_OK;
 }
@@ -204,17 +211,20 @@ struct Plan {
     bool smem_dt = true;
 };
 
-// Tile width W = 2^k ns: the largest power of two for which a tile plus its
-// two halos is expected to hold about fill% of the tile capacity.
-static uint32_t choose_wshift(const trig_detector *det, uint64_t n_hits, const TileConfig &cfg)
+// Tile width W (ns): a tile plus its two halos is expected to hold fill% of
+// the tile capacity at the slice's mean rate; W >= 256 ns and at most 2^20
+// tiles per slice.
+static int64_t choose_tile_w(const trig_detector *det, uint64_t n_hits, const TileConfig &cfg)
 {
     const double span = (double)det->par.slice_ns + 2.0 * (double)det->in_halo;
     const double rate = n_hits > 0 ? (double)n_hits / span : 1e-9;       // hits per ns
     const double target = (double)cfg.cap * cfg.fill_pct / 100.0;
     double w = target / rate - 2.0 * det->tile_halo;
-    uint32_t ws = 10;
-    while (ws < 30 && (double)((int64_t)1 << (ws + 1)) <= w) ++ws;
-    return ws;
+    const double w_min = std::max(256.0, (double)det->par.slice_ns / (double)kMaxTilesPerSlice + 1.0);
+    if (w < w_min) w = w_min;
+    if (w > (double)det->par.slice_ns) w = (double)det->par.slice_ns;
+    if (w > 2e9) w = 2e9;
+    return (int64_t)w;
 }
 
 static int make_plan(const trig_slice_dev *sl, uint32_t n, uintptr_t base, const TileConfig &cfg, Plan &pl,
@@ -257,10 +267,12 @@ static int make_plan(const trig_slice_dev *sl, uint32_t n, uintptr_t base, const
         d.in_lo = x.t0_ns - det->in_halo;
         d.in_hi = x.t0_ns + det->par.slice_ns + det->in_halo;
         d.n_hits = x.n_hits;
-        d.wshift = choose_wshift(det, x.n_hits, cfg);
-        const int64_t W = (int64_t)1 << d.wshift;
+        const int64_t W = choose_tile_w(det, x.n_hits, cfg);
+        d.tile_w = W;
+        d.w_magic = (uint32_t)((((uint64_t)1 << 32) + (uint64_t)W - 1) / (uint64_t)W);
+        d.span32 = (det->par.slice_ns + 2 * det->in_halo + 2 * (int64_t)det->tile_halo + 2 * W) < ((int64_t)1 << 31);
         const uint64_t ng = x.n_hits ? (uint64_t)((det->par.slice_ns + W - 1) / W) : 0;
-        if (ng > 0x3fffffffu) return fail(TRIG_EINVAL, "too many tiles");
+        if (ng > kMaxTilesPerSlice) return fail(TRIG_EINVAL, "too many tiles");
         d.n_tiles = (uint32_t)ng;
         d.item0 = items;
         d.chunk0 = chunks;
@@ -276,6 +288,10 @@ static int make_plan(const trig_slice_dev *sl, uint32_t n, uintptr_t base, const
         d.tile_rank = reinterpret_cast<uint32_t *>(base + off);
         off += align256((size_t)d.n_tiles * 4);
         d.tile_out = reinterpret_cast<uint32_t *>(base + off);
+        off += align256((size_t)d.n_tiles * 4);
+        d.tile_nwin = reinterpret_cast<uint32_t *>(base + off);
+        off += align256((size_t)d.n_tiles * 4);
+        d.tile_wout = reinterpret_cast<uint32_t *>(base + off);
         off += align256((size_t)d.n_tiles * 4);
         d.stage = reinterpret_cast<trig_trigger *>(base + off);
         off += align256((size_t)x.n_hits * sizeof(trig_trigger));
@@ -379,8 +395,59 @@ static int run_graph(const Plan &pl, void *scratch, cudaStream_t st, const TileC
     if ((e = cudaGraphLaunch(ge.exec, st))) return cuda_fail(e, "graph: launch");
     if ((e = cudaEventRecord(ge.done, st))) return cuda_fail(e, "graph: record");
     ge.launched = true;
-    g_launches += 7;
+    g_launches += kPipelineKernels;
     return TRIG_OK;
+}
+
+// ------------------------------------------------------- kernel timing
+
+struct TimedRun {
+    cudaEvent_t ev[kPipelineKernels + 1];
+};
+
+static std::mutex g_time_mu;
+static std::vector<TimedRun> g_time_pending, g_time_free;
+
+static int timed_events(TimedRun &tr)
+{
+    std::lock_guard<std::mutex> lk(g_time_mu);
+    if (!g_time_free.empty()) {
+        tr = g_time_free.back();
+        g_time_free.pop_back();
+        return TRIG_OK;
+    }
+    for (auto &e : tr.ev) {
+        cudaError_t c = cudaEventCreate(&e);
+        if (c) return cuda_fail(c, "timing events");
+    }
+    return TRIG_OK;
+}
+
+extern "C" int trig_kernel_times(double *avg_ms, const char **names, uint32_t max_kernels, uint32_t *n_runs)
+{
+    std::vector<TimedRun> runs;
+    {
+        std::lock_guard<std::mutex> lk(g_time_mu);
+        runs.swap(g_time_pending);
+    }
+    double acc[kPipelineKernels] = {};
+    for (auto &r : runs) {
+        cudaError_t e = cudaEventSynchronize(r.ev[kPipelineKernels]);
+        if (e) return cuda_fail(e, "trig_kernel_times");
+        for (int i = 0; i < kPipelineKernels; ++i) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, r.ev[i], r.ev[i + 1]);
+            acc[i] += ms;
+        }
+    }
+    for (uint32_t i = 0; i < (uint32_t)kPipelineKernels && i < max_kernels; ++i) {
+        if (avg_ms) avg_ms[i] = runs.empty() ? 0.0 : acc[i] / (double)runs.size();
+        if (names) names[i] = kKernelNames[i];
+    }
+    if (n_runs) *n_runs = (uint32_t)runs.size();
+    std::lock_guard<std::mutex> lk(g_time_mu);
+    for (auto &r : runs) g_time_free.push_back(r);
+    return kPipelineKernels;
 }
 
 static int run_plan(const Plan &pl, void *scratch, size_t scratch_bytes, cudaStream_t st, uint32_t flags,
@@ -388,16 +455,27 @@ static int run_plan(const Plan &pl, void *scratch, size_t scratch_bytes, cudaStr
 {
     if (!scratch || ((uintptr_t)scratch & 255u)) return fail(TRIG_EINVAL, "scratch must be 256-byte aligned device memory");
     if (scratch_bytes < pl.bytes) return fail(TRIG_EINVAL, "scratch too small (see trig_batch_scratch_bytes)");
+    if ((flags & TRIG_RUN_GRAPH) && (flags & TRIG_RUN_TIMED)) return fail(TRIG_EINVAL, "TIMED runs cannot use GRAPH");
     if ((flags & TRIG_RUN_GRAPH) && !rows) return run_graph(pl, scratch, st, cfg);
     std::vector<unsigned char> host;
     pack_plan(pl, host);
     cudaError_t e = cudaMemcpyAsync(scratch, host.data(), host.size(), cudaMemcpyHostToDevice, st);
     if (e) return cuda_fail(e, "copy descriptors");
+    TimedRun tr{};
+    const bool timed = (flags & TRIG_RUN_TIMED) && !rows;
+    if (timed) {
+        int rc = timed_events(tr);
+        if (rc) return rc;
+    }
     uint64_t nl = 0;
     e = launch_batch(reinterpret_cast<BatchHeader *>(scratch),
                      reinterpret_cast<SliceDesc *>((char *)scratch + align256(sizeof(BatchHeader))), pl.hdr.n_slices,
-                     pl.max_pmt, pl.smem_dt, cfg, st, &nl, rows);
+                     pl.max_pmt, pl.smem_dt, cfg, st, &nl, rows, timed ? tr.ev : nullptr);
     g_launches += nl;
+    if (timed) {
+        std::lock_guard<std::mutex> lk(g_time_mu);
+        g_time_pending.push_back(tr);
+    }
     if (e) return cuda_fail(e, "launch");
     return TRIG_OK;
 }
@@ -496,13 +574,7 @@ struct PinnedPool {
 
 }  // namespace
 
-struct DetQueue {
-    std::mutex mu;
-    std::condition_variable cv;
-    std::deque<uint64_t> order;                    // submitted ids, oldest first
-    std::map<uint64_t, trig_result *> done;
-    uint64_t in_flight = 0;
-};
+
 
 namespace {
 
@@ -564,6 +636,7 @@ struct Engine {
     }
 
     void run();
+    void fail_slot(Slot &s, cudaError_t err);
     bool launch_batch_on(Slot &s, std::vector<Pending> &batch);
     void collect_stats(Slot &s);
     void finish(Slot &s);
@@ -739,6 +812,29 @@ bool Engine::launch_batch_on(Slot &s, std::vector<Pending> &batch)
     return true;
 }
 
+// A device error: deliver EDEVICE results for the slot's slices (their
+// staging memory is not reused, the device may still reference it) and
+// leave the slot idle.
+void Engine::fail_slot(Slot &s, cudaError_t err)
+{
+    std::fprintf(stderr, "trig engine: batch failed: %s\n", cudaGetErrorString(err));
+    (void)cudaGetLastError();
+    for (auto &p : s.slices) {
+        trig_result *r = static_cast<trig_result *>(std::calloc(1, sizeof(trig_result)));
+        if (r) {
+            r->slice_id = p.id;
+            r->t0_ns = p.t0;
+            r->status = TRIG_EDEVICE;
+        }
+        std::lock_guard<std::mutex> lk(p.q->mu);
+        p.q->done[p.id] = r;
+        p.q->in_flight--;
+        p.q->cv.notify_all();
+    }
+    s.slices.clear();
+    s.state = 0;
+}
+
 void Engine::collect_stats(Slot &s)
 {
     const uint32_t n = (uint32_t)s.slices.size();
@@ -820,13 +916,20 @@ void Engine::run()
             cv.wait(lk);
             continue;
         }
-        // progress in-flight slots
+        // progress in-flight slots; a CUDA error fails the slot's slices
         lk.unlock();
         for (auto &s : slots) {
-            if (s.state == 1 && cudaEventQuery(s.ev_stats) == cudaSuccess) collect_stats(s);
-            if (s.state == 2 && cudaEventQuery(s.ev_done) == cudaSuccess) finish(s);
+            if (s.state == 1) {
+                cudaError_t q = cudaEventQuery(s.ev_stats);
+                if (q == cudaSuccess) collect_stats(s);
+                else if (q != cudaErrorNotReady) fail_slot(s, q);
+            }
+            if (s.state == 2) {
+                cudaError_t q = cudaEventQuery(s.ev_done);
+                if (q == cudaSuccess) finish(s);
+                else if (q != cudaErrorNotReady) fail_slot(s, q);
+            }
         }
-        (void)cudaGetLastError();
         lk.lock();
         // admit a new batch into an idle slot
         bool launched = false;
@@ -894,9 +997,34 @@ extern "C" int trig_engine_stats(uint64_t *batches, uint64_t *slices)
     return TRIG_OK;
 }
 
+// Copies large host buffers with several threads (the submission's copy
+// into pinned staging is on the serving path's critical host work).
+static void parallel_copy(void *dst, const void *src, size_t bytes)
+{
+    const size_t kMinChunk = (size_t)8 << 20;
+    unsigned hw = std::thread::hardware_concurrency();
+    size_t nt = std::min<size_t>(std::max(1u, hw ? hw / 2 : 1u), 16);
+    nt = std::min(nt, bytes / kMinChunk);
+    if (nt <= 1) {
+        std::memcpy(dst, src, bytes);
+        return;
+    }
+    const size_t chunk = ((bytes + nt - 1) / nt + 63) & ~(size_t)63;
+    std::vector<std::thread> th;
+    for (size_t i = 1; i < nt; ++i) {
+        size_t a = i * chunk;
+        if (a >= bytes) break;
+        size_t len = std::min(chunk, bytes - a);
+        th.emplace_back([=] { std::memcpy((char *)dst + a, (const char *)src + a, len); });
+    }
+    std::memcpy(dst, src, std::min(chunk, bytes));
+    for (auto &t : th) t.join();
+}
+
 extern "C" int trig_submit_slice(trig_detector *det, int64_t t0, const trig_hit *hits, const uint64_t *pmt_off,
                                  int is_continuation, uint64_t *slice_id_out)
 {
+    const auto t_entry = Clock::now();
     if (!det || !pmt_off) return fail(TRIG_EINVAL, "NULL argument");
     if (is_continuation) return fail(TRIG_EINVAL, "is_continuation: submissions carry their own halos");
     const uint32_t P = det->n_pmt;
@@ -910,16 +1038,15 @@ extern "C" int trig_submit_slice(trig_detector *det, int64_t t0, const trig_hit 
     if (!e) return fail(TRIG_EDEVICE, "engine failed to start: " + g_last_error);
     Pending p;
     p.det = det;
-    if (!det->q) det->q = std::make_shared<DetQueue>();
     p.q = det->q;
     p.t0 = t0;
     p.n_hits = n;
     const size_t bytes = n * sizeof(trig_hit) + (size_t)(P + 1) * 8;
     p.pinned = e->pool.get(bytes, &p.pinned_bytes);
     if (!p.pinned) return fail(TRIG_EAGAIN, "staging memory full; poll results and retry");
-    if (n) std::memcpy(p.pinned, hits, n * sizeof(trig_hit));
+    if (n) parallel_copy(p.pinned, hits, n * sizeof(trig_hit));
     std::memcpy(p.pinned + n * sizeof(trig_hit), pmt_off, (size_t)(P + 1) * 8);
-    p.t_submit = Clock::now();
+    p.t_submit = t_entry;
     p.id = e->next_id++;
     {
         std::lock_guard<std::mutex> lk(p.q->mu);

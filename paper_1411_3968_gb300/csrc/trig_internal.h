@@ -40,8 +40,10 @@ struct SliceDesc {
     int64_t slice_ns;
     int64_t in_lo, in_hi;   // accepted hit times [in_lo, in_hi)
     uint64_t n_hits;
-    uint32_t wshift;        // tile width W = 1 << wshift
-    uint32_t n_tiles;       // NG
+    int64_t tile_w;         // tile width W (ns); tile g owns [t0 + g W, t0 + (g+1) W)
+    uint32_t w_magic;       // ceil(2^32 / W): 32-bit quotient estimate when span32
+    uint32_t span32;        // all in-range times are < 2^31 ns past t0 - H
+    uint32_t n_tiles;       // NG (<= 2^20)
     uint32_t item0;         // first work item (tile) of this slice
     uint32_t chunk0;        // first structure-pass chunk of this slice
     uint32_t *e_lo;         // [NG][P] first hit index with t >= B_g - H
@@ -50,6 +52,8 @@ struct SliceDesc {
     uint32_t *tile_nfired;  // [NG]
     uint32_t *tile_rank;    // [NG] merged rank of the tile's first core hit
     uint32_t *tile_out;     // [NG] exclusive prefix of tile_nfired
+    uint32_t *tile_nwin;    // [NG] window heads among the tile's triggers
+    uint32_t *tile_wout;    // [NG] exclusive prefix of tile_nwin
     trig_trigger *triggers;
     uint64_t trig_cap;
     trig_window *windows;
@@ -77,14 +81,20 @@ cudaError_t launch_dtmax(const int32_t *xyz, uint32_t n_pmt, uint32_t tol, uint3
                          uint32_t corr, int32_t *dt_exact, uint16_t *dt, uint16_t *dmax_row, cudaStream_t st);
 
 struct TileConfig {
-    uint32_t cap;       // hits per shared-memory tile
+    uint32_t cap;       // hits per shared-memory tile (2048: 2 CTAs per SM, 4096: 1)
     uint32_t fill_pct;  // target fill of a tile (percent of cap)
 };
+constexpr uint32_t kMaxTilesPerSlice = 1u << 20;
 
 // Enqueues the batch pipeline; header/desc already copied to device scratch.
+constexpr int kPipelineKernels = 9;
+extern const char *const kKernelNames[kPipelineKernels];
+
+// ev (optional, kPipelineKernels + 1 events): ev[i] is recorded before
+// pipeline kernel i and ev[kPipelineKernels] after the last one.
 cudaError_t launch_batch(BatchHeader *d_hdr, SliceDesc *d_desc, uint32_t n_slices, uint32_t max_pmt,
                          bool any_smem_dt, const TileConfig &cfg, cudaStream_t st, uint64_t *launches,
-                         bool rows);
+                         bool rows, cudaEvent_t *ev = nullptr);
 
 int device_sm_count();
 

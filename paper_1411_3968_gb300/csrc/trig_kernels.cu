@@ -247,13 +247,26 @@ __global__ void k_prep(BatchHeader *hdr, const SliceDesc *desc)
 
 // ---------------------------------------------------------------- k_bounds
 
-// Number of tile boundaries v_g (g in [0, NG)) with v_g <= t, for
-// v_g = base + g * W (lo edges: base = t0 - H) written as
-// floor((t - base) / W) + 1, clamped to [0, NG].
-__device__ __forceinline__ uint32_t edges_le(int64_t t, int64_t base, uint32_t ws, uint32_t ng)
+// Number of tile edges v_g = base + g * W (g in [0, NG)) with v_g <= t,
+// i.e. floor((t - base) / W) + 1 clamped to [0, NG].  (Slices longer than
+// about 2 s; kept out of line.)
+__device__ __noinline__ uint32_t edges_le64(int64_t t, int64_t base, int64_t W, uint32_t ng)
 {
-    int64_t q = ((t - base) >> ws) + 1;
-    return q <= 0 ? 0u : (q >= (int64_t)ng ? ng : (uint32_t)q);
+    const int64_t rel = t - base;
+    if (rel < 0) return 0u;
+    const int64_t q = rel / W;
+    return q + 1 >= (int64_t)ng ? ng : (uint32_t)(q + 1);
+}
+
+// Same for 0 <= rel < 2^31 and W < 2^31: the high half of rel * ceil(2^32 / W)
+// is the quotient or one more; one multiply corrects it.
+__device__ __forceinline__ uint32_t edges_le32(int64_t rel64, uint32_t W, uint32_t magic, uint32_t ng)
+{
+    if (rel64 < 0) return 0u;
+    const uint32_t rel = (uint32_t)rel64;
+    uint32_t q = __umulhi(rel, magic);
+    if (q * W > rel) --q;
+    return q + 1 >= ng ? ng : q + 1;
 }
 
 __device__ __forceinline__ void fill_edges(uint32_t *e, uint32_t P, uint32_t p, uint32_t g0, uint32_t g1,
@@ -262,56 +275,108 @@ __device__ __forceinline__ void fill_edges(uint32_t *e, uint32_t P, uint32_t p, 
     for (uint32_t g = g0; g < g1; ++g) e[(size_t)g * P + p] = v;
 }
 
-__global__ void __launch_bounds__(256) k_bounds(const BatchHeader *__restrict__ hdr,
-                                                const SliceDesc *__restrict__ desc)
+// Edges after a PMT's last hit, and all edges of the empty PMTs that follow.
+__device__ __noinline__ void fill_run_end(uint32_t *e_lo, uint32_t *e_hi, const uint64_t *poff, uint32_t P,
+                                          uint32_t NG, uint32_t p, uint32_t lo_to, uint32_t hi_to, uint32_t ep)
+{
+    fill_edges(e_lo, P, p, lo_to, NG, ep);
+    fill_edges(e_hi, P, p, hi_to, NG, ep);
+    for (uint32_t q = p + 1; q < P && poff[q] == poff[q + 1]; ++q) {
+        fill_edges(e_lo, P, q, 0, NG, ep);
+        fill_edges(e_hi, P, q, 0, NG, ep);
+    }
+}
+
+// All edges of the empty PMTs before the slice's first hit.
+__device__ __noinline__ void fill_leading_empty(uint32_t *e_lo, uint32_t *e_hi, uint32_t P, uint32_t NG, uint32_t p)
+{
+    for (uint32_t q = 0; q < p; ++q) {
+        fill_edges(e_lo, P, q, 0, NG, 0u);
+        fill_edges(e_hi, P, q, 0, NG, 0u);
+    }
+}
+
+constexpr int kBoundsThreads = 256;
+constexpr int kBoundsUnroll = 4;
+
+// One read of every hit.  Per hit: CSR layout and time order are checked
+// (run starts and ends against pmt_off, neighbours from adjacent lanes), and
+// the tile edges passed between the previous hit of the PMT and this one
+// get this hit's index.
+__global__ void __launch_bounds__(kBoundsThreads) k_bounds(const BatchHeader *__restrict__ hdr,
+                                                           const SliceDesc *__restrict__ desc)
 {
     const uint32_t n_slices = hdr->n_slices, n_chunks = hdr->n_chunks;
+    const uint32_t lane = lane_id();
     for (uint32_t c = blockIdx.x; c < n_chunks; c += gridDim.x) {
         const uint32_t s = find_slice_by_chunk(desc, n_slices, c);
         const SliceDesc &d = desc[s];
-        const uint32_t P = d.n_pmt, NG = d.n_tiles, ws = d.wshift;
+        const uint32_t P = d.n_pmt, NG = d.n_tiles;
+        const int64_t W = d.tile_w;
+        const uint32_t W32 = (uint32_t)W, magic = d.w_magic;
+        const bool span32 = d.span32 != 0;
         const int64_t base_lo = d.t0 - (int64_t)d.halo;             // lo edge g: t0 - H + g W
-        const int64_t base_hi = d.t0 + (int64_t)d.halo;             // hi edge g: t0 + H + (g + 1) W
+        const int64_t base_hi = d.t0 + (int64_t)d.halo + W;         // hi edge g: t0 + H + (g + 1) W
         const uint64_t first = (uint64_t)(c - d.chunk0) * kChunkHits;
-        for (uint32_t k = threadIdx.x; k < kChunkHits; k += blockDim.x) {
-            const uint64_t li = first + k;
-            if (li >= d.n_hits) break;
-            const trig_hit h = load_hit(d.hits + li);
-            const uint32_t p = h.pmt;
-            if (p >= P) { report(d, TRIG_FLAG_BAD_PMT); continue; }
-            const uint64_t sp = d.pmt_off[p], ep = d.pmt_off[p + 1];
-            if (li < sp || li >= ep) { report(d, TRIG_FLAG_BAD_PMT); continue; }
-            const int64_t t = h.t_ns;
-            uint32_t bad = 0;
-            if (t < d.in_lo || t >= d.in_hi) bad |= TRIG_FLAG_OUT_OF_RANGE;
-            const bool is_first = (li == sp);
-            int64_t tprev = 0;
-            if (!is_first) {
-                tprev = d.hits[li - 1].t_ns;
-                if (tprev > t) bad |= TRIG_FLAG_UNSORTED;
+        const uint64_t n_hits = d.n_hits;
+        const trig_hit *__restrict__ hits = d.hits;
+        const uint64_t *__restrict__ poff = d.pmt_off;
+        uint32_t *__restrict__ e_lo = d.e_lo;
+        uint32_t *__restrict__ e_hi = d.e_hi;
+        const int64_t in_lo = d.in_lo, in_hi = d.in_hi;
+        auto cnt_lo = [&](int64_t t) -> uint32_t {
+            return span32 ? edges_le32(t - base_lo, W32, magic, NG) : edges_le64(t, base_lo, W, NG);
+        };
+        auto cnt_hi = [&](int64_t t) -> uint32_t {
+            return span32 ? edges_le32(t - base_hi, W32, magic, NG) : edges_le64(t, base_hi, W, NG);
+        };
+        for (uint32_t k0 = 0; k0 < kChunkHits; k0 += kBoundsThreads * kBoundsUnroll) {
+            trig_hit h[kBoundsUnroll];
+#pragma unroll
+            for (int u = 0; u < kBoundsUnroll; ++u) {
+                const uint64_t li = first + k0 + u * kBoundsThreads + threadIdx.x;
+                if (li < n_hits) h[u] = load_hit(hits + li);
+                else h[u].t_ns = 0, h[u].pmt = 0xffff;
             }
-            if (bad) { report(d, bad); continue; }
-            const uint32_t lo_to = edges_le(t, base_lo, ws, NG);
-            const uint32_t hi_to = edges_le(t, base_hi + ((int64_t)1 << ws), ws, NG);
-            const uint32_t lo_from = is_first ? 0u : edges_le(tprev, base_lo, ws, NG);
-            const uint32_t hi_from = is_first ? 0u : edges_le(tprev, base_hi + ((int64_t)1 << ws), ws, NG);
-            fill_edges(d.e_lo, P, p, lo_from, lo_to, (uint32_t)li);
-            fill_edges(d.e_hi, P, p, hi_from, hi_to, (uint32_t)li);
-            if (li == ep - 1) {
-                // edges after the last hit point past the stream; so do all edges
-                // of the empty PMTs that follow
-                fill_edges(d.e_lo, P, p, lo_to, NG, (uint32_t)ep);
-                fill_edges(d.e_hi, P, p, hi_to, NG, (uint32_t)ep);
-                for (uint32_t q = p + 1; q < P && d.pmt_off[q] == d.pmt_off[q + 1]; ++q) {
-                    fill_edges(d.e_lo, P, q, 0, NG, (uint32_t)ep);
-                    fill_edges(d.e_hi, P, q, 0, NG, (uint32_t)ep);
+#pragma unroll
+            for (int u = 0; u < kBoundsUnroll; ++u) {
+                const uint64_t li = first + k0 + u * kBoundsThreads + threadIdx.x;
+                const bool valid = li < n_hits;
+                const uint32_t p = h[u].pmt;
+                const int64_t t = h[u].t_ns;
+                const uint32_t lo_to = valid ? cnt_lo(t) : 0u;
+                const uint32_t hi_to = valid ? cnt_hi(t) : 0u;
+                // the neighbours' records are the adjacent lanes' (edge lanes load them)
+                uint32_t pp = __shfl_up_sync(0xffffffffu, p, 1);
+                int64_t tp = __shfl_up_sync(0xffffffffu, t, 1);
+                uint32_t lo_p = __shfl_up_sync(0xffffffffu, lo_to, 1);
+                uint32_t hi_p = __shfl_up_sync(0xffffffffu, hi_to, 1);
+                uint32_t pn = __shfl_down_sync(0xffffffffu, p, 1);
+                if (!valid) continue;
+                if (lane == 0 && li > 0) {
+                    const trig_hit q = load_hit(hits + li - 1);
+                    pp = q.pmt;
+                    tp = q.t_ns;
+                    lo_p = cnt_lo(tp);
+                    hi_p = cnt_hi(tp);
                 }
-            }
-            if (li == 0) {
-                for (uint32_t q = 0; q < p; ++q) {
-                    fill_edges(d.e_lo, P, q, 0, NG, 0u);
-                    fill_edges(d.e_hi, P, q, 0, NG, 0u);
+                if (lane == 31 && li + 1 < n_hits) pn = hits[li + 1].pmt;
+                const bool is_first = li == 0 || pp != p;
+                const bool is_last = li + 1 == n_hits || pn != p;
+                uint32_t bad = 0;
+                if (p >= P) bad |= TRIG_FLAG_BAD_PMT;
+                else {
+                    if (is_first && poff[p] != li) bad |= TRIG_FLAG_BAD_PMT;
+                    if (is_last && poff[p + 1] != li + 1) bad |= TRIG_FLAG_BAD_PMT;
+                    if (li + 1 == n_hits && poff[P] != n_hits) bad |= TRIG_FLAG_BAD_PMT;
                 }
+                if (t < in_lo || t >= in_hi) bad |= TRIG_FLAG_OUT_OF_RANGE;
+                if (!is_first && tp > t) bad |= TRIG_FLAG_UNSORTED;
+                if (bad) { report(d, bad); continue; }
+                fill_edges(e_lo, P, p, is_first ? 0u : lo_p, lo_to, (uint32_t)li);
+                fill_edges(e_hi, P, p, is_first ? 0u : hi_p, hi_to, (uint32_t)li);
+                if (is_last) fill_run_end(e_lo, e_hi, poff, P, NG, p, lo_to, hi_to, (uint32_t)(li + 1));
+                if (li == 0 && p > 0) fill_leading_empty(e_lo, e_hi, P, NG, p);
             }
         }
     }
@@ -345,7 +410,6 @@ struct TileLayout {
 };
 
 struct TileCtx {
-    // shared memory
     uint64_t *stage[2];
     uint64_t *temp;
     uint32_t *cnt;
@@ -353,17 +417,14 @@ struct TileCtx {
     uint16_t *floor_s;
     uint16_t *dmax_s;
     uint16_t *dt_s;
-    // current tables
     const uint16_t *dt_g;
     uint32_t P;
-    bool dt_in_smem;
 };
 
-constexpr uint32_t kNC = 512;           // consumer threads
-constexpr uint32_t kNW = kNC / 32;      // consumer warps
 constexpr uint32_t kBarCons = 1;        // named barrier of the consumers
 
-__device__ __forceinline__ void cons_sync() { named_sync(kBarCons, kNC); }
+template <int NC>
+__device__ __forceinline__ void cons_sync() { named_sync(kBarCons, NC); }
 
 __device__ __forceinline__ uint32_t key_t(uint64_t k) { return (uint32_t)(k >> 32); }
 __device__ __forceinline__ uint32_t key_p(uint64_t k) { return (uint32_t)(k >> 16) & 0xffffu; }
@@ -379,40 +440,47 @@ __device__ __forceinline__ uint32_t lb_key(const uint64_t *a, uint32_t n, uint64
     return lo;
 }
 
-// Block-wide (consumer) exclusive scan of cnt[0..nb), nb a multiple of kNC;
-// writes the total to cnt[nb].  Uses scratch words red[kNW].
+// Consumer-wide exclusive scan of cnt[0..nb), nb a multiple of NC; writes
+// the total to cnt[nb].  Scratch words red[0..NC/32].
+template <int NC>
 __device__ void cons_exclusive_scan(uint32_t *cnt, uint32_t nb, uint32_t *red)
 {
-    const uint32_t tid = threadIdx.x, per = nb / kNC;
+    constexpr uint32_t NW = NC / 32;
+    const uint32_t tid = threadIdx.x, per = nb / NC;
     uint32_t local = 0;
     for (uint32_t i = 0; i < per; ++i) local += cnt[tid * per + i];
     uint32_t incl = warp_incl_scan(local);
     if (lane_id() == 31) red[tid >> 5] = incl;
-    cons_sync();
+    cons_sync<NC>();
     if (tid < 32) {
-        uint32_t v = tid < kNW ? red[tid] : 0u;
+        uint32_t v = tid < NW ? red[tid] : 0u;
         uint32_t vi = warp_incl_scan(v);
-        if (tid < kNW) red[tid] = vi - v;
-        if (tid == kNW - 1) red[kNW] = vi;
+        if (tid < NW) red[tid] = vi - v;
+        if (tid == NW - 1) red[NW] = vi;
     }
-    cons_sync();
+    cons_sync<NC>();
     uint32_t run = red[tid >> 5] + incl - local;
     for (uint32_t i = 0; i < per; ++i) {
         uint32_t c = cnt[tid * per + i];
         cnt[tid * per + i] = run;
         run += c;
     }
-    if (tid == 0) cnt[nb] = red[kNW];
-    cons_sync();
+    if (tid == 0) cnt[nb] = red[NW];
+    cons_sync<NC>();
 }
 
 // Merge (sort) the n staged records of `buf` by (t - tb, pmt, charge); the
-// keys land, in order, in the first 8 * n bytes of `buf`.
-template <int CAP>
-__device__ void tile_sort(TileCtx &cx, uint64_t *buf, uint32_t n, int64_t tb, uint32_t span, uint32_t *red)
+// keys land, in order, in the first 8 * n bytes of `buf`.  Counting sort on
+// a time bucket, then each key's rank inside its bucket.
+// Also counts the keys with t_rel < lo_t and < hi_t into red[NC/32 + 1]
+// and red[NC/32 + 2] (the first core index and the core's end).
+template <int CAP, int NC>
+__device__ void tile_sort(TileCtx &cx, uint64_t *buf, uint32_t n, int64_t tb, uint32_t span, uint32_t *red,
+                          uint32_t lo_t, uint32_t hi_t)
 {
+    constexpr uint32_t NW = NC / 32;
     constexpr int NBK = TileLayout<CAP>::NBK;
-    constexpr int PER = CAP / kNC;
+    constexpr int PER = CAP / NC;
     const uint32_t tid = threadIdx.x;
     uint32_t bsh = 0;
     {
@@ -420,16 +488,18 @@ __device__ void tile_sort(TileCtx &cx, uint64_t *buf, uint32_t n, int64_t tb, ui
         uint32_t nb_bits = 31u - __clz((uint32_t)NBK);
         bsh = top > nb_bits ? top - nb_bits : 0u;
     }
-    for (uint32_t i = tid; i < (uint32_t)NBK; i += kNC) cx.cnt[i] = 0;
-    cons_sync();
+    for (uint32_t i = tid; i < (uint32_t)NBK; i += NC) cx.cnt[i] = 0;
+    if (tid == 0) red[NW + 1] = red[NW + 2] = 0;
+    cons_sync<NC>();
     uint64_t kreg[PER];
     uint32_t slot[PER];
+    uint32_t below_lo = 0, below_hi = 0;
 #pragma unroll
     for (int r = 0; r < PER; ++r) {
-        uint32_t i = tid + r * kNC;
+        uint32_t i = tid + r * NC;
         kreg[r] = 0;
         slot[r] = 0;
-        if (i < n) {
+        if (r * NC < n && i < n) {
             const uint64_t *rec = buf + 2 * i;
             int64_t t = (int64_t)rec[0];
             uint32_t w1 = (uint32_t)rec[1];
@@ -439,22 +509,30 @@ __device__ void tile_sort(TileCtx &cx, uint64_t *buf, uint32_t n, int64_t tb, ui
             uint32_t bk = tr >> bsh;
             if (bk >= (uint32_t)NBK) bk = NBK - 1;
             slot[r] = atomicAdd(&cx.cnt[bk], 1u);
+            below_lo += tr < lo_t;
+            below_hi += tr < hi_t;
         }
     }
-    cons_sync();
-    cons_exclusive_scan(cx.cnt, NBK, red);
+    below_lo = __reduce_add_sync(0xffffffffu, below_lo);
+    below_hi = __reduce_add_sync(0xffffffffu, below_hi);
+    if (lane_id() == 0) {
+        if (below_lo) atomicAdd(&red[NW + 1], below_lo);
+        if (below_hi) atomicAdd(&red[NW + 2], below_hi);
+    }
+    cons_sync<NC>();
+    cons_exclusive_scan<NC>(cx.cnt, NBK, red);
 #pragma unroll
     for (int r = 0; r < PER; ++r) {
-        uint32_t i = tid + r * kNC;
-        if (i < n) {
+        uint32_t i = tid + r * NC;
+        if (r * NC < n && i < n) {
             uint32_t bk = key_t(kreg[r]) >> bsh;
             if (bk >= (uint32_t)NBK) bk = NBK - 1;
             cx.temp[cx.cnt[bk] + slot[r]] = kreg[r];
         }
     }
-    cons_sync();
+    cons_sync<NC>();
     // rank inside each bucket; identical keys are interchangeable
-    for (uint32_t j = tid; j < n; j += kNC) {
+    for (uint32_t j = tid; j < n; j += NC) {
         uint64_t k = cx.temp[j];
         uint32_t bk = key_t(k) >> bsh;
         if (bk >= (uint32_t)NBK) bk = NBK - 1;
@@ -466,7 +544,7 @@ __device__ void tile_sort(TileCtx &cx, uint64_t *buf, uint32_t n, int64_t tb, ui
         }
         buf[r] = k;
     }
-    cons_sync();
+    cons_sync<NC>();
 }
 
 struct CoreOut {
@@ -477,109 +555,188 @@ struct CoreOut {
 
 // Seeds, causal counts and emission over the sorted tile keys[0..n).  The
 // core is t_rel in [H, H + core_w).  Fired seeds go to out[0..n_fired).
-template <int CAP, bool SMEM_DT>
-__device__ CoreOut tile_trigger(TileCtx &cx, const uint64_t *keys, uint32_t n, uint32_t H, uint32_t core_w,
-                                int64_t tb, const SliceDesc &d, trig_trigger *out, int64_t dbg_rank_lo,
+struct TrigParams {
+    uint32_t H, tau, q_seed, threshold;
+    trig_hit *dbg_merged;
+    uint32_t *dbg_seedcnt;
+};
+
+// The core is keys[c0, c1) (t_rel in [H, H + core width)).
+template <int CAP, int NC, bool SMEM_DT>
+__device__ CoreOut tile_trigger(TileCtx &cx, const uint64_t *keys, uint32_t n, uint32_t c0, uint32_t c1,
+                                int64_t tb, const TrigParams &tp, trig_trigger *out, int64_t dbg_rank_lo,
                                 uint32_t *red)
 {
+    constexpr uint32_t NW = NC / 32;
     const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
-    const uint32_t c0 = lb_key(keys, n, (uint64_t)H << 32);
-    const uint32_t c1 = lb_key(keys, n, (uint64_t)(H + core_w) << 32);
     const uint32_t ncore = c1 - c0;
-    const uint32_t tau = d.tau, qseed = d.q_seed, P = cx.P;
+    const uint32_t tau = tp.tau, qseed = tp.q_seed, threshold = tp.threshold, P = cx.P;
+    // scratch per seed (all 16-bit, CAP entries each): index, window, count
     uint16_t *seed_idx = reinterpret_cast<uint16_t *>(cx.temp);
-    uint32_t *seed_cnt = reinterpret_cast<uint32_t *>(cx.temp) + CAP / 2;
+    uint16_t *win_lo = seed_idx + CAP;
+    uint16_t *win_hi = seed_idx + 2 * CAP;
+    uint16_t *seed_cnt = seed_idx + 3 * CAP;
 
-    // 1. seed flags (one bit per core hit)
+    // 1. seed flags (one bit per core hit): charge over threshold, or a hit
+    //    on another PMT of the same floor within tau.  A warp holds 32
+    //    consecutive hits; the two neighbours on each side come from the
+    //    adjacent lanes (edge lanes read them), a longer run within tau is
+    //    followed by a loop.
     const uint32_t nwords = (ncore + 31) / 32;
-    for (uint32_t base = 0; base < ncore; base += kNC) {
-        uint32_t i = c0 + base + tid;
-        bool seed = false;
-        if (i < c1) {
-            uint64_t ki = keys[i];
-            seed = key_q(ki) >= qseed;
-            if (!seed) {
-                const uint32_t ti = key_t(ki), pi = key_p(ki), fi = cx.floor_s[pi];
-                for (uint32_t j = i + 1; j < n; ++j) {
-                    uint64_t kj = keys[j];
-                    if (key_t(kj) - ti > tau) break;
-                    uint32_t pj = key_p(kj);
-                    if (pj != pi && cx.floor_s[pj] == fi) { seed = true; break; }
-                }
-                if (!seed) {
-                    for (uint32_t j = i; j-- > 0;) {
-                        uint64_t kj = keys[j];
-                        if (ti - key_t(kj) > tau) break;
-                        uint32_t pj = key_p(kj);
-                        if (pj != pi && cx.floor_s[pj] == fi) { seed = true; break; }
-                    }
-                }
+    for (uint32_t base = 0; base < ncore; base += NC) {
+        const uint32_t i = c0 + base + tid;
+        const bool in = i < c1;
+        // hits past the core (halo) are loaded too: they are neighbours
+        const uint64_t ki = i < n ? keys[i] : ~0ull;
+        const uint32_t ti = key_t(ki), pi = key_p(ki);
+        const uint32_t fi = in ? cx.floor_s[pi] : 0u;
+        bool seed = in && key_q(ki) >= qseed;
+        bool more_up = false, more_dn = false;
+#pragma unroll
+        for (uint32_t dd = 1; dd <= 2; ++dd) {
+            uint64_t ku = __shfl_up_sync(0xffffffffu, ki, dd);
+            uint64_t kd = __shfl_down_sync(0xffffffffu, ki, dd);
+            if (lane < dd) ku = (in && i >= dd) ? keys[i - dd] : ~0ull;
+            if (lane + dd >= 32) kd = (in && i + dd < n) ? keys[i + dd] : ~0ull;
+            if (in && i < dd) ku = ~0ull;
+            if (in && i + dd >= n) kd = ~0ull;
+            const bool near_u = ku != ~0ull && ti - key_t(ku) <= tau;
+            const bool near_d = kd != ~0ull && key_t(kd) - ti <= tau;
+            if (near_u && key_p(ku) != pi && cx.floor_s[key_p(ku)] == fi) seed = true;
+            if (near_d && key_p(kd) != pi && cx.floor_s[key_p(kd)] == fi) seed = true;
+            more_up = near_u;
+            more_dn = near_d;
+        }
+        if (in && !seed && (more_up || more_dn)) {
+            // three or more hits within tau on one side: walk further
+            for (uint32_t j = i + 3; more_dn && j < n; ++j) {
+                const uint64_t kj = keys[j];
+                if (key_t(kj) - ti > tau) break;
+                if (key_p(kj) != pi && cx.floor_s[key_p(kj)] == fi) { seed = true; break; }
+            }
+            for (uint32_t j = i - 2; more_up && !seed && j-- > 0;) {
+                const uint64_t kj = keys[j];
+                if (ti - key_t(kj) > tau) break;
+                if (key_p(kj) != pi && cx.floor_s[key_p(kj)] == fi) { seed = true; break; }
             }
         }
-        uint32_t m = __ballot_sync(0xffffffffu, seed);
+        // halo hits past the core are neighbours only, never seeds here
+        const uint32_t m = __ballot_sync(0xffffffffu, seed && in);
         if (lane == 0 && (base + warp * 32) < ncore) cx.mask[(base + warp * 32) >> 5] = m;
     }
-    cons_sync();
+    cons_sync<NC>();
 
-    // 2. ordered seed list (warp 0)
-    if (warp == 0) {
-        const uint32_t per = (nwords + 31) / 32;
-        uint32_t w0 = lane * per, w1 = min(w0 + per, nwords);
-        uint32_t loc = 0;
-        for (uint32_t w = w0; w < w1; ++w) loc += __popc(cx.mask[w]);
-        uint32_t incl = warp_incl_scan(loc);
-        uint32_t pos = incl - loc;
-        for (uint32_t w = w0; w < w1; ++w) {
-            uint32_t m = cx.mask[w];
-            while (m) {
-                uint32_t b = __ffs(m) - 1;
-                m &= m - 1;
-                seed_idx[pos++] = (uint16_t)(c0 + w * 32 + b);
-            }
+    // 2. ordered seed list: warp w expands a contiguous group of mask words
+    const uint32_t wpw = (nwords + NW - 1) / NW;          // words per warp (<= 32)
+    uint32_t *wtot = red + 2;                             // [NW + 1]
+    {
+        const uint32_t w = warp * wpw + lane;
+        const uint32_t m = (lane < wpw && w < nwords) ? cx.mask[w] : 0u;
+        const uint32_t pc = __popc(m);
+        const uint32_t incl = warp_incl_scan(pc);
+        if (lane == 31) wtot[warp] = incl;
+        cons_sync<NC>();
+        if (warp == 0) {
+            uint32_t v = lane < NW ? wtot[lane] : 0u;
+            uint32_t vi = warp_incl_scan(v);
+            if (lane < NW) wtot[lane] = vi - v;
+            if (lane == NW - 1) wtot[NW] = vi;
         }
-        if (lane == 31) red[0] = incl;
+        cons_sync<NC>();
+        uint32_t pos = wtot[warp] + incl - pc;
+        uint32_t mm = m;
+        while (mm) {
+            const uint32_t bit = __ffs(mm) - 1;
+            mm &= mm - 1;
+            seed_idx[pos++] = (uint16_t)(c0 + w * 32 + bit);
+        }
     }
-    cons_sync();
-    const uint32_t ns = red[0];
+    const uint32_t ns = wtot[NW];
+    cons_sync<NC>();
 
-    // 3. causal count, one warp per seed: c(s) = #{ j : |t_j - t_s| <= min(dt_max, W) }
-    for (uint32_t k = warp; k < ns; k += kNW) {
+    // 2b. each seed's scan range [t_s - d, t_s + d], d = its row's maximum
+    //     of min(dt_max, W): two binary searches per seed, seeds in parallel
+    for (uint32_t k = tid; k < ns; k += NC) {
+        const uint32_t i = seed_idx[k];
+        const uint64_t ks = keys[i];
+        const uint32_t ts = key_t(ks), dm = cx.dmax_s[key_p(ks)];
+        // the window lies within [i - n, i + n]; search each side only
+        uint32_t lo = 0, hi = i;
+        const uint64_t lo_key = (uint64_t)(ts - dm) << 32;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (keys[mid] < lo_key) lo = mid + 1; else hi = mid;
+        }
+        win_lo[k] = (uint16_t)lo;
+        const uint64_t hi_key = (uint64_t)(ts + dm + 1) << 32;
+        lo = i + 1;
+        hi = n;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (keys[mid] < hi_key) lo = mid + 1; else hi = mid;
+        }
+        win_hi[k] = (uint16_t)lo;
+    }
+    cons_sync<NC>();
+
+    // 3. causal count c(s) = #{ j : |t_j - t_s| <= min(dt_max[p_s][p_j], W) },
+    //    a warp per seed over its range; lanes count privately and reduce
+    //    once per seed.
+    const uint32_t per_w = (ns + NW - 1) / NW;
+    const uint32_t k_begin = min(ns, warp * per_w), k_end = min(ns, k_begin + per_w);
+    for (uint32_t k = k_begin; k < k_end; ++k) {
         const uint64_t ks = keys[seed_idx[k]];
         const uint32_t ts = key_t(ks), ps = key_p(ks);
-        const uint32_t dm = cx.dmax_s[ps];
-        const uint32_t hi_t = ts + dm;
-        uint32_t j = lb_key(keys, n, (uint64_t)(ts - dm) << 32) + lane;
+        const uint32_t j0 = win_lo[k], j1 = win_hi[k];
         const uint16_t *row_s = cx.dt_s + (size_t)ps * P;
         const uint16_t *row_g = cx.dt_g + (size_t)ps * P;
-        uint32_t c = 0;
-        for (;; j += 32) {
-            bool in = j < n;
-            uint64_t kj = in ? keys[j] : ~0ull;
-            uint32_t tj = key_t(kj);
-            in = in && tj <= hi_t;
-            bool ok = false;
-            if (in) {
-                uint32_t pj = key_p(kj);
-                uint32_t lim = SMEM_DT ? (uint32_t)row_s[pj] : (uint32_t)__ldg(row_g + pj);
-                uint32_t ad = tj > ts ? tj - ts : ts - tj;
-                ok = ad <= lim;
-            }
-            c += __popc(__ballot_sync(0xffffffffu, ok));
-            if (__ballot_sync(0xffffffffu, in) != 0xffffffffu) break;
+        auto causal = [&](uint32_t j) -> uint32_t {
+            const uint64_t kj = keys[j];
+            const uint32_t tj = key_t(kj), pj = key_p(kj);
+            const uint32_t lim = SMEM_DT ? (uint32_t)row_s[pj] : (uint32_t)__ldg(row_g + pj);
+            const uint32_t ad = tj > ts ? tj - ts : ts - tj;
+            return ad <= lim;
+        };
+        // four independent chains per lane
+        uint32_t ca = 0, cb = 0, cc = 0, cd = 0;
+        uint32_t j = j0 + lane;
+        for (; j + 96 < j1; j += 128) {
+            ca += causal(j);
+            cb += causal(j + 32);
+            cc += causal(j + 64);
+            cd += causal(j + 96);
         }
-        if (lane == 0) seed_cnt[k] = c;
+        for (; j < j1; j += 32) ca += causal(j);
+        const uint32_t c = __reduce_add_sync(0xffffffffu, ca + cb + cc + cd);
+        if (lane == 0) seed_cnt[k] = (uint16_t)c;
     }
-    cons_sync();
+    __syncwarp();
 
-    // 4. emit fired seeds in order (warp 0)
+    // 4. emit fired seeds in order: warps count theirs, a scan of the warp
+    //    totals gives each warp its output offset
+    uint32_t my_f = 0;
+    for (uint32_t k0 = k_begin; k0 < k_end; k0 += 32) {
+        const uint32_t k = k0 + lane;
+        my_f += __popc(__ballot_sync(0xffffffffu, k < k_end && seed_cnt[k] >= threshold));
+    }
+    uint32_t *ftot = red + 2 + (NW + 1);                  // [NW + 1]
+    if (lane == 0) ftot[warp] = my_f;
+    cons_sync<NC>();
     if (warp == 0) {
-        uint32_t F = 0;
-        for (uint32_t k0 = 0; k0 < ns; k0 += 32) {
-            uint32_t k = k0 + lane;
-            bool fired = k < ns && seed_cnt[k] >= d.threshold;
-            uint32_t m = __ballot_sync(0xffffffffu, fired);
+        uint32_t v = lane < NW ? ftot[lane] : 0u;
+        uint32_t vi = warp_incl_scan(v);
+        if (lane < NW) ftot[lane] = vi - v;
+        if (lane == NW - 1) ftot[NW] = vi;
+    }
+    cons_sync<NC>();
+    {
+        uint32_t F = ftot[warp];
+        for (uint32_t k0 = k_begin; k0 < k_end; k0 += 32) {
+            const uint32_t k = k0 + lane;
+            const bool fired = k < k_end && seed_cnt[k] >= threshold;
+            const uint32_t m = __ballot_sync(0xffffffffu, fired);
             if (fired) {
-                uint64_t ks = keys[seed_idx[k]];
+                const uint64_t ks = keys[seed_idx[k]];
                 trig_trigger tr;
                 tr.t_ns = tb + (int64_t)key_t(ks);
                 tr.pmt = (uint16_t)key_p(ks);
@@ -589,31 +746,30 @@ __device__ CoreOut tile_trigger(TileCtx &cx, const uint64_t *keys, uint32_t n, u
             }
             F += __popc(m);
         }
-        if (lane == 0) red[1] = F;
     }
+    const uint32_t n_fired = ftot[NW];
     // 5. optional row outputs (verification)
-    if (d.dbg_merged) {
+    if (tp.dbg_merged) {
         // rows are indexed by merged rank minus the rank of the slice's first owned hit
         const uint64_t dbg_base = (uint64_t)(dbg_rank_lo + (int64_t)c0);
-        for (uint32_t i = tid; i < ncore; i += kNC) {
+        for (uint32_t i = tid; i < ncore; i += NC) {
             uint64_t k = keys[c0 + i];
             trig_hit h;
             h.t_ns = tb + (int64_t)key_t(k);
             h.pmt = (uint16_t)key_p(k);
             h.charge = (uint16_t)key_q(k);
             h.reserved = 0;
-            d.dbg_merged[dbg_base + i] = h;
-            d.dbg_seedcnt[dbg_base + i] = 0xffffffffu;
+            tp.dbg_merged[dbg_base + i] = h;
+            tp.dbg_seedcnt[dbg_base + i] = 0xffffffffu;
         }
-        cons_sync();
-        for (uint32_t k = tid; k < ns; k += kNC) d.dbg_seedcnt[dbg_base + (seed_idx[k] - c0)] = seed_cnt[k];
+        cons_sync<NC>();
+        for (uint32_t k = tid; k < ns; k += NC) tp.dbg_seedcnt[dbg_base + (seed_idx[k] - c0)] = seed_cnt[k];
     }
-    cons_sync();
+    cons_sync<NC>();
     CoreOut r;
-    r.n_fired = red[1];
+    r.n_fired = n_fired;
     r.n_seeds = ns;
     r.c0 = c0;
-    cons_sync();
     return r;
 }
 
@@ -621,27 +777,30 @@ __device__ CoreOut tile_trigger(TileCtx &cx, const uint64_t *keys, uint32_t n, u
 // its core in halves until each piece fits; pieces are staged with plain
 // loads after per-PMT binary searches.  A 1 ns core that still does not
 // fit is reported (TRIG_FLAG_TILE_FULL) and skipped.
-template <int CAP, bool SMEM_DT>
-__device__ void tile_overflow(TileCtx &cx, uint64_t *buf, const SliceDesc &d, uint32_t g, uint32_t *red,
-                              int64_t *stk)
+template <int CAP, int NC, bool SMEM_DT>
+__device__ void tile_overflow(TileCtx &cx, uint64_t *buf, const SliceDesc &d, const TrigParams &tp, uint32_t g,
+                              uint32_t *red, int64_t *stk)
 {
+    constexpr uint32_t NW = NC / 32;
     const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
     const uint32_t P = d.n_pmt, H = d.halo;
-    const int64_t W = (int64_t)1 << d.wshift;
+    const int64_t W = d.tile_w;
     const int64_t Bg = d.t0 + (int64_t)g * W;
     const int64_t core_end = min(Bg + W, d.t0 + d.slice_ns);
+    uint64_t *part = reinterpret_cast<uint64_t *>(red + 8);          // [NW]
+    uint64_t *part2 = reinterpret_cast<uint64_t *>(red + 8 + 2 * NW);  // [NW]
     // merged rank of the tile's first core hit
     uint64_t rk = 0;
-    for (uint32_t p = tid; p < P; p += kNC) {
+    for (uint32_t p = tid; p < P; p += NC) {
         uint64_t sp = d.pmt_off[p], ep = d.pmt_off[p + 1];
         rk += lb_time(d.hits, sp, ep, Bg) - sp;
     }
     rk = warp_sum_u64(rk);
-    if (lane == 0) reinterpret_cast<uint64_t *>(red + 8)[warp] = rk;
-    cons_sync();
+    if (lane == 0) part[warp] = rk;
+    cons_sync<NC>();
     if (tid == 0) {
         uint64_t tot = 0;
-        for (uint32_t w = 0; w < kNW; ++w) tot += reinterpret_cast<uint64_t *>(red + 8)[w];
+        for (uint32_t w = 0; w < NW; ++w) tot += part[w];
         red[4] = (uint32_t)tot;     // tile rank
         red[5] = 0;                 // fired so far
         red[6] = 0;                 // seeds so far
@@ -649,16 +808,16 @@ __device__ void tile_overflow(TileCtx &cx, uint64_t *buf, const SliceDesc &d, ui
         stk[1] = core_end;
         red[7] = 1;                 // stack depth
     }
-    cons_sync();
+    cons_sync<NC>();
     const uint32_t tile_rank = red[4];
     for (int guard = 0; guard < 1 << 20; ++guard) {
         uint32_t depth = red[7];
         if (depth == 0) break;
         const int64_t lo = stk[2 * (depth - 1)], hi = stk[2 * (depth - 1) + 1];
-        cons_sync();
+        cons_sync<NC>();
         // extended count and rank of the piece
         uint64_t tot = 0, rlo = 0;
-        for (uint32_t p = tid; p < P; p += kNC) {
+        for (uint32_t p = tid; p < P; p += NC) {
             uint64_t sp = d.pmt_off[p], ep = d.pmt_off[p + 1];
             uint64_t a = lb_time(d.hits, sp, ep, lo - (int64_t)H);
             uint64_t b = lb_time(d.hits, a, ep, hi + (int64_t)H);
@@ -668,15 +827,15 @@ __device__ void tile_overflow(TileCtx &cx, uint64_t *buf, const SliceDesc &d, ui
         tot = warp_sum_u64(tot);
         rlo = warp_sum_u64(rlo);
         if (lane == 0) {
-            reinterpret_cast<uint64_t *>(red + 8)[warp] = tot;
-            reinterpret_cast<uint64_t *>(red + 8 + 2 * kNW)[warp] = rlo;
+            part[warp] = tot;
+            part2[warp] = rlo;
         }
-        cons_sync();
+        cons_sync<NC>();
         if (tid == 0) {
             uint64_t T = 0, R = 0;
-            for (uint32_t w = 0; w < kNW; ++w) {
-                T += reinterpret_cast<uint64_t *>(red + 8)[w];
-                R += reinterpret_cast<uint64_t *>(red + 8 + 2 * kNW)[w];
+            for (uint32_t w = 0; w < NW; ++w) {
+                T += part[w];
+                R += part2[w];
             }
             red[2] = T > 0xffffffffull ? 0xffffffffu : (uint32_t)T;
             red[3] = (uint32_t)R;
@@ -694,11 +853,11 @@ __device__ void tile_overflow(TileCtx &cx, uint64_t *buf, const SliceDesc &d, ui
                 }
             }
         }
-        cons_sync();
+        cons_sync<NC>();
         const uint32_t total = red[2];
         if (total > (uint32_t)CAP) continue;         // split (or skipped)
         const uint32_t rank_lo = red[3];
-        // stage the piece: PMTs in order, one warp per PMT
+        // stage the piece: PMTs in order, warps take groups of 32 PMTs
         uint32_t dst = 0;
         for (uint32_t p0 = 0; p0 < P; p0 += 32) {
             uint32_t p = p0 + lane;
@@ -710,8 +869,7 @@ __device__ void tile_overflow(TileCtx &cx, uint64_t *buf, const SliceDesc &d, ui
             }
             uint32_t incl = warp_incl_scan((uint32_t)len);
             uint32_t my = dst + incl - (uint32_t)len;
-            // warp w copies the PMTs with (p0 / 32) % kNW == w
-            if (((p0 >> 5) % kNW) == warp) {
+            if (((p0 >> 5) % NW) == warp) {
                 for (uint32_t q = 0; q < 32; ++q) {
                     uint64_t qa = __shfl_sync(0xffffffffu, a, q);
                     uint32_t ql = __shfl_sync(0xffffffffu, (uint32_t)len, q);
@@ -725,33 +883,36 @@ __device__ void tile_overflow(TileCtx &cx, uint64_t *buf, const SliceDesc &d, ui
             }
             dst += __shfl_sync(0xffffffffu, incl, 31);
         }
-        cons_sync();
+        cons_sync<NC>();
         const int64_t tb = lo - (int64_t)H;
         const uint32_t span = (uint32_t)(hi - lo) + 2 * H;
-        tile_sort<CAP>(cx, buf, total, tb, span, red + 64);
+        tile_sort<CAP, NC>(cx, buf, total, tb, span, red + 64, H, H + (uint32_t)(hi - lo));
+        const uint32_t c0 = red[64 + NW + 1], c1 = red[64 + NW + 2];
         const uint32_t fired0 = red[5];
-        CoreOut co = tile_trigger<CAP, SMEM_DT>(cx, buf, total, H, (uint32_t)(hi - lo), tb, d,
-                                                 d.stage + tile_rank + fired0,
-                                                 (int64_t)rank_lo - (int64_t)d.dbg_rank0, red + 64);
+        CoreOut co = tile_trigger<CAP, NC, SMEM_DT>(cx, buf, total, c0, c1, tb, tp,
+                                                     d.stage + tile_rank + fired0,
+                                                     (int64_t)rank_lo - (int64_t)d.dbg_rank0, red + 64);
         if (tid == 0) {
             red[5] = fired0 + co.n_fired;
             red[6] += co.n_seeds;
         }
-        cons_sync();
+        cons_sync<NC>();
     }
     if (tid == 0) {
         d.tile_nfired[g] = red[5];
         d.tile_rank[g] = tile_rank;
         atomicAdd(reinterpret_cast<unsigned long long *>(&d.stats->n_seeds), (unsigned long long)red[6]);
     }
-    cons_sync();
+    cons_sync<NC>();
 }
 
-template <int CAP, bool SMEM_DT>
-__global__ void __launch_bounds__(kNC + 32, 1) k_tile(BatchHeader *__restrict__ hdr,
-                                                      const SliceDesc *__restrict__ desc, uint32_t max_pmt)
+template <int CAP, int NC, bool SMEM_DT>
+__global__ void __launch_bounds__(NC + 32, (CAP <= 2048 ? 2 : 1)) k_tile(BatchHeader *__restrict__ hdr,
+                                                                          const SliceDesc *__restrict__ desc,
+                                                                          uint32_t max_pmt)
 {
     using L = TileLayout<CAP>;
+    constexpr uint32_t NW = NC / 32;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t full_bar[2], empty_bar[2];
     __shared__ ItemInfo info[2];
@@ -778,7 +939,6 @@ __global__ void __launch_bounds__(kNC + 32, 1) k_tile(BatchHeader *__restrict__ 
     cx.dt_s = reinterpret_cast<uint16_t *>(sp);
     cx.dt_g = nullptr;
     cx.P = 0;
-    cx.dt_in_smem = SMEM_DT;
 
     const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = lane_id();
     if (tid == 0) {
@@ -792,17 +952,72 @@ __global__ void __launch_bounds__(kNC + 32, 1) k_tile(BatchHeader *__restrict__ 
 
     const uint32_t n_slices = hdr->n_slices, n_items = hdr->n_items;
 
-    if (warp == kNW) {
+    if (warp == NW) {
         // ------------------------------------------------ producer warp
+        // The next item is dequeued and its per-PMT runs looked up before
+        // waiting for a free buffer, so those global loads overlap the wait.
+        uint32_t s = 0;
+        bool bad = false;
+        const SliceDesc *d = nullptr;
+        constexpr int R = 4;                       // PMTs per lane kept in registers
+        uint32_t item = 0;
+        if (lane == 0) item = atomicAdd(&hdr->queue, 1u);
+        item = __shfl_sync(0xffffffffu, item, 0);
         for (uint32_t it = 0;; ++it) {
             const uint32_t b = it & 1u, use = it >> 1;
+            uint32_t g = 0, P = 0, mode = 2;
+            uint64_t ra[R];
+            uint32_t rl[R];
+            uint64_t tot = 0, rlo = 0;
+            const uint32_t *elo = nullptr, *ehi = nullptr;
+            const uint64_t *poff = nullptr;
+            if (item < n_items) {
+                // items arrive in increasing order: walk the slice index forward
+                if (d == nullptr || item < d->item0) s = find_slice_by_item(desc, n_slices, item), d = nullptr;
+                while (s + 1 < n_slices && desc[s + 1].item0 <= item) ++s, d = nullptr;
+                if (d == nullptr) {
+                    d = &desc[s];
+                    bad = (d->stats->flags & (TRIG_FLAG_BAD_PMT | TRIG_FLAG_UNSORTED | TRIG_FLAG_OUT_OF_RANGE)) != 0;
+                }
+                g = item - d->item0;
+                P = d->n_pmt;
+                elo = d->e_lo + (size_t)g * P;
+                ehi = d->e_hi + (size_t)g * P;
+                poff = d->pmt_off;
+                if (!bad) {
+                    for (uint32_t p0 = 0; p0 < P; p0 += 32 * R) {
+#pragma unroll
+                        for (int r = 0; r < R; ++r) {
+                            const uint32_t p = p0 + r * 32 + lane;
+                            uint64_t a = 0, e = 0, sp_ = 0, ep_ = 0;
+                            if (p < P) {
+                                a = __ldg(elo + p);
+                                e = __ldg(ehi + p);
+                                sp_ = __ldg(poff + p);
+                                ep_ = __ldg(poff + p + 1);
+                                a = min(max(a, sp_), ep_);
+                                e = min(max(e, a), ep_);
+                            }
+                            ra[r] = a;
+                            rl[r] = (uint32_t)(e - a);
+                            tot += e - a;
+                            rlo += a - sp_;
+                        }
+                    }
+                }
+                tot = warp_sum_u64(tot);
+                rlo = warp_sum_u64(rlo);
+                mode = bad ? 2u : (tot > (uint64_t)CAP ? 1u : (tot == 0 ? 2u : 0u));
+            }
+            uint32_t next = 0;
+            if (item < n_items) {
+                if (lane == 0) next = atomicAdd(&hdr->queue, 1u);
+                next = __shfl_sync(0xffffffffu, next, 0);
+            }
             if (it >= 2 && !mbar_wait(&empty_bar[b], (use - 1) & 1u)) {
                 if (lane == 0) atomicOr(&hdr->err, TRIG_FLAG_TIMEOUT);
                 break;
             }
-            uint32_t item = 0;
-            if (lane == 0) item = atomicAdd(&hdr->queue, 1u);
-            item = __shfl_sync(0xffffffffu, item, 0);
             if (item >= n_items) {
                 if (lane == 0) {
                     info[b].item = -1;
@@ -810,27 +1025,6 @@ __global__ void __launch_bounds__(kNC + 32, 1) k_tile(BatchHeader *__restrict__ 
                 }
                 break;
             }
-            const uint32_t s = find_slice_by_item(desc, n_slices, item);
-            const SliceDesc &d = desc[s];
-            const uint32_t g = item - d.item0, P = d.n_pmt;
-            const bool bad = (d.stats->flags & (TRIG_FLAG_BAD_PMT | TRIG_FLAG_UNSORTED | TRIG_FLAG_OUT_OF_RANGE)) != 0;
-            uint64_t tot = 0, rlo = 0;
-            if (!bad) {
-                for (uint32_t p0 = 0; p0 < P; p0 += 32) {
-                    uint32_t p = p0 + lane;
-                    if (p < P) {
-                        uint64_t sp_ = d.pmt_off[p], ep_ = d.pmt_off[p + 1];
-                        uint64_t a = d.e_lo[(size_t)g * P + p], e = d.e_hi[(size_t)g * P + p];
-                        a = min(max(a, sp_), ep_);
-                        e = min(max(e, a), ep_);
-                        tot += e - a;
-                        rlo += a - sp_;
-                    }
-                }
-            }
-            tot = warp_sum_u64(tot);
-            rlo = warp_sum_u64(rlo);
-            const uint32_t mode = bad ? 2u : (tot > (uint64_t)CAP ? 1u : (tot == 0 ? 2u : 0u));
             if (lane == 0) {
                 info[b].item = (int32_t)item;
                 info[b].slice = s;
@@ -844,30 +1038,40 @@ __global__ void __launch_bounds__(kNC + 32, 1) k_tile(BatchHeader *__restrict__ 
             __syncwarp();
             if (mode == 0) {
                 uint32_t dst = 0;
-                for (uint32_t p0 = 0; p0 < P; p0 += 32) {
-                    uint32_t p = p0 + lane;
-                    uint32_t len = 0;
-                    uint64_t a = 0;
-                    if (p < P) {
-                        uint64_t sp_ = d.pmt_off[p], ep_ = d.pmt_off[p + 1];
-                        a = d.e_lo[(size_t)g * P + p];
-                        uint64_t e = d.e_hi[(size_t)g * P + p];
-                        a = min(max(a, sp_), ep_);
-                        e = min(max(e, a), ep_);
-                        len = (uint32_t)(e - a);
+                for (uint32_t p0 = 0; p0 < P; p0 += 32 * R) {
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        uint32_t len = rl[r];
+                        uint64_t a = ra[r];
+                        if (P > 32 * R) {
+                            // wide detectors: registers hold only the last group; reload
+                            const uint32_t p = p0 + r * 32 + lane;
+                            len = 0;
+                            if (p < P) {
+                                const uint64_t sp_ = __ldg(poff + p), ep_ = __ldg(poff + p + 1);
+                                a = min(max((uint64_t)__ldg(elo + p), sp_), ep_);
+                                const uint64_t e = min(max((uint64_t)__ldg(ehi + p), a), ep_);
+                                len = (uint32_t)(e - a);
+                            }
+                        }
+                        const uint32_t incl = warp_incl_scan(len);
+                        if (len)
+                            bulk_g2s(cx.stage[b] + 2 * (size_t)(dst + incl - len), d->hits + a, len * 16u,
+                                     &full_bar[b]);
+                        dst += __shfl_sync(0xffffffffu, incl, 31);
                     }
-                    uint32_t incl = warp_incl_scan(len);
-                    if (len) bulk_g2s(cx.stage[b] + 2 * (size_t)(dst + incl - len), d.hits + a, len * 16u,
-                                      &full_bar[b]);
-                    dst += __shfl_sync(0xffffffffu, incl, 31);
                 }
             }
+            item = next;
         }
         return;
     }
 
     // ---------------------------------------------------- consumer warps
     const SliceDesc *loaded = nullptr;
+    TrigParams tp{};
+    int64_t sl_w = 0, sl_t0 = 0, sl_len = 0;
+    uint64_t sl_rank0 = 0;
     for (uint32_t it = 0;; ++it) {
         const uint32_t b = it & 1u, use = it >> 1;
         if (!mbar_wait(&full_bar[b], use & 1u)) {
@@ -879,18 +1083,28 @@ __global__ void __launch_bounds__(kNC + 32, 1) k_tile(BatchHeader *__restrict__ 
         const SliceDesc &d = desc[inf.slice];
         if (&d != loaded) {
             // (re)load the detector tables of this slice
-            cons_sync();
+            cons_sync<NC>();
             const uint32_t P = d.n_pmt;
-            for (uint32_t p = tid; p < P; p += kNC) {
+            for (uint32_t p = tid; p < P; p += NC) {
                 cx.floor_s[p] = d.floor[p];
                 cx.dmax_s[p] = d.dmax_row[p];
             }
             if (SMEM_DT && P <= kSmemDtMaxPmt)
-                for (uint32_t i = tid; i < P * P; i += kNC) cx.dt_s[i] = d.dt[i];
+                for (uint32_t i = tid; i < P * P; i += NC) cx.dt_s[i] = d.dt[i];
             cx.dt_g = d.dt;
             cx.P = P;
             loaded = &d;
-            cons_sync();
+            tp.H = d.halo;
+            tp.tau = d.tau;
+            tp.q_seed = d.q_seed;
+            tp.threshold = d.threshold;
+            tp.dbg_merged = d.dbg_merged;
+            tp.dbg_seedcnt = d.dbg_seedcnt;
+            sl_w = d.tile_w;
+            sl_t0 = d.t0;
+            sl_len = d.slice_ns;
+            sl_rank0 = d.dbg_rank0;
+            cons_sync<NC>();
         }
         if (inf.mode == 2) {
             if (tid == 0) {
@@ -898,21 +1112,20 @@ __global__ void __launch_bounds__(kNC + 32, 1) k_tile(BatchHeader *__restrict__ 
                 d.tile_rank[inf.g] = 0;
             }
         } else if (inf.mode == 1) {
-            tile_overflow<CAP, SMEM_DT>(cx, cx.stage[b], d, inf.g, red, stk);
+            tile_overflow<CAP, NC, SMEM_DT>(cx, cx.stage[b], d, tp, inf.g, red, stk);
         } else {
-            const int64_t W = (int64_t)1 << d.wshift;
-            const int64_t Bg = d.t0 + (int64_t)inf.g * W;
-            const int64_t core_end = min(Bg + W, d.t0 + d.slice_ns);
-            const uint32_t H = d.halo;
+            const int64_t W = sl_w;
+            const int64_t Bg = sl_t0 + (int64_t)inf.g * W;
+            const int64_t core_end = min(Bg + W, sl_t0 + sl_len);
+            const uint32_t H = tp.H;
             const int64_t tb = Bg - (int64_t)H;
             const uint32_t span = (uint32_t)W + 2 * H;
-            tile_sort<CAP>(cx, cx.stage[b], inf.n, tb, span, red);
+            tile_sort<CAP, NC>(cx, cx.stage[b], inf.n, tb, span, red, H, H + (uint32_t)(core_end - Bg));
             // rank of the core's first hit = rank_lo + c0, known after the sort
-            const uint32_t c0 = lb_key(cx.stage[b], inf.n, (uint64_t)H << 32);
+            const uint32_t c0 = red[NW + 1], c1 = red[NW + 2];
             const uint32_t tile_rank = inf.rank_lo + c0;
-            CoreOut co = tile_trigger<CAP, SMEM_DT>(cx, cx.stage[b], inf.n, H, (uint32_t)(core_end - Bg), tb, d,
-                                                     d.stage + tile_rank,
-                                                     (int64_t)inf.rank_lo - (int64_t)d.dbg_rank0, red);
+            CoreOut co = tile_trigger<CAP, NC, SMEM_DT>(cx, cx.stage[b], inf.n, c0, c1, tb, tp, d.stage + tile_rank,
+                                                         (int64_t)inf.rank_lo - (int64_t)sl_rank0, red);
             if (tid == 0) {
                 d.tile_nfired[inf.g] = co.n_fired;
                 d.tile_rank[inf.g] = tile_rank;
@@ -922,48 +1135,72 @@ __global__ void __launch_bounds__(kNC + 32, 1) k_tile(BatchHeader *__restrict__ 
         // release the buffer to the producer: order our generic-proxy
         // accesses before its next bulk copy into the same buffer
         fence_proxy_async_smem();
-        cons_sync();
+        cons_sync<NC>();
         if (tid == 0) mbar_arrive(&empty_bar[b]);
     }
 }
 
 // ------------------------------------------------------------------ k_scan
 
-__global__ void __launch_bounds__(1024) k_scan(const BatchHeader *__restrict__ hdr, const SliceDesc *__restrict__ desc)
+// Block-wide exclusive scan of vals[0..n) into out[0..n); returns the total.
+__device__ unsigned long long block_scan_u32(const uint32_t *vals, uint32_t *out, uint32_t n, uint32_t *wsum,
+                                             unsigned long long *carry)
 {
-    const uint32_t s = blockIdx.x;
-    if (s >= hdr->n_slices) return;
-    const SliceDesc &d = desc[s];
-    const uint32_t NG = d.n_tiles, tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
-    __shared__ uint32_t wsum[32];
-    __shared__ unsigned long long carry;
-    if (tid == 0) carry = 0;
+    const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5, nw = blockDim.x >> 5;
+    if (tid == 0) *carry = 0;
     __syncthreads();
-    for (uint32_t base = 0; base < NG; base += blockDim.x) {
+    for (uint32_t base = 0; base < n; base += blockDim.x) {
         uint32_t g = base + tid;
-        uint32_t v = g < NG ? d.tile_nfired[g] : 0u;
+        uint32_t v = g < n ? vals[g] : 0u;
         uint32_t incl = warp_incl_scan(v);
         if (lane == 31) wsum[warp] = incl;
         __syncthreads();
         if (warp == 0) {
-            uint32_t w = lane < (blockDim.x >> 5) ? wsum[lane] : 0u;
+            uint32_t w = lane < nw ? wsum[lane] : 0u;
             uint32_t wi = warp_incl_scan(w);
             wsum[lane] = wi - w;
         }
         __syncthreads();
-        unsigned long long c = carry;
-        if (g < NG) d.tile_out[g] = (uint32_t)(c + wsum[warp] + incl - v);
+        unsigned long long c = *carry;
+        if (g < n) out[g] = (uint32_t)(c + wsum[warp] + incl - v);
         __syncthreads();
-        if (tid == blockDim.x - 1) carry = c + wsum[warp] + incl;
+        if (tid == blockDim.x - 1) *carry = c + wsum[warp] + incl;
         __syncthreads();
     }
-    if (tid == 0) {
-        d.stats->n_triggers = carry;
-        if (carry > d.trig_cap) atomicOr(&d.stats->flags, TRIG_FLAG_TRIG_FULL);
+    return *carry;
+}
+
+__global__ void __launch_bounds__(1024) k_scan(const BatchHeader *__restrict__ hdr, const SliceDesc *__restrict__ desc)
+{
+    __shared__ uint32_t wsum[32];
+    __shared__ unsigned long long carry;
+    for (uint32_t s = blockIdx.x; s < hdr->n_slices; s += gridDim.x) {
+        const SliceDesc &d = desc[s];
+        unsigned long long F = block_scan_u32(d.tile_nfired, d.tile_out, d.n_tiles, wsum, &carry);
+        if (threadIdx.x == 0) {
+            d.stats->n_triggers = F;
+            if (F > d.trig_cap) atomicOr(&d.stats->flags, TRIG_FLAG_TRIG_FULL);
+        }
+        __syncthreads();
     }
 }
 
 // ------------------------------------------------------------------ k_copy
+
+// One warp per tile: copy its fired seeds into the dense trigger list and
+// count the window heads among them.  A trigger starts a new window unless
+// it lies within 2h + 1 ns of the previous trigger of the slice (windows
+// [t - h, t + h] merge while lo_next <= hi_cur + 1).
+__device__ __forceinline__ uint32_t find_tile_of_pos(const uint32_t *tile_out, uint32_t ng, uint32_t pos)
+{
+    // last tile g with tile_out[g] <= pos
+    uint32_t lo = 0, hi = ng;
+    while (hi - lo > 1) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (tile_out[mid] <= pos) lo = mid; else hi = mid;
+    }
+    return lo;
+}
 
 __global__ void __launch_bounds__(256) k_copy(const BatchHeader *__restrict__ hdr, const SliceDesc *__restrict__ desc)
 {
@@ -976,90 +1213,172 @@ __global__ void __launch_bounds__(256) k_copy(const BatchHeader *__restrict__ hd
         const SliceDesc &d = desc[s];
         const uint32_t g = item - d.item0;
         const uint32_t F = d.tile_nfired[g];
-        if (!F) continue;
+        if (!F) {
+            if (lane == 0) d.tile_nwin[g] = 0;
+            continue;
+        }
         const trig_trigger *src = d.stage + d.tile_rank[g];
         const uint64_t o = d.tile_out[g];
-        for (uint32_t f = lane; f < F; f += 32) {
-            if (o + f < d.trig_cap) {
+        const int64_t gap = 2 * (int64_t)d.win_half + 1;
+        // the slice's trigger before this tile's first: last of the previous non-empty tile
+        int64_t t_before = 0;
+        const bool has_before = o > 0;
+        if (has_before) {
+            uint32_t gp = find_tile_of_pos(d.tile_out, d.n_tiles, (uint32_t)(o - 1));
+            t_before = d.stage[d.tile_rank[gp] + (uint32_t)(o - 1 - d.tile_out[gp])].t_ns;
+        }
+        uint32_t heads = 0;
+        for (uint32_t f0 = 0; f0 < F; f0 += 32) {
+            const uint32_t f = f0 + lane;
+            int64_t t = 0;
+            bool head = false;
+            if (f < F) {
                 int4 v = *reinterpret_cast<const int4 *>(src + f);
-                *reinterpret_cast<int4 *>(d.triggers + o + f) = v;
+                if (o + f < d.trig_cap) *reinterpret_cast<int4 *>(d.triggers + o + f) = v;
+                t = (int64_t)(((uint64_t)(uint32_t)v.y << 32) | (uint32_t)v.x);
+                int64_t tp = f ? src[f - 1].t_ns : t_before;
+                head = (f == 0 && !has_before) || (t - tp > gap);
             }
+            heads += __popc(__ballot_sync(0xffffffffu, head));
+        }
+        if (lane == 0) d.tile_nwin[g] = heads;
+    }
+}
+
+// ----------------------------------------------------------------- k_wscan
+
+__global__ void __launch_bounds__(1024) k_wscan(const BatchHeader *__restrict__ hdr, const SliceDesc *__restrict__ desc)
+{
+    __shared__ uint32_t wsum[32];
+    __shared__ unsigned long long carry;
+    for (uint32_t s = blockIdx.x; s < hdr->n_slices; s += gridDim.x) {
+        const SliceDesc &d = desc[s];
+        unsigned long long nw = block_scan_u32(d.tile_nwin, d.tile_wout, d.n_tiles, wsum, &carry);
+        if (threadIdx.x == 0) {
+            d.stats->n_windows = nw;
+            if (nw > d.win_cap) atomicOr(&d.stats->flags, TRIG_FLAG_WIN_FULL);
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- k_wwrite
+
+// One warp per tile: window w of a head trigger is tile_wout[g] plus the
+// heads before it in the tile; heads write lo and the first trigger index,
+// tails (the next trigger is a head, or none follows) write hi and the last.
+__global__ void __launch_bounds__(256) k_wwrite(const BatchHeader *__restrict__ hdr, const SliceDesc *__restrict__ desc)
+{
+    const uint32_t n_items = hdr->n_items, n_slices = hdr->n_slices;
+    const uint32_t lane = lane_id();
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t item = gw; item < n_items; item += nw) {
+        const uint32_t s = find_slice_by_item(desc, n_slices, item);
+        const SliceDesc &d = desc[s];
+        if (d.stats->flags & TRIG_FLAG_TRIG_FULL) continue;      // triggers incomplete
+        const uint32_t g = item - d.item0;
+        const uint32_t F = d.tile_nfired[g];
+        if (!F) continue;
+        const uint64_t o = d.tile_out[g];
+        const uint64_t nt = d.stats->n_triggers;
+        const trig_trigger *T = d.triggers;
+        const int64_t gap = 2 * (int64_t)d.win_half + 1;
+        const int64_t h = d.win_half;
+        uint64_t w_run = d.tile_wout[g];     // windows started before this tile
+        for (uint32_t f0 = 0; f0 < F; f0 += 32) {
+            const uint32_t f = f0 + lane;
+            const uint64_t k = o + f;
+            bool head = false, tail = false;
+            int64_t t = 0;
+            if (f < F) {
+                t = T[k].t_ns;
+                head = (k == 0) || (t - T[k - 1].t_ns > gap);
+                tail = (k + 1 == nt) || (T[k + 1].t_ns - t > gap);
+            }
+            const uint32_t m = __ballot_sync(0xffffffffu, head);
+            const uint64_t w = w_run + __popc(m & ((2u << lane) - 1u)) - 1;   // window of trigger k
+            if (head && w < d.win_cap) {
+                d.windows[w].lo_ns = t - h;
+                d.windows[w].n_triggers = k;        // first trigger, turned into a count by k_whits
+            }
+            if (tail && w < d.win_cap) {
+                d.windows[w].hi_ns = t + h;
+                d.windows[w].n_hits = k;            // last trigger, turned into the hit count by k_whits
+            }
+            w_run += __popc(m);
         }
     }
 }
 
-// --------------------------------------------------------------- k_windows
+// ----------------------------------------------------------------- k_whits
 
-// Windows [t - h, t + h] of consecutive triggers (already in time order)
-// belong to one merged window unless t_k - t_{k-1} > 2h + 1.  Each thread
-// takes a contiguous run of triggers; a block scan gives the window index.
-__global__ void __launch_bounds__(512) k_windows(const BatchHeader *__restrict__ hdr, const SliceDesc *__restrict__ desc)
+// Hit rank of time x in PMT p's stream, narrowed by the tile edges the
+// structure pass recorded: x in tile g's core lies between the PMT's
+// offsets at B_g - H and B_{g+1} + H, so the binary search covers a handful
+// of hits.  Outside the slice the first or last tile's outer edge bounds it.
+__device__ __forceinline__ uint64_t rank_in_pmt(const SliceDesc &d, uint32_t p, int64_t x, uint64_t sp, uint64_t ep)
 {
-    const uint32_t s = blockIdx.x;
-    if (s >= hdr->n_slices) return;
-    const SliceDesc &d = desc[s];
-    const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5, nt = blockDim.x;
-    __shared__ uint32_t wsum[32];
-    __shared__ unsigned long long total_w;
-    const uint64_t F = min((unsigned long long)d.stats->n_triggers, (unsigned long long)d.trig_cap);
-    const int64_t h = d.win_half;
-    const int64_t gap = 2 * h + 1;
-    const trig_trigger *T = d.triggers;
-    const uint64_t per = (F + nt - 1) / nt;
-    const uint64_t k0 = min(F, (uint64_t)tid * per), k1 = min(F, k0 + per);
-    auto is_head = [&](uint64_t k) -> bool { return k == 0 || T[k].t_ns - T[k - 1].t_ns > gap; };
-    uint32_t heads = 0;
-    for (uint64_t k = k0; k < k1; ++k) heads += is_head(k);
-    uint32_t incl = warp_incl_scan(heads);
-    if (lane == 31) wsum[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        uint32_t w = lane < (nt >> 5) ? wsum[lane] : 0u;
-        uint32_t wi = warp_incl_scan(w);
-        wsum[lane] = wi - w;
-        if (lane == (nt >> 5) - 1) total_w = wi;
-    }
-    __syncthreads();
-    const uint64_t W = total_w;
-    const uint64_t cap = d.win_cap;
-    // window index of trigger k = (#heads in [0, k]) - 1
-    uint64_t w = (uint64_t)wsum[warp] + incl - heads;   // heads before k0
-    for (uint64_t k = k0; k < k1; ++k) {
-        if (is_head(k)) {
-            if (w < cap) {
-                d.windows[w].lo_ns = T[k].t_ns - h;
-                d.windows[w].n_triggers = k;          // first trigger, fixed below
+    const int64_t W = d.tile_w;
+    const int64_t rel = x - d.t0;
+    int64_t g = rel < 0 ? 0 : rel / W;
+    if (g >= (int64_t)d.n_tiles) g = (int64_t)d.n_tiles - 1;
+    const int64_t Bg = d.t0 + g * W;
+    const size_t at = (size_t)g * d.n_pmt + p;
+    uint64_t lo = sp, hi = ep;
+    const uint64_t a = d.e_lo[at], b = d.e_hi[at];
+    if (x >= Bg - (int64_t)d.halo) lo = max(lo, min(a, ep));
+    if (x <= Bg + W + (int64_t)d.halo) hi = min(hi, max(b, lo));
+    return lb_time(d.hits, lo, hi, x);
+}
+
+// Hits of the submission inside each window: sum over PMTs of the hits in
+// [lo, hi] of that PMT's stream.  A warp per window over the whole batch
+// (lanes take PMTs); the window's slice comes from a prefix over slices.
+__global__ void __launch_bounds__(256) k_whits(const BatchHeader *__restrict__ hdr, const SliceDesc *__restrict__ desc)
+{
+    __shared__ unsigned long long pre[1025];
+    const uint32_t lane = lane_id();
+    const uint32_t n_slices = hdr->n_slices;
+    const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint32_t s0 = 0; s0 < n_slices; s0 += 1024) {
+        const uint32_t ns = min(1024u, n_slices - s0);
+        if (threadIdx.x == 0) {
+            unsigned long long run = 0;
+            for (uint32_t i = 0; i < ns; ++i) {
+                pre[i] = run;
+                const SliceDesc &d = desc[s0 + i];
+                if (!(d.stats->flags & (TRIG_FLAG_TRIG_FULL | TRIG_FLAG_BAD_PMT | TRIG_FLAG_UNSORTED |
+                                        TRIG_FLAG_OUT_OF_RANGE)))
+                    run += min((unsigned long long)d.stats->n_windows, (unsigned long long)d.win_cap);
             }
-            ++w;
+            pre[ns] = run;
         }
-        bool tail = (k + 1 == F) || is_head(k + 1);
-        if (tail && w - 1 < cap) {
-            d.windows[w - 1].hi_ns = T[k].t_ns + h;
-            d.windows[w - 1].n_hits = k;              // last trigger, fixed below
+        __syncthreads();
+        const unsigned long long total = pre[ns];
+        for (uint64_t wi = gw; wi < total; wi += nw) {
+            uint32_t lo = 0, hi = ns;                     // slice: last i with pre[i] <= wi
+            while (hi - lo > 1) {
+                uint32_t mid = (lo + hi) >> 1;
+                if (pre[mid] <= wi) lo = mid; else hi = mid;
+            }
+            const SliceDesc &d = desc[s0 + lo];
+            const uint64_t i = wi - pre[lo];
+            const trig_window win = d.windows[i];
+            uint64_t cnt = 0;
+            for (uint32_t p = lane; p < d.n_pmt; p += 32) {
+                const uint64_t sp = d.pmt_off[p], ep = d.pmt_off[p + 1];
+                cnt += rank_in_pmt(d, p, win.hi_ns + 1, sp, ep) - rank_in_pmt(d, p, win.lo_ns, sp, ep);
+            }
+            cnt = warp_sum_u64(cnt);
+            __syncwarp();
+            if (lane == 0) {
+                d.windows[i].n_triggers = win.n_hits - win.n_triggers + 1;
+                d.windows[i].n_hits = cnt;
+            }
         }
-    }
-    __syncthreads();
-    const uint64_t Wn = min(W, cap);
-    if (tid == 0) {
-        d.stats->n_windows = W;
-        if (W > cap) atomicOr(&d.stats->flags, TRIG_FLAG_WIN_FULL);
-    }
-    const uint32_t P = d.n_pmt;
-    for (uint64_t i = warp; i < Wn; i += nt >> 5) {
-        trig_window win = d.windows[i];
-        uint64_t cnt = 0;
-        for (uint32_t p = lane; p < P; p += 32) {
-            uint64_t sp = d.pmt_off[p], ep = d.pmt_off[p + 1];
-            uint64_t a = lb_time(d.hits, sp, ep, win.lo_ns);
-            uint64_t b = lb_time(d.hits, a, ep, win.hi_ns + 1);
-            cnt += b - a;
-        }
-        cnt = warp_sum_u64(cnt);
-        __syncwarp();
-        if (lane == 0) {
-            d.windows[i].n_triggers = win.n_hits - win.n_triggers + 1;
-            d.windows[i].n_hits = cnt;
-        }
+        __syncthreads();
     }
 }
 
@@ -1122,44 +1441,64 @@ int device_sm_count()
     return n > 0 ? n : 1;
 }
 
-template <int CAP, bool SMEM_DT>
+template <int CAP, int NC, bool SMEM_DT>
 static cudaError_t launch_tile(BatchHeader *hdr, SliceDesc *desc, uint32_t max_pmt, cudaStream_t st)
 {
     size_t smem = TileLayout<CAP>::bytes(max_pmt, SMEM_DT);
-    auto kern = k_tile<CAP, SMEM_DT>;
+    auto kern = k_tile<CAP, NC, SMEM_DT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kNC + 32, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NC + 32, smem);
     if (per_sm < 1) per_sm = 1;
-    kern<<<device_sm_count() * per_sm, kNC + 32, smem, st>>>(hdr, desc, max_pmt);
+    kern<<<device_sm_count() * per_sm, NC + 32, smem, st>>>(hdr, desc, max_pmt);
     return cudaGetLastError();
 }
 
+const char *const kKernelNames[kPipelineKernels] = {"k_prep", "k_bounds", "k_tile",  "k_scan",  "k_copy",
+                                                     "k_wscan", "k_wwrite", "k_whits", "k_status"};
+
 cudaError_t launch_batch(BatchHeader *d_hdr, SliceDesc *d_desc, uint32_t n_slices, uint32_t max_pmt,
-                         bool any_smem_dt, const TileConfig &cfg, cudaStream_t st, uint64_t *launches, bool rows)
+                         bool any_smem_dt, const TileConfig &cfg, cudaStream_t st, uint64_t *launches, bool rows,
+                         cudaEvent_t *ev)
 {
     const int sms = device_sm_count();
+    auto mark = [&](int i) {
+        if (ev) cudaEventRecord(ev[i], st);
+    };
+    const uint32_t sb = n_slices < (uint32_t)sms * 4 ? n_slices : (uint32_t)sms * 4;
+    mark(0);
     k_prep<<<1, 256, 0, st>>>(d_hdr, d_desc);
-    k_bounds<<<sms * 8, 256, 0, st>>>(d_hdr, d_desc);
+    mark(1);
+    k_bounds<<<sms * 8, kBoundsThreads, 0, st>>>(d_hdr, d_desc);
     if (rows) {
         k_rank0<<<n_slices, 256, 0, st>>>(d_hdr, d_desc);
         if (launches) *launches += 1;
     }
+    mark(2);
     cudaError_t e;
     const bool smem_dt = any_smem_dt && max_pmt <= kSmemDtMaxPmt;
     if (cfg.cap == 2048)
-        e = smem_dt ? launch_tile<2048, true>(d_hdr, d_desc, max_pmt, st)
-                    : launch_tile<2048, false>(d_hdr, d_desc, max_pmt, st);
+        e = smem_dt ? launch_tile<2048, 256, true>(d_hdr, d_desc, max_pmt, st)
+                    : launch_tile<2048, 256, false>(d_hdr, d_desc, max_pmt, st);
     else
-        e = smem_dt ? launch_tile<4096, true>(d_hdr, d_desc, max_pmt, st)
-                    : launch_tile<4096, false>(d_hdr, d_desc, max_pmt, st);
+        e = smem_dt ? launch_tile<4096, 512, true>(d_hdr, d_desc, max_pmt, st)
+                    : launch_tile<4096, 512, false>(d_hdr, d_desc, max_pmt, st);
     if (e != cudaSuccess) return e;
-    k_scan<<<n_slices, 1024, 0, st>>>(d_hdr, d_desc);
+    mark(3);
+    k_scan<<<sb, 1024, 0, st>>>(d_hdr, d_desc);
+    mark(4);
     k_copy<<<sms * 4, 256, 0, st>>>(d_hdr, d_desc);
-    k_windows<<<n_slices, 512, 0, st>>>(d_hdr, d_desc);
+    mark(5);
+    k_wscan<<<sb, 1024, 0, st>>>(d_hdr, d_desc);
+    mark(6);
+    k_wwrite<<<sms * 4, 256, 0, st>>>(d_hdr, d_desc);
+    mark(7);
+    k_whits<<<sms * 4, 256, 0, st>>>(d_hdr, d_desc);
+    mark(8);
     k_status<<<1, 256, 0, st>>>(d_hdr, d_desc);
-    if (launches) *launches += 7;
+    mark(9);
+    if (launches) *launches += kPipelineKernels;
     return cudaGetLastError();
 }
 

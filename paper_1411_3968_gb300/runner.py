@@ -57,10 +57,10 @@ class DeviceBatch:
         self.n_hits = sum(len(s.hits) for s in slices)
         self.input_bytes = sum(s.hits.nbytes + np.asarray(s.pmt_off).nbytes for s in slices)
 
-    def run(self, graph: bool = False, stream=None) -> None:
+    def run(self, graph: bool = False, stream=None, timed: bool = False) -> None:
         st = stream if stream is not None else torch.cuda.current_stream(self.device)
-        _lib.trig_batch_run(self.descs, self.scratch.data_ptr(), self.scratch_bytes, st.cuda_stream,
-                            _lib.TRIG_RUN_GRAPH if graph else 0)
+        flags = (_lib.TRIG_RUN_GRAPH if graph else 0) | (_lib.TRIG_RUN_TIMED if timed else 0)
+        _lib.trig_batch_run(self.descs, self.scratch.data_ptr(), self.scratch_bytes, st.cuda_stream, flags)
 
     def run_each(self, stream=None) -> None:
         """Plain per-slice launches: one launch sequence per slice."""
