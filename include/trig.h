@@ -224,6 +224,30 @@ size_t trig_batch_scratch_bytes(const trig_slice_dev *slices, uint32_t n_slices)
 int trig_batch_run(const trig_slice_dev *slices, uint32_t n_slices, void *scratch, size_t scratch_bytes,
                    void *stream, uint32_t flags);
 
+/* The same hot path as trig_batch_run for callers that cannot allocate
+ * device memory: a trigger node's real-time acquisition thread (cudaMalloc
+ * can synchronise the whole device and stall it for milliseconds) or code
+ * that runs while another thread captures a CUDA graph in global mode
+ * (where cudaMalloc is refused).  The scratch is a static device array of
+ * TRIG_NOALLOC_SCRATCH_BYTES inside the library, held by every device that
+ * loads it until the process exits; the caller still passes inputs and
+ * outputs as for trig_batch_run.  Nothing is allocated: no cudaMalloc,
+ * cudaFree or allocating library call.  The paper has no counterpart; this
+ * is a deployment interface.
+ *   - At most TRIG_NOALLOC_MAX_SLICES slices; a batch whose scratch would
+ *     exceed the array (about 3.9 M hits at 16 B of staging per hit) is
+ *     rejected with TRIG_ECAPACITY before anything is launched.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream
+ *     capture.
+ *   - All calls share the array and it keeps the last call's contents; the
+ *     library clears what must start at zero.  Calls whose work overlaps on
+ *     the GPU (different streams, or different host threads) race on it:
+ *     serialise them. */
+#define TRIG_NOALLOC_SCRATCH_BYTES (64u << 20)
+#define TRIG_NOALLOC_MAX_SLICES 16u
+int trig_batch_run_noalloc(const trig_slice_dev *slices, uint32_t n_slices, void *stream);
+
 /* Row-level view of one slice for verification: writes the owned hits in
  * merged (t, pmt, charge) order to merged_out (device, n_hits entries; the
  * owned hits start at index 0) and, for each of them, its causal count if

@@ -41,8 +41,11 @@ EXPORTS = [
     "trig_create", "trig_destroy", "trig_detector_dtmax", "trig_detector_halo_ns", "trig_submit_slice",
     "trig_poll", "trig_result_free", "trig_engine_set_mode", "trig_engine_stats", "trig_last_error",
     "trig_batch_scratch_bytes", "trig_batch_run", "trig_slice_rows", "trig_set_tile_config",
-    "trig_get_tile_config", "trig_kernel_launch_count", "trig_kernel_times",
+    "trig_get_tile_config", "trig_kernel_launch_count", "trig_kernel_times", "trig_batch_run_noalloc",
 ]
+
+NOALLOC_SCRATCH_BYTES = 64 << 20
+NOALLOC_MAX_SLICES = 16
 
 
 class TrigError(RuntimeError):
@@ -109,6 +112,7 @@ def load(path: str | None = None):
         "trig_set_tile_config": (c.c_int, [c.c_uint32, c.c_uint32]),
         "trig_get_tile_config": (c.c_int, [c.POINTER(c.c_uint32), c.POINTER(c.c_uint32)]),
         "trig_kernel_launch_count": (c.c_uint64, []),
+        "trig_batch_run_noalloc": (c.c_int, [c.POINTER(trig_slice_dev), c.c_uint32, c.c_void_p]),
         "trig_kernel_times": (c.c_int, [c.POINTER(c.c_double), c.POINTER(c.c_char_p), c.c_uint32,
                                         c.POINTER(c.c_uint32)]),
     }
@@ -283,6 +287,12 @@ def trig_batch_scratch_bytes(slices) -> int:
 def trig_batch_run(slices, scratch_ptr: int, scratch_bytes: int, stream_ptr: int = 0, flags: int = 0) -> None:
     arr = _array(slices)
     _check(load().trig_batch_run(arr, len(slices), scratch_ptr, scratch_bytes, stream_ptr or None, flags))
+
+
+def trig_batch_run_noalloc(slices, stream_ptr: int = 0) -> None:
+    """trig_batch_run on the library's static scratch (no allocation)."""
+    arr = _array(slices)
+    _check(load().trig_batch_run_noalloc(arr, len(slices), stream_ptr or None))
 
 
 def trig_slice_rows(s: trig_slice_dev, merged_ptr: int, seedcnt_ptr: int, scratch_ptr: int, scratch_bytes: int,

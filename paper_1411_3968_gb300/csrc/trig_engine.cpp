@@ -33,22 +33,26 @@ using namespace trig;
 
 // ---------------------------------------------------------------- errors
 
-static thread_local std::string g_last_error;
+// Per-thread message of the last failure; a fixed buffer, so reporting an
+// error never allocates.
+static thread_local char g_last_error[256];
 
-static int fail(int code, const std::string &msg)
+static int fail(int code, const char *msg)
 {
-    g_last_error = msg;
+    std::snprintf(g_last_error, sizeof g_last_error, "%s", msg);
     return code;
 }
 
+static int fail(int code, const std::string &msg) { return fail(code, msg.c_str()); }
+
 static int cuda_fail(cudaError_t e, const char *what)
 {
-    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    std::snprintf(g_last_error, sizeof g_last_error, "%s: %s", what, cudaGetErrorString(e));
     (void)cudaGetLastError();
-    return fail(e == cudaErrorMemoryAllocation ? TRIG_ENOMEM : TRIG_EDEVICE, m);
+    return e == cudaErrorMemoryAllocation ? TRIG_ENOMEM : TRIG_EDEVICE;
 }
 
-extern "C" const char *trig_last_error(void) { return g_last_error.c_str(); }
+extern "C" const char *trig_last_error(void) { return g_last_error; }
 
 static std::atomic<uint64_t> g_launches{0};
 extern "C" uint64_t trig_kernel_launch_count(void) { return g_launches.load(); }
@@ -227,17 +231,17 @@ static int64_t choose_tile_w(const trig_detector *det, uint64_t n_hits, const Ti
     return (int64_t)w;
 }
 
-static int make_plan(const trig_slice_dev *sl, uint32_t n, uintptr_t base, const TileConfig &cfg, Plan &pl,
-                     bool rows)
+// Plans a batch into caller-provided storage (no allocation): descriptors
+// desc[0..n), the header, the scratch size and the launch shape.
+static int plan_into(const trig_slice_dev *sl, uint32_t n, uintptr_t base, const TileConfig &cfg, BatchHeader &hdr,
+                     SliceDesc *desc, size_t &bytes, uint32_t &max_pmt, bool &smem_dt)
 {
     if (!sl || n == 0) return fail(TRIG_EINVAL, "no slices");
-    pl.desc.assign(n, SliceDesc{});
     size_t off = align256(sizeof(BatchHeader));
-    const size_t desc_off = off;
     off += align256(sizeof(SliceDesc) * n);
     uint32_t items = 0, chunks = 0;
-    pl.max_pmt = 0;
-    pl.smem_dt = true;
+    max_pmt = 0;
+    smem_dt = true;
     for (uint32_t s = 0; s < n; ++s) {
         const trig_slice_dev &x = sl[s];
         const trig_detector *det = x.det;
@@ -247,10 +251,11 @@ static int make_plan(const trig_slice_dev *sl, uint32_t n, uintptr_t base, const
         if (((uintptr_t)x.hits & 15u) != 0) return fail(TRIG_EINVAL, "hits must be 16-byte aligned");
         if ((x.trig_cap && !x.triggers) || (x.win_cap && !x.windows)) return fail(TRIG_EINVAL, "outputs are NULL");
         if (x.t0_ns < -((int64_t)1 << 61) || x.t0_ns > ((int64_t)1 << 61)) return fail(TRIG_EINVAL, "t0 out of range");
-        SliceDesc &d = pl.desc[s];
+        SliceDesc &d = desc[s];
+        d = SliceDesc{};
         const uint32_t P = det->n_pmt;
-        pl.max_pmt = std::max(pl.max_pmt, P);
-        if (P > kSmemDtMaxPmt) pl.smem_dt = false;
+        max_pmt = std::max(max_pmt, P);
+        if (P > kSmemDtMaxPmt) smem_dt = false;
         d.hits = x.hits;
         d.pmt_off = x.pmt_off;
         d.dt = det->dev.dt;
@@ -304,13 +309,21 @@ static int make_plan(const trig_slice_dev *sl, uint32_t n, uintptr_t base, const
         d.dbg_seedcnt = nullptr;
         d.dbg_rank0 = 0;
     }
-    (void)rows;
-    pl.hdr.n_slices = n;
-    pl.hdr.n_items = items;
-    pl.hdr.n_chunks = chunks;
-    pl.bytes = off;
-    (void)desc_off;
+    hdr = BatchHeader{};
+    hdr.n_slices = n;
+    hdr.n_items = items;
+    hdr.n_chunks = chunks;
+    bytes = off;
     return TRIG_OK;
+}
+
+static int make_plan(const trig_slice_dev *sl, uint32_t n, uintptr_t base, const TileConfig &cfg, Plan &pl,
+                     bool rows)
+{
+    (void)rows;
+    if (!sl || n == 0) return fail(TRIG_EINVAL, "no slices");
+    pl.desc.assign(n, SliceDesc{});
+    return plan_into(sl, n, base, cfg, pl.hdr, pl.desc.data(), pl.bytes, pl.max_pmt, pl.smem_dt);
 }
 
 extern "C" size_t trig_batch_scratch_bytes(const trig_slice_dev *slices, uint32_t n_slices)
@@ -510,6 +523,46 @@ extern "C" int trig_slice_rows(const trig_slice_dev *slice, trig_hit *merged_out
     if (e) return cuda_fail(e, "trig_slice_rows");
     // k_rank0 stored the merged ranks of t0 and t0 + S
     *n_owned_out = back.dbg_rank1 - back.dbg_rank0;
+    return TRIG_OK;
+}
+
+// ------------------------------------------------- no-allocation batch
+
+// Callers on a DAQ node's real-time path, or threads running while another
+// thread captures a CUDA graph in global mode, must not call cudaMalloc (it
+// can synchronise the device and stall the other streams, and it is
+// refused during global capture).  This entry point runs a batch in a
+// static device array compiled into the library instead of caller scratch.
+extern "C" int trig_batch_run_noalloc(const trig_slice_dev *slices, uint32_t n_slices, void *stream)
+{
+    if (!slices || n_slices == 0 || n_slices > TRIG_NOALLOC_MAX_SLICES)
+        return fail(TRIG_EINVAL, "trig_batch_run_noalloc: 1 to TRIG_NOALLOC_MAX_SLICES slices");
+    void *scratch = nullptr;
+    size_t cap = 0;
+    cudaError_t e = static_scratch(&scratch, &cap);
+    if (e) return cuda_fail(e, "trig_batch_run_noalloc: static scratch address");
+    const TileConfig cfg = current_cfg();
+    BatchHeader hdr;
+    SliceDesc desc[TRIG_NOALLOC_MAX_SLICES];
+    size_t bytes = 0;
+    uint32_t max_pmt = 0;
+    bool smem_dt = true;
+    int rc = plan_into(slices, n_slices, (uintptr_t)scratch, cfg, hdr, desc, bytes, max_pmt, smem_dt);
+    if (rc) return rc;
+    if (bytes > cap) return fail(TRIG_ECAPACITY, "trig_batch_run_noalloc: batch needs more than TRIG_NOALLOC_SCRATCH_BYTES of scratch");
+    cudaStream_t st = (cudaStream_t)stream;
+    // pageable sources: both copies are staged before the calls return
+    e = cudaMemcpyAsync(scratch, &hdr, sizeof hdr, cudaMemcpyHostToDevice, st);
+    if (!e)
+        e = cudaMemcpyAsync((char *)scratch + align256(sizeof(BatchHeader)), desc, sizeof(SliceDesc) * n_slices,
+                            cudaMemcpyHostToDevice, st);
+    if (e) return cuda_fail(e, "trig_batch_run_noalloc: copy descriptors");
+    uint64_t nl = 0;
+    e = launch_batch(reinterpret_cast<BatchHeader *>(scratch),
+                     reinterpret_cast<SliceDesc *>((char *)scratch + align256(sizeof(BatchHeader))), n_slices,
+                     max_pmt, smem_dt, cfg, st, &nl, false);
+    g_launches += nl;
+    if (e) return cuda_fail(e, "trig_batch_run_noalloc: launch");
     return TRIG_OK;
 }
 
@@ -1035,7 +1088,7 @@ extern "C" int trig_submit_slice(trig_detector *det, int64_t t0, const trig_hit 
     if (n && !hits) return fail(TRIG_EINVAL, "hits is NULL");
     if (n > kMaxSliceHits) return fail(TRIG_EINVAL, "too many hits in one slice");
     Engine *e = engine();
-    if (!e) return fail(TRIG_EDEVICE, "engine failed to start: " + g_last_error);
+    if (!e) return fail(TRIG_EDEVICE, std::string("engine failed to start: ") + g_last_error);
     Pending p;
     p.det = det;
     p.q = det->q;

@@ -98,4 +98,7 @@ cudaError_t launch_batch(BatchHeader *d_hdr, SliceDesc *d_desc, uint32_t n_slice
 
 int device_sm_count();
 
+// Address and size of the library's static scratch array on the current device.
+cudaError_t static_scratch(void **ptr, size_t *bytes);
+
 }  // namespace trig

@@ -24,6 +24,7 @@
 // Every wait on an mbarrier is bounded; a wait that gives up sets
 // TRIG_FLAG_TIMEOUT on the batch and the kernel returns.
 #include <cstdint>
+#include <mutex>
 #include <cuda_runtime.h>
 
 #include "trig_internal.h"
@@ -1429,6 +1430,37 @@ __global__ void k_status(const BatchHeader *__restrict__ hdr, const SliceDesc *_
         else if (f & (TRIG_FLAG_TILE_FULL | TRIG_FLAG_TRIG_FULL | TRIG_FLAG_WIN_FULL)) status = TRIG_ECAPACITY;
         st->status = status;
     }
+}
+
+// ------------------------------------------------- static scratch array
+
+// Scratch of trig_batch_run_noalloc: a fixed device array, present on every
+// device that loads the library until the process exits.  Calls share it
+// and it keeps the previous call's contents; k_prep clears the counters
+// that must start at zero, and everything else is written before it is
+// read.  Calls that overlap on the GPU race on it.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[TRIG_NOALLOC_SCRATCH_BYTES];
+
+// Device address of the array for the current device, looked up once per
+// device (host code may not use the symbol's name as an address).
+cudaError_t static_scratch(void **ptr, size_t *bytes)
+{
+    static std::mutex mu;
+    static void *addr[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e) return e;
+        addr[dev] = p;
+    }
+    *ptr = addr[dev];
+    *bytes = sizeof(g_noalloc_scratch);
+    return cudaSuccess;
 }
 
 // ------------------------------------------------------------------ launch
