@@ -199,8 +199,10 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=20.0, help="detector-seconds per detector")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--slices", type=int, default=64, help="slices of the batched workload (profiling runs)")
-    ap.add_argument("--tile-cap", type=int, default=0, help="tile capacity override (2048 or 4096)")
-    ap.add_argument("--tile-fill", type=int, default=0, help="tile fill percent override")
+    ap.add_argument("--tile-cap", type=int, default=0, help="tile capacity (2048 or 4096); disables autotuning")
+    ap.add_argument("--tile-warps", type=int, default=0, help="consumer warps per block (8 or 16)")
+    ap.add_argument("--tile-fill", type=int, default=0, help="tile fill percent")
+    ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = _dist()
@@ -244,14 +246,23 @@ def main():
     wl = workload.cfg_batched(seed=args.seed + 1000 * rank)
     wl.submissions = wl.submissions[: args.slices]
     log(f"workload ready: {len(wl.submissions)} slices")
-    if args.tile_cap or args.tile_fill:
-        cap0, fill0 = trig.trig_get_tile_config()
-        trig.trig_set_tile_config(args.tile_cap or cap0, args.tile_fill or fill0)
+    manual = bool(args.tile_cap or args.tile_warps or args.tile_fill)
+    if manual:
+        cap0, warps0, fill0 = trig.trig_get_tile_config()
+        trig.trig_set_tile_config(args.tile_cap or cap0, args.tile_warps or warps0, args.tile_fill or fill0)
     dets = [trig.Detector(g.xyz_mm, g.floor_id, par) for g in wl.detectors]
     slices = [SliceIn(dets[s.det_index], s.t0, s.stream.hits, s.stream.pmt_off) for s in wl.submissions]
     batch = DeviceBatch(slices, device=f"cuda:{local}")
     n_hits = batch.n_hits
     stream = torch.cuda.current_stream()
+    tuned = {}
+    if not manual and not args.no_autotune:
+        # per detector: the launch shape that runs its slices fastest (untimed)
+        for i, det in enumerate(dets):
+            sub = [batch.descs[k] for k, s in enumerate(wl.submissions) if s.det_index == i]
+            if sub:
+                tuned[wl.detectors[i].name] = trig.trig_autotune(det, sub, stream.cuda_stream)
+        log(f"autotuned: {tuned}")
 
     # ------------------------------------------------ batched, graph replay
     log(f"device batch ready: {n_hits} hits")
@@ -379,7 +390,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "slices": len(wl.submissions), "hits_per_rank": n_hits,
-                       "tile": list(trig.trig_get_tile_config()),
+                       "tile": {wl.detectors[i].name: trig.trig_detector_tile_config(d) for i, d in enumerate(dets)},
                        "bytes_per_rank": int(batch.input_bytes), "path": "trig_batch_run, CUDA graph replay",
                        "l2": "inputs larger than L2 (no flush needed)", "parallelism": f"dp{ws} (slices)"},
             "detector_s_per_wall_s": len(wl.submissions) * 0.2 * ws / (ms * 1e-3),

@@ -257,12 +257,32 @@ int trig_batch_run_noalloc(const trig_slice_dev *slices, uint32_t n_slices, void
 int trig_slice_rows(const trig_slice_dev *slice, trig_hit *merged_out, uint32_t *seedcnt_out,
                     uint64_t *n_owned_out, void *scratch, size_t scratch_bytes, void *stream);
 
-/* Device launch configuration of the tile kernel: tile capacity (hits per
- * shared-memory tile including halos) and target fill fraction (percent)
- * used to choose the tile width.  cap must be 2048, 4096 or 8192;
+/* Default launch shape of the tile kernel for detectors that have not been
+ * tuned: tile capacity (hits per shared-memory tile including halos),
+ * consumer warps per block and target fill (percent of the capacity a tile
+ * plus its halos should hold at the slice's mean rate; it sets the tile
+ * width).  (cap, warps) must be (4096, 16), (4096, 8) or (2048, 8);
  * fill_pct in [10, 95].  Applies to later runs in this process. */
-int trig_set_tile_config(uint32_t cap, uint32_t fill_pct);
-int trig_get_tile_config(uint32_t *cap, uint32_t *fill_pct);
+int trig_set_tile_config(uint32_t cap, uint32_t warps, uint32_t fill_pct);
+int trig_get_tile_config(uint32_t *cap, uint32_t *warps, uint32_t *fill_pct);
+
+/* Autotuner: times every launch shape (3 (cap, warps) pairs x 4 fills) on
+ * the given device-resident slices, which must all belong to det, keeps the
+ * fastest on det (later runs use it for det's slices; a batch mixing
+ * detectors takes the shape of the one with the most hits) and, when the
+ * environment variable TRIG_TUNE_CACHE names a file, appends
+ * "<gpu> <n_pmt> <cap> <warps> <fill> <ms>" to it; trig_create applies a
+ * cached entry for the same GPU and PMT count.  Allocates its own scratch
+ * and synchronises the stream. */
+typedef struct {
+    uint32_t cap, warps, fill_pct, n_tried;
+    double ms;                  /* mean time of the chosen shape per batch */
+} trig_tune_result;
+int trig_autotune(trig_detector *det, const trig_slice_dev *slices, uint32_t n_slices, void *stream,
+                  trig_tune_result *out);
+
+/* det's launch shape (tuned or default); returns 1 if tuned, 0 if not. */
+int trig_detector_tile_config(const trig_detector *det, uint32_t *cap, uint32_t *warps, uint32_t *fill_pct);
 
 /* Kernel launches issued by trig_batch_run so far (graph replays count
  * their kernels). */

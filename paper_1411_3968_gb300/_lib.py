@@ -42,6 +42,7 @@ EXPORTS = [
     "trig_poll", "trig_result_free", "trig_engine_set_mode", "trig_engine_stats", "trig_last_error",
     "trig_batch_scratch_bytes", "trig_batch_run", "trig_slice_rows", "trig_set_tile_config",
     "trig_get_tile_config", "trig_kernel_launch_count", "trig_kernel_times", "trig_batch_run_noalloc",
+    "trig_autotune", "trig_detector_tile_config",
 ]
 
 NOALLOC_SCRATCH_BYTES = 64 << 20
@@ -70,6 +71,11 @@ class trig_result(ctypes.Structure):
                 ("flags", ctypes.c_uint32), ("n_hits", ctypes.c_uint64), ("n_seeds", ctypes.c_uint64),
                 ("n_triggers", ctypes.c_uint64), ("n_windows", ctypes.c_uint64), ("triggers", ctypes.c_void_p),
                 ("windows", ctypes.c_void_p), ("latency_ns", ctypes.c_int64)]
+
+
+class trig_tune_result(ctypes.Structure):
+    _fields_ = [("cap", ctypes.c_uint32), ("warps", ctypes.c_uint32), ("fill_pct", ctypes.c_uint32),
+                ("n_tried", ctypes.c_uint32), ("ms", ctypes.c_double)]
 
 
 class trig_slice_dev(ctypes.Structure):
@@ -109,8 +115,12 @@ def load(path: str | None = None):
                                      c.c_uint32]),
         "trig_slice_rows": (c.c_int, [c.POINTER(trig_slice_dev), c.c_void_p, c.c_void_p, c.POINTER(c.c_uint64),
                                       c.c_void_p, c.c_size_t, c.c_void_p]),
-        "trig_set_tile_config": (c.c_int, [c.c_uint32, c.c_uint32]),
-        "trig_get_tile_config": (c.c_int, [c.POINTER(c.c_uint32), c.POINTER(c.c_uint32)]),
+        "trig_set_tile_config": (c.c_int, [c.c_uint32, c.c_uint32, c.c_uint32]),
+        "trig_get_tile_config": (c.c_int, [c.POINTER(c.c_uint32), c.POINTER(c.c_uint32), c.POINTER(c.c_uint32)]),
+        "trig_autotune": (c.c_int, [c.c_void_p, c.POINTER(trig_slice_dev), c.c_uint32, c.c_void_p,
+                                    c.POINTER(trig_tune_result)]),
+        "trig_detector_tile_config": (c.c_int, [c.c_void_p, c.POINTER(c.c_uint32), c.POINTER(c.c_uint32),
+                                                c.POINTER(c.c_uint32)]),
         "trig_kernel_launch_count": (c.c_uint64, []),
         "trig_batch_run_noalloc": (c.c_int, [c.POINTER(trig_slice_dev), c.c_uint32, c.c_void_p]),
         "trig_kernel_times": (c.c_int, [c.POINTER(c.c_double), c.POINTER(c.c_char_p), c.c_uint32,
@@ -238,14 +248,30 @@ def trig_engine_stats() -> tuple[int, int]:
     return int(b.value), int(s.value)
 
 
-def trig_set_tile_config(cap: int, fill_pct: int) -> None:
-    _check(load().trig_set_tile_config(int(cap), int(fill_pct)))
+def trig_set_tile_config(cap: int, warps: int, fill_pct: int) -> None:
+    _check(load().trig_set_tile_config(int(cap), int(warps), int(fill_pct)))
 
 
-def trig_get_tile_config() -> tuple[int, int]:
-    c, f = ctypes.c_uint32(), ctypes.c_uint32()
-    _check(load().trig_get_tile_config(ctypes.byref(c), ctypes.byref(f)))
-    return int(c.value), int(f.value)
+def trig_get_tile_config() -> tuple[int, int, int]:
+    c, w, f = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+    _check(load().trig_get_tile_config(ctypes.byref(c), ctypes.byref(w), ctypes.byref(f)))
+    return int(c.value), int(w.value), int(f.value)
+
+
+def trig_autotune(det: "Detector", slices, stream_ptr: int = 0) -> dict:
+    """Tune det's launch shape on device-resident slices of det."""
+    arr = _array(slices)
+    r = trig_tune_result()
+    _check(load().trig_autotune(det.handle, arr, len(slices), stream_ptr or None, ctypes.byref(r)))
+    return {"cap": r.cap, "warps": r.warps, "fill_pct": r.fill_pct, "n_tried": r.n_tried, "ms": r.ms}
+
+
+def trig_detector_tile_config(det: "Detector") -> dict:
+    c, w, f = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+    t = load().trig_detector_tile_config(det.handle, ctypes.byref(c), ctypes.byref(w), ctypes.byref(f))
+    if t < 0:
+        _check(t)
+    return {"cap": int(c.value), "warps": int(w.value), "fill_pct": int(f.value), "tuned": bool(t)}
 
 
 def trig_kernel_launch_count() -> int:

@@ -58,21 +58,23 @@ static std::atomic<uint64_t> g_launches{0};
 extern "C" uint64_t trig_kernel_launch_count(void) { return g_launches.load(); }
 
 static std::mutex g_cfg_mu;
-static TileConfig g_cfg{4096, 60};
+static TileConfig g_cfg{4096, 16, 60};
 
-extern "C" int trig_set_tile_config(uint32_t cap, uint32_t fill_pct)
+extern "C" int trig_set_tile_config(uint32_t cap, uint32_t warps, uint32_t fill_pct)
 {
-    if ((cap != 2048 && cap != 4096) || fill_pct < 10 || fill_pct > 95)
-        return fail(TRIG_EINVAL, "trig_set_tile_config: cap must be 2048 or 4096, fill_pct in [10, 95]");
+    if (!valid_tile_shape(cap, warps) || fill_pct < 10 || fill_pct > 95)
+        return fail(TRIG_EINVAL, "trig_set_tile_config: (cap, warps) in {(4096,16), (4096,8), (2048,8)}, "
+                                 "fill_pct in [10, 95]");
     std::lock_guard<std::mutex> lk(g_cfg_mu);
-    g_cfg = TileConfig{cap, fill_pct};
+    g_cfg = TileConfig{cap, warps, fill_pct};
     return TRIG_OK;
 }
 
-extern "C" int trig_get_tile_config(uint32_t *cap, uint32_t *fill_pct)
+extern "C" int trig_get_tile_config(uint32_t *cap, uint32_t *warps, uint32_t *fill_pct)
 {
     std::lock_guard<std::mutex> lk(g_cfg_mu);
     if (cap) *cap = g_cfg.cap;
+    if (warps) *warps = g_cfg.warps;
     if (fill_pct) *fill_pct = g_cfg.fill_pct;
     return TRIG_OK;
 }
@@ -82,6 +84,8 @@ static TileConfig current_cfg()
     std::lock_guard<std::mutex> lk(g_cfg_mu);
     return g_cfg;
 }
+
+static bool tune_cache_lookup(uint32_t n_pmt, TileConfig &out);
 
 // ------------------------------------------------------------- detectors
 
@@ -104,6 +108,8 @@ struct trig_detector {
     DetDev dev{};
     int32_t *d_xyz = nullptr;
     std::shared_ptr<DetQueue> q;
+    bool tuned = false;           // tile shape chosen by trig_autotune (or its cache)
+    TileConfig tile{};
 };
 
 static void free_det_dev(trig_detector *d)
@@ -189,6 +195,11 @@ extern "C" int trig_create(const trig_geometry *g, const trig_params *params, tr
     d->in_halo = std::max<int64_t>({(int64_t)params->corr_window_ns, (int64_t)params->win_half_ns,
                                     (int64_t)params->floor_tau_ns});
     d->q = std::make_shared<DetQueue>();
+    TileConfig cached{};
+    if (tune_cache_lookup(P, cached)) {
+        d->tuned = true;
+        d->tile = cached;
+    }
     *out = d.release();
     return TRIG_OK;
 }
@@ -213,6 +224,7 @@ struct Plan {
     size_t bytes = 0;
     uint32_t max_pmt = 0;
     bool smem_dt = true;
+    TileConfig shape{};         // launch shape of this batch
 };
 
 // Tile width W (ns): a tile plus its two halos is expected to hold fill% of
@@ -222,7 +234,8 @@ static int64_t choose_tile_w(const trig_detector *det, uint64_t n_hits, const Ti
 {
     const double span = (double)det->par.slice_ns + 2.0 * (double)det->in_halo;
     const double rate = n_hits > 0 ? (double)n_hits / span : 1e-9;       // hits per ns
-    const double target = (double)cfg.cap * cfg.fill_pct / 100.0;
+    const uint32_t fill = det->tuned ? det->tile.fill_pct : cfg.fill_pct;
+    const double target = (double)cfg.cap * fill / 100.0;
     double w = target / rate - 2.0 * det->tile_halo;
     const double w_min = std::max(256.0, (double)det->par.slice_ns / (double)kMaxTilesPerSlice + 1.0);
     if (w < w_min) w = w_min;
@@ -233,10 +246,30 @@ static int64_t choose_tile_w(const trig_detector *det, uint64_t n_hits, const Ti
 
 // Plans a batch into caller-provided storage (no allocation): descriptors
 // desc[0..n), the header, the scratch size and the launch shape.
-static int plan_into(const trig_slice_dev *sl, uint32_t n, uintptr_t base, const TileConfig &cfg, BatchHeader &hdr,
-                     SliceDesc *desc, size_t &bytes, uint32_t &max_pmt, bool &smem_dt)
+// The launch shape of a batch: the tuned shape of the detector with the
+// most hits in it, else the global configuration.
+static TileConfig batch_shape(const trig_slice_dev *sl, uint32_t n, const TileConfig &cfg)
+{
+    TileConfig out = cfg;
+    uint64_t best = 0;
+    for (uint32_t s = 0; s < n; ++s) {
+        const trig_detector *det = sl[s].det;
+        if (det && det->tuned && sl[s].n_hits >= best) {
+            best = sl[s].n_hits;
+            out.cap = det->tile.cap;
+            out.warps = det->tile.warps;
+        }
+    }
+    return out;
+}
+
+static int plan_into(const trig_slice_dev *sl, uint32_t n, uintptr_t base, const TileConfig &cfg_in,
+                     BatchHeader &hdr, SliceDesc *desc, size_t &bytes, uint32_t &max_pmt, bool &smem_dt,
+                     TileConfig *shape_out = nullptr)
 {
     if (!sl || n == 0) return fail(TRIG_EINVAL, "no slices");
+    const TileConfig cfg = batch_shape(sl, n, cfg_in);
+    if (shape_out) *shape_out = cfg;
     size_t off = align256(sizeof(BatchHeader));
     off += align256(sizeof(SliceDesc) * n);
     uint32_t items = 0, chunks = 0;
@@ -323,7 +356,7 @@ static int make_plan(const trig_slice_dev *sl, uint32_t n, uintptr_t base, const
     (void)rows;
     if (!sl || n == 0) return fail(TRIG_EINVAL, "no slices");
     pl.desc.assign(n, SliceDesc{});
-    return plan_into(sl, n, base, cfg, pl.hdr, pl.desc.data(), pl.bytes, pl.max_pmt, pl.smem_dt);
+    return plan_into(sl, n, base, cfg, pl.hdr, pl.desc.data(), pl.bytes, pl.max_pmt, pl.smem_dt, &pl.shape);
 }
 
 extern "C" size_t trig_batch_scratch_bytes(const trig_slice_dev *slices, uint32_t n_slices)
@@ -346,12 +379,12 @@ static void pack_plan(const Plan &pl, std::vector<unsigned char> &buf)
 struct GraphKey {
     cudaStream_t stream;
     uintptr_t scratch;
-    uint32_t n_slices, max_pmt, cap, fill;
+    uint32_t n_slices, max_pmt, cap, warps;
     bool smem_dt;
     bool operator<(const GraphKey &o) const
     {
-        return std::tie(stream, scratch, n_slices, max_pmt, cap, fill, smem_dt) <
-               std::tie(o.stream, o.scratch, o.n_slices, o.max_pmt, o.cap, o.fill, o.smem_dt);
+        return std::tie(stream, scratch, n_slices, max_pmt, cap, warps, smem_dt) <
+               std::tie(o.stream, o.scratch, o.n_slices, o.max_pmt, o.cap, o.warps, o.smem_dt);
     }
 };
 
@@ -366,9 +399,10 @@ struct GraphEntry {
 static std::mutex g_graph_mu;
 static std::map<GraphKey, GraphEntry> g_graphs;
 
-static int run_graph(const Plan &pl, void *scratch, cudaStream_t st, const TileConfig &cfg)
+static int run_graph(const Plan &pl, void *scratch, cudaStream_t st)
 {
-    GraphKey key{st, (uintptr_t)scratch, pl.hdr.n_slices, pl.max_pmt, cfg.cap, cfg.fill_pct, pl.smem_dt};
+    const TileConfig &cfg = pl.shape;
+    GraphKey key{st, (uintptr_t)scratch, pl.hdr.n_slices, pl.max_pmt, cfg.cap, cfg.warps, pl.smem_dt};
     std::vector<unsigned char> host;
     pack_plan(pl, host);
     std::lock_guard<std::mutex> lk(g_graph_mu);
@@ -463,13 +497,13 @@ extern "C" int trig_kernel_times(double *avg_ms, const char **names, uint32_t ma
     return kPipelineKernels;
 }
 
-static int run_plan(const Plan &pl, void *scratch, size_t scratch_bytes, cudaStream_t st, uint32_t flags,
-                    const TileConfig &cfg, bool rows)
+static int run_plan(const Plan &pl, void *scratch, size_t scratch_bytes, cudaStream_t st, uint32_t flags, bool rows)
 {
+    const TileConfig &cfg = pl.shape;
     if (!scratch || ((uintptr_t)scratch & 255u)) return fail(TRIG_EINVAL, "scratch must be 256-byte aligned device memory");
     if (scratch_bytes < pl.bytes) return fail(TRIG_EINVAL, "scratch too small (see trig_batch_scratch_bytes)");
     if ((flags & TRIG_RUN_GRAPH) && (flags & TRIG_RUN_TIMED)) return fail(TRIG_EINVAL, "TIMED runs cannot use GRAPH");
-    if ((flags & TRIG_RUN_GRAPH) && !rows) return run_graph(pl, scratch, st, cfg);
+    if ((flags & TRIG_RUN_GRAPH) && !rows) return run_graph(pl, scratch, st);
     std::vector<unsigned char> host;
     pack_plan(pl, host);
     cudaError_t e = cudaMemcpyAsync(scratch, host.data(), host.size(), cudaMemcpyHostToDevice, st);
@@ -500,7 +534,7 @@ extern "C" int trig_batch_run(const trig_slice_dev *slices, uint32_t n_slices, v
     Plan pl;
     int rc = make_plan(slices, n_slices, (uintptr_t)scratch, cfg, pl, false);
     if (rc) return rc;
-    return run_plan(pl, scratch, scratch_bytes, (cudaStream_t)stream, flags, cfg, false);
+    return run_plan(pl, scratch, scratch_bytes, (cudaStream_t)stream, flags, false);
 }
 
 extern "C" int trig_slice_rows(const trig_slice_dev *slice, trig_hit *merged_out, uint32_t *seedcnt_out,
@@ -514,7 +548,7 @@ extern "C" int trig_slice_rows(const trig_slice_dev *slice, trig_hit *merged_out
     pl.desc[0].dbg_merged = merged_out;
     pl.desc[0].dbg_seedcnt = seedcnt_out;
     cudaStream_t st = (cudaStream_t)stream;
-    rc = run_plan(pl, scratch, scratch_bytes, st, 0, cfg, true);
+    rc = run_plan(pl, scratch, scratch_bytes, st, 0, true);
     if (rc) return rc;
     SliceDesc back;
     cudaError_t e = cudaMemcpyAsync(&back, (char *)scratch + align256(sizeof(BatchHeader)), sizeof(SliceDesc),
@@ -524,6 +558,144 @@ extern "C" int trig_slice_rows(const trig_slice_dev *slice, trig_hit *merged_out
     // k_rank0 stored the merged ranks of t0 and t0 + S
     *n_owned_out = back.dbg_rank1 - back.dbg_rank0;
     return TRIG_OK;
+}
+
+// ------------------------------------------------------------- autotuner
+
+static std::string gpu_name()
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return "unknown";
+    std::string n = prop.name;
+    for (auto &c : n)
+        if (c == ' ' || c == '\t') c = '_';
+    return n;
+}
+
+// Cache file (path in TRIG_TUNE_CACHE): one line per (GPU, PMT count):
+// "<gpu> <n_pmt> <cap> <warps> <fill_pct> <ms>".
+static bool tune_cache_lookup(uint32_t n_pmt, TileConfig &out)
+{
+    const char *path = std::getenv("TRIG_TUNE_CACHE");
+    if (!path) return false;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return false;
+    const std::string gpu = gpu_name();
+    char g[256];
+    unsigned p, c, w, fl;
+    double ms;
+    bool found = false;
+    while (std::fscanf(f, "%255s %u %u %u %u %lf", g, &p, &c, &w, &fl, &ms) == 6)
+        if (gpu == g && p == n_pmt && valid_tile_shape(c, w)) {
+            out = TileConfig{c, w, fl};
+            found = true;
+        }
+    std::fclose(f);
+    return found;
+}
+
+static void tune_cache_store(uint32_t n_pmt, const TileConfig &cfg, double ms)
+{
+    const char *path = std::getenv("TRIG_TUNE_CACHE");
+    if (!path) return;
+    FILE *f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "%s %u %u %u %u %.6f\n", gpu_name().c_str(), n_pmt, cfg.cap, cfg.warps, cfg.fill_pct, ms);
+    std::fclose(f);
+}
+
+// Times every candidate launch shape on the given slices of one detector
+// and keeps the fastest for that detector: the tile capacity, consumer
+// warps per block and tile fill that suit its PMT count and rate.
+extern "C" int trig_autotune(trig_detector *det, const trig_slice_dev *slices, uint32_t n_slices, void *stream,
+                             trig_tune_result *out)
+{
+    if (!det || !slices || n_slices == 0) return fail(TRIG_EINVAL, "trig_autotune: NULL argument");
+    for (uint32_t s = 0; s < n_slices; ++s)
+        if (slices[s].det != det) return fail(TRIG_EINVAL, "trig_autotune: all slices must belong to det");
+    static const uint32_t shapes[][2] = {{4096, 16}, {4096, 8}, {2048, 8}};
+    static const uint32_t fills[] = {40, 55, 70, 85};
+    cudaStream_t st = (cudaStream_t)stream;
+    // scratch for the largest candidate
+    const bool was_tuned = det->tuned;
+    const TileConfig was = det->tile;
+    size_t need = 0;
+    for (auto &sh : shapes)
+        for (uint32_t f : fills) {
+            det->tuned = true;
+            det->tile = TileConfig{sh[0], sh[1], f};
+            need = std::max(need, trig_batch_scratch_bytes(slices, n_slices));
+        }
+    det->tuned = was_tuned;
+    det->tile = was;
+    if (!need) return fail(TRIG_EINVAL, "trig_autotune: cannot plan these slices");
+    void *scratch = nullptr;
+    cudaError_t e = cudaMalloc(&scratch, need);
+    if (e) return cuda_fail(e, "trig_autotune: scratch");
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    TileConfig best{};
+    double best_ms = 1e30;
+    uint32_t tried = 0;
+    int rc = TRIG_OK;
+    for (auto &sh : shapes) {
+        for (uint32_t f : fills) {
+            det->tuned = true;
+            det->tile = TileConfig{sh[0], sh[1], f};
+            rc = trig_batch_run(slices, n_slices, scratch, need, stream, 0);       // warm-up
+            if (rc) break;
+            cudaEventRecord(a, st);
+            for (int r = 0; r < 3 && !rc; ++r) rc = trig_batch_run(slices, n_slices, scratch, need, stream, 0);
+            cudaEventRecord(b, st);
+            if (rc) break;
+            e = cudaEventSynchronize(b);
+            if (e) {
+                rc = cuda_fail(e, "trig_autotune: timing");
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, a, b);
+            ms /= 3.f;
+            ++tried;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = det->tile;
+            }
+        }
+        if (rc) break;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(scratch);
+    if (rc || !tried) {
+        det->tuned = was_tuned;
+        det->tile = was;
+        return rc ? rc : fail(TRIG_EDEVICE, "trig_autotune: nothing timed");
+    }
+    det->tuned = true;
+    det->tile = best;
+    tune_cache_store(det->n_pmt, best, best_ms);
+    if (out) {
+        out->cap = best.cap;
+        out->warps = best.warps;
+        out->fill_pct = best.fill_pct;
+        out->n_tried = tried;
+        out->ms = best_ms;
+    }
+    return TRIG_OK;
+}
+
+extern "C" int trig_detector_tile_config(const trig_detector *det, uint32_t *cap, uint32_t *warps, uint32_t *fill_pct)
+{
+    if (!det) return fail(TRIG_EINVAL, "NULL detector");
+    const TileConfig c = det->tuned ? det->tile : current_cfg();
+    if (cap) *cap = c.cap;
+    if (warps) *warps = c.warps;
+    if (fill_pct) *fill_pct = c.fill_pct;
+    return det->tuned ? 1 : 0;
 }
 
 // ------------------------------------------------- no-allocation batch
@@ -547,7 +719,8 @@ extern "C" int trig_batch_run_noalloc(const trig_slice_dev *slices, uint32_t n_s
     size_t bytes = 0;
     uint32_t max_pmt = 0;
     bool smem_dt = true;
-    int rc = plan_into(slices, n_slices, (uintptr_t)scratch, cfg, hdr, desc, bytes, max_pmt, smem_dt);
+    TileConfig shape{};
+    int rc = plan_into(slices, n_slices, (uintptr_t)scratch, cfg, hdr, desc, bytes, max_pmt, smem_dt, &shape);
     if (rc) return rc;
     if (bytes > cap) return fail(TRIG_ECAPACITY, "trig_batch_run_noalloc: batch needs more than TRIG_NOALLOC_SCRATCH_BYTES of scratch");
     cudaStream_t st = (cudaStream_t)stream;
@@ -560,7 +733,7 @@ extern "C" int trig_batch_run_noalloc(const trig_slice_dev *slices, uint32_t n_s
     uint64_t nl = 0;
     e = launch_batch(reinterpret_cast<BatchHeader *>(scratch),
                      reinterpret_cast<SliceDesc *>((char *)scratch + align256(sizeof(BatchHeader))), n_slices,
-                     max_pmt, smem_dt, cfg, st, &nl, false);
+                     max_pmt, smem_dt, shape, st, &nl, false);
     g_launches += nl;
     if (e) return cuda_fail(e, "trig_batch_run_noalloc: launch");
     return TRIG_OK;

@@ -80,10 +80,19 @@ constexpr uint32_t kChunkHits = 4096;       // structure-pass chunk
 cudaError_t launch_dtmax(const int32_t *xyz, uint32_t n_pmt, uint32_t tol, uint32_t n_num, uint32_t n_den,
                          uint32_t corr, int32_t *dt_exact, uint16_t *dt, uint16_t *dmax_row, cudaStream_t st);
 
+// Launch shape of the tile kernel: hits per shared-memory tile, consumer
+// warps per block, and the target fill of a tile (percent of cap) that sets
+// the tile width.  Valid (cap, warps): (4096, 16), (4096, 8), (2048, 8);
+// the 2048-hit tile runs two blocks per SM.
 struct TileConfig {
-    uint32_t cap;       // hits per shared-memory tile (2048: 2 CTAs per SM, 4096: 1)
-    uint32_t fill_pct;  // target fill of a tile (percent of cap)
+    uint32_t cap;
+    uint32_t warps;
+    uint32_t fill_pct;
 };
+inline bool valid_tile_shape(uint32_t cap, uint32_t warps)
+{
+    return (cap == 4096 && (warps == 16 || warps == 8)) || (cap == 2048 && warps == 8);
+}
 constexpr uint32_t kMaxTilesPerSlice = 1u << 20;
 
 // Enqueues the batch pipeline; header/desc already copied to device scratch.

@@ -1513,6 +1513,9 @@ cudaError_t launch_batch(BatchHeader *d_hdr, SliceDesc *d_desc, uint32_t n_slice
     if (cfg.cap == 2048)
         e = smem_dt ? launch_tile<2048, 256, true>(d_hdr, d_desc, max_pmt, st)
                     : launch_tile<2048, 256, false>(d_hdr, d_desc, max_pmt, st);
+    else if (cfg.warps == 8)
+        e = smem_dt ? launch_tile<4096, 256, true>(d_hdr, d_desc, max_pmt, st)
+                    : launch_tile<4096, 256, false>(d_hdr, d_desc, max_pmt, st);
     else
         e = smem_dt ? launch_tile<4096, 512, true>(d_hdr, d_desc, max_pmt, st)
                     : launch_tile<4096, 512, false>(d_hdr, d_desc, max_pmt, st);

@@ -232,14 +232,41 @@ def test_result_independent_of_tile_configuration(pkg, params):
     ref = oracle.run(g.xyz_mm, g.floor_id, params, wl.runs[0].hits, wl.run_slices[0][:2])
     old = pkg.trig_get_tile_config()
     try:
-        for cap, fill in ((2048, 30), (2048, 90), (4096, 15), (4096, 60), (4096, 95)):
-            pkg.trig_set_tile_config(cap, fill)
+        for cap, warps, fill in ((2048, 8, 30), (2048, 8, 90), (4096, 8, 50), (4096, 16, 15), (4096, 16, 60),
+                                 (4096, 16, 95)):
+            pkg.trig_set_tile_config(cap, warps, fill)
             _, res = _run(pkg, d, subs)
             for k in range(2):
-                _assert_same(res[k], ref[k], f"cap {cap} fill {fill} slice {k}")
+                _assert_same(res[k], ref[k], f"cap {cap} warps {warps} fill {fill} slice {k}")
     finally:
         pkg.trig_set_tile_config(*old)
     d.close()
+
+
+def test_autotuned_shape_keeps_results(pkg, params, tmp_path, monkeypatch):
+    """The autotuner picks a launch shape per detector and records it in the
+    cache file; results stay exact under the chosen shape, and a new
+    detector of the same size picks the cached shape up."""
+    from paper_1411_3968_gb300.runner import DeviceBatch, SliceIn
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("TRIG_TUNE_CACHE", str(cache))
+    wl = workload.cfg_km3()
+    g = wl.detectors[0]
+    d = _det(pkg, g, params)
+    b = DeviceBatch([SliceIn(d, s.t0, s.stream.hits, s.stream.pmt_off) for s in wl.submissions[:3]])
+    r = pkg.trig_autotune(d, b.descs)
+    assert r["n_tried"] == 12 and r["ms"] > 0
+    assert pkg.trig_detector_tile_config(d) == dict(cap=r["cap"], warps=r["warps"], fill_pct=r["fill_pct"], tuned=True)
+    b.run(graph=True)
+    ref = oracle.run(g.xyz_mm, g.floor_id, params, wl.runs[0].hits, wl.run_slices[0][:3])
+    for k, res in enumerate(b.results()):
+        _assert_same(res, ref[k], f"tuned slice {k}")
+    line = cache.read_text().split()
+    assert int(line[1]) == g.n_pmt and int(line[2]) == r["cap"] and int(line[3]) == r["warps"]
+    d2 = _det(pkg, g, params)
+    assert pkg.trig_detector_tile_config(d2)["tuned"]
+    d.close()
+    d2.close()
 
 
 def test_dense_burst_takes_split_path(pkg, params):
