@@ -376,51 +376,93 @@ static void pack_plan(const Plan &pl, std::vector<unsigned char> &buf)
 
 // ------------------------------------------------------------ graph cache
 
+// A graph is replayed only for the plan it was captured with: the same
+// stream, scratch and descriptor bytes (so the same slices, buffers and
+// tile shape).  A repeated batch (a fixed set of resident slices run again
+// and again) replays its graph; a new batch captures a new one.  At most
+// kMaxGraphs are kept, the least recently used is dropped.
 struct GraphKey {
     cudaStream_t stream;
     uintptr_t scratch;
-    uint32_t n_slices, max_pmt, cap, warps;
-    bool smem_dt;
+    uint64_t plan_hash;
+    size_t plan_bytes;
     bool operator<(const GraphKey &o) const
     {
-        return std::tie(stream, scratch, n_slices, max_pmt, cap, warps, smem_dt) <
-               std::tie(o.stream, o.scratch, o.n_slices, o.max_pmt, o.cap, o.warps, o.smem_dt);
+        return std::tie(stream, scratch, plan_hash, plan_bytes) < std::tie(o.stream, o.scratch, o.plan_hash, o.plan_bytes);
     }
 };
 
 struct GraphEntry {
     cudaGraphExec_t exec = nullptr;
     unsigned char *pinned = nullptr;     // header + descriptors, copied by the graph's first node
-    size_t bytes = 0;
-    cudaEvent_t done = nullptr;          // last replay finished reading `pinned`
+    std::vector<unsigned char> plan;     // the plan bytes (hash collisions are checked against it)
+    cudaEvent_t done = nullptr;          // last replay finished
     bool launched = false;
+    uint64_t last_use = 0;
 };
 
+constexpr size_t kMaxGraphs = 64;
 static std::mutex g_graph_mu;
 static std::map<GraphKey, GraphEntry> g_graphs;
+static uint64_t g_graph_clock = 0;
+
+static uint64_t fnv1a(const unsigned char *p, size_t n)
+{
+    uint64_t h = 1469598103934665603ull;
+    for (size_t i = 0; i < n; ++i) h = (h ^ p[i]) * 1099511628211ull;
+    return h;
+}
+
+static void drop_graph(GraphEntry &ge)
+{
+    if (ge.launched) cudaEventSynchronize(ge.done);
+    if (ge.exec) cudaGraphExecDestroy(ge.exec);
+    if (ge.done) cudaEventDestroy(ge.done);
+    if (ge.pinned) cudaFreeHost(ge.pinned);
+    ge = GraphEntry{};
+}
 
 static int run_graph(const Plan &pl, void *scratch, cudaStream_t st)
 {
     const TileConfig &cfg = pl.shape;
-    GraphKey key{st, (uintptr_t)scratch, pl.hdr.n_slices, pl.max_pmt, cfg.cap, cfg.warps, pl.smem_dt};
     std::vector<unsigned char> host;
     pack_plan(pl, host);
+    GraphKey key{st, (uintptr_t)scratch, fnv1a(host.data(), host.size()), host.size()};
     std::lock_guard<std::mutex> lk(g_graph_mu);
+    auto found = g_graphs.find(key);
+    if (found != g_graphs.end() && found->second.plan != host) {
+        drop_graph(found->second);          // hash collision: recapture
+        g_graphs.erase(found);
+        found = g_graphs.end();
+    }
+    if (found == g_graphs.end() && g_graphs.size() >= kMaxGraphs) {
+        auto lru = g_graphs.begin();
+        for (auto it = g_graphs.begin(); it != g_graphs.end(); ++it)
+            if (it->second.last_use < lru->second.last_use) lru = it;
+        drop_graph(lru->second);
+        g_graphs.erase(lru);
+    }
     GraphEntry &ge = g_graphs[key];
+    ge.last_use = ++g_graph_clock;
     cudaError_t e;
     if (!ge.exec) {
-        if ((e = cudaMallocHost(&ge.pinned, host.size()))) return cuda_fail(e, "graph: pinned descriptors");
-        ge.bytes = host.size();
-        if ((e = cudaEventCreateWithFlags(&ge.done, cudaEventDisableTiming))) return cuda_fail(e, "graph: event");
+        auto forget = [&](int rc) {
+            drop_graph(ge);
+            g_graphs.erase(key);
+            return rc;
+        };
+        if ((e = cudaMallocHost(&ge.pinned, host.size()))) return forget(cuda_fail(e, "graph: pinned descriptors"));
+        if ((e = cudaEventCreateWithFlags(&ge.done, cudaEventDisableTiming))) return forget(cuda_fail(e, "graph: event"));
         std::memcpy(ge.pinned, host.data(), host.size());
+        ge.plan = host;
         // capture on a private stream (the caller's may be the legacy default
         // stream, which cannot capture); replays go to the caller's stream
         cudaGraph_t graph;
         cudaStream_t cap;
-        if ((e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking))) return cuda_fail(e, "graph: stream");
+        if ((e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking))) return forget(cuda_fail(e, "graph: stream"));
         if ((e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal))) {
             cudaStreamDestroy(cap);
-            return cuda_fail(e, "graph: capture");
+            return forget(cuda_fail(e, "graph: capture"));
         }
         uint64_t nl = 0;
         cudaError_t ce = cudaMemcpyAsync(scratch, ge.pinned, host.size(), cudaMemcpyHostToDevice, cap);
@@ -430,15 +472,20 @@ static int run_graph(const Plan &pl, void *scratch, cudaStream_t st)
                               pl.hdr.n_slices, pl.max_pmt, pl.smem_dt, cfg, cap, &nl, false);
         e = cudaStreamEndCapture(cap, &graph);
         cudaStreamDestroy(cap);
-        if (ce) return cuda_fail(ce, "graph: capture launch");
-        if (e) return cuda_fail(e, "graph: end capture");
+        if (ce) {
+            if (!e) cudaGraphDestroy(graph);
+            return forget(cuda_fail(ce, "graph: capture launch"));
+        }
+        if (e) return forget(cuda_fail(e, "graph: end capture"));
         e = cudaGraphInstantiate(&ge.exec, graph, 0);
         cudaGraphDestroy(graph);
-        if (e) { ge.exec = nullptr; return cuda_fail(e, "graph: instantiate"); }
-    } else {
-        if (ge.launched && (e = cudaEventSynchronize(ge.done))) return cuda_fail(e, "graph: wait previous");
-        std::memcpy(ge.pinned, host.data(), host.size());
+        if (e) {
+            ge.exec = nullptr;
+            return forget(cuda_fail(e, "graph: instantiate"));
+        }
     }
+    // a replay reads the same descriptor bytes as the previous one, so it
+    // need not wait for it: stream order serialises the two
     if ((e = cudaGraphLaunch(ge.exec, st))) return cuda_fail(e, "graph: launch");
     if ((e = cudaEventRecord(ge.done, st))) return cuda_fail(e, "graph: record");
     ge.launched = true;
@@ -798,6 +845,18 @@ struct PinnedPool {
     }
 };
 
+// Results and their arrays are ordinary heap memory (trig_result_free).
+trig_result *new_result(uint64_t id, int64_t t0, int32_t status)
+{
+    trig_result *r = static_cast<trig_result *>(std::calloc(1, sizeof(trig_result)));
+    if (!r) return nullptr;
+    r->slice_id = id;
+    r->t0_ns = t0;
+    r->status = status;
+    return r;
+}
+
+
 }  // namespace
 
 
@@ -816,6 +875,8 @@ struct Slot {
     std::vector<size_t> out_off;                    // per slice offset into bounce
     std::vector<trig_slice_dev> dev;
     std::vector<uint64_t> trig_n, win_n;
+    std::vector<size_t> win_off;                    // per slice offset of its windows in bounce
+    bool lost = false;                              // bounce could not grow: outputs dropped
 };
 
 constexpr int kSlots = 3;
@@ -909,7 +970,8 @@ struct ArenaLayout {
 
 bool Engine::launch_batch_on(Slot &s, std::vector<Pending> &batch)
 {
-    // layout of the arena
+    // layout of the arena: inputs and outputs of every slice, then the
+    // batch scratch
     const uint32_t n = (uint32_t)batch.size();
     std::vector<trig_slice_dev> dev(n);
     ArenaLayout L;
@@ -917,27 +979,27 @@ bool Engine::launch_batch_on(Slot &s, std::vector<Pending> &batch)
     for (uint32_t i = 0; i < n; ++i) {
         const Pending &p = batch[i];
         const uint32_t P = p.det->n_pmt;
-        L.hits.push_back(off);
-        off += align256(p.n_hits * sizeof(trig_hit));
-        L.offs.push_back(off);
-        off += align256((size_t)(P + 1) * 8);
-        L.trig.push_back(off);
-        off += align256(std::max<uint64_t>(p.n_hits, 1) * sizeof(trig_trigger));
-        L.win.push_back(off);
-        off += align256(win_cap_for(p.det) * sizeof(trig_window));
-        L.stats.push_back(off);
-        off += align256(sizeof(trig_slice_stats));
         dev[i].det = p.det;
         dev[i].n_hits = p.n_hits;
         dev[i].t0_ns = p.t0;
         dev[i].trig_cap = std::max<uint64_t>(p.n_hits, 1);
         dev[i].win_cap = win_cap_for(p.det);
-        // temporary non-null pointers for planning (real ones set below)
+        // placeholder pointers for sizing (the real ones are set below)
         dev[i].hits = reinterpret_cast<const trig_hit *>(256);
         dev[i].pmt_off = reinterpret_cast<const uint64_t *>(256);
         dev[i].triggers = reinterpret_cast<trig_trigger *>(256);
         dev[i].windows = reinterpret_cast<trig_window *>(256);
         dev[i].stats = reinterpret_cast<trig_slice_stats *>(256);
+        L.hits.push_back(off);
+        off += align256(p.n_hits * sizeof(trig_hit));
+        L.offs.push_back(off);
+        off += align256((size_t)(P + 1) * 8);
+        L.trig.push_back(off);
+        off += align256(dev[i].trig_cap * sizeof(trig_trigger));
+        L.win.push_back(off);
+        off += align256(dev[i].win_cap * sizeof(trig_window));
+        L.stats.push_back(off);
+        off += align256(sizeof(trig_slice_stats));
     }
     L.scratch = off;
     L.scratch_bytes = trig_batch_scratch_bytes(dev.data(), n);
@@ -945,22 +1007,21 @@ bool Engine::launch_batch_on(Slot &s, std::vector<Pending> &batch)
         fatal = g_last_error;
         return false;
     }
-    L.bytes = off + align256(L.scratch_bytes);
-    // grow the arena when needed, admitting by free device memory
+    off += align256(L.scratch_bytes);
+    L.bytes = off;
+    // grow the arena when needed (geometrically, so a serving mix settles
+    // after a few batches); admission: the device must have the memory,
+    // keeping a reserve, else the batch waits for other slots to finish
     if (s.arena_bytes < L.bytes) {
         size_t free_b = 0, total_b = 0;
         cudaMemGetInfo(&free_b, &total_b);
-        if (L.bytes + s.arena_bytes > free_b + ((size_t)256 << 20) * 0) {
-            if (s.arena && L.bytes <= free_b + s.arena_bytes) {
-                // fits after releasing the old arena
-            } else if (L.bytes > free_b + s.arena_bytes) {
-                return false;   // not now: wait for other slots to finish
-            }
-        }
+        const size_t reserve = total_b / 50;
+        size_t want = std::max(L.bytes, s.arena_bytes + s.arena_bytes / 2);
+        if (want > free_b + s.arena_bytes - std::min(free_b + s.arena_bytes, reserve)) want = L.bytes;
+        if (L.bytes + reserve > free_b + s.arena_bytes) return false;
         if (s.arena) cudaFree(s.arena);
         s.arena = nullptr;
         s.arena_bytes = 0;
-        size_t want = L.bytes + L.bytes / 4;
         if (cudaMalloc(&s.arena, want) != cudaSuccess) {
             (void)cudaGetLastError();
             if (cudaMalloc(&s.arena, L.bytes) != cudaSuccess) {
@@ -972,7 +1033,6 @@ bool Engine::launch_batch_on(Slot &s, std::vector<Pending> &batch)
         s.arena_bytes = want;
     }
     char *A = static_cast<char *>(s.arena);
-    size_t bounce_need = 0;
     s.out_off.assign(n, 0);
     for (uint32_t i = 0; i < n; ++i) {
         dev[i].hits = reinterpret_cast<const trig_hit *>(A + L.hits[i]);
@@ -980,22 +1040,23 @@ bool Engine::launch_batch_on(Slot &s, std::vector<Pending> &batch)
         dev[i].triggers = reinterpret_cast<trig_trigger *>(A + L.trig[i]);
         dev[i].windows = reinterpret_cast<trig_window *>(A + L.win[i]);
         dev[i].stats = reinterpret_cast<trig_slice_stats *>(A + L.stats[i]);
-        s.out_off[i] = bounce_need;
-        bounce_need += align256(dev[i].trig_cap * sizeof(trig_trigger)) + align256(dev[i].win_cap * sizeof(trig_window));
     }
-    const size_t stats_off = bounce_need;
-    bounce_need += align256(n * sizeof(trig_slice_stats));
+    // the pinned bounce buffer takes the per-slice counters now, and the
+    // triggers and windows (by their actual counts) once those are known
+    const size_t stats_off = 0;
+    const size_t bounce_need = align256(n * sizeof(trig_slice_stats));
     if (s.bounce_bytes < bounce_need) {
         if (s.bounce) cudaFreeHost(s.bounce);
         s.bounce = nullptr;
         s.bounce_bytes = 0;
         void *p = nullptr;
-        if (cudaMallocHost(&p, bounce_need) != cudaSuccess) {
+        const size_t want = std::max(bounce_need, s.bounce_bytes + s.bounce_bytes / 2);
+        if (cudaMallocHost(&p, want) != cudaSuccess) {
             (void)cudaGetLastError();
             return false;
         }
         s.bounce = static_cast<unsigned char *>(p);
-        s.bounce_bytes = bounce_need;
+        s.bounce_bytes = want;
     }
     // copies in, run, stats back
     cudaError_t e = cudaSuccess;
@@ -1013,8 +1074,9 @@ bool Engine::launch_batch_on(Slot &s, std::vector<Pending> &batch)
         (void)cudaGetLastError();
         return false;
     }
-    const uint32_t flags = (mode == 1) ? TRIG_RUN_GRAPH : 0u;
-    int rc = trig_batch_run(dev.data(), n, A + L.scratch, L.scratch_bytes, s.stream, flags);
+    // batches of the engine vary in size and composition from one launch
+    // to the next, so they are launched directly rather than from graphs
+    int rc = trig_batch_run(dev.data(), n, A + L.scratch, L.scratch_bytes, s.stream, 0);
     if (rc) {
         fatal = g_last_error;
         return false;
@@ -1033,7 +1095,6 @@ bool Engine::launch_batch_on(Slot &s, std::vector<Pending> &batch)
     s.state = 1;
     s.trig_n.assign(n, 0);
     s.win_n.assign(n, 0);
-    s.out_off.push_back(stats_off);   // last entry: stats
     batches++;
     return true;
 }
@@ -1046,12 +1107,7 @@ void Engine::fail_slot(Slot &s, cudaError_t err)
     std::fprintf(stderr, "trig engine: batch failed: %s\n", cudaGetErrorString(err));
     (void)cudaGetLastError();
     for (auto &p : s.slices) {
-        trig_result *r = static_cast<trig_result *>(std::calloc(1, sizeof(trig_result)));
-        if (r) {
-            r->slice_id = p.id;
-            r->t0_ns = p.t0;
-            r->status = TRIG_EDEVICE;
-        }
+        trig_result *r = new_result(p.id, p.t0, TRIG_EDEVICE);
         std::lock_guard<std::mutex> lk(p.q->mu);
         p.q->done[p.id] = r;
         p.q->in_flight--;
@@ -1064,41 +1120,65 @@ void Engine::fail_slot(Slot &s, cudaError_t err)
 void Engine::collect_stats(Slot &s)
 {
     const uint32_t n = (uint32_t)s.slices.size();
-    const size_t stats_off = s.out_off[n];
-    const trig_slice_stats *st = reinterpret_cast<const trig_slice_stats *>(s.bounce + stats_off);
+    const trig_slice_stats *st = reinterpret_cast<const trig_slice_stats *>(s.bounce);
+    // output bytes by the actual counts; the bounce buffer holds the
+    // counters first, then each slice's triggers and windows
+    size_t need = align256(n * sizeof(trig_slice_stats));
+    std::vector<size_t> toff(n), woff(n);
+    for (uint32_t i = 0; i < n; ++i) {
+        s.trig_n[i] = std::min<uint64_t>(st[i].n_triggers, s.dev[i].trig_cap);
+        s.win_n[i] = std::min<uint64_t>(st[i].n_windows, s.dev[i].win_cap);
+        toff[i] = need;
+        need += align256(s.trig_n[i] * sizeof(trig_trigger));
+        woff[i] = need;
+        need += align256(s.win_n[i] * sizeof(trig_window));
+    }
+    if (s.bounce_bytes < need) {
+        // grow (geometrically) keeping the counters already read
+        const size_t want = std::max(need, s.bounce_bytes + s.bounce_bytes / 2);
+        void *p = nullptr;
+        if (cudaMallocHost(&p, want) != cudaSuccess) {
+            (void)cudaGetLastError();
+            for (uint32_t i = 0; i < n; ++i) s.trig_n[i] = s.win_n[i] = 0;
+            s.lost = true;
+            s.state = 2;
+            cudaEventRecord(s.ev_done, s.stream);
+            return;
+        }
+        std::memcpy(p, s.bounce, align256(n * sizeof(trig_slice_stats)));
+        cudaFreeHost(s.bounce);
+        s.bounce = static_cast<unsigned char *>(p);
+        s.bounce_bytes = want;
+    }
+    s.out_off.assign(toff.begin(), toff.end());
+    s.win_off.assign(woff.begin(), woff.end());
     cudaError_t e = cudaSuccess;
     for (uint32_t i = 0; i < n && !e; ++i) {
-        uint64_t nt = std::min<uint64_t>(st[i].n_triggers, s.dev[i].trig_cap);
-        uint64_t nw = std::min<uint64_t>(st[i].n_windows, s.dev[i].win_cap);
-        s.trig_n[i] = nt;
-        s.win_n[i] = nw;
-        unsigned char *dst = s.bounce + s.out_off[i];
-        if (nt) e = cudaMemcpyAsync(dst, s.dev[i].triggers, nt * sizeof(trig_trigger), cudaMemcpyDeviceToHost, s.stream);
-        if (!e && nw)
-            e = cudaMemcpyAsync(dst + align256(s.dev[i].trig_cap * sizeof(trig_trigger)), s.dev[i].windows,
-                                nw * sizeof(trig_window), cudaMemcpyDeviceToHost, s.stream);
+        if (s.trig_n[i])
+            e = cudaMemcpyAsync(s.bounce + toff[i], s.dev[i].triggers, s.trig_n[i] * sizeof(trig_trigger),
+                                cudaMemcpyDeviceToHost, s.stream);
+        if (!e && s.win_n[i])
+            e = cudaMemcpyAsync(s.bounce + woff[i], s.dev[i].windows, s.win_n[i] * sizeof(trig_window),
+                                cudaMemcpyDeviceToHost, s.stream);
     }
     if (!e) e = cudaEventRecord(s.ev_done, s.stream);
     if (e) {
         fatal = cudaGetErrorString(e);
         (void)cudaGetLastError();
     }
+    s.lost = false;
     s.state = 2;
 }
 
 void Engine::finish(Slot &s)
 {
     const uint32_t n = (uint32_t)s.slices.size();
-    const size_t stats_off = s.out_off[n];
-    const trig_slice_stats *st = reinterpret_cast<const trig_slice_stats *>(s.bounce + stats_off);
+    const trig_slice_stats *st = reinterpret_cast<const trig_slice_stats *>(s.bounce);
     const auto now = Clock::now();
     for (uint32_t i = 0; i < n; ++i) {
         Pending &p = s.slices[i];
-        trig_result *r = static_cast<trig_result *>(std::calloc(1, sizeof(trig_result)));
+        trig_result *r = new_result(p.id, p.t0, s.lost ? TRIG_ENOMEM : st[i].status);
         if (r) {
-            r->slice_id = p.id;
-            r->t0_ns = p.t0;
-            r->status = st[i].status;
             r->flags = st[i].flags;
             r->n_hits = st[i].n_hits;
             r->n_seeds = st[i].n_seeds;
@@ -1106,13 +1186,12 @@ void Engine::finish(Slot &s)
             r->n_windows = s.win_n[i];
             if (r->n_triggers) {
                 r->triggers = static_cast<trig_trigger *>(std::malloc(r->n_triggers * sizeof(trig_trigger)));
-                if (r->triggers) std::memcpy(r->triggers, s.bounce + s.out_off[i], r->n_triggers * sizeof(trig_trigger));
+                if (r->triggers)
+                    std::memcpy(r->triggers, s.bounce + s.out_off[i], r->n_triggers * sizeof(trig_trigger));
             }
             if (r->n_windows) {
                 r->windows = static_cast<trig_window *>(std::malloc(r->n_windows * sizeof(trig_window)));
-                if (r->windows)
-                    std::memcpy(r->windows, s.bounce + s.out_off[i] + align256(s.dev[i].trig_cap * sizeof(trig_trigger)),
-                                r->n_windows * sizeof(trig_window));
+                if (r->windows) std::memcpy(r->windows, s.bounce + s.win_off[i], r->n_windows * sizeof(trig_window));
             }
             if ((r->n_triggers && !r->triggers) || (r->n_windows && !r->windows)) r->status = TRIG_ENOMEM;
             r->latency_ns = std::chrono::duration_cast<std::chrono::nanoseconds>(now - p.t_submit).count();
@@ -1180,12 +1259,7 @@ void Engine::run()
                     } else {
                         // cannot run at all: fail these slices
                         for (auto &p : batch) {
-                            trig_result *r = static_cast<trig_result *>(std::calloc(1, sizeof(trig_result)));
-                            if (r) {
-                                r->slice_id = p.id;
-                                r->t0_ns = p.t0;
-                                r->status = fatal.empty() ? TRIG_ENOMEM : TRIG_EDEVICE;
-                            }
+                            trig_result *r = new_result(p.id, p.t0, fatal.empty() ? TRIG_ENOMEM : TRIG_EDEVICE);
                             pool.put(p.pinned, p.pinned_bytes);
                             std::lock_guard<std::mutex> ql(p.q->mu);
                             p.q->done[p.id] = r;

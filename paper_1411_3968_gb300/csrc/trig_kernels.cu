@@ -144,6 +144,34 @@ __device__ __forceinline__ uint64_t lb_time(const trig_hit *h, uint64_t lo, uint
     return lo;
 }
 
+// --------------------------------------------------------------- self-check
+
+// Built with -DTRIG_CHECK, every computed index into global or shared
+// memory is checked first; a violation is recorded (the first one: site
+// number, index, limit) and the access is skipped.  Without TRIG_CHECK the
+// checks compile to nothing.
+#ifdef TRIG_CHECK
+struct CheckRecord {
+    unsigned int site;
+    unsigned int count;
+    unsigned long long index, limit;
+};
+__device__ CheckRecord g_check;
+__device__ __noinline__ bool check_fail(unsigned site, unsigned long long index, unsigned long long limit)
+{
+    if (atomicAdd(&g_check.count, 1u) == 0) {
+        g_check.site = site;
+        g_check.index = index;
+        g_check.limit = limit;
+    }
+    return false;
+}
+#define CHECK(site, idx, lim) \
+    (((unsigned long long)(idx) < (unsigned long long)(lim)) ? true : check_fail((site), (idx), (lim)))
+#else
+#define CHECK(site, idx, lim) true
+#endif
+
 // ------------------------------------------------------------------- dt_max
 
 // Exact integer causality table.  For PMTs d mm apart the light needs
@@ -273,7 +301,8 @@ __device__ __forceinline__ uint32_t edges_le32(int64_t rel64, uint32_t W, uint32
 __device__ __forceinline__ void fill_edges(uint32_t *e, uint32_t P, uint32_t p, uint32_t g0, uint32_t g1,
                                            uint32_t v)
 {
-    for (uint32_t g = g0; g < g1; ++g) e[(size_t)g * P + p] = v;
+    for (uint32_t g = g0; g < g1; ++g)
+        if (CHECK(1, (size_t)g * P + p, (size_t)g1 * P)) e[(size_t)g * P + p] = v;
 }
 
 // Edges after a PMT's last hit, and all edges of the empty PMTs that follow.
@@ -649,7 +678,8 @@ __device__ CoreOut tile_trigger(TileCtx &cx, const uint64_t *keys, uint32_t n, u
         while (mm) {
             const uint32_t bit = __ffs(mm) - 1;
             mm &= mm - 1;
-            seed_idx[pos++] = (uint16_t)(c0 + w * 32 + bit);
+            if (CHECK(2, pos, CAP)) seed_idx[pos] = (uint16_t)(c0 + w * 32 + bit);
+            ++pos;
         }
     }
     const uint32_t ns = wtot[NW];
@@ -689,11 +719,14 @@ __device__ CoreOut tile_trigger(TileCtx &cx, const uint64_t *keys, uint32_t n, u
         const uint64_t ks = keys[seed_idx[k]];
         const uint32_t ts = key_t(ks), ps = key_p(ks);
         const uint32_t j0 = win_lo[k], j1 = win_hi[k];
+        if (!CHECK(12, j1, n + 1) || !CHECK(13, ps, P)) continue;
         const uint16_t *row_s = cx.dt_s + (size_t)ps * P;
         const uint16_t *row_g = cx.dt_g + (size_t)ps * P;
         auto causal = [&](uint32_t j) -> uint32_t {
+            if (!CHECK(10, j, n)) return 0u;
             const uint64_t kj = keys[j];
             const uint32_t tj = key_t(kj), pj = key_p(kj);
+            if (!CHECK(11, pj, P)) return 0u;
             const uint32_t lim = SMEM_DT ? (uint32_t)row_s[pj] : (uint32_t)__ldg(row_g + pj);
             const uint32_t ad = tj > ts ? tj - ts : ts - tj;
             return ad <= lim;
@@ -743,7 +776,8 @@ __device__ CoreOut tile_trigger(TileCtx &cx, const uint64_t *keys, uint32_t n, u
                 tr.pmt = (uint16_t)key_p(ks);
                 tr.charge = (uint16_t)key_q(ks);
                 tr.count = seed_cnt[k];
-                out[F + __popc(m & ((1u << lane) - 1u))] = tr;
+                const uint32_t o_ = F + __popc(m & ((1u << lane) - 1u));
+                if (CHECK(3, o_, ncore)) out[o_] = tr;
             }
             F += __popc(m);
         }
@@ -877,6 +911,7 @@ __device__ void tile_overflow(TileCtx &cx, uint64_t *buf, const SliceDesc &d, co
                     uint32_t qd = __shfl_sync(0xffffffffu, my, q);
                     for (uint32_t e = lane; e < ql; e += 32) {
                         trig_hit h = load_hit(d.hits + qa + e);
+                        if (!CHECK(4, qd + e, CAP) || !CHECK(5, qa + e, d.n_hits)) continue;
                         buf[2 * (qd + e)] = (uint64_t)h.t_ns;
                         buf[2 * (qd + e) + 1] = (uint64_t)h.pmt | ((uint64_t)h.charge << 16);
                     }
@@ -1056,7 +1091,7 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 2048 ? 2 : 1)) k_tile(BatchHe
                             }
                         }
                         const uint32_t incl = warp_incl_scan(len);
-                        if (len)
+                        if (len && CHECK(6, dst + incl, CAP + 1) && CHECK(7, a + len, d->n_hits + 1))
                             bulk_g2s(cx.stage[b] + 2 * (size_t)(dst + incl - len), d->hits + a, len * 16u,
                                      &full_bar[b]);
                         dst += __shfl_sync(0xffffffffu, incl, 31);
@@ -1127,7 +1162,7 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 2048 ? 2 : 1)) k_tile(BatchHe
             const uint32_t tile_rank = inf.rank_lo + c0;
             CoreOut co = tile_trigger<CAP, NC, SMEM_DT>(cx, cx.stage[b], inf.n, c0, c1, tb, tp, d.stage + tile_rank,
                                                          (int64_t)inf.rank_lo - (int64_t)sl_rank0, red);
-            if (tid == 0) {
+            if (tid == 0 && CHECK(14, (uint64_t)tile_rank + co.n_fired, d.n_hits + 1) && CHECK(15, inf.g, d.n_tiles)) {
                 d.tile_nfired[inf.g] = co.n_fired;
                 d.tile_rank[inf.g] = tile_rank;
                 atomicAdd(reinterpret_cast<unsigned long long *>(&d.stats->n_seeds), (unsigned long long)co.n_seeds);
@@ -1218,6 +1253,7 @@ __global__ void __launch_bounds__(256) k_copy(const BatchHeader *__restrict__ hd
             if (lane == 0) d.tile_nwin[g] = 0;
             continue;
         }
+        if (!CHECK(8, (uint64_t)d.tile_rank[g] + F, d.n_hits + 1)) continue;
         const trig_trigger *src = d.stage + d.tile_rank[g];
         const uint64_t o = d.tile_out[g];
         const int64_t gap = 2 * (int64_t)d.win_half + 1;
@@ -1366,6 +1402,7 @@ __global__ void __launch_bounds__(256) k_whits(const BatchHeader *__restrict__ h
             }
             const SliceDesc &d = desc[s0 + lo];
             const uint64_t i = wi - pre[lo];
+            if (!CHECK(9, i, d.win_cap)) continue;
             const trig_window win = d.windows[i];
             uint64_t cnt = 0;
             for (uint32_t p = lane; p < d.n_pmt; p += 32) {
@@ -1432,6 +1469,21 @@ __global__ void k_status(const BatchHeader *__restrict__ hdr, const SliceDesc *_
     }
 }
 
+#ifdef TRIG_CHECK
+// First recorded check failure of the process (checked builds only).
+extern "C" int trig_check_record(unsigned *site, unsigned *count, unsigned long long *index,
+                                 unsigned long long *limit)
+{
+    CheckRecord r{};
+    if (cudaMemcpyFromSymbol(&r, g_check, sizeof r) != cudaSuccess) return -1;
+    *site = r.site;
+    *count = r.count;
+    *index = r.index;
+    *limit = r.limit;
+    return 0;
+}
+#endif
+
 // ------------------------------------------------- static scratch array
 
 // Scratch of trig_batch_run_noalloc: a fixed device array, present on every
@@ -1473,12 +1525,36 @@ int device_sm_count()
     return n > 0 ? n : 1;
 }
 
+// The dynamic shared memory limit of a kernel is per-function state that
+// CUDA graphs do not capture: a graph replayed after the limit was lowered
+// for a smaller launch would exceed it.  So each tile kernel's limit is set
+// once per device, to the device's opt-in maximum, and never lowered.
+template <typename K>
+static cudaError_t raise_smem_limit(K kern, bool *done)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (done[dev]) return cudaSuccess;
+    int optin = 0;
+    if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev))) return e;
+    cudaFuncAttributes fa;
+    if ((e = cudaFuncGetAttributes(&fa, kern))) return e;
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  optin - (int)fa.sharedSizeBytes)))
+        return e;
+    done[dev] = true;
+    return cudaSuccess;
+}
+
 template <int CAP, int NC, bool SMEM_DT>
 static cudaError_t launch_tile(BatchHeader *hdr, SliceDesc *desc, uint32_t max_pmt, cudaStream_t st)
 {
+    static bool limit_set[64] = {};
     size_t smem = TileLayout<CAP>::bytes(max_pmt, SMEM_DT);
     auto kern = k_tile<CAP, NC, SMEM_DT>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = raise_smem_limit(kern, limit_set);
     if (e != cudaSuccess) return e;
     int per_sm = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NC + 32, smem);

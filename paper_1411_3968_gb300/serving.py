@@ -21,12 +21,29 @@ import numpy as np
 from . import _lib
 
 
+def warm_up(dets, pools, rounds: int = 2) -> None:
+    """Runs every pool slice through the engine a few times, unmeasured: a
+    server that runs continuously has its staging memory, device arenas and
+    CUDA graphs in place; this brings a fresh process to that state."""
+    for _ in range(rounds):
+        for i, det in enumerate(dets):
+            for t0, st in pools[i]:
+                _lib.trig_submit_slice(det, t0, st.hits, st.pmt_off)
+        for i, det in enumerate(dets):
+            for _ in pools[i]:
+                r = _lib.trig_poll(det, 120_000)
+                if r is None or r.status != 0:
+                    raise RuntimeError(f"warm-up slice failed: {None if r is None else (r.status, r.flags)}")
+
+
 def replay(dets, pools, rate_factor: float, detector_seconds: float, slice_ns: int, seed: int = 0,
-           mode: int = 1) -> dict:
+           mode: int = 1, warmup_rounds: int = 2) -> dict:
     """dets[i] receives pools[i][k % len(pools[i])] as its k-th slice; the
     arrival gaps of each detector are exponential with mean
     slice_ns / rate_factor (wall clock)."""
     _lib.trig_engine_set_mode(mode)
+    if warmup_rounds:
+        warm_up(dets, pools, warmup_rounds)
     rng = np.random.Generator(np.random.PCG64(seed))
     n_per = max(1, int(round(detector_seconds * 1e9 / slice_ns)))
     mean_gap = slice_ns * 1e-9 / rate_factor

@@ -103,3 +103,29 @@ def test_engine_rejects_bad_offsets(pkg, params):
     with pytest.raises(pkg.TrigError):
         pkg.trig_submit_slice(det, 0, np.zeros(3, workload.HIT_DTYPE), off)   # decreasing offsets
     det.close()
+
+
+def test_graph_replay_after_a_smaller_launch_of_the_same_kernel(pkg, params):
+    """A graph captured for a batch that needs more shared memory is
+    replayed after a smaller launch of the same tile kernel; the kernel's
+    shared-memory limit must still admit the graph's launch."""
+    from paper_1411_3968_gb300.runner import DeviceBatch, SliceIn
+    km3, nemo = workload.cfg_km3(), workload.cfg_nemo()
+    dk = pkg.Detector(km3.detectors[0].xyz_mm, km3.detectors[0].floor_id, params)
+    dn = pkg.Detector(nemo.detectors[0].xyz_mm, nemo.detectors[0].floor_id, params)
+    big = DeviceBatch([SliceIn(dk, s.t0, s.stream.hits, s.stream.pmt_off) for s in km3.submissions[:1]])
+    small = DeviceBatch([SliceIn(dn, s.t0, s.stream.hits, s.stream.pmt_off) for s in nemo.submissions])
+    big.run(graph=True)
+    first = big.results()
+    small.run()
+    small.results()
+    big.run(graph=True)
+    again = big.results()
+    ref = oracle.run(km3.detectors[0].xyz_mm, km3.detectors[0].floor_id, params, km3.runs[0].hits,
+                     km3.run_slices[0][:1])[0]
+    for res in (first, again):
+        stats, trig, win = res[0]
+        assert int(stats["status"]) == 0
+        assert np.array_equal(trig["t"], ref.triggers["t"]) and np.array_equal(win["n_hits"], ref.windows["n_hits"])
+    dk.close()
+    dn.close()
