@@ -261,12 +261,12 @@ int trig_slice_rows(const trig_slice_dev *slice, trig_hit *merged_out, uint32_t 
  * tuned: tile capacity (hits per shared-memory tile including halos),
  * consumer warps per block and target fill (percent of the capacity a tile
  * plus its halos should hold at the slice's mean rate; it sets the tile
- * width).  (cap, warps) must be (4096, 16), (4096, 8) or (2048, 8);
+ * width).  (cap, warps) must be (4096, 16), (4096, 8), (2048, 16) or (2048, 8);
  * fill_pct in [10, 95].  Applies to later runs in this process. */
 int trig_set_tile_config(uint32_t cap, uint32_t warps, uint32_t fill_pct);
 int trig_get_tile_config(uint32_t *cap, uint32_t *warps, uint32_t *fill_pct);
 
-/* Autotuner: times every launch shape (3 (cap, warps) pairs x 4 fills) on
+/* Autotuner: times every launch shape (4 (cap, warps) pairs x 4 fills) on
  * the given device-resident slices, which must all belong to det, keeps the
  * fastest on det (later runs use it for det's slices; a batch mixing
  * detectors takes the shape of the one with the most hits) and, when the
@@ -290,9 +290,10 @@ uint64_t trig_kernel_launch_count(void);
 
 /* Average device time per kernel of the pipeline over the runs made with
  * TRIG_RUN_TIMED since the previous call (waits for their events), in the
- * launch order k_prep, k_bounds, k_tile, k_scan, k_copy, k_windows,
- * k_status.  avg_ms[i] and names[i] (static strings) for i < max_kernels;
- * returns the number of kernels (7) and the number of runs in *n_runs. */
+ * launch order k_prep, k_bounds, k_tile, k_scan, k_copy, k_wscan, k_wwrite,
+ * k_whits, k_status.  avg_ms[i] and names[i] (static strings) for
+ * i < max_kernels; returns the number of kernels (9) and the number of runs
+ * in *n_runs. */
 int trig_kernel_times(double *avg_ms, const char **names, uint32_t max_kernels, uint32_t *n_runs);
 
 #ifdef __cplusplus

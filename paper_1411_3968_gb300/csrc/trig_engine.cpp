@@ -662,7 +662,7 @@ extern "C" int trig_autotune(trig_detector *det, const trig_slice_dev *slices, u
     if (!det || !slices || n_slices == 0) return fail(TRIG_EINVAL, "trig_autotune: NULL argument");
     for (uint32_t s = 0; s < n_slices; ++s)
         if (slices[s].det != det) return fail(TRIG_EINVAL, "trig_autotune: all slices must belong to det");
-    static const uint32_t shapes[][2] = {{4096, 16}, {4096, 8}, {2048, 8}};
+    static const uint32_t shapes[][2] = {{4096, 16}, {4096, 8}, {2048, 16}, {2048, 8}};
     static const uint32_t fills[] = {40, 55, 70, 85};
     cudaStream_t st = (cudaStream_t)stream;
     // scratch for the largest candidate

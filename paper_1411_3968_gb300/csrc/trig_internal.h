@@ -82,8 +82,8 @@ cudaError_t launch_dtmax(const int32_t *xyz, uint32_t n_pmt, uint32_t tol, uint3
 
 // Launch shape of the tile kernel: hits per shared-memory tile, consumer
 // warps per block, and the target fill of a tile (percent of cap) that sets
-// the tile width.  Valid (cap, warps): (4096, 16), (4096, 8), (2048, 8);
-// the 2048-hit tile runs two blocks per SM.
+// the tile width.  Valid (cap, warps): (4096, 16), (4096, 8), (2048, 16),
+// (2048, 8); the 2048-hit tiles run two blocks per SM.
 struct TileConfig {
     uint32_t cap;
     uint32_t warps;
@@ -91,7 +91,7 @@ struct TileConfig {
 };
 inline bool valid_tile_shape(uint32_t cap, uint32_t warps)
 {
-    return (cap == 4096 && (warps == 16 || warps == 8)) || (cap == 2048 && warps == 8);
+    return (cap == 4096 || cap == 2048) && (warps == 16 || warps == 8);
 }
 constexpr uint32_t kMaxTilesPerSlice = 1u << 20;
 

@@ -425,7 +425,7 @@ struct ItemInfo {
 
 template <int CAP>
 struct TileLayout {
-    static constexpr int NBK = CAP / 2;                    // time buckets of the in-tile sort
+    static constexpr int NBK = CAP / 2;                    // time buckets of the in-tile merge
     static constexpr size_t kStage = (size_t)CAP * 16;     // one staging buffer
     static constexpr size_t kTemp = (size_t)CAP * 8;
     static constexpr size_t kCnt = (size_t)(NBK + 1) * 4;
@@ -460,16 +460,6 @@ __device__ __forceinline__ uint32_t key_t(uint64_t k) { return (uint32_t)(k >> 3
 __device__ __forceinline__ uint32_t key_p(uint64_t k) { return (uint32_t)(k >> 16) & 0xffffu; }
 __device__ __forceinline__ uint32_t key_q(uint64_t k) { return (uint32_t)k & 0xffffu; }
 
-__device__ __forceinline__ uint32_t lb_key(const uint64_t *a, uint32_t n, uint64_t v)
-{
-    uint32_t lo = 0, hi = n;
-    while (lo < hi) {
-        uint32_t mid = (lo + hi) >> 1;
-        if (a[mid] < v) lo = mid + 1; else hi = mid;
-    }
-    return lo;
-}
-
 // Consumer-wide exclusive scan of cnt[0..nb), nb a multiple of NC; writes
 // the total to cnt[nb].  Scratch words red[0..NC/32].
 template <int NC>
@@ -499,14 +489,26 @@ __device__ void cons_exclusive_scan(uint32_t *cnt, uint32_t nb, uint32_t *red)
     cons_sync<NC>();
 }
 
+// Bucket of a time relative to the tile base: t_rel >> bsh, the last bucket
+// taking everything beyond.
+template <int CAP>
+__device__ __forceinline__ uint32_t bucket_of(uint32_t t_rel, uint32_t bsh)
+{
+    constexpr uint32_t NBK = TileLayout<CAP>::NBK;
+    const uint32_t b = t_rel >> bsh;
+    return b < NBK ? b : NBK - 1;
+}
+
 // Merge (sort) the n staged records of `buf` by (t - tb, pmt, charge); the
 // keys land, in order, in the first 8 * n bytes of `buf`.  Counting sort on
-// a time bucket, then each key's rank inside its bucket.
-// Also counts the keys with t_rel < lo_t and < hi_t into red[NC/32 + 1]
-// and red[NC/32 + 2] (the first core index and the core's end).
+// the time bucket t_rel >> bsh, then each key's rank inside its bucket;
+// cx.cnt[b] keeps the index of bucket b's first key (cx.cnt[NBK] = n), so a
+// time range maps to an index range without a search.  Also counts the keys
+// with t_rel < lo_t and < hi_t into red[NC/32 + 1] and red[NC/32 + 2] (the
+// first core index and the core's end).  Returns bsh.
 template <int CAP, int NC>
-__device__ void tile_sort(TileCtx &cx, uint64_t *buf, uint32_t n, int64_t tb, uint32_t span, uint32_t *red,
-                          uint32_t lo_t, uint32_t hi_t)
+__device__ uint32_t tile_sort(TileCtx &cx, uint64_t *buf, uint32_t n, int64_t tb, uint32_t span, uint32_t *red,
+                              uint32_t lo_t, uint32_t hi_t)
 {
     constexpr uint32_t NW = NC / 32;
     constexpr int NBK = TileLayout<CAP>::NBK;
@@ -536,9 +538,7 @@ __device__ void tile_sort(TileCtx &cx, uint64_t *buf, uint32_t n, int64_t tb, ui
             int64_t rel = t - tb;
             uint32_t tr = rel < 0 ? 0u : (rel > 0xffffffffll ? 0xffffffffu : (uint32_t)rel);
             kreg[r] = ((uint64_t)tr << 32) | ((uint64_t)(w1 & 0xffffu) << 16) | (uint64_t)(w1 >> 16);
-            uint32_t bk = tr >> bsh;
-            if (bk >= (uint32_t)NBK) bk = NBK - 1;
-            slot[r] = atomicAdd(&cx.cnt[bk], 1u);
+            slot[r] = atomicAdd(&cx.cnt[bucket_of<CAP>(tr, bsh)], 1u);
             below_lo += tr < lo_t;
             below_hi += tr < hi_t;
         }
@@ -555,17 +555,14 @@ __device__ void tile_sort(TileCtx &cx, uint64_t *buf, uint32_t n, int64_t tb, ui
     for (int r = 0; r < PER; ++r) {
         uint32_t i = tid + r * NC;
         if (r * NC < n && i < n) {
-            uint32_t bk = key_t(kreg[r]) >> bsh;
-            if (bk >= (uint32_t)NBK) bk = NBK - 1;
-            cx.temp[cx.cnt[bk] + slot[r]] = kreg[r];
+            cx.temp[cx.cnt[bucket_of<CAP>(key_t(kreg[r]), bsh)] + slot[r]] = kreg[r];
         }
     }
     cons_sync<NC>();
     // rank inside each bucket; identical keys are interchangeable
     for (uint32_t j = tid; j < n; j += NC) {
         uint64_t k = cx.temp[j];
-        uint32_t bk = key_t(k) >> bsh;
-        if (bk >= (uint32_t)NBK) bk = NBK - 1;
+        const uint32_t bk = bucket_of<CAP>(key_t(k), bsh);
         uint32_t s0 = cx.cnt[bk], s1 = cx.cnt[bk + 1];
         uint32_t r = s0;
         for (uint32_t m = s0; m < s1; ++m) {
@@ -575,6 +572,7 @@ __device__ void tile_sort(TileCtx &cx, uint64_t *buf, uint32_t n, int64_t tb, ui
         buf[r] = k;
     }
     cons_sync<NC>();
+    return bsh;
 }
 
 struct CoreOut {
@@ -593,7 +591,7 @@ struct TrigParams {
 
 // The core is keys[c0, c1) (t_rel in [H, H + core width)).
 template <int CAP, int NC, bool SMEM_DT>
-__device__ CoreOut tile_trigger(TileCtx &cx, const uint64_t *keys, uint32_t n, uint32_t c0, uint32_t c1,
+__device__ CoreOut tile_trigger(TileCtx &cx, const uint64_t *keys, uint32_t n, uint32_t bsh, uint32_t c0, uint32_t c1,
                                 int64_t tb, const TrigParams &tp, trig_trigger *out, int64_t dbg_rank_lo,
                                 uint32_t *red)
 {
@@ -601,11 +599,11 @@ __device__ CoreOut tile_trigger(TileCtx &cx, const uint64_t *keys, uint32_t n, u
     const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
     const uint32_t ncore = c1 - c0;
     const uint32_t tau = tp.tau, qseed = tp.q_seed, threshold = tp.threshold, P = cx.P;
-    // scratch per seed (all 16-bit, CAP entries each): index, window, count
+    // scratch per seed (CAP entries each): index and count (16-bit), scan
+    // range (32-bit)
     uint16_t *seed_idx = reinterpret_cast<uint16_t *>(cx.temp);
-    uint16_t *win_lo = seed_idx + CAP;
-    uint16_t *win_hi = seed_idx + 2 * CAP;
-    uint16_t *seed_cnt = seed_idx + 3 * CAP;
+    uint16_t *seed_cnt = seed_idx + CAP;
+    const uint32_t *boff = cx.cnt;          // bucket offsets of the sorted keys
 
     // 1. seed flags (one bit per core hit): charge over threshold, or a hit
     //    on another PMT of the same floor within tau.  A warp holds 32
@@ -685,69 +683,75 @@ __device__ CoreOut tile_trigger(TileCtx &cx, const uint64_t *keys, uint32_t n, u
     const uint32_t ns = wtot[NW];
     cons_sync<NC>();
 
-    // 2b. each seed's scan range [t_s - d, t_s + d], d = its row's maximum
-    //     of min(dt_max, W): two binary searches per seed, seeds in parallel
+    // 2b. each seed's scan range: the keys of the buckets covering
+    //     [t_s - d, t_s + d], d its row's maximum (keys beyond fail the test
+    //     below); one thread per seed
+    uint32_t *swin = reinterpret_cast<uint32_t *>(seed_cnt + CAP);    // j0 | j1 << 16
     for (uint32_t k = tid; k < ns; k += NC) {
-        const uint32_t i = seed_idx[k];
-        const uint64_t ks = keys[i];
+        const uint64_t ks = keys[seed_idx[k]];
         const uint32_t ts = key_t(ks), dm = cx.dmax_s[key_p(ks)];
-        // the window lies within [i - n, i + n]; search each side only
-        uint32_t lo = 0, hi = i;
-        const uint64_t lo_key = (uint64_t)(ts - dm) << 32;
-        while (lo < hi) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (keys[mid] < lo_key) lo = mid + 1; else hi = mid;
-        }
-        win_lo[k] = (uint16_t)lo;
-        const uint64_t hi_key = (uint64_t)(ts + dm + 1) << 32;
-        lo = i + 1;
-        hi = n;
-        while (lo < hi) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (keys[mid] < hi_key) lo = mid + 1; else hi = mid;
-        }
-        win_hi[k] = (uint16_t)lo;
+        const uint32_t j0 = boff[bucket_of<CAP>(ts >= dm ? ts - dm : 0u, bsh)];
+        const uint32_t j1 = boff[bucket_of<CAP>(ts + dm, bsh) + 1];
+        swin[k] = j0 | (j1 << 16);
     }
     cons_sync<NC>();
 
-    // 3. causal count c(s) = #{ j : |t_j - t_s| <= min(dt_max[p_s][p_j], W) },
-    //    a warp per seed over its range; lanes count privately and reduce
-    //    once per seed.
+    // 3. causal count c(s) = #{ j : |t_j - t_s| <= min(dt_max[p_s][p_j], W) }
+    //    over the seed's scan range: a group of G lanes per seed (G from the
+    //    tile's density), seeds dealt round-robin to the groups, four
+    //    independent tests per lane in flight
+    {
+        // expected keys in a scan range: 2H + 1 ns at the tile's density
+        const unsigned long long span_n = n ? (unsigned long long)key_t(keys[n - 1]) + 1ull : 1ull;
+        const unsigned long long est = (unsigned long long)(2u * tp.H + 1u) * n / span_n;
+        const uint32_t lg = est >= 48 ? 5u : est >= 20 ? 4u : 3u;
+        const uint32_t G = 1u << lg, gl = lane & (G - 1u), gid = tid >> lg, NG = NC >> lg;
+        const uint32_t rounds = (ns + NG - 1) / NG;
+        for (uint32_t r = 0; r < rounds; ++r) {
+            const uint32_t k = r * NG + gid;
+            uint32_t c = 0;
+            if (k < ns) {
+                const uint32_t w = swin[k];
+                const uint64_t ks = keys[seed_idx[k]];
+                const uint32_t ts = key_t(ks), ps = key_p(ks);
+                const uint32_t j0 = w & 0xffffu, j1 = w >> 16;
+                if (CHECK(12, j1, n + 1) && CHECK(13, ps, P)) {
+                    const uint16_t *row_s = cx.dt_s + (size_t)ps * P;
+                    const uint16_t *row_g = cx.dt_g + (size_t)ps * P;
+                    auto causal = [&](uint32_t j) -> uint32_t {
+                        const uint64_t kj = keys[j];
+                        const uint32_t tj = key_t(kj), pj = key_p(kj);
+                        if (!CHECK(11, pj, P)) return 0u;
+                        const uint32_t lim = SMEM_DT ? (uint32_t)row_s[pj] : (uint32_t)__ldg(row_g + pj);
+                        return (tj > ts ? tj - ts : ts - tj) <= lim;
+                    };
+                    uint32_t ca = 0, cb = 0, cc = 0, cd = 0;
+                    uint32_t j = j0 + gl;
+                    for (; j + 3 * G < j1; j += 4 * G) {
+                        ca += causal(j);
+                        cb += causal(j + G);
+                        cc += causal(j + 2 * G);
+                        cd += causal(j + 3 * G);
+                    }
+                    for (; j < j1; j += G) ca += causal(j);
+                    c = ca + cb + cc + cd;
+                }
+            }
+            if (lg == 5) {
+                c = __reduce_add_sync(0xffffffffu, c);
+            } else {
+                for (uint32_t off = G >> 1; off; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
+            }
+            if (k < ns && gl == 0) seed_cnt[k] = (uint16_t)c;
+        }
+    }
+    cons_sync<NC>();
+
+    // 4. emit fired seeds in order: warp w takes a contiguous range of the
+    //    seed list, warps count theirs, a scan of the warp totals gives each
+    //    warp its output offset
     const uint32_t per_w = (ns + NW - 1) / NW;
     const uint32_t k_begin = min(ns, warp * per_w), k_end = min(ns, k_begin + per_w);
-    for (uint32_t k = k_begin; k < k_end; ++k) {
-        const uint64_t ks = keys[seed_idx[k]];
-        const uint32_t ts = key_t(ks), ps = key_p(ks);
-        const uint32_t j0 = win_lo[k], j1 = win_hi[k];
-        if (!CHECK(12, j1, n + 1) || !CHECK(13, ps, P)) continue;
-        const uint16_t *row_s = cx.dt_s + (size_t)ps * P;
-        const uint16_t *row_g = cx.dt_g + (size_t)ps * P;
-        auto causal = [&](uint32_t j) -> uint32_t {
-            if (!CHECK(10, j, n)) return 0u;
-            const uint64_t kj = keys[j];
-            const uint32_t tj = key_t(kj), pj = key_p(kj);
-            if (!CHECK(11, pj, P)) return 0u;
-            const uint32_t lim = SMEM_DT ? (uint32_t)row_s[pj] : (uint32_t)__ldg(row_g + pj);
-            const uint32_t ad = tj > ts ? tj - ts : ts - tj;
-            return ad <= lim;
-        };
-        // four independent chains per lane
-        uint32_t ca = 0, cb = 0, cc = 0, cd = 0;
-        uint32_t j = j0 + lane;
-        for (; j + 96 < j1; j += 128) {
-            ca += causal(j);
-            cb += causal(j + 32);
-            cc += causal(j + 64);
-            cd += causal(j + 96);
-        }
-        for (; j < j1; j += 32) ca += causal(j);
-        const uint32_t c = __reduce_add_sync(0xffffffffu, ca + cb + cc + cd);
-        if (lane == 0) seed_cnt[k] = (uint16_t)c;
-    }
-    __syncwarp();
-
-    // 4. emit fired seeds in order: warps count theirs, a scan of the warp
-    //    totals gives each warp its output offset
     uint32_t my_f = 0;
     for (uint32_t k0 = k_begin; k0 < k_end; k0 += 32) {
         const uint32_t k = k0 + lane;
@@ -808,6 +812,7 @@ __device__ CoreOut tile_trigger(TileCtx &cx, const uint64_t *keys, uint32_t n, u
     return r;
 }
 
+// Overflow path: the tile holds more than CAP hits with its halo.  Split
 // Overflow path: the tile holds more than CAP hits with its halo.  Split
 // its core in halves until each piece fits; pieces are staged with plain
 // loads after per-PMT binary searches.  A 1 ns core that still does not
@@ -922,10 +927,10 @@ __device__ void tile_overflow(TileCtx &cx, uint64_t *buf, const SliceDesc &d, co
         cons_sync<NC>();
         const int64_t tb = lo - (int64_t)H;
         const uint32_t span = (uint32_t)(hi - lo) + 2 * H;
-        tile_sort<CAP, NC>(cx, buf, total, tb, span, red + 64, H, H + (uint32_t)(hi - lo));
+        const uint32_t bsh = tile_sort<CAP, NC>(cx, buf, total, tb, span, red + 64, H, H + (uint32_t)(hi - lo));
         const uint32_t c0 = red[64 + NW + 1], c1 = red[64 + NW + 2];
         const uint32_t fired0 = red[5];
-        CoreOut co = tile_trigger<CAP, NC, SMEM_DT>(cx, buf, total, c0, c1, tb, tp,
+        CoreOut co = tile_trigger<CAP, NC, SMEM_DT>(cx, buf, total, bsh, c0, c1, tb, tp,
                                                      d.stage + tile_rank + fired0,
                                                      (int64_t)rank_lo - (int64_t)d.dbg_rank0, red + 64);
         if (tid == 0) {
@@ -1156,12 +1161,14 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 2048 ? 2 : 1)) k_tile(BatchHe
             const uint32_t H = tp.H;
             const int64_t tb = Bg - (int64_t)H;
             const uint32_t span = (uint32_t)W + 2 * H;
-            tile_sort<CAP, NC>(cx, cx.stage[b], inf.n, tb, span, red, H, H + (uint32_t)(core_end - Bg));
+            const uint32_t hi_t = H + (uint32_t)(core_end - Bg);
+            const uint32_t bsh = tile_sort<CAP, NC>(cx, cx.stage[b], inf.n, tb, span, red, H, hi_t);
             // rank of the core's first hit = rank_lo + c0, known after the sort
             const uint32_t c0 = red[NW + 1], c1 = red[NW + 2];
             const uint32_t tile_rank = inf.rank_lo + c0;
-            CoreOut co = tile_trigger<CAP, NC, SMEM_DT>(cx, cx.stage[b], inf.n, c0, c1, tb, tp, d.stage + tile_rank,
-                                                         (int64_t)inf.rank_lo - (int64_t)sl_rank0, red);
+            CoreOut co = tile_trigger<CAP, NC, SMEM_DT>(cx, cx.stage[b], inf.n, bsh, c0, c1, tb, tp,
+                                                         d.stage + tile_rank, (int64_t)inf.rank_lo - (int64_t)sl_rank0,
+                                                         red);
             if (tid == 0 && CHECK(14, (uint64_t)tile_rank + co.n_fired, d.n_hits + 1) && CHECK(15, inf.g, d.n_tiles)) {
                 d.tile_nfired[inf.g] = co.n_fired;
                 d.tile_rank[inf.g] = tile_rank;
@@ -1586,7 +1593,10 @@ cudaError_t launch_batch(BatchHeader *d_hdr, SliceDesc *d_desc, uint32_t n_slice
     mark(2);
     cudaError_t e;
     const bool smem_dt = any_smem_dt && max_pmt <= kSmemDtMaxPmt;
-    if (cfg.cap == 2048)
+    if (cfg.cap == 2048 && cfg.warps == 16)
+        e = smem_dt ? launch_tile<2048, 512, true>(d_hdr, d_desc, max_pmt, st)
+                    : launch_tile<2048, 512, false>(d_hdr, d_desc, max_pmt, st);
+    else if (cfg.cap == 2048)
         e = smem_dt ? launch_tile<2048, 256, true>(d_hdr, d_desc, max_pmt, st)
                     : launch_tile<2048, 256, false>(d_hdr, d_desc, max_pmt, st);
     else if (cfg.warps == 8)

@@ -57,13 +57,23 @@ class DeviceBatch:
         self.n_hits = sum(len(s.hits) for s in slices)
         self.input_bytes = sum(s.hits.nbytes + np.asarray(s.pmt_off).nbytes for s in slices)
 
+    def ensure_scratch(self) -> None:
+        """Grows the scratch when the batch plan needs more, e.g. after the
+        autotuner changed a detector's tile shape."""
+        need = _lib.trig_batch_scratch_bytes(self.descs)
+        if need > self.scratch_bytes:
+            self.scratch = _dev_bytes(need + 256, self.device)
+            self.scratch_bytes = need
+
     def run(self, graph: bool = False, stream=None, timed: bool = False) -> None:
+        self.ensure_scratch()
         st = stream if stream is not None else torch.cuda.current_stream(self.device)
         flags = (_lib.TRIG_RUN_GRAPH if graph else 0) | (_lib.TRIG_RUN_TIMED if timed else 0)
         _lib.trig_batch_run(self.descs, self.scratch.data_ptr(), self.scratch_bytes, st.cuda_stream, flags)
 
     def run_each(self, stream=None) -> None:
         """Plain per-slice launches: one launch sequence per slice."""
+        self.ensure_scratch()
         st = stream if stream is not None else torch.cuda.current_stream(self.device)
         for d in self.descs:
             _lib.trig_batch_run([d], self.scratch.data_ptr(), self.scratch_bytes, st.cuda_stream, 0)
@@ -87,6 +97,7 @@ class DeviceBatch:
         n = max(len(s.hits), 1)
         merged = _dev_bytes(n * HIT_DTYPE.itemsize, self.device)
         seedcnt = _dev_bytes(n * 4, self.device)
+        self.ensure_scratch()
         st = torch.cuda.current_stream(self.device)
         n_owned = _lib.trig_slice_rows(self.descs[i], merged.data_ptr(), seedcnt.data_ptr(), self.scratch.data_ptr(),
                                        self.scratch_bytes, st.cuda_stream)
