@@ -10,6 +10,7 @@
 // submission order.  Up to kSlots batches are in flight, so copies of one
 // batch overlap the kernels of another.
 #include <algorithm>
+#include <cmath>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -224,6 +225,7 @@ struct Plan {
     size_t bytes = 0;
     uint32_t max_pmt = 0;
     bool smem_dt = true;
+    bool any_wide = false;
     TileConfig shape{};         // launch shape of this batch
 };
 
@@ -242,6 +244,39 @@ static int64_t choose_tile_w(const trig_detector *det, uint64_t n_hits, const Ti
     if (w > (double)det->par.slice_ns) w = (double)det->par.slice_ns;
     if (w > 2e9) w = 2e9;
     return (int64_t)w;
+}
+
+// Bucket grid of a wide slice: buckets of Wb ns from O = t0 - lead * Wb,
+// tiles of m buckets, hh buckets of halo on each side (hh * Wb >= H).  Wb
+// is about H / 2, smaller when a bucket would hold more than an eighth of a
+// tile at the slice's mean rate; m fills a tile with its halos to the
+// target fill.
+struct WideGrid {
+    uint32_t wb, hh, m, lead, nb;
+};
+
+static WideGrid wide_grid(const trig_detector *det, uint64_t n_hits, const TileConfig &cfg)
+{
+    const double S = (double)det->par.slice_ns;
+    const double span = S + 2.0 * (double)det->in_halo;
+    const double rate = n_hits > 0 ? (double)n_hits / span : 1e-9;        // hits per ns
+    const uint32_t fill = det->tuned ? det->tile.fill_pct : cfg.fill_pct;
+    const double target = (double)cfg.cap * fill / 100.0;
+    const uint32_t H = det->tile_halo;
+    double wb = std::max(64.0, std::ceil(H / 2.0));
+    wb = std::min(wb, std::max(64.0, std::floor(target / 8.0 / rate)));
+    wb = std::max(wb, std::ceil(span / (double)(1u << 22)));                 // at most ~4M buckets
+    WideGrid g{};
+    g.wb = (uint32_t)std::min(wb, 1e9);
+    g.hh = H ? (H + g.wb - 1) / g.wb : 0;
+    double m = std::floor(target / ((double)g.wb * rate)) - 2.0 * g.hh;
+    m = std::min(m, std::ceil(S / g.wb));
+    m = std::min(m, std::floor(2e9 / g.wb) - 2.0 * g.hh);       // staged span below 2^31 ns
+    m = std::max(1.0, m);
+    g.m = (uint32_t)m;
+    g.lead = (uint32_t)(((uint64_t)det->in_halo + g.wb - 1) / g.wb);
+    g.nb = g.lead + (uint32_t)(((uint64_t)det->par.slice_ns + (uint64_t)det->in_halo + g.wb - 1) / g.wb) + 1;
+    return g;
 }
 
 // Plans a batch into caller-provided storage (no allocation): descriptors
@@ -265,7 +300,7 @@ static TileConfig batch_shape(const trig_slice_dev *sl, uint32_t n, const TileCo
 
 static int plan_into(const trig_slice_dev *sl, uint32_t n, uintptr_t base, const TileConfig &cfg_in,
                      BatchHeader &hdr, SliceDesc *desc, size_t &bytes, uint32_t &max_pmt, bool &smem_dt,
-                     TileConfig *shape_out = nullptr)
+                     bool &any_wide, TileConfig *shape_out = nullptr)
 {
     if (!sl || n == 0) return fail(TRIG_EINVAL, "no slices");
     const TileConfig cfg = batch_shape(sl, n, cfg_in);
@@ -275,6 +310,7 @@ static int plan_into(const trig_slice_dev *sl, uint32_t n, uintptr_t base, const
     uint32_t items = 0, chunks = 0;
     max_pmt = 0;
     smem_dt = true;
+    any_wide = false;
     for (uint32_t s = 0; s < n; ++s) {
         const trig_slice_dev &x = sl[s];
         const trig_detector *det = x.det;
@@ -305,7 +341,24 @@ static int plan_into(const trig_slice_dev *sl, uint32_t n, uintptr_t base, const
         d.in_lo = x.t0_ns - det->in_halo;
         d.in_hi = x.t0_ns + det->par.slice_ns + det->in_halo;
         d.n_hits = x.n_hits;
-        const int64_t W = choose_tile_w(det, x.n_hits, cfg);
+        const bool wide = P >= kWideMinPmt;
+        any_wide |= wide;
+        int64_t W = 0;
+        if (wide) {
+            const WideGrid wg = wide_grid(det, x.n_hits, cfg);
+            W = (int64_t)wg.m * wg.wb;
+            d.wide = 1;
+            d.bkt_w = wg.wb;
+            d.bkt_magic = (uint32_t)((((uint64_t)1 << 32) + wg.wb - 1) / wg.wb);
+            d.bkt_lead = wg.lead;
+            d.bkt_per_tile = wg.m;
+            d.bkt_halo = wg.hh;
+            d.n_bkt = wg.nb;
+            d.bkt32 = (uint64_t)wg.nb * wg.wb < ((uint64_t)1 << 31);
+            d.bkt_origin = x.t0_ns - (int64_t)wg.lead * wg.wb;
+        } else {
+            W = choose_tile_w(det, x.n_hits, cfg);
+        }
         d.tile_w = W;
         d.w_magic = (uint32_t)((((uint64_t)1 << 32) + (uint64_t)W - 1) / (uint64_t)W);
         d.span32 = (det->par.slice_ns + 2 * det->in_halo + 2 * (int64_t)det->tile_halo + 2 * W) < ((int64_t)1 << 31);
@@ -316,11 +369,22 @@ static int plan_into(const trig_slice_dev *sl, uint32_t n, uintptr_t base, const
         d.chunk0 = chunks;
         items += d.n_tiles;
         chunks += (uint32_t)((x.n_hits + kChunkHits - 1) / kChunkHits);
-        const size_t eb = (size_t)d.n_tiles * P * 4;
-        d.e_lo = reinterpret_cast<uint32_t *>(base + off);
-        off += align256(eb);
-        d.e_hi = reinterpret_cast<uint32_t *>(base + off);
-        off += align256(eb);
+        if (wide) {
+            d.bkt_cnt = reinterpret_cast<uint32_t *>(base + off);
+            off += align256((size_t)d.n_bkt * 4);
+            d.bkt_off = reinterpret_cast<uint32_t *>(base + off);
+            off += align256(((size_t)d.n_bkt + 1) * 4);
+            d.bkt_part = reinterpret_cast<uint32_t *>(base + off);
+            off += align256(((size_t)d.n_bkt + kBktChunk - 1) / kBktChunk * 4);
+            d.tbuf = reinterpret_cast<trig_hit *>(base + off);
+            off += align256((size_t)x.n_hits * sizeof(trig_hit));
+        } else {
+            const size_t eb = (size_t)d.n_tiles * P * 4;
+            d.e_lo = reinterpret_cast<uint32_t *>(base + off);
+            off += align256(eb);
+            d.e_hi = reinterpret_cast<uint32_t *>(base + off);
+            off += align256(eb);
+        }
         d.tile_nfired = reinterpret_cast<uint32_t *>(base + off);
         off += align256((size_t)d.n_tiles * 4);
         d.tile_rank = reinterpret_cast<uint32_t *>(base + off);
@@ -344,6 +408,7 @@ static int plan_into(const trig_slice_dev *sl, uint32_t n, uintptr_t base, const
     }
     hdr = BatchHeader{};
     hdr.n_slices = n;
+    hdr.any_wide = any_wide ? 1u : 0u;
     hdr.n_items = items;
     hdr.n_chunks = chunks;
     bytes = off;
@@ -356,7 +421,8 @@ static int make_plan(const trig_slice_dev *sl, uint32_t n, uintptr_t base, const
     (void)rows;
     if (!sl || n == 0) return fail(TRIG_EINVAL, "no slices");
     pl.desc.assign(n, SliceDesc{});
-    return plan_into(sl, n, base, cfg, pl.hdr, pl.desc.data(), pl.bytes, pl.max_pmt, pl.smem_dt, &pl.shape);
+    return plan_into(sl, n, base, cfg, pl.hdr, pl.desc.data(), pl.bytes, pl.max_pmt, pl.smem_dt, pl.any_wide,
+                     &pl.shape);
 }
 
 extern "C" size_t trig_batch_scratch_bytes(const trig_slice_dev *slices, uint32_t n_slices)
@@ -399,6 +465,7 @@ struct GraphEntry {
     cudaEvent_t done = nullptr;          // last replay finished
     bool launched = false;
     uint64_t last_use = 0;
+    uint64_t launches = 0;               // kernels per replay
 };
 
 constexpr size_t kMaxGraphs = 64;
@@ -469,7 +536,8 @@ static int run_graph(const Plan &pl, void *scratch, cudaStream_t st)
         if (!ce)
             ce = launch_batch(reinterpret_cast<BatchHeader *>(scratch),
                               reinterpret_cast<SliceDesc *>((char *)scratch + align256(sizeof(BatchHeader))),
-                              pl.hdr.n_slices, pl.max_pmt, pl.smem_dt, cfg, cap, &nl, false);
+                              pl.hdr.n_slices, pl.max_pmt, pl.smem_dt, pl.any_wide, cfg, cap, &nl, false);
+        ge.launches = nl;
         e = cudaStreamEndCapture(cap, &graph);
         cudaStreamDestroy(cap);
         if (ce) {
@@ -489,7 +557,7 @@ static int run_graph(const Plan &pl, void *scratch, cudaStream_t st)
     if ((e = cudaGraphLaunch(ge.exec, st))) return cuda_fail(e, "graph: launch");
     if ((e = cudaEventRecord(ge.done, st))) return cuda_fail(e, "graph: record");
     ge.launched = true;
-    g_launches += kPipelineKernels;
+    g_launches += ge.launches;
     return TRIG_OK;
 }
 
@@ -564,7 +632,7 @@ static int run_plan(const Plan &pl, void *scratch, size_t scratch_bytes, cudaStr
     uint64_t nl = 0;
     e = launch_batch(reinterpret_cast<BatchHeader *>(scratch),
                      reinterpret_cast<SliceDesc *>((char *)scratch + align256(sizeof(BatchHeader))), pl.hdr.n_slices,
-                     pl.max_pmt, pl.smem_dt, cfg, st, &nl, rows, timed ? tr.ev : nullptr);
+                     pl.max_pmt, pl.smem_dt, pl.any_wide, cfg, st, &nl, rows, timed ? tr.ev : nullptr);
     g_launches += nl;
     if (timed) {
         std::lock_guard<std::mutex> lk(g_time_mu);
@@ -765,9 +833,10 @@ extern "C" int trig_batch_run_noalloc(const trig_slice_dev *slices, uint32_t n_s
     SliceDesc desc[TRIG_NOALLOC_MAX_SLICES];
     size_t bytes = 0;
     uint32_t max_pmt = 0;
-    bool smem_dt = true;
+    bool smem_dt = true, any_wide = false;
     TileConfig shape{};
-    int rc = plan_into(slices, n_slices, (uintptr_t)scratch, cfg, hdr, desc, bytes, max_pmt, smem_dt, &shape);
+    int rc = plan_into(slices, n_slices, (uintptr_t)scratch, cfg, hdr, desc, bytes, max_pmt, smem_dt, any_wide,
+                       &shape);
     if (rc) return rc;
     if (bytes > cap) return fail(TRIG_ECAPACITY, "trig_batch_run_noalloc: batch needs more than TRIG_NOALLOC_SCRATCH_BYTES of scratch");
     cudaStream_t st = (cudaStream_t)stream;
@@ -780,7 +849,7 @@ extern "C" int trig_batch_run_noalloc(const trig_slice_dev *slices, uint32_t n_s
     uint64_t nl = 0;
     e = launch_batch(reinterpret_cast<BatchHeader *>(scratch),
                      reinterpret_cast<SliceDesc *>((char *)scratch + align256(sizeof(BatchHeader))), n_slices,
-                     max_pmt, smem_dt, shape, st, &nl, false);
+                     max_pmt, smem_dt, any_wide, shape, st, &nl, false);
     g_launches += nl;
     if (e) return cuda_fail(e, "trig_batch_run_noalloc: launch");
     return TRIG_OK;

@@ -13,6 +13,8 @@ namespace trig {
 // Limits of this implementation.
 constexpr uint32_t kMaxPmt = 4096;          // PMTs per detector
 constexpr uint32_t kSmemDtMaxPmt = 96;      // dt table lives in shared memory up to this P
+constexpr uint32_t kWideMinPmt = 129;       // from this P on, slices are staged from a bucketed copy
+constexpr uint32_t kBktChunk = 1024;        // buckets per block of the bucket scan
 constexpr uint64_t kMaxSliceHits = 0xFFFFFFF0ull;
 
 // Detector tables resident on the device (owned by trig_detector).
@@ -46,8 +48,25 @@ struct SliceDesc {
     uint32_t n_tiles;       // NG (<= 2^20)
     uint32_t item0;         // first work item (tile) of this slice
     uint32_t chunk0;        // first structure-pass chunk of this slice
-    uint32_t *e_lo;         // [NG][P] first hit index with t >= B_g - H
-    uint32_t *e_hi;         // [NG][P] first hit index with t >= B_{g+1} + H
+    uint32_t *e_lo;         // [NG][P] first hit index with t >= B_g - H (narrow slices)
+    uint32_t *e_hi;         // [NG][P] first hit index with t >= B_{g+1} + H (narrow slices)
+    // Wide slices (P >= kWideMinPmt): the hits are also copied, grouped by
+    // time bucket [O + b Wb, O + (b+1) Wb), into tbuf; tile g's core is the
+    // buckets [lead + g m, lead + (g+1) m) and it stages those plus `hh`
+    // buckets on each side, one contiguous range of tbuf.
+    uint32_t wide;
+    uint32_t bkt_w;         // Wb (ns)
+    uint32_t bkt_magic;     // ceil(2^32 / Wb)
+    uint32_t bkt_lead;      // buckets before t0
+    uint32_t bkt_per_tile;  // m
+    uint32_t bkt_halo;      // hh = ceil(H / Wb)
+    uint32_t n_bkt;         // NB
+    uint32_t bkt32;         // every in-range time is < 2^31 ns past O
+    int64_t bkt_origin;     // O = t0 - lead * Wb
+    uint32_t *bkt_cnt;      // [NB] hits per bucket, then fill cursors
+    uint32_t *bkt_off;      // [NB + 1] exclusive prefix of the counts
+    uint32_t *bkt_part;     // [ceil(NB / kBktChunk)] sums of the counts per chunk
+    trig_hit *tbuf;         // [n_hits] hits in bucket order
     trig_trigger *stage;    // [n_hits] fired seeds at their merged rank
     uint32_t *tile_nfired;  // [NG]
     uint32_t *tile_rank;    // [NG] merged rank of the tile's first core hit
@@ -71,7 +90,8 @@ struct BatchHeader {
     uint32_t n_chunks;      // total structure-pass chunks
     uint32_t err;
     uint32_t queue;         // tile work queue head
-    uint32_t pad[3];
+    uint32_t any_wide;      // a slice of the batch is wide
+    uint32_t pad[2];
 };
 
 constexpr uint32_t kChunkHits = 4096;       // structure-pass chunk
@@ -96,13 +116,16 @@ inline bool valid_tile_shape(uint32_t cap, uint32_t warps)
 constexpr uint32_t kMaxTilesPerSlice = 1u << 20;
 
 // Enqueues the batch pipeline; header/desc already copied to device scratch.
-constexpr int kPipelineKernels = 9;
+constexpr int kPipelineKernels = 12;
 extern const char *const kKernelNames[kPipelineKernels];
 
-// ev (optional, kPipelineKernels + 1 events): ev[i] is recorded before
-// pipeline kernel i and ev[kPipelineKernels] after the last one.
+// any_wide: the batch holds a wide slice (the bucket sums, scan and
+// scatter kernels run only then).  ev (optional, kPipelineKernels + 1 events): ev[i]
+// is recorded before pipeline kernel i and ev[kPipelineKernels] after the
+// last one (a kernel that does not run gets an empty interval).
+// *launches is increased by the number of kernels launched.
 cudaError_t launch_batch(BatchHeader *d_hdr, SliceDesc *d_desc, uint32_t n_slices, uint32_t max_pmt,
-                         bool any_smem_dt, const TileConfig &cfg, cudaStream_t st, uint64_t *launches,
+                         bool any_smem_dt, bool any_wide, const TileConfig &cfg, cudaStream_t st, uint64_t *launches,
                          bool rows, cudaEvent_t *ev = nullptr);
 
 int device_sm_count();

@@ -254,6 +254,25 @@ __device__ __forceinline__ void report(const SliceDesc &d, uint32_t flags)
     atomicOr(&d.stats->flags, flags);
 }
 
+// Time bucket of a wide slice: floor((t - O) / Wb) clamped to [0, NB).
+// For offsets below 2^31 the high half of rel * ceil(2^32 / Wb) is the
+// quotient or one more; one multiply corrects it.
+__device__ __forceinline__ uint32_t bkt_index(const SliceDesc &d, int64_t t)
+{
+    const int64_t rel = t - d.bkt_origin;
+    if (rel <= 0) return 0u;
+    uint32_t q;
+    if (d.bkt32 && rel < ((int64_t)1 << 31)) {
+        const uint32_t r = (uint32_t)rel;
+        q = __umulhi(r, d.bkt_magic);
+        if (q * d.bkt_w > r) --q;
+    } else {
+        const int64_t q64 = rel / (int64_t)d.bkt_w;
+        q = q64 >= (int64_t)d.n_bkt ? d.n_bkt : (uint32_t)q64;
+    }
+    return q < d.n_bkt ? q : d.n_bkt - 1;
+}
+
 // ---------------------------------------------------------------- k_prep
 
 __global__ void k_prep(BatchHeader *hdr, const SliceDesc *desc)
@@ -271,6 +290,13 @@ __global__ void k_prep(BatchHeader *hdr, const SliceDesc *desc)
         st->n_seeds = 0;
         st->n_triggers = 0;
         st->n_windows = 0;
+    }
+    // bucket counts of the wide slices start at zero
+    for (uint32_t s = 0; hdr->any_wide && s < n; ++s) {
+        if (!desc[s].wide) continue;
+        uint32_t *cnt = desc[s].bkt_cnt;
+        const uint32_t nb = desc[s].n_bkt;
+        for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += gridDim.x * blockDim.x) cnt[i] = 0;
     }
 }
 
@@ -329,6 +355,51 @@ __device__ __noinline__ void fill_leading_empty(uint32_t *e_lo, uint32_t *e_hi, 
 constexpr int kBoundsThreads = 256;
 constexpr int kBoundsUnroll = 4;
 
+// Structure pass over one chunk of a wide slice: the same checks of the CSR
+// layout and time order, then each valid hit counted in its time bucket.
+__device__ __noinline__ void bounds_wide_chunk(const SliceDesc &d, uint64_t first)
+{
+    const uint32_t lane = lane_id(), P = d.n_pmt;
+    const uint64_t n_hits = d.n_hits;
+    const trig_hit *__restrict__ hits = d.hits;
+    const uint64_t *__restrict__ poff = d.pmt_off;
+    for (uint32_t k0 = 0; k0 < kChunkHits; k0 += kBoundsThreads) {
+        const uint64_t li = first + k0 + threadIdx.x;
+        const bool valid = li < n_hits;
+        trig_hit h;
+        if (valid) h = load_hit(hits + li);
+        else h.t_ns = 0, h.pmt = 0xffff;
+        const uint32_t p = h.pmt;
+        const int64_t t = h.t_ns;
+        uint32_t pp = __shfl_up_sync(0xffffffffu, p, 1);
+        int64_t tp = __shfl_up_sync(0xffffffffu, t, 1);
+        uint32_t pn = __shfl_down_sync(0xffffffffu, p, 1);
+        if (!valid) continue;
+        if (lane == 0 && li > 0) {
+            const trig_hit q = load_hit(hits + li - 1);
+            pp = q.pmt;
+            tp = q.t_ns;
+        }
+        if (lane == 31 && li + 1 < n_hits) pn = hits[li + 1].pmt;
+        const bool is_first = li == 0 || pp != p;
+        const bool is_last = li + 1 == n_hits || pn != p;
+        uint32_t bad = 0;
+        if (p >= P) bad |= TRIG_FLAG_BAD_PMT;
+        else {
+            if (is_first && poff[p] != li) bad |= TRIG_FLAG_BAD_PMT;
+            if (is_last && poff[p + 1] != li + 1) bad |= TRIG_FLAG_BAD_PMT;
+            if (li + 1 == n_hits && poff[P] != n_hits) bad |= TRIG_FLAG_BAD_PMT;
+        }
+        if (t < d.in_lo || t >= d.in_hi) bad |= TRIG_FLAG_OUT_OF_RANGE;
+        if (!is_first && tp > t) bad |= TRIG_FLAG_UNSORTED;
+        if (bad) {
+            report(d, bad);
+            continue;
+        }
+        atomicAdd(&d.bkt_cnt[bkt_index(d, t)], 1u);
+    }
+}
+
 // One read of every hit.  Per hit: CSR layout and time order are checked
 // (run starts and ends against pmt_off, neighbours from adjacent lanes), and
 // the tile edges passed between the previous hit of the PMT and this one
@@ -354,6 +425,10 @@ __global__ void __launch_bounds__(kBoundsThreads) k_bounds(const BatchHeader *__
         uint32_t *__restrict__ e_lo = d.e_lo;
         uint32_t *__restrict__ e_hi = d.e_hi;
         const int64_t in_lo = d.in_lo, in_hi = d.in_hi;
+        if (d.wide) {
+            bounds_wide_chunk(d, first);
+            continue;
+        }
         auto cnt_lo = [&](int64_t t) -> uint32_t {
             return span32 ? edges_le32(t - base_lo, W32, magic, NG) : edges_le64(t, base_lo, W, NG);
         };
@@ -412,6 +487,109 @@ __global__ void __launch_bounds__(kBoundsThreads) k_bounds(const BatchHeader *__
     }
 }
 
+// ----------------------------------------------------------- k_bsum, k_bscan
+
+// Wide slices: bucket offsets = exclusive prefix of the bucket counts, in
+// two grid-wide passes over chunks of kBktChunk buckets (a block per chunk):
+// the chunk sums, then each chunk's scan from the sums of the chunks before
+// it.  The counts are reset to serve as fill cursors of the scatter.
+__global__ void __launch_bounds__(kBktChunk) k_bsum(const BatchHeader *__restrict__ hdr,
+                                                    const SliceDesc *__restrict__ desc)
+{
+    __shared__ uint32_t wsum[32];
+    const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
+    for (uint32_t s = 0; s < hdr->n_slices; ++s) {
+        const SliceDesc &d = desc[s];
+        if (!d.wide) continue;
+        const uint32_t nb = d.n_bkt, nch = (nb + kBktChunk - 1) / kBktChunk;
+        for (uint32_t c = blockIdx.x; c < nch; c += gridDim.x) {
+            const uint32_t i = c * kBktChunk + tid;
+            uint32_t v = i < nb ? d.bkt_cnt[i] : 0u;
+            v = __reduce_add_sync(0xffffffffu, v);
+            if (lane == 0) wsum[warp] = v;
+            __syncthreads();
+            if (warp == 0) {
+                uint32_t t = lane < kBktChunk / 32 ? wsum[lane] : 0u;
+                t = __reduce_add_sync(0xffffffffu, t);
+                if (lane == 0) d.bkt_part[c] = t;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kBktChunk) k_bscan(const BatchHeader *__restrict__ hdr,
+                                                     const SliceDesc *__restrict__ desc)
+{
+    __shared__ uint32_t wsum[33];
+    __shared__ uint32_t base;
+    const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
+    constexpr uint32_t NW = kBktChunk / 32;
+    for (uint32_t s = 0; s < hdr->n_slices; ++s) {
+        const SliceDesc &d = desc[s];
+        if (!d.wide) continue;
+        const uint32_t nb = d.n_bkt, nch = (nb + kBktChunk - 1) / kBktChunk;
+        for (uint32_t c = blockIdx.x; c < nch; c += gridDim.x) {
+            // sum of the chunks before c
+            uint32_t pre = 0;
+            for (uint32_t q = tid; q < c; q += kBktChunk) pre += d.bkt_part[q];
+            pre = __reduce_add_sync(0xffffffffu, pre);
+            if (lane == 0) wsum[warp] = pre;
+            __syncthreads();
+            if (warp == 0) {
+                uint32_t t = lane < NW ? wsum[lane] : 0u;
+                t = __reduce_add_sync(0xffffffffu, t);
+                if (lane == 0) base = t;
+            }
+            __syncthreads();
+            // the chunk's own exclusive scan
+            const uint32_t i = c * kBktChunk + tid;
+            const uint32_t v = i < nb ? d.bkt_cnt[i] : 0u;
+            const uint32_t incl = warp_incl_scan(v);
+            if (lane == 31) wsum[warp] = incl;
+            __syncthreads();
+            if (warp == 0) {
+                const uint32_t w = lane < NW ? wsum[lane] : 0u;
+                const uint32_t wi = warp_incl_scan(w);
+                if (lane < NW) wsum[lane] = wi - w;
+                if (lane == NW - 1) wsum[32] = wi;
+            }
+            __syncthreads();
+            if (i < nb) {
+                d.bkt_off[i] = base + wsum[warp] + incl - v;
+                d.bkt_cnt[i] = 0;
+            }
+            if (c == nch - 1 && tid == 0) d.bkt_off[nb] = base + wsum[32];
+            __syncthreads();
+        }
+    }
+}
+
+// --------------------------------------------------------------- k_scatter
+
+// Wide slices: every hit copied to its time bucket's range of tbuf (the
+// order inside a bucket is arbitrary; the tile pass sorts).  Slices with
+// malformed input (flagged by the structure pass) are skipped.
+__global__ void __launch_bounds__(256) k_scatter(const BatchHeader *__restrict__ hdr, const SliceDesc *__restrict__ desc)
+{
+    const uint32_t n_slices = hdr->n_slices, n_chunks = hdr->n_chunks;
+    for (uint32_t c = blockIdx.x; c < n_chunks; c += gridDim.x) {
+        const SliceDesc &d = desc[find_slice_by_chunk(desc, n_slices, c)];
+        if (!d.wide) continue;
+        if (d.stats->flags & (TRIG_FLAG_BAD_PMT | TRIG_FLAG_UNSORTED | TRIG_FLAG_OUT_OF_RANGE)) continue;
+        const uint64_t first = (uint64_t)(c - d.chunk0) * kChunkHits;
+        for (uint32_t k = threadIdx.x; k < kChunkHits; k += blockDim.x) {
+            const uint64_t li = first + k;
+            if (li >= d.n_hits) break;
+            const int4 v = *reinterpret_cast<const int4 *>(d.hits + li);
+            const int64_t t = (int64_t)(((uint64_t)(uint32_t)v.y << 32) | (uint32_t)v.x);
+            const uint32_t b = bkt_index(d, t);
+            const uint32_t pos = d.bkt_off[b] + atomicAdd(&d.bkt_cnt[b], 1u);
+            if (CHECK(17, pos, d.n_hits)) *reinterpret_cast<int4 *>(d.tbuf + pos) = v;
+        }
+    }
+}
+
 // ------------------------------------------------------------------ k_tile
 
 struct ItemInfo {
@@ -421,6 +599,8 @@ struct ItemInfo {
     uint32_t n;         // staged hits
     uint32_t rank_lo;   // merged rank of the first staged hit
     uint32_t mode;      // 0 staged, 1 overflow (split path), 2 skip (bad slice or empty)
+    uint32_t lo_t;      // B_g minus the time of the staged range's start
+    uint32_t span;      // length of the staged time range (ns)
 };
 
 template <int CAP>
@@ -1006,12 +1186,11 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 2048 ? 2 : 1)) k_tile(BatchHe
         item = __shfl_sync(0xffffffffu, item, 0);
         for (uint32_t it = 0;; ++it) {
             const uint32_t b = it & 1u, use = it >> 1;
-            uint32_t g = 0, P = 0, mode = 2;
+            uint32_t g = 0, P = 0, mode = 2, lo_t = 0, span = 0;
             uint64_t ra[R];
             uint32_t rl[R];
             uint64_t tot = 0, rlo = 0;
-            const uint32_t *elo = nullptr, *ehi = nullptr;
-            const uint64_t *poff = nullptr;
+            bool wide = false;
             if (item < n_items) {
                 // items arrive in increasing order: walk the slice index forward
                 if (d == nullptr || item < d->item0) s = find_slice_by_item(desc, n_slices, item), d = nullptr;
@@ -1022,14 +1201,31 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 2048 ? 2 : 1)) k_tile(BatchHe
                 }
                 g = item - d->item0;
                 P = d->n_pmt;
-                elo = d->e_lo + (size_t)g * P;
-                ehi = d->e_hi + (size_t)g * P;
-                poff = d->pmt_off;
-                if (!bad) {
-                    for (uint32_t p0 = 0; p0 < P; p0 += 32 * R) {
+                wide = d->wide != 0;
+                if (wide) {
+                    // one contiguous range of the bucketed copy: the core
+                    // buckets and hh buckets of halo on each side
+                    const uint32_t hh = d->bkt_halo, m = d->bkt_per_tile;
+                    const uint32_t c_lo = d->bkt_lead + g * m;
+                    const uint32_t b_lo = c_lo > hh ? c_lo - hh : 0u;
+                    const uint32_t b_hi = min(c_lo + m + hh, d->n_bkt);
+                    lo_t = (c_lo - b_lo) * d->bkt_w;
+                    span = (b_hi - b_lo) * d->bkt_w;
+                    if (!bad) {
+                        rlo = __ldg(d->bkt_off + b_lo);
+                        tot = __ldg(d->bkt_off + b_hi) - rlo;
+                    }
+                } else {
+                    // the PMTs' runs [lb(B_g - H), lb(B_{g+1} + H)), P <= 32 R
+                    const uint32_t *elo = d->e_lo + (size_t)g * P;
+                    const uint32_t *ehi = d->e_hi + (size_t)g * P;
+                    const uint64_t *poff = d->pmt_off;
+                    lo_t = d->halo;
+                    span = (uint32_t)d->tile_w + 2u * d->halo;
+                    if (!bad) {
 #pragma unroll
                         for (int r = 0; r < R; ++r) {
-                            const uint32_t p = p0 + r * 32 + lane;
+                            const uint32_t p = r * 32 + lane;
                             uint64_t a = 0, e = 0, sp_ = 0, ep_ = 0;
                             if (p < P) {
                                 a = __ldg(elo + p);
@@ -1045,9 +1241,9 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 2048 ? 2 : 1)) k_tile(BatchHe
                             rlo += a - sp_;
                         }
                     }
+                    tot = warp_sum_u64(tot);
+                    rlo = warp_sum_u64(rlo);
                 }
-                tot = warp_sum_u64(tot);
-                rlo = warp_sum_u64(rlo);
                 mode = bad ? 2u : (tot > (uint64_t)CAP ? 1u : (tot == 0 ? 2u : 0u));
             }
             uint32_t next = 0;
@@ -1073,34 +1269,25 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 2048 ? 2 : 1)) k_tile(BatchHe
                 info[b].n = (uint32_t)min(tot, (uint64_t)CAP);
                 info[b].rank_lo = (uint32_t)rlo;
                 info[b].mode = mode;
+                info[b].lo_t = lo_t;
+                info[b].span = span;
                 if (mode == 0) mbar_arrive_expect_tx(&full_bar[b], (uint32_t)tot * 16u);
                 else mbar_arrive(&full_bar[b]);
             }
             __syncwarp();
-            if (mode == 0) {
+            if (mode == 0 && wide) {
+                if (lane == 0 && CHECK(7, rlo + tot, d->n_hits + 1))
+                    bulk_g2s(cx.stage[b], d->tbuf + rlo, (uint32_t)tot * 16u, &full_bar[b]);
+            } else if (mode == 0) {
                 uint32_t dst = 0;
-                for (uint32_t p0 = 0; p0 < P; p0 += 32 * R) {
 #pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        uint32_t len = rl[r];
-                        uint64_t a = ra[r];
-                        if (P > 32 * R) {
-                            // wide detectors: registers hold only the last group; reload
-                            const uint32_t p = p0 + r * 32 + lane;
-                            len = 0;
-                            if (p < P) {
-                                const uint64_t sp_ = __ldg(poff + p), ep_ = __ldg(poff + p + 1);
-                                a = min(max((uint64_t)__ldg(elo + p), sp_), ep_);
-                                const uint64_t e = min(max((uint64_t)__ldg(ehi + p), a), ep_);
-                                len = (uint32_t)(e - a);
-                            }
-                        }
-                        const uint32_t incl = warp_incl_scan(len);
-                        if (len && CHECK(6, dst + incl, CAP + 1) && CHECK(7, a + len, d->n_hits + 1))
-                            bulk_g2s(cx.stage[b] + 2 * (size_t)(dst + incl - len), d->hits + a, len * 16u,
-                                     &full_bar[b]);
-                        dst += __shfl_sync(0xffffffffu, incl, 31);
-                    }
+                for (int r = 0; r < R; ++r) {
+                    const uint32_t len = rl[r];
+                    const uint64_t a = ra[r];
+                    const uint32_t incl = warp_incl_scan(len);
+                    if (len && CHECK(6, dst + incl, CAP + 1) && CHECK(7, a + len, d->n_hits + 1))
+                        bulk_g2s(cx.stage[b] + 2 * (size_t)(dst + incl - len), d->hits + a, len * 16u, &full_bar[b]);
+                    dst += __shfl_sync(0xffffffffu, incl, 31);
                 }
             }
             item = next;
@@ -1158,11 +1345,11 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 2048 ? 2 : 1)) k_tile(BatchHe
             const int64_t W = sl_w;
             const int64_t Bg = sl_t0 + (int64_t)inf.g * W;
             const int64_t core_end = min(Bg + W, sl_t0 + sl_len);
-            const uint32_t H = tp.H;
-            const int64_t tb = Bg - (int64_t)H;
-            const uint32_t span = (uint32_t)W + 2 * H;
-            const uint32_t hi_t = H + (uint32_t)(core_end - Bg);
-            const uint32_t bsh = tile_sort<CAP, NC>(cx, cx.stage[b], inf.n, tb, span, red, H, hi_t);
+            // the staged range starts lo_t (>= H) before the core
+            const uint32_t lo_t = inf.lo_t;
+            const int64_t tb = Bg - (int64_t)lo_t;
+            const uint32_t hi_t = lo_t + (uint32_t)(core_end - Bg);
+            const uint32_t bsh = tile_sort<CAP, NC>(cx, cx.stage[b], inf.n, tb, inf.span, red, lo_t, hi_t);
             // rank of the core's first hit = rank_lo + c0, known after the sort
             const uint32_t c0 = red[NW + 1], c1 = red[NW + 2];
             const uint32_t tile_rank = inf.rank_lo + c0;
@@ -1412,9 +1599,25 @@ __global__ void __launch_bounds__(256) k_whits(const BatchHeader *__restrict__ h
             if (!CHECK(9, i, d.win_cap)) continue;
             const trig_window win = d.windows[i];
             uint64_t cnt = 0;
-            for (uint32_t p = lane; p < d.n_pmt; p += 32) {
-                const uint64_t sp = d.pmt_off[p], ep = d.pmt_off[p + 1];
-                cnt += rank_in_pmt(d, p, win.hi_ns + 1, sp, ep) - rank_in_pmt(d, p, win.lo_ns, sp, ep);
+            if (d.wide) {
+                // whole buckets between the edge buckets, plus the edge
+                // buckets' hits inside [lo, hi]
+                const uint32_t bl = bkt_index(d, win.lo_ns), bh = bkt_index(d, win.hi_ns);
+                if (bl + 1 < bh && lane == 0) cnt = d.bkt_off[bh] - d.bkt_off[bl + 1];
+                const uint32_t e0 = d.bkt_off[bl], e1 = d.bkt_off[bl + 1];
+                for (uint32_t j = e0 + lane; j < e1; j += 32) {
+                    const int64_t t = d.tbuf[j].t_ns;
+                    cnt += t >= win.lo_ns && t <= win.hi_ns;
+                }
+                if (bh != bl) {
+                    const uint32_t f0 = d.bkt_off[bh], f1 = d.bkt_off[bh + 1];
+                    for (uint32_t j = f0 + lane; j < f1; j += 32) cnt += d.tbuf[j].t_ns <= win.hi_ns;
+                }
+            } else {
+                for (uint32_t p = lane; p < d.n_pmt; p += 32) {
+                    const uint64_t sp = d.pmt_off[p], ep = d.pmt_off[p + 1];
+                    cnt += rank_in_pmt(d, p, win.hi_ns + 1, sp, ep) - rank_in_pmt(d, p, win.lo_ns, sp, ep);
+                }
             }
             cnt = warp_sum_u64(cnt);
             __syncwarp();
@@ -1570,27 +1773,42 @@ static cudaError_t launch_tile(BatchHeader *hdr, SliceDesc *desc, uint32_t max_p
     return cudaGetLastError();
 }
 
-const char *const kKernelNames[kPipelineKernels] = {"k_prep", "k_bounds", "k_tile",  "k_scan",  "k_copy",
-                                                     "k_wscan", "k_wwrite", "k_whits", "k_status"};
+const char *const kKernelNames[kPipelineKernels] = {"k_prep",  "k_bounds", "k_bsum",   "k_bscan",
+                                                     "k_scatter", "k_tile", "k_scan",   "k_copy",
+                                                     "k_wscan", "k_wwrite", "k_whits",  "k_status"};
 
 cudaError_t launch_batch(BatchHeader *d_hdr, SliceDesc *d_desc, uint32_t n_slices, uint32_t max_pmt,
-                         bool any_smem_dt, const TileConfig &cfg, cudaStream_t st, uint64_t *launches, bool rows,
-                         cudaEvent_t *ev)
+                         bool any_smem_dt, bool any_wide, const TileConfig &cfg, cudaStream_t st, uint64_t *launches,
+                         bool rows, cudaEvent_t *ev)
 {
     const int sms = device_sm_count();
     auto mark = [&](int i) {
         if (ev) cudaEventRecord(ev[i], st);
     };
     const uint32_t sb = n_slices < (uint32_t)sms * 4 ? n_slices : (uint32_t)sms * 4;
+    uint64_t nl = 0;
     mark(0);
-    k_prep<<<1, 256, 0, st>>>(d_hdr, d_desc);
+    k_prep<<<any_wide ? sms : 1, 256, 0, st>>>(d_hdr, d_desc);
     mark(1);
     k_bounds<<<sms * 8, kBoundsThreads, 0, st>>>(d_hdr, d_desc);
+    nl += 2;
     if (rows) {
         k_rank0<<<n_slices, 256, 0, st>>>(d_hdr, d_desc);
-        if (launches) *launches += 1;
+        nl += 1;
     }
     mark(2);
+    if (any_wide) {
+        k_bsum<<<sms * 2, kBktChunk, 0, st>>>(d_hdr, d_desc);
+        mark(3);
+        k_bscan<<<sms * 2, kBktChunk, 0, st>>>(d_hdr, d_desc);
+        mark(4);
+        k_scatter<<<sms * 8, 256, 0, st>>>(d_hdr, d_desc);
+        nl += 3;
+    } else {
+        mark(3);
+        mark(4);
+    }
+    mark(5);
     cudaError_t e;
     const bool smem_dt = any_smem_dt && max_pmt <= kSmemDtMaxPmt;
     if (cfg.cap == 2048 && cfg.warps == 16)
@@ -1606,20 +1824,21 @@ cudaError_t launch_batch(BatchHeader *d_hdr, SliceDesc *d_desc, uint32_t n_slice
         e = smem_dt ? launch_tile<4096, 512, true>(d_hdr, d_desc, max_pmt, st)
                     : launch_tile<4096, 512, false>(d_hdr, d_desc, max_pmt, st);
     if (e != cudaSuccess) return e;
-    mark(3);
-    k_scan<<<sb, 1024, 0, st>>>(d_hdr, d_desc);
-    mark(4);
-    k_copy<<<sms * 4, 256, 0, st>>>(d_hdr, d_desc);
-    mark(5);
-    k_wscan<<<sb, 1024, 0, st>>>(d_hdr, d_desc);
     mark(6);
-    k_wwrite<<<sms * 4, 256, 0, st>>>(d_hdr, d_desc);
+    k_scan<<<sb, 1024, 0, st>>>(d_hdr, d_desc);
     mark(7);
-    k_whits<<<sms * 4, 256, 0, st>>>(d_hdr, d_desc);
+    k_copy<<<sms * 4, 256, 0, st>>>(d_hdr, d_desc);
     mark(8);
-    k_status<<<1, 256, 0, st>>>(d_hdr, d_desc);
+    k_wscan<<<sb, 1024, 0, st>>>(d_hdr, d_desc);
     mark(9);
-    if (launches) *launches += kPipelineKernels;
+    k_wwrite<<<sms * 4, 256, 0, st>>>(d_hdr, d_desc);
+    mark(10);
+    k_whits<<<sms * 4, 256, 0, st>>>(d_hdr, d_desc);
+    mark(11);
+    k_status<<<1, 256, 0, st>>>(d_hdr, d_desc);
+    mark(12);
+    nl += 7;
+    if (launches) *launches += nl;
     return cudaGetLastError();
 }
 
