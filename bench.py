@@ -30,6 +30,11 @@ if ROOT not in sys.path:
 
 METRIC = "hits/s (batched+served vs plain per-slice) at % HBM roofline; p99 slice latency"
 WORKLOAD = "batched: 64 slices of 200 ms, 32/84-PMT towers, per-slice rate U[50,500] kHz"
+WORKLOADS = {
+    "batched": WORKLOAD,
+    "scaled": "scaled array: one 200 ms slice (+3 us halos) of 2688 PMTs (32 towers of 84 on a 90 m grid), "
+              "55 kHz, 1000 muons",
+}
 TILE_BYTES_PER_HIT = 16          # k_tile reads every 16-byte hit once (halo re-reads excluded)
 BOUNDS_BYTES_PER_HIT = 16        # k_bounds reads every hit once
 
@@ -199,6 +204,8 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=20.0, help="detector-seconds per detector")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--slices", type=int, default=64, help="slices of the batched workload (profiling runs)")
+    ap.add_argument("--workload", default="batched", choices=sorted(WORKLOADS),
+                    help="batched (the default step) or the scaled 2688-PMT array (profiling runs)")
     ap.add_argument("--tile-cap", type=int, default=0, help="tile capacity (2048 or 4096); disables autotuning")
     ap.add_argument("--tile-warps", type=int, default=0, help="consumer warps per block (8 or 16)")
     ap.add_argument("--tile-fill", type=int, default=0, help="tile fill percent")
@@ -243,7 +250,10 @@ def main():
         return float(t.item())
 
     par = dict(workload.DEFAULT_PARAMS)
-    wl = workload.cfg_batched(seed=args.seed + 1000 * rank)
+    if args.workload == "scaled":
+        wl = workload.cfg_scaled(seed=args.seed + 1000 * rank)
+    else:
+        wl = workload.cfg_batched(seed=args.seed + 1000 * rank)
     wl.submissions = wl.submissions[: args.slices]
     log(f"workload ready: {len(wl.submissions)} slices")
     manual = bool(args.tile_cap or args.tile_warps or args.tile_fill)
@@ -321,13 +331,16 @@ def main():
                              "kernel_ms": bounds_ms},
                 "pipeline": {"bytes_per_hit": TILE_BYTES_PER_HIT + BOUNDS_BYTES_PER_HIT,
                              "achieved": (TILE_BYTES_PER_HIT + BOUNDS_BYTES_PER_HIT) * n_hits / (ms * 1e-3) / 1e9}}
+    # DRAM bytes per hit of k_tile from an ncu capture of this workload
+    # (profiles/k_tile_traffic.json), valid while the kernel source matches
     traffic_file = os.path.join(ROOT, "profiles", "k_tile_traffic.json")
     if os.path.exists(traffic_file):
         try:
             tf = json.load(open(traffic_file))
-            if tf.get("source_hash") == _tile_source_hash():
-                roofline["traffic"] = tf["bytes_per_hit"] * n_hits
-        except (OSError, ValueError, KeyError):
+            per_hit = tf.get("bytes_per_hit", {}).get(args.workload)
+            if tf.get("source_hash") == _tile_source_hash() and per_hit:
+                roofline["traffic"] = per_hit * n_hits
+        except (OSError, ValueError, AttributeError):
             pass
 
     # ---------------------------------------------------- e2e, host buffers
@@ -389,7 +402,7 @@ def main():
             "metric": METRIC, "value": value, "unit": "hits/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "slices": len(wl.submissions), "hits_per_rank": n_hits,
+            "config": {"workload": WORKLOADS[args.workload], "slices": len(wl.submissions), "hits_per_rank": n_hits,
                        "tile": {wl.detectors[i].name: trig.trig_detector_tile_config(d) for i, d in enumerate(dets)},
                        "bytes_per_rank": int(batch.input_bytes), "path": "trig_batch_run, CUDA graph replay",
                        "l2": "inputs larger than L2 (no flush needed)", "parallelism": f"dp{ws} (slices)"},
