@@ -261,12 +261,13 @@ int trig_slice_rows(const trig_slice_dev *slice, trig_hit *merged_out, uint32_t 
  * tuned: tile capacity (hits per shared-memory tile including halos),
  * consumer warps per block and target fill (percent of the capacity a tile
  * plus its halos should hold at the slice's mean rate; it sets the tile
- * width).  (cap, warps) must be (4096, 16), (4096, 8), (2048, 16) or (2048, 8);
+ * width).  (cap, warps) must be (4096, 16), (4096, 8), (2048, 16), (2048, 8)
+ * or (1024, 4);
  * fill_pct in [10, 95].  Applies to later runs in this process. */
 int trig_set_tile_config(uint32_t cap, uint32_t warps, uint32_t fill_pct);
 int trig_get_tile_config(uint32_t *cap, uint32_t *warps, uint32_t *fill_pct);
 
-/* Autotuner: times every launch shape (4 (cap, warps) pairs x 4 fills) on
+/* Autotuner: times every launch shape (5 (cap, warps) pairs x 4 fills) on
  * the given device-resident slices, which must all belong to det, keeps the
  * fastest on det (later runs use it for det's slices; a batch mixing
  * detectors takes the shape of the one with the most hits) and, when the

@@ -242,7 +242,9 @@ static int64_t choose_tile_w(const trig_detector *det, uint64_t n_hits, const Ti
     const double w_min = std::max(256.0, (double)det->par.slice_ns / (double)kMaxTilesPerSlice + 1.0);
     if (w < w_min) w = w_min;
     if (w > (double)det->par.slice_ns) w = (double)det->par.slice_ns;
-    if (w > 2e9) w = 2e9;
+    // a tile plus its halos spans less than kMaxTileSpan ns
+    const double w_max = std::max(1.0, (double)(kMaxTileSpan - 1) - 2.0 * det->tile_halo);
+    if (w > w_max) w = w_max;
     return (int64_t)w;
 }
 
@@ -271,7 +273,7 @@ static WideGrid wide_grid(const trig_detector *det, uint64_t n_hits, const TileC
     g.hh = H ? (H + g.wb - 1) / g.wb : 0;
     double m = std::floor(target / ((double)g.wb * rate)) - 2.0 * g.hh;
     m = std::min(m, std::ceil(S / g.wb));
-    m = std::min(m, std::floor(2e9 / g.wb) - 2.0 * g.hh);       // staged span below 2^31 ns
+    m = std::min(m, std::floor((double)(kMaxTileSpan - 1) / g.wb) - 2.0 * g.hh);   // staged span below 2^20 ns
     m = std::max(1.0, m);
     g.m = (uint32_t)m;
     g.lead = (uint32_t)(((uint64_t)det->in_halo + g.wb - 1) / g.wb);
@@ -346,6 +348,8 @@ static int plan_into(const trig_slice_dev *sl, uint32_t n, uintptr_t base, const
         int64_t W = 0;
         if (wide) {
             const WideGrid wg = wide_grid(det, x.n_hits, cfg);
+            if ((uint64_t)(wg.m + 2 * wg.hh) * wg.wb >= (uint64_t)kMaxTileSpan)
+                return fail(TRIG_EINVAL, "slice too long for this detector's tiles");
             W = (int64_t)wg.m * wg.wb;
             d.wide = 1;
             d.bkt_w = wg.wb;
@@ -730,7 +734,7 @@ extern "C" int trig_autotune(trig_detector *det, const trig_slice_dev *slices, u
     if (!det || !slices || n_slices == 0) return fail(TRIG_EINVAL, "trig_autotune: NULL argument");
     for (uint32_t s = 0; s < n_slices; ++s)
         if (slices[s].det != det) return fail(TRIG_EINVAL, "trig_autotune: all slices must belong to det");
-    static const uint32_t shapes[][2] = {{4096, 16}, {4096, 8}, {2048, 16}, {2048, 8}};
+    static const uint32_t shapes[][2] = {{4096, 16}, {4096, 8}, {2048, 16}, {2048, 8}, {1024, 4}};
     static const uint32_t fills[] = {40, 55, 70, 85};
     cudaStream_t st = (cudaStream_t)stream;
     // scratch for the largest candidate

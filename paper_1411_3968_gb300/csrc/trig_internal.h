@@ -15,6 +15,10 @@ constexpr uint32_t kMaxPmt = 4096;          // PMTs per detector
 constexpr uint32_t kSmemDtMaxPmt = 96;      // dt table lives in shared memory up to this P
 constexpr uint32_t kWideMinPmt = 129;       // from this P on, slices are staged from a bucketed copy
 constexpr uint32_t kBktChunk = 1024;        // buckets per block of the bucket scan
+// A tile plus its halos spans less than 2^20 ns, so a hit's time within the
+// staged range and its PMT (< 2^12) pack into 32 bits.
+constexpr uint32_t kTileSpanBits = 20;
+constexpr int64_t kMaxTileSpan = ((int64_t)1 << kTileSpanBits) - 1;
 constexpr uint64_t kMaxSliceHits = 0xFFFFFFF0ull;
 
 // Detector tables resident on the device (owned by trig_detector).
@@ -103,7 +107,8 @@ cudaError_t launch_dtmax(const int32_t *xyz, uint32_t n_pmt, uint32_t tol, uint3
 // Launch shape of the tile kernel: hits per shared-memory tile, consumer
 // warps per block, and the target fill of a tile (percent of cap) that sets
 // the tile width.  Valid (cap, warps): (4096, 16), (4096, 8), (2048, 16),
-// (2048, 8); the 2048-hit tiles run two blocks per SM.
+// (2048, 8), (1024, 4); smaller tiles run more blocks per SM (up to 2 for
+// 2048 hits, 4 or more for 1024).
 struct TileConfig {
     uint32_t cap;
     uint32_t warps;
@@ -111,7 +116,7 @@ struct TileConfig {
 };
 inline bool valid_tile_shape(uint32_t cap, uint32_t warps)
 {
-    return (cap == 4096 || cap == 2048) && (warps == 16 || warps == 8);
+    return ((cap == 4096 || cap == 2048) && (warps == 16 || warps == 8)) || (cap == 1024 && warps == 4);
 }
 constexpr uint32_t kMaxTilesPerSlice = 1u << 20;
 

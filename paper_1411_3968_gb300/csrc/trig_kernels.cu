@@ -640,6 +640,12 @@ __device__ __forceinline__ uint32_t key_t(uint64_t k) { return (uint32_t)(k >> 3
 __device__ __forceinline__ uint32_t key_p(uint64_t k) { return (uint32_t)(k >> 16) & 0xffffu; }
 __device__ __forceinline__ uint32_t key_q(uint64_t k) { return (uint32_t)k & 0xffffu; }
 
+// Packed key of the trigger phases: time within the staged range (below
+// 2^20 ns) and PMT (below 2^12).  0xffffffff marks "no hit".
+constexpr uint32_t kPkNone = 0xffffffffu;
+__device__ __forceinline__ uint32_t pk_t(uint32_t k) { return k >> 12; }
+__device__ __forceinline__ uint32_t pk_p(uint32_t k) { return k & 0xfffu; }
+
 // Consumer-wide exclusive scan of cnt[0..nb), nb a multiple of NC; writes
 // the total to cnt[nb].  Scratch words red[0..NC/32].
 template <int NC>
@@ -680,7 +686,9 @@ __device__ __forceinline__ uint32_t bucket_of(uint32_t t_rel, uint32_t bsh)
 }
 
 // Merge (sort) the n staged records of `buf` by (t - tb, pmt, charge); the
-// keys land, in order, in the first 8 * n bytes of `buf`.  Counting sort on
+// keys land, in order, in the first 8 * n bytes of `buf`, and their packed
+// 32-bit forms (t_rel << 12 | pmt, the staged range spans < 2^20 ns) at
+// buf + CAP.  Counting sort on
 // the time bucket t_rel >> bsh, then each key's rank inside its bucket;
 // cx.cnt[b] keeps the index of bucket b's first key (cx.cnt[NBK] = n), so a
 // time range maps to an index range without a search.  Also counts the keys
@@ -690,6 +698,7 @@ template <int CAP, int NC>
 __device__ uint32_t tile_sort(TileCtx &cx, uint64_t *buf, uint32_t n, int64_t tb, uint32_t span, uint32_t *red,
                               uint32_t lo_t, uint32_t hi_t)
 {
+    uint32_t *pk = reinterpret_cast<uint32_t *>(buf + CAP);      // packed keys, upper half of the buffer
     constexpr uint32_t NW = NC / 32;
     constexpr int NBK = TileLayout<CAP>::NBK;
     constexpr int PER = CAP / NC;
@@ -750,6 +759,7 @@ __device__ uint32_t tile_sort(TileCtx &cx, uint64_t *buf, uint32_t n, int64_t tb
             r += (o < k) || (o == k && m < j);
         }
         buf[r] = k;
+        pk[r] = (key_t(k) << 12) | key_p(k);
     }
     cons_sync<NC>();
     return bsh;
@@ -789,43 +799,44 @@ __device__ CoreOut tile_trigger(TileCtx &cx, const uint64_t *keys, uint32_t n, u
     //    on another PMT of the same floor within tau.  A warp holds 32
     //    consecutive hits; the two neighbours on each side come from the
     //    adjacent lanes (edge lanes read them), a longer run within tau is
-    //    followed by a loop.
+    //    followed by a loop.  Packed keys carry time and PMT.
+    const uint32_t *pk = reinterpret_cast<const uint32_t *>(keys + CAP);
     const uint32_t nwords = (ncore + 31) / 32;
     for (uint32_t base = 0; base < ncore; base += NC) {
         const uint32_t i = c0 + base + tid;
         const bool in = i < c1;
         // hits past the core (halo) are loaded too: they are neighbours
-        const uint64_t ki = i < n ? keys[i] : ~0ull;
-        const uint32_t ti = key_t(ki), pi = key_p(ki);
+        const uint32_t ki = i < n ? pk[i] : kPkNone;
+        const uint32_t ti = pk_t(ki), pi = pk_p(ki);
         const uint32_t fi = in ? cx.floor_s[pi] : 0u;
-        bool seed = in && key_q(ki) >= qseed;
+        bool seed = in && key_q(keys[i]) >= qseed;
         bool more_up = false, more_dn = false;
 #pragma unroll
         for (uint32_t dd = 1; dd <= 2; ++dd) {
-            uint64_t ku = __shfl_up_sync(0xffffffffu, ki, dd);
-            uint64_t kd = __shfl_down_sync(0xffffffffu, ki, dd);
-            if (lane < dd) ku = (in && i >= dd) ? keys[i - dd] : ~0ull;
-            if (lane + dd >= 32) kd = (in && i + dd < n) ? keys[i + dd] : ~0ull;
-            if (in && i < dd) ku = ~0ull;
-            if (in && i + dd >= n) kd = ~0ull;
-            const bool near_u = ku != ~0ull && ti - key_t(ku) <= tau;
-            const bool near_d = kd != ~0ull && key_t(kd) - ti <= tau;
-            if (near_u && key_p(ku) != pi && cx.floor_s[key_p(ku)] == fi) seed = true;
-            if (near_d && key_p(kd) != pi && cx.floor_s[key_p(kd)] == fi) seed = true;
+            uint32_t ku = __shfl_up_sync(0xffffffffu, ki, dd);
+            uint32_t kd = __shfl_down_sync(0xffffffffu, ki, dd);
+            if (lane < dd) ku = (in && i >= dd) ? pk[i - dd] : kPkNone;
+            if (lane + dd >= 32) kd = (in && i + dd < n) ? pk[i + dd] : kPkNone;
+            if (in && i < dd) ku = kPkNone;
+            if (in && i + dd >= n) kd = kPkNone;
+            const bool near_u = ku != kPkNone && ti - pk_t(ku) <= tau;
+            const bool near_d = kd != kPkNone && pk_t(kd) - ti <= tau;
+            if (near_u && pk_p(ku) != pi && cx.floor_s[pk_p(ku)] == fi) seed = true;
+            if (near_d && pk_p(kd) != pi && cx.floor_s[pk_p(kd)] == fi) seed = true;
             more_up = near_u;
             more_dn = near_d;
         }
         if (in && !seed && (more_up || more_dn)) {
             // three or more hits within tau on one side: walk further
             for (uint32_t j = i + 3; more_dn && j < n; ++j) {
-                const uint64_t kj = keys[j];
-                if (key_t(kj) - ti > tau) break;
-                if (key_p(kj) != pi && cx.floor_s[key_p(kj)] == fi) { seed = true; break; }
+                const uint32_t kj = pk[j];
+                if (pk_t(kj) - ti > tau) break;
+                if (pk_p(kj) != pi && cx.floor_s[pk_p(kj)] == fi) { seed = true; break; }
             }
             for (uint32_t j = i - 2; more_up && !seed && j-- > 0;) {
-                const uint64_t kj = keys[j];
-                if (ti - key_t(kj) > tau) break;
-                if (key_p(kj) != pi && cx.floor_s[key_p(kj)] == fi) { seed = true; break; }
+                const uint32_t kj = pk[j];
+                if (ti - pk_t(kj) > tau) break;
+                if (pk_p(kj) != pi && cx.floor_s[pk_p(kj)] == fi) { seed = true; break; }
             }
         }
         // halo hits past the core are neighbours only, never seeds here
@@ -868,8 +879,8 @@ __device__ CoreOut tile_trigger(TileCtx &cx, const uint64_t *keys, uint32_t n, u
     //     below); one thread per seed
     uint32_t *swin = reinterpret_cast<uint32_t *>(seed_cnt + CAP);    // j0 | j1 << 16
     for (uint32_t k = tid; k < ns; k += NC) {
-        const uint64_t ks = keys[seed_idx[k]];
-        const uint32_t ts = key_t(ks), dm = cx.dmax_s[key_p(ks)];
+        const uint32_t ks = pk[seed_idx[k]];
+        const uint32_t ts = pk_t(ks), dm = cx.dmax_s[pk_p(ks)];
         const uint32_t j0 = boff[bucket_of<CAP>(ts >= dm ? ts - dm : 0u, bsh)];
         const uint32_t j1 = boff[bucket_of<CAP>(ts + dm, bsh) + 1];
         swin[k] = j0 | (j1 << 16);
@@ -882,7 +893,7 @@ __device__ CoreOut tile_trigger(TileCtx &cx, const uint64_t *keys, uint32_t n, u
     //    independent tests per lane in flight
     {
         // expected keys in a scan range: 2H + 1 ns at the tile's density
-        const unsigned long long span_n = n ? (unsigned long long)key_t(keys[n - 1]) + 1ull : 1ull;
+        const unsigned long long span_n = n ? (unsigned long long)pk_t(pk[n - 1]) + 1ull : 1ull;
         const unsigned long long est = (unsigned long long)(2u * tp.H + 1u) * n / span_n;
         const uint32_t lg = est >= 48 ? 5u : est >= 20 ? 4u : 3u;
         const uint32_t G = 1u << lg, gl = lane & (G - 1u), gid = tid >> lg, NG = NC >> lg;
@@ -892,15 +903,15 @@ __device__ CoreOut tile_trigger(TileCtx &cx, const uint64_t *keys, uint32_t n, u
             uint32_t c = 0;
             if (k < ns) {
                 const uint32_t w = swin[k];
-                const uint64_t ks = keys[seed_idx[k]];
-                const uint32_t ts = key_t(ks), ps = key_p(ks);
+                const uint32_t ks = pk[seed_idx[k]];
+                const uint32_t ts = pk_t(ks), ps = pk_p(ks);
                 const uint32_t j0 = w & 0xffffu, j1 = w >> 16;
                 if (CHECK(12, j1, n + 1) && CHECK(13, ps, P)) {
                     const uint16_t *row_s = cx.dt_s + (size_t)ps * P;
                     const uint16_t *row_g = cx.dt_g + (size_t)ps * P;
                     auto causal = [&](uint32_t j) -> uint32_t {
-                        const uint64_t kj = keys[j];
-                        const uint32_t tj = key_t(kj), pj = key_p(kj);
+                        const uint32_t kj = pk[j];
+                        const uint32_t tj = pk_t(kj), pj = pk_p(kj);
                         if (!CHECK(11, pj, P)) return 0u;
                         const uint32_t lim = SMEM_DT ? (uint32_t)row_s[pj] : (uint32_t)__ldg(row_g + pj);
                         return (tj > ts ? tj - ts : ts - tj) <= lim;
@@ -1128,7 +1139,7 @@ __device__ void tile_overflow(TileCtx &cx, uint64_t *buf, const SliceDesc &d, co
 }
 
 template <int CAP, int NC, bool SMEM_DT>
-__global__ void __launch_bounds__(NC + 32, (CAP <= 2048 ? 2 : 1)) k_tile(BatchHeader *__restrict__ hdr,
+__global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 1)) k_tile(BatchHeader *__restrict__ hdr,
                                                                           const SliceDesc *__restrict__ desc,
                                                                           uint32_t max_pmt)
 {
@@ -1811,7 +1822,10 @@ cudaError_t launch_batch(BatchHeader *d_hdr, SliceDesc *d_desc, uint32_t n_slice
     mark(5);
     cudaError_t e;
     const bool smem_dt = any_smem_dt && max_pmt <= kSmemDtMaxPmt;
-    if (cfg.cap == 2048 && cfg.warps == 16)
+    if (cfg.cap == 1024)
+        e = smem_dt ? launch_tile<1024, 128, true>(d_hdr, d_desc, max_pmt, st)
+                    : launch_tile<1024, 128, false>(d_hdr, d_desc, max_pmt, st);
+    else if (cfg.cap == 2048 && cfg.warps == 16)
         e = smem_dt ? launch_tile<2048, 512, true>(d_hdr, d_desc, max_pmt, st)
                     : launch_tile<2048, 512, false>(d_hdr, d_desc, max_pmt, st);
     else if (cfg.cap == 2048)
