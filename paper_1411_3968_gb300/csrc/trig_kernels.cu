@@ -909,22 +909,28 @@ __device__ CoreOut tile_trigger(TileCtx &cx, const uint64_t *keys, uint32_t n, u
                 if (CHECK(12, j1, n + 1) && CHECK(13, ps, P)) {
                     const uint16_t *row_s = cx.dt_s + (size_t)ps * P;
                     const uint16_t *row_g = cx.dt_g + (size_t)ps * P;
-                    auto causal = [&](uint32_t j) -> uint32_t {
-                        const uint32_t kj = pk[j];
+                    // key kj counts when |t_j - t_s| <= dt[p_s][p_j]
+                    auto causal = [&](uint32_t kj) -> uint32_t {
                         const uint32_t tj = pk_t(kj), pj = pk_p(kj);
                         if (!CHECK(11, pj, P)) return 0u;
                         const uint32_t lim = SMEM_DT ? (uint32_t)row_s[pj] : (uint32_t)__ldg(row_g + pj);
                         return (tj > ts ? tj - ts : ts - tj) <= lim;
                     };
+                    // each lane takes four consecutive keys per 16-byte load
+                    // (from j0 rounded down to a multiple of 4, inside the
+                    // CAP-entry key array); positions outside [j0, j1) use
+                    // the seed's own key, which is never looked up out of
+                    // range, and are not counted
                     uint32_t ca = 0, cb = 0, cc = 0, cd = 0;
-                    uint32_t j = j0 + gl;
-                    for (; j + 3 * G < j1; j += 4 * G) {
-                        ca += causal(j);
-                        cb += causal(j + G);
-                        cc += causal(j + 2 * G);
-                        cd += causal(j + 3 * G);
+                    for (uint32_t q = (j0 & ~3u) + 4 * gl; q < j1; q += 4 * G) {
+                        const uint4 v = *reinterpret_cast<const uint4 *>(pk + q);
+                        const bool m0 = q >= j0, m1 = q + 1 >= j0 && q + 1 < j1;
+                        const bool m2 = q + 2 >= j0 && q + 2 < j1, m3 = q + 3 < j1;
+                        ca += m0 & causal(m0 ? v.x : ks);
+                        cb += m1 & causal(m1 ? v.y : ks);
+                        cc += m2 & causal(m2 ? v.z : ks);
+                        cd += m3 & causal(m3 ? v.w : ks);
                     }
-                    for (; j < j1; j += G) ca += causal(j);
                     c = ca + cb + cc + cd;
                 }
             }
