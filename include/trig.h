@@ -52,6 +52,8 @@ extern "C" {
 #define TRIG_FLAG_TRIG_FULL    0x10u  /* more triggers than trig_cap             */
 #define TRIG_FLAG_WIN_FULL     0x20u  /* more windows than win_cap               */
 #define TRIG_FLAG_TIMEOUT      0x40u  /* a bounded device wait gave up            */
+#define TRIG_FLAG_EV_FULL      0x80u  /* more event hits than ev_cap, or a halo of
+                                         more than TRIG_EV_HALO_MAX hits              */
 
 /* ----------------------------------------------------------------- types */
 
@@ -114,6 +116,8 @@ typedef struct {
     uint64_t n_seeds;
     uint64_t n_triggers;        /* may exceed trig_cap (then TRIG_FLAG_TRIG_FULL) */
     uint64_t n_windows;         /* may exceed win_cap  (then TRIG_FLAG_WIN_FULL)  */
+    uint64_t n_events;          /* hits inside the merged windows (event runs
+                                   only; may exceed ev_cap, then TRIG_FLAG_EV_FULL) */
 } trig_slice_stats;
 
 typedef struct trig_detector trig_detector;
@@ -128,6 +132,10 @@ typedef struct {
     trig_trigger *triggers;     /* n_triggers entries, (t, pmt, charge) order */
     trig_window *windows;       /* n_windows entries, time order              */
     int64_t latency_ns;         /* submit -> result ready (host clock)        */
+    trig_hit *events;           /* n_events hits inside the windows, in (t,
+                                   pmt, charge) order, when the detector
+                                   extracts events (trig_set_events); else NULL */
+    uint64_t n_events;
 } trig_result;
 
 /* ------------------------------------------------------------- detectors */
@@ -217,12 +225,44 @@ size_t trig_batch_scratch_bytes(const trig_slice_dev *slices, uint32_t n_slices)
  * reaches this point.  `scratch` is device memory of at least
  * trig_batch_scratch_bytes(), 256-byte aligned; it must not be used by
  * anything else until the work completes.  flags: TRIG_RUN_GRAPH replays
- * the launch sequence from a cached CUDA graph (one per stream and scratch
- * pointer).  EINVAL on bad arguments (nothing is launched). */
+ * the launch sequence from a cached CUDA graph (one per stream, scratch
+ * pointer and batch plan; a new batch captures a new graph).  EINVAL on bad
+ * arguments (nothing is launched). */
 #define TRIG_RUN_GRAPH 0x1u
 #define TRIG_RUN_TIMED 0x2u   /* record CUDA events around each kernel (not with GRAPH) */
 int trig_batch_run(const trig_slice_dev *slices, uint32_t n_slices, void *scratch, size_t scratch_bytes,
                    void *stream, uint32_t flags);
+
+/* Event extraction: the Event Manager's payload ("DAQ system of NEMO
+ * Phase II": a 6 us window around each trigger seed is stored; "Sorting and
+ * triggering in GPU": all hits within +-3 us of a seed are tagged and sent
+ * back).  For each slice, every hit of the submission (owned range and
+ * halos) inside one of its merged windows, in (t, pmt, charge) order; the
+ * windows are disjoint and time-ordered, so window w's hits start at the
+ * sum of n_hits of the windows before it.  events is device memory of
+ * ev_cap entries (ev_cap 0 skips the slice); stats.n_events gets the count.
+ * When the status is not TRIG_OK the events buffer is not written.
+ * The leading and trailing halos of a slice may hold at most
+ * TRIG_EV_HALO_MAX hits each for extraction (else TRIG_FLAG_EV_FULL). */
+#define TRIG_EV_HALO_MAX 8192u
+typedef struct {
+    trig_hit *events;           /* device, ev_cap entries */
+    uint64_t ev_cap;
+} trig_slice_events;
+
+/* Scratch for trig_batch_run_events (more than trig_batch_scratch_bytes:
+ * the merged stream of each slice with events). */
+size_t trig_batch_events_scratch_bytes(const trig_slice_dev *slices, const trig_slice_events *events,
+                                       uint32_t n_slices);
+
+/* trig_batch_run plus event extraction for the slices whose events entry
+ * has ev_cap > 0.  Same stream, scratch, flags and error rules. */
+int trig_batch_run_events(const trig_slice_dev *slices, const trig_slice_events *events, uint32_t n_slices,
+                          void *scratch, size_t scratch_bytes, void *stream, uint32_t flags);
+
+/* Engine: extract events for det's later submissions (on = 1) or not
+ * (on = 0, the default); results then carry events/n_events. */
+int trig_set_events(trig_detector *det, int on);
 
 /* The same hot path as trig_batch_run for callers that cannot allocate
  * device memory: a trigger node's real-time acquisition thread (cudaMalloc

@@ -13,6 +13,8 @@ Python face of ``oracle.c`` (plain C, compiled with gcc on first use):
   Manager's time-ordered merge ("DAQ system of NEMO Phase II").
 * ``run(det, params, hits, slice_t0s)``  seeds with counts, triggers and
   merged windows per slice ("Sorting and triggering in GPU").
+* ``events(hits, windows)``  the event payload: the hits inside a slice's
+  merged windows, in (t, pmt, charge) order.
 """
 from __future__ import annotations
 
@@ -160,6 +162,21 @@ def run(xyz_mm, floor_id, params: dict, hits: np.ndarray, slice_t0s, threads: in
     finally:
         lib.oracle_free(res, n)
     return out
+
+
+def events(hits: np.ndarray, windows: np.ndarray) -> np.ndarray:
+    """The event payload of a slice ("DAQ system of NEMO Phase II": the
+    window around each trigger seed is stored; "Sorting and triggering in
+    GPU": all hits within +-3 us of a seed are tagged and sent back): every
+    hit with lo <= t <= hi for one of the slice's merged windows, ordered by
+    (t, pmt, charge).  The windows are disjoint and time-ordered, so a hit
+    belongs to the last window whose lo is <= t, if t <= that window's hi."""
+    h = merge(hits)
+    if len(windows) == 0 or len(h) == 0:
+        return h[:0]
+    k = np.searchsorted(windows["lo"], h["t"], side="right") - 1
+    inside = (k >= 0) & (h["t"] <= windows["hi"][np.maximum(k, 0)])
+    return h[inside]
 
 
 def threads_used(threads: int = 0) -> int:

@@ -7,6 +7,7 @@ from ._lib import (  # noqa: F401
     TRIG_OK, TRIG_EINVAL, TRIG_ENOMEM, TRIG_EAGAIN, TRIG_ETIMEOUT, TRIG_EDEVICE, TRIG_ECAPACITY,
     TRIG_RUN_GRAPH, TRIG_RUN_TIMED, load, trig_batch_run, trig_batch_scratch_bytes, trig_create, trig_destroy,
     trig_engine_set_mode, trig_engine_stats, trig_get_tile_config, trig_kernel_launch_count, trig_kernel_times, trig_last_error,
-    trig_autotune, trig_batch_run_noalloc, trig_detector_tile_config,
+    trig_autotune, trig_batch_run_noalloc, trig_detector_tile_config, trig_batch_run_events,
+    trig_batch_events_scratch_bytes, trig_set_events, TRIG_FLAG_EV_FULL,
     trig_poll, trig_set_tile_config, trig_slice_rows, trig_submit_slice, win_cap_for,
 )

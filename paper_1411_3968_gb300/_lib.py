@@ -26,6 +26,8 @@ TRIG_FLAG_TILE_FULL = 0x08
 TRIG_FLAG_TRIG_FULL = 0x10
 TRIG_FLAG_WIN_FULL = 0x20
 TRIG_FLAG_TIMEOUT = 0x40
+TRIG_FLAG_EV_FULL = 0x80
+TRIG_EV_HALO_MAX = 8192
 
 TRIG_RUN_GRAPH = 0x1
 TRIG_RUN_TIMED = 0x2
@@ -34,7 +36,7 @@ HIT_DTYPE = np.dtype([("t", "<i8"), ("pmt", "<u2"), ("charge", "<u2"), ("reserve
 TRIGGER_DTYPE = np.dtype([("t", "<i8"), ("pmt", "<u2"), ("charge", "<u2"), ("count", "<u4")])
 WINDOW_DTYPE = np.dtype([("lo", "<i8"), ("hi", "<i8"), ("n_hits", "<u8"), ("n_triggers", "<u8")])
 STATS_DTYPE = np.dtype([("status", "<i4"), ("flags", "<u4"), ("n_hits", "<u8"), ("n_seeds", "<u8"),
-                        ("n_triggers", "<u8"), ("n_windows", "<u8")])
+                        ("n_triggers", "<u8"), ("n_windows", "<u8"), ("n_events", "<u8")])
 
 # symbols declared in include/trig.h
 EXPORTS = [
@@ -42,7 +44,8 @@ EXPORTS = [
     "trig_poll", "trig_result_free", "trig_engine_set_mode", "trig_engine_stats", "trig_last_error",
     "trig_batch_scratch_bytes", "trig_batch_run", "trig_slice_rows", "trig_set_tile_config",
     "trig_get_tile_config", "trig_kernel_launch_count", "trig_kernel_times", "trig_batch_run_noalloc",
-    "trig_autotune", "trig_detector_tile_config",
+    "trig_autotune", "trig_detector_tile_config", "trig_batch_events_scratch_bytes", "trig_batch_run_events",
+    "trig_set_events",
 ]
 
 NOALLOC_SCRATCH_BYTES = 64 << 20
@@ -70,7 +73,12 @@ class trig_result(ctypes.Structure):
     _fields_ = [("slice_id", ctypes.c_uint64), ("t0_ns", ctypes.c_int64), ("status", ctypes.c_int32),
                 ("flags", ctypes.c_uint32), ("n_hits", ctypes.c_uint64), ("n_seeds", ctypes.c_uint64),
                 ("n_triggers", ctypes.c_uint64), ("n_windows", ctypes.c_uint64), ("triggers", ctypes.c_void_p),
-                ("windows", ctypes.c_void_p), ("latency_ns", ctypes.c_int64)]
+                ("windows", ctypes.c_void_p), ("latency_ns", ctypes.c_int64), ("events", ctypes.c_void_p),
+                ("n_events", ctypes.c_uint64)]
+
+
+class trig_slice_events(ctypes.Structure):
+    _fields_ = [("events", ctypes.c_void_p), ("ev_cap", ctypes.c_uint64)]
 
 
 class trig_tune_result(ctypes.Structure):
@@ -125,6 +133,11 @@ def load(path: str | None = None):
         "trig_batch_run_noalloc": (c.c_int, [c.POINTER(trig_slice_dev), c.c_uint32, c.c_void_p]),
         "trig_kernel_times": (c.c_int, [c.POINTER(c.c_double), c.POINTER(c.c_char_p), c.c_uint32,
                                         c.POINTER(c.c_uint32)]),
+        "trig_batch_events_scratch_bytes": (c.c_size_t, [c.POINTER(trig_slice_dev), c.POINTER(trig_slice_events),
+                                                         c.c_uint32]),
+        "trig_batch_run_events": (c.c_int, [c.POINTER(trig_slice_dev), c.POINTER(trig_slice_events), c.c_uint32,
+                                            c.c_void_p, c.c_size_t, c.c_void_p, c.c_uint32]),
+        "trig_set_events": (c.c_int, [c.c_void_p, c.c_int]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -215,6 +228,8 @@ class Result:
         self.latency_ns = int(r.latency_ns)
         self.triggers = _copy(r.triggers, r.n_triggers, TRIGGER_DTYPE)
         self.windows = _copy(r.windows, r.n_windows, WINDOW_DTYPE)
+        self.n_events = int(r.n_events)
+        self.events = _copy(r.events, r.n_events if r.events else 0, HIT_DTYPE)
 
 
 def _copy(ptr, n, dtype):
@@ -236,6 +251,11 @@ def trig_poll(det: Detector, timeout_ms: int = -1) -> Result | None:
         return Result(out.contents)
     finally:
         lib.trig_result_free(out)
+
+
+def trig_set_events(det: "Detector", on: bool = True) -> None:
+    """Engine results of det's later submissions carry the event payload."""
+    _check(load().trig_set_events(det.handle, 1 if on else 0))
 
 
 def trig_engine_set_mode(mode: int) -> None:
@@ -313,6 +333,23 @@ def trig_batch_scratch_bytes(slices) -> int:
 def trig_batch_run(slices, scratch_ptr: int, scratch_bytes: int, stream_ptr: int = 0, flags: int = 0) -> None:
     arr = _array(slices)
     _check(load().trig_batch_run(arr, len(slices), scratch_ptr, scratch_bytes, stream_ptr or None, flags))
+
+
+def _events_array(events):
+    return (trig_slice_events * len(events))(*events)
+
+
+def trig_batch_events_scratch_bytes(slices, events) -> int:
+    n = load().trig_batch_events_scratch_bytes(_array(slices), _events_array(events), len(slices))
+    if n == 0:
+        raise TrigError(TRIG_EINVAL, trig_last_error())
+    return int(n)
+
+
+def trig_batch_run_events(slices, events, scratch_ptr: int, scratch_bytes: int, stream_ptr: int = 0,
+                          flags: int = 0) -> None:
+    _check(load().trig_batch_run_events(_array(slices), _events_array(events), len(slices), scratch_ptr,
+                                        scratch_bytes, stream_ptr or None, flags))
 
 
 def trig_batch_run_noalloc(slices, stream_ptr: int = 0) -> None:

@@ -111,6 +111,7 @@ struct trig_detector {
     std::shared_ptr<DetQueue> q;
     bool tuned = false;           // tile shape chosen by trig_autotune (or its cache)
     TileConfig tile{};
+    bool events = false;          // engine results carry the event payload
 };
 
 static void free_det_dev(trig_detector *d)
@@ -207,6 +208,13 @@ extern "C" int trig_create(const trig_geometry *g, const trig_params *params, tr
 
 extern "C" int64_t trig_detector_halo_ns(const trig_detector *d) { return d ? d->in_halo : -1; }
 
+extern "C" int trig_set_events(trig_detector *det, int on)
+{
+    if (!det) return fail(TRIG_EINVAL, "NULL detector");
+    det->events = on != 0;
+    return TRIG_OK;
+}
+
 extern "C" int trig_detector_dtmax(const trig_detector *d, int32_t *dt_out)
 {
     if (!d || !dt_out) return fail(TRIG_EINVAL, "NULL argument");
@@ -226,6 +234,7 @@ struct Plan {
     uint32_t max_pmt = 0;
     bool smem_dt = true;
     bool any_wide = false;
+    bool any_events = false;
     TileConfig shape{};         // launch shape of this batch
 };
 
@@ -302,8 +311,10 @@ static TileConfig batch_shape(const trig_slice_dev *sl, uint32_t n, const TileCo
 
 static int plan_into(const trig_slice_dev *sl, uint32_t n, uintptr_t base, const TileConfig &cfg_in,
                      BatchHeader &hdr, SliceDesc *desc, size_t &bytes, uint32_t &max_pmt, bool &smem_dt,
-                     bool &any_wide, TileConfig *shape_out = nullptr)
+                     bool &any_wide, TileConfig *shape_out = nullptr, const trig_slice_events *ev = nullptr,
+                     bool *any_events_out = nullptr)
 {
+    bool any_events = false;
     if (!sl || n == 0) return fail(TRIG_EINVAL, "no slices");
     const TileConfig cfg = batch_shape(sl, n, cfg_in);
     if (shape_out) *shape_out = cfg;
@@ -409,10 +420,29 @@ static int plan_into(const trig_slice_dev *sl, uint32_t n, uintptr_t base, const
         d.dbg_merged = nullptr;
         d.dbg_seedcnt = nullptr;
         d.dbg_rank0 = 0;
+        d.ev = nullptr;
+        d.ev_cap = 0;
+        if (ev && ev[s].ev_cap > 0) {
+            // event extraction: the tile pass writes the merged stream (row
+            // outputs from merged rank 0, no seed counts)
+            if (!ev[s].events || ((uintptr_t)ev[s].events & 15u)) return fail(TRIG_EINVAL, "events must be 16-byte aligned device memory");
+            if (x.n_hits > 0xFFFFFFFFull) return fail(TRIG_EINVAL, "event extraction takes slices below 2^32 hits");
+            any_events = true;
+            d.ev = ev[s].events;
+            d.ev_cap = ev[s].ev_cap;
+            d.dbg_merged = reinterpret_cast<trig_hit *>(base + off);
+            off += align256((size_t)x.n_hits * sizeof(trig_hit));
+            d.win_rlo = reinterpret_cast<uint32_t *>(base + off);
+            off += align256((size_t)x.win_cap * 4);
+            d.ev_off = reinterpret_cast<uint32_t *>(base + off);
+            off += align256(((size_t)x.win_cap + 1) * 4);
+        }
     }
+    if (any_events_out) *any_events_out = any_events;
     hdr = BatchHeader{};
     hdr.n_slices = n;
     hdr.any_wide = any_wide ? 1u : 0u;
+    hdr.any_events = any_events ? 1u : 0u;
     hdr.n_items = items;
     hdr.n_chunks = chunks;
     bytes = off;
@@ -420,19 +450,27 @@ static int plan_into(const trig_slice_dev *sl, uint32_t n, uintptr_t base, const
 }
 
 static int make_plan(const trig_slice_dev *sl, uint32_t n, uintptr_t base, const TileConfig &cfg, Plan &pl,
-                     bool rows)
+                     bool rows, const trig_slice_events *ev = nullptr)
 {
     (void)rows;
     if (!sl || n == 0) return fail(TRIG_EINVAL, "no slices");
     pl.desc.assign(n, SliceDesc{});
     return plan_into(sl, n, base, cfg, pl.hdr, pl.desc.data(), pl.bytes, pl.max_pmt, pl.smem_dt, pl.any_wide,
-                     &pl.shape);
+                     &pl.shape, ev, &pl.any_events);
 }
 
 extern "C" size_t trig_batch_scratch_bytes(const trig_slice_dev *slices, uint32_t n_slices)
 {
     Plan pl;
     if (make_plan(slices, n_slices, 0, current_cfg(), pl, false)) return 0;
+    return pl.bytes;
+}
+
+extern "C" size_t trig_batch_events_scratch_bytes(const trig_slice_dev *slices, const trig_slice_events *events,
+                                                  uint32_t n_slices)
+{
+    Plan pl;
+    if (make_plan(slices, n_slices, 0, current_cfg(), pl, false, events)) return 0;
     return pl.bytes;
 }
 
@@ -540,7 +578,8 @@ static int run_graph(const Plan &pl, void *scratch, cudaStream_t st)
         if (!ce)
             ce = launch_batch(reinterpret_cast<BatchHeader *>(scratch),
                               reinterpret_cast<SliceDesc *>((char *)scratch + align256(sizeof(BatchHeader))),
-                              pl.hdr.n_slices, pl.max_pmt, pl.smem_dt, pl.any_wide, cfg, cap, &nl, false);
+                              pl.hdr.n_slices, pl.max_pmt, pl.smem_dt, pl.any_wide, pl.any_events, cfg, cap, &nl,
+                              false);
         ge.launches = nl;
         e = cudaStreamEndCapture(cap, &graph);
         cudaStreamDestroy(cap);
@@ -636,7 +675,8 @@ static int run_plan(const Plan &pl, void *scratch, size_t scratch_bytes, cudaStr
     uint64_t nl = 0;
     e = launch_batch(reinterpret_cast<BatchHeader *>(scratch),
                      reinterpret_cast<SliceDesc *>((char *)scratch + align256(sizeof(BatchHeader))), pl.hdr.n_slices,
-                     pl.max_pmt, pl.smem_dt, pl.any_wide, cfg, st, &nl, rows, timed ? tr.ev : nullptr);
+                     pl.max_pmt, pl.smem_dt, pl.any_wide, pl.any_events, cfg, st, &nl, rows,
+                     timed ? tr.ev : nullptr);
     g_launches += nl;
     if (timed) {
         std::lock_guard<std::mutex> lk(g_time_mu);
@@ -644,6 +684,18 @@ static int run_plan(const Plan &pl, void *scratch, size_t scratch_bytes, cudaStr
     }
     if (e) return cuda_fail(e, "launch");
     return TRIG_OK;
+}
+
+extern "C" int trig_batch_run_events(const trig_slice_dev *slices, const trig_slice_events *events,
+                                     uint32_t n_slices, void *scratch, size_t scratch_bytes, void *stream,
+                                     uint32_t flags)
+{
+    if (!events) return fail(TRIG_EINVAL, "events is NULL");
+    const TileConfig cfg = current_cfg();
+    Plan pl;
+    int rc = make_plan(slices, n_slices, (uintptr_t)scratch, cfg, pl, false, events);
+    if (rc) return rc;
+    return run_plan(pl, scratch, scratch_bytes, (cudaStream_t)stream, flags, false);
 }
 
 extern "C" int trig_batch_run(const trig_slice_dev *slices, uint32_t n_slices, void *scratch, size_t scratch_bytes,
@@ -853,7 +905,7 @@ extern "C" int trig_batch_run_noalloc(const trig_slice_dev *slices, uint32_t n_s
     uint64_t nl = 0;
     e = launch_batch(reinterpret_cast<BatchHeader *>(scratch),
                      reinterpret_cast<SliceDesc *>((char *)scratch + align256(sizeof(BatchHeader))), n_slices,
-                     max_pmt, smem_dt, any_wide, shape, st, &nl, false);
+                     max_pmt, smem_dt, any_wide, false, shape, st, &nl, false);
     g_launches += nl;
     if (e) return cuda_fail(e, "trig_batch_run_noalloc: launch");
     return TRIG_OK;
@@ -949,6 +1001,9 @@ struct Slot {
     std::vector<trig_slice_dev> dev;
     std::vector<uint64_t> trig_n, win_n;
     std::vector<size_t> win_off;                    // per slice offset of its windows in bounce
+    std::vector<size_t> ev_off;                     // per slice offset of its events in bounce
+    std::vector<trig_slice_events> evs;             // per slice event output (ev_cap 0: none)
+    std::vector<uint64_t> ev_n;
     bool lost = false;                              // bounce could not grow: outputs dropped
 };
 
@@ -1035,7 +1090,7 @@ uint64_t win_cap_for(const trig_detector *det)
 // Device footprint of a batch in one arena: inputs, outputs, stats, scratch.
 struct ArenaLayout {
     size_t bytes = 0;
-    std::vector<size_t> hits, offs, trig, win, stats;
+    std::vector<size_t> hits, offs, trig, win, stats, ev;
     size_t scratch = 0, scratch_bytes = 0;
 };
 
@@ -1073,9 +1128,21 @@ bool Engine::launch_batch_on(Slot &s, std::vector<Pending> &batch)
         off += align256(dev[i].win_cap * sizeof(trig_window));
         L.stats.push_back(off);
         off += align256(sizeof(trig_slice_stats));
+        L.ev.push_back(off);
+        if (p.det->events) off += align256(std::max<uint64_t>(p.n_hits, 1) * sizeof(trig_hit));
+    }
+    // event outputs (placeholders for sizing; the real pointers are set below)
+    std::vector<trig_slice_events> evs(n);
+    bool any_ev = false;
+    for (uint32_t i = 0; i < n; ++i) {
+        if (!batch[i].det->events) continue;
+        any_ev = true;
+        evs[i].events = reinterpret_cast<trig_hit *>(256);
+        evs[i].ev_cap = std::max<uint64_t>(batch[i].n_hits, 1);
     }
     L.scratch = off;
-    L.scratch_bytes = trig_batch_scratch_bytes(dev.data(), n);
+    L.scratch_bytes = any_ev ? trig_batch_events_scratch_bytes(dev.data(), evs.data(), n)
+                             : trig_batch_scratch_bytes(dev.data(), n);
     if (!L.scratch_bytes) {
         fatal = g_last_error;
         return false;
@@ -1113,6 +1180,7 @@ bool Engine::launch_batch_on(Slot &s, std::vector<Pending> &batch)
         dev[i].triggers = reinterpret_cast<trig_trigger *>(A + L.trig[i]);
         dev[i].windows = reinterpret_cast<trig_window *>(A + L.win[i]);
         dev[i].stats = reinterpret_cast<trig_slice_stats *>(A + L.stats[i]);
+        if (evs[i].ev_cap) evs[i].events = reinterpret_cast<trig_hit *>(A + L.ev[i]);
     }
     // the pinned bounce buffer takes the per-slice counters now, and the
     // triggers and windows (by their actual counts) once those are known
@@ -1149,7 +1217,8 @@ bool Engine::launch_batch_on(Slot &s, std::vector<Pending> &batch)
     }
     // batches of the engine vary in size and composition from one launch
     // to the next, so they are launched directly rather than from graphs
-    int rc = trig_batch_run(dev.data(), n, A + L.scratch, L.scratch_bytes, s.stream, 0);
+    int rc = any_ev ? trig_batch_run_events(dev.data(), evs.data(), n, A + L.scratch, L.scratch_bytes, s.stream, 0)
+                    : trig_batch_run(dev.data(), n, A + L.scratch, L.scratch_bytes, s.stream, 0);
     if (rc) {
         fatal = g_last_error;
         return false;
@@ -1165,6 +1234,7 @@ bool Engine::launch_batch_on(Slot &s, std::vector<Pending> &batch)
     }
     s.slices = std::move(batch);
     s.dev = std::move(dev);
+    s.evs = std::move(evs);
     s.state = 1;
     s.trig_n.assign(n, 0);
     s.win_n.assign(n, 0);
@@ -1197,7 +1267,8 @@ void Engine::collect_stats(Slot &s)
     // output bytes by the actual counts; the bounce buffer holds the
     // counters first, then each slice's triggers and windows
     size_t need = align256(n * sizeof(trig_slice_stats));
-    std::vector<size_t> toff(n), woff(n);
+    std::vector<size_t> toff(n), woff(n), eoff(n);
+    s.ev_n.assign(n, 0);
     for (uint32_t i = 0; i < n; ++i) {
         s.trig_n[i] = std::min<uint64_t>(st[i].n_triggers, s.dev[i].trig_cap);
         s.win_n[i] = std::min<uint64_t>(st[i].n_windows, s.dev[i].win_cap);
@@ -1205,6 +1276,10 @@ void Engine::collect_stats(Slot &s)
         need += align256(s.trig_n[i] * sizeof(trig_trigger));
         woff[i] = need;
         need += align256(s.win_n[i] * sizeof(trig_window));
+        if (s.evs[i].ev_cap && !(st[i].flags & TRIG_FLAG_EV_FULL))
+            s.ev_n[i] = std::min<uint64_t>(st[i].n_events, s.evs[i].ev_cap);
+        eoff[i] = need;
+        need += align256(s.ev_n[i] * sizeof(trig_hit));
     }
     if (s.bounce_bytes < need) {
         // grow (geometrically) keeping the counters already read
@@ -1212,7 +1287,7 @@ void Engine::collect_stats(Slot &s)
         void *p = nullptr;
         if (cudaMallocHost(&p, want) != cudaSuccess) {
             (void)cudaGetLastError();
-            for (uint32_t i = 0; i < n; ++i) s.trig_n[i] = s.win_n[i] = 0;
+            for (uint32_t i = 0; i < n; ++i) s.trig_n[i] = s.win_n[i] = s.ev_n[i] = 0;
             s.lost = true;
             s.state = 2;
             cudaEventRecord(s.ev_done, s.stream);
@@ -1225,6 +1300,7 @@ void Engine::collect_stats(Slot &s)
     }
     s.out_off.assign(toff.begin(), toff.end());
     s.win_off.assign(woff.begin(), woff.end());
+    s.ev_off.assign(eoff.begin(), eoff.end());
     cudaError_t e = cudaSuccess;
     for (uint32_t i = 0; i < n && !e; ++i) {
         if (s.trig_n[i])
@@ -1232,6 +1308,9 @@ void Engine::collect_stats(Slot &s)
                                 cudaMemcpyDeviceToHost, s.stream);
         if (!e && s.win_n[i])
             e = cudaMemcpyAsync(s.bounce + woff[i], s.dev[i].windows, s.win_n[i] * sizeof(trig_window),
+                                cudaMemcpyDeviceToHost, s.stream);
+        if (!e && s.ev_n[i])
+            e = cudaMemcpyAsync(s.bounce + eoff[i], s.evs[i].events, s.ev_n[i] * sizeof(trig_hit),
                                 cudaMemcpyDeviceToHost, s.stream);
     }
     if (!e) e = cudaEventRecord(s.ev_done, s.stream);
@@ -1266,7 +1345,15 @@ void Engine::finish(Slot &s)
                 r->windows = static_cast<trig_window *>(std::malloc(r->n_windows * sizeof(trig_window)));
                 if (r->windows) std::memcpy(r->windows, s.bounce + s.win_off[i], r->n_windows * sizeof(trig_window));
             }
-            if ((r->n_triggers && !r->triggers) || (r->n_windows && !r->windows)) r->status = TRIG_ENOMEM;
+            if (s.evs[i].ev_cap) {
+                r->n_events = s.lost ? 0 : st[i].n_events;
+                if (s.ev_n[i]) {
+                    r->events = static_cast<trig_hit *>(std::malloc(s.ev_n[i] * sizeof(trig_hit)));
+                    if (r->events) std::memcpy(r->events, s.bounce + s.ev_off[i], s.ev_n[i] * sizeof(trig_hit));
+                }
+            }
+            if ((r->n_triggers && !r->triggers) || (r->n_windows && !r->windows) || (s.ev_n[i] && !r->events))
+                r->status = TRIG_ENOMEM;
             r->latency_ns = std::chrono::duration_cast<std::chrono::nanoseconds>(now - p.t_submit).count();
         }
         pool.put(p.pinned, p.pinned_bytes);
@@ -1462,6 +1549,7 @@ extern "C" void trig_result_free(trig_result *r)
     if (!r) return;
     std::free(r->triggers);
     std::free(r->windows);
+    std::free(r->events);
     std::free(r);
 }
 

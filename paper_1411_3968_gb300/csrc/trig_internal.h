@@ -82,7 +82,14 @@ struct SliceDesc {
     trig_window *windows;
     uint64_t win_cap;
     trig_slice_stats *stats;
-    trig_hit *dbg_merged;   // optional row outputs, indexed by merged rank - rank(t0)
+    // event extraction (ev != nullptr): the slice's hits in merged order,
+    // each window's first merged rank and its offset in the event output
+    trig_hit *ev;
+    uint64_t ev_cap;
+    uint32_t *win_rlo;      // [win_cap]
+    uint32_t *ev_off;       // [win_cap + 1]
+    trig_hit *dbg_merged;   // merged rows, indexed by merged rank - dbg_rank0 (row outputs,
+                            // or the slice's merged stream for event extraction)
     uint32_t *dbg_seedcnt;
     uint64_t dbg_rank0;     // merged rank of the first owned hit (row outputs only)
     uint64_t dbg_rank1;     // merged rank of the first hit after the owned range
@@ -95,7 +102,8 @@ struct BatchHeader {
     uint32_t err;
     uint32_t queue;         // tile work queue head
     uint32_t any_wide;      // a slice of the batch is wide
-    uint32_t pad[2];
+    uint32_t any_events;    // a slice of the batch extracts events
+    uint32_t pad;
 };
 
 constexpr uint32_t kChunkHits = 4096;       // structure-pass chunk
@@ -121,17 +129,18 @@ inline bool valid_tile_shape(uint32_t cap, uint32_t warps)
 constexpr uint32_t kMaxTilesPerSlice = 1u << 20;
 
 // Enqueues the batch pipeline; header/desc already copied to device scratch.
-constexpr int kPipelineKernels = 12;
+constexpr int kPipelineKernels = 15;
 extern const char *const kKernelNames[kPipelineKernels];
 
 // any_wide: the batch holds a wide slice (the bucket sums, scan and
-// scatter kernels run only then).  ev (optional, kPipelineKernels + 1 events): ev[i]
+// scatter kernels run only then); any_events: a slice extracts events (the
+// halo, event-offset and event-copy kernels run only then).  ev (optional, kPipelineKernels + 1 events): ev[i]
 // is recorded before pipeline kernel i and ev[kPipelineKernels] after the
 // last one (a kernel that does not run gets an empty interval).
 // *launches is increased by the number of kernels launched.
 cudaError_t launch_batch(BatchHeader *d_hdr, SliceDesc *d_desc, uint32_t n_slices, uint32_t max_pmt,
-                         bool any_smem_dt, bool any_wide, const TileConfig &cfg, cudaStream_t st, uint64_t *launches,
-                         bool rows, cudaEvent_t *ev = nullptr);
+                         bool any_smem_dt, bool any_wide, bool any_events, const TileConfig &cfg, cudaStream_t st,
+                         uint64_t *launches, bool rows, cudaEvent_t *ev = nullptr);
 
 int device_sm_count();
 

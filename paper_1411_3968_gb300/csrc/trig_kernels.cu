@@ -290,6 +290,7 @@ __global__ void k_prep(BatchHeader *hdr, const SliceDesc *desc)
         st->n_seeds = 0;
         st->n_triggers = 0;
         st->n_windows = 0;
+        st->n_events = 0;
     }
     // bucket counts of the wide slices start at zero
     for (uint32_t s = 0; hdr->any_wide && s < n; ++s) {
@@ -984,7 +985,9 @@ __device__ CoreOut tile_trigger(TileCtx &cx, const uint64_t *keys, uint32_t n, u
         }
     }
     const uint32_t n_fired = ftot[NW];
-    // 5. optional row outputs (verification)
+    // 5. optional row outputs: the merged core rows (verification, and the
+    //    merged stream of event extraction) and each row's causal count
+    //    (verification only)
     if (tp.dbg_merged) {
         // rows are indexed by merged rank minus the rank of the slice's first owned hit
         const uint64_t dbg_base = (uint64_t)(dbg_rank_lo + (int64_t)c0);
@@ -996,10 +999,12 @@ __device__ CoreOut tile_trigger(TileCtx &cx, const uint64_t *keys, uint32_t n, u
             h.charge = (uint16_t)key_q(k);
             h.reserved = 0;
             tp.dbg_merged[dbg_base + i] = h;
-            tp.dbg_seedcnt[dbg_base + i] = 0xffffffffu;
+            if (tp.dbg_seedcnt) tp.dbg_seedcnt[dbg_base + i] = 0xffffffffu;
         }
-        cons_sync<NC>();
-        for (uint32_t k = tid; k < ns; k += NC) tp.dbg_seedcnt[dbg_base + (seed_idx[k] - c0)] = seed_cnt[k];
+        if (tp.dbg_seedcnt) {
+            cons_sync<NC>();
+            for (uint32_t k = tid; k < ns; k += NC) tp.dbg_seedcnt[dbg_base + (seed_idx[k] - c0)] = seed_cnt[k];
+        }
     }
     cons_sync<NC>();
     CoreOut r;
@@ -1616,34 +1621,200 @@ __global__ void __launch_bounds__(256) k_whits(const BatchHeader *__restrict__ h
             if (!CHECK(9, i, d.win_cap)) continue;
             const trig_window win = d.windows[i];
             uint64_t cnt = 0;
+            uint64_t below = 0;     // hits before lo: the window's first merged rank
             if (d.wide) {
                 // whole buckets between the edge buckets, plus the edge
                 // buckets' hits inside [lo, hi]
                 const uint32_t bl = bkt_index(d, win.lo_ns), bh = bkt_index(d, win.hi_ns);
                 if (bl + 1 < bh && lane == 0) cnt = d.bkt_off[bh] - d.bkt_off[bl + 1];
                 const uint32_t e0 = d.bkt_off[bl], e1 = d.bkt_off[bl + 1];
+                if (lane == 0) below = e0;
                 for (uint32_t j = e0 + lane; j < e1; j += 32) {
                     const int64_t t = d.tbuf[j].t_ns;
                     cnt += t >= win.lo_ns && t <= win.hi_ns;
+                    below += t < win.lo_ns;
                 }
                 if (bh != bl) {
                     const uint32_t f0 = d.bkt_off[bh], f1 = d.bkt_off[bh + 1];
                     for (uint32_t j = f0 + lane; j < f1; j += 32) cnt += d.tbuf[j].t_ns <= win.hi_ns;
                 }
             } else {
-                for (uint32_t p = lane; p < d.n_pmt; p += 32) {
-                    const uint64_t sp = d.pmt_off[p], ep = d.pmt_off[p + 1];
-                    cnt += rank_in_pmt(d, p, win.hi_ns + 1, sp, ep) - rank_in_pmt(d, p, win.lo_ns, sp, ep);
+                if (d.ev) {
+                    for (uint32_t p = lane; p < d.n_pmt; p += 32) {
+                        const uint64_t sp = d.pmt_off[p], ep = d.pmt_off[p + 1];
+                        const uint64_t a = rank_in_pmt(d, p, win.lo_ns, sp, ep);
+                        cnt += rank_in_pmt(d, p, win.hi_ns + 1, sp, ep) - a;
+                        below += a - sp;
+                    }
+                } else {
+                    for (uint32_t p = lane; p < d.n_pmt; p += 32) {
+                        const uint64_t sp = d.pmt_off[p], ep = d.pmt_off[p + 1];
+                        cnt += rank_in_pmt(d, p, win.hi_ns + 1, sp, ep) - rank_in_pmt(d, p, win.lo_ns, sp, ep);
+                    }
                 }
             }
             cnt = warp_sum_u64(cnt);
+            if (d.ev) below = warp_sum_u64(below);
             __syncwarp();
             if (lane == 0) {
                 d.windows[i].n_triggers = win.n_hits - win.n_triggers + 1;
                 d.windows[i].n_hits = cnt;
+                if (d.ev) d.win_rlo[i] = (uint32_t)below;
             }
         }
         __syncthreads();
+    }
+}
+
+// ----------------------------------------------------- event extraction
+
+// The slice's leading halo (t < t0) and trailing halo (t >= t0 + S) in
+// merged order at the two ends of its merged stream (the tile pass writes
+// the owned hits between them, at their merged ranks).  One block per
+// slice; each halo is gathered into shared memory as keys relative to its
+// start and ranked by counting.  More than TRIG_EV_HALO_MAX hits in a halo
+// sets TRIG_FLAG_EV_FULL.
+constexpr uint32_t kEvHaloThreads = 1024;
+
+__device__ void ev_halo_side(const SliceDesc &d, bool lead, uint64_t *keys, uint32_t *psum, int64_t base, int64_t t_cut)
+{
+    const uint32_t tid = threadIdx.x, P = d.n_pmt;
+    const trig_hit *hits = d.hits;
+    const uint64_t *poff = d.pmt_off;
+    // per-PMT counts of the halo hits (each thread a contiguous run of PMTs)
+    const uint32_t per = (P + kEvHaloThreads - 1) / kEvHaloThreads;
+    const uint32_t p0 = min(P, tid * per), p1 = min(P, p0 + per);
+    uint32_t local = 0;
+    for (uint32_t p = p0; p < p1; ++p) {
+        const uint64_t a = lb_time(hits, poff[p], poff[p + 1], t_cut);
+        local += (uint32_t)(lead ? a - poff[p] : poff[p + 1] - a);
+    }
+    // exclusive block scan of the per-thread counts
+    psum[tid] = local;
+    __syncthreads();
+    for (uint32_t off = 1; off < kEvHaloThreads; off <<= 1) {
+        const uint32_t v = tid >= off ? psum[tid - off] : 0u;
+        __syncthreads();
+        psum[tid] += v;
+        __syncthreads();
+    }
+    const uint32_t total = psum[kEvHaloThreads - 1];
+    uint32_t at = psum[tid] - local;
+    __syncthreads();
+    if (total > TRIG_EV_HALO_MAX) {
+        if (tid == 0) report(d, TRIG_FLAG_EV_FULL);
+        return;
+    }
+    for (uint32_t p = p0; p < p1; ++p) {
+        const uint64_t a = lb_time(hits, poff[p], poff[p + 1], t_cut);
+        const uint64_t b = lead ? poff[p] : a, e = lead ? a : poff[p + 1];
+        for (uint64_t j = b; j < e; ++j, ++at) {
+            const trig_hit h = load_hit(hits + j);
+            keys[at] = ((uint64_t)(uint32_t)(h.t_ns - base) << 32) | ((uint64_t)h.pmt << 16) | h.charge;
+        }
+    }
+    __syncthreads();
+    const uint64_t dst0 = lead ? 0 : d.n_hits - total;
+    for (uint32_t i = tid; i < total; i += kEvHaloThreads) {
+        const uint64_t k = keys[i];
+        uint32_t r = 0;
+        for (uint32_t j = 0; j < total; ++j) {
+            const uint64_t o = keys[j];
+            r += (o < k) || (o == k && j < i);
+        }
+        trig_hit h;
+        h.t_ns = base + (int64_t)(k >> 32);
+        h.pmt = (uint16_t)(k >> 16);
+        h.charge = (uint16_t)k;
+        h.reserved = 0;
+        d.dbg_merged[dst0 + r] = h;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kEvHaloThreads) k_evhalo(const BatchHeader *__restrict__ hdr,
+                                                           const SliceDesc *__restrict__ desc)
+{
+    extern __shared__ __align__(16) unsigned char ev_smem[];
+    uint64_t *keys = reinterpret_cast<uint64_t *>(ev_smem);
+    uint32_t *psum = reinterpret_cast<uint32_t *>(keys + TRIG_EV_HALO_MAX);
+    for (uint32_t s = blockIdx.x; s < hdr->n_slices; s += gridDim.x) {
+        const SliceDesc &d = desc[s];
+        if (!d.ev || d.ev_cap == 0) continue;
+        if (d.stats->flags & (TRIG_FLAG_BAD_PMT | TRIG_FLAG_UNSORTED | TRIG_FLAG_OUT_OF_RANGE)) continue;
+        ev_halo_side(d, true, keys, psum, d.in_lo, d.t0);
+        ev_halo_side(d, false, keys, psum, d.t0 + d.slice_ns, d.t0 + d.slice_ns);
+    }
+}
+
+// Offsets of the windows in the event output: exclusive prefix of their hit
+// counts (one block per slice); the total is n_events.
+__global__ void __launch_bounds__(1024) k_escan(const BatchHeader *__restrict__ hdr, const SliceDesc *__restrict__ desc)
+{
+    __shared__ uint32_t wsum[33];
+    const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5, nwp = blockDim.x >> 5;
+    for (uint32_t s = blockIdx.x; s < hdr->n_slices; s += gridDim.x) {
+        const SliceDesc &d = desc[s];
+        if (!d.ev || d.ev_cap == 0) continue;
+        if (d.stats->flags & (TRIG_FLAG_BAD_PMT | TRIG_FLAG_UNSORTED | TRIG_FLAG_OUT_OF_RANGE | TRIG_FLAG_TRIG_FULL |
+                              TRIG_FLAG_WIN_FULL)) {
+            if (tid == 0) d.stats->n_events = 0;
+            continue;
+        }
+        const uint32_t nw = (uint32_t)min((unsigned long long)d.stats->n_windows, (unsigned long long)d.win_cap);
+        uint32_t carry = 0;
+        for (uint32_t base = 0; base < nw; base += blockDim.x) {
+            const uint32_t i = base + tid;
+            const uint32_t v = i < nw ? (uint32_t)d.windows[i].n_hits : 0u;
+            const uint32_t incl = warp_incl_scan(v);
+            if (lane == 31) wsum[warp] = incl;
+            __syncthreads();
+            if (warp == 0) {
+                const uint32_t w = lane < nwp ? wsum[lane] : 0u;
+                const uint32_t wi = warp_incl_scan(w);
+                if (lane < nwp) wsum[lane] = wi - w;
+                if (lane == nwp - 1) wsum[32] = wi;
+            }
+            __syncthreads();
+            if (i < nw) d.ev_off[i] = carry + wsum[warp] + incl - v;
+            carry += wsum[32];
+            __syncthreads();
+        }
+        if (tid == 0) {
+            d.ev_off[nw] = carry;
+            d.stats->n_events = carry;
+            if (carry > d.ev_cap) atomicOr(&d.stats->flags, TRIG_FLAG_EV_FULL);
+        }
+        __syncthreads();
+    }
+}
+
+// The event output: event e of window w is merged hit win_rlo[w] + e -
+// ev_off[w].  Slices with any capacity flag (including a skipped 1 ns tile
+// piece, whose rows the merged stream lacks) copy nothing.
+__global__ void __launch_bounds__(256) k_events(const BatchHeader *__restrict__ hdr, const SliceDesc *__restrict__ desc)
+{
+    const uint64_t gt = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
+    for (uint32_t s = 0; s < hdr->n_slices; ++s) {
+        const SliceDesc &d = desc[s];
+        if (!d.ev || d.ev_cap == 0) continue;
+        if (d.stats->flags & (TRIG_FLAG_BAD_PMT | TRIG_FLAG_UNSORTED | TRIG_FLAG_OUT_OF_RANGE | TRIG_FLAG_TRIG_FULL |
+                              TRIG_FLAG_WIN_FULL | TRIG_FLAG_EV_FULL | TRIG_FLAG_TILE_FULL))
+            continue;
+        const uint32_t nw = (uint32_t)min((unsigned long long)d.stats->n_windows, (unsigned long long)d.win_cap);
+        const uint64_t ne = d.stats->n_events;
+        for (uint64_t e = gt; e < ne; e += nt) {
+            // window of event e: last w with ev_off[w] <= e
+            uint32_t lo = 0, hi = nw;
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (d.ev_off[mid] <= e) lo = mid; else hi = mid;
+            }
+            const uint64_t src = (uint64_t)d.win_rlo[lo] + (e - d.ev_off[lo]);
+            if (CHECK(18, src, d.n_hits) && CHECK(19, e, d.ev_cap))
+                *reinterpret_cast<int4 *>(d.ev + e) = *reinterpret_cast<const int4 *>(d.dbg_merged + src);
+        }
     }
 }
 
@@ -1691,7 +1862,8 @@ __global__ void k_status(const BatchHeader *__restrict__ hdr, const SliceDesc *_
         int32_t status = TRIG_OK;
         if (f & (TRIG_FLAG_BAD_PMT | TRIG_FLAG_UNSORTED | TRIG_FLAG_OUT_OF_RANGE)) status = TRIG_EINVAL;
         else if (f & TRIG_FLAG_TIMEOUT) status = TRIG_ETIMEOUT;
-        else if (f & (TRIG_FLAG_TILE_FULL | TRIG_FLAG_TRIG_FULL | TRIG_FLAG_WIN_FULL)) status = TRIG_ECAPACITY;
+        else if (f & (TRIG_FLAG_TILE_FULL | TRIG_FLAG_TRIG_FULL | TRIG_FLAG_WIN_FULL | TRIG_FLAG_EV_FULL))
+            status = TRIG_ECAPACITY;
         st->status = status;
     }
 }
@@ -1790,13 +1962,13 @@ static cudaError_t launch_tile(BatchHeader *hdr, SliceDesc *desc, uint32_t max_p
     return cudaGetLastError();
 }
 
-const char *const kKernelNames[kPipelineKernels] = {"k_prep",  "k_bounds", "k_bsum",   "k_bscan",
-                                                     "k_scatter", "k_tile", "k_scan",   "k_copy",
-                                                     "k_wscan", "k_wwrite", "k_whits",  "k_status"};
+const char *const kKernelNames[kPipelineKernels] = {"k_prep",   "k_bounds", "k_bsum",  "k_bscan",  "k_scatter",
+                                                     "k_tile",   "k_evhalo", "k_scan",  "k_copy",   "k_wscan",
+                                                     "k_wwrite", "k_whits",  "k_escan", "k_events", "k_status"};
 
 cudaError_t launch_batch(BatchHeader *d_hdr, SliceDesc *d_desc, uint32_t n_slices, uint32_t max_pmt,
-                         bool any_smem_dt, bool any_wide, const TileConfig &cfg, cudaStream_t st, uint64_t *launches,
-                         bool rows, cudaEvent_t *ev)
+                         bool any_smem_dt, bool any_wide, bool any_events, const TileConfig &cfg, cudaStream_t st,
+                         uint64_t *launches, bool rows, cudaEvent_t *ev)
 {
     const int sms = device_sm_count();
     auto mark = [&](int i) {
@@ -1845,18 +2017,40 @@ cudaError_t launch_batch(BatchHeader *d_hdr, SliceDesc *d_desc, uint32_t n_slice
                     : launch_tile<4096, 512, false>(d_hdr, d_desc, max_pmt, st);
     if (e != cudaSuccess) return e;
     mark(6);
-    k_scan<<<sb, 1024, 0, st>>>(d_hdr, d_desc);
+    if (any_events) {
+        static bool ev_limit_set[64] = {};
+        int dev = 0;
+        if ((e = cudaGetDevice(&dev))) return e;
+        const int ev_smem = (int)(TRIG_EV_HALO_MAX * 8 + kEvHaloThreads * 4);
+        if (dev >= 0 && dev < 64 && !ev_limit_set[dev]) {
+            if ((e = cudaFuncSetAttribute(k_evhalo, cudaFuncAttributeMaxDynamicSharedMemorySize, ev_smem))) return e;
+            ev_limit_set[dev] = true;
+        }
+        k_evhalo<<<sb, kEvHaloThreads, ev_smem, st>>>(d_hdr, d_desc);
+        nl += 1;
+    }
     mark(7);
-    k_copy<<<sms * 4, 256, 0, st>>>(d_hdr, d_desc);
+    k_scan<<<sb, 1024, 0, st>>>(d_hdr, d_desc);
     mark(8);
-    k_wscan<<<sb, 1024, 0, st>>>(d_hdr, d_desc);
+    k_copy<<<sms * 4, 256, 0, st>>>(d_hdr, d_desc);
     mark(9);
-    k_wwrite<<<sms * 4, 256, 0, st>>>(d_hdr, d_desc);
+    k_wscan<<<sb, 1024, 0, st>>>(d_hdr, d_desc);
     mark(10);
-    k_whits<<<sms * 4, 256, 0, st>>>(d_hdr, d_desc);
+    k_wwrite<<<sms * 4, 256, 0, st>>>(d_hdr, d_desc);
     mark(11);
-    k_status<<<1, 256, 0, st>>>(d_hdr, d_desc);
+    k_whits<<<sms * 4, 256, 0, st>>>(d_hdr, d_desc);
     mark(12);
+    if (any_events) {
+        k_escan<<<sb, 1024, 0, st>>>(d_hdr, d_desc);
+        mark(13);
+        k_events<<<sms * 8, 256, 0, st>>>(d_hdr, d_desc);
+        nl += 2;
+    } else {
+        mark(13);
+    }
+    mark(14);
+    k_status<<<1, 256, 0, st>>>(d_hdr, d_desc);
+    mark(15);
     nl += 7;
     if (launches) *launches += nl;
     return cudaGetLastError();

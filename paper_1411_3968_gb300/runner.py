@@ -36,7 +36,7 @@ class DeviceBatch:
     """Inputs resident in HBM, outputs and scratch pre-allocated; run()
     enqueues the whole hot path for all slices on the current stream."""
 
-    def __init__(self, slices: list[SliceIn], device="cuda", trig_cap: int | None = None):
+    def __init__(self, slices: list[SliceIn], device="cuda", trig_cap: int | None = None, events: bool = False):
         self.slices = slices
         self.device = torch.device(device)
         self.hits = [_to_dev(s.hits, self.device) for s in slices]
@@ -52,15 +52,26 @@ class DeviceBatch:
                                              int(s.t0), self.trig[i].data_ptr(), self.trig_cap[i],
                                              self.win[i].data_ptr(), self.win_cap[i],
                                              self.stats.data_ptr() + i * STATS_DTYPE.itemsize))
-        self.scratch_bytes = _lib.trig_batch_scratch_bytes(self.descs)
+        # optional event outputs (all hits inside the merged windows)
+        self.events = None
+        if events:
+            self.ev_cap = [max(1, len(s.hits)) for s in slices]
+            self.ev = [_dev_bytes(c * HIT_DTYPE.itemsize, self.device) for c in self.ev_cap]
+            self.events = [_lib.trig_slice_events(self.ev[i].data_ptr(), self.ev_cap[i]) for i in range(len(slices))]
+        self.scratch_bytes = self._scratch_need()
         self.scratch = _dev_bytes(self.scratch_bytes + 256, self.device)
         self.n_hits = sum(len(s.hits) for s in slices)
         self.input_bytes = sum(s.hits.nbytes + np.asarray(s.pmt_off).nbytes for s in slices)
 
+    def _scratch_need(self) -> int:
+        if self.events is not None:
+            return _lib.trig_batch_events_scratch_bytes(self.descs, self.events)
+        return _lib.trig_batch_scratch_bytes(self.descs)
+
     def ensure_scratch(self) -> None:
         """Grows the scratch when the batch plan needs more, e.g. after the
         autotuner changed a detector's tile shape."""
-        need = _lib.trig_batch_scratch_bytes(self.descs)
+        need = self._scratch_need()
         if need > self.scratch_bytes:
             self.scratch = _dev_bytes(need + 256, self.device)
             self.scratch_bytes = need
@@ -69,7 +80,11 @@ class DeviceBatch:
         self.ensure_scratch()
         st = stream if stream is not None else torch.cuda.current_stream(self.device)
         flags = (_lib.TRIG_RUN_GRAPH if graph else 0) | (_lib.TRIG_RUN_TIMED if timed else 0)
-        _lib.trig_batch_run(self.descs, self.scratch.data_ptr(), self.scratch_bytes, st.cuda_stream, flags)
+        if self.events is not None:
+            _lib.trig_batch_run_events(self.descs, self.events, self.scratch.data_ptr(), self.scratch_bytes,
+                                       st.cuda_stream, flags)
+        else:
+            _lib.trig_batch_run(self.descs, self.scratch.data_ptr(), self.scratch_bytes, st.cuda_stream, flags)
 
     def run_each(self, stream=None) -> None:
         """Plain per-slice launches: one launch sequence per slice."""
@@ -89,6 +104,21 @@ class DeviceBatch:
             trig = np.frombuffer(self.trig[i][: nt * TRIGGER_DTYPE.itemsize].cpu().numpy().tobytes(), TRIGGER_DTYPE)
             win = np.frombuffer(self.win[i][: nw * WINDOW_DTYPE.itemsize].cpu().numpy().tobytes(), WINDOW_DTYPE)
             out.append((stats[i], trig.copy(), win.copy()))
+        return out
+
+    def event_hits(self):
+        """Per slice: the event payload (hits inside the merged windows, in
+        (t, pmt, charge) order) and n_events; run() must have been called."""
+        torch.cuda.synchronize(self.device)
+        stats = np.frombuffer(self.stats.cpu().numpy().tobytes()[: len(self.slices) * STATS_DTYPE.itemsize],
+                              STATS_DTYPE).copy()
+        out = []
+        for i in range(len(self.slices)):
+            ne = int(stats[i]["n_events"])
+            full = bool(stats[i]["flags"] & _lib.TRIG_FLAG_EV_FULL)
+            k = 0 if full else min(ne, self.ev_cap[i])
+            ev = np.frombuffer(self.ev[i][: k * HIT_DTYPE.itemsize].cpu().numpy().tobytes(), HIT_DTYPE).copy()
+            out.append((ev, ne, full))
         return out
 
     def rows(self, i: int):

@@ -34,12 +34,43 @@ def test_binding_covers_header(lib_path):
     assert sorted(_lib.EXPORTS) == _declared()
 
 
+def _c_layout(structs):
+    """sizeof and field offsets of the header's structs, from gcc."""
+    import subprocess
+    import tempfile
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "trig.h"', 'int main(void) {']
+    for name, fields in structs.items():
+        lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for f in fields:
+            lines.append(f'printf("{name}.{f} %zu\\n", offsetof({name}, {f}));')
+    lines.append('return 0; }')
+    with tempfile.TemporaryDirectory() as d:
+        src, exe = os.path.join(d, "l.c"), os.path.join(d, "l")
+        open(src, "w").write("\n".join(lines))
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), src, "-o", exe], check=True)
+        out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout
+    return {k: int(v) for k, v in (ln.split() for ln in out.splitlines())}
+
+
 def test_binding_struct_sizes_match_header():
     from paper_1411_3968_gb300 import _lib
-    assert ctypes.sizeof(_lib.trig_params) == 40
-    assert ctypes.sizeof(_lib.trig_slice_dev) == 80
-    assert _lib.HIT_DTYPE.itemsize == 16 and _lib.TRIGGER_DTYPE.itemsize == 16
-    assert _lib.WINDOW_DTYPE.itemsize == 32 and _lib.STATS_DTYPE.itemsize == 40
+    ct = {"trig_params": _lib.trig_params, "trig_slice_dev": _lib.trig_slice_dev, "trig_result": _lib.trig_result,
+          "trig_slice_events": _lib.trig_slice_events, "trig_tune_result": _lib.trig_tune_result,
+          "trig_geometry": _lib.trig_geometry}
+    np_types = {"trig_hit": _lib.HIT_DTYPE, "trig_trigger": _lib.TRIGGER_DTYPE, "trig_window": _lib.WINDOW_DTYPE,
+                "trig_slice_stats": _lib.STATS_DTYPE}
+    c_names = {"trig_hit": ["t_ns", "pmt", "charge", "reserved"], "trig_trigger": ["t_ns", "pmt", "charge", "count"],
+               "trig_window": ["lo_ns", "hi_ns", "n_hits", "n_triggers"],
+               "trig_slice_stats": ["status", "flags", "n_hits", "n_seeds", "n_triggers", "n_windows", "n_events"]}
+    lay = _c_layout({**{k: [f for f, _ in v._fields_] for k, v in ct.items()}, **c_names})
+    for name, cls in ct.items():
+        assert ctypes.sizeof(cls) == lay[name], name
+        for f, _ in cls._fields_:
+            assert getattr(cls, f).offset == lay[f"{name}.{f}"], (name, f)
+    for name, dt in np_types.items():
+        assert dt.itemsize == lay[name], name
+        for (f, _), cf in zip(dt.descr, c_names[name]):
+            assert dt.fields[f][1] == lay[f"{name}.{cf}"], (name, f)
 
 
 def test_oracle_and_generator_build():

@@ -129,3 +129,23 @@ def test_graph_replay_after_a_smaller_launch_of_the_same_kernel(pkg, params):
         assert np.array_equal(trig["t"], ref.triggers["t"]) and np.array_equal(win["n_hits"], ref.windows["n_hits"])
     dk.close()
     dn.close()
+
+
+def test_engine_event_payload(pkg, params):
+    """trig_set_events: engine results carry the hits inside their windows."""
+    wl = workload.cfg_km3()
+    g = wl.detectors[0]
+    det = pkg.Detector(g.xyz_mm, g.floor_id, params)
+    pkg.trig_set_events(det, True)
+    pkg.trig_engine_set_mode(1)
+    for s in wl.submissions:
+        pkg.trig_submit_slice(det, s.t0, s.stream.hits, s.stream.pmt_off)
+    ref = oracle.run(g.xyz_mm, g.floor_id, params, wl.runs[0].hits, wl.run_slices[0])
+    for k in range(len(ref)):
+        r = pkg.trig_poll(det, 60_000)
+        _same(r, ref[k], f"slice {k}")
+        want = oracle.events(wl.runs[0].hits, ref[k].windows)
+        assert r.n_events == len(want) == len(r.events)
+        for f in ("t", "pmt", "charge"):
+            assert np.array_equal(r.events[f], want[f]), (k, f)
+    det.close()

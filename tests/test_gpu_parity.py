@@ -421,3 +421,75 @@ def test_wide_detector_burst_and_row_outputs(pkg, params):
     assert np.array_equal(merged["t"][is_seed], ref[0].seeds["t"])
     assert np.array_equal(seedcnt[is_seed], ref[0].seeds["count"])
     d.close()
+
+
+# ------------------------------------------------------------ event payload
+
+def _events_run(pkg, det, subs, graph=False):
+    from paper_1411_3968_gb300.runner import DeviceBatch, SliceIn
+    b = DeviceBatch([SliceIn(det if not isinstance(det, list) else det[i], t0, s.hits, s.pmt_off)
+                     for i, (t0, s) in enumerate(subs)], events=True)
+    b.run(graph=graph)
+    return b.results(), b.event_hits()
+
+
+def _assert_events(ev_res, ref_hits, ref_windows, ctx):
+    ev, ne, full = ev_res
+    want = oracle.events(ref_hits, ref_windows)
+    assert not full, ctx
+    assert ne == len(want) == int(ref_windows["n_hits"].sum()), (ctx, ne, len(want))
+    for f in ("t", "pmt", "charge"):
+        assert np.array_equal(ev[f], want[f]), (ctx, f)
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_events_km3_five_slices(pkg, params, graph):
+    """The hits inside the merged windows of five contiguous KM3Net-It
+    slices (with bursts), in merged order, halos included."""
+    wl = workload.cfg_km3()
+    g = wl.detectors[0]
+    d = _det(pkg, g, params)
+    res, evs = _events_run(pkg, d, [(s.t0, s.stream) for s in wl.submissions], graph=graph)
+    ref = oracle.run(g.xyz_mm, g.floor_id, params, wl.runs[0].hits, wl.run_slices[0])
+    for k in range(len(ref)):
+        _assert_same(res[k], ref[k], f"km3 slice {k}")
+        _assert_events(evs[k], wl.runs[0].hits, ref[k].windows, f"km3 events {k}")
+    d.close()
+
+
+def test_events_nemo_and_wide_detector(pkg, params):
+    for g, rate, slice_ns in ((workload.nemo_tower(), 50e3, 200_000_000), (_tower_array(3, 1), 150e3, 4_000_000)):
+        par = dict(params, slice_ns=slice_ns)
+        t0 = workload.T_ORIGIN_NS
+        t0s = [t0, t0 + slice_ns]
+        full = workload.gen_stream(g, t0 - 3000, t0 + 2 * slice_ns + 3000, rate, n_muons=30, seed=4, stream=120)
+        d = _det(pkg, g, par)
+        res, evs = _events_run(pkg, d, _subs_from_run(full, t0s, slice_ns))
+        ref = oracle.run(g.xyz_mm, g.floor_id, par, full.hits, t0s)
+        for k in range(2):
+            _assert_same(res[k], ref[k], f"{g.n_pmt} slice {k}")
+            _assert_events(evs[k], full.hits, ref[k].windows, f"{g.n_pmt} events {k}")
+        d.close()
+
+
+def test_events_capacity_flag(pkg, params):
+    """An event buffer smaller than the payload: TRIG_FLAG_EV_FULL, status
+    ECAPACITY, n_events still counted, triggers and windows unaffected."""
+    import torch
+    from paper_1411_3968_gb300 import _lib
+    from paper_1411_3968_gb300.runner import DeviceBatch, SliceIn
+    wl = workload.cfg_nemo()
+    g = wl.detectors[0]
+    d = _det(pkg, g, params)
+    s = wl.submissions[0]
+    b = DeviceBatch([SliceIn(d, s.t0, s.stream.hits, s.stream.pmt_off)], events=True)
+    b.events[0] = _lib.trig_slice_events(b.ev[0].data_ptr(), 10)
+    b.ev_cap[0] = 10
+    b.ensure_scratch()
+    b.run()
+    stats, trig, win = b.results()[0]
+    ref = oracle.run(g.xyz_mm, g.floor_id, params, wl.runs[0].hits, wl.run_slices[0])[0]
+    assert int(stats["status"]) == pkg.TRIG_ECAPACITY and int(stats["flags"]) & _lib.TRIG_FLAG_EV_FULL
+    assert int(stats["n_events"]) == int(ref.windows["n_hits"].sum())
+    assert np.array_equal(trig["t"], ref.triggers["t"]) and np.array_equal(win["n_hits"], ref.windows["n_hits"])
+    d.close()

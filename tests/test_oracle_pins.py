@@ -314,3 +314,48 @@ def test_trigger_list_independent_of_slicing(params):
     for x, y in zip(a, c):
         assert np.array_equal(x.triggers, y.triggers)
         assert np.array_equal(x.windows, y.windows)
+
+
+# ------------------------------------------------------------ event payload
+
+def test_events_golden_fixture():
+    """The windows fixture's event payload, derived by hand: window 1 holds
+    the seeds at 400000 and 406001 and the PMT 1 hit at its inclusive end
+    409001; the PMT 1 hit at 409002 is in the gap; window 2 holds 409003 (its
+    inclusive start) and the seed at 412003; window 3 the two PMT 20 seeds."""
+    fx = json.load(open(os.path.join(GOLDEN, "windows_nemo32.json")))
+    g = workload.nemo_tower()
+    par = dict(workload.DEFAULT_PARAMS, **fx["params"])
+    hits = np.zeros(len(fx["hits"]), oracle.HIT_DTYPE)
+    for i, (t, p, q) in enumerate(fx["hits"]):
+        hits[i] = (t, p, q, 0)
+    res = oracle.run(g.xyz_mm, g.floor_id, par, hits, fx["slices"])[0]
+    ev = oracle.events(hits, res.windows)
+    expect = [1000400000, 1000406001, 1000409001, 1000409003, 1000412003, 1000500000, 1000506000]
+    assert ev["t"].tolist() == expect
+    assert len(ev) == int(res.windows["n_hits"].sum())
+
+
+def test_events_bruteforce_and_window_counts():
+    """On random dense slices: the payload equals a plain double loop over
+    windows and hits, and its size equals the windows' hit counts that the
+    C oracle computes independently."""
+    rng = np.random.Generator(np.random.PCG64(77))
+    g = workload.nemo_tower()
+    for case in range(6):
+        par = dict(workload.DEFAULT_PARAMS, slice_ns=50_000, threshold=int(rng.integers(1, 5)),
+                   win_half_ns=int(rng.integers(50, 3000)))
+        t0 = 10_000_000
+        n = int(rng.integers(50, 400))
+        hits = np.zeros(n, oracle.HIT_DTYPE)
+        hits["t"] = rng.integers(t0 - 3000, t0 + par["slice_ns"] + 3000, n)
+        hits["pmt"] = rng.integers(0, 32, n)
+        hits["charge"] = rng.integers(1, 500, n)
+        res = oracle.run(g.xyz_mm, g.floor_id, par, hits, [t0])[0]
+        ev = oracle.events(hits, res.windows)
+        want = []
+        for h in sorted(hits.tolist(), key=lambda x: (x[0], x[1], x[2])):
+            if any(lo <= h[0] <= hi for lo, hi, _, _ in res.windows.tolist()):
+                want.append(h[:3])
+        assert [tuple(x)[:3] for x in ev.tolist()] == [tuple(x) for x in want], case
+        assert len(ev) == int(res.windows["n_hits"].sum()), case
