@@ -203,6 +203,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=20.0, help="detector-seconds per detector")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-events", action="store_true", help="skip the event-extraction leg")
     ap.add_argument("--slices", type=int, default=64, help="slices of the batched workload (profiling runs)")
     ap.add_argument("--workload", default="batched", choices=sorted(WORKLOADS),
                     help="batched (the default step) or the scaled 2688-PMT array (profiling runs)")
@@ -336,6 +337,29 @@ def main():
         except (OSError, ValueError, AttributeError):
             pass
 
+    # ------------------------------- event extraction on the same slices
+    events = None
+    if not args.no_events:
+        batch.set_events(True)
+        for _ in range(args.warmup):
+            batch.run(graph=True)
+        torch.cuda.synchronize()
+        k_ev = max(3, args.steps // 5)
+        e0.record(stream)
+        for _ in range(k_ev):
+            batch.run(graph=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_ev = max_over_ranks(e0.elapsed_time(e1) / k_ev)
+        evs = batch.event_hits()
+        n_ev = sum(ne for _, ne, _ in evs)
+        events = {"value": total_hits / (ms_ev * 1e-3), "unit": "hits/s", "ms_per_step": ms_ev,
+                  "events_per_step": int(n_ev), "event_bytes_per_step": int(n_ev) * 16,
+                  "complete": not any(full for _, _, full in evs),
+                  "path": "trig_batch_run_events, CUDA graph replay"}
+        batch.set_events(False)
+        log(f"events: {ms_ev:.3f} ms/step, {n_ev} event hits")
+
     # ---------------------------------------------------- e2e, host buffers
     e2e = None
     trig.trig_engine_set_mode(1)
@@ -405,6 +429,7 @@ def main():
             "kernels_ms": kt, "timed_runs": n_runs,
             "roofline": roofline,
             "e2e": e2e,
+            "events": events,
             "latency": latency,
             "cpu_baseline": cpu,
             "clocks": clocks,

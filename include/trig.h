@@ -332,11 +332,12 @@ uint64_t trig_kernel_launch_count(void);
 /* Average device time per kernel of the pipeline over the runs made with
  * TRIG_RUN_TIMED since the previous call (waits for their events), in the
  * launch order k_prep, k_bounds, k_bsum, k_bscan, k_scatter, k_tile,
- * k_scan, k_copy, k_wscan, k_wwrite, k_whits, k_status (k_bsum, k_bscan and
- * k_scatter run only for batches with a detector of 129 or more PMTs and
- * read 0 otherwise).  avg_ms[i] and names[i] (static strings) for
- * i < max_kernels; returns the number of kernels (12) and the number of
- * runs in *n_runs. */
+ * k_evhalo, k_scan, k_copy, k_wscan, k_wwrite, k_whits, k_escan (with
+ * k_wrank), k_events, k_status.  k_bsum, k_bscan and k_scatter run only for
+ * batches with a detector of 129 or more PMTs, k_evhalo, k_wrank, k_escan
+ * and k_events only for event extraction; the others read about 0.
+ * avg_ms[i] and names[i] (static strings) for i < max_kernels; returns the
+ * number of kernels (15) and the number of runs in *n_runs. */
 int trig_kernel_times(double *avg_ms, const char **names, uint32_t max_kernels, uint32_t *n_runs);
 
 #ifdef __cplusplus

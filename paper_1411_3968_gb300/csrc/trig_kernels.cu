@@ -1621,48 +1621,68 @@ __global__ void __launch_bounds__(256) k_whits(const BatchHeader *__restrict__ h
             if (!CHECK(9, i, d.win_cap)) continue;
             const trig_window win = d.windows[i];
             uint64_t cnt = 0;
-            uint64_t below = 0;     // hits before lo: the window's first merged rank
             if (d.wide) {
                 // whole buckets between the edge buckets, plus the edge
                 // buckets' hits inside [lo, hi]
                 const uint32_t bl = bkt_index(d, win.lo_ns), bh = bkt_index(d, win.hi_ns);
                 if (bl + 1 < bh && lane == 0) cnt = d.bkt_off[bh] - d.bkt_off[bl + 1];
                 const uint32_t e0 = d.bkt_off[bl], e1 = d.bkt_off[bl + 1];
-                if (lane == 0) below = e0;
                 for (uint32_t j = e0 + lane; j < e1; j += 32) {
                     const int64_t t = d.tbuf[j].t_ns;
                     cnt += t >= win.lo_ns && t <= win.hi_ns;
-                    below += t < win.lo_ns;
                 }
                 if (bh != bl) {
                     const uint32_t f0 = d.bkt_off[bh], f1 = d.bkt_off[bh + 1];
                     for (uint32_t j = f0 + lane; j < f1; j += 32) cnt += d.tbuf[j].t_ns <= win.hi_ns;
                 }
             } else {
-                if (d.ev) {
-                    for (uint32_t p = lane; p < d.n_pmt; p += 32) {
-                        const uint64_t sp = d.pmt_off[p], ep = d.pmt_off[p + 1];
-                        const uint64_t a = rank_in_pmt(d, p, win.lo_ns, sp, ep);
-                        cnt += rank_in_pmt(d, p, win.hi_ns + 1, sp, ep) - a;
-                        below += a - sp;
-                    }
-                } else {
-                    for (uint32_t p = lane; p < d.n_pmt; p += 32) {
-                        const uint64_t sp = d.pmt_off[p], ep = d.pmt_off[p + 1];
-                        cnt += rank_in_pmt(d, p, win.hi_ns + 1, sp, ep) - rank_in_pmt(d, p, win.lo_ns, sp, ep);
-                    }
+                for (uint32_t p = lane; p < d.n_pmt; p += 32) {
+                    const uint64_t sp = d.pmt_off[p], ep = d.pmt_off[p + 1];
+                    cnt += rank_in_pmt(d, p, win.hi_ns + 1, sp, ep) - rank_in_pmt(d, p, win.lo_ns, sp, ep);
                 }
             }
             cnt = warp_sum_u64(cnt);
-            if (d.ev) below = warp_sum_u64(below);
             __syncwarp();
             if (lane == 0) {
                 d.windows[i].n_triggers = win.n_hits - win.n_triggers + 1;
                 d.windows[i].n_hits = cnt;
-                if (d.ev) d.win_rlo[i] = (uint32_t)below;
             }
         }
         __syncthreads();
+    }
+}
+
+// Event slices: each window's first merged rank (the hits with t < lo),
+// from the same narrowed per-PMT searches, or from the bucket offsets plus
+// the edge bucket of a wide slice.  A warp per window, as k_whits.
+__global__ void __launch_bounds__(256) k_wrank(const BatchHeader *__restrict__ hdr, const SliceDesc *__restrict__ desc)
+{
+    const uint32_t lane = lane_id();
+    const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarp = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint32_t s = 0; s < hdr->n_slices; ++s) {
+        const SliceDesc &d = desc[s];
+        if (!d.ev || d.ev_cap == 0) continue;
+        if (d.stats->flags & (TRIG_FLAG_TRIG_FULL | TRIG_FLAG_BAD_PMT | TRIG_FLAG_UNSORTED | TRIG_FLAG_OUT_OF_RANGE))
+            continue;
+        const uint64_t nw = min((unsigned long long)d.stats->n_windows, (unsigned long long)d.win_cap);
+        for (uint64_t i = gw; i < nw; i += nwarp) {
+            const int64_t lo_ns = d.windows[i].lo_ns;
+            uint64_t below = 0;
+            if (d.wide) {
+                const uint32_t bl = bkt_index(d, lo_ns);
+                const uint32_t e0 = d.bkt_off[bl], e1 = d.bkt_off[bl + 1];
+                if (lane == 0) below = e0;
+                for (uint32_t j = e0 + lane; j < e1; j += 32) below += d.tbuf[j].t_ns < lo_ns;
+            } else {
+                for (uint32_t p = lane; p < d.n_pmt; p += 32) {
+                    const uint64_t sp = d.pmt_off[p], ep = d.pmt_off[p + 1];
+                    below += rank_in_pmt(d, p, lo_ns, sp, ep) - sp;
+                }
+            }
+            below = warp_sum_u64(below);
+            if (lane == 0 && CHECK(20, i, d.win_cap)) d.win_rlo[i] = (uint32_t)below;
+        }
     }
 }
 
@@ -2041,10 +2061,11 @@ cudaError_t launch_batch(BatchHeader *d_hdr, SliceDesc *d_desc, uint32_t n_slice
     k_whits<<<sms * 4, 256, 0, st>>>(d_hdr, d_desc);
     mark(12);
     if (any_events) {
+        k_wrank<<<sms * 4, 256, 0, st>>>(d_hdr, d_desc);
         k_escan<<<sb, 1024, 0, st>>>(d_hdr, d_desc);
         mark(13);
         k_events<<<sms * 8, 256, 0, st>>>(d_hdr, d_desc);
-        nl += 2;
+        nl += 3;
     } else {
         mark(13);
     }

@@ -55,13 +55,25 @@ class DeviceBatch:
         # optional event outputs (all hits inside the merged windows)
         self.events = None
         if events:
-            self.ev_cap = [max(1, len(s.hits)) for s in slices]
-            self.ev = [_dev_bytes(c * HIT_DTYPE.itemsize, self.device) for c in self.ev_cap]
-            self.events = [_lib.trig_slice_events(self.ev[i].data_ptr(), self.ev_cap[i]) for i in range(len(slices))]
+            self._alloc_events()
         self.scratch_bytes = self._scratch_need()
         self.scratch = _dev_bytes(self.scratch_bytes + 256, self.device)
         self.n_hits = sum(len(s.hits) for s in slices)
         self.input_bytes = sum(s.hits.nbytes + np.asarray(s.pmt_off).nbytes for s in slices)
+
+    def _alloc_events(self) -> None:
+        self.ev_cap = [max(1, len(s.hits)) for s in self.slices]
+        self.ev = [_dev_bytes(c * HIT_DTYPE.itemsize, self.device) for c in self.ev_cap]
+        self.events = [_lib.trig_slice_events(self.ev[i].data_ptr(), self.ev_cap[i]) for i in range(len(self.slices))]
+
+    def set_events(self, on: bool) -> None:
+        """Turns event extraction on (buffers of one entry per hit) or off
+        for later runs of the same resident slices."""
+        if on and self.events is None:
+            self._alloc_events()
+        elif not on:
+            self.events = None
+            self.ev = None
 
     def _scratch_need(self) -> int:
         if self.events is not None:
