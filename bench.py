@@ -378,7 +378,8 @@ def main():
 
     if not args.no_e2e:
         log("e2e: start")
-        e2e_step()
+        for _ in range(args.warmup):        # fills the engine's device and pinned block pools
+            e2e_step()
         torch.cuda.synchronize()
         barrier()
         t = time.perf_counter()

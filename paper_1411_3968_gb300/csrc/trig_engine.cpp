@@ -2,13 +2,15 @@
 // CUDA-graph replay and the continuously batching slice engine.
 //
 // Serving model (the paper's TGPU, "CPU-GPU"): slices of several detectors
-// arrive on the host; each submission is copied into pinned staging memory
+// arrive on the host; each submission is copied straight from the caller's
+// (pageable) memory into a device block before trig_submit_slice returns,
 // and queued; a worker thread forms batches from whatever is pending,
-// admits a batch when a slot (stream + device arena) is free and the device
-// has the memory, copies it to the GPU, runs the whole trigger for all its
-// slices in one launch sequence, and hands results back per detector in
-// submission order.  Up to kSlots batches are in flight, so copies of one
-// batch overlap the kernels of another.
+// admits a batch when a slot (stream + device arena for outputs and
+// scratch) is free and the device has the memory, runs the whole trigger
+// for all its slices in one launch sequence, and hands results back per
+// detector in submission order.  Up to kSlots batches are in flight, so the
+// submissions' copies and the result read-back overlap other batches'
+// kernels.
 #include <algorithm>
 #include <cmath>
 #include <atomic>
@@ -922,21 +924,25 @@ struct Pending {
     std::shared_ptr<DetQueue> q;
     uint64_t id = 0;
     int64_t t0 = 0;
-    unsigned char *pinned = nullptr;     // hits then pmt_off
-    size_t pinned_bytes = 0;
+    unsigned char *dblk = nullptr;       // device copy: hits, then pmt_off at pmt_at
+    size_t dbytes = 0;
+    size_t pmt_at = 0;
     uint64_t n_hits = 0;
     Clock::time_point t_submit;
 };
 
-struct PinnedPool {
+// Device blocks for submitted slices, in power-of-two size classes and
+// reused once their batch completes.  Growth keeps a reserve of free
+// device memory (2 % of the total) for the slot arenas; idle blocks of
+// other classes are released first when the limit is reached.
+struct DevicePool {
     std::mutex mu;
     std::multimap<size_t, unsigned char *> free_blocks;
-    size_t used = 0, limit = (size_t)24 << 30;
+    size_t used = 0;
     unsigned char *get(size_t bytes, size_t *got)
     {
-        size_t cls = 1;
+        size_t cls = (size_t)1 << 16;
         while (cls < bytes) cls <<= 1;
-        if (cls < 4096) cls = 4096;
         std::lock_guard<std::mutex> lk(mu);
         auto it = free_blocks.find(cls);
         if (it != free_blocks.end()) {
@@ -945,15 +951,57 @@ struct PinnedPool {
             *got = cls;
             return p;
         }
-        if (used + cls > limit) {
-            // drop idle blocks of other sizes first
-            for (auto f = free_blocks.begin(); f != free_blocks.end() && used + cls > limit;) {
-                cudaFreeHost(f->second);
-                used -= f->first;
-                f = free_blocks.erase(f);
-            }
-            if (used + cls > limit) return nullptr;
+        size_t free_b = 0, total_b = 0;
+        cudaMemGetInfo(&free_b, &total_b);
+        const size_t reserve = total_b / 50;
+        for (auto f = free_blocks.begin(); f != free_blocks.end() && free_b < cls + reserve;) {
+            cudaFree(f->second);
+            used -= f->first;
+            free_b += f->first;
+            f = free_blocks.erase(f);
         }
+        if (free_b < cls + reserve) return nullptr;
+        void *p = nullptr;
+        if (cudaMalloc(&p, cls) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return nullptr;
+        }
+        used += cls;
+        *got = cls;
+        return static_cast<unsigned char *>(p);
+    }
+    void put(unsigned char *p, size_t cls)
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        free_blocks.emplace(cls, p);
+    }
+};
+
+// Pinned host blocks that results are read back into (the device-to-host
+// copy lands where the caller reads it), in power-of-two size classes,
+// returned by trig_result_free; at most 24 GB.
+struct HostPool {
+    std::mutex mu;
+    std::multimap<size_t, unsigned char *> free_blocks;
+    size_t used = 0, limit = (size_t)24 << 30;
+    unsigned char *get(size_t bytes, size_t *got)
+    {
+        size_t cls = 4096;
+        while (cls < bytes) cls <<= 1;
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = free_blocks.find(cls);
+        if (it != free_blocks.end()) {
+            unsigned char *p = it->second;
+            free_blocks.erase(it);
+            *got = cls;
+            return p;
+        }
+        for (auto f = free_blocks.begin(); f != free_blocks.end() && used + cls > limit;) {
+            cudaFreeHost(f->second);
+            used -= f->first;
+            f = free_blocks.erase(f);
+        }
+        if (used + cls > limit) return nullptr;
         void *p = nullptr;
         if (cudaMallocHost(&p, cls) != cudaSuccess) {
             (void)cudaGetLastError();
@@ -970,15 +1018,23 @@ struct PinnedPool {
     }
 };
 
-// Results and their arrays are ordinary heap memory (trig_result_free).
+// A result and the pinned block its arrays live in (NULL for results
+// without arrays); trig_result_free returns the block to its pool.
+struct ResultBox {
+    trig_result pub;
+    HostPool *pool;
+    unsigned char *blk;
+    size_t cls;
+};
+
 trig_result *new_result(uint64_t id, int64_t t0, int32_t status)
 {
-    trig_result *r = static_cast<trig_result *>(std::calloc(1, sizeof(trig_result)));
-    if (!r) return nullptr;
-    r->slice_id = id;
-    r->t0_ns = t0;
-    r->status = status;
-    return r;
+    ResultBox *b = static_cast<ResultBox *>(std::calloc(1, sizeof(ResultBox)));
+    if (!b) return nullptr;
+    b->pub.slice_id = id;
+    b->pub.t0_ns = t0;
+    b->pub.status = status;
+    return &b->pub;
 }
 
 
@@ -997,14 +1053,16 @@ struct Slot {
     size_t bounce_bytes = 0;
     int state = 0;                                  // 0 idle, 1 computing, 2 copying back
     std::vector<Pending> slices;
-    std::vector<size_t> out_off;                    // per slice offset into bounce
+    std::vector<size_t> out_off;                    // per slice offset of its triggers in its block
     std::vector<trig_slice_dev> dev;
     std::vector<uint64_t> trig_n, win_n;
-    std::vector<size_t> win_off;                    // per slice offset of its windows in bounce
-    std::vector<size_t> ev_off;                     // per slice offset of its events in bounce
+    std::vector<size_t> win_off;                    // per slice offset of its windows in its block
+    std::vector<size_t> ev_off;                     // per slice offset of its events in its block
+    std::vector<unsigned char *> rblk;              // per slice pinned result block (NULL: none)
+    std::vector<size_t> rcls;
     std::vector<trig_slice_events> evs;             // per slice event output (ev_cap 0: none)
     std::vector<uint64_t> ev_n;
-    bool lost = false;                              // bounce could not grow: outputs dropped
+    std::vector<uint8_t> lost;                      // per slice: no result block, outputs dropped
 };
 
 constexpr int kSlots = 3;
@@ -1016,7 +1074,8 @@ struct Engine {
     std::condition_variable cv;
     std::deque<Pending> pending;
     Slot slots[kSlots];
-    PinnedPool pool;
+    DevicePool pool;
+    HostPool rpool;
     std::thread worker;
     bool stop = false;
     int mode = 1;
@@ -1087,10 +1146,11 @@ uint64_t win_cap_for(const trig_detector *det)
     return (uint64_t)((det->par.slice_ns + 2 * h) / (2 * h + 2)) + 2;
 }
 
-// Device footprint of a batch in one arena: inputs, outputs, stats, scratch.
+// Device footprint of a batch in one arena: outputs, stats, events, scratch
+// (the inputs stay in the submissions' device blocks).
 struct ArenaLayout {
     size_t bytes = 0;
-    std::vector<size_t> hits, offs, trig, win, stats, ev;
+    std::vector<size_t> trig, win, stats, ev;
     size_t scratch = 0, scratch_bytes = 0;
 };
 
@@ -1098,8 +1158,8 @@ struct ArenaLayout {
 
 bool Engine::launch_batch_on(Slot &s, std::vector<Pending> &batch)
 {
-    // layout of the arena: inputs and outputs of every slice, then the
-    // batch scratch
+    // layout of the arena: the outputs of every slice, then the batch
+    // scratch
     const uint32_t n = (uint32_t)batch.size();
     std::vector<trig_slice_dev> dev(n);
     ArenaLayout L;
@@ -1113,15 +1173,13 @@ bool Engine::launch_batch_on(Slot &s, std::vector<Pending> &batch)
         dev[i].trig_cap = std::max<uint64_t>(p.n_hits, 1);
         dev[i].win_cap = win_cap_for(p.det);
         // placeholder pointers for sizing (the real ones are set below)
-        dev[i].hits = reinterpret_cast<const trig_hit *>(256);
-        dev[i].pmt_off = reinterpret_cast<const uint64_t *>(256);
+        // the inputs are the submission's device copy
+        dev[i].hits = reinterpret_cast<const trig_hit *>(p.dblk);
+        dev[i].pmt_off = reinterpret_cast<const uint64_t *>(p.dblk + p.pmt_at);
         dev[i].triggers = reinterpret_cast<trig_trigger *>(256);
         dev[i].windows = reinterpret_cast<trig_window *>(256);
         dev[i].stats = reinterpret_cast<trig_slice_stats *>(256);
-        L.hits.push_back(off);
-        off += align256(p.n_hits * sizeof(trig_hit));
-        L.offs.push_back(off);
-        off += align256((size_t)(P + 1) * 8);
+        (void)P;
         L.trig.push_back(off);
         off += align256(dev[i].trig_cap * sizeof(trig_trigger));
         L.win.push_back(off);
@@ -1175,8 +1233,6 @@ bool Engine::launch_batch_on(Slot &s, std::vector<Pending> &batch)
     char *A = static_cast<char *>(s.arena);
     s.out_off.assign(n, 0);
     for (uint32_t i = 0; i < n; ++i) {
-        dev[i].hits = reinterpret_cast<const trig_hit *>(A + L.hits[i]);
-        dev[i].pmt_off = reinterpret_cast<const uint64_t *>(A + L.offs[i]);
         dev[i].triggers = reinterpret_cast<trig_trigger *>(A + L.trig[i]);
         dev[i].windows = reinterpret_cast<trig_window *>(A + L.win[i]);
         dev[i].stats = reinterpret_cast<trig_slice_stats *>(A + L.stats[i]);
@@ -1199,22 +1255,8 @@ bool Engine::launch_batch_on(Slot &s, std::vector<Pending> &batch)
         s.bounce = static_cast<unsigned char *>(p);
         s.bounce_bytes = want;
     }
-    // copies in, run, stats back
+    // run, stats back
     cudaError_t e = cudaSuccess;
-    for (uint32_t i = 0; i < n && !e; ++i) {
-        const Pending &p = batch[i];
-        if (p.n_hits)
-            e = cudaMemcpyAsync((void *)dev[i].hits, p.pinned, p.n_hits * sizeof(trig_hit), cudaMemcpyHostToDevice,
-                                s.stream);
-        if (!e)
-            e = cudaMemcpyAsync((void *)dev[i].pmt_off, p.pinned + p.n_hits * sizeof(trig_hit),
-                                (size_t)(p.det->n_pmt + 1) * 8, cudaMemcpyHostToDevice, s.stream);
-    }
-    if (e) {
-        fatal = cudaGetErrorString(e);
-        (void)cudaGetLastError();
-        return false;
-    }
     // batches of the engine vary in size and composition from one launch
     // to the next, so they are launched directly rather than from graphs
     int rc = any_ev ? trig_batch_run_events(dev.data(), evs.data(), n, A + L.scratch, L.scratch_bytes, s.stream, 0)
@@ -1264,61 +1306,47 @@ void Engine::collect_stats(Slot &s)
 {
     const uint32_t n = (uint32_t)s.slices.size();
     const trig_slice_stats *st = reinterpret_cast<const trig_slice_stats *>(s.bounce);
-    // output bytes by the actual counts; the bounce buffer holds the
-    // counters first, then each slice's triggers and windows
-    size_t need = align256(n * sizeof(trig_slice_stats));
-    std::vector<size_t> toff(n), woff(n), eoff(n);
+    // per slice one pinned block sized by the actual counts: triggers,
+    // windows, events
+    s.out_off.assign(n, 0);
+    s.win_off.assign(n, 0);
+    s.ev_off.assign(n, 0);
+    s.rblk.assign(n, nullptr);
+    s.rcls.assign(n, 0);
+    s.lost.assign(n, 0);
     s.ev_n.assign(n, 0);
-    for (uint32_t i = 0; i < n; ++i) {
-        s.trig_n[i] = std::min<uint64_t>(st[i].n_triggers, s.dev[i].trig_cap);
-        s.win_n[i] = std::min<uint64_t>(st[i].n_windows, s.dev[i].win_cap);
-        toff[i] = need;
-        need += align256(s.trig_n[i] * sizeof(trig_trigger));
-        woff[i] = need;
-        need += align256(s.win_n[i] * sizeof(trig_window));
-        if (s.evs[i].ev_cap && !(st[i].flags & TRIG_FLAG_EV_FULL))
-            s.ev_n[i] = std::min<uint64_t>(st[i].n_events, s.evs[i].ev_cap);
-        eoff[i] = need;
-        need += align256(s.ev_n[i] * sizeof(trig_hit));
-    }
-    if (s.bounce_bytes < need) {
-        // grow (geometrically) keeping the counters already read
-        const size_t want = std::max(need, s.bounce_bytes + s.bounce_bytes / 2);
-        void *p = nullptr;
-        if (cudaMallocHost(&p, want) != cudaSuccess) {
-            (void)cudaGetLastError();
-            for (uint32_t i = 0; i < n; ++i) s.trig_n[i] = s.win_n[i] = s.ev_n[i] = 0;
-            s.lost = true;
-            s.state = 2;
-            cudaEventRecord(s.ev_done, s.stream);
-            return;
-        }
-        std::memcpy(p, s.bounce, align256(n * sizeof(trig_slice_stats)));
-        cudaFreeHost(s.bounce);
-        s.bounce = static_cast<unsigned char *>(p);
-        s.bounce_bytes = want;
-    }
-    s.out_off.assign(toff.begin(), toff.end());
-    s.win_off.assign(woff.begin(), woff.end());
-    s.ev_off.assign(eoff.begin(), eoff.end());
     cudaError_t e = cudaSuccess;
     for (uint32_t i = 0; i < n && !e; ++i) {
+        s.trig_n[i] = std::min<uint64_t>(st[i].n_triggers, s.dev[i].trig_cap);
+        s.win_n[i] = std::min<uint64_t>(st[i].n_windows, s.dev[i].win_cap);
+        if (s.evs[i].ev_cap && !(st[i].flags & TRIG_FLAG_EV_FULL))
+            s.ev_n[i] = std::min<uint64_t>(st[i].n_events, s.evs[i].ev_cap);
+        const size_t tb = align256(s.trig_n[i] * sizeof(trig_trigger));
+        const size_t wb = align256(s.win_n[i] * sizeof(trig_window));
+        const size_t eb = s.ev_n[i] * sizeof(trig_hit);
+        s.win_off[i] = tb;
+        s.ev_off[i] = tb + wb;
+        if (tb + wb + eb == 0) continue;
+        s.rblk[i] = rpool.get(tb + wb + eb, &s.rcls[i]);
+        if (!s.rblk[i]) {
+            s.lost[i] = 1;
+            s.trig_n[i] = s.win_n[i] = s.ev_n[i] = 0;
+            continue;
+        }
         if (s.trig_n[i])
-            e = cudaMemcpyAsync(s.bounce + toff[i], s.dev[i].triggers, s.trig_n[i] * sizeof(trig_trigger),
+            e = cudaMemcpyAsync(s.rblk[i], s.dev[i].triggers, s.trig_n[i] * sizeof(trig_trigger),
                                 cudaMemcpyDeviceToHost, s.stream);
         if (!e && s.win_n[i])
-            e = cudaMemcpyAsync(s.bounce + woff[i], s.dev[i].windows, s.win_n[i] * sizeof(trig_window),
+            e = cudaMemcpyAsync(s.rblk[i] + tb, s.dev[i].windows, s.win_n[i] * sizeof(trig_window),
                                 cudaMemcpyDeviceToHost, s.stream);
         if (!e && s.ev_n[i])
-            e = cudaMemcpyAsync(s.bounce + eoff[i], s.evs[i].events, s.ev_n[i] * sizeof(trig_hit),
-                                cudaMemcpyDeviceToHost, s.stream);
+            e = cudaMemcpyAsync(s.rblk[i] + tb + wb, s.evs[i].events, eb, cudaMemcpyDeviceToHost, s.stream);
     }
     if (!e) e = cudaEventRecord(s.ev_done, s.stream);
     if (e) {
         fatal = cudaGetErrorString(e);
         (void)cudaGetLastError();
     }
-    s.lost = false;
     s.state = 2;
 }
 
@@ -1329,34 +1357,28 @@ void Engine::finish(Slot &s)
     const auto now = Clock::now();
     for (uint32_t i = 0; i < n; ++i) {
         Pending &p = s.slices[i];
-        trig_result *r = new_result(p.id, p.t0, s.lost ? TRIG_ENOMEM : st[i].status);
+        trig_result *r = new_result(p.id, p.t0, s.lost[i] ? TRIG_ENOMEM : st[i].status);
         if (r) {
+            ResultBox *box = reinterpret_cast<ResultBox *>(r);
             r->flags = st[i].flags;
             r->n_hits = st[i].n_hits;
             r->n_seeds = st[i].n_seeds;
             r->n_triggers = s.trig_n[i];
             r->n_windows = s.win_n[i];
-            if (r->n_triggers) {
-                r->triggers = static_cast<trig_trigger *>(std::malloc(r->n_triggers * sizeof(trig_trigger)));
-                if (r->triggers)
-                    std::memcpy(r->triggers, s.bounce + s.out_off[i], r->n_triggers * sizeof(trig_trigger));
+            if (s.rblk[i]) {
+                box->pool = &rpool;
+                box->blk = s.rblk[i];
+                box->cls = s.rcls[i];
+                if (r->n_triggers) r->triggers = reinterpret_cast<trig_trigger *>(s.rblk[i]);
+                if (r->n_windows) r->windows = reinterpret_cast<trig_window *>(s.rblk[i] + s.win_off[i]);
+                if (s.ev_n[i]) r->events = reinterpret_cast<trig_hit *>(s.rblk[i] + s.ev_off[i]);
             }
-            if (r->n_windows) {
-                r->windows = static_cast<trig_window *>(std::malloc(r->n_windows * sizeof(trig_window)));
-                if (r->windows) std::memcpy(r->windows, s.bounce + s.win_off[i], r->n_windows * sizeof(trig_window));
-            }
-            if (s.evs[i].ev_cap) {
-                r->n_events = s.lost ? 0 : st[i].n_events;
-                if (s.ev_n[i]) {
-                    r->events = static_cast<trig_hit *>(std::malloc(s.ev_n[i] * sizeof(trig_hit)));
-                    if (r->events) std::memcpy(r->events, s.bounce + s.ev_off[i], s.ev_n[i] * sizeof(trig_hit));
-                }
-            }
-            if ((r->n_triggers && !r->triggers) || (r->n_windows && !r->windows) || (s.ev_n[i] && !r->events))
-                r->status = TRIG_ENOMEM;
+            if (s.evs[i].ev_cap) r->n_events = s.lost[i] ? 0 : st[i].n_events;
             r->latency_ns = std::chrono::duration_cast<std::chrono::nanoseconds>(now - p.t_submit).count();
+        } else if (s.rblk[i]) {
+            rpool.put(s.rblk[i], s.rcls[i]);
         }
-        pool.put(p.pinned, p.pinned_bytes);
+        pool.put(p.dblk, p.dbytes);
         {
             std::lock_guard<std::mutex> lk(p.q->mu);
             p.q->done[p.id] = r;
@@ -1420,7 +1442,8 @@ void Engine::run()
                         // cannot run at all: fail these slices
                         for (auto &p : batch) {
                             trig_result *r = new_result(p.id, p.t0, fatal.empty() ? TRIG_ENOMEM : TRIG_EDEVICE);
-                            pool.put(p.pinned, p.pinned_bytes);
+                            // after a launch error kernels may still read the block: keep it
+                            if (fatal.empty()) pool.put(p.dblk, p.dbytes);
                             std::lock_guard<std::mutex> ql(p.q->mu);
                             p.q->done[p.id] = r;
                             p.q->in_flight--;
@@ -1457,30 +1480,6 @@ extern "C" int trig_engine_stats(uint64_t *batches, uint64_t *slices)
     return TRIG_OK;
 }
 
-// Copies large host buffers with several threads (the submission's copy
-// into pinned staging is on the serving path's critical host work).
-static void parallel_copy(void *dst, const void *src, size_t bytes)
-{
-    const size_t kMinChunk = (size_t)8 << 20;
-    unsigned hw = std::thread::hardware_concurrency();
-    size_t nt = std::min<size_t>(std::max(1u, hw ? hw / 2 : 1u), 16);
-    nt = std::min(nt, bytes / kMinChunk);
-    if (nt <= 1) {
-        std::memcpy(dst, src, bytes);
-        return;
-    }
-    const size_t chunk = ((bytes + nt - 1) / nt + 63) & ~(size_t)63;
-    std::vector<std::thread> th;
-    for (size_t i = 1; i < nt; ++i) {
-        size_t a = i * chunk;
-        if (a >= bytes) break;
-        size_t len = std::min(chunk, bytes - a);
-        th.emplace_back([=] { std::memcpy((char *)dst + a, (const char *)src + a, len); });
-    }
-    std::memcpy(dst, src, std::min(chunk, bytes));
-    for (auto &t : th) t.join();
-}
-
 extern "C" int trig_submit_slice(trig_detector *det, int64_t t0, const trig_hit *hits, const uint64_t *pmt_off,
                                  int is_continuation, uint64_t *slice_id_out)
 {
@@ -1501,11 +1500,34 @@ extern "C" int trig_submit_slice(trig_detector *det, int64_t t0, const trig_hit 
     p.q = det->q;
     p.t0 = t0;
     p.n_hits = n;
-    const size_t bytes = n * sizeof(trig_hit) + (size_t)(P + 1) * 8;
-    p.pinned = e->pool.get(bytes, &p.pinned_bytes);
-    if (!p.pinned) return fail(TRIG_EAGAIN, "staging memory full; poll results and retry");
-    if (n) parallel_copy(p.pinned, hits, n * sizeof(trig_hit));
-    std::memcpy(p.pinned + n * sizeof(trig_hit), pmt_off, (size_t)(P + 1) * 8);
+    // copy the slice to a device block now (the caller may reuse its
+    // buffers on return): pageable host memory straight to the device, on a
+    // stream of this thread's own
+    p.pmt_at = align256(n * sizeof(trig_hit));
+    const size_t bytes = p.pmt_at + (size_t)(P + 1) * 8;
+    int prev_dev = -1;
+    cudaGetDevice(&prev_dev);
+    if (prev_dev != e->device) cudaSetDevice(e->device);
+    p.dblk = e->pool.get(bytes, &p.dbytes);
+    if (!p.dblk) {
+        if (prev_dev != e->device) cudaSetDevice(prev_dev);
+        return fail(TRIG_EAGAIN, "device staging memory full; poll results and retry");
+    }
+    thread_local cudaStream_t copy_stream = nullptr;
+    thread_local int copy_dev = -1;
+    cudaError_t ce = cudaSuccess;
+    if (!copy_stream || copy_dev != e->device) {
+        ce = cudaStreamCreateWithFlags(&copy_stream, cudaStreamNonBlocking);
+        copy_dev = e->device;
+    }
+    if (!ce && n) ce = cudaMemcpyAsync(p.dblk, hits, n * sizeof(trig_hit), cudaMemcpyHostToDevice, copy_stream);
+    if (!ce) ce = cudaMemcpyAsync(p.dblk + p.pmt_at, pmt_off, (size_t)(P + 1) * 8, cudaMemcpyHostToDevice, copy_stream);
+    if (!ce) ce = cudaStreamSynchronize(copy_stream);
+    if (prev_dev != e->device) cudaSetDevice(prev_dev);
+    if (ce) {
+        (void)cudaGetLastError();
+        return fail(TRIG_EDEVICE, std::string("copying the slice to the device: ") + cudaGetErrorString(ce));
+    }
     p.t_submit = t_entry;
     p.id = e->next_id++;
     {
@@ -1547,10 +1569,9 @@ extern "C" int trig_poll(trig_detector *det, int timeout_ms, trig_result **out)
 extern "C" void trig_result_free(trig_result *r)
 {
     if (!r) return;
-    std::free(r->triggers);
-    std::free(r->windows);
-    std::free(r->events);
-    std::free(r);
+    ResultBox *box = reinterpret_cast<ResultBox *>(r);
+    if (box->blk && box->pool) box->pool->put(box->blk, box->cls);
+    std::free(box);
 }
 
 extern "C" int trig_destroy(trig_detector *det)
