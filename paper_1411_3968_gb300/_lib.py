@@ -217,8 +217,43 @@ def trig_submit_slice(det: Detector, t0: int, hits: np.ndarray, pmt_off: np.ndar
     return int(sid.value)
 
 
+class _Owner:
+    """Frees a trig_result when the last array viewing it is gone."""
+
+    def __init__(self, ptr):
+        self.ptr = ptr
+
+    def __del__(self):
+        try:
+            load().trig_result_free(self.ptr)
+        except Exception:
+            pass
+
+
+class _View:
+    """Read-only numpy view of library memory that keeps its owner alive."""
+
+    def __init__(self, owner, addr, n, dtype):
+        self.owner = owner
+        self.__array_interface__ = {"shape": (n,), "typestr": dtype.str, "descr": dtype.descr,
+                                    "data": (addr, True), "version": 3}
+
+
+def _view(owner, ptr, n, dtype):
+    n = int(n)
+    if n == 0 or not ptr:
+        return np.empty(0, dtype)
+    return np.asarray(_View(owner, ptr, n, dtype)).view(dtype)
+
+
 class Result:
-    def __init__(self, r: trig_result):
+    """One slice's result.  Its arrays are read-only views of the library's
+    result memory (no copy), released once the Result and every array taken
+    from it are gone."""
+
+    def __init__(self, ptr):
+        r = ptr.contents
+        owner = _Owner(ptr)
         self.slice_id = int(r.slice_id)
         self.t0 = int(r.t0_ns)
         self.status = int(r.status)
@@ -226,10 +261,11 @@ class Result:
         self.n_hits = int(r.n_hits)
         self.n_seeds = int(r.n_seeds)
         self.latency_ns = int(r.latency_ns)
-        self.triggers = _copy(r.triggers, r.n_triggers, TRIGGER_DTYPE)
-        self.windows = _copy(r.windows, r.n_windows, WINDOW_DTYPE)
+        self.triggers = _view(owner, r.triggers, r.n_triggers, TRIGGER_DTYPE)
+        self.windows = _view(owner, r.windows, r.n_windows, WINDOW_DTYPE)
         self.n_events = int(r.n_events)
-        self.events = _copy(r.events, r.n_events if r.events else 0, HIT_DTYPE)
+        self.events = _view(owner, r.events, r.n_events if r.events else 0, HIT_DTYPE)
+        self._owner = owner
 
 
 def _copy(ptr, n, dtype):
@@ -247,10 +283,7 @@ def trig_poll(det: Detector, timeout_ms: int = -1) -> Result | None:
     if rc == TRIG_EAGAIN:
         return None
     _check(rc)
-    try:
-        return Result(out.contents)
-    finally:
-        lib.trig_result_free(out)
+    return Result(out)
 
 
 def trig_set_events(det: "Detector", on: bool = True) -> None:
