@@ -89,6 +89,16 @@ typedef struct {
     uint32_t threshold;         /* fire when c(s) >= threshold                      */
     uint32_t win_half_ns;       /* event window [t - h, t + h], merged when touching */
     int64_t slice_ns;           /* a slice owns [t0, t0 + slice_ns)                 */
+    /* Level-0 trigger ("Muon trigger strategy", "Sorting and triggering in
+     * GPU": N7TW1000 / DN7TW1000, N hits within TW, applied before the
+     * seed triggers).  With l0_hits = N > 0 a seed counts only if some
+     * window [a, a + TW) containing it holds at least N hits, or, with
+     * l0_distinct_pmts, hits of at least N different PMTs (then n_pmt must
+     * be at most 128).  l0_hits = 0 turns it off; TW <= 60000 ns. */
+    uint32_t l0_hits;
+    uint32_t l0_window_ns;
+    uint32_t l0_distinct_pmts;
+    uint32_t l0_reserved;       /* 0 */
 } trig_params;
 
 /* A fired seed: its hit and causal count c(s). 16 bytes. */

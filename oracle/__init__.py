@@ -56,6 +56,10 @@ class _Params(ctypes.Structure):
         ("threshold", ctypes.c_uint32),
         ("win_half_ns", ctypes.c_uint32),
         ("slice_ns", ctypes.c_int64),
+        ("l0_hits", ctypes.c_uint32),
+        ("l0_window_ns", ctypes.c_uint32),
+        ("l0_distinct_pmts", ctypes.c_uint32),
+        ("l0_reserved", ctypes.c_uint32),
     ]
 
 
@@ -99,7 +103,7 @@ def _load():
 def _params(p: dict) -> _Params:
     s = _Params()
     for name, _ in _Params._fields_:
-        setattr(s, name, int(p[name]))
+        setattr(s, name, int(p.get(name, 0)))
     return s
 
 

@@ -27,6 +27,12 @@
  *           W the 3 us correlation interval; s itself and hits on its own
  *           PMT are included.  Obtained by testing every hit in
  *           [t_s - W, t_s + W] -- the brute force over the window.
+ *   level 0 (optional, "Muon trigger strategy": N hits in a fixed time
+ *           window TW, N7TW1000, applied before the other triggers; its
+ *           DN variant counts different PMTs): a seed is kept only if some
+ *           window [a, a + TW) that contains it holds at least N hits (N
+ *           different PMTs).  Only windows starting at a hit need testing:
+ *           moving a window's start up to its first hit loses nothing.
  *   trigger seeds with c(s) >= threshold, in (t, pmt, charge) order.
  *   windows [t_s - h, t_s + h] around every trigger (the 6 us window centred
  *           on the seed), merged while lo_next <= hi_cur + 1; n_hits counts
@@ -152,6 +158,31 @@ static int push_seed(oracle_seed **v, uint64_t *n, uint64_t *cap, oracle_seed s)
     return 0;
 }
 
+/* Level 0 at the seed H[s]: some window [t_j, t_j + TW) with
+ * t_s - TW < t_j <= t_s holds at least N hits (N different PMTs). */
+static int level0_pass(const run_job *job, uint64_t s)
+{
+    const oracle_params *par = job->par;
+    const oracle_hit *H = job->sorted;
+    const uint64_t n = job->n;
+    const int64_t ts = H[s].t_ns, TW = par->l0_window_ns;
+    for (uint64_t j = lower_bound_t(H, n, ts - TW + 1); j < n && H[j].t_ns <= ts; ++j) {
+        const int64_t a = H[j].t_ns;
+        const uint64_t b = lower_bound_t(H, n, a);        /* every hit of the window */
+        uint32_t count = 0;
+        if (!par->l0_distinct_pmts) {
+            for (uint64_t q = b; q < n && H[q].t_ns < a + TW; ++q) ++count;
+        } else {
+            unsigned char seen[4096];
+            memset(seen, 0, job->n_pmt);
+            for (uint64_t q = b; q < n && H[q].t_ns < a + TW; ++q)
+                if (!seen[H[q].pmt]) { seen[H[q].pmt] = 1; ++count; }
+        }
+        if (count >= par->l0_hits) return 1;
+    }
+    return 0;
+}
+
 static int run_slice(run_job *job, uint32_t k)
 {
     const oracle_params *par = job->par;
@@ -179,6 +210,7 @@ static int run_slice(run_job *job, uint32_t k)
                 }
             }
         }
+        if (is_seed && par->l0_hits > 0) is_seed = level0_pass(job, s);
         if (!is_seed) continue;
         uint32_t c = 0;
         for (uint64_t j = lower_bound_t(H, n, hs->t_ns - W); j < n && H[j].t_ns <= hs->t_ns + W; ++j) {

@@ -23,6 +23,10 @@ typedef struct {
     uint32_t threshold;       /* fire when c(s) >= threshold                */
     uint32_t win_half_ns;     /* event window [t - h, t + h]                */
     int64_t slice_ns;         /* owned range of a slice: [t0, t0 + S)       */
+    uint32_t l0_hits;         /* level 0: N hits (0 = off) ...              */
+    uint32_t l0_window_ns;    /* ... within TW ns ...                       */
+    uint32_t l0_distinct_pmts;/* ... counting different PMTs only if 1      */
+    uint32_t l0_reserved;
 } oracle_params;
 
 typedef struct {

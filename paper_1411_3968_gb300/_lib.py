@@ -66,7 +66,9 @@ class trig_geometry(ctypes.Structure):
 class trig_params(ctypes.Structure):
     _fields_ = [("q_seed_adc", ctypes.c_uint32), ("floor_tau_ns", ctypes.c_uint32), ("tol_ns", ctypes.c_uint32),
                 ("n_num", ctypes.c_uint32), ("n_den", ctypes.c_uint32), ("corr_window_ns", ctypes.c_uint32),
-                ("threshold", ctypes.c_uint32), ("win_half_ns", ctypes.c_uint32), ("slice_ns", ctypes.c_int64)]
+                ("threshold", ctypes.c_uint32), ("win_half_ns", ctypes.c_uint32), ("slice_ns", ctypes.c_int64),
+                ("l0_hits", ctypes.c_uint32), ("l0_window_ns", ctypes.c_uint32), ("l0_distinct_pmts", ctypes.c_uint32),
+                ("l0_reserved", ctypes.c_uint32)]
 
 
 class trig_result(ctypes.Structure):
@@ -171,7 +173,7 @@ class Detector:
         self.params = dict(params)
         g = trig_geometry(self.n_pmt, self.xyz.ctypes.data, self.floor_id.ctypes.data,
                           None if self.tower_id is None else self.tower_id.ctypes.data)
-        p = trig_params(*(int(params[f]) for f, _ in trig_params._fields_))
+        p = trig_params(*(int(params.get(f, 0)) for f, _ in trig_params._fields_))
         h = ctypes.c_void_p()
         _check(lib.trig_create(ctypes.byref(g), ctypes.byref(p), ctypes.byref(h)))
         self.handle = h

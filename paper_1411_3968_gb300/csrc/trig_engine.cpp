@@ -135,6 +135,10 @@ static int check_params(const trig_params *p)
     if (p->corr_window_ns > 60000 || p->win_half_ns > 60000 || p->floor_tau_ns > 60000)
         return fail(TRIG_EINVAL, "corr_window_ns, win_half_ns and floor_tau_ns must be <= 60000");
     if (p->q_seed_adc > 65536) return fail(TRIG_EINVAL, "q_seed_adc > 65536");
+    if (p->l0_hits > 0 && (p->l0_window_ns == 0 || p->l0_window_ns > 60000))
+        return fail(TRIG_EINVAL, "l0_window_ns must be in [1, 60000] when l0_hits > 0");
+    if (p->l0_hits > 4096) return fail(TRIG_EINVAL, "l0_hits > 4096");
+    if (p->l0_distinct_pmts > 1 || p->l0_reserved != 0) return fail(TRIG_EINVAL, "l0_distinct_pmts is 0 or 1, l0_reserved 0");
     return TRIG_OK;
 }
 
@@ -147,6 +151,8 @@ extern "C" int trig_create(const trig_geometry *g, const trig_params *params, tr
     int rc = check_params(params);
     if (rc) return rc;
     const uint32_t P = g->n_pmt;
+    if (params->l0_hits > 0 && params->l0_distinct_pmts && P > 128)
+        return fail(TRIG_EINVAL, "the distinct-PMT level 0 needs n_pmt <= 128");
     for (uint32_t i = 0; i < 3 * P; ++i)
         if (g->xyz_mm[i] > 100000000 || g->xyz_mm[i] < -100000000)
             return fail(TRIG_EINVAL, "coordinates must lie within +-1e8 mm");
@@ -193,11 +199,14 @@ extern "C" int trig_create(const trig_geometry *g, const trig_params *params, tr
         free_det_dev(d.get());
         return cuda_fail(e, "trig_create: building dt_max");
     }
-    uint32_t H = params->floor_tau_ns;
+    // the tile halo covers every hit a core hit's seed test, level 0 and
+    // causal count look at; the accepted input halo as well
+    const uint32_t l0w = params->l0_hits > 0 ? params->l0_window_ns : 0u;
+    uint32_t H = std::max(params->floor_tau_ns, l0w);
     for (uint16_t v : dmax) H = std::max<uint32_t>(H, v);
     d->tile_halo = H;
     d->in_halo = std::max<int64_t>({(int64_t)params->corr_window_ns, (int64_t)params->win_half_ns,
-                                    (int64_t)params->floor_tau_ns});
+                                    (int64_t)params->floor_tau_ns, (int64_t)l0w});
     d->q = std::make_shared<DetQueue>();
     TileConfig cached{};
     if (tune_cache_lookup(P, cached)) {
@@ -350,6 +359,9 @@ static int plan_into(const trig_slice_dev *sl, uint32_t n, uintptr_t base, const
         d.q_seed = det->par.q_seed_adc;
         d.tau = det->par.floor_tau_ns;
         d.threshold = det->par.threshold;
+        d.l0_hits = det->par.l0_hits;
+        d.l0_window = det->par.l0_window_ns;
+        d.l0_distinct = det->par.l0_distinct_pmts;
         d.win_half = det->par.win_half_ns;
         d.t0 = x.t0_ns;
         d.slice_ns = det->par.slice_ns;

@@ -42,6 +42,10 @@ struct SliceDesc {
     uint32_t tau;
     uint32_t threshold;
     uint32_t win_half;
+    uint32_t l0_hits;       // level 0: N hits (0 = off) within l0_window ns,
+    uint32_t l0_window;     //   of different PMTs if l0_distinct
+    uint32_t l0_distinct;
+    uint32_t pad_l0;
     int64_t t0;
     int64_t slice_ns;
     int64_t in_lo, in_hi;   // accepted hit times [in_lo, in_hi)

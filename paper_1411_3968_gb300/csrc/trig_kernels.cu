@@ -776,9 +776,59 @@ struct CoreOut {
 // core is t_rel in [H, H + core_w).  Fired seeds go to out[0..n_fired).
 struct TrigParams {
     uint32_t H, tau, q_seed, threshold;
+    uint32_t l0_hits, l0_window, l0_distinct;
     trig_hit *dbg_merged;
     uint32_t *dbg_seedcnt;
 };
+
+// Level 0 at sorted index i: some window [t_j, t_j + TW) with
+// t_i - TW < t_j <= t_i holds at least N hits, or hits of N different PMTs
+// (P <= 128).  Only the first index of each time starts a window; every
+// hit within TW of a core hit is staged (the tile halo covers TW).  The
+// distinct count slides the window back start by start, keeping per-PMT
+// counts, so it reads each hit within 2 TW once.
+__device__ __noinline__ bool level0_pass(const uint32_t *pk, uint32_t n, uint32_t i, uint32_t N, uint32_t TW,
+                                         bool distinct)
+{
+    const uint32_t ts = pk_t(pk[i]);
+    uint32_t j = i;
+    while (j > 0 && pk_t(pk[j - 1]) == ts) --j;             // first index of t_i
+    if (!distinct) {
+        for (;;) {
+            const uint32_t tj = pk_t(pk[j]);
+            if (j + N - 1 < n && pk_t(pk[j + N - 1]) - tj < TW) return true;
+            if (j == 0) return false;
+            const uint32_t tp = pk_t(pk[j - 1]);
+            if (ts - tp >= TW) return false;
+            for (--j; j > 0 && pk_t(pk[j - 1]) == tp; --j) {
+            }
+        }
+    }
+    uint16_t cnt[128];
+    for (uint32_t p = 0; p < 128; ++p) cnt[p] = 0;
+    uint32_t distinct_n = 0, e = j;
+    for (;;) {
+        const uint32_t tj = pk_t(pk[j]);
+        while (e < n && pk_t(pk[e]) - tj < TW) {                // extend the end
+            if (cnt[pk_p(pk[e]) & 127u]++ == 0) ++distinct_n;
+            ++e;
+        }
+        if (distinct_n >= N) return true;
+        if (j == 0) return false;
+        const uint32_t tp = pk_t(pk[j - 1]);
+        if (ts - tp >= TW) return false;
+        // the previous start: add its hits, drop hits at or past tp + TW
+        uint32_t nj = j - 1;
+        while (nj > 0 && pk_t(pk[nj - 1]) == tp) --nj;
+        for (uint32_t q = nj; q < j; ++q)
+            if (cnt[pk_p(pk[q]) & 127u]++ == 0) ++distinct_n;
+        while (e > j && pk_t(pk[e - 1]) - tp >= TW) {
+            --e;
+            if (--cnt[pk_p(pk[e]) & 127u] == 0) --distinct_n;
+        }
+        j = nj;
+    }
+}
 
 // The core is keys[c0, c1) (t_rel in [H, H + core width)).
 template <int CAP, int NC, bool SMEM_DT>
@@ -840,6 +890,8 @@ __device__ CoreOut tile_trigger(TileCtx &cx, const uint64_t *keys, uint32_t n, u
                 if (pk_p(kj) != pi && cx.floor_s[pk_p(kj)] == fi) { seed = true; break; }
             }
         }
+        // level 0 (N hits within TW) before the seed triggers count
+        if (tp.l0_hits && seed && in) seed = level0_pass(pk, n, i, tp.l0_hits, tp.l0_window, tp.l0_distinct != 0);
         // halo hits past the core are neighbours only, never seeds here
         const uint32_t m = __ballot_sync(0xffffffffu, seed && in);
         if (lane == 0 && (base + warp * 32) < ncore) cx.mask[(base + warp * 32) >> 5] = m;
@@ -1348,6 +1400,9 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 
             tp.tau = d.tau;
             tp.q_seed = d.q_seed;
             tp.threshold = d.threshold;
+            tp.l0_hits = d.l0_hits;
+            tp.l0_window = d.l0_window;
+            tp.l0_distinct = d.l0_distinct;
             tp.dbg_merged = d.dbg_merged;
             tp.dbg_seedcnt = d.dbg_seedcnt;
             sl_w = d.tile_w;

@@ -493,3 +493,68 @@ def test_events_capacity_flag(pkg, params):
     assert int(stats["n_events"]) == int(ref.windows["n_hits"].sum())
     assert np.array_equal(trig["t"], ref.triggers["t"]) and np.array_equal(win["n_hits"], ref.windows["n_hits"])
     d.close()
+
+
+# ------------------------------------------------------------------ level 0
+
+@pytest.mark.parametrize("distinct", [0, 1])
+def test_level0_towers(pkg, params, distinct):
+    """N7TW1000 (and its distinct-PMT form) before the seed triggers, on
+    the KM3Net-It run with bursts and the NEMO slice: exact against the
+    oracle."""
+    for wl in (workload.cfg_km3(), workload.cfg_nemo()):
+        g = wl.detectors[0]
+        par = dict(params, l0_hits=7, l0_window_ns=1000, l0_distinct_pmts=distinct)
+        d = _det(pkg, g, par)
+        _, res = _run(pkg, d, [(s.t0, s.stream) for s in wl.submissions])
+        ref = oracle.run(g.xyz_mm, g.floor_id, par, wl.runs[0].hits, wl.run_slices[0])
+        for k in range(len(ref)):
+            _assert_same(res[k], ref[k], f"{g.name} level0 distinct={distinct} slice {k}")
+        d.close()
+
+
+@pytest.mark.parametrize("case", range(6))
+def test_level0_random_dense(pkg, params, case):
+    rng = np.random.Generator(np.random.PCG64(900 + case))
+    g = [workload.nemo_tower, workload.km3_tower][case % 2]()
+    par = dict(params, slice_ns=int(rng.choice([20_000, 200_000])), threshold=int(rng.integers(1, 5)),
+               l0_hits=int(rng.integers(2, 9)), l0_window_ns=int(rng.choice([30, 300, 1000, 4000])),
+               l0_distinct_pmts=int(case % 3 == 0))
+    t0 = 5_000_000
+    n = int(rng.integers(300, 3000))
+    t = rng.integers(t0 - 4000, t0 + 2 * par["slice_ns"] + 4000, n)
+    t[: n // 3] = t[n // 3: 2 * (n // 3)] + rng.integers(-200, 201, n // 3)
+    hits = np.zeros(n, workload.HIT_DTYPE)
+    hits["t"] = t
+    hits["pmt"] = rng.integers(0, g.n_pmt, n)
+    hits["charge"] = rng.integers(1, 500, n)
+    t0s = [t0, t0 + par["slice_ns"]]
+    full = _stream_from_hits(hits, g.n_pmt)
+    d = _det(pkg, g, par)
+    halo = d.halo_ns
+    _, res = _run(pkg, d, _subs_from_run(full, t0s, par["slice_ns"], halo))
+    ref = oracle.run(g.xyz_mm, g.floor_id, par, hits, t0s)
+    for k in range(2):
+        _assert_same(res[k], ref[k], f"case {case} slice {k}")
+    d.close()
+
+
+def test_level0_wide_detector(pkg, params):
+    g = _tower_array(3, 1)
+    par = dict(params, slice_ns=2_000_000, l0_hits=10, l0_window_ns=800)
+    t0 = workload.T_ORIGIN_NS
+    t0s = [t0, t0 + par["slice_ns"]]
+    full = workload.gen_stream(g, t0 - 3000, t0 + 2 * par["slice_ns"] + 3000, 120e3, n_muons=30, seed=8, stream=140)
+    d = _det(pkg, g, par)
+    _, res = _run(pkg, d, _subs_from_run(full, t0s, par["slice_ns"]))
+    ref = oracle.run(g.xyz_mm, g.floor_id, par, full.hits, t0s)
+    for k in range(2):
+        _assert_same(res[k], ref[k], f"wide level0 slice {k}")
+    d.close()
+
+
+def test_level0_parameter_checks(pkg, params):
+    with pytest.raises(pkg.TrigError):
+        _det(pkg, _tower_array(2, 1), dict(params, l0_hits=7, l0_distinct_pmts=1))   # > 128 PMTs
+    with pytest.raises(pkg.TrigError):
+        _det(pkg, workload.nemo_tower(), dict(params, l0_hits=7, l0_window_ns=0))

@@ -359,3 +359,74 @@ def test_events_bruteforce_and_window_counts():
                 want.append(h[:3])
         assert [tuple(x)[:3] for x in ev.tolist()] == [tuple(x) for x in want], case
         assert len(ev) == int(res.windows["n_hits"].sum()), case
+
+
+# ------------------------------------------------------------------ level 0
+
+def _fixture_hits(fx):
+    hits = np.zeros(len(fx["hits"]), oracle.HIT_DTYPE)
+    for i, (t, p, q) in enumerate(fx["hits"]):
+        hits[i] = (t, p, q, 0)
+    return hits
+
+
+def test_level0_golden_fixture():
+    fx = json.load(open(os.path.join(GOLDEN, "level0", "nemo32.json")))
+    g = workload.nemo_tower()
+    hits = _fixture_hits(fx)
+    base = dict(workload.DEFAULT_PARAMS, **fx["params"])
+    for mode, par in (("off", dict(base, l0_hits=0)), ("count", base), ("distinct", dict(base, l0_distinct_pmts=1))):
+        res = oracle.run(g.xyz_mm, g.floor_id, par, hits, fx["slices"])[0]
+        assert res.seeds["t"].tolist() == fx["expected_seed_times"][mode], mode
+
+
+def _level0_brute(sorted_hits, s, n_req, tw, distinct):
+    """Level 0 at sorted hit s by every window start a in (t_s - TW, t_s]."""
+    t = sorted_hits["t"]
+    ts = int(t[s])
+    for a in sorted(set(int(x) for x in t if ts - tw < x <= ts)):
+        inside = sorted_hits[(t >= a) & (t < a + tw)]
+        k = len(set(inside["pmt"].tolist())) if distinct else len(inside)
+        if k >= n_req:
+            return True
+    return False
+
+
+def test_level0_bruteforce_and_index_reading():
+    """Random dense slices: the oracle's level-0 keeps exactly the seeds a
+    direct window search keeps, with unchanged counts; for the hit count the
+    paper's index form t[i + N - 1] - t[i] < TW over consecutive merged
+    hits keeps the same seeds."""
+    rng = np.random.Generator(np.random.PCG64(123))
+    g = workload.nemo_tower()
+    for case in range(8):
+        n_req = int(rng.integers(2, 8))
+        tw = int(rng.choice([50, 200, 1000]))
+        distinct = int(case % 2)
+        par = dict(workload.DEFAULT_PARAMS, slice_ns=40_000, threshold=1, l0_window_ns=tw,
+                   l0_distinct_pmts=distinct, q_seed_adc=250)
+        t0 = 10_000_000
+        n = int(rng.integers(100, 500))
+        hits = np.zeros(n, oracle.HIT_DTYPE)
+        hits["t"] = rng.integers(t0 - 3000, t0 + par["slice_ns"] + 3000, n)
+        hits["pmt"] = rng.integers(0, 32, n)
+        hits["charge"] = rng.integers(1, 400, n)
+        off = oracle.run(g.xyz_mm, g.floor_id, dict(par, l0_hits=0), hits, [t0])[0]
+        on = oracle.run(g.xyz_mm, g.floor_id, dict(par, l0_hits=n_req), hits, [t0])[0]
+        sh = oracle.merge(hits)
+        key = list(zip(sh["t"].tolist(), sh["pmt"].tolist(), sh["charge"].tolist()))
+        keep = []
+        for sd in off.seeds.tolist():
+            s = key.index(tuple(sd[:3]))
+            if _level0_brute(sh, s, n_req, tw, distinct):
+                keep.append(sd)
+        assert on.seeds.tolist() == keep, case
+        if not distinct:
+            idx = []
+            for sd in off.seeds.tolist():
+                s = key.index(tuple(sd[:3]))
+                ok = any(0 <= i and i + n_req - 1 < len(sh) and int(sh["t"][i + n_req - 1]) - int(sh["t"][i]) < tw
+                         for i in range(s - n_req + 1, s + 1))
+                if ok:
+                    idx.append(sd)
+            assert idx == keep, case
