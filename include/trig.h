@@ -73,7 +73,8 @@ typedef struct {
     uint32_t n_pmt;
     const int32_t *xyz_mm;      /* host, 3 * n_pmt: x, y, z of PMT p       */
     const uint32_t *floor_id;   /* host, n_pmt                              */
-    const uint32_t *tower_id;   /* host, n_pmt, informational (may be NULL) */
+    const uint32_t *tower_id;   /* host, n_pmt, or NULL (one tower): groups
+                                   floors for the consecutive-floor test */
 } trig_geometry;
 
 /* Trigger constants.  The paper names the primitives (QTRIG charge
@@ -98,7 +99,29 @@ typedef struct {
     uint32_t l0_hits;
     uint32_t l0_window_ns;
     uint32_t l0_distinct_pmts;
-    uint32_t l0_reserved;       /* 0 */
+    /* Seed rule.  0: charge >= q_seed_adc, or a hit on another PMT of the
+     * same floor within floor_tau_ns.  1: the paper's combination of
+     * coincidences ("Sorting and triggering in GPU", "Results and
+     * perspectives": [SC and AFC] or [FC and AFC]): a hit is a seed iff a
+     * hit on a consecutive floor of its tower lies within afc_window_ns
+     * (AFC), and a hit on an adjacent PMT within sc_window_ns (SC) or on
+     * another PMT of its floor within fc_window_ns (FC).  Adjacent PMTs:
+     * different PMTs of one floor at most sc_dist_mm apart.  Consecutive
+     * floors: neighbours when a tower's floors (trig_geometry.tower_id,
+     * NULL = one tower) are ordered by the z of their lowest PMT, ties by
+     * floor_id.  Level 0 applies after either rule; with threshold = 1
+     * every seed fires (c(s) >= 1 always), which is the paper's trigger
+     * ladder N7TW, then [SC and AFC] or [FC and AFC]. */
+    uint32_t seed_rule;
+    uint32_t sc_window_ns;      /* <= 60000 */
+    uint32_t fc_window_ns;      /* <= 60000 */
+    uint32_t afc_window_ns;     /* <= 60000 */
+    uint32_t sc_dist_mm;
+    /* 1: c(s) counts the different PMTs among the causally related hits
+     * (the distinct-PMT variant, robust to a single PMT's bursts; n_pmt
+     * must be at most 128); 0: c(s) counts hits. */
+    uint32_t count_distinct_pmts;
+    uint32_t reserved;          /* 0 */
 } trig_params;
 
 /* A fired seed: its hit and causal count c(s). 16 bytes. */

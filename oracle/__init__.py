@@ -59,7 +59,13 @@ class _Params(ctypes.Structure):
         ("l0_hits", ctypes.c_uint32),
         ("l0_window_ns", ctypes.c_uint32),
         ("l0_distinct_pmts", ctypes.c_uint32),
-        ("l0_reserved", ctypes.c_uint32),
+        ("seed_rule", ctypes.c_uint32),
+        ("sc_window_ns", ctypes.c_uint32),
+        ("fc_window_ns", ctypes.c_uint32),
+        ("afc_window_ns", ctypes.c_uint32),
+        ("sc_dist_mm", ctypes.c_uint32),
+        ("count_distinct_pmts", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32),
     ]
 
 
@@ -89,7 +95,8 @@ def _load():
         lib.oracle_merge.restype = ctypes.c_int
         lib.oracle_merge.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p]
         lib.oracle_run.restype = ctypes.c_int
-        lib.oracle_run.argtypes = [ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(_Params),
+        lib.oracle_run.argtypes = [ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.POINTER(_Params),
                                    ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_uint32,
                                    ctypes.c_int, ctypes.POINTER(_SliceResult)]
         lib.oracle_free.restype = None
@@ -141,17 +148,22 @@ class SliceResult:
     windows: np.ndarray     # WINDOW_DTYPE
 
 
-def run(xyz_mm, floor_id, params: dict, hits: np.ndarray, slice_t0s, threads: int = 0) -> list[SliceResult]:
-    """Trigger every slice [t0, t0 + slice_ns) against the whole hit set."""
+def run(xyz_mm, floor_id, params: dict, hits: np.ndarray, slice_t0s, threads: int = 0,
+        tower_id=None) -> list[SliceResult]:
+    """Trigger every slice [t0, t0 + slice_ns) against the whole hit set.
+    tower_id (per PMT, optional) groups floors into towers for the
+    consecutive-floor coincidence; None puts every floor in one tower."""
     lib = _load()
     xyz = np.ascontiguousarray(xyz_mm, np.int32)
     fl = np.ascontiguousarray(floor_id, np.uint32)
+    tw = None if tower_id is None else np.ascontiguousarray(tower_id, np.uint32)
     h = np.ascontiguousarray(hits, HIT_DTYPE)
     t0s = np.ascontiguousarray(np.asarray(slice_t0s, np.int64))
     n = len(t0s)
     res = (_SliceResult * max(n, 1))()
     par = _params(params)
-    rc = lib.oracle_run(xyz.shape[0], xyz.ctypes.data, fl.ctypes.data, ctypes.byref(par), h.ctypes.data,
+    rc = lib.oracle_run(xyz.shape[0], xyz.ctypes.data, fl.ctypes.data, None if tw is None else tw.ctypes.data,
+                        ctypes.byref(par), h.ctypes.data,
                         len(h), t0s.ctypes.data, n, int(threads), res)
     if rc:
         raise RuntimeError(f"oracle_run failed ({rc})")

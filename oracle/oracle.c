@@ -33,6 +33,19 @@
  *           window [a, a + TW) that contains it holds at least N hits (N
  *           different PMTs).  Only windows starting at a hit need testing:
  *           moving a window's start up to its first hit loses nothing.
+ *   ladder  (seed_rule 1, the combination of "Sorting and triggering in
+ *           GPU" and "Results and perspectives": N7TW1000, then [SC and
+ *           AFC] or [FC and AFC]) replaces the seed rule above: hit s is a
+ *           seed iff some hit on a consecutive floor of its tower lies within
+ *           the AFC window (AFC), and some hit on an adjacent PMT lies within
+ *           the SC window (SC) or some hit on another PMT of its floor within
+ *           the FC window (FC).  Adjacent PMTs: different PMTs of one floor
+ *           at most sc_dist apart.  Consecutive floors: floors of one tower
+ *           next to each other when the tower's floors are ordered by
+ *           height (the z of a floor's lowest PMT), ties by floor id.
+ *           Level 0 then applies as above.
+ *   distinct (count_distinct_pmts, the distinct-PMT variant of the count):
+ *           c(s) = the number of different PMTs among the hits j above.
  *   trigger seeds with c(s) >= threshold, in (t, pmt, charge) order.
  *   windows [t_s - h, t_s + h] around every trigger (the 6 us window centred
  *           on the seed), merged while lo_next <= hi_cur + 1; n_hits counts
@@ -133,6 +146,9 @@ static uint64_t lower_bound_t(const oracle_hit *s, uint64_t n, int64_t t)
 typedef struct {
     uint32_t n_pmt;
     const uint32_t *floor_id;
+    const uint32_t *tower_id;   /* n_pmt, or NULL: a single tower */
+    const int32_t *xyz_mm;
+    const uint32_t *floor_rank; /* n_pmt: rank of p's floor among its tower's floors */
     const int32_t *dt;          /* n_pmt * n_pmt, exact dt_max */
     const oracle_params *par;
     const oracle_hit *sorted;
@@ -183,6 +199,53 @@ static int level0_pass(const run_job *job, uint64_t s)
     return 0;
 }
 
+static uint32_t tower_of(const run_job *job, uint32_t p)
+{
+    return job->tower_id ? job->tower_id[p] : 0u;
+}
+
+/* Different PMTs of one floor at most sc_dist_mm apart. */
+static int adjacent_pmts(const run_job *job, uint32_t p, uint32_t q)
+{
+    if (p == q || job->floor_id[p] != job->floor_id[q]) return 0;
+    const int64_t dx = (int64_t)job->xyz_mm[3 * p] - job->xyz_mm[3 * q];
+    const int64_t dy = (int64_t)job->xyz_mm[3 * p + 1] - job->xyz_mm[3 * q + 1];
+    const int64_t dz = (int64_t)job->xyz_mm[3 * p + 2] - job->xyz_mm[3 * q + 2];
+    const int64_t r = job->par->sc_dist_mm;
+    return dx * dx + dy * dy + dz * dz <= r * r;
+}
+
+/* PMTs on two floors of one tower that are next to each other in height. */
+static int consecutive_floors(const run_job *job, uint32_t p, uint32_t q)
+{
+    if (tower_of(job, p) != tower_of(job, q)) return 0;
+    const int64_t a = job->floor_rank[p], b = job->floor_rank[q];
+    return a - b == 1 || b - a == 1;
+}
+
+/* The paper's combination at H[s]: [SC and AFC] or [FC and AFC]. */
+static int ladder_seed(const run_job *job, uint64_t s)
+{
+    const oracle_params *par = job->par;
+    const oracle_hit *H = job->sorted;
+    const uint64_t n = job->n;
+    const int64_t ts = H[s].t_ns;
+    int64_t wmax = par->sc_window_ns;
+    if (par->fc_window_ns > wmax) wmax = par->fc_window_ns;
+    if (par->afc_window_ns > wmax) wmax = par->afc_window_ns;
+    int sc = 0, fc = 0, afc = 0;
+    for (uint64_t j = lower_bound_t(H, n, ts - wmax); j < n && H[j].t_ns <= ts + wmax; ++j) {
+        if (j == s) continue;
+        int64_t d = H[j].t_ns - ts;
+        if (d < 0) d = -d;
+        const uint32_t p = H[s].pmt, q = H[j].pmt;
+        if (d <= par->sc_window_ns && adjacent_pmts(job, p, q)) sc = 1;
+        if (d <= par->fc_window_ns && p != q && job->floor_id[p] == job->floor_id[q]) fc = 1;
+        if (d <= par->afc_window_ns && consecutive_floors(job, p, q)) afc = 1;
+    }
+    return (sc && afc) || (fc && afc);
+}
+
 static int run_slice(run_job *job, uint32_t k)
 {
     const oracle_params *par = job->par;
@@ -200,8 +263,8 @@ static int run_slice(run_job *job, uint32_t k)
     uint64_t last = lower_bound_t(H, n, T1);
     for (uint64_t s = first; s < last; ++s) {
         const oracle_hit *hs = &H[s];
-        int is_seed = hs->charge >= par->q_seed_adc;
-        if (!is_seed) {
+        int is_seed = par->seed_rule == 1 ? ladder_seed(job, s) : hs->charge >= par->q_seed_adc;
+        if (!is_seed && par->seed_rule != 1) {
             for (uint64_t j = lower_bound_t(H, n, hs->t_ns - tau); j < n && H[j].t_ns <= hs->t_ns + tau; ++j) {
                 if (j == s) continue;
                 if (H[j].pmt != hs->pmt && job->floor_id[H[j].pmt] == job->floor_id[hs->pmt]) {
@@ -213,12 +276,16 @@ static int run_slice(run_job *job, uint32_t k)
         if (is_seed && par->l0_hits > 0) is_seed = level0_pass(job, s);
         if (!is_seed) continue;
         uint32_t c = 0;
+        unsigned char seen[4096];
+        if (par->count_distinct_pmts) memset(seen, 0, job->n_pmt);
         for (uint64_t j = lower_bound_t(H, n, hs->t_ns - W); j < n && H[j].t_ns <= hs->t_ns + W; ++j) {
             int64_t lim = job->dt[(size_t)hs->pmt * job->n_pmt + H[j].pmt];
             if (lim > W) lim = W;
             int64_t dtj = H[j].t_ns - hs->t_ns;
             if (dtj < 0) dtj = -dtj;
-            if (dtj <= lim) ++c;
+            if (dtj > lim) continue;
+            if (!par->count_distinct_pmts) ++c;
+            else if (!seen[H[j].pmt]) { seen[H[j].pmt] = 1; ++c; }
         }
         oracle_seed sd = {hs->t_ns, hs->pmt, hs->charge, c};
         if (push_seed(&res->seeds, &res->n_seeds, &cap_s, sd)) return -2;
@@ -265,9 +332,42 @@ static void *run_worker(void *arg)
     return NULL;
 }
 
-int oracle_run(uint32_t n_pmt, const int32_t *xyz_mm, const uint32_t *floor_id, const oracle_params *par,
-               const oracle_hit *hits, uint64_t n_hits, const int64_t *slice_t0, uint32_t n_slices,
-               int n_threads, oracle_slice_result *out)
+/* Floor order of the towers: rank[p] = how many different floors of p's
+ * tower lie below p's floor, floors compared by (height, floor id), the
+ * height of a floor being the z of its lowest PMT. */
+static void floor_ranks(uint32_t n_pmt, const int32_t *xyz_mm, const uint32_t *floor_id, const uint32_t *tower_id,
+                        uint32_t *rank)
+{
+    int64_t *height = (int64_t *)malloc(n_pmt * sizeof(int64_t));
+    unsigned char *counted = (unsigned char *)malloc(n_pmt);
+    if (!height || !counted) { free(height); free(counted); memset(rank, 0, n_pmt * sizeof(uint32_t)); return; }
+    for (uint32_t p = 0; p < n_pmt; ++p) {
+        height[p] = xyz_mm[3 * p + 2];
+        for (uint32_t q = 0; q < n_pmt; ++q)
+            if (floor_id[q] == floor_id[p] && xyz_mm[3 * q + 2] < height[p]) height[p] = xyz_mm[3 * q + 2];
+    }
+    for (uint32_t p = 0; p < n_pmt; ++p) {
+        const uint32_t tp = tower_id ? tower_id[p] : 0u;
+        memset(counted, 0, n_pmt);
+        rank[p] = 0;
+        for (uint32_t q = 0; q < n_pmt; ++q) {
+            if ((tower_id ? tower_id[q] : 0u) != tp) continue;
+            const int below = height[q] < height[p] || (height[q] == height[p] && floor_id[q] < floor_id[p]);
+            if (!below) continue;
+            /* count each floor once: its first PMT of this tower */
+            uint32_t first = q;
+            for (uint32_t r = 0; r < q; ++r)
+                if (floor_id[r] == floor_id[q] && (tower_id ? tower_id[r] : 0u) == tp) { first = r; break; }
+            if (!counted[first]) { counted[first] = 1; ++rank[p]; }
+        }
+    }
+    free(height);
+    free(counted);
+}
+
+int oracle_run(uint32_t n_pmt, const int32_t *xyz_mm, const uint32_t *floor_id, const uint32_t *tower_id,
+               const oracle_params *par, const oracle_hit *hits, uint64_t n_hits, const int64_t *slice_t0,
+               uint32_t n_slices, int n_threads, oracle_slice_result *out)
 {
     if (!xyz_mm || !floor_id || !par || (n_hits && !hits) || (n_slices && (!slice_t0 || !out)))
         return -1;
@@ -279,12 +379,18 @@ int oracle_run(uint32_t n_pmt, const int32_t *xyz_mm, const uint32_t *floor_id, 
     oracle_hit *sorted = (oracle_hit *)malloc((n_hits ? n_hits : 1) * sizeof(oracle_hit));
     if (!dt || !sorted) { free(dt); free(sorted); return -2; }
     oracle_dtmax(n_pmt, xyz_mm, par->tol_ns, par->n_num, par->n_den, dt);
+    uint32_t *rank = (uint32_t *)malloc((n_pmt ? n_pmt : 1) * sizeof(uint32_t));
+    if (!rank) { free(dt); free(sorted); return -2; }
+    if (par->seed_rule == 1) floor_ranks(n_pmt, xyz_mm, floor_id, tower_id, rank);
     int rc = oracle_merge(hits, n_hits, sorted);
-    if (rc) { free(dt); free(sorted); return rc; }
+    if (rc) { free(dt); free(sorted); free(rank); return rc; }
 
     run_job job;
     job.n_pmt = n_pmt;
     job.floor_id = floor_id;
+    job.tower_id = tower_id;
+    job.xyz_mm = xyz_mm;
+    job.floor_rank = rank;
     job.dt = dt;
     job.par = par;
     job.sorted = sorted;
@@ -308,6 +414,7 @@ int oracle_run(uint32_t n_pmt, const int32_t *xyz_mm, const uint32_t *floor_id, 
     pthread_mutex_destroy(&job.mu);
     free(dt);
     free(sorted);
+    free(rank);
     if (job.error) { oracle_free(out, n_slices); return job.error; }
     return 0;
 }

@@ -26,7 +26,14 @@ typedef struct {
     uint32_t l0_hits;         /* level 0: N hits (0 = off) ...              */
     uint32_t l0_window_ns;    /* ... within TW ns ...                       */
     uint32_t l0_distinct_pmts;/* ... counting different PMTs only if 1      */
-    uint32_t l0_reserved;
+    uint32_t seed_rule;       /* 0: QTRIG or floor coincidence within tau;
+                                 1: [SC and AFC] or [FC and AFC]            */
+    uint32_t sc_window_ns;    /* SC: adjacent PMTs, |dt| <= this            */
+    uint32_t fc_window_ns;    /* FC: same floor, |dt| <= this               */
+    uint32_t afc_window_ns;   /* AFC: consecutive floors, |dt| <= this      */
+    uint32_t sc_dist_mm;      /* adjacent: same floor, at most this apart   */
+    uint32_t count_distinct_pmts; /* c(s) counts different PMTs if 1        */
+    uint32_t reserved;
 } oracle_params;
 
 typedef struct {
@@ -53,7 +60,8 @@ int64_t oracle_dtmax_pair(int64_t d2_mm2, uint32_t tol_ns, uint32_t n_num, uint3
 int oracle_dtmax(uint32_t n_pmt, const int32_t *xyz_mm, uint32_t tol_ns, uint32_t n_num, uint32_t n_den,
                  int32_t *dt_out);
 int oracle_merge(const oracle_hit *hits, uint64_t n, oracle_hit *sorted_out);
-int oracle_run(uint32_t n_pmt, const int32_t *xyz_mm, const uint32_t *floor_id, const oracle_params *par,
+int oracle_run(uint32_t n_pmt, const int32_t *xyz_mm, const uint32_t *floor_id, const uint32_t *tower_id,
+               const oracle_params *par,
                const oracle_hit *hits, uint64_t n_hits, const int64_t *slice_t0, uint32_t n_slices,
                int n_threads, oracle_slice_result *out);
 void oracle_free(oracle_slice_result *r, uint32_t n_slices);

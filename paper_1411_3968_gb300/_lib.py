@@ -68,7 +68,10 @@ class trig_params(ctypes.Structure):
                 ("n_num", ctypes.c_uint32), ("n_den", ctypes.c_uint32), ("corr_window_ns", ctypes.c_uint32),
                 ("threshold", ctypes.c_uint32), ("win_half_ns", ctypes.c_uint32), ("slice_ns", ctypes.c_int64),
                 ("l0_hits", ctypes.c_uint32), ("l0_window_ns", ctypes.c_uint32), ("l0_distinct_pmts", ctypes.c_uint32),
-                ("l0_reserved", ctypes.c_uint32)]
+                ("seed_rule", ctypes.c_uint32), ("sc_window_ns", ctypes.c_uint32),
+                ("fc_window_ns", ctypes.c_uint32), ("afc_window_ns", ctypes.c_uint32),
+                ("sc_dist_mm", ctypes.c_uint32), ("count_distinct_pmts", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
 
 
 class trig_result(ctypes.Structure):

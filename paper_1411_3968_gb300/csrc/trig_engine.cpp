@@ -122,6 +122,7 @@ static void free_det_dev(trig_detector *d)
     cudaFree(d->dev.dt_exact);
     cudaFree(d->dev.floor);
     cudaFree(d->dev.dmax_row);
+    cudaFree(d->dev.rel);
     cudaFree(d->d_xyz);
     d->dev = DetDev{};
     d->d_xyz = nullptr;
@@ -138,8 +139,60 @@ static int check_params(const trig_params *p)
     if (p->l0_hits > 0 && (p->l0_window_ns == 0 || p->l0_window_ns > 60000))
         return fail(TRIG_EINVAL, "l0_window_ns must be in [1, 60000] when l0_hits > 0");
     if (p->l0_hits > 4096) return fail(TRIG_EINVAL, "l0_hits > 4096");
-    if (p->l0_distinct_pmts > 1 || p->l0_reserved != 0) return fail(TRIG_EINVAL, "l0_distinct_pmts is 0 or 1, l0_reserved 0");
+    if (p->l0_distinct_pmts > 1) return fail(TRIG_EINVAL, "l0_distinct_pmts is 0 or 1");
+    if (p->seed_rule > 1) return fail(TRIG_EINVAL, "seed_rule is 0 or 1");
+    if (p->sc_window_ns > 60000 || p->fc_window_ns > 60000 || p->afc_window_ns > 60000)
+        return fail(TRIG_EINVAL, "sc_window_ns, fc_window_ns and afc_window_ns must be <= 60000");
+    if (p->count_distinct_pmts > 1 || p->reserved != 0)
+        return fail(TRIG_EINVAL, "count_distinct_pmts is 0 or 1, reserved 0");
     return TRIG_OK;
+}
+
+// Relations of the coincidence seed rule, rel[p * P + q] (kRel* bits):
+// another PMT of the same floor; adjacent (same floor, at most sc_dist_mm
+// apart); on a consecutive floor of the same tower.  A tower's floors are
+// ordered by the z of their lowest PMT, then by floor id.
+static std::vector<uint8_t> pmt_relations(const trig_geometry *g, uint32_t sc_dist_mm)
+{
+    const uint32_t P = g->n_pmt;
+    auto tower = [&](uint32_t p) { return g->tower_id ? g->tower_id[p] : 0u; };
+    std::map<uint32_t, int32_t> low;                    // floor id -> z of its lowest PMT
+    for (uint32_t p = 0; p < P; ++p) {
+        auto it = low.find(g->floor_id[p]);
+        const int32_t z = g->xyz_mm[3 * p + 2];
+        if (it == low.end()) low.emplace(g->floor_id[p], z);
+        else it->second = std::min(it->second, z);
+    }
+    // per tower: its floors in height order -> position in that order
+    std::map<uint32_t, std::vector<std::pair<int32_t, uint32_t>>> floors;
+    for (uint32_t p = 0; p < P; ++p) floors[tower(p)].push_back({low[g->floor_id[p]], g->floor_id[p]});
+    std::map<std::pair<uint32_t, uint32_t>, int64_t> level;    // (tower, floor id) -> position
+    for (auto &tf : floors) {
+        auto &v = tf.second;
+        std::sort(v.begin(), v.end());
+        v.erase(std::unique(v.begin(), v.end()), v.end());
+        for (size_t i = 0; i < v.size(); ++i) level[{tf.first, v[i].second}] = (int64_t)i;
+    }
+    std::vector<int64_t> lv(P);
+    for (uint32_t p = 0; p < P; ++p) lv[p] = level[{tower(p), g->floor_id[p]}];
+    const int64_t r2 = (int64_t)sc_dist_mm * sc_dist_mm;
+    std::vector<uint8_t> rel((size_t)P * P, 0);
+    for (uint32_t p = 0; p < P; ++p)
+        for (uint32_t q = 0; q < P; ++q) {
+            uint8_t r = 0;
+            if (p != q && g->floor_id[p] == g->floor_id[q]) {
+                r |= kRelFloor;
+                int64_t d2 = 0;
+                for (int c = 0; c < 3; ++c) {
+                    const int64_t dc = (int64_t)g->xyz_mm[3 * p + c] - g->xyz_mm[3 * q + c];
+                    d2 += dc * dc;
+                }
+                if (d2 <= r2) r |= kRelAdjacent;
+            }
+            if (tower(p) == tower(q) && (lv[p] - lv[q] == 1 || lv[q] - lv[p] == 1)) r |= kRelNextFloor;
+            rel[(size_t)p * P + q] = r;
+        }
+    return rel;
 }
 
 extern "C" int trig_create(const trig_geometry *g, const trig_params *params, trig_detector **out)
@@ -153,6 +206,8 @@ extern "C" int trig_create(const trig_geometry *g, const trig_params *params, tr
     const uint32_t P = g->n_pmt;
     if (params->l0_hits > 0 && params->l0_distinct_pmts && P > 128)
         return fail(TRIG_EINVAL, "the distinct-PMT level 0 needs n_pmt <= 128");
+    if (params->count_distinct_pmts && P > 128)
+        return fail(TRIG_EINVAL, "the distinct-PMT causal count needs n_pmt <= 128");
     for (uint32_t i = 0; i < 3 * P; ++i)
         if (g->xyz_mm[i] > 100000000 || g->xyz_mm[i] < -100000000)
             return fail(TRIG_EINVAL, "coordinates must lie within +-1e8 mm");
@@ -177,7 +232,8 @@ extern "C" int trig_create(const trig_geometry *g, const trig_params *params, tr
     cudaError_t e;
     if ((e = cudaMalloc(&d->dev.dt, PP * 2)) || (e = cudaMalloc(&d->dev.dt_exact, PP * 4)) ||
         (e = cudaMalloc(&d->dev.floor, (size_t)P * 2)) || (e = cudaMalloc(&d->dev.dmax_row, (size_t)P * 2)) ||
-        (e = cudaMalloc(&d->d_xyz, (size_t)3 * P * 4))) {
+        (e = cudaMalloc(&d->d_xyz, (size_t)3 * P * 4)) ||
+        (params->seed_rule == 1 && (e = cudaMalloc(&d->dev.rel, PP)))) {
         free_det_dev(d.get());
         return cuda_fail(e, "trig_create: cudaMalloc");
     }
@@ -187,7 +243,10 @@ extern "C" int trig_create(const trig_geometry *g, const trig_params *params, tr
         return cuda_fail(e, "trig_create: stream");
     }
     std::vector<uint16_t> dmax(P);
+    std::vector<uint8_t> rel;
+    if (params->seed_rule == 1) rel = pmt_relations(g, params->sc_dist_mm);
     e = cudaMemcpyAsync(d->d_xyz, g->xyz_mm, (size_t)3 * P * 4, cudaMemcpyHostToDevice, st);
+    if (!e && !rel.empty()) e = cudaMemcpyAsync(d->dev.rel, rel.data(), PP, cudaMemcpyHostToDevice, st);
     if (!e) e = cudaMemcpyAsync(d->dev.floor, floor_dense.data(), (size_t)P * 2, cudaMemcpyHostToDevice, st);
     if (!e)
         e = launch_dtmax(d->d_xyz, P, params->tol_ns, params->n_num, params->n_den, params->corr_window_ns,
@@ -202,11 +261,14 @@ extern "C" int trig_create(const trig_geometry *g, const trig_params *params, tr
     // the tile halo covers every hit a core hit's seed test, level 0 and
     // causal count look at; the accepted input halo as well
     const uint32_t l0w = params->l0_hits > 0 ? params->l0_window_ns : 0u;
-    uint32_t H = std::max(params->floor_tau_ns, l0w);
+    const uint32_t cw = params->seed_rule == 1
+                            ? std::max({params->sc_window_ns, params->fc_window_ns, params->afc_window_ns})
+                            : params->floor_tau_ns;
+    uint32_t H = std::max(cw, l0w);
     for (uint16_t v : dmax) H = std::max<uint32_t>(H, v);
     d->tile_halo = H;
     d->in_halo = std::max<int64_t>({(int64_t)params->corr_window_ns, (int64_t)params->win_half_ns,
-                                    (int64_t)params->floor_tau_ns, (int64_t)l0w});
+                                    (int64_t)cw, (int64_t)l0w});
     d->q = std::make_shared<DetQueue>();
     TileConfig cached{};
     if (tune_cache_lookup(P, cached)) {
@@ -362,6 +424,12 @@ static int plan_into(const trig_slice_dev *sl, uint32_t n, uintptr_t base, const
         d.l0_hits = det->par.l0_hits;
         d.l0_window = det->par.l0_window_ns;
         d.l0_distinct = det->par.l0_distinct_pmts;
+        d.seed_rule = det->par.seed_rule;
+        d.sc_w = det->par.sc_window_ns;
+        d.fc_w = det->par.fc_window_ns;
+        d.afc_w = det->par.afc_window_ns;
+        d.count_distinct = det->par.count_distinct_pmts;
+        d.rel = det->dev.rel;
         d.win_half = det->par.win_half_ns;
         d.t0 = x.t0_ns;
         d.slice_ns = det->par.slice_ns;

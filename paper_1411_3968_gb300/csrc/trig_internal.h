@@ -27,7 +27,13 @@ struct DetDev {
     int32_t *dt_exact;    // [P*P] exact dt_max
     uint16_t *floor;      // [P] dense floor index
     uint16_t *dmax_row;   // [P] max_q min(dt_max[p][q], W)
+    uint8_t *rel;         // [P*P] relation of PMTs p, q (seed rule 1 only), kRel* bits
 };
+
+// PMT relations of the coincidence seed rule.
+constexpr uint8_t kRelFloor = 1;        // another PMT of the same floor (FC)
+constexpr uint8_t kRelAdjacent = 2;     // adjacent PMT: same floor, within sc_dist (SC)
+constexpr uint8_t kRelNextFloor = 4;    // PMT on a consecutive floor of the same tower (AFC)
 
 // Per-slice descriptor in device scratch, written by the host each run.
 struct SliceDesc {
@@ -45,7 +51,10 @@ struct SliceDesc {
     uint32_t l0_hits;       // level 0: N hits (0 = off) within l0_window ns,
     uint32_t l0_window;     //   of different PMTs if l0_distinct
     uint32_t l0_distinct;
-    uint32_t pad_l0;
+    uint32_t seed_rule;     // 0: charge or floor coincidence; 1: [SC and AFC] or [FC and AFC]
+    uint32_t sc_w, fc_w, afc_w;     // coincidence windows of seed rule 1 (ns)
+    uint32_t count_distinct;        // c(s) counts different PMTs (P <= 128)
+    const uint8_t *rel;     // [P*P] kRel* bits (seed rule 1)
     int64_t t0;
     int64_t slice_ns;
     int64_t in_lo, in_hi;   // accepted hit times [in_lo, in_hi)

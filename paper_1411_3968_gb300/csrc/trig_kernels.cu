@@ -777,9 +777,89 @@ struct CoreOut {
 struct TrigParams {
     uint32_t H, tau, q_seed, threshold;
     uint32_t l0_hits, l0_window, l0_distinct;
+    uint32_t seed_rule, sc_w, fc_w, afc_w, count_distinct;
+    const uint8_t *rel;
     trig_hit *dbg_merged;
     uint32_t *dbg_seedcnt;
 };
+
+// Seed rule 1 at sorted index i: [SC and AFC] or [FC and AFC].  Walks the
+// keys within the widest of the three windows on both sides (all staged:
+// the tile halo covers it) and looks each pair up in the PMT relation row
+// of p_i.
+__device__ __noinline__ bool coincidence_seed(const uint32_t *pk, uint32_t n, uint32_t i, const uint8_t *rel,
+                                              uint32_t P, uint32_t sc, uint32_t fc, uint32_t afc)
+{
+    const uint32_t ki = pk[i], ti = pk_t(ki), pi = pk_p(ki);
+    if (!CHECK(14, pi, P)) return false;
+    const uint8_t *row = rel + (size_t)pi * P;
+    const uint32_t wmax = max(sc, max(fc, afc));
+    bool c = false, a = false;
+    for (uint32_t j = i + 1; j < n; ++j) {
+        const uint32_t kj = pk[j], d = pk_t(kj) - ti;
+        if (d > wmax) break;
+        if (!CHECK(15, pk_p(kj), P)) continue;
+        const uint32_t r = __ldg(row + pk_p(kj));
+        c = c || ((r & kRelAdjacent) && d <= sc) || ((r & kRelFloor) && d <= fc);
+        a = a || ((r & kRelNextFloor) && d <= afc);
+        if (a && c) return true;
+    }
+    for (uint32_t j = i; j-- > 0;) {
+        const uint32_t kj = pk[j], d = ti - pk_t(kj);
+        if (d > wmax) break;
+        if (!CHECK(15, pk_p(kj), P)) continue;
+        const uint32_t r = __ldg(row + pk_p(kj));
+        c = c || ((r & kRelAdjacent) && d <= sc) || ((r & kRelFloor) && d <= fc);
+        a = a || ((r & kRelNextFloor) && d <= afc);
+        if (a && c) return true;
+    }
+    return false;
+}
+
+// Distinct-PMT causal count (P <= 128): c(s) = the number of different
+// PMTs among the keys j with |t_j - t_s| <= min(dt_max[p_s][p_j], W).
+// Eight lanes per seed each collect a 128-bit PMT set over every eighth key
+// of the seed's scan range; the sets are OR-ed and counted.
+template <int NC, bool SMEM_DT>
+__device__ __noinline__ void count_distinct_pmts(const TileCtx &cx, const uint32_t *pk, uint32_t n, uint32_t ns,
+                                                 const uint16_t *seed_idx, const uint32_t *swin, uint16_t *seed_cnt)
+{
+    constexpr uint32_t G = 8, NG = NC / G;
+    const uint32_t tid = threadIdx.x, gl = tid & (G - 1u), gid = tid / G, P = cx.P;
+    const uint32_t rounds = (ns + NG - 1) / NG;
+    for (uint32_t r = 0; r < rounds; ++r) {
+        const uint32_t k = r * NG + gid;
+        uint32_t m0 = 0, m1 = 0, m2 = 0, m3 = 0;
+        if (k < ns) {
+            const uint32_t w = swin[k];
+            const uint32_t ks = pk[seed_idx[k]];
+            const uint32_t ts = pk_t(ks), ps = pk_p(ks);
+            const uint32_t j0 = w & 0xffffu, j1 = w >> 16;
+            if (CHECK(12, j1, n + 1) && CHECK(13, ps, P)) {
+                const uint16_t *row_s = cx.dt_s + (size_t)ps * P;
+                const uint16_t *row_g = cx.dt_g + (size_t)ps * P;
+                for (uint32_t q = j0 + gl; q < j1; q += G) {
+                    const uint32_t kj = pk[q], tj = pk_t(kj), pj = pk_p(kj);
+                    if (!CHECK(11, pj, P)) continue;
+                    const uint32_t lim = SMEM_DT ? (uint32_t)row_s[pj] : (uint32_t)__ldg(row_g + pj);
+                    if ((tj > ts ? tj - ts : ts - tj) > lim) continue;
+                    const uint32_t b = 1u << (pj & 31u), h = pj >> 5;
+                    m0 |= h == 0 ? b : 0u;
+                    m1 |= h == 1 ? b : 0u;
+                    m2 |= h == 2 ? b : 0u;
+                    m3 |= h == 3 ? b : 0u;
+                }
+            }
+        }
+        for (uint32_t off = G >> 1; off; off >>= 1) {
+            m0 |= __shfl_xor_sync(0xffffffffu, m0, off);
+            m1 |= __shfl_xor_sync(0xffffffffu, m1, off);
+            m2 |= __shfl_xor_sync(0xffffffffu, m2, off);
+            m3 |= __shfl_xor_sync(0xffffffffu, m3, off);
+        }
+        if (k < ns && gl == 0) seed_cnt[k] = (uint16_t)(__popc(m0) + __popc(m1) + __popc(m2) + __popc(m3));
+    }
+}
 
 // Level 0 at sorted index i: some window [t_j, t_j + TW) with
 // t_i - TW < t_j <= t_i holds at least N hits, or hits of N different PMTs
@@ -862,6 +942,10 @@ __device__ CoreOut tile_trigger(TileCtx &cx, const uint64_t *keys, uint32_t n, u
         const uint32_t fi = in ? cx.floor_s[pi] : 0u;
         bool seed = in && key_q(keys[i]) >= qseed;
         bool more_up = false, more_dn = false;
+        if (tp.seed_rule == 1) {
+            // the paper's combination of coincidences replaces the rule below
+            seed = in && coincidence_seed(pk, n, i, tp.rel, P, tp.sc_w, tp.fc_w, tp.afc_w);
+        } else {
 #pragma unroll
         for (uint32_t dd = 1; dd <= 2; ++dd) {
             uint32_t ku = __shfl_up_sync(0xffffffffu, ki, dd);
@@ -889,6 +973,7 @@ __device__ CoreOut tile_trigger(TileCtx &cx, const uint64_t *keys, uint32_t n, u
                 if (ti - pk_t(kj) > tau) break;
                 if (pk_p(kj) != pi && cx.floor_s[pk_p(kj)] == fi) { seed = true; break; }
             }
+        }
         }
         // level 0 (N hits within TW) before the seed triggers count
         if (tp.l0_hits && seed && in) seed = level0_pass(pk, n, i, tp.l0_hits, tp.l0_window, tp.l0_distinct != 0);
@@ -944,7 +1029,9 @@ __device__ CoreOut tile_trigger(TileCtx &cx, const uint64_t *keys, uint32_t n, u
     //    over the seed's scan range: a group of G lanes per seed (G from the
     //    tile's density), seeds dealt round-robin to the groups, four
     //    independent tests per lane in flight
-    {
+    if (tp.count_distinct) {
+        count_distinct_pmts<NC, SMEM_DT>(cx, pk, n, ns, seed_idx, swin, seed_cnt);
+    } else {
         // expected keys in a scan range: 2H + 1 ns at the tile's density
         const unsigned long long span_n = n ? (unsigned long long)pk_t(pk[n - 1]) + 1ull : 1ull;
         const unsigned long long est = (unsigned long long)(2u * tp.H + 1u) * n / span_n;
@@ -1371,7 +1458,9 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 
 
     // ---------------------------------------------------- consumer warps
     const SliceDesc *loaded = nullptr;
-    TrigParams tp{};
+    // the slice's trigger parameters live in shared memory (written by one
+    // thread when the slice changes), keeping registers for the tile phases
+    __shared__ TrigParams tp;
     int64_t sl_w = 0, sl_t0 = 0, sl_len = 0;
     uint64_t sl_rank0 = 0;
     for (uint32_t it = 0;; ++it) {
@@ -1396,15 +1485,23 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 
             cx.dt_g = d.dt;
             cx.P = P;
             loaded = &d;
-            tp.H = d.halo;
-            tp.tau = d.tau;
-            tp.q_seed = d.q_seed;
-            tp.threshold = d.threshold;
-            tp.l0_hits = d.l0_hits;
-            tp.l0_window = d.l0_window;
-            tp.l0_distinct = d.l0_distinct;
-            tp.dbg_merged = d.dbg_merged;
-            tp.dbg_seedcnt = d.dbg_seedcnt;
+            if (tid == 0) {
+                tp.H = d.halo;
+                tp.tau = d.tau;
+                tp.q_seed = d.q_seed;
+                tp.threshold = d.threshold;
+                tp.l0_hits = d.l0_hits;
+                tp.l0_window = d.l0_window;
+                tp.l0_distinct = d.l0_distinct;
+                tp.seed_rule = d.seed_rule;
+                tp.sc_w = d.sc_w;
+                tp.fc_w = d.fc_w;
+                tp.afc_w = d.afc_w;
+                tp.count_distinct = d.count_distinct;
+                tp.rel = d.rel;
+                tp.dbg_merged = d.dbg_merged;
+                tp.dbg_seedcnt = d.dbg_seedcnt;
+            }
             sl_w = d.tile_w;
             sl_t0 = d.t0;
             sl_len = d.slice_ns;

@@ -33,7 +33,7 @@ def pkg():
 
 
 def _det(pkg, geom, par):
-    return pkg.Detector(geom.xyz_mm, geom.floor_id, par)
+    return pkg.Detector(geom.xyz_mm, geom.floor_id, par, tower_id=geom.tower_id)
 
 
 def _run(pkg, det, subs, graph=False, each=False):
@@ -558,3 +558,84 @@ def test_level0_parameter_checks(pkg, params):
         _det(pkg, _tower_array(2, 1), dict(params, l0_hits=7, l0_distinct_pmts=1))   # > 128 PMTs
     with pytest.raises(pkg.TrigError):
         _det(pkg, workload.nemo_tower(), dict(params, l0_hits=7, l0_window_ns=0))
+
+
+# ------------------------------------------- coincidence ladder, distinct count
+
+LADDER = dict(seed_rule=1, threshold=1)
+
+
+@pytest.mark.parametrize("variant", ["ladder", "ladder_n7tw", "ladder_c4", "distinct", "distinct_ladder"])
+def test_rule_variants_towers(pkg, params, variant):
+    """The paper's coincidence ladder ([SC and AFC] or [FC and AFC], alone,
+    after N7TW1000, or followed by the causal count at 4) and the
+    distinct-PMT causal count, on the KM3Net-It run with bursts and on the
+    NEMO slice: exact against the oracle."""
+    extra = {"ladder": LADDER, "ladder_n7tw": dict(LADDER, l0_hits=7, l0_window_ns=1000),
+             "ladder_c4": dict(seed_rule=1), "distinct": dict(count_distinct_pmts=1),
+             "distinct_ladder": dict(LADDER, count_distinct_pmts=1, threshold=3)}[variant]
+    for wl in (workload.cfg_km3(), workload.cfg_nemo()):
+        g = wl.detectors[0]
+        par = dict(params, **extra)
+        d = _det(pkg, g, par)
+        _, res = _run(pkg, d, [(s.t0, s.stream) for s in wl.submissions])
+        ref = oracle.run(g.xyz_mm, g.floor_id, par, wl.runs[0].hits, wl.run_slices[0], tower_id=g.tower_id)
+        assert sum(len(r.seeds) for r in ref) > 0, variant
+        for k in range(len(ref)):
+            _assert_same(res[k], ref[k], f"{g.name} {variant} slice {k}")
+        d.close()
+
+
+@pytest.mark.parametrize("case", range(6))
+def test_rule_variants_random_dense(pkg, params, case):
+    """Dense random slices with clustered coincidences, several tile
+    widths' worth of hits: random windows, distances and thresholds."""
+    rng = np.random.Generator(np.random.PCG64(950 + case))
+    g = [workload.nemo_tower, workload.km3_tower][case % 2]()
+    par = dict(params, slice_ns=int(rng.choice([20_000, 200_000])), seed_rule=int(case % 3 != 2),
+               threshold=int(rng.integers(1, 4)), count_distinct_pmts=int(case % 2 == 0),
+               sc_window_ns=int(rng.choice([20, 60])), fc_window_ns=int(rng.choice([10, 100])),
+               afc_window_ns=int(rng.choice([100, 250, 700])), sc_dist_mm=int(rng.choice([1000, 7000])))
+    t0 = 5_000_000
+    n = int(rng.integers(1500, 5000))
+    t = rng.integers(t0 - 4000, t0 + 2 * par["slice_ns"] + 4000, n)
+    t[: n // 2] = t[n // 2: 2 * (n // 2)] + rng.integers(-300, 301, n // 2)
+    hits = np.zeros(n, workload.HIT_DTYPE)
+    hits["t"] = t
+    hits["pmt"] = rng.integers(0, g.n_pmt, n)
+    hits["charge"] = rng.integers(1, 500, n)
+    t0s = [t0, t0 + par["slice_ns"]]
+    full = _stream_from_hits(hits, g.n_pmt)
+    d = _det(pkg, g, par)
+    _, res = _run(pkg, d, _subs_from_run(full, t0s, par["slice_ns"], d.halo_ns))
+    ref = oracle.run(g.xyz_mm, g.floor_id, par, hits, t0s, tower_id=g.tower_id)
+    assert sum(len(r.seeds) for r in ref) > 0
+    for k in range(2):
+        _assert_same(res[k], ref[k], f"case {case} slice {k}")
+    d.close()
+
+
+def test_ladder_wide_detector_with_towers(pkg, params):
+    """A 3 x 1 tower array (252 PMTs, bucketed staging): the consecutive-
+    floor test uses the tower ids."""
+    g = _tower_array(3, 1)
+    par = dict(params, slice_ns=2_000_000, seed_rule=1, threshold=2)
+    t0 = workload.T_ORIGIN_NS
+    t0s = [t0, t0 + par["slice_ns"]]
+    full = workload.gen_stream(g, t0 - 3000, t0 + 2 * par["slice_ns"] + 3000, 150e3, n_muons=40, seed=9, stream=141)
+    d = _det(pkg, g, par)
+    _, res = _run(pkg, d, _subs_from_run(full, t0s, par["slice_ns"]))
+    ref = oracle.run(g.xyz_mm, g.floor_id, par, full.hits, t0s, tower_id=g.tower_id)
+    assert sum(len(r.seeds) for r in ref) > 0
+    for k in range(2):
+        _assert_same(res[k], ref[k], f"wide ladder slice {k}")
+    d.close()
+
+
+def test_rule_parameter_checks(pkg, params):
+    with pytest.raises(pkg.TrigError):
+        _det(pkg, _tower_array(2, 1), dict(params, count_distinct_pmts=1))      # > 128 PMTs
+    with pytest.raises(pkg.TrigError):
+        _det(pkg, workload.nemo_tower(), dict(params, seed_rule=2))
+    with pytest.raises(pkg.TrigError):
+        _det(pkg, workload.nemo_tower(), dict(params, seed_rule=1, afc_window_ns=60001))

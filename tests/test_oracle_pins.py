@@ -430,3 +430,187 @@ def test_level0_bruteforce_and_index_reading():
                 if ok:
                     idx.append(sd)
             assert idx == keep, case
+
+
+# ------------------------------------- coincidence ladder, distinct count
+
+def test_ladder_golden_fixture():
+    fx = json.load(open(os.path.join(GOLDEN, "ladder", "nemo32.json")))
+    g = workload.nemo_tower()
+    hits = _fixture_hits(fx)
+    for name, v in fx["variants"].items():
+        par = dict(workload.DEFAULT_PARAMS, **fx["params"])
+        par.update(v["params"])
+        res = oracle.run(g.xyz_mm, g.floor_id, par, hits, fx["slices"])[0]
+        assert res.seeds["t"].tolist() == v["seed_times"], name
+        assert res.triggers["t"].tolist() == v["seed_times"], name      # threshold 1: every seed fires
+
+
+def test_distinct_count_golden_fixture():
+    fx = json.load(open(os.path.join(GOLDEN, "distinct", "nemo32.json")))
+    g = workload.nemo_tower()
+    hits = _fixture_hits(fx)
+    for mode, flag in (("count", 0), ("distinct", 1)):
+        par = dict(workload.DEFAULT_PARAMS, **fx["params"], count_distinct_pmts=flag)
+        res = oracle.run(g.xyz_mm, g.floor_id, par, hits, fx["slices"])[0]
+        assert _tuples(res.seeds, SEED_F) == [tuple(x) for x in fx["expected_seeds"][mode]], mode
+
+
+def _floor_levels(det):
+    """Per PMT: position of its floor among its tower's floors, ordered by
+    the height of each floor's lowest PMT, then floor id (pure Python)."""
+    lowest = {}
+    for p in range(det.n_pmt):
+        f = int(det.floor_id[p])
+        lowest[f] = min(lowest.get(f, 1 << 62), int(det.xyz_mm[p][2]))
+    order = {}
+    for p in range(det.n_pmt):
+        order.setdefault(int(det.tower_id[p]), set()).add((lowest[int(det.floor_id[p])], int(det.floor_id[p])))
+    pos = {tw: {f: i for i, (_, f) in enumerate(sorted(s))} for tw, s in order.items()}
+    return [pos[int(det.tower_id[p])][int(det.floor_id[p])] for p in range(det.n_pmt)]
+
+
+def _brute_ext(det, par, hits, t0):
+    """All pairs, no ordering: the coincidence ladder (seed rule 1) with its
+    level-0 filter off, and the causal count of hits or of different PMTs."""
+    xyz = [tuple(int(c) for c in row) for row in det.xyz_mm]
+    floor = [int(f) for f in det.floor_id]
+    tower = [int(x) for x in det.tower_id]
+    level = _floor_levels(det)
+    W = par["corr_window_ns"]
+    H = [(int(h["t"]), int(h["pmt"]), int(h["charge"])) for h in hits]
+
+    def d2(a, b):
+        return sum((xyz[a][c] - xyz[b][c]) ** 2 for c in range(3))
+
+    def is_seed(i):
+        ts, ps, qs = H[i]
+        if par["seed_rule"] == 0:
+            return qs >= par["q_seed_adc"] or any(
+                pj != ps and floor[pj] == floor[ps] and abs(tj - ts) <= par["floor_tau_ns"] for (tj, pj, _) in H)
+        sc = fc = afc = False
+        for j, (tj, pj, _) in enumerate(H):
+            if j == i:
+                continue
+            d = abs(tj - ts)
+            same_floor = pj != ps and floor[pj] == floor[ps]
+            sc |= same_floor and d2(ps, pj) <= par["sc_dist_mm"] ** 2 and d <= par["sc_window_ns"]
+            fc |= same_floor and d <= par["fc_window_ns"]
+            afc |= tower[pj] == tower[ps] and abs(level[pj] - level[ps]) == 1 and d <= par["afc_window_ns"]
+        return (sc and afc) or (fc and afc)
+
+    out = []
+    for i, (ts, ps, qs) in enumerate(H):
+        if not (t0 <= ts < t0 + par["slice_ns"]) or not is_seed(i):
+            continue
+        rel = [pj for (tj, pj, _) in H if abs(tj - ts) <= min(par["tol_ns"] + _k_exact(d2(ps, pj), par["n_num"],
+                                                                                      par["n_den"]), W)]
+        c = len(set(rel)) if par["count_distinct_pmts"] else len(rel)
+        out.append((ts, ps, qs, c))
+    return sorted(out)
+
+
+def _ladder_clusters(rng, det, lo, hi):
+    """Random hits plus clusters of 3-8 hits within a few hundred ns on one
+    floor, its neighbours in height (any tower) and the same PMT (ties and
+    repeats included), so that every coincidence type occurs."""
+    by_z = {}
+    for p in range(det.n_pmt):
+        by_z.setdefault(int(det.xyz_mm[p][2]), []).append(p)
+    zs = sorted(by_z)
+    rows = [(int(x), int(rng.integers(0, det.n_pmt)), int(rng.integers(1, 400)))
+            for x in rng.integers(lo, hi, 60)]
+    for _ in range(int(rng.integers(25, 40))):
+        c = int(rng.integers(lo, hi))
+        k = int(rng.integers(0, len(zs)))
+        pool = by_z[zs[k]] + (by_z[zs[k - 1]] if k else []) + (by_z[zs[k + 1]] if k + 1 < len(zs) else [])
+        if rng.random() < 0.7:          # mostly one tower
+            tw = det.tower_id[pool[int(rng.integers(0, len(pool)))]]
+            pool = [p for p in pool if det.tower_id[p] == tw]
+        for _ in range(int(rng.integers(3, 9))):
+            rows.append((c + int(rng.integers(-150, 151)), int(rng.choice(pool)), int(rng.integers(1, 400))))
+    rows += rows[-3:]
+    hits = np.zeros(len(rows), oracle.HIT_DTYPE)
+    for i, (t, p, q) in enumerate(rows):
+        hits[i] = (t, p, q, 0)
+    return hits
+
+
+@pytest.mark.parametrize("case", range(8))
+def test_ladder_and_distinct_count_match_bruteforce(case, params):
+    """Tiny dense slices on a tower and on a two-tower array (tower ids
+    matter for AFC): the oracle's seeds and counts equal the all-pairs
+    definition for both seed rules and both count forms."""
+    rng = np.random.Generator(np.random.PCG64(700 + case))
+    det = [workload.nemo_tower, workload.km3_tower, lambda: workload.tower_array(nx=2, ny=1)][case % 3]()
+    par = dict(params, slice_ns=10_000, threshold=1, seed_rule=int(case % 2 == 0),
+               count_distinct_pmts=int(case % 4 < 2 and det.n_pmt <= 128),
+               sc_window_ns=int(rng.choice([20, 60])), fc_window_ns=int(rng.choice([10, 100])),
+               afc_window_ns=int(rng.choice([100, 250])), sc_dist_mm=int(rng.choice([1000, 7000])))
+    t0 = 2_000_000
+    hits = _ladder_clusters(rng, det, t0 - 3000, t0 + par["slice_ns"] + 3000)
+    got = oracle.run(det.xyz_mm, det.floor_id, par, hits, [t0], tower_id=det.tower_id)[0]
+    want = _brute_ext(det, par, hits, t0)
+    assert len(want) >= 10, case
+    assert _tuples(got.seeds, SEED_F) == want, case
+
+
+def test_ladder_accidental_rate_closed_form(params):
+    """Pure Poisson background, the paper's windows: a hit on PMT p is a
+    seed iff another PMT of its floor has a hit within +-fc (SC implies FC
+    here: adjacent PMTs share the floor and sc <= fc) and a PMT of a
+    consecutive floor one within +-afc.  The two sets of PMTs are disjoint,
+    so P = (1 - exp(-lam_fc)) (1 - exp(-lam_afc)), lam = sum R (2 w + 1 ns).
+    The top and bottom floors have one consecutive floor, the others two."""
+    det = workload.nemo_tower()
+    par = dict(params, seed_rule=1, threshold=1)
+    n_slices, rate = 40, 50e3
+    S = par["slice_ns"]
+    t_org = workload.T_ORIGIN_NS
+    st = workload.gen_stream(det, t_org - 3000, t_org + n_slices * S + 3000, rate, seed=21, stream=81)
+    t0s = [t_org + k * S for k in range(n_slices)]
+    res = oracle.run(det.xyz_mm, det.floor_id, par, st.hits, t0s)
+    obs = sum(len(r.seeds) for r in res)
+    own = st.hits[(st.hits["t"] >= t0s[0]) & (st.hits["t"] < t0s[-1] + S)]
+    n_floors = int(det.floor_id.max()) + 1
+    fl = det.floor_id[own["pmt"]]
+    n_next = np.where((fl == 0) | (fl == n_floors - 1), 4, 8)
+    lam_fc = 3 * rate * (2 * par["fc_window_ns"] + 1) * 1e-9
+    lam_afc = n_next * rate * (2 * par["afc_window_ns"] + 1) * 1e-9
+    expect = float(((1 - math.exp(-lam_fc)) * (1 - np.exp(-lam_afc))).sum())
+    sigma = math.sqrt(3 * expect)
+    assert abs(obs - expect) < 4 * sigma, (obs, expect, sigma)
+    # counting a single consecutive floor everywhere moves it by far more
+    wrong = float(((1 - math.exp(-lam_fc)) * (1 - np.exp(-4 * rate * (2 * par["afc_window_ns"] + 1) * 1e-9))).sum())
+    assert abs(wrong - expect) > 4 * sigma
+
+
+def test_distinct_count_closed_form(params):
+    """Every hit a seed, distinct-PMT count, Poisson background on the
+    84-PMT tower at a high rate: E[c(s) - 1] = sum_{q != p_s} (1 -
+    exp(-R (2 min(dt_max[p_s][q], W) + 1 ns))) -- the seed's own PMT is
+    always in the set; every other PMT is in it iff it has a hit in its
+    range.  The plain count's expectation sum R (2 dt + 1) is far off."""
+    det = workload.km3_tower()
+    par = dict(params, q_seed_adc=0, threshold=0, slice_ns=100_000, count_distinct_pmts=1)
+    rate = 400e3
+    n_slices = 40
+    t_org = workload.T_ORIGIN_NS
+    S = par["slice_ns"]
+    st = workload.gen_stream(det, t_org - 3000, t_org + n_slices * S + 3000, rate, seed=31, stream=91)
+    t0s = [t_org + k * S for k in range(n_slices)]
+    res = oracle.run(det.xyz_mm, det.floor_id, par, st.hits, t0s)
+    dt = np.minimum(oracle.dtmax(det.xyz_mm, par).astype(np.float64), par["corr_window_ns"])
+    lam = rate * (2 * dt + 1) * 1e-9
+    np.fill_diagonal(lam, 0.0)
+    per_pmt = (1 - np.exp(-lam)).sum(1)
+    per_pmt_plain = lam.sum(1)
+    means, expects, plains = [], [], []
+    for r in res:
+        means.append(r.seeds["count"].astype(np.float64).mean() - 1)
+        expects.append(per_pmt[r.seeds["pmt"]].mean())
+        plains.append(per_pmt_plain[r.seeds["pmt"]].mean())
+    means = np.array(means)
+    err = means.std(ddof=1) / math.sqrt(len(means))
+    assert abs(means.mean() - np.mean(expects)) < 4 * err + 1e-9, (means.mean(), np.mean(expects), err)
+    assert abs(means.mean() - np.mean(plains)) > 4 * err

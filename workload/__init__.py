@@ -357,4 +357,6 @@ CONFIGS = {
 
 DEFAULT_PARAMS = dict(q_seed_adc=300, floor_tau_ns=20, tol_ns=20, n_num=6900, n_den=1499,
                       corr_window_ns=3000, threshold=4, win_half_ns=3000, slice_ns=SLICE_NS,
-                      l0_hits=0, l0_window_ns=1000, l0_distinct_pmts=0)
+                      l0_hits=0, l0_window_ns=1000, l0_distinct_pmts=0,
+                      seed_rule=0, sc_window_ns=20, fc_window_ns=100, afc_window_ns=250, sc_dist_mm=1000,
+                      count_distinct_pmts=0)
