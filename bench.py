@@ -204,7 +204,7 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=20.0, help="detector-seconds per detector")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-events", action="store_true", help="skip the event-extraction leg")
-    ap.add_argument("--no-level0", action="store_true", help="skip the level-0 leg")
+    ap.add_argument("--no-rules", action="store_true", help="skip the trigger-rule variants leg")
     ap.add_argument("--slices", type=int, default=64, help="slices of the batched workload (profiling runs)")
     ap.add_argument("--workload", default="batched", choices=sorted(WORKLOADS),
                     help="batched (the default step) or the scaled 2688-PMT array (profiling runs)")
@@ -361,30 +361,38 @@ def main():
         batch.set_events(False)
         log(f"events: {ms_ev:.3f} ms/step, {n_ev} event hits")
 
-    # ------------------- level-0 prefilter (N7TW1000) on the same slices
-    level0 = None
-    if not args.no_level0:
-        par0 = dict(par, l0_hits=7, l0_window_ns=1000)
-        dets0 = [trig.Detector(g.xyz_mm, g.floor_id, par0) for g in wl.detectors]
-        batch0 = DeviceBatch([SliceIn(dets0[s.det_index], s.t0, s.stream.hits, s.stream.pmt_off)
-                              for s in wl.submissions], device=f"cuda:{local}")
-        for _ in range(args.warmup):
-            batch0.run(graph=True)
-        torch.cuda.synchronize()
-        k_l0 = max(3, args.steps // 5)
-        e0.record(stream)
-        for _ in range(k_l0):
-            batch0.run(graph=True)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms_l0 = max_over_ranks(e0.elapsed_time(e1) / k_l0)
-        n_tr0 = sum(int(st["n_triggers"]) for st, _, _ in batch0.results())
+    # ------------- trigger-rule variants of the paper on the same slices
+    rules = None
+    if not args.no_rules:
+        rules = {}
         n_tr = sum(int(st["n_triggers"]) for st, _, _ in batch.results())
-        level0 = {"value": total_hits / (ms_l0 * 1e-3), "unit": "hits/s", "ms_per_step": ms_l0,
-                  "rule": "N7TW1000 before the seed triggers", "triggers_per_step": n_tr0,
-                  "triggers_per_step_without": n_tr, "path": "trig_batch_run, CUDA graph replay"}
-        del batch0, dets0
-        log(f"level0: {ms_l0:.3f} ms/step, triggers {n_tr0} of {n_tr}")
+        variants = {
+            "level0": ("N7TW1000 level 0 in front of the seed rule", dict(l0_hits=7, l0_window_ns=1000)),
+            "ladder": ("the paper's ladder: N7TW1000, then [SC and AFC] or [FC and AFC], every seed tagged",
+                       dict(l0_hits=7, l0_window_ns=1000, seed_rule=1, threshold=1)),
+            "distinct": ("causal count over different PMTs, fire at 4", dict(count_distinct_pmts=1)),
+        }
+        for name, (rule, extra) in variants.items():
+            par_v = dict(par, **extra)
+            dets_v = [trig.Detector(g.xyz_mm, g.floor_id, par_v, tower_id=g.tower_id) for g in wl.detectors]
+            batch_v = DeviceBatch([SliceIn(dets_v[s.det_index], s.t0, s.stream.hits, s.stream.pmt_off)
+                                   for s in wl.submissions], device=f"cuda:{local}")
+            for _ in range(args.warmup):
+                batch_v.run(graph=True)
+            torch.cuda.synchronize()
+            k_v = max(3, args.steps // 5)
+            e0.record(stream)
+            for _ in range(k_v):
+                batch_v.run(graph=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_v = max_over_ranks(e0.elapsed_time(e1) / k_v)
+            n_tr_v = sum(int(st["n_triggers"]) for st, _, _ in batch_v.results())
+            rules[name] = {"value": total_hits / (ms_v * 1e-3), "unit": "hits/s", "ms_per_step": ms_v, "rule": rule,
+                           "triggers_per_step": n_tr_v, "triggers_per_step_default_rule": n_tr,
+                           "path": "trig_batch_run, CUDA graph replay"}
+            del batch_v, dets_v
+            log(f"rule {name}: {ms_v:.3f} ms/step, triggers {n_tr_v} (default rule {n_tr})")
 
     # ---------------------------------------------------- e2e, host buffers
     e2e = None
@@ -457,7 +465,7 @@ def main():
             "roofline": roofline,
             "e2e": e2e,
             "events": events,
-            "level0": level0,
+            "rules": rules,
             "latency": latency,
             "cpu_baseline": cpu,
             "clocks": clocks,

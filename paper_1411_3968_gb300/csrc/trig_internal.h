@@ -116,7 +116,7 @@ struct BatchHeader {
     uint32_t queue;         // tile work queue head
     uint32_t any_wide;      // a slice of the batch is wide
     uint32_t any_events;    // a slice of the batch extracts events
-    uint32_t pad;
+    uint32_t any_ext;       // a slice uses level 0, seed rule 1 or the distinct count
 };
 
 constexpr uint32_t kChunkHits = 4096;       // structure-pass chunk
@@ -147,12 +147,15 @@ extern const char *const kKernelNames[kPipelineKernels];
 
 // any_wide: the batch holds a wide slice (the bucket sums, scan and
 // scatter kernels run only then); any_events: a slice extracts events (the
-// halo, event-offset and event-copy kernels run only then).  ev (optional, kPipelineKernels + 1 events): ev[i]
+// halo, event-offset and event-copy kernels run only then); any_ext: a slice
+// uses level 0, seed rule 1 or the distinct count (the tile kernel built
+// with those rules runs, else the one without them).  ev (optional, kPipelineKernels + 1 events): ev[i]
 // is recorded before pipeline kernel i and ev[kPipelineKernels] after the
 // last one (a kernel that does not run gets an empty interval).
 // *launches is increased by the number of kernels launched.
 cudaError_t launch_batch(BatchHeader *d_hdr, SliceDesc *d_desc, uint32_t n_slices, uint32_t max_pmt,
-                         bool any_smem_dt, bool any_wide, bool any_events, const TileConfig &cfg, cudaStream_t st,
+                         bool any_smem_dt, bool any_wide, bool any_events, bool any_ext, const TileConfig &cfg,
+                         cudaStream_t st,
                          uint64_t *launches, bool rows, cudaEvent_t *ev = nullptr);
 
 int device_sm_count();

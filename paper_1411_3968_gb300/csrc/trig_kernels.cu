@@ -911,7 +911,7 @@ __device__ __noinline__ bool level0_pass(const uint32_t *pk, uint32_t n, uint32_
 }
 
 // The core is keys[c0, c1) (t_rel in [H, H + core width)).
-template <int CAP, int NC, bool SMEM_DT>
+template <int CAP, int NC, bool SMEM_DT, bool EXT>
 __device__ CoreOut tile_trigger(TileCtx &cx, const uint64_t *keys, uint32_t n, uint32_t bsh, uint32_t c0, uint32_t c1,
                                 int64_t tb, const TrigParams &tp, trig_trigger *out, int64_t dbg_rank_lo,
                                 uint32_t *red)
@@ -942,7 +942,7 @@ __device__ CoreOut tile_trigger(TileCtx &cx, const uint64_t *keys, uint32_t n, u
         const uint32_t fi = in ? cx.floor_s[pi] : 0u;
         bool seed = in && key_q(keys[i]) >= qseed;
         bool more_up = false, more_dn = false;
-        if (tp.seed_rule == 1) {
+        if (EXT && tp.seed_rule == 1) {
             // the paper's combination of coincidences replaces the rule below
             seed = in && coincidence_seed(pk, n, i, tp.rel, P, tp.sc_w, tp.fc_w, tp.afc_w);
         } else {
@@ -976,7 +976,7 @@ __device__ CoreOut tile_trigger(TileCtx &cx, const uint64_t *keys, uint32_t n, u
         }
         }
         // level 0 (N hits within TW) before the seed triggers count
-        if (tp.l0_hits && seed && in) seed = level0_pass(pk, n, i, tp.l0_hits, tp.l0_window, tp.l0_distinct != 0);
+        if (EXT && tp.l0_hits && seed && in) seed = level0_pass(pk, n, i, tp.l0_hits, tp.l0_window, tp.l0_distinct != 0);
         // halo hits past the core are neighbours only, never seeds here
         const uint32_t m = __ballot_sync(0xffffffffu, seed && in);
         if (lane == 0 && (base + warp * 32) < ncore) cx.mask[(base + warp * 32) >> 5] = m;
@@ -1029,7 +1029,7 @@ __device__ CoreOut tile_trigger(TileCtx &cx, const uint64_t *keys, uint32_t n, u
     //    over the seed's scan range: a group of G lanes per seed (G from the
     //    tile's density), seeds dealt round-robin to the groups, four
     //    independent tests per lane in flight
-    if (tp.count_distinct) {
+    if (EXT && tp.count_distinct) {
         count_distinct_pmts<NC, SMEM_DT>(cx, pk, n, ns, seed_idx, swin, seed_cnt);
     } else {
         // expected keys in a scan range: 2H + 1 ns at the tile's density
@@ -1158,7 +1158,7 @@ __device__ CoreOut tile_trigger(TileCtx &cx, const uint64_t *keys, uint32_t n, u
 // its core in halves until each piece fits; pieces are staged with plain
 // loads after per-PMT binary searches.  A 1 ns core that still does not
 // fit is reported (TRIG_FLAG_TILE_FULL) and skipped.
-template <int CAP, int NC, bool SMEM_DT>
+template <int CAP, int NC, bool SMEM_DT, bool EXT>
 __device__ void tile_overflow(TileCtx &cx, uint64_t *buf, const SliceDesc &d, const TrigParams &tp, uint32_t g,
                               uint32_t *red, int64_t *stk)
 {
@@ -1271,7 +1271,7 @@ __device__ void tile_overflow(TileCtx &cx, uint64_t *buf, const SliceDesc &d, co
         const uint32_t bsh = tile_sort<CAP, NC>(cx, buf, total, tb, span, red + 64, H, H + (uint32_t)(hi - lo));
         const uint32_t c0 = red[64 + NW + 1], c1 = red[64 + NW + 2];
         const uint32_t fired0 = red[5];
-        CoreOut co = tile_trigger<CAP, NC, SMEM_DT>(cx, buf, total, bsh, c0, c1, tb, tp,
+        CoreOut co = tile_trigger<CAP, NC, SMEM_DT, EXT>(cx, buf, total, bsh, c0, c1, tb, tp,
                                                      d.stage + tile_rank + fired0,
                                                      (int64_t)rank_lo - (int64_t)d.dbg_rank0, red + 64);
         if (tid == 0) {
@@ -1288,7 +1288,7 @@ __device__ void tile_overflow(TileCtx &cx, uint64_t *buf, const SliceDesc &d, co
     cons_sync<NC>();
 }
 
-template <int CAP, int NC, bool SMEM_DT>
+template <int CAP, int NC, bool SMEM_DT, bool EXT>
 __global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 1)) k_tile(BatchHeader *__restrict__ hdr,
                                                                           const SliceDesc *__restrict__ desc,
                                                                           uint32_t max_pmt)
@@ -1514,7 +1514,7 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 
                 d.tile_rank[inf.g] = 0;
             }
         } else if (inf.mode == 1) {
-            tile_overflow<CAP, NC, SMEM_DT>(cx, cx.stage[b], d, tp, inf.g, red, stk);
+            tile_overflow<CAP, NC, SMEM_DT, EXT>(cx, cx.stage[b], d, tp, inf.g, red, stk);
         } else {
             const int64_t W = sl_w;
             const int64_t Bg = sl_t0 + (int64_t)inf.g * W;
@@ -1527,7 +1527,7 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 
             // rank of the core's first hit = rank_lo + c0, known after the sort
             const uint32_t c0 = red[NW + 1], c1 = red[NW + 2];
             const uint32_t tile_rank = inf.rank_lo + c0;
-            CoreOut co = tile_trigger<CAP, NC, SMEM_DT>(cx, cx.stage[b], inf.n, bsh, c0, c1, tb, tp,
+            CoreOut co = tile_trigger<CAP, NC, SMEM_DT, EXT>(cx, cx.stage[b], inf.n, bsh, c0, c1, tb, tp,
                                                          d.stage + tile_rank, (int64_t)inf.rank_lo - (int64_t)sl_rank0,
                                                          red);
             if (tid == 0 && CHECK(14, (uint64_t)tile_rank + co.n_fired, d.n_hits + 1) && CHECK(15, inf.g, d.n_tiles)) {
@@ -2119,12 +2119,12 @@ static cudaError_t raise_smem_limit(K kern, bool *done)
     return cudaSuccess;
 }
 
-template <int CAP, int NC, bool SMEM_DT>
+template <int CAP, int NC, bool SMEM_DT, bool EXT = false>
 static cudaError_t launch_tile(BatchHeader *hdr, SliceDesc *desc, uint32_t max_pmt, cudaStream_t st)
 {
     static bool limit_set[64] = {};
     size_t smem = TileLayout<CAP>::bytes(max_pmt, SMEM_DT);
-    auto kern = k_tile<CAP, NC, SMEM_DT>;
+    auto kern = k_tile<CAP, NC, SMEM_DT, EXT>;
     cudaError_t e = raise_smem_limit(kern, limit_set);
     if (e != cudaSuccess) return e;
     int per_sm = 1;
@@ -2139,8 +2139,8 @@ const char *const kKernelNames[kPipelineKernels] = {"k_prep",   "k_bounds", "k_b
                                                      "k_wwrite", "k_whits",  "k_escan", "k_events", "k_status"};
 
 cudaError_t launch_batch(BatchHeader *d_hdr, SliceDesc *d_desc, uint32_t n_slices, uint32_t max_pmt,
-                         bool any_smem_dt, bool any_wide, bool any_events, const TileConfig &cfg, cudaStream_t st,
-                         uint64_t *launches, bool rows, cudaEvent_t *ev)
+                         bool any_smem_dt, bool any_wide, bool any_events, bool any_ext, const TileConfig &cfg,
+                         cudaStream_t st, uint64_t *launches, bool rows, cudaEvent_t *ev)
 {
     const int sms = device_sm_count();
     auto mark = [&](int i) {
@@ -2172,7 +2172,18 @@ cudaError_t launch_batch(BatchHeader *d_hdr, SliceDesc *d_desc, uint32_t n_slice
     mark(5);
     cudaError_t e;
     const bool smem_dt = any_smem_dt && max_pmt <= kSmemDtMaxPmt;
-    if (cfg.cap == 1024)
+    if (any_ext) {
+        // level 0, seed rule 1, distinct count: one build per shape, dt rows
+        // read through the cache
+        if (cfg.cap == 1024)
+            e = launch_tile<1024, 128, false, true>(d_hdr, d_desc, max_pmt, st);
+        else if (cfg.cap == 2048)
+            e = cfg.warps == 16 ? launch_tile<2048, 512, false, true>(d_hdr, d_desc, max_pmt, st)
+                                : launch_tile<2048, 256, false, true>(d_hdr, d_desc, max_pmt, st);
+        else
+            e = cfg.warps == 8 ? launch_tile<4096, 256, false, true>(d_hdr, d_desc, max_pmt, st)
+                               : launch_tile<4096, 512, false, true>(d_hdr, d_desc, max_pmt, st);
+    } else if (cfg.cap == 1024)
         e = smem_dt ? launch_tile<1024, 128, true>(d_hdr, d_desc, max_pmt, st)
                     : launch_tile<1024, 128, false>(d_hdr, d_desc, max_pmt, st);
     else if (cfg.cap == 2048 && cfg.warps == 16)
