@@ -15,6 +15,8 @@ Python face of ``oracle.c`` (plain C, compiled with gcc on first use):
   merged windows per slice ("Sorting and triggering in GPU").
 * ``events(hits, windows)``  the event payload: the hits inside a slice's
   merged windows, in (t, pmt, charge) order.
+* ``oracle.array.select(...)``  the multi-tower selection and window
+  readback ("Results and perspectives"), numpy over the towers' triggers.
 """
 from __future__ import annotations
 

@@ -1,5 +1,6 @@
 """GB300-native online muon trigger for underwater neutrino telescopes
-(arXiv 1411.3968): C ABI in include/trig.h, sm_103a kernels in csrc/,
+(arXiv 1411.3968): C ABI in include/trig.h (multi-tower selection in
+include/trig_array.h), sm_103a kernels in csrc/,
 Python binding in _lib.  PyTorch (optional) is used only by callers for
 device memory and streams; see runner.py."""
 from ._lib import (  # noqa: F401
@@ -10,4 +11,6 @@ from ._lib import (  # noqa: F401
     trig_autotune, trig_batch_run_noalloc, trig_detector_tile_config, trig_batch_run_events,
     trig_batch_events_scratch_bytes, trig_set_events, TRIG_FLAG_EV_FULL,
     trig_poll, trig_set_tile_config, trig_slice_rows, trig_submit_slice, win_cap_for,
+    Array, ASEED_DTYPE, ASTATS_DTYPE, TRIG_AFLAG_SEED_FULL, TRIG_AFLAG_WIN_FULL, TRIG_AFLAG_HIT_FULL,
+    TRIG_AFLAG_TOWER_INCOMPLETE, trig_array_scratch_bytes, trig_array_select,
 )

@@ -38,14 +38,22 @@ WINDOW_DTYPE = np.dtype([("lo", "<i8"), ("hi", "<i8"), ("n_hits", "<u8"), ("n_tr
 STATS_DTYPE = np.dtype([("status", "<i4"), ("flags", "<u4"), ("n_hits", "<u8"), ("n_seeds", "<u8"),
                         ("n_triggers", "<u8"), ("n_windows", "<u8"), ("n_events", "<u8")])
 
-# symbols declared in include/trig.h
+ASEED_DTYPE = np.dtype([("t", "<i8"), ("pmt", "<u2"), ("tower", "<u2"), ("n_towers", "<u4")])
+ASTATS_DTYPE = np.dtype([("n_tower_triggers", "<u8"), ("n_selected", "<u8"), ("n_windows", "<u8"),
+                         ("n_hits", "<u8"), ("flags", "<u4"), ("status", "<i4")])
+TRIG_AFLAG_SEED_FULL = 0x01
+TRIG_AFLAG_WIN_FULL = 0x02
+TRIG_AFLAG_HIT_FULL = 0x04
+TRIG_AFLAG_TOWER_INCOMPLETE = 0x08
+
+# symbols declared in include/trig.h and include/trig_array.h
 EXPORTS = [
     "trig_create", "trig_destroy", "trig_detector_dtmax", "trig_detector_halo_ns", "trig_submit_slice",
     "trig_poll", "trig_result_free", "trig_engine_set_mode", "trig_engine_stats", "trig_last_error",
     "trig_batch_scratch_bytes", "trig_batch_run", "trig_slice_rows", "trig_set_tile_config",
     "trig_get_tile_config", "trig_kernel_launch_count", "trig_kernel_times", "trig_batch_run_noalloc",
     "trig_autotune", "trig_detector_tile_config", "trig_batch_events_scratch_bytes", "trig_batch_run_events",
-    "trig_set_events",
+    "trig_set_events", "trig_array_create", "trig_array_destroy", "trig_array_scratch_bytes", "trig_array_select",
 ]
 
 NOALLOC_SCRATCH_BYTES = 64 << 20
@@ -98,6 +106,17 @@ class trig_slice_dev(ctypes.Structure):
                 ("stats", ctypes.c_void_p)]
 
 
+class trig_array_params(ctypes.Structure):
+    _fields_ = [("min_towers", ctypes.c_uint32), ("corr_window_ns", ctypes.c_uint32),
+                ("win_half_ns", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+class trig_array_out(ctypes.Structure):
+    _fields_ = [("seeds", ctypes.c_void_p), ("seed_cap", ctypes.c_uint64), ("windows", ctypes.c_void_p),
+                ("win_cap", ctypes.c_uint64), ("frag_off", ctypes.c_void_p), ("hits", ctypes.c_void_p),
+                ("hit_cap", ctypes.c_uint64), ("stats", ctypes.c_void_p)]
+
+
 _lib = None
 
 
@@ -143,6 +162,12 @@ def load(path: str | None = None):
         "trig_batch_run_events": (c.c_int, [c.POINTER(trig_slice_dev), c.POINTER(trig_slice_events), c.c_uint32,
                                             c.c_void_p, c.c_size_t, c.c_void_p, c.c_uint32]),
         "trig_set_events": (c.c_int, [c.c_void_p, c.c_int]),
+        "trig_array_create": (c.c_int, [c.POINTER(c.c_void_p), c.c_uint32, c.POINTER(trig_array_params),
+                                        c.POINTER(c.c_void_p)]),
+        "trig_array_destroy": (c.c_int, [c.c_void_p]),
+        "trig_array_scratch_bytes": (c.c_size_t, [c.c_void_p, c.POINTER(trig_slice_dev), c.POINTER(trig_array_out)]),
+        "trig_array_select": (c.c_int, [c.c_void_p, c.POINTER(trig_slice_dev), c.POINTER(trig_array_out), c.c_void_p,
+                                        c.c_size_t, c.c_void_p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -408,3 +433,42 @@ def win_cap_for(params: dict) -> int:
     """A window capacity that can never overflow for one slice."""
     h = int(params["win_half_ns"])
     return (int(params["slice_ns"]) + 2 * h) // (2 * h + 2) + 2
+
+
+# ------------------------------------------------------- multi-tower selection
+
+class Array:
+    """Towers grouped for the cross-tower selection (trig_array_create)."""
+
+    def __init__(self, towers: list, min_towers: int = 2, corr_window_ns: int = 3000, win_half_ns: int = 3000):
+        self.towers = list(towers)
+        self.params = dict(min_towers=min_towers, corr_window_ns=corr_window_ns, win_half_ns=win_half_ns)
+        arr = (ctypes.c_void_p * len(self.towers))(*[t.handle.value for t in self.towers])
+        p = trig_array_params(int(min_towers), int(corr_window_ns), int(win_half_ns), 0)
+        h = ctypes.c_void_p()
+        _check(load().trig_array_create(arr, len(self.towers), ctypes.byref(p), ctypes.byref(h)))
+        self.handle = h
+
+    def close(self):
+        if self.handle and self.handle.value:
+            load().trig_array_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def trig_array_scratch_bytes(array: Array, slices, out: trig_array_out) -> int:
+    n = load().trig_array_scratch_bytes(array.handle, _array(slices), ctypes.byref(out))
+    if n == 0:
+        raise TrigError(TRIG_EINVAL, trig_last_error())
+    return int(n)
+
+
+def trig_array_select(array: Array, slices, out: trig_array_out, scratch_ptr: int, scratch_bytes: int,
+                      stream_ptr: int = 0) -> None:
+    _check(load().trig_array_select(array.handle, _array(slices), ctypes.byref(out), scratch_ptr, scratch_bytes,
+                                    stream_ptr or None))

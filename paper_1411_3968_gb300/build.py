@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(HERE, "libtrig.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["trig_kernels.cu", "trig_engine.cpp"]
+SOURCES = ["trig_kernels.cu", "trig_engine.cpp", "trig_array.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -23,7 +23,8 @@ def _nvcc() -> str:
 
 
 def _newest_input() -> float:
-    files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, "trig.h"), __file__]
+    files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)]
+    files.append(__file__)
     return max(os.path.getmtime(f) for f in files)
 
 

@@ -116,6 +116,22 @@ struct trig_detector {
     bool events = false;          // engine results carry the event payload
 };
 
+namespace trig {
+bool detector_info(const trig_detector *d, DetInfo *out)
+{
+    if (!d || !out) return false;
+    out->n_pmt = d->n_pmt;
+    out->xyz = d->xyz.data();
+    out->par = d->par;
+    out->in_halo = d->in_halo;
+    out->device = d->device;
+    return true;
+}
+int report_error(int code, const char *msg) { return fail(code, msg); }
+int report_cuda_error(cudaError_t e, const char *what) { return cuda_fail(e, what); }
+void count_launches(uint64_t n) { g_launches += n; }
+}  // namespace trig
+
 static void free_det_dev(trig_detector *d)
 {
     cudaFree(d->dev.dt);

@@ -160,6 +160,21 @@ cudaError_t launch_batch(BatchHeader *d_hdr, SliceDesc *d_desc, uint32_t n_slice
 
 int device_sm_count();
 
+// What other translation units of the library read of a detector.
+struct DetInfo {
+    uint32_t n_pmt;
+    const int32_t *xyz;     // host, 3 * n_pmt (the detector's copy)
+    trig_params par;
+    int64_t in_halo;        // accepted halo around a slice
+    int device;
+};
+bool detector_info(const trig_detector *d, DetInfo *out);
+
+// The library's error reporting (trig_last_error) and launch counter.
+int report_error(int code, const char *msg);
+int report_cuda_error(cudaError_t e, const char *what);
+void count_launches(uint64_t n);
+
 // Address and size of the library's static scratch array on the current device.
 cudaError_t static_scratch(void **ptr, size_t *bytes);
 

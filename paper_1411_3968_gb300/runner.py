@@ -8,7 +8,7 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import HIT_DTYPE, STATS_DTYPE, TRIGGER_DTYPE, WINDOW_DTYPE
+from ._lib import ASEED_DTYPE, ASTATS_DTYPE, HIT_DTYPE, STATS_DTYPE, TRIGGER_DTYPE, WINDOW_DTYPE
 
 
 def _dev_bytes(nbytes: int, device) -> torch.Tensor:
@@ -146,3 +146,59 @@ class DeviceBatch:
         m = np.frombuffer(merged[: n_owned * HIT_DTYPE.itemsize].cpu().numpy().tobytes(), HIT_DTYPE).copy()
         c = np.frombuffer(seedcnt[: n_owned * 4].cpu().numpy().tobytes(), np.uint32).copy()
         return m, c
+
+
+class ArrayBatch:
+    """The towers' slices of one period resident in HBM; run() enqueues each
+    tower's trigger (one trig_batch_run over the towers) and then the
+    cross-tower selection with the window readback (trig_array_select) on
+    one stream.  slices[b] must be tower b of `array`."""
+
+    def __init__(self, array: "_lib.Array", slices: list[SliceIn], device="cuda", seed_cap: int | None = None,
+                 win_cap: int | None = None, hit_cap: int | None = None):
+        self.array = array
+        self.batch = DeviceBatch(slices, device=device)
+        dev = self.batch.device
+        nt = len(slices)
+        n_trig = sum(self.batch.trig_cap)
+        h = int(array.params["win_half_ns"])
+        span = int(slices[0].det.params["slice_ns"]) + 2 * h
+        self.seed_cap = max(1, n_trig if seed_cap is None else seed_cap)
+        self.win_cap = max(1, min(n_trig, span // (2 * h + 2) + 1) if win_cap is None else win_cap)
+        self.hit_cap = max(1, self.batch.n_hits if hit_cap is None else hit_cap)
+        self.seeds = _dev_bytes(self.seed_cap * ASEED_DTYPE.itemsize, dev)
+        self.windows = _dev_bytes(self.win_cap * WINDOW_DTYPE.itemsize, dev)
+        self.frag_off = _dev_bytes((self.win_cap * nt + 1) * 8, dev)
+        self.hits = _dev_bytes(self.hit_cap * HIT_DTYPE.itemsize, dev)
+        self.stats = _dev_bytes(ASTATS_DTYPE.itemsize, dev)
+        self.out = _lib.trig_array_out(self.seeds.data_ptr(), self.seed_cap, self.windows.data_ptr(), self.win_cap,
+                                       self.frag_off.data_ptr(), self.hits.data_ptr(), self.hit_cap,
+                                       self.stats.data_ptr())
+        self.scratch_bytes = _lib.trig_array_scratch_bytes(array, self.batch.descs, self.out)
+        self.scratch = _dev_bytes(self.scratch_bytes + 256, dev)
+        self.n_towers = nt
+
+    def run(self, graph: bool = False, stream=None) -> None:
+        st = stream if stream is not None else torch.cuda.current_stream(self.batch.device)
+        self.batch.run(graph=graph, stream=st)
+        self.select(st)
+
+    def select(self, stream=None) -> None:
+        """The selection and readback alone, on the towers' last results."""
+        st = stream if stream is not None else torch.cuda.current_stream(self.batch.device)
+        _lib.trig_array_select(self.array, self.batch.descs, self.out, self.scratch.data_ptr(), self.scratch_bytes,
+                               st.cuda_stream)
+
+    def results(self):
+        """(stats, selected seeds, windows, fragment offsets, readback hits),
+        each cut to what was stored."""
+        torch.cuda.synchronize(self.batch.device)
+        st = np.frombuffer(self.stats.cpu().numpy().tobytes()[: ASTATS_DTYPE.itemsize], ASTATS_DTYPE)[0].copy()
+        ns = min(int(st["n_selected"]), self.seed_cap)
+        nw = min(int(st["n_windows"]), self.win_cap)
+        nh = min(int(st["n_hits"]), self.hit_cap)
+        seeds = np.frombuffer(self.seeds[: ns * ASEED_DTYPE.itemsize].cpu().numpy().tobytes(), ASEED_DTYPE).copy()
+        wins = np.frombuffer(self.windows[: nw * WINDOW_DTYPE.itemsize].cpu().numpy().tobytes(), WINDOW_DTYPE).copy()
+        frag = np.frombuffer(self.frag_off[: (nw * self.n_towers + 1) * 8].cpu().numpy().tobytes(), np.uint64).copy()
+        hits = np.frombuffer(self.hits[: nh * HIT_DTYPE.itemsize].cpu().numpy().tobytes(), HIT_DTYPE).copy()
+        return st, seeds, wins, frag, hits

@@ -10,9 +10,13 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _declared():
-    src = open(os.path.join(ROOT, "include", "trig.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(trig_[a-z_0-9]+)\s*\(", src)))
+    names = set()
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(trig_[a-z_0-9]+)\s*\(", src))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")
@@ -38,7 +42,8 @@ def _c_layout(structs):
     """sizeof and field offsets of the header's structs, from gcc."""
     import subprocess
     import tempfile
-    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "trig.h"', 'int main(void) {']
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "trig.h"', '#include "trig_array.h"',
+             'int main(void) {']
     for name, fields in structs.items():
         lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
         for f in fields:
@@ -56,12 +61,16 @@ def test_binding_struct_sizes_match_header():
     from paper_1411_3968_gb300 import _lib
     ct = {"trig_params": _lib.trig_params, "trig_slice_dev": _lib.trig_slice_dev, "trig_result": _lib.trig_result,
           "trig_slice_events": _lib.trig_slice_events, "trig_tune_result": _lib.trig_tune_result,
-          "trig_geometry": _lib.trig_geometry}
+          "trig_geometry": _lib.trig_geometry, "trig_array_params": _lib.trig_array_params,
+          "trig_array_out": _lib.trig_array_out}
     np_types = {"trig_hit": _lib.HIT_DTYPE, "trig_trigger": _lib.TRIGGER_DTYPE, "trig_window": _lib.WINDOW_DTYPE,
-                "trig_slice_stats": _lib.STATS_DTYPE}
+                "trig_slice_stats": _lib.STATS_DTYPE, "trig_array_seed": _lib.ASEED_DTYPE,
+                "trig_array_stats": _lib.ASTATS_DTYPE}
     c_names = {"trig_hit": ["t_ns", "pmt", "charge", "reserved"], "trig_trigger": ["t_ns", "pmt", "charge", "count"],
                "trig_window": ["lo_ns", "hi_ns", "n_hits", "n_triggers"],
-               "trig_slice_stats": ["status", "flags", "n_hits", "n_seeds", "n_triggers", "n_windows", "n_events"]}
+               "trig_slice_stats": ["status", "flags", "n_hits", "n_seeds", "n_triggers", "n_windows", "n_events"],
+               "trig_array_seed": ["t_ns", "pmt", "tower", "n_towers"],
+               "trig_array_stats": ["n_tower_triggers", "n_selected", "n_windows", "n_hits", "flags", "status"]}
     lay = _c_layout({**{k: [f for f, _ in v._fields_] for k, v in ct.items()}, **c_names})
     for name, cls in ct.items():
         assert ctypes.sizeof(cls) == lay[name], name

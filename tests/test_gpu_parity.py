@@ -639,3 +639,118 @@ def test_rule_parameter_checks(pkg, params):
         _det(pkg, workload.nemo_tower(), dict(params, seed_rule=2))
     with pytest.raises(pkg.TrigError):
         _det(pkg, workload.nemo_tower(), dict(params, seed_rule=1, afc_window_ns=60001))
+
+
+# ------------------------------------------------------ multi-tower selection
+
+def _array_oracle(wl, par, K, W, h, k=0):
+    import oracle.array as oa
+    nt = len(wl.detectors)
+    seeds = [oracle.run(g.xyz_mm, g.floor_id, par, wl.runs[b].hits, [wl.run_slices[b][k]])[0].triggers
+             for b, g in enumerate(wl.detectors)]
+    return oa.select([g.xyz_mm for g in wl.detectors], par, K, W, h, seeds,
+                     [(wl.runs[b].hits, wl.runs[b].pmt_off) for b in range(nt)])
+
+
+def _array_run(pkg, wl, par, K, W, h, k=0, graph=False, **caps):
+    from paper_1411_3968_gb300.runner import ArrayBatch, SliceIn
+    nt = len(wl.detectors)
+    dets = [_det(pkg, g, par) for g in wl.detectors]
+    arr = pkg.Array(dets, min_towers=K, corr_window_ns=W, win_half_ns=h)
+    subs = wl.submissions[k * nt:(k + 1) * nt]
+    ab = ArrayBatch(arr, [SliceIn(dets[s.det_index], s.t0, s.stream.hits, s.stream.pmt_off) for s in subs], **caps)
+    ab.run(graph=graph)
+    out = ab.results()
+    return out, (ab, arr, dets)
+
+
+def _assert_array_same(got, ref, ctx=""):
+    st, seeds, wins, frag, hits = got
+    assert int(st["status"]) == 0 and int(st["flags"]) == 0, (ctx, st)
+    assert int(st["n_selected"]) == len(ref.seeds), ctx
+    for f in ("t", "pmt", "tower", "n_towers"):
+        assert np.array_equal(seeds[f], ref.seeds[f]), (ctx, f)
+    assert len(wins) == len(ref.windows), ctx
+    for f in ("lo", "hi", "n_hits", "n_triggers"):
+        assert np.array_equal(wins[f], ref.windows[f]), (ctx, f)
+    assert np.array_equal(frag, ref.frag_off), ctx
+    for f in ("t", "pmt", "charge"):
+        assert np.array_equal(hits[f], ref.hits[f]), (ctx, f)
+
+
+@pytest.mark.parametrize("K,W,h", [(2, 3000, 3000), (1, 3000, 3000), (3, 3000, 2000), (2, 800, 3000)])
+def test_array_selection_towers8(pkg, params, K, W, h):
+    """The eight KM3Net-It towers, one 200 ms slice each: selected seeds,
+    merged windows, fragment offsets and the readback, exact against the
+    oracle."""
+    wl = workload.cfg_towers8()
+    got, keep = _array_run(pkg, wl, params, K, W, h)
+    ref = _array_oracle(wl, params, K, W, h)
+    assert len(ref.seeds) > 0
+    _assert_array_same(got, ref, f"K={K} W={W} h={h}")
+
+
+def test_array_selection_two_slices_graph(pkg, params):
+    """Two contiguous periods (each tower's submission carries its halos),
+    the towers' trigger as a graph replay before the selection."""
+    wl = workload.cfg_towers8(seed=3, n_slices=2)
+    for k in range(2):
+        got, keep = _array_run(pkg, wl, params, 2, 3000, 3000, k=k, graph=True)
+        _assert_array_same(got, _array_oracle(wl, params, 2, 3000, 3000, k=k), f"period {k}")
+
+
+def test_array_selection_capacity_flags(pkg, params):
+    """Outputs smaller than needed: the flags say so and what was stored is
+    the prefix of the full result."""
+    wl = workload.cfg_towers8()
+    ref = _array_oracle(wl, params, 2, 3000, 3000)
+    nw = max(1, len(ref.windows) // 2)
+    (st, seeds, wins, frag, hits), keep = _array_run(pkg, wl, params, 2, 3000, 3000, seed_cap=5, win_cap=nw,
+                                                      hit_cap=10)
+    assert st["flags"] & pkg.TRIG_AFLAG_SEED_FULL and st["flags"] & pkg.TRIG_AFLAG_WIN_FULL
+    assert st["flags"] & pkg.TRIG_AFLAG_HIT_FULL and int(st["status"]) == pkg.TRIG_ECAPACITY
+    assert int(st["n_selected"]) == len(ref.seeds) and int(st["n_windows"]) == len(ref.windows)
+    assert np.array_equal(seeds["t"], ref.seeds["t"][:5])
+    assert np.array_equal(wins["lo"], ref.windows["lo"][:nw])
+    assert np.array_equal(frag, ref.frag_off[: nw * 8 + 1])
+    assert np.array_equal(hits["t"], ref.hits["t"][:10])
+
+
+def test_array_golden_fixture_on_gpu(pkg, params):
+    """The hand-derived two-tower fixture through the CUDA path."""
+    import json
+    fx = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "array", "two_towers.json")))
+    from paper_1411_3968_gb300.runner import ArrayBatch, SliceIn
+    t0 = fx["t0"]
+    towers = workload.split_towers(workload.tower_array(nx=2, ny=1))
+    par = dict(params, **fx["tower_params"])
+    streams = [workload.stream_from_rows([(t0 + t, p, q) for (t, p, q) in rows], 84) for rows in fx["hits_rel"]]
+    dets = [_det(pkg, g, par) for g in towers]
+    for name, v in fx["variants"].items():
+        ap = dict(fx["array_params"], **v["array_params"])
+        arr = pkg.Array(dets, **ap)
+        ab = ArrayBatch(arr, [SliceIn(d, t0, st.hits, st.pmt_off) for d, st in zip(dets, streams)])
+        ab.run()
+        st, seeds, wins, frag, hits = ab.results()
+        assert int(st["status"]) == 0, name
+        assert [[int(s["t"]) - t0, int(s["pmt"]), int(s["tower"]), int(s["n_towers"])] for s in seeds] == \
+            v["seeds_rel"], name
+        assert [[int(w["lo"]) - t0, int(w["hi"]) - t0, int(w["n_hits"]), int(w["n_triggers"])] for w in wins] == \
+            v["windows_rel"], name
+        frags = [[[int(x["t"]) - t0, int(x["pmt"]), int(x["charge"])] for x in hits[int(a):int(b)]]
+                 for a, b in zip(frag[:-1], frag[1:])]
+        assert frags == v["fragments_rel"], name
+        del ab
+        arr.close()
+
+
+def test_array_parameter_checks(pkg, params):
+    towers = workload.split_towers(workload.tower_array(nx=2, ny=1))
+    dets = [_det(pkg, g, params) for g in towers]
+    with pytest.raises(pkg.TrigError):
+        pkg.Array(dets, min_towers=0)
+    with pytest.raises(pkg.TrigError):
+        pkg.Array(dets, win_half_ns=4000)                   # beyond the towers' 3000 ns halo
+    odd = _det(pkg, towers[1], dict(params, tol_ns=25))
+    with pytest.raises(pkg.TrigError):
+        pkg.Array([dets[0], odd])

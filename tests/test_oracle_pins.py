@@ -614,3 +614,100 @@ def test_distinct_count_closed_form(params):
     err = means.std(ddof=1) / math.sqrt(len(means))
     assert abs(means.mean() - np.mean(expects)) < 4 * err + 1e-9, (means.mean(), np.mean(expects), err)
     assert abs(means.mean() - np.mean(plains)) > 4 * err
+
+
+# ------------------------------------------------------ multi-tower selection
+
+def _array_case(fx_hits_rel, t0, tower_par):
+    g = workload.tower_array(nx=2, ny=1)
+    towers = workload.split_towers(g)
+    streams = [workload.stream_from_rows([(t0 + t, p, q) for (t, p, q) in rows], 84) for rows in fx_hits_rel]
+    seeds = [oracle.run(tw.xyz_mm, tw.floor_id, tower_par, st.hits, [t0])[0].triggers for tw, st in zip(towers, streams)]
+    return towers, streams, seeds
+
+
+def test_array_selection_golden_fixture():
+    import oracle.array as oa
+    fx = json.load(open(os.path.join(GOLDEN, "array", "two_towers.json")))
+    t0 = fx["t0"]
+    tower_par = dict(workload.DEFAULT_PARAMS, **fx["tower_params"])
+    towers, streams, seeds = _array_case(fx["hits_rel"], t0, tower_par)
+    for name, v in fx["variants"].items():
+        ap = dict(fx["array_params"], **v["array_params"])
+        r = oa.select([tw.xyz_mm for tw in towers], tower_par, ap["min_towers"], ap["corr_window_ns"],
+                      ap["win_half_ns"], seeds, [(st.hits, st.pmt_off) for st in streams])
+        assert [[int(s["t"]) - t0, int(s["pmt"]), int(s["tower"]), int(s["n_towers"])] for s in r.seeds] == \
+            v["seeds_rel"], name
+        assert [[int(w["lo"]) - t0, int(w["hi"]) - t0, int(w["n_hits"]), int(w["n_triggers"])] for w in r.windows] \
+            == v["windows_rel"], name
+        frags = [[[int(h["t"]) - t0, int(h["pmt"]), int(h["charge"])] for h in r.hits[int(a):int(b)]]
+                 for a, b in zip(r.frag_off[:-1], r.frag_off[1:])]
+        assert frags == v["fragments_rel"], name
+
+
+def _array_brute(tower_xyz, par, K, W, h, seeds, streams):
+    """All pairs of seeds, the distance in pure Python, no search."""
+    allp = [(b, s) for b, S in enumerate(seeds) for s in S.tolist()]
+    out = []
+    for a, s in allp:
+        ts, ps = s[0], s[1]
+        tw = set()
+        for b, j in allp:
+            d = sum((int(tower_xyz[a][ps][c]) - int(tower_xyz[b][j[1]][c])) ** 2 for c in range(3))
+            lim = min(par["tol_ns"] + _k_exact(d, par["n_num"], par["n_den"]), W)
+            if abs(j[0] - ts) <= lim:
+                tw.add(b)
+        if len(tw) >= K:
+            out.append((ts, a, s, len(tw)))
+    out.sort(key=lambda x: (x[0], x[1]))
+    sel = [(x[0], x[2][1], x[1], x[3]) for x in out]
+    wins = []
+    for (t, _, _, _) in sel:
+        if wins and t - h <= wins[-1][1] + 1:
+            wins[-1][1] = max(wins[-1][1], t + h)
+            wins[-1][2] += 1
+        else:
+            wins.append([t - h, t + h, 1])
+    frags = []
+    for lo, hi, _ in wins:
+        for b, (hits, off) in enumerate(streams):
+            frags.append([(int(x["t"]), int(x["pmt"]), int(x["charge"])) for x in hits if lo <= int(x["t"]) <= hi])
+    return sel, [(lo, hi, k) for lo, hi, k in wins], frags
+
+
+@pytest.mark.parametrize("case", range(4))
+def test_array_selection_matches_bruteforce(case, params):
+    """Random seeds on two or three towers: selection, windows and readback
+    equal the all-pairs definition."""
+    import oracle.array as oa
+    rng = np.random.Generator(np.random.PCG64(1300 + case))
+    g = workload.tower_array(nx=2 + case % 2, ny=1)
+    towers = workload.split_towers(g)
+    par = dict(params, threshold=1, slice_ns=40_000)
+    t0 = 3_000_000
+    K = int(rng.integers(1, 4))
+    W, h = int(rng.choice([600, 3000])), int(rng.choice([500, 3000]))
+    streams, seeds = [], []
+    centers = rng.integers(t0, t0 + par["slice_ns"], 12)
+    for tw in towers:
+        rows = []
+        for c in centers:
+            for _ in range(int(rng.integers(0, 3))):
+                rows.append((int(c + rng.integers(-700, 701)), int(rng.integers(0, 84)), 300))
+        for _ in range(30):
+            rows.append((int(rng.integers(t0 - 4000, t0 + par["slice_ns"] + 4000)), int(rng.integers(0, 84)),
+                         int(rng.integers(1, 300))))
+        st = workload.stream_from_rows(rows, 84)
+        streams.append(st)
+        seeds.append(oracle.run(tw.xyz_mm, tw.floor_id, par, st.hits, [t0])[0].triggers)
+    r = oa.select([tw.xyz_mm for tw in towers], par, K, W, h, seeds, [(s.hits, s.pmt_off) for s in streams])
+    sel, wins, frags = _array_brute([tw.xyz_mm for tw in towers], par, K, W, h, seeds,
+                                    [(s.hits, s.pmt_off) for s in streams])
+    assert len(sel) > 0
+    assert [(int(s["t"]), int(s["pmt"]), int(s["tower"]), int(s["n_towers"])) for s in r.seeds] == sel
+    assert [(int(w["lo"]), int(w["hi"]), int(w["n_triggers"])) for w in r.windows] == wins
+    got = [[(int(x["t"]), int(x["pmt"]), int(x["charge"])) for x in r.hits[int(a):int(b)]]
+           for a, b in zip(r.frag_off[:-1], r.frag_off[1:])]
+    assert got == frags
+    assert [int(w["n_hits"]) for w in r.windows] == [
+        sum(len(f) for f in frags[k * len(towers):(k + 1) * len(towers)]) for k in range(len(wins))]

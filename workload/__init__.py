@@ -241,6 +241,46 @@ def concat_streams(parts: list[Stream]) -> Stream:
     return Stream(np.concatenate(segs) if segs else np.empty(0, HIT_DTYPE), off)
 
 
+def split_towers(det: Detector) -> list[Detector]:
+    """The towers of an array as detectors of their own, PMTs renumbered
+    from 0 in their array order, positions kept in the array's frame."""
+    out = []
+    for tw in sorted(set(det.tower_id.tolist())):
+        idx = np.nonzero(det.tower_id == tw)[0]
+        out.append(Detector(f"{det.name}.t{tw}", np.ascontiguousarray(det.xyz_mm[idx]),
+                            np.ascontiguousarray(det.floor_id[idx]), np.ascontiguousarray(det.tower_id[idx])))
+    return out
+
+
+def split_stream(stream: Stream, det: Detector) -> list[Stream]:
+    """An array's stream cut into per-tower streams (the PMT numbering of
+    split_towers); a tower's PMTs must be contiguous in the array."""
+    out = []
+    for tw in sorted(set(det.tower_id.tolist())):
+        idx = np.nonzero(det.tower_id == tw)[0]
+        p0, p1 = int(idx[0]), int(idx[-1]) + 1
+        if p1 - p0 != len(idx):
+            raise ValueError("a tower's PMTs are not contiguous")
+        a, b = int(stream.pmt_off[p0]), int(stream.pmt_off[p1])
+        hits = stream.hits[a:b].copy()
+        hits["pmt"] -= p0
+        out.append(Stream(hits, (stream.pmt_off[p0:p1 + 1] - stream.pmt_off[p0]).astype(np.uint64)))
+    return out
+
+
+def stream_from_rows(rows, n_pmt: int) -> Stream:
+    """(t, pmt, charge) rows in any order as a stream grouped by PMT, time
+    order within a PMT (equal times keep their row order)."""
+    hits = np.zeros(len(rows), HIT_DTYPE)
+    for i, (t, p, q) in enumerate(rows):
+        hits[i] = (t, p, q, 0)
+    order = np.lexsort((np.arange(len(hits)), hits["t"], hits["pmt"]))
+    hits = hits[order]
+    off = np.zeros(n_pmt + 1, np.uint64)
+    np.cumsum(np.bincount(hits["pmt"], minlength=n_pmt), out=off[1:])
+    return Stream(hits, off)
+
+
 # --------------------------------------------------------------- workloads
 
 @dataclass
@@ -329,6 +369,22 @@ def cfg_scaled(seed: int = 0, threads=None) -> Workload:
     return Workload("array2688_1slice", [det], subs, [full], [t0s])
 
 
+def cfg_towers8(seed: int = 0, n_slices: int = 1, threads=None) -> Workload:
+    """The eight KM3Net-It towers of the paper's proposed DAQ (84 PMTs each,
+    4 x 2 on a 90 m grid) as eight detectors: contiguous 200 ms slices with
+    halos at 55 kHz, 1000 muons per slice crossing the array.  Submission
+    k * 8 + b is tower b's slice k; runs[b] is tower b's whole stream."""
+    arr = tower_array(nx=4, ny=2)
+    towers = split_towers(arr)
+    full, subs, t0s = _contiguous(arr, 0, n_slices, 55e3, seed, stream=6, n_muons=1000 * n_slices,
+                                  threads=threads)
+    out = []
+    for s in subs:
+        for b, st in enumerate(split_stream(s.stream, arr)):
+            out.append(Submission(b, s.t0, st))
+    return Workload(f"towers8_{n_slices}slice", towers, out, split_stream(full, arr), [list(t0s) for _ in towers])
+
+
 def cfg_serving_pool(seed: int = 0, slices_per_det: int = 20, threads=None,
                      dets: list[tuple[str, float]] | None = None) -> Workload:
     """Pre-generated slice pools of 4 detectors (32 @ 50 kHz, 84 @ 55 kHz,
@@ -352,6 +408,7 @@ CONFIGS = {
     "km3": cfg_km3,
     "batched": cfg_batched,
     "scaled": cfg_scaled,
+    "towers8": cfg_towers8,
     "serving": cfg_serving_pool,
 }
 
