@@ -620,16 +620,40 @@ struct TileLayout {
     }
 };
 
+// Dynamic shared memory of the tile kernel (layout TileLayout<CAP>).
+extern __shared__ __align__(128) unsigned char g_tile_smem[];
+
+// The tile kernel's shared-memory regions sit at fixed offsets, so their
+// addresses are recomputed where used instead of living in registers
+// through every phase; only the PMT-table stride depends on the launch.
+template <int CAP>
 struct TileCtx {
-    uint64_t *stage[2];
-    uint64_t *temp;
-    uint32_t *cnt;
-    uint32_t *mask;
-    uint16_t *floor_s;
-    uint16_t *dmax_s;
-    uint16_t *dt_s;
-    const uint16_t *dt_g;
-    uint32_t P;
+    using L = TileLayout<CAP>;
+    uint32_t P;             // PMTs of the loaded slice
+    uint32_t pp;            // PMT table stride: the launch's max_pmt rounded up to 8
+    const uint16_t *dt_g;   // the loaded slice's dt table in global memory
+    __device__ __forceinline__ uint64_t *stage(uint32_t b) const
+    {
+        return reinterpret_cast<uint64_t *>(g_tile_smem + (size_t)b * L::kStage);
+    }
+    __device__ __forceinline__ uint64_t *temp() const
+    {
+        return reinterpret_cast<uint64_t *>(g_tile_smem + 2 * L::kStage);
+    }
+    __device__ __forceinline__ uint32_t *cnt() const
+    {
+        return reinterpret_cast<uint32_t *>(g_tile_smem + 2 * L::kStage + L::kTemp);
+    }
+    __device__ __forceinline__ uint32_t *mask() const
+    {
+        return reinterpret_cast<uint32_t *>(g_tile_smem + 2 * L::kStage + L::kTemp + L::kCnt);
+    }
+    __device__ __forceinline__ uint16_t *floor_s() const
+    {
+        return reinterpret_cast<uint16_t *>(g_tile_smem + 2 * L::kStage + L::kTemp + L::kCnt + L::kMask);
+    }
+    __device__ __forceinline__ uint16_t *dmax_s() const { return floor_s() + pp; }
+    __device__ __forceinline__ uint16_t *dt_s() const { return floor_s() + 2 * (size_t)pp; }
 };
 
 constexpr uint32_t kBarCons = 1;        // named barrier of the consumers
@@ -691,12 +715,12 @@ __device__ __forceinline__ uint32_t bucket_of(uint32_t t_rel, uint32_t bsh)
 // 32-bit forms (t_rel << 12 | pmt, the staged range spans < 2^20 ns) at
 // buf + CAP.  Counting sort on
 // the time bucket t_rel >> bsh, then each key's rank inside its bucket;
-// cx.cnt[b] keeps the index of bucket b's first key (cx.cnt[NBK] = n), so a
+// cx.cnt()[b] keeps the index of bucket b's first key (cx.cnt()[NBK] = n), so a
 // time range maps to an index range without a search.  Also counts the keys
 // with t_rel < lo_t and < hi_t into red[NC/32 + 1] and red[NC/32 + 2] (the
 // first core index and the core's end).  Returns bsh.
 template <int CAP, int NC>
-__device__ uint32_t tile_sort(TileCtx &cx, uint64_t *buf, uint32_t n, int64_t tb, uint32_t span, uint32_t *red,
+__device__ uint32_t tile_sort(TileCtx<CAP> &cx, uint64_t *buf, uint32_t n, int64_t tb, uint32_t span, uint32_t *red,
                               uint32_t lo_t, uint32_t hi_t)
 {
     uint32_t *pk = reinterpret_cast<uint32_t *>(buf + CAP);      // packed keys, upper half of the buffer
@@ -710,7 +734,7 @@ __device__ uint32_t tile_sort(TileCtx &cx, uint64_t *buf, uint32_t n, int64_t tb
         uint32_t nb_bits = 31u - __clz((uint32_t)NBK);
         bsh = top > nb_bits ? top - nb_bits : 0u;
     }
-    for (uint32_t i = tid; i < (uint32_t)NBK; i += NC) cx.cnt[i] = 0;
+    for (uint32_t i = tid; i < (uint32_t)NBK; i += NC) cx.cnt()[i] = 0;
     if (tid == 0) red[NW + 1] = red[NW + 2] = 0;
     cons_sync<NC>();
     uint64_t kreg[PER];
@@ -728,7 +752,7 @@ __device__ uint32_t tile_sort(TileCtx &cx, uint64_t *buf, uint32_t n, int64_t tb
             int64_t rel = t - tb;
             uint32_t tr = rel < 0 ? 0u : (rel > 0xffffffffll ? 0xffffffffu : (uint32_t)rel);
             kreg[r] = ((uint64_t)tr << 32) | ((uint64_t)(w1 & 0xffffu) << 16) | (uint64_t)(w1 >> 16);
-            slot[r] = atomicAdd(&cx.cnt[bucket_of<CAP>(tr, bsh)], 1u);
+            slot[r] = atomicAdd(&cx.cnt()[bucket_of<CAP>(tr, bsh)], 1u);
             below_lo += tr < lo_t;
             below_hi += tr < hi_t;
         }
@@ -740,23 +764,23 @@ __device__ uint32_t tile_sort(TileCtx &cx, uint64_t *buf, uint32_t n, int64_t tb
         if (below_hi) atomicAdd(&red[NW + 2], below_hi);
     }
     cons_sync<NC>();
-    cons_exclusive_scan<NC>(cx.cnt, NBK, red);
+    cons_exclusive_scan<NC>(cx.cnt(), NBK, red);
 #pragma unroll
     for (int r = 0; r < PER; ++r) {
         uint32_t i = tid + r * NC;
         if (r * NC < n && i < n) {
-            cx.temp[cx.cnt[bucket_of<CAP>(key_t(kreg[r]), bsh)] + slot[r]] = kreg[r];
+            cx.temp()[cx.cnt()[bucket_of<CAP>(key_t(kreg[r]), bsh)] + slot[r]] = kreg[r];
         }
     }
     cons_sync<NC>();
     // rank inside each bucket; identical keys are interchangeable
     for (uint32_t j = tid; j < n; j += NC) {
-        uint64_t k = cx.temp[j];
+        uint64_t k = cx.temp()[j];
         const uint32_t bk = bucket_of<CAP>(key_t(k), bsh);
-        uint32_t s0 = cx.cnt[bk], s1 = cx.cnt[bk + 1];
+        uint32_t s0 = cx.cnt()[bk], s1 = cx.cnt()[bk + 1];
         uint32_t r = s0;
         for (uint32_t m = s0; m < s1; ++m) {
-            uint64_t o = cx.temp[m];
+            uint64_t o = cx.temp()[m];
             r += (o < k) || (o == k && m < j);
         }
         buf[r] = k;
@@ -820,8 +844,8 @@ __device__ __noinline__ bool coincidence_seed(const uint32_t *pk, uint32_t n, ui
 // PMTs among the keys j with |t_j - t_s| <= min(dt_max[p_s][p_j], W).
 // Eight lanes per seed each collect a 128-bit PMT set over every eighth key
 // of the seed's scan range; the sets are OR-ed and counted.
-template <int NC, bool SMEM_DT>
-__device__ __noinline__ void count_distinct_pmts(const TileCtx &cx, const uint32_t *pk, uint32_t n, uint32_t ns,
+template <int CAP, int NC, bool SMEM_DT>
+__device__ __noinline__ void count_distinct_pmts(const TileCtx<CAP> &cx, const uint32_t *pk, uint32_t n, uint32_t ns,
                                                  const uint16_t *seed_idx, const uint32_t *swin, uint16_t *seed_cnt)
 {
     constexpr uint32_t G = 8, NG = NC / G;
@@ -836,7 +860,7 @@ __device__ __noinline__ void count_distinct_pmts(const TileCtx &cx, const uint32
             const uint32_t ts = pk_t(ks), ps = pk_p(ks);
             const uint32_t j0 = w & 0xffffu, j1 = w >> 16;
             if (CHECK(12, j1, n + 1) && CHECK(13, ps, P)) {
-                const uint16_t *row_s = cx.dt_s + (size_t)ps * P;
+                const uint16_t *row_s = cx.dt_s() + (size_t)ps * P;
                 const uint16_t *row_g = cx.dt_g + (size_t)ps * P;
                 for (uint32_t q = j0 + gl; q < j1; q += G) {
                     const uint32_t kj = pk[q], tj = pk_t(kj), pj = pk_p(kj);
@@ -912,7 +936,7 @@ __device__ __noinline__ bool level0_pass(const uint32_t *pk, uint32_t n, uint32_
 
 // The core is keys[c0, c1) (t_rel in [H, H + core width)).
 template <int CAP, int NC, bool SMEM_DT, bool EXT>
-__device__ CoreOut tile_trigger(TileCtx &cx, const uint64_t *keys, uint32_t n, uint32_t bsh, uint32_t c0, uint32_t c1,
+__device__ CoreOut tile_trigger(TileCtx<CAP> &cx, const uint64_t *keys, uint32_t n, uint32_t bsh, uint32_t c0, uint32_t c1,
                                 int64_t tb, const TrigParams &tp, trig_trigger *out, int64_t dbg_rank_lo,
                                 uint32_t *red)
 {
@@ -922,9 +946,9 @@ __device__ CoreOut tile_trigger(TileCtx &cx, const uint64_t *keys, uint32_t n, u
     const uint32_t tau = tp.tau, qseed = tp.q_seed, threshold = tp.threshold, P = cx.P;
     // scratch per seed (CAP entries each): index and count (16-bit), scan
     // range (32-bit)
-    uint16_t *seed_idx = reinterpret_cast<uint16_t *>(cx.temp);
+    uint16_t *seed_idx = reinterpret_cast<uint16_t *>(cx.temp());
     uint16_t *seed_cnt = seed_idx + CAP;
-    const uint32_t *boff = cx.cnt;          // bucket offsets of the sorted keys
+    const uint32_t *boff = cx.cnt();          // bucket offsets of the sorted keys
 
     // 1. seed flags (one bit per core hit): charge over threshold, or a hit
     //    on another PMT of the same floor within tau.  A warp holds 32
@@ -939,7 +963,7 @@ __device__ CoreOut tile_trigger(TileCtx &cx, const uint64_t *keys, uint32_t n, u
         // hits past the core (halo) are loaded too: they are neighbours
         const uint32_t ki = i < n ? pk[i] : kPkNone;
         const uint32_t ti = pk_t(ki), pi = pk_p(ki);
-        const uint32_t fi = in ? cx.floor_s[pi] : 0u;
+        const uint32_t fi = in ? cx.floor_s()[pi] : 0u;
         bool seed = in && key_q(keys[i]) >= qseed;
         bool more_up = false, more_dn = false;
         if (EXT && tp.seed_rule == 1) {
@@ -956,8 +980,8 @@ __device__ CoreOut tile_trigger(TileCtx &cx, const uint64_t *keys, uint32_t n, u
             if (in && i + dd >= n) kd = kPkNone;
             const bool near_u = ku != kPkNone && ti - pk_t(ku) <= tau;
             const bool near_d = kd != kPkNone && pk_t(kd) - ti <= tau;
-            if (near_u && pk_p(ku) != pi && cx.floor_s[pk_p(ku)] == fi) seed = true;
-            if (near_d && pk_p(kd) != pi && cx.floor_s[pk_p(kd)] == fi) seed = true;
+            if (near_u && pk_p(ku) != pi && cx.floor_s()[pk_p(ku)] == fi) seed = true;
+            if (near_d && pk_p(kd) != pi && cx.floor_s()[pk_p(kd)] == fi) seed = true;
             more_up = near_u;
             more_dn = near_d;
         }
@@ -966,12 +990,12 @@ __device__ CoreOut tile_trigger(TileCtx &cx, const uint64_t *keys, uint32_t n, u
             for (uint32_t j = i + 3; more_dn && j < n; ++j) {
                 const uint32_t kj = pk[j];
                 if (pk_t(kj) - ti > tau) break;
-                if (pk_p(kj) != pi && cx.floor_s[pk_p(kj)] == fi) { seed = true; break; }
+                if (pk_p(kj) != pi && cx.floor_s()[pk_p(kj)] == fi) { seed = true; break; }
             }
             for (uint32_t j = i - 2; more_up && !seed && j-- > 0;) {
                 const uint32_t kj = pk[j];
                 if (ti - pk_t(kj) > tau) break;
-                if (pk_p(kj) != pi && cx.floor_s[pk_p(kj)] == fi) { seed = true; break; }
+                if (pk_p(kj) != pi && cx.floor_s()[pk_p(kj)] == fi) { seed = true; break; }
             }
         }
         }
@@ -979,7 +1003,7 @@ __device__ CoreOut tile_trigger(TileCtx &cx, const uint64_t *keys, uint32_t n, u
         if (EXT && tp.l0_hits && seed && in) seed = level0_pass(pk, n, i, tp.l0_hits, tp.l0_window, tp.l0_distinct != 0);
         // halo hits past the core are neighbours only, never seeds here
         const uint32_t m = __ballot_sync(0xffffffffu, seed && in);
-        if (lane == 0 && (base + warp * 32) < ncore) cx.mask[(base + warp * 32) >> 5] = m;
+        if (lane == 0 && (base + warp * 32) < ncore) cx.mask()[(base + warp * 32) >> 5] = m;
     }
     cons_sync<NC>();
 
@@ -988,7 +1012,7 @@ __device__ CoreOut tile_trigger(TileCtx &cx, const uint64_t *keys, uint32_t n, u
     uint32_t *wtot = red + 2;                             // [NW + 1]
     {
         const uint32_t w = warp * wpw + lane;
-        const uint32_t m = (lane < wpw && w < nwords) ? cx.mask[w] : 0u;
+        const uint32_t m = (lane < wpw && w < nwords) ? cx.mask()[w] : 0u;
         const uint32_t pc = __popc(m);
         const uint32_t incl = warp_incl_scan(pc);
         if (lane == 31) wtot[warp] = incl;
@@ -1018,7 +1042,7 @@ __device__ CoreOut tile_trigger(TileCtx &cx, const uint64_t *keys, uint32_t n, u
     uint32_t *swin = reinterpret_cast<uint32_t *>(seed_cnt + CAP);    // j0 | j1 << 16
     for (uint32_t k = tid; k < ns; k += NC) {
         const uint32_t ks = pk[seed_idx[k]];
-        const uint32_t ts = pk_t(ks), dm = cx.dmax_s[pk_p(ks)];
+        const uint32_t ts = pk_t(ks), dm = cx.dmax_s()[pk_p(ks)];
         const uint32_t j0 = boff[bucket_of<CAP>(ts >= dm ? ts - dm : 0u, bsh)];
         const uint32_t j1 = boff[bucket_of<CAP>(ts + dm, bsh) + 1];
         swin[k] = j0 | (j1 << 16);
@@ -1030,7 +1054,7 @@ __device__ CoreOut tile_trigger(TileCtx &cx, const uint64_t *keys, uint32_t n, u
     //    tile's density), seeds dealt round-robin to the groups, four
     //    independent tests per lane in flight
     if (EXT && tp.count_distinct) {
-        count_distinct_pmts<NC, SMEM_DT>(cx, pk, n, ns, seed_idx, swin, seed_cnt);
+        count_distinct_pmts<CAP, NC, SMEM_DT>(cx, pk, n, ns, seed_idx, swin, seed_cnt);
     } else {
         // expected keys in a scan range: 2H + 1 ns at the tile's density
         const unsigned long long span_n = n ? (unsigned long long)pk_t(pk[n - 1]) + 1ull : 1ull;
@@ -1047,7 +1071,7 @@ __device__ CoreOut tile_trigger(TileCtx &cx, const uint64_t *keys, uint32_t n, u
                 const uint32_t ts = pk_t(ks), ps = pk_p(ks);
                 const uint32_t j0 = w & 0xffffu, j1 = w >> 16;
                 if (CHECK(12, j1, n + 1) && CHECK(13, ps, P)) {
-                    const uint16_t *row_s = cx.dt_s + (size_t)ps * P;
+                    const uint16_t *row_s = cx.dt_s() + (size_t)ps * P;
                     const uint16_t *row_g = cx.dt_g + (size_t)ps * P;
                     // key kj counts when |t_j - t_s| <= dt[p_s][p_j]
                     auto causal = [&](uint32_t kj) -> uint32_t {
@@ -1159,7 +1183,7 @@ __device__ CoreOut tile_trigger(TileCtx &cx, const uint64_t *keys, uint32_t n, u
 // loads after per-PMT binary searches.  A 1 ns core that still does not
 // fit is reported (TRIG_FLAG_TILE_FULL) and skipped.
 template <int CAP, int NC, bool SMEM_DT, bool EXT>
-__device__ void tile_overflow(TileCtx &cx, uint64_t *buf, const SliceDesc &d, const TrigParams &tp, uint32_t g,
+__device__ void tile_overflow(TileCtx<CAP> &cx, uint64_t *buf, const SliceDesc &d, const TrigParams &tp, uint32_t g,
                               uint32_t *red, int64_t *stk)
 {
     constexpr uint32_t NW = NC / 32;
@@ -1293,32 +1317,14 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 
                                                                           const SliceDesc *__restrict__ desc,
                                                                           uint32_t max_pmt)
 {
-    using L = TileLayout<CAP>;
     constexpr uint32_t NW = NC / 32;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t full_bar[2], empty_bar[2];
     __shared__ ItemInfo info[2];
     __shared__ __align__(16) uint32_t red[64 + 64];
     __shared__ int64_t stk[128];
 
-    TileCtx cx;
-    unsigned char *sp = smem_raw;
-    cx.stage[0] = reinterpret_cast<uint64_t *>(sp);
-    sp += L::kStage;
-    cx.stage[1] = reinterpret_cast<uint64_t *>(sp);
-    sp += L::kStage;
-    cx.temp = reinterpret_cast<uint64_t *>(sp);
-    sp += L::kTemp;
-    cx.cnt = reinterpret_cast<uint32_t *>(sp);
-    sp += L::kCnt;
-    cx.mask = reinterpret_cast<uint32_t *>(sp);
-    sp += L::kMask;
-    const uint32_t pp = (max_pmt + 7) & ~7u;
-    cx.floor_s = reinterpret_cast<uint16_t *>(sp);
-    sp += (size_t)pp * 2;
-    cx.dmax_s = reinterpret_cast<uint16_t *>(sp);
-    sp += (size_t)pp * 2;
-    cx.dt_s = reinterpret_cast<uint16_t *>(sp);
+    TileCtx<CAP> cx;
+    cx.pp = (max_pmt + 7) & ~7u;
     cx.dt_g = nullptr;
     cx.P = 0;
 
@@ -1438,7 +1444,7 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 
             __syncwarp();
             if (mode == 0 && wide) {
                 if (lane == 0 && CHECK(7, rlo + tot, d->n_hits + 1))
-                    bulk_g2s(cx.stage[b], d->tbuf + rlo, (uint32_t)tot * 16u, &full_bar[b]);
+                    bulk_g2s(cx.stage(b), d->tbuf + rlo, (uint32_t)tot * 16u, &full_bar[b]);
             } else if (mode == 0) {
                 uint32_t dst = 0;
 #pragma unroll
@@ -1447,7 +1453,7 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 
                     const uint64_t a = ra[r];
                     const uint32_t incl = warp_incl_scan(len);
                     if (len && CHECK(6, dst + incl, CAP + 1) && CHECK(7, a + len, d->n_hits + 1))
-                        bulk_g2s(cx.stage[b] + 2 * (size_t)(dst + incl - len), d->hits + a, len * 16u, &full_bar[b]);
+                        bulk_g2s(cx.stage(b) + 2 * (size_t)(dst + incl - len), d->hits + a, len * 16u, &full_bar[b]);
                     dst += __shfl_sync(0xffffffffu, incl, 31);
                 }
             }
@@ -1461,15 +1467,16 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 
     // the slice's trigger parameters live in shared memory (written by one
     // thread when the slice changes), keeping registers for the tile phases
     __shared__ TrigParams tp;
-    int64_t sl_w = 0, sl_t0 = 0, sl_len = 0;
-    uint64_t sl_rank0 = 0;
+    // the loaded slice's tile width, t0, length and merged rank of its first
+    // owned hit, also kept in shared memory
+    __shared__ int64_t sl[4];
     for (uint32_t it = 0;; ++it) {
         const uint32_t b = it & 1u, use = it >> 1;
         if (!mbar_wait(&full_bar[b], use & 1u)) {
             if (tid == 0) atomicOr(&hdr->err, TRIG_FLAG_TIMEOUT);
             break;
         }
-        const ItemInfo inf = info[b];
+        const ItemInfo &inf = info[b];      // stable until this buffer is released
         if (inf.item < 0) break;
         const SliceDesc &d = desc[inf.slice];
         if (&d != loaded) {
@@ -1477,11 +1484,11 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 
             cons_sync<NC>();
             const uint32_t P = d.n_pmt;
             for (uint32_t p = tid; p < P; p += NC) {
-                cx.floor_s[p] = d.floor[p];
-                cx.dmax_s[p] = d.dmax_row[p];
+                cx.floor_s()[p] = d.floor[p];
+                cx.dmax_s()[p] = d.dmax_row[p];
             }
             if (SMEM_DT && P <= kSmemDtMaxPmt)
-                for (uint32_t i = tid; i < P * P; i += NC) cx.dt_s[i] = d.dt[i];
+                for (uint32_t i = tid; i < P * P; i += NC) cx.dt_s()[i] = d.dt[i];
             cx.dt_g = d.dt;
             cx.P = P;
             loaded = &d;
@@ -1502,10 +1509,12 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 
                 tp.dbg_merged = d.dbg_merged;
                 tp.dbg_seedcnt = d.dbg_seedcnt;
             }
-            sl_w = d.tile_w;
-            sl_t0 = d.t0;
-            sl_len = d.slice_ns;
-            sl_rank0 = d.dbg_rank0;
+            if (tid == 0) {
+                sl[0] = d.tile_w;
+                sl[1] = d.t0;
+                sl[2] = d.slice_ns;
+                sl[3] = (int64_t)d.dbg_rank0;
+            }
             cons_sync<NC>();
         }
         if (inf.mode == 2) {
@@ -1514,21 +1523,21 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 
                 d.tile_rank[inf.g] = 0;
             }
         } else if (inf.mode == 1) {
-            tile_overflow<CAP, NC, SMEM_DT, EXT>(cx, cx.stage[b], d, tp, inf.g, red, stk);
+            tile_overflow<CAP, NC, SMEM_DT, EXT>(cx, cx.stage(b), d, tp, inf.g, red, stk);
         } else {
-            const int64_t W = sl_w;
-            const int64_t Bg = sl_t0 + (int64_t)inf.g * W;
-            const int64_t core_end = min(Bg + W, sl_t0 + sl_len);
+            const int64_t W = sl[0];
+            const int64_t Bg = sl[1] + (int64_t)inf.g * W;
+            const int64_t core_end = min(Bg + W, sl[1] + sl[2]);
             // the staged range starts lo_t (>= H) before the core
             const uint32_t lo_t = inf.lo_t;
             const int64_t tb = Bg - (int64_t)lo_t;
             const uint32_t hi_t = lo_t + (uint32_t)(core_end - Bg);
-            const uint32_t bsh = tile_sort<CAP, NC>(cx, cx.stage[b], inf.n, tb, inf.span, red, lo_t, hi_t);
+            const uint32_t bsh = tile_sort<CAP, NC>(cx, cx.stage(b), inf.n, tb, inf.span, red, lo_t, hi_t);
             // rank of the core's first hit = rank_lo + c0, known after the sort
             const uint32_t c0 = red[NW + 1], c1 = red[NW + 2];
             const uint32_t tile_rank = inf.rank_lo + c0;
-            CoreOut co = tile_trigger<CAP, NC, SMEM_DT, EXT>(cx, cx.stage[b], inf.n, bsh, c0, c1, tb, tp,
-                                                         d.stage + tile_rank, (int64_t)inf.rank_lo - (int64_t)sl_rank0,
+            CoreOut co = tile_trigger<CAP, NC, SMEM_DT, EXT>(cx, cx.stage(b), inf.n, bsh, c0, c1, tb, tp,
+                                                         d.stage + tile_rank, (int64_t)inf.rank_lo - sl[3],
                                                          red);
             if (tid == 0 && CHECK(14, (uint64_t)tile_rank + co.n_fired, d.n_hits + 1) && CHECK(15, inf.g, d.n_tiles)) {
                 d.tile_nfired[inf.g] = co.n_fired;
