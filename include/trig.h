@@ -228,6 +228,15 @@ int trig_engine_stats(uint64_t *batches, uint64_t *slices);
 /* Message of the calling thread's last failure ("" if none). */
 const char *trig_last_error(void);
 
+/* Page-locked host memory for a producer's slice buffers (the Hit
+ * Manager's output, "DAQ system of NEMO Phase II"): trig_submit_slice
+ * copies such buffers to the device by DMA, without the driver's staging
+ * of pageable memory, whose speed depends on how the host's pages are
+ * laid out.  *out receives `bytes` bytes (16-byte aligned) owned by the
+ * caller until trig_host_free.  Errors: TRIG_EINVAL, TRIG_ENOMEM. */
+int trig_host_alloc(size_t bytes, void **out);
+int trig_host_free(void *ptr);
+
 /* ------------------------------------------------------- device batches */
 
 /* One slice for trig_batch_run.  All buffers are device memory owned by the

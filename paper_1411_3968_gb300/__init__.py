@@ -12,5 +12,5 @@ from ._lib import (  # noqa: F401
     trig_batch_events_scratch_bytes, trig_set_events, TRIG_FLAG_EV_FULL,
     trig_poll, trig_set_tile_config, trig_slice_rows, trig_submit_slice, win_cap_for,
     Array, ASEED_DTYPE, ASTATS_DTYPE, TRIG_AFLAG_SEED_FULL, TRIG_AFLAG_WIN_FULL, TRIG_AFLAG_HIT_FULL,
-    TRIG_AFLAG_TOWER_INCOMPLETE, trig_array_scratch_bytes, trig_array_select,
+    TRIG_AFLAG_TOWER_INCOMPLETE, trig_array_scratch_bytes, trig_array_select, pinned_copy,
 )

@@ -53,7 +53,7 @@ EXPORTS = [
     "trig_batch_scratch_bytes", "trig_batch_run", "trig_slice_rows", "trig_set_tile_config",
     "trig_get_tile_config", "trig_kernel_launch_count", "trig_kernel_times", "trig_batch_run_noalloc",
     "trig_autotune", "trig_detector_tile_config", "trig_batch_events_scratch_bytes", "trig_batch_run_events",
-    "trig_set_events", "trig_array_create", "trig_array_destroy", "trig_array_scratch_bytes", "trig_array_select",
+    "trig_set_events", "trig_host_alloc", "trig_host_free", "trig_array_create", "trig_array_destroy", "trig_array_scratch_bytes", "trig_array_select",
 ]
 
 NOALLOC_SCRATCH_BYTES = 64 << 20
@@ -162,6 +162,8 @@ def load(path: str | None = None):
         "trig_batch_run_events": (c.c_int, [c.POINTER(trig_slice_dev), c.POINTER(trig_slice_events), c.c_uint32,
                                             c.c_void_p, c.c_size_t, c.c_void_p, c.c_uint32]),
         "trig_set_events": (c.c_int, [c.c_void_p, c.c_int]),
+        "trig_host_alloc": (c.c_int, [c.c_size_t, c.POINTER(c.c_void_p)]),
+        "trig_host_free": (c.c_int, [c.c_void_p]),
         "trig_array_create": (c.c_int, [c.POINTER(c.c_void_p), c.c_uint32, c.POINTER(trig_array_params),
                                         c.POINTER(c.c_void_p)]),
         "trig_array_destroy": (c.c_int, [c.c_void_p]),
@@ -261,12 +263,13 @@ class _Owner:
 
 
 class _View:
-    """Read-only numpy view of library memory that keeps its owner alive."""
+    """Numpy view of library memory (read-only unless stated) that keeps its
+    owner alive."""
 
-    def __init__(self, owner, addr, n, dtype):
+    def __init__(self, owner, addr, n, dtype, readonly=True):
         self.owner = owner
         self.__array_interface__ = {"shape": (n,), "typestr": dtype.str, "descr": dtype.descr,
-                                    "data": (addr, True), "version": 3}
+                                    "data": (addr, readonly), "version": 3}
 
 
 def _view(owner, ptr, n, dtype):
@@ -314,6 +317,36 @@ def trig_poll(det: Detector, timeout_ms: int = -1) -> Result | None:
         return None
     _check(rc)
     return Result(out)
+
+
+class _HostBlock:
+    """Page-locked host memory from trig_host_alloc, freed with the last
+    array viewing it."""
+
+    def __init__(self, nbytes: int):
+        p = ctypes.c_void_p()
+        _check(load().trig_host_alloc(int(nbytes), ctypes.byref(p)))
+        self.ptr = p.value
+
+    def __del__(self):
+        try:
+            if self.ptr:
+                load().trig_host_free(ctypes.c_void_p(self.ptr))
+                self.ptr = None
+        except Exception:
+            pass
+
+
+def pinned_copy(a: np.ndarray) -> np.ndarray:
+    """A copy of `a` in page-locked host memory (trig_host_alloc): slices
+    submitted from it reach the device by DMA."""
+    a = np.ascontiguousarray(a)
+    if a.nbytes == 0:
+        return a.copy()
+    blk = _HostBlock(a.nbytes)
+    out = np.asarray(_View(blk, blk.ptr, a.nbytes, np.dtype(np.uint8), readonly=False)).view(a.dtype).reshape(a.shape)
+    np.copyto(out, a)
+    return out
 
 
 def trig_set_events(det: "Detector", on: bool = True) -> None:

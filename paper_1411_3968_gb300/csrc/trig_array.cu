@@ -15,8 +15,10 @@
 //   k_ahead     window heads among the merged triggers (gap > 2h + 1)
 //   scan        window index of every head; k_awin_a / k_awin_b write the
 //               windows (and a compact copy of their bounds)
-//   k_amark     every tower hit finds its window by binary search in the
-//               compact bounds, counts itself into its (window, PMT) cell
+//   k_abkt      per 4 us time bucket, the first window that can hold it
+//   k_amark     every tower hit finds its window (bucket table, then a
+//               search among the bucket's few windows), counts itself into
+//               its (window, PMT) cell
 //               and, at the start of a run, records the run's first index
 //   scan        cell offsets in (window, tower, PMT) order
 //   k_afrag     fragment offsets, window hit counts, status
@@ -76,6 +78,10 @@ struct AHeader {
     uint32_t *cell_first;       // [win_cap * pt] first hit index of each (window, PMT) run
     uint32_t *win_id;           // [n_hits] window of each tower hit, or kNone
     uint32_t *part;             // scan partial sums
+    uint32_t *bkt_win;          // [n_bkt + 1] first stored window ending at or after each time bucket
+    int64_t bkt_org;            // time of bucket 0 (t0 - h): no window starts earlier
+    uint32_t bkt_shift;         // bucket width 2^bkt_shift ns
+    uint32_t n_bkt;
     // written on the device
     uint32_t n[kMaxTowers];     // triggers per tower
     uint32_t off[kMaxTowers + 1];
@@ -394,15 +400,36 @@ __global__ void k_azero(AHeader *h)
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) h->cell_cnt[i] = 0;
 }
 
-// window of time t: the last stored window with lo <= t, if t <= its hi
-__device__ __forceinline__ uint32_t window_of(const AHeader *h, uint32_t ns, int64_t t)
+// first stored window w in [lo, hi) with whi[w] >= t (hi if none)
+__device__ __forceinline__ uint32_t first_ending_at(const int64_t *whi, uint32_t lo, uint32_t hi, int64_t t)
 {
-    uint32_t lo = 0, hi = ns;                  // first w with wlo[w] > t
     while (lo < hi) {
         const uint32_t mid = (lo + hi) >> 1;
-        if (h->wlo[mid] <= t) lo = mid + 1; else hi = mid;
+        if (whi[mid] < t) lo = mid + 1; else hi = mid;
     }
-    return (lo > 0 && t <= h->whi[lo - 1]) ? lo - 1 : kNone;
+    return lo;
+}
+
+// Bucket table of the window search: bkt_win[j] = the first stored window
+// ending at or after the start of time bucket j.  The windows are disjoint
+// and ordered, so a time in bucket j can only lie in windows
+// bkt_win[j] .. bkt_win[j + 1].
+__global__ void k_abkt(AHeader *h)
+{
+    const uint32_t ns = h->n_win_stored, nb = h->n_bkt;
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j <= nb; j += gridDim.x * blockDim.x)
+        h->bkt_win[j] = first_ending_at(h->whi, 0, ns, h->bkt_org + ((int64_t)j << h->bkt_shift));
+}
+
+// window of time t among the stored ones, or kNone
+__device__ __forceinline__ uint32_t window_of(const AHeader *h, uint32_t ns, int64_t t)
+{
+    if (t < h->bkt_org) return kNone;
+    const uint64_t j = (uint64_t)(t - h->bkt_org) >> h->bkt_shift;
+    if (j >= h->n_bkt) return kNone;
+    const uint32_t lo = h->bkt_win[j], hi = min(h->bkt_win[j + 1] + 1u, ns);
+    const uint32_t w = first_ending_at(h->whi, lo, hi, t);
+    return (w < ns && h->wlo[w] <= t) ? w : kNone;
 }
 
 __global__ void k_amark(AHeader *h, const ATower *tw)
@@ -549,8 +576,9 @@ inline size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct ALayout {
     size_t hdr, towers, sel_flag, sel_pos, sel, merged_t, head, head_pos, win_first, wlo, whi, cell_cnt, cell_off,
-        cell_first, win_id, part, bytes;
+        cell_first, win_id, part, bkt_win, bytes;
     uint64_t cap, n_hits, cells, part_n;
+    uint32_t bkt_shift, n_bkt;
 };
 
 int array_layout(const trig_array *a, const trig_slice_dev *slices, const trig_array_out *out, ALayout &L)
@@ -574,6 +602,17 @@ int array_layout(const trig_array *a, const trig_slice_dev *slices, const trig_a
     if (out->win_cap > 0xffffffffull / a->nt || cells >= 0xfffffff0ull)
         return report_error(TRIG_EINVAL, "win_cap too large for this array");
     const uint64_t part_n = std::max(cap, cells) / kScanBlock + 2;
+    // buckets of the window search over [t0 - h, t0 + S + h], at most 2^20
+    int64_t span = 1;
+    for (uint32_t b = 0; b < a->nt; ++b) {
+        DetInfo di{};
+        detector_info(a->towers[b], &di);
+        span = std::max<int64_t>(span, di.par.slice_ns + 2 * (int64_t)a->par.win_half_ns + 1);
+    }
+    uint32_t shift = 12;
+    while (((span >> shift) + 1) > ((int64_t)1 << 20)) ++shift;
+    L.bkt_shift = shift;
+    L.n_bkt = (uint32_t)((span >> shift) + 1);
     size_t o = 0;
     auto take = [&](size_t &field, size_t bytes) {
         field = o;
@@ -595,6 +634,7 @@ int array_layout(const trig_array *a, const trig_slice_dev *slices, const trig_a
     take(L.cell_first, 4 * (size_t)(cells + 1));
     take(L.win_id, 4 * (size_t)(n_hits + 1));
     take(L.part, 4 * (size_t)part_n);
+    take(L.bkt_win, 4 * ((size_t)L.n_bkt + 2));
     L.bytes = o;
     L.cap = cap;
     L.n_hits = n_hits;
@@ -649,6 +689,10 @@ extern "C" int trig_array_select(trig_array *a, const trig_slice_dev *slices, co
     hd.cell_first = reinterpret_cast<uint32_t *>(sp + L.cell_first);
     hd.win_id = reinterpret_cast<uint32_t *>(sp + L.win_id);
     hd.part = reinterpret_cast<uint32_t *>(sp + L.part);
+    hd.bkt_win = reinterpret_cast<uint32_t *>(sp + L.bkt_win);
+    hd.bkt_org = slices[0].t0_ns - (int64_t)a->par.win_half_ns;
+    hd.bkt_shift = L.bkt_shift;
+    hd.n_bkt = L.n_bkt;
     ATower tw[kMaxTowers];
     uint64_t hit0 = 0;
     for (uint32_t b = 0; b < a->nt; ++b) {
@@ -683,12 +727,13 @@ extern "C" int trig_array_select(trig_array *a, const trig_slice_dev *slices, co
     launch_scan<false>(hd.head, &d_h->n_sel, L.cap, hd.part, scan_total, hd.head_pos, st, nl);
     k_awin_a<<<grid, 256, 0, st>>>(d_h);
     k_awin_b<<<grid, 256, 0, st>>>(d_h);
+    k_abkt<<<grid, 256, 0, st>>>(d_h);
     k_azero<<<grid * 2, 256, 0, st>>>(d_h);
     k_amark<<<grid * 2, 256, 0, st>>>(d_h, d_t);
     launch_scan<false>(hd.cell_cnt, &d_h->n_cells, L.cells, hd.part, scan_total, hd.cell_off, st, nl);
     k_afrag<<<grid, 256, 0, st>>>(d_h, d_t);
     k_acopy<<<grid * 2, 256, 0, st>>>(d_h, d_t);
-    count_launches(nl + 12);
+    count_launches(nl + 13);
     e = cudaGetLastError();
     return e ? report_cuda_error(e, "trig_array_select: launch") : TRIG_OK;
 }

@@ -57,6 +57,26 @@ static int cuda_fail(cudaError_t e, const char *what)
 
 extern "C" const char *trig_last_error(void) { return g_last_error; }
 
+extern "C" int trig_host_alloc(size_t bytes, void **out)
+{
+    if (!out || bytes == 0) return fail(TRIG_EINVAL, "trig_host_alloc: out is NULL or bytes is 0");
+    *out = nullptr;
+    cudaError_t e = cudaHostAlloc(out, bytes, cudaHostAllocPortable);
+    if (e) {
+        *out = nullptr;
+        (void)cudaGetLastError();
+        return fail(TRIG_ENOMEM, "trig_host_alloc: cudaHostAlloc failed");
+    }
+    return TRIG_OK;
+}
+
+extern "C" int trig_host_free(void *ptr)
+{
+    if (!ptr) return fail(TRIG_EINVAL, "trig_host_free: NULL");
+    cudaError_t e = cudaFreeHost(ptr);
+    return e ? cuda_fail(e, "trig_host_free") : TRIG_OK;
+}
+
 static std::atomic<uint64_t> g_launches{0};
 extern "C" uint64_t trig_kernel_launch_count(void) { return g_launches.load(); }
 

@@ -355,6 +355,7 @@ __device__ __noinline__ void fill_leading_empty(uint32_t *e_lo, uint32_t *e_hi, 
 
 constexpr int kBoundsThreads = 256;
 constexpr int kBoundsUnroll = 4;
+constexpr uint32_t kBoundsPerWarp = kChunkHits / (kBoundsThreads / 32);    // consecutive hits per warp
 
 // Structure pass over one chunk of a wide slice: the same checks of the CSR
 // layout and time order, then each valid hit counted in its time bucket.
@@ -405,7 +406,7 @@ __device__ __noinline__ void bounds_wide_chunk(const SliceDesc &d, uint64_t firs
 // (run starts and ends against pmt_off, neighbours from adjacent lanes), and
 // the tile edges passed between the previous hit of the PMT and this one
 // get this hit's index.
-__global__ void __launch_bounds__(kBoundsThreads) k_bounds(const BatchHeader *__restrict__ hdr,
+__global__ void __launch_bounds__(kBoundsThreads, 4) k_bounds(const BatchHeader *__restrict__ hdr,
                                                            const SliceDesc *__restrict__ desc)
 {
     const uint32_t n_slices = hdr->n_slices, n_chunks = hdr->n_chunks;
@@ -430,58 +431,93 @@ __global__ void __launch_bounds__(kBoundsThreads) k_bounds(const BatchHeader *__
             bounds_wide_chunk(d, first);
             continue;
         }
-        auto cnt_lo = [&](int64_t t) -> uint32_t {
-            return span32 ? edges_le32(t - base_lo, W32, magic, NG) : edges_le64(t, base_lo, W, NG);
+        // tile edges at or below t: lo edge g at base_lo + g W, hi edge g at
+        // base_lo + D + g W with D = 2H + W = a W + b; with t - base_lo =
+        // q W + r the hi count is q - a + 1 - (r < b), so one division
+        // serves both
+        const uint32_t D32 = 2u * d.halo + W32, a32 = span32 ? D32 / W32 : 0u, b32 = D32 - a32 * W32;
+        auto edges = [&](int64_t t, uint32_t &lo, uint32_t &hi) {
+            if (span32) {
+                const int64_t x64 = t - base_lo;
+                if (x64 < 0) {
+                    lo = hi = 0u;
+                    return;
+                }
+                const uint32_t x = (uint32_t)x64;
+                uint32_t q = __umulhi(x, magic);
+                if (q * W32 > x) --q;
+                const uint32_t r = x - q * W32;
+                lo = q + 1 >= NG ? NG : q + 1;
+                const int32_t qh = (int32_t)q - (int32_t)a32 + 1 - (r < b32 ? 1 : 0);
+                hi = qh <= 0 ? 0u : ((uint32_t)qh >= NG ? NG : (uint32_t)qh);
+            } else {
+                lo = edges_le64(t, base_lo, W, NG);
+                hi = edges_le64(t, base_hi, W, NG);
+            }
         };
-        auto cnt_hi = [&](int64_t t) -> uint32_t {
-            return span32 ? edges_le32(t - base_hi, W32, magic, NG) : edges_le64(t, base_hi, W, NG);
-        };
-        for (uint32_t k0 = 0; k0 < kChunkHits; k0 += kBoundsThreads * kBoundsUnroll) {
+        // each warp walks kBoundsPerWarp consecutive hits, 32 at a time: a
+        // hit's predecessor is the previous lane's (lane 0: the previous
+        // step's lane 31; the first step loads it).  The first hit of a run
+        // closes the previous PMT's run.
+        const uint32_t warp = threadIdx.x >> 5;
+        const uint64_t wbase = first + (uint64_t)warp * kBoundsPerWarp;
+        uint32_t c_p = 0xffffu, c_lo = 0u, c_hi = 0u;
+        int64_t c_t = 0;
+        if (wbase > 0 && wbase <= n_hits) {
+            const trig_hit q = load_hit(hits + wbase - 1);
+            c_p = q.pmt;
+            c_t = q.t_ns;
+            edges(c_t, c_lo, c_hi);
+        }
+        for (uint32_t k0 = 0; k0 < kBoundsPerWarp; k0 += 32 * kBoundsUnroll) {
             trig_hit h[kBoundsUnroll];
 #pragma unroll
             for (int u = 0; u < kBoundsUnroll; ++u) {
-                const uint64_t li = first + k0 + u * kBoundsThreads + threadIdx.x;
+                const uint64_t li = wbase + k0 + u * 32 + lane;
                 if (li < n_hits) h[u] = load_hit(hits + li);
                 else h[u].t_ns = 0, h[u].pmt = 0xffff;
             }
 #pragma unroll
             for (int u = 0; u < kBoundsUnroll; ++u) {
-                const uint64_t li = first + k0 + u * kBoundsThreads + threadIdx.x;
+                const uint64_t li = wbase + k0 + u * 32 + lane;
                 const bool valid = li < n_hits;
                 const uint32_t p = h[u].pmt;
                 const int64_t t = h[u].t_ns;
-                const uint32_t lo_to = valid ? cnt_lo(t) : 0u;
-                const uint32_t hi_to = valid ? cnt_hi(t) : 0u;
-                // the neighbours' records are the adjacent lanes' (edge lanes load them)
+                uint32_t lo_to = 0u, hi_to = 0u;
+                if (valid) edges(t, lo_to, hi_to);
                 uint32_t pp = __shfl_up_sync(0xffffffffu, p, 1);
                 int64_t tp = __shfl_up_sync(0xffffffffu, t, 1);
                 uint32_t lo_p = __shfl_up_sync(0xffffffffu, lo_to, 1);
                 uint32_t hi_p = __shfl_up_sync(0xffffffffu, hi_to, 1);
-                uint32_t pn = __shfl_down_sync(0xffffffffu, p, 1);
-                if (!valid) continue;
-                if (lane == 0 && li > 0) {
-                    const trig_hit q = load_hit(hits + li - 1);
-                    pp = q.pmt;
-                    tp = q.t_ns;
-                    lo_p = cnt_lo(tp);
-                    hi_p = cnt_hi(tp);
+                if (lane == 0) {
+                    pp = c_p;
+                    tp = c_t;
+                    lo_p = c_lo;
+                    hi_p = c_hi;
                 }
-                if (lane == 31 && li + 1 < n_hits) pn = hits[li + 1].pmt;
+                c_p = __shfl_sync(0xffffffffu, p, 31);
+                c_t = __shfl_sync(0xffffffffu, t, 31);
+                c_lo = __shfl_sync(0xffffffffu, lo_to, 31);
+                c_hi = __shfl_sync(0xffffffffu, hi_to, 31);
+                if (!valid) continue;
                 const bool is_first = li == 0 || pp != p;
-                const bool is_last = li + 1 == n_hits || pn != p;
                 uint32_t bad = 0;
+                if (is_first && li > 0 && pp < P) {
+                    // hit li - 1 was the last of PMT pp's run
+                    if (poff[pp + 1] != li) bad |= TRIG_FLAG_BAD_PMT;
+                    fill_run_end(e_lo, e_hi, poff, P, NG, pp, lo_p, hi_p, (uint32_t)li);
+                }
                 if (p >= P) bad |= TRIG_FLAG_BAD_PMT;
                 else {
                     if (is_first && poff[p] != li) bad |= TRIG_FLAG_BAD_PMT;
-                    if (is_last && poff[p + 1] != li + 1) bad |= TRIG_FLAG_BAD_PMT;
-                    if (li + 1 == n_hits && poff[P] != n_hits) bad |= TRIG_FLAG_BAD_PMT;
+                    if (li + 1 == n_hits && (poff[p + 1] != n_hits || poff[P] != n_hits)) bad |= TRIG_FLAG_BAD_PMT;
                 }
                 if (t < in_lo || t >= in_hi) bad |= TRIG_FLAG_OUT_OF_RANGE;
                 if (!is_first && tp > t) bad |= TRIG_FLAG_UNSORTED;
                 if (bad) { report(d, bad); continue; }
                 fill_edges(e_lo, P, p, is_first ? 0u : lo_p, lo_to, (uint32_t)li);
                 fill_edges(e_hi, P, p, is_first ? 0u : hi_p, hi_to, (uint32_t)li);
-                if (is_last) fill_run_end(e_lo, e_hi, poff, P, NG, p, lo_to, hi_to, (uint32_t)(li + 1));
+                if (li + 1 == n_hits) fill_run_end(e_lo, e_hi, poff, P, NG, p, lo_to, hi_to, (uint32_t)(li + 1));
                 if (li == 0 && p > 0) fill_leading_empty(e_lo, e_hi, P, NG, p);
             }
         }

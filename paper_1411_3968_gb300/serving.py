@@ -144,7 +144,9 @@ def main():
     par = dict(workload.DEFAULT_PARAMS)
     wl = workload.cfg_serving_pool(seed=args.seed, slices_per_det=args.pool)
     dets = [_lib.Detector(g.xyz_mm, g.floor_id, par) for g in wl.detectors]
-    pools = [[(s.t0, s.stream) for s in wl.submissions if s.det_index == i] for i in range(len(dets))]
+    # the slice pools sit in page-locked host memory, as a DAQ front end's buffers would
+    pools = [[(s.t0, workload.Stream(_lib.pinned_copy(s.stream.hits), _lib.pinned_copy(s.stream.pmt_off)))
+              for s in wl.submissions if s.det_index == i] for i in range(len(dets))]
     out = replay(dets, pools, args.rate, args.detector_seconds, par["slice_ns"], args.seed, args.mode)
     print(json.dumps(out))
 
