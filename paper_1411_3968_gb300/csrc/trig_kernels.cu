@@ -970,6 +970,62 @@ __device__ __noinline__ bool level0_pass(const uint32_t *pk, uint32_t n, uint32_
     }
 }
 
+// Causal count c(s) = #{ j : |t_j - t_s| <= min(dt_max[p_s][p_j], W) }
+// over each seed's scan range keys [j0, j1): a group of 2^LG lanes per seed,
+// seeds dealt round-robin to the groups, four independent tests per lane in
+// flight.
+template <int CAP, int NC, bool SMEM_DT, uint32_t LG>
+__device__ __forceinline__ void count_causal(const TileCtx<CAP> &cx, const uint32_t *pk, uint32_t n, uint32_t ns,
+                                             const uint16_t *seed_idx, const uint32_t *swin, uint16_t *seed_cnt)
+{
+    constexpr uint32_t G = 1u << LG, NG = NC >> LG;
+    const uint32_t tid = threadIdx.x, gl = tid & (G - 1u), gid = tid >> LG, P = cx.P;
+    const uint32_t rounds = (ns + NG - 1) / NG;
+    for (uint32_t r = 0; r < rounds; ++r) {
+        const uint32_t k = r * NG + gid;
+        uint32_t c = 0;
+        if (k < ns) {
+            const uint32_t w = swin[k];
+            const uint32_t ks = pk[seed_idx[k]];
+            const uint32_t ts = pk_t(ks), ps = pk_p(ks);
+            const uint32_t j0 = w & 0xffffu, j1 = w >> 16;
+            if (CHECK(12, j1, n + 1) && CHECK(13, ps, P)) {
+                const uint16_t *row_s = cx.dt_s() + (size_t)ps * P;
+                const uint16_t *row_g = cx.dt_g + (size_t)ps * P;
+                // key kj counts when |t_j - t_s| <= dt[p_s][p_j]
+                auto causal = [&](uint32_t kj) -> uint32_t {
+                    const uint32_t tj = pk_t(kj), pj = pk_p(kj);
+                    if (!CHECK(11, pj, P)) return 0u;
+                    const uint32_t lim = SMEM_DT ? (uint32_t)row_s[pj] : (uint32_t)__ldg(row_g + pj);
+                    return (tj > ts ? tj - ts : ts - tj) <= lim;
+                };
+                // each lane takes four consecutive keys per 16-byte load (from
+                // j0 rounded down to a multiple of 4, inside the CAP-entry key
+                // array); positions outside [j0, j1) use the seed's own key,
+                // which is never looked up out of range, and are not counted
+                uint32_t ca = 0, cb = 0, cc = 0, cd = 0;
+                for (uint32_t q = (j0 & ~3u) + 4 * gl; q < j1; q += 4 * G) {
+                    const uint4 v = *reinterpret_cast<const uint4 *>(pk + q);
+                    const bool m0 = q >= j0, m1 = q + 1 >= j0 && q + 1 < j1;
+                    const bool m2 = q + 2 >= j0 && q + 2 < j1, m3 = q + 3 < j1;
+                    ca += m0 & causal(m0 ? v.x : ks);
+                    cb += m1 & causal(m1 ? v.y : ks);
+                    cc += m2 & causal(m2 ? v.z : ks);
+                    cd += m3 & causal(m3 ? v.w : ks);
+                }
+                c = ca + cb + cc + cd;
+            }
+        }
+        if (LG == 5) {
+            c = __reduce_add_sync(0xffffffffu, c);
+        } else {
+#pragma unroll
+            for (uint32_t off = G >> 1; off; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
+        }
+        if (k < ns && gl == 0) seed_cnt[k] = (uint16_t)c;
+    }
+}
+
 // The core is keys[c0, c1) (t_rel in [H, H + core width)).
 template <int CAP, int NC, bool SMEM_DT, bool EXT>
 __device__ CoreOut tile_trigger(TileCtx<CAP> &cx, const uint64_t *keys, uint32_t n, uint32_t bsh, uint32_t c0, uint32_t c1,
@@ -1085,62 +1141,21 @@ __device__ CoreOut tile_trigger(TileCtx<CAP> &cx, const uint64_t *keys, uint32_t
     }
     cons_sync<NC>();
 
-    // 3. causal count c(s) = #{ j : |t_j - t_s| <= min(dt_max[p_s][p_j], W) }
-    //    over the seed's scan range: a group of G lanes per seed (G from the
-    //    tile's density), seeds dealt round-robin to the groups, four
-    //    independent tests per lane in flight
+    // 3. causal count c(s) over each seed's scan range (count_causal), or
+    //    its distinct-PMT form
     if (EXT && tp.count_distinct) {
         count_distinct_pmts<CAP, NC, SMEM_DT>(cx, pk, n, ns, seed_idx, swin, seed_cnt);
     } else {
-        // expected keys in a scan range: 2H + 1 ns at the tile's density
+        // expected keys in a scan range: 2H + 1 ns at the tile's density.
+        // Sparse tiles give each seed 4 lanes (a few dozen keys each, the
+        // per-seed setup amortised); dense ones a whole warp (hundreds of
+        // keys, conflict-free contiguous loads).  Both sizes are compiled.
         const unsigned long long span_n = n ? (unsigned long long)pk_t(pk[n - 1]) + 1ull : 1ull;
         const unsigned long long est = (unsigned long long)(2u * tp.H + 1u) * n / span_n;
-        const uint32_t lg = est >= 48 ? 5u : est >= 20 ? 4u : 3u;
-        const uint32_t G = 1u << lg, gl = lane & (G - 1u), gid = tid >> lg, NG = NC >> lg;
-        const uint32_t rounds = (ns + NG - 1) / NG;
-        for (uint32_t r = 0; r < rounds; ++r) {
-            const uint32_t k = r * NG + gid;
-            uint32_t c = 0;
-            if (k < ns) {
-                const uint32_t w = swin[k];
-                const uint32_t ks = pk[seed_idx[k]];
-                const uint32_t ts = pk_t(ks), ps = pk_p(ks);
-                const uint32_t j0 = w & 0xffffu, j1 = w >> 16;
-                if (CHECK(12, j1, n + 1) && CHECK(13, ps, P)) {
-                    const uint16_t *row_s = cx.dt_s() + (size_t)ps * P;
-                    const uint16_t *row_g = cx.dt_g + (size_t)ps * P;
-                    // key kj counts when |t_j - t_s| <= dt[p_s][p_j]
-                    auto causal = [&](uint32_t kj) -> uint32_t {
-                        const uint32_t tj = pk_t(kj), pj = pk_p(kj);
-                        if (!CHECK(11, pj, P)) return 0u;
-                        const uint32_t lim = SMEM_DT ? (uint32_t)row_s[pj] : (uint32_t)__ldg(row_g + pj);
-                        return (tj > ts ? tj - ts : ts - tj) <= lim;
-                    };
-                    // each lane takes four consecutive keys per 16-byte load
-                    // (from j0 rounded down to a multiple of 4, inside the
-                    // CAP-entry key array); positions outside [j0, j1) use
-                    // the seed's own key, which is never looked up out of
-                    // range, and are not counted
-                    uint32_t ca = 0, cb = 0, cc = 0, cd = 0;
-                    for (uint32_t q = (j0 & ~3u) + 4 * gl; q < j1; q += 4 * G) {
-                        const uint4 v = *reinterpret_cast<const uint4 *>(pk + q);
-                        const bool m0 = q >= j0, m1 = q + 1 >= j0 && q + 1 < j1;
-                        const bool m2 = q + 2 >= j0 && q + 2 < j1, m3 = q + 3 < j1;
-                        ca += m0 & causal(m0 ? v.x : ks);
-                        cb += m1 & causal(m1 ? v.y : ks);
-                        cc += m2 & causal(m2 ? v.z : ks);
-                        cd += m3 & causal(m3 ? v.w : ks);
-                    }
-                    c = ca + cb + cc + cd;
-                }
-            }
-            if (lg == 5) {
-                c = __reduce_add_sync(0xffffffffu, c);
-            } else {
-                for (uint32_t off = G >> 1; off; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
-            }
-            if (k < ns && gl == 0) seed_cnt[k] = (uint16_t)c;
-        }
+        if (est >= 600)
+            count_causal<CAP, NC, SMEM_DT, 5>(cx, pk, n, ns, seed_idx, swin, seed_cnt);
+        else
+            count_causal<CAP, NC, SMEM_DT, 2>(cx, pk, n, ns, seed_idx, swin, seed_cnt);
     }
     cons_sync<NC>();
 
