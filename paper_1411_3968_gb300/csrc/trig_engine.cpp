@@ -423,7 +423,7 @@ static int plan_into(const trig_slice_dev *sl, uint32_t n, uintptr_t base, const
                      bool &any_wide, TileConfig *shape_out = nullptr, const trig_slice_events *ev = nullptr,
                      bool *any_events_out = nullptr)
 {
-    bool any_events = false, any_ext = false;
+    bool any_events = false, any_ext = false, dense = false;
     if (!sl || n == 0) return fail(TRIG_EINVAL, "no slices");
     const TileConfig cfg = batch_shape(sl, n, cfg_in);
     if (shape_out) *shape_out = cfg;
@@ -475,6 +475,10 @@ static int plan_into(const trig_slice_dev *sl, uint32_t n, uintptr_t base, const
         const bool wide = P >= kWideMinPmt;
         any_wide |= wide;
         any_ext |= det->par.l0_hits > 0 || det->par.seed_rule != 0 || det->par.count_distinct_pmts != 0;
+        {
+            const double span = (double)det->par.slice_ns + 2.0 * (double)det->in_halo;
+            dense |= (double)x.n_hits / span * (2.0 * det->tile_halo + 1.0) >= kDenseKeys;
+        }
         int64_t W = 0;
         if (wide) {
             const WideGrid wg = wide_grid(det, x.n_hits, cfg);
@@ -563,6 +567,7 @@ static int plan_into(const trig_slice_dev *sl, uint32_t n, uintptr_t base, const
     hdr.any_wide = any_wide ? 1u : 0u;
     hdr.any_events = any_events ? 1u : 0u;
     hdr.any_ext = any_ext ? 1u : 0u;
+    hdr.dense = dense ? 1u : 0u;
     hdr.n_items = items;
     hdr.n_chunks = chunks;
     bytes = off;
@@ -699,7 +704,7 @@ static int run_graph(const Plan &pl, void *scratch, cudaStream_t st)
             ce = launch_batch(reinterpret_cast<BatchHeader *>(scratch),
                               reinterpret_cast<SliceDesc *>((char *)scratch + align256(sizeof(BatchHeader))),
                               pl.hdr.n_slices, pl.max_pmt, pl.smem_dt, pl.any_wide, pl.any_events,
-                              pl.hdr.any_ext != 0, cfg, cap, &nl,
+                              pl.hdr.any_ext != 0, pl.hdr.dense != 0, cfg, cap, &nl,
                               false);
         ge.launches = nl;
         e = cudaStreamEndCapture(cap, &graph);
@@ -796,7 +801,8 @@ static int run_plan(const Plan &pl, void *scratch, size_t scratch_bytes, cudaStr
     uint64_t nl = 0;
     e = launch_batch(reinterpret_cast<BatchHeader *>(scratch),
                      reinterpret_cast<SliceDesc *>((char *)scratch + align256(sizeof(BatchHeader))), pl.hdr.n_slices,
-                     pl.max_pmt, pl.smem_dt, pl.any_wide, pl.any_events, pl.hdr.any_ext != 0, cfg, st, &nl, rows,
+                     pl.max_pmt, pl.smem_dt, pl.any_wide, pl.any_events, pl.hdr.any_ext != 0, pl.hdr.dense != 0, cfg,
+                     st, &nl, rows,
                      timed ? tr.ev : nullptr);
     g_launches += nl;
     if (timed) {
@@ -1026,7 +1032,7 @@ extern "C" int trig_batch_run_noalloc(const trig_slice_dev *slices, uint32_t n_s
     uint64_t nl = 0;
     e = launch_batch(reinterpret_cast<BatchHeader *>(scratch),
                      reinterpret_cast<SliceDesc *>((char *)scratch + align256(sizeof(BatchHeader))), n_slices,
-                     max_pmt, smem_dt, any_wide, false, hdr.any_ext != 0, shape, st, &nl, false);
+                     max_pmt, smem_dt, any_wide, false, hdr.any_ext != 0, hdr.dense != 0, shape, st, &nl, false);
     g_launches += nl;
     if (e) return cuda_fail(e, "trig_batch_run_noalloc: launch");
     return TRIG_OK;

@@ -117,7 +117,13 @@ struct BatchHeader {
     uint32_t any_wide;      // a slice of the batch is wide
     uint32_t any_events;    // a slice of the batch extracts events
     uint32_t any_ext;       // a slice uses level 0, seed rule 1 or the distinct count
+    uint32_t dense;         // a slice expects kDenseKeys or more keys per causal scan range
+    uint32_t pad;
 };
+
+// Expected keys in a seed's scan range (2H + 1 ns at the slice's mean rate)
+// from which the causal count gives each seed a warp instead of 4 lanes.
+constexpr double kDenseKeys = 600.0;
 
 constexpr uint32_t kChunkHits = 4096;       // structure-pass chunk
 
@@ -149,12 +155,14 @@ extern const char *const kKernelNames[kPipelineKernels];
 // scatter kernels run only then); any_events: a slice extracts events (the
 // halo, event-offset and event-copy kernels run only then); any_ext: a slice
 // uses level 0, seed rule 1 or the distinct count (the tile kernel built
-// with those rules runs, else the one without them).  ev (optional, kPipelineKernels + 1 events): ev[i]
+// with those rules runs, else the one without them); dense: the tile kernel
+// built with a warp per seed in the causal count runs.  ev (optional, kPipelineKernels + 1 events): ev[i]
 // is recorded before pipeline kernel i and ev[kPipelineKernels] after the
 // last one (a kernel that does not run gets an empty interval).
 // *launches is increased by the number of kernels launched.
 cudaError_t launch_batch(BatchHeader *d_hdr, SliceDesc *d_desc, uint32_t n_slices, uint32_t max_pmt,
-                         bool any_smem_dt, bool any_wide, bool any_events, bool any_ext, const TileConfig &cfg,
+                         bool any_smem_dt, bool any_wide, bool any_events, bool any_ext, bool dense,
+                         const TileConfig &cfg,
                          cudaStream_t st,
                          uint64_t *launches, bool rows, cudaEvent_t *ev = nullptr);
 

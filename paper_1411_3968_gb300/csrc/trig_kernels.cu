@@ -1027,7 +1027,7 @@ __device__ __forceinline__ void count_causal(const TileCtx<CAP> &cx, const uint3
 }
 
 // The core is keys[c0, c1) (t_rel in [H, H + core width)).
-template <int CAP, int NC, bool SMEM_DT, bool EXT>
+template <int CAP, int NC, bool SMEM_DT, bool EXT, bool DENSE>
 __device__ CoreOut tile_trigger(TileCtx<CAP> &cx, const uint64_t *keys, uint32_t n, uint32_t bsh, uint32_t c0, uint32_t c1,
                                 int64_t tb, const TrigParams &tp, trig_trigger *out, int64_t dbg_rank_lo,
                                 uint32_t *red)
@@ -1146,16 +1146,11 @@ __device__ CoreOut tile_trigger(TileCtx<CAP> &cx, const uint64_t *keys, uint32_t
     if (EXT && tp.count_distinct) {
         count_distinct_pmts<CAP, NC, SMEM_DT>(cx, pk, n, ns, seed_idx, swin, seed_cnt);
     } else {
-        // expected keys in a scan range: 2H + 1 ns at the tile's density.
-        // Sparse tiles give each seed 4 lanes (a few dozen keys each, the
-        // per-seed setup amortised); dense ones a whole warp (hundreds of
-        // keys, conflict-free contiguous loads).  Both sizes are compiled.
-        const unsigned long long span_n = n ? (unsigned long long)pk_t(pk[n - 1]) + 1ull : 1ull;
-        const unsigned long long est = (unsigned long long)(2u * tp.H + 1u) * n / span_n;
-        if (est >= 600)
-            count_causal<CAP, NC, SMEM_DT, 5>(cx, pk, n, ns, seed_idx, swin, seed_cnt);
-        else
-            count_causal<CAP, NC, SMEM_DT, 2>(cx, pk, n, ns, seed_idx, swin, seed_cnt);
+        // sparse batches give each seed 4 lanes (a few dozen keys each, the
+        // per-seed setup amortised), dense ones a whole warp (hundreds of
+        // keys, conflict-free contiguous loads); one size per build keeps
+        // a single count loop in the kernel
+        count_causal<CAP, NC, SMEM_DT, DENSE ? 5u : 2u>(cx, pk, n, ns, seed_idx, swin, seed_cnt);
     }
     cons_sync<NC>();
 
@@ -1233,7 +1228,7 @@ __device__ CoreOut tile_trigger(TileCtx<CAP> &cx, const uint64_t *keys, uint32_t
 // its core in halves until each piece fits; pieces are staged with plain
 // loads after per-PMT binary searches.  A 1 ns core that still does not
 // fit is reported (TRIG_FLAG_TILE_FULL) and skipped.
-template <int CAP, int NC, bool SMEM_DT, bool EXT>
+template <int CAP, int NC, bool SMEM_DT, bool EXT, bool DENSE>
 __device__ void tile_overflow(TileCtx<CAP> &cx, uint64_t *buf, const SliceDesc &d, const TrigParams &tp, uint32_t g,
                               uint32_t *red, int64_t *stk)
 {
@@ -1346,7 +1341,7 @@ __device__ void tile_overflow(TileCtx<CAP> &cx, uint64_t *buf, const SliceDesc &
         const uint32_t bsh = tile_sort<CAP, NC>(cx, buf, total, tb, span, red + 64, H, H + (uint32_t)(hi - lo));
         const uint32_t c0 = red[64 + NW + 1], c1 = red[64 + NW + 2];
         const uint32_t fired0 = red[5];
-        CoreOut co = tile_trigger<CAP, NC, SMEM_DT, EXT>(cx, buf, total, bsh, c0, c1, tb, tp,
+        CoreOut co = tile_trigger<CAP, NC, SMEM_DT, EXT, DENSE>(cx, buf, total, bsh, c0, c1, tb, tp,
                                                      d.stage + tile_rank + fired0,
                                                      (int64_t)rank_lo - (int64_t)d.dbg_rank0, red + 64);
         if (tid == 0) {
@@ -1363,7 +1358,7 @@ __device__ void tile_overflow(TileCtx<CAP> &cx, uint64_t *buf, const SliceDesc &
     cons_sync<NC>();
 }
 
-template <int CAP, int NC, bool SMEM_DT, bool EXT>
+template <int CAP, int NC, bool SMEM_DT, bool EXT, bool DENSE>
 __global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 1)) k_tile(BatchHeader *__restrict__ hdr,
                                                                           const SliceDesc *__restrict__ desc,
                                                                           uint32_t max_pmt)
@@ -1574,7 +1569,7 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 
                 d.tile_rank[inf.g] = 0;
             }
         } else if (inf.mode == 1) {
-            tile_overflow<CAP, NC, SMEM_DT, EXT>(cx, cx.stage(b), d, tp, inf.g, red, stk);
+            tile_overflow<CAP, NC, SMEM_DT, EXT, DENSE>(cx, cx.stage(b), d, tp, inf.g, red, stk);
         } else {
             const int64_t W = sl[0];
             const int64_t Bg = sl[1] + (int64_t)inf.g * W;
@@ -1587,7 +1582,7 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 
             // rank of the core's first hit = rank_lo + c0, known after the sort
             const uint32_t c0 = red[NW + 1], c1 = red[NW + 2];
             const uint32_t tile_rank = inf.rank_lo + c0;
-            CoreOut co = tile_trigger<CAP, NC, SMEM_DT, EXT>(cx, cx.stage(b), inf.n, bsh, c0, c1, tb, tp,
+            CoreOut co = tile_trigger<CAP, NC, SMEM_DT, EXT, DENSE>(cx, cx.stage(b), inf.n, bsh, c0, c1, tb, tp,
                                                          d.stage + tile_rank, (int64_t)inf.rank_lo - sl[3],
                                                          red);
             if (tid == 0 && CHECK(14, (uint64_t)tile_rank + co.n_fired, d.n_hits + 1) && CHECK(15, inf.g, d.n_tiles)) {
@@ -2179,12 +2174,12 @@ static cudaError_t raise_smem_limit(K kern, bool *done)
     return cudaSuccess;
 }
 
-template <int CAP, int NC, bool SMEM_DT, bool EXT = false>
+template <int CAP, int NC, bool SMEM_DT, bool EXT = false, bool DENSE = false>
 static cudaError_t launch_tile(BatchHeader *hdr, SliceDesc *desc, uint32_t max_pmt, cudaStream_t st)
 {
     static bool limit_set[64] = {};
     size_t smem = TileLayout<CAP>::bytes(max_pmt, SMEM_DT);
-    auto kern = k_tile<CAP, NC, SMEM_DT, EXT>;
+    auto kern = k_tile<CAP, NC, SMEM_DT, EXT, DENSE>;
     cudaError_t e = raise_smem_limit(kern, limit_set);
     if (e != cudaSuccess) return e;
     int per_sm = 1;
@@ -2199,8 +2194,8 @@ const char *const kKernelNames[kPipelineKernels] = {"k_prep",   "k_bounds", "k_b
                                                      "k_wwrite", "k_whits",  "k_escan", "k_events", "k_status"};
 
 cudaError_t launch_batch(BatchHeader *d_hdr, SliceDesc *d_desc, uint32_t n_slices, uint32_t max_pmt,
-                         bool any_smem_dt, bool any_wide, bool any_events, bool any_ext, const TileConfig &cfg,
-                         cudaStream_t st, uint64_t *launches, bool rows, cudaEvent_t *ev)
+                         bool any_smem_dt, bool any_wide, bool any_events, bool any_ext, bool dense,
+                         const TileConfig &cfg, cudaStream_t st, uint64_t *launches, bool rows, cudaEvent_t *ev)
 {
     const int sms = device_sm_count();
     auto mark = [&](int i) {
@@ -2243,6 +2238,16 @@ cudaError_t launch_batch(BatchHeader *d_hdr, SliceDesc *d_desc, uint32_t n_slice
         else
             e = cfg.warps == 8 ? launch_tile<4096, 256, false, true>(d_hdr, d_desc, max_pmt, st)
                                : launch_tile<4096, 512, false, true>(d_hdr, d_desc, max_pmt, st);
+    } else if (dense) {
+        // a warp per seed in the causal count; dt rows read through the cache
+        if (cfg.cap == 1024)
+            e = launch_tile<1024, 128, false, false, true>(d_hdr, d_desc, max_pmt, st);
+        else if (cfg.cap == 2048)
+            e = cfg.warps == 16 ? launch_tile<2048, 512, false, false, true>(d_hdr, d_desc, max_pmt, st)
+                                : launch_tile<2048, 256, false, false, true>(d_hdr, d_desc, max_pmt, st);
+        else
+            e = cfg.warps == 8 ? launch_tile<4096, 256, false, false, true>(d_hdr, d_desc, max_pmt, st)
+                               : launch_tile<4096, 512, false, false, true>(d_hdr, d_desc, max_pmt, st);
     } else if (cfg.cap == 1024)
         e = smem_dt ? launch_tile<1024, 128, true>(d_hdr, d_desc, max_pmt, st)
                     : launch_tile<1024, 128, false>(d_hdr, d_desc, max_pmt, st);
