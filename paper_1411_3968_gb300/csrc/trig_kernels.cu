@@ -876,13 +876,26 @@ __device__ __noinline__ bool coincidence_seed(const uint32_t *pk, uint32_t n, ui
     return false;
 }
 
+// A seed's scan range: the keys [j0, j1) of the buckets covering
+// [t_s - d, t_s + d], d its row's maximum (keys beyond fail the causal
+// test), from the sorted tile's bucket offsets.
+template <int CAP>
+__device__ __forceinline__ void seed_range(const TileCtx<CAP> &cx, uint32_t ts, uint32_t ps, uint32_t bsh,
+                                           uint32_t &j0, uint32_t &j1)
+{
+    const uint32_t dm = ps < cx.P ? (uint32_t)cx.dmax_s()[ps] : 0u;
+    const uint32_t *boff = cx.cnt();
+    j0 = boff[bucket_of<CAP>(ts >= dm ? ts - dm : 0u, bsh)];
+    j1 = boff[bucket_of<CAP>(ts + dm, bsh) + 1];
+}
+
 // Distinct-PMT causal count (P <= 128): c(s) = the number of different
 // PMTs among the keys j with |t_j - t_s| <= min(dt_max[p_s][p_j], W).
 // Eight lanes per seed each collect a 128-bit PMT set over every eighth key
 // of the seed's scan range; the sets are OR-ed and counted.
 template <int CAP, int NC, bool SMEM_DT>
 __device__ __noinline__ void count_distinct_pmts(const TileCtx<CAP> &cx, const uint32_t *pk, uint32_t n, uint32_t ns,
-                                                 const uint16_t *seed_idx, const uint32_t *swin, uint16_t *seed_cnt)
+                                                 const uint16_t *seed_idx, uint32_t bsh, uint16_t *seed_cnt)
 {
     constexpr uint32_t G = 8, NG = NC / G;
     const uint32_t tid = threadIdx.x, gl = tid & (G - 1u), gid = tid / G, P = cx.P;
@@ -891,10 +904,10 @@ __device__ __noinline__ void count_distinct_pmts(const TileCtx<CAP> &cx, const u
         const uint32_t k = r * NG + gid;
         uint32_t m0 = 0, m1 = 0, m2 = 0, m3 = 0;
         if (k < ns) {
-            const uint32_t w = swin[k];
             const uint32_t ks = pk[seed_idx[k]];
             const uint32_t ts = pk_t(ks), ps = pk_p(ks);
-            const uint32_t j0 = w & 0xffffu, j1 = w >> 16;
+            uint32_t j0, j1;
+            seed_range<CAP>(cx, ts, ps, bsh, j0, j1);
             if (CHECK(12, j1, n + 1) && CHECK(13, ps, P)) {
                 const uint16_t *row_s = cx.dt_s() + (size_t)ps * P;
                 const uint16_t *row_g = cx.dt_g + (size_t)ps * P;
@@ -971,12 +984,13 @@ __device__ __noinline__ bool level0_pass(const uint32_t *pk, uint32_t n, uint32_
 }
 
 // Causal count c(s) = #{ j : |t_j - t_s| <= min(dt_max[p_s][p_j], W) }
-// over each seed's scan range keys [j0, j1): a group of 2^LG lanes per seed,
+// over each seed's scan range keys [j0, j1) (seed_range): a group of 2^LG
+// lanes per seed,
 // seeds dealt round-robin to the groups, four independent tests per lane in
 // flight.
 template <int CAP, int NC, bool SMEM_DT, uint32_t LG>
 __device__ __forceinline__ void count_causal(const TileCtx<CAP> &cx, const uint32_t *pk, uint32_t n, uint32_t ns,
-                                             const uint16_t *seed_idx, const uint32_t *swin, uint16_t *seed_cnt)
+                                             const uint16_t *seed_idx, uint32_t bsh, uint16_t *seed_cnt)
 {
     constexpr uint32_t G = 1u << LG, NG = NC >> LG;
     const uint32_t tid = threadIdx.x, gl = tid & (G - 1u), gid = tid >> LG, P = cx.P;
@@ -985,10 +999,10 @@ __device__ __forceinline__ void count_causal(const TileCtx<CAP> &cx, const uint3
         const uint32_t k = r * NG + gid;
         uint32_t c = 0;
         if (k < ns) {
-            const uint32_t w = swin[k];
             const uint32_t ks = pk[seed_idx[k]];
             const uint32_t ts = pk_t(ks), ps = pk_p(ks);
-            const uint32_t j0 = w & 0xffffu, j1 = w >> 16;
+            uint32_t j0, j1;
+            seed_range<CAP>(cx, ts, ps, bsh, j0, j1);
             if (CHECK(12, j1, n + 1) && CHECK(13, ps, P)) {
                 const uint16_t *row_s = cx.dt_s() + (size_t)ps * P;
                 const uint16_t *row_g = cx.dt_g + (size_t)ps * P;
@@ -1036,11 +1050,9 @@ __device__ CoreOut tile_trigger(TileCtx<CAP> &cx, const uint64_t *keys, uint32_t
     const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
     const uint32_t ncore = c1 - c0;
     const uint32_t tau = tp.tau, qseed = tp.q_seed, threshold = tp.threshold, P = cx.P;
-    // scratch per seed (CAP entries each): index and count (16-bit), scan
-    // range (32-bit)
+    // scratch per seed (CAP entries each): index and count (16-bit)
     uint16_t *seed_idx = reinterpret_cast<uint16_t *>(cx.temp());
     uint16_t *seed_cnt = seed_idx + CAP;
-    const uint32_t *boff = cx.cnt();          // bucket offsets of the sorted keys
 
     // 1. seed flags (one bit per core hit): charge over threshold, or a hit
     //    on another PMT of the same floor within tau.  A warp holds 32
@@ -1128,29 +1140,16 @@ __device__ CoreOut tile_trigger(TileCtx<CAP> &cx, const uint64_t *keys, uint32_t
     const uint32_t ns = wtot[NW];
     cons_sync<NC>();
 
-    // 2b. each seed's scan range: the keys of the buckets covering
-    //     [t_s - d, t_s + d], d its row's maximum (keys beyond fail the test
-    //     below); one thread per seed
-    uint32_t *swin = reinterpret_cast<uint32_t *>(seed_cnt + CAP);    // j0 | j1 << 16
-    for (uint32_t k = tid; k < ns; k += NC) {
-        const uint32_t ks = pk[seed_idx[k]];
-        const uint32_t ts = pk_t(ks), dm = cx.dmax_s()[pk_p(ks)];
-        const uint32_t j0 = boff[bucket_of<CAP>(ts >= dm ? ts - dm : 0u, bsh)];
-        const uint32_t j1 = boff[bucket_of<CAP>(ts + dm, bsh) + 1];
-        swin[k] = j0 | (j1 << 16);
-    }
-    cons_sync<NC>();
-
     // 3. causal count c(s) over each seed's scan range (count_causal), or
     //    its distinct-PMT form
     if (EXT && tp.count_distinct) {
-        count_distinct_pmts<CAP, NC, SMEM_DT>(cx, pk, n, ns, seed_idx, swin, seed_cnt);
+        count_distinct_pmts<CAP, NC, SMEM_DT>(cx, pk, n, ns, seed_idx, bsh, seed_cnt);
     } else {
         // sparse batches give each seed 4 lanes (a few dozen keys each, the
         // per-seed setup amortised), dense ones a whole warp (hundreds of
         // keys, conflict-free contiguous loads); one size per build keeps
         // a single count loop in the kernel
-        count_causal<CAP, NC, SMEM_DT, DENSE ? 5u : 2u>(cx, pk, n, ns, seed_idx, swin, seed_cnt);
+        count_causal<CAP, NC, SMEM_DT, DENSE ? 5u : 2u>(cx, pk, n, ns, seed_idx, bsh, seed_cnt);
     }
     cons_sync<NC>();
 

@@ -754,3 +754,24 @@ def test_array_parameter_checks(pkg, params):
     odd = _det(pkg, towers[1], dict(params, tol_ns=25))
     with pytest.raises(pkg.TrigError):
         pkg.Array([dets[0], odd])
+
+
+def test_sparse_and_dense_count_builds_agree(pkg, params):
+    """A tower slice alone runs the 4-lanes-per-seed build; batched with the
+    dense 2688-PMT slice it runs the warp-per-seed build.  Both equal the
+    oracle."""
+    wl = workload.cfg_nemo()
+    g = wl.detectors[0]
+    d = _det(pkg, g, params)
+    s = wl.submissions[0]
+    ref = oracle.run(g.xyz_mm, g.floor_id, params, wl.runs[0].hits, wl.run_slices[0])[0]
+    _, alone = _run(pkg, d, [(s.t0, s.stream)])
+    _assert_same(alone[0], ref, "sparse build")
+    arr = _tower_array(8, 4)
+    da = _det(pkg, arr, params)
+    t0 = workload.T_ORIGIN_NS + 10 * params["slice_ns"]
+    st = workload.gen_stream(arr, t0 - 3000, t0 + params["slice_ns"] + 3000, 55e3, n_muons=20, seed=12, stream=150)
+    _, both = _run(pkg, [d, da], [(s.t0, s.stream), (t0, st)])
+    _assert_same(both[0], ref, "dense build")
+    d.close()
+    da.close()
