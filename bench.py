@@ -177,8 +177,8 @@ def run_reference(args, ws, rank):
     h0, s0, _ = run_pieces(pieces[:16])
     rate = h0 / max(s0, 1e-6)
     mean_hits = h0 / 16.0
-    budget = 120.0 / max(1, args.warmup + args.steps)
-    per_step = int(max(1, min(len(pieces), round(budget * rate / max(mean_hits, 1.0)))))
+    step_s = 120.0 / max(1, args.warmup + args.steps)
+    per_step = int(max(1, min(len(pieces), round(step_s * rate / max(mean_hits, 1.0)))))
     nxt = [16]
 
     def step():

@@ -230,7 +230,7 @@ const char *trig_last_error(void);
 
 /* Page-locked host memory for a producer's slice buffers (the Hit
  * Manager's output, "DAQ system of NEMO Phase II"): trig_submit_slice
- * copies such buffers to the device by DMA, without the driver's staging
+ * copies such buffers to the device by DMA, without the CUDA driver's staging
  * of pageable memory, whose speed depends on how the host's pages are
  * laid out.  *out receives `bytes` bytes (16-byte aligned) owned by the
  * caller until trig_host_free.  Errors: TRIG_EINVAL, TRIG_ENOMEM. */
