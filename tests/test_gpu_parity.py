@@ -775,3 +775,51 @@ def test_sparse_and_dense_count_builds_agree(pkg, params):
     _assert_same(both[0], ref, "dense build")
     d.close()
     da.close()
+
+
+@pytest.mark.parametrize("n", [31, 32, 33, 511, 512, 513, 4095, 4096, 4097, 9000])
+def test_structure_pass_walk_edges(pkg, params, n):
+    """Hit counts around the structure pass's warp range (512) and chunk
+    (4096); PMT runs that start or end a warp range; only the first, only
+    the last, or a single PMT populated: results equal the oracle."""
+    g = workload.km3_tower()
+    rng = np.random.Generator(np.random.PCG64(2000 + n))
+    par = dict(params, slice_ns=20_000)
+    t0 = 7_000_000
+    for layout in ("mixed", "first", "last", "single"):
+        if layout == "mixed":
+            pmts = rng.integers(0, g.n_pmt, n)
+        elif layout == "first":
+            pmts = np.zeros(n, np.int64)
+        elif layout == "last":
+            pmts = np.full(n, g.n_pmt - 1)
+        else:
+            pmts = np.full(n, 40)
+        hits = np.zeros(n, workload.HIT_DTYPE)
+        hits["t"] = rng.integers(t0, t0 + par["slice_ns"], n)
+        hits["pmt"] = pmts
+        hits["charge"] = rng.integers(1, 500, n)
+        d = _det(pkg, g, par)
+        _, res = _run(pkg, d, [(t0, _stream_from_hits(hits, g.n_pmt))])
+        ref = oracle.run(g.xyz_mm, g.floor_id, par, hits, [t0])[0]
+        _assert_same(res[0], ref, f"n={n} {layout}")
+        d.close()
+
+
+def test_array_selection_with_an_empty_tower(pkg, params):
+    """One tower submits no hits (no triggers, empty fragments) and another
+    only background far below threshold: selection and readback equal the
+    oracle, with K = 2 and K = 1."""
+    wl = workload.cfg_towers8(seed=5)
+    nt = len(wl.detectors)
+    subs = list(wl.submissions[:nt])
+    runs = list(wl.runs)
+    empty = workload.Stream(np.zeros(0, workload.HIT_DTYPE), np.zeros(85, np.uint64))
+    subs[3] = workload.Submission(3, subs[3].t0, empty)
+    runs[3] = empty
+    wl2 = workload.Workload("towers8_empty3", wl.detectors, subs, runs, wl.run_slices)
+    for K in (2, 1):
+        got, keep = _array_run(pkg, wl2, params, K, 3000, 3000)
+        ref = _array_oracle(wl2, params, K, 3000, 3000)
+        _assert_array_same(got, ref, f"empty tower K={K}")
+        assert not (ref.seeds["tower"] == 3).any()
