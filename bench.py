@@ -368,6 +368,17 @@ def main():
             per_hit = tf.get("bytes_per_hit", {}).get(args.workload)
             if tf.get("source_hash") == _tile_source_hash() and per_hit:
                 roofline["traffic"] = per_hit * n_hits
+            # the kernel's binding resource is instruction issue: its warp
+            # instructions per hit (same capture) at one instruction per
+            # cycle on each of the 4 schedulers of every SM, at the SM clock
+            # sampled during the timed region
+            wiph = tf.get("warp_inst_per_hit", {}).get(args.workload)
+            mhz = (clocks or {}).get("sm_mhz")
+            if tf.get("source_hash") == _tile_source_hash() and wiph and mhz:
+                sms = torch.cuda.get_device_properties(local).multi_processor_count
+                bound_ms = wiph * n_hits / (sms * 4 * mhz * 1e6) * 1e3
+                roofline["issue"] = {"warp_inst_per_hit": wiph, "sms": sms, "sm_mhz": mhz,
+                                     "bound_ms": bound_ms, "frac": bound_ms / tile_ms}
         except (OSError, ValueError, AttributeError):
             pass
 
