@@ -169,3 +169,24 @@ def test_engine_event_payload(pkg, params):
         for f in ("t", "pmt", "charge"):
             assert np.array_equal(r.events[f], want[f]), (k, f)
     det.close()
+
+
+@pytest.mark.parametrize("extra", [dict(l0_hits=7, l0_window_ns=1000), dict(seed_rule=1, threshold=1),
+                                   dict(count_distinct_pmts=1)], ids=["level0", "ladder", "distinct"])
+def test_engine_with_the_paper_rules(pkg, params, extra):
+    """The engine's batches take the extended-rule tile kernel when a
+    detector uses level 0, the coincidence ladder or the distinct count:
+    results equal the oracle."""
+    pkg.trig_engine_set_mode(1)
+    wl = workload.cfg_km3()
+    g = wl.detectors[0]
+    par = dict(params, **extra)
+    det = pkg.Detector(g.xyz_mm, g.floor_id, par, tower_id=g.tower_id)
+    for s in wl.submissions:
+        pkg.trig_submit_slice(det, s.t0, s.stream.hits, s.stream.pmt_off)
+    ref = oracle.run(g.xyz_mm, g.floor_id, par, wl.runs[0].hits, wl.run_slices[0], tower_id=g.tower_id)
+    for k in range(len(ref)):
+        r = pkg.trig_poll(det, 60_000)
+        assert r is not None
+        _same(r, ref[k], f"{extra} slice {k}")
+    det.close()
