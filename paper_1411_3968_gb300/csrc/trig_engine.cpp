@@ -86,8 +86,8 @@ static TileConfig g_cfg{4096, 16, 60};
 extern "C" int trig_set_tile_config(uint32_t cap, uint32_t warps, uint32_t fill_pct)
 {
     if (!valid_tile_shape(cap, warps) || fill_pct < 10 || fill_pct > 95)
-        return fail(TRIG_EINVAL, "trig_set_tile_config: (cap, warps) in {(4096,16), (4096,8), (2048,8)}, "
-                                 "fill_pct in [10, 95]");
+        return fail(TRIG_EINVAL, "trig_set_tile_config: (cap, warps) in {(4096,16), (4096,8), (2048,16), (2048,8), "
+                                 "(1024,4)}, fill_pct in [10, 95]");
     std::lock_guard<std::mutex> lk(g_cfg_mu);
     g_cfg = TileConfig{cap, warps, fill_pct};
     return TRIG_OK;
@@ -914,7 +914,7 @@ extern "C" int trig_autotune(trig_detector *det, const trig_slice_dev *slices, u
     for (uint32_t s = 0; s < n_slices; ++s)
         if (slices[s].det != det) return fail(TRIG_EINVAL, "trig_autotune: all slices must belong to det");
     static const uint32_t shapes[][2] = {{4096, 16}, {4096, 8}, {2048, 16}, {2048, 8}, {1024, 4}};
-    static const uint32_t fills[] = {40, 55, 70, 85};
+    static const uint32_t fills[] = {55, 75, 90, 95};
     cudaStream_t st = (cudaStream_t)stream;
     // scratch for the largest candidate
     const bool was_tuned = det->tuned;
