@@ -1069,11 +1069,12 @@ struct DevicePool {
         size_t cls = (size_t)1 << 16;
         while (cls < bytes) cls <<= 1;
         std::lock_guard<std::mutex> lk(mu);
-        auto it = free_blocks.find(cls);
-        if (it != free_blocks.end()) {
+        // the smallest free block that fits, up to four classes larger
+        auto it = free_blocks.lower_bound(cls);
+        if (it != free_blocks.end() && it->first <= 4 * cls) {
             unsigned char *p = it->second;
+            *got = it->first;
             free_blocks.erase(it);
-            *got = cls;
             return p;
         }
         size_t free_b = 0, total_b = 0;
@@ -1114,11 +1115,14 @@ struct HostPool {
         size_t cls = 4096;
         while (cls < bytes) cls <<= 1;
         std::lock_guard<std::mutex> lk(mu);
-        auto it = free_blocks.find(cls);
-        if (it != free_blocks.end()) {
+        // the smallest free block that fits, up to four classes larger: a
+        // new page-locked allocation stalls the engine thread for
+        // milliseconds
+        auto it = free_blocks.lower_bound(cls);
+        if (it != free_blocks.end() && it->first <= 4 * cls) {
             unsigned char *p = it->second;
+            *got = it->first;
             free_blocks.erase(it);
-            *got = cls;
             return p;
         }
         for (auto f = free_blocks.begin(); f != free_blocks.end() && used + cls > limit;) {
