@@ -105,8 +105,9 @@ size_t trig_array_scratch_bytes(const trig_array *array, const trig_slice_dev *s
  * by trig_batch_run (or its no-alloc or events form) on `stream` or before
  * it.  Enqueues the selection kernels on `stream` (a cudaStream_t) and
  * returns; stats and outputs are valid once the stream reaches this point.
- * Errors: TRIG_EINVAL (mismatched slices), TRIG_ECAPACITY (scratch too
- * small), TRIG_EDEVICE. */
+ * scratch is device memory, 256-byte aligned, of trig_array_scratch_bytes.
+ * Errors: TRIG_EINVAL (mismatched slices, unaligned scratch),
+ * TRIG_ECAPACITY (scratch too small), TRIG_EDEVICE. */
 int trig_array_select(trig_array *array, const trig_slice_dev *slices, const trig_array_out *out, void *scratch,
                       size_t scratch_bytes, void *stream);
 

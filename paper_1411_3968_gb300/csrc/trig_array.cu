@@ -657,7 +657,9 @@ extern "C" int trig_array_select(trig_array *a, const trig_slice_dev *slices, co
     ALayout L{};
     int rc = array_layout(a, slices, out, L);
     if (rc) return rc;
-    if (!scratch || scratch_bytes < L.bytes) return report_error(TRIG_ECAPACITY, "trig_array_select: scratch too small");
+    if (!scratch || ((uintptr_t)scratch & 255u))
+        return report_error(TRIG_EINVAL, "trig_array_select: scratch must be 256-byte aligned device memory");
+    if (scratch_bytes < L.bytes) return report_error(TRIG_ECAPACITY, "trig_array_select: scratch too small");
     char *sp = static_cast<char *>(scratch);
     AHeader hd{};
     hd.nt = a->nt;
