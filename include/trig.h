@@ -12,12 +12,20 @@
  * data sent to the Event Manager, "DAQ system of NEMO Phase II") are merged
  * and returned.
  *
+ * The paper's other rules are parameters of the same path: the level-0
+ * trigger (N hits within TW, optionally on different PMTs), its combination
+ * of simple, floor and adjacent-floor coincidences, and a causal count over
+ * different PMTs (trig_params).
+ *
  * Two faces:
  *   - the engine (trig_create / trig_submit_slice / trig_poll / trig_destroy):
  *     host buffers in, host results out; slices from all detectors are
  *     batched continuously on one GPU;
  *   - the device batch call (trig_batch_run): device buffers in and out, the
- *     caller owns all memory, one launch sequence for many slices.
+ *     caller owns all memory, one launch sequence for many slices; its
+ *     events form also copies every hit inside the windows, and
+ *     trig_array.h selects across the towers of an array and reads their
+ *     windows back.
  *
  * All functions return TRIG_OK (0) or a negative TRIG_E* code and never
  * throw.  trig_last_error() gives a message for the calling thread's last
