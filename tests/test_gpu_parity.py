@@ -823,3 +823,35 @@ def test_array_selection_with_an_empty_tower(pkg, params):
         ref = _array_oracle(wl2, params, K, 3000, 3000)
         _assert_array_same(got, ref, f"empty tower K={K}")
         assert not (ref.seeds["tower"] == 3).any()
+
+
+def test_maximum_pmt_count(pkg, params):
+    """A detector at the 4096-PMT limit (512 floors of 8 PMTs scattered in a
+    1 km box): the wide path with the largest dt table, exact against the
+    oracle; one PMT more is refused."""
+    rng = np.random.Generator(np.random.PCG64(4096))
+    P = 4096
+    xyz = rng.integers(-500_000, 500_000, (P, 3)).astype(np.int32)
+    floor = (np.arange(P) // 8).astype(np.uint32)
+    xyz[:, 2] = (floor.astype(np.int64) * 2000 - 500_000).astype(np.int32)    # floors stacked 2 m apart
+    g = workload.Detector("max4096", xyz, floor, np.zeros(P, np.uint32))
+    # most pairs sit beyond the 3 us clamp, so counts run near 300: a
+    # threshold of 330 fires about a fifth of the seeds in 30 windows
+    par = dict(params, slice_ns=1_000_000, threshold=330)
+    t0 = 50_000_000
+    n = 60_000
+    hits = np.zeros(n, workload.HIT_DTYPE)
+    hits["t"] = rng.integers(t0 - 3000, t0 + par["slice_ns"] + 3000, n)
+    hits["t"][: n // 4] = hits["t"][n // 4: n // 2] + rng.integers(-15, 16, n // 4)
+    hits["t"] = np.clip(hits["t"], t0 - 3000, t0 + par["slice_ns"] + 2999)     # inside the accepted halos
+    hits["pmt"] = rng.integers(0, P, n)
+    hits["pmt"][: n // 4] = (hits["pmt"][n // 4: n // 2] // 8) * 8 + rng.integers(0, 8, n // 4)
+    hits["charge"] = rng.integers(1, 500, n)
+    d = _det(pkg, g, par)
+    _, res = _run(pkg, d, [(t0, _stream_from_hits(hits, P))])
+    ref = oracle.run(g.xyz_mm, g.floor_id, par, hits, [t0])[0]
+    assert 0 < len(ref.triggers) < len(ref.seeds) and len(ref.windows) > 1
+    _assert_same(res[0], ref, "4096 PMTs")
+    d.close()
+    with pytest.raises(pkg.TrigError):
+        pkg.Detector(np.zeros((P + 1, 3), np.int32), np.zeros(P + 1, np.uint32), params)
