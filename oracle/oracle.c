@@ -189,7 +189,7 @@ static int level0_pass(const run_job *job, uint64_t s)
         if (!par->l0_distinct_pmts) {
             for (uint64_t q = b; q < n && H[q].t_ns < a + TW; ++q) ++count;
         } else {
-            unsigned char seen[4096];
+            unsigned char seen[ORACLE_MAX_PMT];
             memset(seen, 0, job->n_pmt);
             for (uint64_t q = b; q < n && H[q].t_ns < a + TW; ++q)
                 if (!seen[H[q].pmt]) { seen[H[q].pmt] = 1; ++count; }
@@ -276,7 +276,7 @@ static int run_slice(run_job *job, uint32_t k)
         if (is_seed && par->l0_hits > 0) is_seed = level0_pass(job, s);
         if (!is_seed) continue;
         uint32_t c = 0;
-        unsigned char seen[4096];
+        unsigned char seen[ORACLE_MAX_PMT];
         if (par->count_distinct_pmts) memset(seen, 0, job->n_pmt);
         for (uint64_t j = lower_bound_t(H, n, hs->t_ns - W); j < n && H[j].t_ns <= hs->t_ns + W; ++j) {
             int64_t lim = job->dt[(size_t)hs->pmt * job->n_pmt + H[j].pmt];
@@ -371,6 +371,8 @@ int oracle_run(uint32_t n_pmt, const int32_t *xyz_mm, const uint32_t *floor_id, 
 {
     if (!xyz_mm || !floor_id || !par || (n_hits && !hits) || (n_slices && (!slice_t0 || !out)))
         return -1;
+    /* the distinct-PMT forms mark PMTs in a 4096-entry array per seed */
+    if (n_pmt == 0 || n_pmt > ORACLE_MAX_PMT) return -1;
     for (uint64_t i = 0; i < n_hits; ++i)
         if (hits[i].pmt >= n_pmt) return -1;
     memset(out, 0, n_slices * sizeof(oracle_slice_result));

@@ -60,6 +60,9 @@ int64_t oracle_dtmax_pair(int64_t d2_mm2, uint32_t tol_ns, uint32_t n_num, uint3
 int oracle_dtmax(uint32_t n_pmt, const int32_t *xyz_mm, uint32_t tol_ns, uint32_t n_num, uint32_t n_den,
                  int32_t *dt_out);
 int oracle_merge(const oracle_hit *hits, uint64_t n, oracle_hit *sorted_out);
+/* Largest detector the oracle takes (oracle_run returns -1 above it or at 0). */
+#define ORACLE_MAX_PMT 4096u
+
 int oracle_run(uint32_t n_pmt, const int32_t *xyz_mm, const uint32_t *floor_id, const uint32_t *tower_id,
                const oracle_params *par,
                const oracle_hit *hits, uint64_t n_hits, const int64_t *slice_t0, uint32_t n_slices,

@@ -555,6 +555,36 @@ def test_ladder_and_distinct_count_match_bruteforce(case, params):
     assert _tuples(got.seeds, SEED_F) == want, case
 
 
+def test_oracle_pmt_limit(params):
+    """The oracle takes detectors of 1 to 4096 PMTs (its distinct-PMT forms
+    keep a 4096-entry mark array per seed) and refuses larger ones instead
+    of overrunning that array.  At the limit, the distinct count of seeds
+    with hits on PMT 4095 equals the all-pairs definition."""
+    from types import SimpleNamespace
+    rng = np.random.Generator(np.random.PCG64(41))
+    P = 4096
+    xyz = np.zeros((P, 3), np.int32)
+    xyz[:, 0] = rng.integers(-3000, 3000, P)                  # a 6 m cube: every pair causal within ~48 ns
+    xyz[:, 1] = rng.integers(-3000, 3000, P)
+    xyz[:, 2] = rng.integers(-3000, 3000, P)
+    det = SimpleNamespace(n_pmt=P, xyz_mm=xyz, floor_id=np.arange(P, dtype=np.uint32) // 4,
+                          tower_id=np.zeros(P, np.uint32))
+    t0 = 1_000_000
+    pm = [4095, 4094, 4095, 4093, 4092, 0, 1, 4095, 4095, 2]
+    hits = np.zeros(len(pm), oracle.HIT_DTYPE)
+    hits["t"] = t0 + 100 + 7 * np.arange(len(pm))
+    hits["pmt"] = pm
+    hits["charge"] = 400                                        # every hit is a charge seed
+    par = dict(params, slice_ns=10_000, threshold=1, count_distinct_pmts=1)
+    got = oracle.run(det.xyz_mm, det.floor_id, par, hits, [t0], tower_id=det.tower_id)[0]
+    want = _brute_ext(det, par, hits, t0)
+    assert _tuples(got.seeds, SEED_F) == want
+    assert max(c for (_, _, _, c) in want) >= 5                 # repeats of PMT 4095 counted once
+    for bad in (0, P + 1):
+        with pytest.raises(RuntimeError):
+            oracle.run(np.zeros((bad, 3), np.int32), np.zeros(bad, np.uint32), par, hits[:0], [t0])
+
+
 def test_ladder_accidental_rate_closed_form(params):
     """Pure Poisson background, the paper's windows: a hit on PMT p is a
     seed iff another PMT of its floor has a hit within +-fc (SC implies FC
