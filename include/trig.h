@@ -189,8 +189,10 @@ typedef struct {
  * failures.  The detector is bound to the CUDA device current at creation. */
 int trig_create(const trig_geometry *geometry, const trig_params *params, trig_detector **out);
 
-/* Drains the detector's in-flight slices, then frees it.  Results not yet
- * polled are discarded.  NULL is accepted. */
+/* Drains the detector's in-flight slices, then frees it and its device
+ * tables (the end of a run of the paper's per-tower TGPU, "Results and
+ * perspectives").  Results not yet polled are discarded; the detector's
+ * resident slice tail is freed.  NULL is accepted. */
 int trig_destroy(trig_detector *det);
 
 /* Copies the exact (unclamped) dt_max table into host memory dt_out
@@ -198,8 +200,10 @@ int trig_destroy(trig_detector *det);
 int trig_detector_dtmax(const trig_detector *det, int32_t *dt_out);
 
 /* Halo the detector needs around each slice: hits in
- * [t0 - halo, t0 + slice_ns + halo) are accepted and used; halo =
- * max(corr_window_ns, win_half_ns, floor_tau_ns). */
+ * [t0 - halo, t0 + slice_ns + halo) are accepted and used; halo is the
+ * largest of corr_window_ns, win_half_ns, the seed rule's coincidence window
+ * (floor_tau_ns, or the largest of sc/fc/afc_window_ns under seed rule 1)
+ * and l0_window_ns when level 0 is on. */
 int64_t trig_detector_halo_ns(const trig_detector *det);
 
 /* ---------------------------------------------------------------- engine */
@@ -207,22 +211,40 @@ int64_t trig_detector_halo_ns(const trig_detector *det);
 /* Submits one slice (host memory).  hits are grouped by PMT (CSR):
  * hits[pmt_off[p] .. pmt_off[p+1]) are PMT p's hits in non-decreasing time;
  * pmt_off has n_pmt + 1 entries, pmt_off[0] == 0, and pmt_off[n_pmt] is the
- * hit count (< 2^32).  The producer includes the halos: every hit in
- * [t0 - halo, t0 + slice_ns + halo) that the detector recorded (the paper's
- * "proceeds on first hits of the next time slice", "Preparation in CPU").
- * Seeds are only those in [t0, t0 + slice_ns).  The hits are copied before
- * the call returns.  EINVAL on malformed offsets; EAGAIN when the engine's
- * staging memory is full (poll, then retry).  Malformed hit records (bad
- * pmt, unsorted streams, out-of-range times) are detected on the device and
- * reported through the result's status (EINVAL) and flags. */
+ * hit count (< 2^32).  Seeds are only those in [t0, t0 + slice_ns).  The
+ * hits are copied before the call returns.
+ *
+ * Halos ("Preparation in CPU": at the end of a slice the trigger proceeds
+ * on the first hits of the next one).  The producer always includes the
+ * trailing halo, the hits of [t0 + slice_ns, t0 + slice_ns + halo).  The
+ * leading halo [t0 - halo, t0) comes from one of two places:
+ *   - is_continuation = 0: from the submission itself (every hit of
+ *     [t0 - halo, t0 + slice_ns + halo) the detector recorded; none for the
+ *     first slice of a run);
+ *   - is_continuation = 1: from the device.  The library keeps the last
+ *     `halo` ns of every submission of the detector, [t0' + slice_ns - halo,
+ *     t0' + slice_ns), resident on the device and prepends them PMT by PMT;
+ *     t0 must then be the previous submission's t0' + slice_ns, and the
+ *     submission holds no hit before t0.
+ * Submissions of one detector are serialised.  EINVAL on malformed offsets
+ * or a continuation that does not follow the previous submission; EAGAIN
+ * when the engine's staging memory is full (poll, then retry).  Malformed
+ * hit records (bad pmt, unsorted streams, out-of-range times) are detected
+ * on the device and reported through the result's status (EINVAL) and
+ * flags. */
 int trig_submit_slice(trig_detector *det, int64_t slice_t0_ns, const trig_hit *hits, const uint64_t *pmt_off,
                       int is_continuation, uint64_t *slice_id_out);
 
-/* Returns the detector's oldest unreturned result (slices complete in
- * submission order per detector).  Waits up to timeout_ms (0: do not wait,
- * < 0: wait without limit); EAGAIN if nothing is ready in time. */
+/* Returns the detector's oldest unreturned result: the triggered windows
+ * handed to the Event Manager ("DAQ system of NEMO Phase II": the 6 us
+ * window around each trigger seed is kept).  Slices complete in submission
+ * order per detector.  Waits up to timeout_ms (0: do not wait, < 0: wait
+ * without limit); EAGAIN if nothing is ready in time.  *out is owned by the
+ * library until trig_result_free. */
 int trig_poll(trig_detector *det, int timeout_ms, trig_result **out);
 
+/* Returns a result's memory (its trigger, window and event arrays) to the
+ * library.  NULL is accepted. */
 void trig_result_free(trig_result *res);
 
 /* Engine policy: 0 = plain (every slice is its own launch sequence),
@@ -233,8 +255,35 @@ int trig_engine_set_mode(int mode);
 /* Engine counters since start: batches launched, slices completed. */
 int trig_engine_stats(uint64_t *batches, uint64_t *slices);
 
-/* Message of the calling thread's last failure ("" if none). */
+/* Message of the calling thread's last failure ("" if none): the library's
+ * own error report (the paper has no error interface).  The string is
+ * thread-local and valid until the thread's next failing call. */
 const char *trig_last_error(void);
+
+/* Engine controls for operations and tests (the engine's own policy; the
+ * paper has no counterpart).
+ *   trig_engine_hold(1): admit no new batch (submissions still queue) until
+ *     trig_engine_hold(0); the queued slices then share batches.
+ *   trig_engine_set_staging_limit(bytes): device staging memory that queued
+ *     and running submissions may hold at once (0: no limit beyond free
+ *     device memory, the default); a submission beyond it gets TRIG_EAGAIN.
+ *   trig_engine_fail_result_allocs(n): failure injection on the host: the
+ *     next n requests for result memory fail as if page-locked memory were
+ *     exhausted; those slices complete with status TRIG_ENOMEM and no
+ *     arrays. */
+int trig_engine_hold(int on);
+int trig_engine_set_staging_limit(uint64_t bytes);
+int trig_engine_fail_result_allocs(uint32_t n);
+
+/* Bounded device waits.  Every wait of the tile pass (the stager waiting
+ * for a free buffer, the consumers waiting for a staged tile) gives up after
+ * limit_ns of the GPU's global timer (default 1 s; 0 restores it, at most
+ * 600 s), sets TRIG_FLAG_TIMEOUT and ends the pass; the batch's slices then
+ * report TRIG_ETIMEOUT with no output, and the device stays usable.
+ * stall = 1 is a test control: later batches stage no tile, so the first
+ * wait of every block runs out with no copy in flight; stall = 0 ends it.
+ * Applies to batches planned after the call. */
+int trig_set_device_wait(uint64_t limit_ns, int stall);
 
 /* Page-locked host memory for a producer's slice buffers (the Hit
  * Manager's output, "DAQ system of NEMO Phase II"): trig_submit_slice
@@ -324,6 +373,14 @@ int trig_set_events(trig_detector *det, int on);
  * outputs as for trig_batch_run.  Nothing is allocated: no cudaMalloc,
  * cudaFree or allocating library call.  The paper has no counterpart; this
  * is a deployment interface.
+ *   - stream must be a stream the caller created, best with
+ *     cudaStreamNonBlocking: NULL (the legacy default stream) is refused
+ *     with TRIG_EINVAL, since it synchronises with other streams and is
+ *     forbidden while another thread captures in global mode.  The batch's
+ *     descriptors travel as a kernel parameter, so the call does not wait
+ *     for earlier work on the stream.
+ *   - A stream that is capturing is refused with TRIG_EINVAL: the call must
+ *     not be captured into a CUDA graph.
  *   - At most TRIG_NOALLOC_MAX_SLICES slices; a batch whose scratch would
  *     exceed the array (about 3.9 M hits at 16 B of staging per hit) is
  *     rejected with TRIG_ECAPACITY before anything is launched.

@@ -54,6 +54,7 @@ EXPORTS = [
     "trig_get_tile_config", "trig_kernel_launch_count", "trig_kernel_times", "trig_batch_run_noalloc",
     "trig_autotune", "trig_detector_tile_config", "trig_batch_events_scratch_bytes", "trig_batch_run_events",
     "trig_set_events", "trig_host_alloc", "trig_host_free", "trig_array_create", "trig_array_destroy", "trig_array_scratch_bytes", "trig_array_select",
+    "trig_engine_hold", "trig_engine_set_staging_limit", "trig_engine_fail_result_allocs", "trig_set_device_wait",
 ]
 
 NOALLOC_SCRATCH_BYTES = 64 << 20
@@ -141,6 +142,10 @@ def load(path: str | None = None):
         "trig_result_free": (None, [c.POINTER(trig_result)]),
         "trig_engine_set_mode": (c.c_int, [c.c_int]),
         "trig_engine_stats": (c.c_int, [c.POINTER(c.c_uint64), c.POINTER(c.c_uint64)]),
+        "trig_engine_hold": (c.c_int, [c.c_int]),
+        "trig_engine_set_staging_limit": (c.c_int, [c.c_uint64]),
+        "trig_engine_fail_result_allocs": (c.c_int, [c.c_uint32]),
+        "trig_set_device_wait": (c.c_int, [c.c_uint64, c.c_int]),
         "trig_last_error": (c.c_char_p, []),
         "trig_batch_scratch_bytes": (c.c_size_t, [c.POINTER(trig_slice_dev), c.c_uint32]),
         "trig_batch_run": (c.c_int, [c.POINTER(trig_slice_dev), c.c_uint32, c.c_void_p, c.c_size_t, c.c_void_p,
@@ -364,6 +369,27 @@ def trig_engine_stats() -> tuple[int, int]:
     return int(b.value), int(s.value)
 
 
+def trig_engine_hold(on: bool) -> None:
+    """Admit no new engine batch while on (submissions still queue)."""
+    _check(load().trig_engine_hold(1 if on else 0))
+
+
+def trig_engine_set_staging_limit(nbytes: int) -> None:
+    """Device staging memory the engine's submissions may hold (0: no limit)."""
+    _check(load().trig_engine_set_staging_limit(int(nbytes)))
+
+
+def trig_engine_fail_result_allocs(n: int) -> None:
+    """Failure injection: the next n result-memory requests fail (TRIG_ENOMEM results)."""
+    _check(load().trig_engine_fail_result_allocs(int(n)))
+
+
+def trig_set_device_wait(limit_ns: int = 0, stall: bool = False) -> None:
+    """Limit of the tile pass's device waits (0: the default second); stall
+    is the test control that stages nothing, so the waits run out."""
+    _check(load().trig_set_device_wait(int(limit_ns), 1 if stall else 0))
+
+
 def trig_set_tile_config(cap: int, warps: int, fill_pct: int) -> None:
     _check(load().trig_set_tile_config(int(cap), int(warps), int(fill_pct)))
 
@@ -448,8 +474,9 @@ def trig_batch_run_events(slices, events, scratch_ptr: int, scratch_bytes: int, 
                                         scratch_bytes, stream_ptr or None, flags))
 
 
-def trig_batch_run_noalloc(slices, stream_ptr: int = 0) -> None:
-    """trig_batch_run on the library's static scratch (no allocation)."""
+def trig_batch_run_noalloc(slices, stream_ptr: int) -> None:
+    """trig_batch_run on the library's static scratch (no allocation), on a
+    stream the caller created (the legacy default stream is refused)."""
     arr = _array(slices)
     _check(load().trig_batch_run_noalloc(arr, len(slices), stream_ptr or None))
 

@@ -102,6 +102,19 @@ extern "C" int trig_get_tile_config(uint32_t *cap, uint32_t *warps, uint32_t *fi
     return TRIG_OK;
 }
 
+// Limit of the tile pass's device waits and the stall test control.
+static std::atomic<uint64_t> g_wait_ns{kDefaultWaitNs};
+static std::atomic<uint32_t> g_stall{0};
+
+extern "C" int trig_set_device_wait(uint64_t limit_ns, int stall)
+{
+    if (stall != 0 && stall != 1) return fail(TRIG_EINVAL, "stall must be 0 or 1");
+    if (limit_ns > (uint64_t)600 * kDefaultWaitNs) return fail(TRIG_EINVAL, "limit_ns must be at most 600 s");
+    g_wait_ns = limit_ns ? limit_ns : kDefaultWaitNs;
+    g_stall = (uint32_t)stall;
+    return TRIG_OK;
+}
+
 static TileConfig current_cfg()
 {
     std::lock_guard<std::mutex> lk(g_cfg_mu);
@@ -120,6 +133,19 @@ struct DetQueue {
     uint64_t in_flight = 0;
 };
 
+// The detector's resident slice tail: the hits of its last submission in
+// [t0 + S - halo, t0 + S) (halo = the accepted input halo), grouped by PMT,
+// kept on the device as the leading halo of a continuation submission.
+struct TailState {
+    std::mutex mu;                  // serialises the detector's submissions
+    bool have = false;
+    int64_t next_t0 = 0;            // t0 of the slice that may continue it
+    trig_hit *d_hits = nullptr;     // device, cap entries
+    uint64_t *d_off = nullptr;      // device, n_pmt + 1 offsets
+    size_t cap = 0;
+    std::vector<uint64_t> off;      // host copy of the offsets
+};
+
 struct trig_detector {
     uint32_t n_pmt = 0;
     trig_params par{};
@@ -134,6 +160,7 @@ struct trig_detector {
     bool tuned = false;           // tile shape chosen by trig_autotune (or its cache)
     TileConfig tile{};
     bool events = false;          // engine results carry the event payload
+    TailState tail;
 };
 
 namespace trig {
@@ -154,6 +181,10 @@ void count_launches(uint64_t n) { g_launches += n; }
 
 static void free_det_dev(trig_detector *d)
 {
+    cudaFree(d->tail.d_hits);
+    cudaFree(d->tail.d_off);
+    d->tail.d_hits = nullptr;
+    d->tail.d_off = nullptr;
     cudaFree(d->dev.dt);
     cudaFree(d->dev.dt_exact);
     cudaFree(d->dev.floor);
@@ -570,6 +601,8 @@ static int plan_into(const trig_slice_dev *sl, uint32_t n, uintptr_t base, const
     hdr.dense = dense ? 1u : 0u;
     hdr.n_items = items;
     hdr.n_chunks = chunks;
+    hdr.wait_ns = g_wait_ns.load();
+    hdr.stall = g_stall.load();
     bytes = off;
     return TRIG_OK;
 }
@@ -1007,32 +1040,40 @@ extern "C" int trig_batch_run_noalloc(const trig_slice_dev *slices, uint32_t n_s
 {
     if (!slices || n_slices == 0 || n_slices > TRIG_NOALLOC_MAX_SLICES)
         return fail(TRIG_EINVAL, "trig_batch_run_noalloc: 1 to TRIG_NOALLOC_MAX_SLICES slices");
+    cudaStream_t st = (cudaStream_t)stream;
+    // the legacy default stream synchronises with every blocking stream,
+    // and another thread's global-mode capture forbids its use
+    if (st == nullptr || st == cudaStreamLegacy)
+        return fail(TRIG_EINVAL, "trig_batch_run_noalloc: pass a stream created with cudaStreamNonBlocking");
+    // the shared static array would be baked into a graph and raced by
+    // every replay: the call is not for capture
+    cudaStreamCaptureStatus cap_status = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &cap_status);
+    if (e) return cuda_fail(e, "trig_batch_run_noalloc: stream capture status");
+    if (cap_status != cudaStreamCaptureStatusNone)
+        return fail(TRIG_EINVAL, "trig_batch_run_noalloc: the stream is capturing; this call must not be captured");
     void *scratch = nullptr;
     size_t cap = 0;
-    cudaError_t e = static_scratch(&scratch, &cap);
+    e = static_scratch(&scratch, &cap);
     if (e) return cuda_fail(e, "trig_batch_run_noalloc: static scratch address");
     const TileConfig cfg = current_cfg();
-    BatchHeader hdr;
-    SliceDesc desc[TRIG_NOALLOC_MAX_SLICES];
+    NoallocPlan plan;
     size_t bytes = 0;
     uint32_t max_pmt = 0;
     bool smem_dt = true, any_wide = false;
     TileConfig shape{};
-    int rc = plan_into(slices, n_slices, (uintptr_t)scratch, cfg, hdr, desc, bytes, max_pmt, smem_dt, any_wide,
-                       &shape);
+    int rc = plan_into(slices, n_slices, (uintptr_t)scratch, cfg, plan.hdr, plan.desc, bytes, max_pmt, smem_dt,
+                       any_wide, &shape);
     if (rc) return rc;
     if (bytes > cap) return fail(TRIG_ECAPACITY, "trig_batch_run_noalloc: batch needs more than TRIG_NOALLOC_SCRATCH_BYTES of scratch");
-    cudaStream_t st = (cudaStream_t)stream;
-    // pageable sources: both copies are staged before the calls return
-    e = cudaMemcpyAsync(scratch, &hdr, sizeof hdr, cudaMemcpyHostToDevice, st);
-    if (!e)
-        e = cudaMemcpyAsync((char *)scratch + align256(sizeof(BatchHeader)), desc, sizeof(SliceDesc) * n_slices,
-                            cudaMemcpyHostToDevice, st);
-    if (e) return cuda_fail(e, "trig_batch_run_noalloc: copy descriptors");
-    uint64_t nl = 0;
-    e = launch_batch(reinterpret_cast<BatchHeader *>(scratch),
-                     reinterpret_cast<SliceDesc *>((char *)scratch + align256(sizeof(BatchHeader))), n_slices,
-                     max_pmt, smem_dt, any_wide, false, hdr.any_ext != 0, hdr.dense != 0, shape, st, &nl, false);
+    plan.n = n_slices;
+    BatchHeader *d_hdr = reinterpret_cast<BatchHeader *>(scratch);
+    SliceDesc *d_desc = reinterpret_cast<SliceDesc *>((char *)scratch + align256(sizeof(BatchHeader)));
+    e = launch_put_plan(plan, d_hdr, d_desc, st);
+    if (e) return cuda_fail(e, "trig_batch_run_noalloc: descriptors");
+    uint64_t nl = 1;
+    e = launch_batch(d_hdr, d_desc, n_slices, max_pmt, smem_dt, any_wide, false, plan.hdr.any_ext != 0,
+                     plan.hdr.dense != 0, shape, st, &nl, false);
     g_launches += nl;
     if (e) return cuda_fail(e, "trig_batch_run_noalloc: launch");
     return TRIG_OK;
@@ -1064,16 +1105,20 @@ struct DevicePool {
     std::mutex mu;
     std::multimap<size_t, unsigned char *> free_blocks;
     size_t used = 0;
+    size_t in_use = 0;              // bytes of blocks handed out and not yet returned
+    size_t limit = 0;               // 0: no limit beyond free device memory
     unsigned char *get(size_t bytes, size_t *got)
     {
         size_t cls = (size_t)1 << 16;
         while (cls < bytes) cls <<= 1;
         std::lock_guard<std::mutex> lk(mu);
+        if (limit && in_use + cls > limit) return nullptr;
         // the smallest free block that fits, up to four classes larger
         auto it = free_blocks.lower_bound(cls);
         if (it != free_blocks.end() && it->first <= 4 * cls) {
             unsigned char *p = it->second;
             *got = it->first;
+            in_use += it->first;
             free_blocks.erase(it);
             return p;
         }
@@ -1093,12 +1138,14 @@ struct DevicePool {
             return nullptr;
         }
         used += cls;
+        in_use += cls;
         *got = cls;
         return static_cast<unsigned char *>(p);
     }
     void put(unsigned char *p, size_t cls)
     {
         std::lock_guard<std::mutex> lk(mu);
+        in_use -= cls;
         free_blocks.emplace(cls, p);
     }
 };
@@ -1110,11 +1157,16 @@ struct HostPool {
     std::mutex mu;
     std::multimap<size_t, unsigned char *> free_blocks;
     size_t used = 0, limit = (size_t)24 << 30;
+    uint32_t fail_next = 0;         // failure injection: the next n requests fail
     unsigned char *get(size_t bytes, size_t *got)
     {
         size_t cls = 4096;
         while (cls < bytes) cls <<= 1;
         std::lock_guard<std::mutex> lk(mu);
+        if (fail_next) {
+            --fail_next;
+            return nullptr;
+        }
         // the smallest free block that fits, up to four classes larger: a
         // new page-locked allocation stalls the engine thread for
         // milliseconds
@@ -1207,6 +1259,7 @@ struct Engine {
     HostPool rpool;
     std::thread worker;
     bool stop = false;
+    bool hold = false;              // admit no new batch while set
     int mode = 1;
     std::atomic<uint64_t> next_id{1};
     std::atomic<uint64_t> batches{0}, completed{0};
@@ -1528,7 +1581,7 @@ void Engine::run()
         bool busy = false;
         for (auto &s : slots) busy |= s.state != 0;
         if (stop && !busy && pending.empty()) break;
-        if (!busy && pending.empty()) {
+        if (!busy && (pending.empty() || hold)) {
             cv.wait(lk);
             continue;
         }
@@ -1549,7 +1602,7 @@ void Engine::run()
         lk.lock();
         // admit a new batch into an idle slot
         bool launched = false;
-        if (!pending.empty()) {
+        if (!pending.empty() && !hold) {
             for (auto &s : slots) {
                 if (s.state != 0) continue;
                 std::vector<Pending> batch;
@@ -1600,6 +1653,37 @@ extern "C" int trig_engine_set_mode(int mode)
     return TRIG_OK;
 }
 
+extern "C" int trig_engine_hold(int on)
+{
+    if (on != 0 && on != 1) return fail(TRIG_EINVAL, "on must be 0 or 1");
+    Engine *e = engine();
+    if (!e) return TRIG_EDEVICE;
+    {
+        std::lock_guard<std::mutex> lk(e->mu);
+        e->hold = on != 0;
+    }
+    e->cv.notify_all();
+    return TRIG_OK;
+}
+
+extern "C" int trig_engine_set_staging_limit(uint64_t bytes)
+{
+    Engine *e = engine();
+    if (!e) return TRIG_EDEVICE;
+    std::lock_guard<std::mutex> lk(e->pool.mu);
+    e->pool.limit = (size_t)bytes;
+    return TRIG_OK;
+}
+
+extern "C" int trig_engine_fail_result_allocs(uint32_t n)
+{
+    Engine *e = engine();
+    if (!e) return TRIG_EDEVICE;
+    std::lock_guard<std::mutex> lk(e->rpool.mu);
+    e->rpool.fail_next = n;
+    return TRIG_OK;
+}
+
 extern "C" int trig_engine_stats(uint64_t *batches, uint64_t *slices)
 {
     Engine *e = engine();
@@ -1609,38 +1693,76 @@ extern "C" int trig_engine_stats(uint64_t *batches, uint64_t *slices)
     return TRIG_OK;
 }
 
+// First index i in [lo, hi) of a time-ordered host run with hits[i].t_ns >= v
+// (for a run that is not ordered: some index in [lo, hi]).
+static uint64_t host_lb(const trig_hit *h, uint64_t lo, uint64_t hi, int64_t v)
+{
+    while (lo < hi) {
+        const uint64_t mid = lo + (hi - lo) / 2;
+        if (h[mid].t_ns < v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
 extern "C" int trig_submit_slice(trig_detector *det, int64_t t0, const trig_hit *hits, const uint64_t *pmt_off,
                                  int is_continuation, uint64_t *slice_id_out)
 {
     const auto t_entry = Clock::now();
     if (!det || !pmt_off) return fail(TRIG_EINVAL, "NULL argument");
-    if (is_continuation) return fail(TRIG_EINVAL, "is_continuation: submissions carry their own halos");
+    if (is_continuation != 0 && is_continuation != 1) return fail(TRIG_EINVAL, "is_continuation must be 0 or 1");
     const uint32_t P = det->n_pmt;
     if (pmt_off[0] != 0) return fail(TRIG_EINVAL, "pmt_off[0] must be 0");
     for (uint32_t p = 0; p < P; ++p)
         if (pmt_off[p + 1] < pmt_off[p]) return fail(TRIG_EINVAL, "pmt_off must be non-decreasing");
     const uint64_t n = pmt_off[P];
     if (n && !hits) return fail(TRIG_EINVAL, "hits is NULL");
-    if (n > kMaxSliceHits) return fail(TRIG_EINVAL, "too many hits in one slice");
+    const int64_t S = det->par.slice_ns, halo = det->in_halo;
+    if (halo > S) return fail(TRIG_EINVAL, "the detector's halo is longer than its slice");
+    if (t0 < -((int64_t)1 << 61) || t0 > ((int64_t)1 << 61)) return fail(TRIG_EINVAL, "t0 out of range");
     Engine *e = engine();
     if (!e) return fail(TRIG_EDEVICE, std::string("engine failed to start: ") + g_last_error);
+    // one submission of a detector at a time: its resident tail changes here
+    TailState &tl = det->tail;
+    std::lock_guard<std::mutex> tail_lock(tl.mu);
+    uint64_t T = 0;                                   // resident tail hits prepended
+    if (is_continuation) {
+        if (!tl.have) return fail(TRIG_EINVAL, "is_continuation: the detector has no previous submission");
+        if (t0 != tl.next_t0) return fail(TRIG_EINVAL, "is_continuation: t0 must be the previous slice's t0 + slice_ns");
+        T = tl.off[P];
+        // the resident tail is the leading halo: the submission starts at t0
+        for (uint32_t q = 0; q < P; ++q)
+            if (pmt_off[q + 1] > pmt_off[q] && hits[pmt_off[q]].t_ns < t0)
+                return fail(TRIG_EINVAL, "is_continuation: the submission holds hits before t0");
+    }
+    if (n + T > kMaxSliceHits) return fail(TRIG_EINVAL, "too many hits in one slice");
     Pending p;
     p.det = det;
     p.q = det->q;
     p.t0 = t0;
-    p.n_hits = n;
+    p.n_hits = n + T;
     // copy the slice to a device block now (the caller may reuse its
-    // buffers on return): pageable host memory straight to the device, on a
-    // stream of this thread's own
-    p.pmt_at = align256(n * sizeof(trig_hit));
+    // buffers on return), on a stream of this thread's own; a continuation
+    // goes to a second block first and is combined with the resident tail
+    p.pmt_at = align256(p.n_hits * sizeof(trig_hit));
     const size_t bytes = p.pmt_at + (size_t)(P + 1) * 8;
     int prev_dev = -1;
     cudaGetDevice(&prev_dev);
+    struct DeviceGuard {
+        int prev, dev;
+        ~DeviceGuard() { if (prev != dev) cudaSetDevice(prev); }
+    } guard{prev_dev, e->device};
     if (prev_dev != e->device) cudaSetDevice(e->device);
     p.dblk = e->pool.get(bytes, &p.dbytes);
-    if (!p.dblk) {
-        if (prev_dev != e->device) cudaSetDevice(prev_dev);
-        return fail(TRIG_EAGAIN, "device staging memory full; poll results and retry");
+    if (!p.dblk) return fail(TRIG_EAGAIN, "device staging memory full; poll results and retry");
+    unsigned char *raw = nullptr;
+    size_t raw_bytes = 0, raw_pmt_at = 0;
+    if (T) {
+        raw_pmt_at = align256(n * sizeof(trig_hit));
+        raw = e->pool.get(raw_pmt_at + (size_t)(P + 1) * 8, &raw_bytes);
+        if (!raw) {
+            e->pool.put(p.dblk, p.dbytes);
+            return fail(TRIG_EAGAIN, "device staging memory full; poll results and retry");
+        }
     }
     thread_local cudaStream_t copy_stream = nullptr;
     thread_local int copy_dev = -1;
@@ -1649,14 +1771,53 @@ extern "C" int trig_submit_slice(trig_detector *det, int64_t t0, const trig_hit 
         ce = cudaStreamCreateWithFlags(&copy_stream, cudaStreamNonBlocking);
         copy_dev = e->device;
     }
-    if (!ce && n) ce = cudaMemcpyAsync(p.dblk, hits, n * sizeof(trig_hit), cudaMemcpyHostToDevice, copy_stream);
-    if (!ce) ce = cudaMemcpyAsync(p.dblk + p.pmt_at, pmt_off, (size_t)(P + 1) * 8, cudaMemcpyHostToDevice, copy_stream);
+    unsigned char *dst = T ? raw : p.dblk;
+    const size_t dst_pmt_at = T ? raw_pmt_at : p.pmt_at;
+    if (!ce && n) ce = cudaMemcpyAsync(dst, hits, n * sizeof(trig_hit), cudaMemcpyHostToDevice, copy_stream);
+    if (!ce) ce = cudaMemcpyAsync(dst + dst_pmt_at, pmt_off, (size_t)(P + 1) * 8, cudaMemcpyHostToDevice, copy_stream);
+    if (!ce && T)
+        ce = launch_prepend(tl.d_hits, tl.d_off, T, reinterpret_cast<const trig_hit *>(raw),
+                            reinterpret_cast<const uint64_t *>(raw + raw_pmt_at), n, P,
+                            reinterpret_cast<trig_hit *>(p.dblk), reinterpret_cast<uint64_t *>(p.dblk + p.pmt_at),
+                            copy_stream);
     if (!ce) ce = cudaStreamSynchronize(copy_stream);
-    if (prev_dev != e->device) cudaSetDevice(prev_dev);
+    // the next slice's leading halo: this submission's hits in
+    // [t0 + S - halo, t0 + S), PMT by PMT (a producer's unordered stream
+    // gives some sub-range; the device flags such a slice)
+    std::vector<uint64_t> toff(P + 1, 0);
+    std::vector<trig_hit> th;
+    if (!ce) {
+        for (uint32_t q = 0; q < P; ++q) {
+            const uint64_t a = host_lb(hits, pmt_off[q], pmt_off[q + 1], t0 + S - halo);
+            const uint64_t b = host_lb(hits, a, pmt_off[q + 1], t0 + S);
+            th.insert(th.end(), hits + a, hits + b);
+            toff[q + 1] = th.size();
+        }
+        if (th.size() > tl.cap) {
+            cudaFree(tl.d_hits);
+            tl.d_hits = nullptr;
+            tl.cap = 0;
+            const size_t want = std::max<size_t>(th.size() + th.size() / 2, 1024);
+            ce = cudaMalloc(&tl.d_hits, want * sizeof(trig_hit));
+            if (!ce) tl.cap = want;
+        }
+        if (!ce && !tl.d_off) ce = cudaMalloc(&tl.d_off, (size_t)(P + 1) * 8);
+        if (!ce && !th.empty())
+            ce = cudaMemcpyAsync(tl.d_hits, th.data(), th.size() * sizeof(trig_hit), cudaMemcpyHostToDevice,
+                                 copy_stream);
+        if (!ce) ce = cudaMemcpyAsync(tl.d_off, toff.data(), (size_t)(P + 1) * 8, cudaMemcpyHostToDevice, copy_stream);
+        if (!ce) ce = cudaStreamSynchronize(copy_stream);
+    }
+    if (raw) e->pool.put(raw, raw_bytes);
     if (ce) {
         (void)cudaGetLastError();
+        tl.have = false;                              // the resident tail is not valid now
+        e->pool.put(p.dblk, p.dbytes);
         return fail(TRIG_EDEVICE, std::string("copying the slice to the device: ") + cudaGetErrorString(ce));
     }
+    tl.off = std::move(toff);
+    tl.have = true;
+    tl.next_t0 = t0 + S;
     p.t_submit = t_entry;
     p.id = e->next_id++;
     {

@@ -118,8 +118,11 @@ struct BatchHeader {
     uint32_t any_events;    // a slice of the batch extracts events
     uint32_t any_ext;       // a slice uses level 0, seed rule 1 or the distinct count
     uint32_t dense;         // a slice expects kDenseKeys or more keys per causal scan range
-    uint32_t pad;
+    uint32_t stall;         // test control: the tile pass's stagers fill nothing, so its waits run out
+    uint64_t wait_ns;       // limit of every device wait (ns); a wait that runs out sets TRIG_FLAG_TIMEOUT
 };
+
+constexpr uint64_t kDefaultWaitNs = 1000000000ull;     // one second
 
 // Expected keys in a seed's scan range (2H + 1 ns at the slice's mean rate)
 // from which the causal count gives each seed a warp instead of 4 lanes.
@@ -168,6 +171,12 @@ cudaError_t launch_batch(BatchHeader *d_hdr, SliceDesc *d_desc, uint32_t n_slice
 
 int device_sm_count();
 
+// Continuation submissions: the combined slice (resident tail of each PMT,
+// then the submission's hits of that PMT) into out / out_off.
+cudaError_t launch_prepend(const trig_hit *tail, const uint64_t *tail_off, uint64_t n_tail, const trig_hit *fresh,
+                           const uint64_t *fresh_off, uint64_t n_fresh, uint32_t P, trig_hit *out, uint64_t *out_off,
+                           cudaStream_t st);
+
 // What other translation units of the library read of a detector.
 struct DetInfo {
     uint32_t n_pmt;
@@ -185,5 +194,16 @@ void count_launches(uint64_t n);
 
 // Address and size of the library's static scratch array on the current device.
 cudaError_t static_scratch(void **ptr, size_t *bytes);
+
+// A no-allocation batch's header and descriptors, passed by value to the
+// kernel that writes them into the static scratch array.
+struct NoallocPlan {
+    BatchHeader hdr;
+    SliceDesc desc[TRIG_NOALLOC_MAX_SLICES];
+    uint32_t n;
+};
+static_assert(sizeof(BatchHeader) % 4 == 0 && sizeof(SliceDesc) % 4 == 0, "copied as 32-bit words");
+static_assert(sizeof(NoallocPlan) <= 32000, "kernel parameter space");
+cudaError_t launch_put_plan(const NoallocPlan &plan, BatchHeader *hdr, SliceDesc *desc, cudaStream_t st);
 
 }  // namespace trig

@@ -23,6 +23,7 @@
 //
 // Every wait on an mbarrier is bounded; a wait that gives up sets
 // TRIG_FLAG_TIMEOUT on the batch and the kernel returns.
+#include <algorithm>
 #include <cstdint>
 #include <mutex>
 #include <cuda_runtime.h>
@@ -67,14 +68,39 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 
-// Bounded wait: about a second at most, then report failure.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+// try_wait with a suspend-time hint: a thread whose phase is not complete
+// is suspended until it completes or about `ns` nanoseconds pass, instead
+// of spinning and issuing instructions.
+__device__ __forceinline__ bool mbar_try_wait_hint(uint64_t *bar, uint32_t parity, uint32_t ns)
 {
-    for (uint32_t i = 0; i < (1u << 22); ++i) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if (i >= 8) __nanosleep(i < 4096 ? 32 : 256);
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(ns)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait: gives up after limit_ns of the GPU's global timer and
+// reports failure.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t_start = global_ns();
+    for (;;) {
+        if (mbar_try_wait_hint(bar, parity, 20000u)) return true;
+        if (global_ns() - t_start > limit_ns) return false;
     }
-    return false;
 }
 
 // Bulk (non-tensor) TMA copy global -> shared, completing on an mbarrier.
@@ -640,16 +666,35 @@ struct ItemInfo {
     uint32_t span;      // length of the staged time range (ns)
 };
 
+// Shared memory of the tile kernel, in this order: the staging buffers of
+// CAP 16-byte records (two, or one for the 2048-hit tile: its tile pass
+// hands the buffer back once it has read it, so the next tile's copy
+// overlaps the rest of the pass, and two blocks of it then fit on an SM); the tile's packed keys in merged order (+16 bytes:
+// the causal count reads 16 bytes at a time past the last key); the keys in
+// bucket order (reused as the seed list and seed counts once merged); the
+// charges in bucket order and in merged order; the bucket offsets; the seed
+// mask; the PMT tables (floor, row maximum of dt, and dt itself when the
+// detector's table fits).
 template <int CAP>
 struct TileLayout {
-    static constexpr int NBK = CAP / 2;                    // time buckets of the in-tile merge
+    static constexpr int NBK = CAP;                        // time buckets of the in-tile merge
+    static constexpr uint32_t NS = CAP == 2048 ? 1u : 2u;  // staging buffers
     static constexpr size_t kStage = (size_t)CAP * 16;     // one staging buffer
-    static constexpr size_t kTemp = (size_t)CAP * 8;
+    static constexpr size_t kPkS = (size_t)CAP * 4 + 16;
+    static constexpr size_t kPkB = (size_t)CAP * 4;
+    static constexpr size_t kChg = (size_t)CAP * 2;
     static constexpr size_t kCnt = (size_t)(NBK + 1) * 4;
     static constexpr size_t kMask = (size_t)(CAP / 32) * 4;
+    static constexpr size_t oPkS = NS * kStage;
+    static constexpr size_t oPkB = oPkS + kPkS;
+    static constexpr size_t oChgB = oPkB + kPkB;
+    static constexpr size_t oChgS = oChgB + kChg;
+    static constexpr size_t oCnt = oChgS + kChg;
+    static constexpr size_t oMask = oCnt + kCnt;
+    static constexpr size_t oTab = (oMask + kMask + 15) & ~(size_t)15;
     static size_t bytes(uint32_t P, bool smem_dt)
     {
-        size_t b = 2 * kStage + kTemp + kCnt + kMask;
+        size_t b = oTab;
         b += 2 * (size_t)((P + 7) & ~7u) * 2;              // floor + dmax_row
         if (smem_dt) b += (size_t)P * P * 2;
         return (b + 127) & ~(size_t)127;
@@ -672,22 +717,18 @@ struct TileCtx {
     {
         return reinterpret_cast<uint64_t *>(g_tile_smem + (size_t)b * L::kStage);
     }
-    __device__ __forceinline__ uint64_t *temp() const
+    __device__ __forceinline__ uint32_t *pk_s() const { return reinterpret_cast<uint32_t *>(g_tile_smem + L::oPkS); }
+    __device__ __forceinline__ uint32_t *pk_b() const { return reinterpret_cast<uint32_t *>(g_tile_smem + L::oPkB); }
+    __device__ __forceinline__ uint16_t *seed_idx() const { return reinterpret_cast<uint16_t *>(g_tile_smem + L::oPkB); }
+    __device__ __forceinline__ uint16_t *seed_cnt() const
     {
-        return reinterpret_cast<uint64_t *>(g_tile_smem + 2 * L::kStage);
+        return reinterpret_cast<uint16_t *>(g_tile_smem + L::oPkB) + CAP;
     }
-    __device__ __forceinline__ uint32_t *cnt() const
-    {
-        return reinterpret_cast<uint32_t *>(g_tile_smem + 2 * L::kStage + L::kTemp);
-    }
-    __device__ __forceinline__ uint32_t *mask() const
-    {
-        return reinterpret_cast<uint32_t *>(g_tile_smem + 2 * L::kStage + L::kTemp + L::kCnt);
-    }
-    __device__ __forceinline__ uint16_t *floor_s() const
-    {
-        return reinterpret_cast<uint16_t *>(g_tile_smem + 2 * L::kStage + L::kTemp + L::kCnt + L::kMask);
-    }
+    __device__ __forceinline__ uint16_t *chg_b() const { return reinterpret_cast<uint16_t *>(g_tile_smem + L::oChgB); }
+    __device__ __forceinline__ uint16_t *chg_s() const { return reinterpret_cast<uint16_t *>(g_tile_smem + L::oChgS); }
+    __device__ __forceinline__ uint32_t *cnt() const { return reinterpret_cast<uint32_t *>(g_tile_smem + L::oCnt); }
+    __device__ __forceinline__ uint32_t *mask() const { return reinterpret_cast<uint32_t *>(g_tile_smem + L::oMask); }
+    __device__ __forceinline__ uint16_t *floor_s() const { return reinterpret_cast<uint16_t *>(g_tile_smem + L::oTab); }
     __device__ __forceinline__ uint16_t *dmax_s() const { return floor_s() + pp; }
     __device__ __forceinline__ uint16_t *dt_s() const { return floor_s() + 2 * (size_t)pp; }
 };
@@ -744,86 +785,6 @@ __device__ __forceinline__ uint32_t bucket_of(uint32_t t_rel, uint32_t bsh)
     constexpr uint32_t NBK = TileLayout<CAP>::NBK;
     const uint32_t b = t_rel >> bsh;
     return b < NBK ? b : NBK - 1;
-}
-
-// Merge (sort) the n staged records of `buf` by (t - tb, pmt, charge); the
-// keys land, in order, in the first 8 * n bytes of `buf`, and their packed
-// 32-bit forms (t_rel << 12 | pmt, the staged range spans < 2^20 ns) at
-// buf + CAP.  Counting sort on
-// the time bucket t_rel >> bsh, then each key's rank inside its bucket;
-// cx.cnt()[b] keeps the index of bucket b's first key (cx.cnt()[NBK] = n), so a
-// time range maps to an index range without a search.  Also counts the keys
-// with t_rel < lo_t and < hi_t into red[NC/32 + 1] and red[NC/32 + 2] (the
-// first core index and the core's end).  Returns bsh.
-template <int CAP, int NC>
-__device__ uint32_t tile_sort(TileCtx<CAP> &cx, uint64_t *buf, uint32_t n, int64_t tb, uint32_t span, uint32_t *red,
-                              uint32_t lo_t, uint32_t hi_t)
-{
-    uint32_t *pk = reinterpret_cast<uint32_t *>(buf + CAP);      // packed keys, upper half of the buffer
-    constexpr uint32_t NW = NC / 32;
-    constexpr int NBK = TileLayout<CAP>::NBK;
-    constexpr int PER = CAP / NC;
-    const uint32_t tid = threadIdx.x;
-    uint32_t bsh = 0;
-    {
-        uint32_t top = span > 1 ? 32u - __clz(span - 1u) : 0u;    // bits of span - 1
-        uint32_t nb_bits = 31u - __clz((uint32_t)NBK);
-        bsh = top > nb_bits ? top - nb_bits : 0u;
-    }
-    for (uint32_t i = tid; i < (uint32_t)NBK; i += NC) cx.cnt()[i] = 0;
-    if (tid == 0) red[NW + 1] = red[NW + 2] = 0;
-    cons_sync<NC>();
-    uint64_t kreg[PER];
-    uint32_t slot[PER];
-    uint32_t below_lo = 0, below_hi = 0;
-#pragma unroll
-    for (int r = 0; r < PER; ++r) {
-        uint32_t i = tid + r * NC;
-        kreg[r] = 0;
-        slot[r] = 0;
-        if (r * NC < n && i < n) {
-            const uint64_t *rec = buf + 2 * i;
-            int64_t t = (int64_t)rec[0];
-            uint32_t w1 = (uint32_t)rec[1];
-            int64_t rel = t - tb;
-            uint32_t tr = rel < 0 ? 0u : (rel > 0xffffffffll ? 0xffffffffu : (uint32_t)rel);
-            kreg[r] = ((uint64_t)tr << 32) | ((uint64_t)(w1 & 0xffffu) << 16) | (uint64_t)(w1 >> 16);
-            slot[r] = atomicAdd(&cx.cnt()[bucket_of<CAP>(tr, bsh)], 1u);
-            below_lo += tr < lo_t;
-            below_hi += tr < hi_t;
-        }
-    }
-    below_lo = __reduce_add_sync(0xffffffffu, below_lo);
-    below_hi = __reduce_add_sync(0xffffffffu, below_hi);
-    if (lane_id() == 0) {
-        if (below_lo) atomicAdd(&red[NW + 1], below_lo);
-        if (below_hi) atomicAdd(&red[NW + 2], below_hi);
-    }
-    cons_sync<NC>();
-    cons_exclusive_scan<NC>(cx.cnt(), NBK, red);
-#pragma unroll
-    for (int r = 0; r < PER; ++r) {
-        uint32_t i = tid + r * NC;
-        if (r * NC < n && i < n) {
-            cx.temp()[cx.cnt()[bucket_of<CAP>(key_t(kreg[r]), bsh)] + slot[r]] = kreg[r];
-        }
-    }
-    cons_sync<NC>();
-    // rank inside each bucket; identical keys are interchangeable
-    for (uint32_t j = tid; j < n; j += NC) {
-        uint64_t k = cx.temp()[j];
-        const uint32_t bk = bucket_of<CAP>(key_t(k), bsh);
-        uint32_t s0 = cx.cnt()[bk], s1 = cx.cnt()[bk + 1];
-        uint32_t r = s0;
-        for (uint32_t m = s0; m < s1; ++m) {
-            uint64_t o = cx.temp()[m];
-            r += (o < k) || (o == k && m < j);
-        }
-        buf[r] = k;
-        pk[r] = (key_t(k) << 12) | key_p(k);
-    }
-    cons_sync<NC>();
-    return bsh;
 }
 
 struct CoreOut {
@@ -1040,122 +1001,235 @@ __device__ __forceinline__ void count_causal(const TileCtx<CAP> &cx, const uint3
     }
 }
 
-// The core is keys[c0, c1) (t_rel in [H, H + core width)).
+// Bucket shift of a staged range of `span` ns: buckets of 2^bsh ns, NBK of
+// them cover the range.
+template <int CAP>
+__device__ __forceinline__ uint32_t bucket_shift(uint32_t span)
+{
+    const uint32_t top = span > 1 ? 32u - __clz(span - 1u) : 0u;      // bits of span - 1
+    const uint32_t nb_bits = 31u - __clz((uint32_t)TileLayout<CAP>::NBK);
+    return top > nb_bits ? top - nb_bits : 0u;
+}
+
+// One staged tile through the whole trigger: the n records of `stage` (16
+// bytes each, time t_ns, PMT and charge; any order) span [tb, tb + span);
+// the core is t - tb in [lo_t, hi_t).
+//
+//  A. every record becomes a packed key (t - tb) << 12 | pmt and is counted
+//     in its time bucket (t - tb) >> bsh; the stage buffer is then handed
+//     back to the producer (release_bar), the rest works on the keys;
+//  B. bucket offsets (exclusive scan of the counts);
+//  C. keys (and charges) scattered to bucket order, then each key ranked
+//     inside its bucket by (t, pmt, charge): the k-way merge of the PMT
+//     runs ("DAQ system of NEMO Phase II"), one key per bucket on average;
+//  D. seeds ("Sorting and triggering in GPU"): a charge over q_seed, or
+//     another PMT of the same floor within tau -- each hit walks forward
+//     through the merged keys while they are within tau, so every pair is
+//     seen once, and both hits of a pair are marked; seed rule 1 and level 0
+//     of the extended builds (EXT) test each core hit instead;
+//  E. the ordered seed list; F. the causal count of every seed ("Muon
+//     trigger strategy"); G. the fired seeds, in merged order, to out.
+//
+// Returns the counts and c0 = the number of staged keys before the core (the
+// core is keys [c0, c1) of the merged order).  cnt and mask are zero on
+// entry and on return.
 template <int CAP, int NC, bool SMEM_DT, bool EXT, bool DENSE>
-__device__ CoreOut tile_trigger(TileCtx<CAP> &cx, const uint64_t *keys, uint32_t n, uint32_t bsh, uint32_t c0, uint32_t c1,
-                                int64_t tb, const TrigParams &tp, trig_trigger *out, int64_t dbg_rank_lo,
-                                uint32_t *red)
+__device__ CoreOut tile_pass(TileCtx<CAP> &cx, const uint64_t *stage, uint32_t n, int64_t tb, uint32_t span,
+                             uint32_t lo_t, uint32_t hi_t, const TrigParams &tp, trig_trigger *out, bool out_at_c0,
+                             int64_t dbg_rank_lo, uint64_t *release_bar)
 {
     constexpr uint32_t NW = NC / 32;
+    constexpr int PER = CAP / NC;
     const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
-    const uint32_t ncore = c1 - c0;
-    const uint32_t tau = tp.tau, qseed = tp.q_seed, threshold = tp.threshold, P = cx.P;
-    // scratch per seed (CAP entries each): index and count (16-bit)
-    uint16_t *seed_idx = reinterpret_cast<uint16_t *>(cx.temp());
-    uint16_t *seed_cnt = seed_idx + CAP;
+    const uint32_t bsh = bucket_shift<CAP>(span);
+    __shared__ uint32_t s_red[NW + 1];
+    __shared__ uint32_t s_below[2];
+    __shared__ uint32_t s_tot[2 * (NW + 1)];
+    uint32_t *cnt = cx.cnt();
+    uint32_t *mask = cx.mask();
 
-    // 1. seed flags (one bit per core hit): charge over threshold, or a hit
-    //    on another PMT of the same floor within tau.  A warp holds 32
-    //    consecutive hits; the two neighbours on each side come from the
-    //    adjacent lanes (edge lanes read them), a longer run within tau is
-    //    followed by a loop.  Packed keys carry time and PMT.
-    const uint32_t *pk = reinterpret_cast<const uint32_t *>(keys + CAP);
-    const uint32_t nwords = (ncore + 31) / 32;
-    for (uint32_t base = 0; base < ncore; base += NC) {
-        const uint32_t i = c0 + base + tid;
-        const bool in = i < c1;
-        // hits past the core (halo) are loaded too: they are neighbours
-        const uint32_t ki = i < n ? pk[i] : kPkNone;
-        const uint32_t ti = pk_t(ki), pi = pk_p(ki);
-        const uint32_t fi = in ? cx.floor_s()[pi] : 0u;
-        bool seed = in && key_q(keys[i]) >= qseed;
-        bool more_up = false, more_dn = false;
-        if (EXT && tp.seed_rule == 1) {
-            // the paper's combination of coincidences replaces the rule below
-            seed = in && coincidence_seed(pk, n, i, tp.rel, P, tp.sc_w, tp.fc_w, tp.afc_w);
-        } else {
+    // A. keys and bucket counts
+    uint32_t key[PER], cs[PER];           // packed key; charge << 16 | slot in the bucket
+    uint32_t below_lo = 0, below_hi = 0;
 #pragma unroll
-        for (uint32_t dd = 1; dd <= 2; ++dd) {
-            uint32_t ku = __shfl_up_sync(0xffffffffu, ki, dd);
-            uint32_t kd = __shfl_down_sync(0xffffffffu, ki, dd);
-            if (lane < dd) ku = (in && i >= dd) ? pk[i - dd] : kPkNone;
-            if (lane + dd >= 32) kd = (in && i + dd < n) ? pk[i + dd] : kPkNone;
-            if (in && i < dd) ku = kPkNone;
-            if (in && i + dd >= n) kd = kPkNone;
-            const bool near_u = ku != kPkNone && ti - pk_t(ku) <= tau;
-            const bool near_d = kd != kPkNone && pk_t(kd) - ti <= tau;
-            if (near_u && pk_p(ku) != pi && cx.floor_s()[pk_p(ku)] == fi) seed = true;
-            if (near_d && pk_p(kd) != pi && cx.floor_s()[pk_p(kd)] == fi) seed = true;
-            more_up = near_u;
-            more_dn = near_d;
+    for (int r = 0; r < PER; ++r) {
+        const uint32_t i = tid + r * NC;
+        key[r] = kPkNone;
+        cs[r] = 0;
+        if (i < n) {
+            const uint4 v = *reinterpret_cast<const uint4 *>(stage + 2 * i);
+            // t - tb in 32 bits (the staged range spans less than 2^20 ns)
+            const uint32_t tr = min(v.x - (uint32_t)tb, span - 1u);
+            key[r] = (tr << 12) | (v.z & 0xfffu);
+            const uint32_t slot = atomicAdd(&cnt[bucket_of<CAP>(tr, bsh)], 1u);
+            cs[r] = (v.z & 0xffff0000u) | slot;
+            below_lo += tr < lo_t;
+            below_hi += tr < hi_t;
         }
-        if (in && !seed && (more_up || more_dn)) {
-            // three or more hits within tau on one side: walk further
-            for (uint32_t j = i + 3; more_dn && j < n; ++j) {
-                const uint32_t kj = pk[j];
-                if (pk_t(kj) - ti > tau) break;
-                if (pk_p(kj) != pi && cx.floor_s()[pk_p(kj)] == fi) { seed = true; break; }
+    }
+    below_lo = __reduce_add_sync(0xffffffffu, below_lo);
+    below_hi = __reduce_add_sync(0xffffffffu, below_hi);
+    if (tid == 0) s_below[0] = s_below[1] = 0;
+    cons_sync<NC>();
+    if (lane == 0) {
+        if (below_lo) atomicAdd(&s_below[0], below_lo);
+        if (below_hi) atomicAdd(&s_below[1], below_hi);
+    }
+    // the stage buffer has been read: order those reads before the
+    // producer's next bulk copy into it, then hand it back
+    if (release_bar) fence_proxy_async_smem();
+
+    // B. bucket offsets (the scan's barriers also publish s_below and end
+    //    every read of the stage buffer)
+    cons_exclusive_scan<NC>(cnt, TileLayout<CAP>::NBK, s_red);
+    if (release_bar && tid == 0) mbar_arrive(release_bar);
+    const uint32_t c0 = s_below[0], c1 = s_below[1];
+
+    // C. bucket order, then the rank inside the bucket
+    uint32_t *pk_b = cx.pk_b(), *pk = cx.pk_s();
+    uint16_t *chg_b = cx.chg_b(), *chg = cx.chg_s();
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+        if (key[r] != kPkNone) {
+            const uint32_t pos = cnt[bucket_of<CAP>(key[r] >> 12, bsh)] + (cs[r] & 0xffffu);
+            if (CHECK(22, pos, CAP)) {
+                pk_b[pos] = key[r];
+                chg_b[pos] = (uint16_t)(cs[r] >> 16);
             }
-            for (uint32_t j = i - 2; more_up && !seed && j-- > 0;) {
-                const uint32_t kj = pk[j];
-                if (ti - pk_t(kj) > tau) break;
-                if (pk_p(kj) != pi && cx.floor_s()[pk_p(kj)] == fi) { seed = true; break; }
+        }
+    }
+    cons_sync<NC>();
+    const bool charge_rule = !(EXT && tp.seed_rule == 1);
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+        const uint32_t k = key[r];
+        if (k == kPkNone) continue;
+        const uint32_t b = bucket_of<CAP>(k >> 12, bsh);
+        const uint32_t s0 = cnt[b], s1 = cnt[b + 1], q = cs[r] >> 16, pos = s0 + (cs[r] & 0xffffu);
+        uint32_t rk = s0;
+        for (uint32_t m = s0; m < s1; ++m) {
+            const uint32_t o = pk_b[m];
+            rk += o < k;
+            if (o == k) {                          // equal time and PMT: charge, then position
+                const uint32_t oq = chg_b[m];
+                rk += oq < q || (oq == q && m < pos);
             }
         }
+        if (CHECK(23, rk, CAP)) {
+            pk[rk] = k;
+            chg[rk] = (uint16_t)q;
+            const uint32_t tr = k >> 12;
+            if (charge_rule && q >= tp.q_seed && tr >= lo_t && tr < hi_t) atomicOr(&mask[rk >> 5], 1u << (rk & 31u));
         }
-        // level 0 (N hits within TW) before the seed triggers count
-        if (EXT && tp.l0_hits && seed && in) seed = level0_pass(pk, n, i, tp.l0_hits, tp.l0_window, tp.l0_distinct != 0);
-        // halo hits past the core are neighbours only, never seeds here
-        const uint32_t m = __ballot_sync(0xffffffffu, seed && in);
-        if (lane == 0 && (base + warp * 32) < ncore) cx.mask()[(base + warp * 32) >> 5] = m;
     }
     cons_sync<NC>();
 
-    // 2. ordered seed list: warp w expands a contiguous group of mask words
-    const uint32_t wpw = (nwords + NW - 1) / NW;          // words per warp (<= 32)
-    uint32_t *wtot = red + 2;                             // [NW + 1]
+    // D. seed flags of the core keys [c0, c1)
+    const uint32_t P = cx.P;
+    if (EXT && tp.seed_rule == 1) {
+        for (uint32_t base = c0 & ~31u; base < c1; base += NC) {
+            const uint32_t i = base + tid;
+            const bool seed = i >= c0 && i < c1 && coincidence_seed(pk, n, i, tp.rel, P, tp.sc_w, tp.fc_w, tp.afc_w);
+            const uint32_t m = __ballot_sync(0xffffffffu, seed);
+            if (lane == 0 && m) atomicOr(&mask[(base >> 5) + warp], m);
+        }
+    } else {
+        // keys that can pair with a core key: [c0, c1) widened by tau on
+        // both sides, found by walking from the core's ends
+        const uint32_t tau = tp.tau;
+        const uint16_t *fl = cx.floor_s();
+        for (uint32_t base = 0; base < n; base += NC) {
+            const uint32_t i = base + tid;
+            bool mine = false;
+            if (i < n) {
+                const uint32_t ki = pk[i], ti = ki >> 12;
+                if (ti + tau >= lo_t && ti < hi_t + tau) {
+                    const uint32_t pi = ki & 0xfffu;
+                    const uint32_t fi = fl[pi];
+                    const bool ci = i >= c0 && i < c1;
+                    for (uint32_t j = i + 1; j < n; ++j) {
+                        const uint32_t kj = pk[j];
+                        if ((kj >> 12) - ti > tau) break;
+                        const uint32_t pj = kj & 0xfffu;
+                        if (pj != pi && fl[pj] == fi) {
+                            mine |= ci;
+                            if (j >= c0 && j < c1) atomicOr(&mask[j >> 5], 1u << (j & 31u));
+                        }
+                    }
+                }
+            }
+            const uint32_t m = __ballot_sync(0xffffffffu, mine);
+            if (lane == 0 && m) atomicOr(&mask[(base >> 5) + warp], m);
+        }
+    }
+    cons_sync<NC>();
+    if (EXT && tp.l0_hits) {
+        // level 0 (N hits within TW) before the seed triggers count
+        for (uint32_t base = c0 & ~31u; base < c1; base += NC) {
+            const uint32_t i = base + tid;
+            const uint32_t w = (i >= c0 && i < c1) ? mask[i >> 5] : 0u;
+            const bool drop = ((w >> (i & 31u)) & 1u) &&
+                              !level0_pass(pk, n, i, tp.l0_hits, tp.l0_window, tp.l0_distinct != 0);
+            const uint32_t m = __ballot_sync(0xffffffffu, drop);
+            if (lane == 0 && m) atomicAnd(&mask[(base >> 5) + warp], ~m);
+        }
+        cons_sync<NC>();
+    }
+
+    // E. ordered seed list: warp w expands a contiguous group of mask words
+    uint16_t *seed_idx = cx.seed_idx(), *seed_cnt = cx.seed_cnt();
+    const uint32_t w_lo = c0 >> 5, w_hi = (c1 + 31) >> 5;
+    const uint32_t nwords = w_hi - w_lo;
+    const uint32_t wpw = (nwords + NW - 1) / NW;          // words per warp (<= CAP / 32 / NW)
+    uint32_t *wtot = s_tot;                               // [NW + 1]
     {
-        const uint32_t w = warp * wpw + lane;
-        const uint32_t m = (lane < wpw && w < nwords) ? cx.mask()[w] : 0u;
-        const uint32_t pc = __popc(m);
-        const uint32_t incl = warp_incl_scan(pc);
-        if (lane == 31) wtot[warp] = incl;
+        uint32_t pc = 0;
+        for (uint32_t x = 0; x < wpw; x += 32) {
+            const uint32_t w = w_lo + warp * wpw + x + lane;
+            if (x + lane < wpw && w < w_hi) pc += __popc(mask[w]);
+        }
+        pc = __reduce_add_sync(0xffffffffu, pc);
+        if (lane == 0) wtot[warp] = pc;
         cons_sync<NC>();
         if (warp == 0) {
-            uint32_t v = lane < NW ? wtot[lane] : 0u;
-            uint32_t vi = warp_incl_scan(v);
+            const uint32_t v = lane < NW ? wtot[lane] : 0u;
+            const uint32_t vi = warp_incl_scan(v);
             if (lane < NW) wtot[lane] = vi - v;
             if (lane == NW - 1) wtot[NW] = vi;
         }
         cons_sync<NC>();
-        uint32_t pos = wtot[warp] + incl - pc;
-        uint32_t mm = m;
-        while (mm) {
-            const uint32_t bit = __ffs(mm) - 1;
-            mm &= mm - 1;
-            if (CHECK(2, pos, CAP)) seed_idx[pos] = (uint16_t)(c0 + w * 32 + bit);
-            ++pos;
+        uint32_t pos = wtot[warp];
+        for (uint32_t x = 0; x < wpw; x += 32) {
+            const uint32_t w = w_lo + warp * wpw + x + lane;
+            const uint32_t m = (x + lane < wpw && w < w_hi) ? mask[w] : 0u;
+            const uint32_t c = __popc(m);
+            const uint32_t incl = warp_incl_scan(c);
+            uint32_t at = pos + incl - c;
+            uint32_t mm = m;
+            while (mm) {
+                const uint32_t bit = __ffs(mm) - 1;
+                mm &= mm - 1;
+                if (CHECK(2, at, CAP)) seed_idx[at] = (uint16_t)(w * 32 + bit);
+                ++at;
+            }
+            pos += __shfl_sync(0xffffffffu, incl, 31);
         }
     }
     const uint32_t ns = wtot[NW];
     cons_sync<NC>();
 
-    // 3. causal count c(s) over each seed's scan range (count_causal), or
-    //    its distinct-PMT form
+    // F. causal count c(s) over each seed's scan range, or its distinct-PMT
+    //    form (sparse batches give each seed 4 lanes, dense ones a warp)
     if (EXT && tp.count_distinct) {
         count_distinct_pmts<CAP, NC, SMEM_DT>(cx, pk, n, ns, seed_idx, bsh, seed_cnt);
     } else {
-        // sparse batches give each seed 4 lanes (a few dozen keys each, the
-        // per-seed setup amortised), dense ones a whole warp (hundreds of
-        // keys, conflict-free contiguous loads); one size per build keeps
-        // a single count loop in the kernel
         count_causal<CAP, NC, SMEM_DT, DENSE ? 5u : 2u>(cx, pk, n, ns, seed_idx, bsh, seed_cnt);
     }
     cons_sync<NC>();
 
-    // 4. emit fired seeds in order: warp w takes a contiguous range of the
-    //    seed list, warps count theirs, a scan of the warp totals gives each
-    //    warp its output offset
+    // G. emit the fired seeds in order: warp w takes a contiguous range of
+    //    the seed list, a scan of the warp totals gives its output offset
+    const uint32_t threshold = tp.threshold;
     const uint32_t per_w = (ns + NW - 1) / NW;
     const uint32_t k_begin = min(ns, warp * per_w), k_end = min(ns, k_begin + per_w);
     uint32_t my_f = 0;
@@ -1163,16 +1237,17 @@ __device__ CoreOut tile_trigger(TileCtx<CAP> &cx, const uint64_t *keys, uint32_t
         const uint32_t k = k0 + lane;
         my_f += __popc(__ballot_sync(0xffffffffu, k < k_end && seed_cnt[k] >= threshold));
     }
-    uint32_t *ftot = red + 2 + (NW + 1);                  // [NW + 1]
+    uint32_t *ftot = s_tot + (NW + 1);                    // [NW + 1]
     if (lane == 0) ftot[warp] = my_f;
     cons_sync<NC>();
     if (warp == 0) {
-        uint32_t v = lane < NW ? ftot[lane] : 0u;
-        uint32_t vi = warp_incl_scan(v);
+        const uint32_t v = lane < NW ? ftot[lane] : 0u;
+        const uint32_t vi = warp_incl_scan(v);
         if (lane < NW) ftot[lane] = vi - v;
         if (lane == NW - 1) ftot[NW] = vi;
     }
     cons_sync<NC>();
+    trig_trigger *dst = out + (out_at_c0 ? c0 : 0u);
     {
         uint32_t F = ftot[warp];
         for (uint32_t k0 = k_begin; k0 < k_end; k0 += 32) {
@@ -1180,31 +1255,32 @@ __device__ CoreOut tile_trigger(TileCtx<CAP> &cx, const uint64_t *keys, uint32_t
             const bool fired = k < k_end && seed_cnt[k] >= threshold;
             const uint32_t m = __ballot_sync(0xffffffffu, fired);
             if (fired) {
-                const uint64_t ks = keys[seed_idx[k]];
+                const uint32_t i = seed_idx[k];
+                const uint32_t ks = pk[i];
                 trig_trigger tr;
-                tr.t_ns = tb + (int64_t)key_t(ks);
-                tr.pmt = (uint16_t)key_p(ks);
-                tr.charge = (uint16_t)key_q(ks);
+                tr.t_ns = tb + (int64_t)(ks >> 12);
+                tr.pmt = (uint16_t)(ks & 0xfffu);
+                tr.charge = chg[i];
                 tr.count = seed_cnt[k];
                 const uint32_t o_ = F + __popc(m & ((1u << lane) - 1u));
-                if (CHECK(3, o_, ncore)) out[o_] = tr;
+                if (CHECK(3, o_, c1 - c0)) dst[o_] = tr;
             }
             F += __popc(m);
         }
     }
     const uint32_t n_fired = ftot[NW];
-    // 5. optional row outputs: the merged core rows (verification, and the
-    //    merged stream of event extraction) and each row's causal count
-    //    (verification only)
+    // optional row outputs: the merged core rows (verification, and the
+    // merged stream of event extraction) and each row's causal count
+    // (verification only); rows are indexed by merged rank minus the rank
+    // of the slice's first owned hit
     if (tp.dbg_merged) {
-        // rows are indexed by merged rank minus the rank of the slice's first owned hit
         const uint64_t dbg_base = (uint64_t)(dbg_rank_lo + (int64_t)c0);
-        for (uint32_t i = tid; i < ncore; i += NC) {
-            uint64_t k = keys[c0 + i];
+        for (uint32_t i = tid; i < c1 - c0; i += NC) {
+            const uint32_t k = pk[c0 + i];
             trig_hit h;
-            h.t_ns = tb + (int64_t)key_t(k);
-            h.pmt = (uint16_t)key_p(k);
-            h.charge = (uint16_t)key_q(k);
+            h.t_ns = tb + (int64_t)(k >> 12);
+            h.pmt = (uint16_t)(k & 0xfffu);
+            h.charge = chg[c0 + i];
             h.reserved = 0;
             tp.dbg_merged[dbg_base + i] = h;
             if (tp.dbg_seedcnt) tp.dbg_seedcnt[dbg_base + i] = 0xffffffffu;
@@ -1214,12 +1290,15 @@ __device__ CoreOut tile_trigger(TileCtx<CAP> &cx, const uint64_t *keys, uint32_t
             for (uint32_t k = tid; k < ns; k += NC) tp.dbg_seedcnt[dbg_base + (seed_idx[k] - c0)] = seed_cnt[k];
         }
     }
+    // leave the bucket counts and the seed mask zero for the next tile
+    for (uint32_t i = tid; i < (uint32_t)TileLayout<CAP>::NBK; i += NC) cnt[i] = 0;
+    for (uint32_t w = w_lo + tid; w < w_hi; w += NC) mask[w] = 0;
     cons_sync<NC>();
-    CoreOut r;
-    r.n_fired = n_fired;
-    r.n_seeds = ns;
-    r.c0 = c0;
-    return r;
+    CoreOut co;
+    co.n_fired = n_fired;
+    co.n_seeds = ns;
+    co.c0 = c0;
+    return co;
 }
 
 // Overflow path: the tile holds more than CAP hits with its halo.  Split
@@ -1337,12 +1416,10 @@ __device__ void tile_overflow(TileCtx<CAP> &cx, uint64_t *buf, const SliceDesc &
         cons_sync<NC>();
         const int64_t tb = lo - (int64_t)H;
         const uint32_t span = (uint32_t)(hi - lo) + 2 * H;
-        const uint32_t bsh = tile_sort<CAP, NC>(cx, buf, total, tb, span, red + 64, H, H + (uint32_t)(hi - lo));
-        const uint32_t c0 = red[64 + NW + 1], c1 = red[64 + NW + 2];
         const uint32_t fired0 = red[5];
-        CoreOut co = tile_trigger<CAP, NC, SMEM_DT, EXT, DENSE>(cx, buf, total, bsh, c0, c1, tb, tp,
-                                                     d.stage + tile_rank + fired0,
-                                                     (int64_t)rank_lo - (int64_t)d.dbg_rank0, red + 64);
+        CoreOut co = tile_pass<CAP, NC, SMEM_DT, EXT, DENSE>(cx, buf, total, tb, span, H, H + (uint32_t)(hi - lo), tp,
+                                                             d.stage + tile_rank + fired0, false,
+                                                             (int64_t)rank_lo - (int64_t)d.dbg_rank0, nullptr);
         if (tid == 0) {
             red[5] = fired0 + co.n_fired;
             red[6] += co.n_seeds;
@@ -1363,6 +1440,7 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 
                                                                           uint32_t max_pmt)
 {
     constexpr uint32_t NW = NC / 32;
+    constexpr uint32_t NSTG = TileLayout<CAP>::NS;
     __shared__ uint64_t full_bar[2], empty_bar[2];
     __shared__ ItemInfo info[2];
     __shared__ __align__(16) uint32_t red[64 + 64];
@@ -1384,8 +1462,12 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 
     __syncthreads();
 
     const uint32_t n_slices = hdr->n_slices, n_items = hdr->n_items;
+    const uint64_t wait_ns = hdr->wait_ns;
 
     if (warp == NW) {
+        // test control: stage nothing, so that the consumers' first wait
+        // runs out (no copy is ever in flight)
+        if (hdr->stall) return;
         // ------------------------------------------------ producer warp
         // The next item is dequeued and its per-PMT runs looked up before
         // waiting for a free buffer, so those global loads overlap the wait.
@@ -1397,7 +1479,7 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 
         if (lane == 0) item = atomicAdd(&hdr->queue, 1u);
         item = __shfl_sync(0xffffffffu, item, 0);
         for (uint32_t it = 0;; ++it) {
-            const uint32_t b = it & 1u, use = it >> 1;
+            const uint32_t b = it % NSTG, use = it / NSTG;
             uint32_t g = 0, P = 0, mode = 2, lo_t = 0, span = 0;
             uint64_t ra[R];
             uint32_t rl[R];
@@ -1463,7 +1545,7 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 
                 if (lane == 0) next = atomicAdd(&hdr->queue, 1u);
                 next = __shfl_sync(0xffffffffu, next, 0);
             }
-            if (it >= 2 && !mbar_wait(&empty_bar[b], (use - 1) & 1u)) {
+            if (it >= NSTG && !mbar_wait(&empty_bar[b], (use - 1) & 1u, wait_ns)) {
                 if (lane == 0) atomicOr(&hdr->err, TRIG_FLAG_TIMEOUT);
                 break;
             }
@@ -1508,6 +1590,10 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 
     }
 
     // ---------------------------------------------------- consumer warps
+    // the tile pass expects zero bucket counts and seed mask (and leaves them so)
+    for (uint32_t i = tid; i < (uint32_t)TileLayout<CAP>::NBK; i += NC) cx.cnt()[i] = 0;
+    for (uint32_t i = tid; i < (uint32_t)CAP / 32; i += NC) cx.mask()[i] = 0;
+    cons_sync<NC>();
     const SliceDesc *loaded = nullptr;
     // the slice's trigger parameters live in shared memory (written by one
     // thread when the slice changes), keeping registers for the tile phases
@@ -1516,8 +1602,8 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 
     // owned hit, also kept in shared memory
     __shared__ int64_t sl[4];
     for (uint32_t it = 0;; ++it) {
-        const uint32_t b = it & 1u, use = it >> 1;
-        if (!mbar_wait(&full_bar[b], use & 1u)) {
+        const uint32_t b = it % NSTG, use = it / NSTG;
+        if (!mbar_wait(&full_bar[b], use & 1u, wait_ns)) {
             if (tid == 0) atomicOr(&hdr->err, TRIG_FLAG_TIMEOUT);
             break;
         }
@@ -1571,24 +1657,26 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 
             tile_overflow<CAP, NC, SMEM_DT, EXT, DENSE>(cx, cx.stage(b), d, tp, inf.g, red, stk);
         } else {
             const int64_t W = sl[0];
-            const int64_t Bg = sl[1] + (int64_t)inf.g * W;
+            const uint32_t g = inf.g, n_st = inf.n, rank_lo = inf.rank_lo, span = inf.span;
+            const int64_t Bg = sl[1] + (int64_t)g * W;
             const int64_t core_end = min(Bg + W, sl[1] + sl[2]);
             // the staged range starts lo_t (>= H) before the core
             const uint32_t lo_t = inf.lo_t;
             const int64_t tb = Bg - (int64_t)lo_t;
             const uint32_t hi_t = lo_t + (uint32_t)(core_end - Bg);
-            const uint32_t bsh = tile_sort<CAP, NC>(cx, cx.stage(b), inf.n, tb, inf.span, red, lo_t, hi_t);
-            // rank of the core's first hit = rank_lo + c0, known after the sort
-            const uint32_t c0 = red[NW + 1], c1 = red[NW + 2];
-            const uint32_t tile_rank = inf.rank_lo + c0;
-            CoreOut co = tile_trigger<CAP, NC, SMEM_DT, EXT, DENSE>(cx, cx.stage(b), inf.n, bsh, c0, c1, tb, tp,
-                                                         d.stage + tile_rank, (int64_t)inf.rank_lo - sl[3],
-                                                         red);
-            if (tid == 0 && CHECK(14, (uint64_t)tile_rank + co.n_fired, d.n_hits + 1) && CHECK(15, inf.g, d.n_tiles)) {
-                d.tile_nfired[inf.g] = co.n_fired;
-                d.tile_rank[inf.g] = tile_rank;
+            // the pass hands the buffer back as soon as it has read it (inf
+            // is not read after that); the core's first hit has merged rank
+            // rank_lo + c0
+            CoreOut co = tile_pass<CAP, NC, SMEM_DT, EXT, DENSE>(cx, cx.stage(b), n_st, tb, span, lo_t, hi_t, tp,
+                                                                 d.stage + rank_lo, true,
+                                                                 (int64_t)rank_lo - sl[3], &empty_bar[b]);
+            const uint32_t tile_rank = rank_lo + co.c0;
+            if (tid == 0 && CHECK(14, (uint64_t)tile_rank + co.n_fired, d.n_hits + 1) && CHECK(15, g, d.n_tiles)) {
+                d.tile_nfired[g] = co.n_fired;
+                d.tile_rank[g] = tile_rank;
                 atomicAdd(reinterpret_cast<unsigned long long *>(&d.stats->n_seeds), (unsigned long long)co.n_seeds);
             }
+            continue;
         }
         // release the buffer to the producer: order our generic-proxy
         // accesses before its next bulk copy into the same buffer
@@ -1630,6 +1718,7 @@ __device__ unsigned long long block_scan_u32(const uint32_t *vals, uint32_t *out
 
 __global__ void __launch_bounds__(1024) k_scan(const BatchHeader *__restrict__ hdr, const SliceDesc *__restrict__ desc)
 {
+    if (hdr->err) return;           // the tile pass gave up: its per-tile outputs are not valid
     __shared__ uint32_t wsum[32];
     __shared__ unsigned long long carry;
     for (uint32_t s = blockIdx.x; s < hdr->n_slices; s += gridDim.x) {
@@ -1662,6 +1751,7 @@ __device__ __forceinline__ uint32_t find_tile_of_pos(const uint32_t *tile_out, u
 
 __global__ void __launch_bounds__(256) k_copy(const BatchHeader *__restrict__ hdr, const SliceDesc *__restrict__ desc)
 {
+    if (hdr->err) return;           // the tile pass gave up: its per-tile outputs are not valid
     const uint32_t n_items = hdr->n_items, n_slices = hdr->n_slices;
     const uint32_t lane = lane_id();
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -1708,6 +1798,7 @@ __global__ void __launch_bounds__(256) k_copy(const BatchHeader *__restrict__ hd
 
 __global__ void __launch_bounds__(1024) k_wscan(const BatchHeader *__restrict__ hdr, const SliceDesc *__restrict__ desc)
 {
+    if (hdr->err) return;           // the tile pass gave up: its per-tile outputs are not valid
     __shared__ uint32_t wsum[32];
     __shared__ unsigned long long carry;
     for (uint32_t s = blockIdx.x; s < hdr->n_slices; s += gridDim.x) {
@@ -1728,6 +1819,7 @@ __global__ void __launch_bounds__(1024) k_wscan(const BatchHeader *__restrict__ 
 // tails (the next trigger is a head, or none follows) write hi and the last.
 __global__ void __launch_bounds__(256) k_wwrite(const BatchHeader *__restrict__ hdr, const SliceDesc *__restrict__ desc)
 {
+    if (hdr->err) return;           // the tile pass gave up: its per-tile outputs are not valid
     const uint32_t n_items = hdr->n_items, n_slices = hdr->n_slices;
     const uint32_t lane = lane_id();
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -1796,6 +1888,7 @@ __device__ __forceinline__ uint64_t rank_in_pmt(const SliceDesc &d, uint32_t p, 
 // (lanes take PMTs); the window's slice comes from a prefix over slices.
 __global__ void __launch_bounds__(256) k_whits(const BatchHeader *__restrict__ hdr, const SliceDesc *__restrict__ desc)
 {
+    if (hdr->err) return;           // the tile pass gave up: its per-tile outputs are not valid
     __shared__ unsigned long long pre[1025];
     const uint32_t lane = lane_id();
     const uint32_t n_slices = hdr->n_slices;
@@ -1863,6 +1956,7 @@ __global__ void __launch_bounds__(256) k_whits(const BatchHeader *__restrict__ h
 // the edge bucket of a wide slice.  A warp per window, as k_whits.
 __global__ void __launch_bounds__(256) k_wrank(const BatchHeader *__restrict__ hdr, const SliceDesc *__restrict__ desc)
 {
+    if (hdr->err) return;           // the tile pass gave up: its per-tile outputs are not valid
     const uint32_t lane = lane_id();
     const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarp = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -1961,6 +2055,7 @@ __device__ void ev_halo_side(const SliceDesc &d, bool lead, uint64_t *keys, uint
 __global__ void __launch_bounds__(kEvHaloThreads) k_evhalo(const BatchHeader *__restrict__ hdr,
                                                            const SliceDesc *__restrict__ desc)
 {
+    if (hdr->err) return;           // the tile pass gave up: its per-tile outputs are not valid
     extern __shared__ __align__(16) unsigned char ev_smem[];
     uint64_t *keys = reinterpret_cast<uint64_t *>(ev_smem);
     uint32_t *psum = reinterpret_cast<uint32_t *>(keys + TRIG_EV_HALO_MAX);
@@ -1977,6 +2072,7 @@ __global__ void __launch_bounds__(kEvHaloThreads) k_evhalo(const BatchHeader *__
 // counts (one block per slice); the total is n_events.
 __global__ void __launch_bounds__(1024) k_escan(const BatchHeader *__restrict__ hdr, const SliceDesc *__restrict__ desc)
 {
+    if (hdr->err) return;           // the tile pass gave up: its per-tile outputs are not valid
     __shared__ uint32_t wsum[33];
     const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5, nwp = blockDim.x >> 5;
     for (uint32_t s = blockIdx.x; s < hdr->n_slices; s += gridDim.x) {
@@ -2020,6 +2116,7 @@ __global__ void __launch_bounds__(1024) k_escan(const BatchHeader *__restrict__ 
 // piece, whose rows the merged stream lacks) copy nothing.
 __global__ void __launch_bounds__(256) k_events(const BatchHeader *__restrict__ hdr, const SliceDesc *__restrict__ desc)
 {
+    if (hdr->err) return;           // the tile pass gave up: its per-tile outputs are not valid
     const uint64_t gt = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
     for (uint32_t s = 0; s < hdr->n_slices; ++s) {
@@ -2074,6 +2171,64 @@ __global__ void k_rank0(const BatchHeader *__restrict__ hdr, SliceDesc *__restri
         d.dbg_rank0 = acc;
         d.dbg_rank1 = acc1;
     }
+}
+
+// -------------------------------------------------------------- k_prepend
+
+// Largest p in [0, P) with off[p] <= x, for non-decreasing offsets with
+// off[0] = 0 <= x < off[P].
+__device__ __forceinline__ uint32_t run_of(const uint64_t *off, uint32_t P, uint64_t x)
+{
+    uint32_t lo = 0, hi = P;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (off[mid] <= x) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// A continuation submission ("Preparation in CPU": at the end of a slice the
+// trigger proceeds on the first hits of the next one; here the next slice
+// starts on the last hits of the previous one): PMT p's stream of the
+// combined slice is the detector's resident tail of p followed by the
+// submission's hits of p.  Tail hit j of PMT p lands at j + fresh_off[p],
+// fresh hit i at i + tail_off[p + 1]; the combined offsets are the sums.
+__global__ void k_prepend(const trig_hit *__restrict__ tail, const uint64_t *__restrict__ tail_off, uint64_t n_tail,
+                          const trig_hit *__restrict__ fresh, const uint64_t *__restrict__ fresh_off,
+                          uint64_t n_fresh, uint32_t P, trig_hit *__restrict__ out, uint64_t *__restrict__ out_off)
+{
+    const uint64_t n = n_tail + n_fresh, total = n + P + 1;
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total;
+         x += (uint64_t)gridDim.x * blockDim.x) {
+        if (x >= n) {
+            const uint64_t q = x - n;
+            out_off[q] = tail_off[q] + fresh_off[q];
+            continue;
+        }
+        const trig_hit *src;
+        uint64_t dst;
+        if (x < n_tail) {
+            const uint32_t p = run_of(tail_off, P, x);
+            src = tail + x;
+            dst = x + fresh_off[p];
+        } else {
+            const uint64_t i = x - n_tail;
+            const uint32_t p = run_of(fresh_off, P, i);
+            src = fresh + i;
+            dst = i + tail_off[p + 1];
+        }
+        if (CHECK(21, dst, n)) *reinterpret_cast<int4 *>(out + dst) = *reinterpret_cast<const int4 *>(src);
+    }
+}
+
+cudaError_t launch_prepend(const trig_hit *tail, const uint64_t *tail_off, uint64_t n_tail, const trig_hit *fresh,
+                           const uint64_t *fresh_off, uint64_t n_fresh, uint32_t P, trig_hit *out, uint64_t *out_off,
+                           cudaStream_t st)
+{
+    const uint64_t total = n_tail + n_fresh + P + 1;
+    const uint64_t blocks = std::min<uint64_t>((total + 255) / 256, (uint64_t)device_sm_count() * 16);
+    k_prepend<<<(unsigned)blocks, 256, 0, st>>>(tail, tail_off, n_tail, fresh, fresh_off, n_fresh, P, out, out_off);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- k_status
@@ -2138,6 +2293,27 @@ cudaError_t static_scratch(void **ptr, size_t *bytes)
     *ptr = addr[dev];
     *bytes = sizeof(g_noalloc_scratch);
     return cudaSuccess;
+}
+
+// ------------------------------------------------- no-allocation upload
+
+// The batch header and descriptors of trig_batch_run_noalloc travel as the
+// kernel's parameter (copied at launch), so nothing is read from host memory
+// after the call returns and no copy waits on the caller's stream.
+__global__ void k_put_plan(const NoallocPlan plan, BatchHeader *hdr, SliceDesc *desc)
+{
+    const uint32_t nw_hdr = sizeof(BatchHeader) / 4;
+    const uint32_t nw_desc = plan.n * (uint32_t)(sizeof(SliceDesc) / 4);
+    const uint32_t *src_h = reinterpret_cast<const uint32_t *>(&plan.hdr);
+    const uint32_t *src_d = reinterpret_cast<const uint32_t *>(plan.desc);
+    for (uint32_t i = threadIdx.x; i < nw_hdr; i += blockDim.x) reinterpret_cast<uint32_t *>(hdr)[i] = src_h[i];
+    for (uint32_t i = threadIdx.x; i < nw_desc; i += blockDim.x) reinterpret_cast<uint32_t *>(desc)[i] = src_d[i];
+}
+
+cudaError_t launch_put_plan(const NoallocPlan &plan, BatchHeader *hdr, SliceDesc *desc, cudaStream_t st)
+{
+    k_put_plan<<<1, 256, 0, st>>>(plan, hdr, desc);
+    return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ launch

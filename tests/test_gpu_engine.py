@@ -69,8 +69,10 @@ def test_engine_from_page_locked_buffers(pkg, params):
 
 
 def test_engine_alone_equals_in_mix(pkg, params):
-    """Four detectors (32, 84, 84, 2688 PMTs) submitted interleaved share
-    batches; each result equals the same slice run alone (tolerance 0)."""
+    """Four detectors (32, 84, 84, 2688 PMTs) submitted interleaved while the
+    engine holds admission, so that they share one batch: each result
+    equals the same slice run alone (tolerance 0), and every detector's
+    results equal the oracle."""
     wl = workload.cfg_serving_pool(slices_per_det=2)
     dets = [pkg.Detector(g.xyz_mm, g.floor_id, params) for g in wl.detectors]
     pkg.trig_engine_set_mode(1)
@@ -79,40 +81,114 @@ def test_engine_alone_equals_in_mix(pkg, params):
     for i, s in enumerate(wl.submissions):
         pkg.trig_submit_slice(dets[s.det_index], s.t0, s.stream.hits, s.stream.pmt_off)
         alone[i] = pkg.trig_poll(dets[s.det_index], 60_000)
-    # mixed: everything at once
-    order = list(range(len(wl.submissions)))
+    # mixed: everything interleaved, admitted at once
     rng = np.random.Generator(np.random.PCG64(4))
     by_det = {}
-    for i in order:
+    for i in range(len(wl.submissions)):
         by_det.setdefault(wl.submissions[i].det_index, []).append(i)
     seq = []
     while any(by_det.values()):
         d = int(rng.choice([k for k, v in by_det.items() if v]))
         seq.append(by_det[d].pop(0))
-    for i in seq:
-        s = wl.submissions[i]
-        pkg.trig_submit_slice(dets[s.det_index], s.t0, s.stream.hits, s.stream.pmt_off)
+    b0, s0 = pkg.trig_engine_stats()
+    pkg.trig_engine_hold(True)
+    try:
+        for i in seq:
+            s = wl.submissions[i]
+            pkg.trig_submit_slice(dets[s.det_index], s.t0, s.stream.hits, s.stream.pmt_off)
+    finally:
+        pkg.trig_engine_hold(False)
     mixed = {}
-    for i in seq:
-        pass
     for d_index, det in enumerate(dets):
         for i in [j for j in range(len(wl.submissions)) if wl.submissions[j].det_index == d_index]:
             mixed[i] = pkg.trig_poll(det, 120_000)
+    b1, s1 = pkg.trig_engine_stats()
+    assert s1 - s0 == len(seq)
+    assert b1 - b0 == 1, (b1 - b0, s1 - s0)           # one batch held every detector's slices
     for i in alone:
         a, m = alone[i], mixed[i]
         assert a.status == 0 and m.status == 0
         assert a.n_seeds == m.n_seeds
         assert np.array_equal(a.triggers, m.triggers)
         assert np.array_equal(a.windows, m.windows)
-    # and one detector against the oracle
-    k = 1
-    g = wl.detectors[k]
-    ref = oracle.run(g.xyz_mm, g.floor_id, params, wl.runs[k].hits, wl.run_slices[k])
-    idx = [j for j in range(len(wl.submissions)) if wl.submissions[j].det_index == k]
-    for r_i, j in enumerate(idx):
-        _same(mixed[j], ref[r_i], f"det {k} slice {r_i}")
+    # every detector against the oracle
+    for k, g in enumerate(wl.detectors):
+        ref = oracle.run(g.xyz_mm, g.floor_id, params, wl.runs[k].hits, wl.run_slices[k], threads=0)
+        idx = [j for j in range(len(wl.submissions)) if wl.submissions[j].det_index == k]
+        assert len(idx) == len(ref) == 2
+        for r_i, j in enumerate(idx):
+            _same(mixed[j], ref[r_i], f"det {k} ({g.n_pmt} PMTs) slice {r_i}")
     for d in dets:
         d.close()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_engine_continuation_matches_oracle(pkg, params, mode):
+    """Contiguous slices of two detectors, interleaved: the first slice of
+    each run carries both halos, the later ones start at t0 and ask the
+    library for the leading halo it kept on the device
+    (is_continuation = 1).  Every result equals the oracle on the whole
+    run."""
+    pkg.trig_engine_set_mode(mode)
+    wl = workload.cfg_serving_pool(slices_per_det=4, dets=[("nemo", 120e3), ("km3", 55e3)])
+    dets = [pkg.Detector(g.xyz_mm, g.floor_id, params) for g in wl.detectors]
+    halo = dets[0].halo_ns
+    S = params["slice_ns"]
+    order = []
+    for k in range(4):
+        for d in (0, 1):
+            order.append((d, k))
+    for d, k in order:
+        t0 = wl.run_slices[d][k]
+        if k == 0:
+            st = workload.cut(wl.runs[d], t0 - halo, t0 + S + halo)
+            pkg.trig_submit_slice(dets[d], t0, st.hits, st.pmt_off)
+        else:
+            st = workload.cut(wl.runs[d], t0, t0 + S + halo)
+            pkg.trig_submit_slice(dets[d], t0, st.hits, st.pmt_off, is_continuation=1)
+    for d, g in enumerate(wl.detectors):
+        ref = oracle.run(g.xyz_mm, g.floor_id, params, wl.runs[d].hits, wl.run_slices[d], threads=0)
+        for k in range(4):
+            r = pkg.trig_poll(dets[d], 60_000)
+            assert r is not None
+            _same(r, ref[k], f"mode {mode} det {d} slice {k}")
+            want_hits = int(np.count_nonzero((wl.runs[d].hits["t"] >= wl.run_slices[d][k] - halo) &
+                                             (wl.runs[d].hits["t"] < wl.run_slices[d][k] + S + halo)))
+            assert r.n_hits == want_hits
+    for det in dets:
+        det.close()
+    pkg.trig_engine_set_mode(1)
+
+
+def test_engine_continuation_refused(pkg, params):
+    """A continuation needs a previous submission of the detector, the next
+    t0, and no hit before t0; each case is refused (EINVAL) and leaves the
+    resident tail usable."""
+    wl = workload.cfg_serving_pool(slices_per_det=3, dets=[("nemo", 80e3)])
+    g = wl.detectors[0]
+    det = pkg.Detector(g.xyz_mm, g.floor_id, params)
+    halo, S = det.halo_ns, params["slice_ns"]
+    t0s = wl.run_slices[0]
+    full = wl.runs[0]
+    st1 = workload.cut(full, t0s[1], t0s[1] + S + halo)
+    with pytest.raises(pkg.TrigError) as e:                  # nothing submitted yet
+        pkg.trig_submit_slice(det, t0s[1], st1.hits, st1.pmt_off, is_continuation=1)
+    assert e.value.code == pkg.TRIG_EINVAL
+    st0 = workload.cut(full, t0s[0] - halo, t0s[0] + S + halo)
+    pkg.trig_submit_slice(det, t0s[0], st0.hits, st0.pmt_off)
+    st2 = workload.cut(full, t0s[2], t0s[2] + S + halo)
+    with pytest.raises(pkg.TrigError) as e:                  # not the next slice
+        pkg.trig_submit_slice(det, t0s[2], st2.hits, st2.pmt_off, is_continuation=1)
+    assert e.value.code == pkg.TRIG_EINVAL
+    with_halo = workload.cut(full, t0s[1] - halo, t0s[1] + S + halo)
+    with pytest.raises(pkg.TrigError) as e:                  # carries its own leading halo
+        pkg.trig_submit_slice(det, t0s[1], with_halo.hits, with_halo.pmt_off, is_continuation=1)
+    assert e.value.code == pkg.TRIG_EINVAL
+    pkg.trig_submit_slice(det, t0s[1], st1.hits, st1.pmt_off, is_continuation=1)
+    ref = oracle.run(g.xyz_mm, g.floor_id, params, full.hits, t0s[:2])
+    for k in range(2):
+        _same(pkg.trig_poll(det, 60_000), ref[k], f"slice {k}")
+    det.close()
 
 
 def test_engine_rejects_bad_offsets(pkg, params):

@@ -196,28 +196,37 @@ def test_scaled_array_config(pkg, params):
     d.close()
 
 
-def test_batched_config_sampled(pkg, params):
-    """All 64 slices in one launch; 8 of them checked in full against the
-    oracle, the rest by invariants (status, monotone counts, windows)."""
+def _oracle_each(jobs, threads=None):
+    """oracle.run on independent (geometry, hits, t0) jobs, one slice per
+    call, spread over the host cores (the oracle's C code runs without the
+    interpreter lock)."""
+    from concurrent.futures import ThreadPoolExecutor
+    import oracle as orc
+
+    def one(job):
+        g, par, hits, t0 = job
+        return orc.run(g.xyz_mm, g.floor_id, par, hits, [t0], threads=1)[0]
+
+    with ThreadPoolExecutor(threads or os.cpu_count() or 4) as ex:
+        return list(ex.map(one, jobs))
+
+
+def test_batched_config_all_slices(pkg, params):
+    """The headline workload: all 64 slices in one launch sequence (graph
+    replay), every slice compared with the oracle element by element.  The
+    slices are independent runs (no halos), so each gets its own oracle
+    call."""
     wl = workload.cfg_batched()
     dets = [_det(pkg, g, params) for g in wl.detectors]
-    subs = [(s.t0, s.stream) for s in wl.submissions]
     from paper_1411_3968_gb300.runner import DeviceBatch, SliceIn
     b = DeviceBatch([SliceIn(dets[s.det_index], s.t0, s.stream.hits, s.stream.pmt_off) for s in wl.submissions])
     b.run(graph=True)
+    b.run(graph=True)                   # the replay, as the bench times it
     res = b.results()
-    pick = [0, 7, 13, 21, 30, 42, 55, 63]
-    for k in pick:
-        s = wl.submissions[k]
-        g = wl.detectors[s.det_index]
-        ref = oracle.run(g.xyz_mm, g.floor_id, params, s.stream.hits, [s.t0])[0]
-        _assert_same(res[k], ref, f"batched slice {k}")
-    for k, (stats, trig, win) in enumerate(res):
-        assert int(stats["status"]) == 0
-        assert np.all(np.diff(trig["t"]) >= 0)
-        assert np.all(trig["count"] >= params["threshold"])
-        assert int(win["n_triggers"].sum()) == len(trig)
-        assert np.all(win["lo"][1:] > win["hi"][:-1] + 1)
+    refs = _oracle_each([(wl.detectors[s.det_index], params, s.stream.hits, s.t0) for s in wl.submissions])
+    assert len(res) == len(refs) == 64
+    for k, (r, ref) in enumerate(zip(res, refs)):
+        _assert_same(r, ref, f"batched slice {k}")
     for d in dets:
         d.close()
 
