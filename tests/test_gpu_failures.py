@@ -129,9 +129,11 @@ def test_device_wait_runs_out_and_the_device_stays_usable(pkg, params, km3):
 
 
 def test_device_wait_parameters_checked(pkg):
-    with pytest.raises(pkg.TrigError):
-        pkg.trig_set_device_wait(0, stall=2)
-    with pytest.raises(pkg.TrigError):
-        pkg.trig_set_device_wait(601 * 10**9)
-    with pytest.raises(pkg.TrigError):
-        pkg.trig_engine_hold(2)
+    lib = pkg.load()
+    try:
+        assert lib.trig_set_device_wait(0, 2) == pkg.TRIG_EINVAL
+        assert lib.trig_set_device_wait(601 * 10**9, 0) == pkg.TRIG_EINVAL
+        assert lib.trig_engine_hold(2) == pkg.TRIG_EINVAL
+    finally:
+        pkg.trig_set_device_wait(0, stall=False)
+        pkg.trig_engine_hold(False)
