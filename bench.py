@@ -37,6 +37,7 @@ WORKLOADS = {
 }
 TILE_BYTES_PER_HIT = 16          # k_tile reads every 16-byte hit once (halo re-reads excluded)
 BOUNDS_BYTES_PER_HIT = 16        # k_bounds reads every hit once
+SCATTER_BYTES_PER_HIT = 32       # k_scatter (detectors of 129 PMTs or more) reads and writes every hit
 
 
 _T0 = time.time()
@@ -117,28 +118,6 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-def _oracle_time(wl, par, ids):
-    """Oracle on the slices `ids` of the workload, one call per detector type
-    (the oracle's threads take the slices of a call in parallel).  Slices of
-    a call are independent runs far apart in time except for neighbours; the
-    timing, not the output, is used here."""
-    import oracle
-    hits, secs, threads = 0, 0.0, 0
-    hw = oracle.threads_used(0)
-    for d in (0, 1):
-        sel = [wl.submissions[k] for k in ids if wl.submissions[k].det_index == d]
-        if not sel:
-            continue
-        g = wl.detectors[d]
-        allh = np.concatenate([s.stream.hits for s in sel])
-        t = time.perf_counter()
-        oracle.run(g.xyz_mm, g.floor_id, par, allh, [s.t0 for s in sel], threads=0)
-        secs += time.perf_counter() - t
-        hits += sum(s.stream.n_hits for s in sel)
-        threads = max(threads, min(hw, len(sel)))
-    return hits, secs, threads
-
-
 def run_reference(args, ws, rank):
     """The CPU oracle, as it stands, on the host cores.  Each step is a
     bounded sample of the same workload: a rotating set of 20 ms pieces of
@@ -205,23 +184,28 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(wl, par, target_s=12.0):
+def cpu_baseline(wl, par, n_slices=32):
     """The oracle on the host cores over a bounded sample of the workload:
-    groups of 16 slices until about target_s seconds of CPU work."""
-    hits, secs, used, cores = 0, 0.0, 0, 0
-    n = len(wl.submissions)
-    i = 0
-    while i < n and secs < target_s:
-        ids = list(range(i, min(n, i + 16)))
-        i += len(ids)
-        h, t, c = _oracle_time(wl, par, ids)
-        hits += h
-        secs += t
-        used += len(ids)
-        cores = max(cores, c)
-    return {"value": hits / secs, "unit": "hits/s", "cores": cores, "kind": "oracle",
-            "sample": f"{used} of 64 slices ({hits} hits), one oracle call per tower type per 16 slices",
-            "seconds": secs}
+    the first n_slices slices, one oracle call per slice (the slices are
+    independent runs), spread over a pool of as many threads as the host
+    has cores (the oracle's C code runs without the interpreter lock)."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    sel = wl.submissions[:n_slices]
+    cores = os.cpu_count() or 1
+
+    def one(s):
+        g = wl.detectors[s.det_index]
+        oracle.run(g.xyz_mm, g.floor_id, par, s.stream.hits, [s.t0], threads=1)
+
+    t = time.perf_counter()
+    with ThreadPoolExecutor(cores) as ex:
+        list(ex.map(one, sel))
+    secs = time.perf_counter() - t
+    hits = sum(s.stream.n_hits for s in sel)
+    return {"value": hits / secs, "unit": "hits/s", "cores": min(cores, len(sel)), "kind": "oracle",
+            "sample": f"{len(sel)} of {len(wl.submissions)} slices ({hits} hits), one oracle call per slice on "
+                      f"{min(cores, len(sel))} threads", "seconds": secs}
 
 
 def main():
@@ -233,7 +217,10 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--serve-seconds", type=float, default=20.0, help="detector-seconds per detector")
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
+                    help="detector-seconds per detector of the 4x runs (1x: half, saturating runs: a third)")
+    ap.add_argument("--serve-pool", type=int, default=20, help="contiguous slices per detector in the replay pool")
+    ap.add_argument("--no-scaled", action="store_true", help="skip the 2688-PMT array leg")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-events", action="store_true", help="skip the event-extraction leg")
     ap.add_argument("--no-rules", action="store_true", help="skip the trigger-rule variants leg")
@@ -474,10 +461,51 @@ def main():
         del ab, arr8, dets8
         log(f"array: {ms_a:.3f} ms/step, selection {ms_sel:.3f} ms, {array['selected']} selected")
 
+    # -------------- the scaled array: one 200 ms slice of 2688 PMTs (29.6 M hits)
+    scaled = None
+    if not args.no_scaled and args.workload == "batched":
+        wls = workload.cfg_scaled(seed=args.seed + 1000 * rank)
+        gs = wls.detectors[0]
+        dsc = trig.Detector(gs.xyz_mm, gs.floor_id, par)
+        bs = DeviceBatch([SliceIn(dsc, s.t0, s.stream.hits, s.stream.pmt_off) for s in wls.submissions],
+                         device=f"cuda:{local}")
+        if not manual and not args.no_autotune:
+            trig.trig_autotune(dsc, bs.descs, stream.cuda_stream)
+        for _ in range(args.warmup):
+            bs.run(graph=True)
+        torch.cuda.synchronize()
+        k_s = max(5, args.steps)
+        e0.record(stream)
+        for _ in range(k_s):
+            bs.run(graph=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_s = max_over_ranks(e0.elapsed_time(e1) / k_s)
+        trig.trig_kernel_times()
+        for _ in range(k_s):
+            bs.run(timed=True)
+        torch.cuda.synchronize()
+        kts, _ = trig.trig_kernel_times()
+        n_s = bs.n_hits
+        t_ms = kts.get("k_tile", float("nan"))
+        ach_s = TILE_BYTES_PER_HIT * n_s / (t_ms * 1e-3) / 1e9
+        pipe_b = TILE_BYTES_PER_HIT + BOUNDS_BYTES_PER_HIT + SCATTER_BYTES_PER_HIT
+        scaled = {"workload": WORKLOADS["scaled"], "value": sum_over_ranks(float(n_s)) / (ms_s * 1e-3),
+                  "unit": "hits/s", "ms_per_step": ms_s, "hits_per_step": int(n_s),
+                  "tile": trig.trig_detector_tile_config(dsc), "kernels_ms": kts,
+                  "roofline": {"bound": "hbm", "kernel": "k_tile", "achieved": ach_s, "peak": _peaks()[0],
+                               "unit": "GB/s", "frac": ach_s / _peaks()[0], "kernel_ms": t_ms,
+                               "algorithmic_bytes_per_launch": TILE_BYTES_PER_HIT * n_s},
+                  "pipeline": {"bytes_per_hit": pipe_b, "achieved": pipe_b * n_s / (ms_s * 1e-3) / 1e9,
+                               "note": "structure pass 16 B + bucket-major copy 32 B + tile pass 16 B per hit"},
+                  "path": "trig_batch_run, CUDA graph replay"}
+        del bs, dsc
+        log(f"scaled: {ms_s:.3f} ms/step, k_tile {t_ms:.3f} ms")
+
     # ---------------------------------------------------- e2e, host buffers
     e2e = None
     trig.trig_engine_set_mode(1)
-    k_e2e = max(1, min(args.steps, 3))
+    k_e2e = max(5, min(args.steps, 20))
     # the producer's slices sit in page-locked host memory (trig_host_alloc),
     # as a DAQ front end would hold them; each step copies them in again
     pinned = [] if args.no_e2e else [(trig.pinned_copy(s.stream.hits), trig.pinned_copy(s.stream.pmt_off))
@@ -500,15 +528,24 @@ def main():
             e2e_step()
         torch.cuda.synchronize()
         barrier()
+        trig.trig_engine_trace(len(wl.submissions) * k_e2e + 16)
         t = time.perf_counter()
         d2h = 0
         for _ in range(k_e2e):
             d2h = e2e_step()
         torch.cuda.synchronize()
         e2e_s = max_over_ranks((time.perf_counter() - t) / k_e2e)
+        tr = trig.trig_engine_trace_read(len(wl.submissions) * k_e2e + 16)
+        trig.trig_engine_trace(0)
+        # the engine's batches' device time (CUDA events around each batch's
+        # kernels on its own stream), per step
+        _, first = np.unique(tr["batch"], return_index=True)
+        dev_ms = float(np.sum(tr["device_ms"][first])) / k_e2e if len(tr) else float("nan")
         h2d = sum(s.stream.hits.nbytes + s.stream.pmt_off.nbytes for s in wl.submissions)
         e2e = {"value": total_hits / e2e_s, "unit": "hits/s", "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s * 1e3,
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s * 1e3, "steps": k_e2e,
+               "device_ms_per_step": dev_ms, "batches_per_step": len(first) / k_e2e,
+               "h2d_bound_ms": h2d / 210e9 * 1e3,
                "path": "trig_submit_slice/trig_poll from page-locked host buffers, engine batched mode"}
 
     # ------------------------------------------------ served latency (rank 0)
@@ -518,16 +555,18 @@ def main():
         # the served replay runs in its own process (its own engine and CUDA
         # context), bounded by a timeout
         log("serving: start")
-        cmd = [sys.executable, "-m", "paper_1411_3968_gb300.serving", "--rate", "4", "--pool", "3",
-               "--detector-seconds", str(args.serve_seconds), "--seed", str(args.seed)]
+        ss = args.serve_seconds
+        cmd = [sys.executable, "-m", "paper_1411_3968_gb300.serving", "--pool", str(args.serve_pool),
+               "--seed", str(args.seed), "--runs", f"4:1:{ss}", f"4:0:{ss}", f"1:1:{ss / 2}",
+               f"sat:1:{ss / 3}", f"sat:0:{ss / 3}"]
         env = dict(os.environ, CUDA_VISIBLE_DEVICES=os.environ.get("CUDA_VISIBLE_DEVICES", str(local)))
         try:
-            out = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=300, env=env)
+            out = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=900, env=env)
             line = [x for x in out.stdout.splitlines() if x.startswith("{")]
             latency = json.loads(line[-1]) if line else {"error": out.stderr[-500:]}
         except subprocess.TimeoutExpired:
             latency = {"error": "serving replay timed out"}
-        latency["detectors"] = "32@50kHz, 84@55kHz, 84@55kHz, 2688@55kHz"
+        latency["command"] = " ".join(cmd[1:])
     log("serving: done")
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -551,6 +590,7 @@ def main():
             "events": events,
             "rules": rules,
             "array": array,
+            "scaled": scaled,
             "latency": latency,
             "cpu_baseline": cpu,
             "clocks": clocks,

@@ -275,6 +275,33 @@ int trig_engine_hold(int on);
 int trig_engine_set_staging_limit(uint64_t bytes);
 int trig_engine_fail_result_allocs(uint32_t n);
 
+/* Engine trace: one record per completed slice, for latency studies (the
+ * engine's own instrumentation; the paper has no counterpart).  Times are
+ * steady-clock ns since trig_engine_trace was called. */
+typedef struct {
+    uint64_t slice_id;
+    uint64_t batch;             /* engine batch number, from 1             */
+    uint32_t batch_slices;      /* slices in that batch                     */
+    uint32_t n_pmt;
+    uint64_t n_hits;            /* hits of the submission (with the tail)   */
+    int32_t status;
+    uint32_t continuation;      /* submitted with is_continuation = 1       */
+    int64_t t_submit_ns;        /* trig_submit_slice entered                */
+    int64_t t_queued_ns;        /* copied to the device and queued          */
+    int64_t t_launch_ns;        /* its batch launched                       */
+    int64_t t_stats_ns;         /* its batch's counters reached the host    */
+    int64_t t_done_ns;          /* result delivered to trig_poll            */
+    float device_ms;            /* its batch's device time (CUDA events from
+                                   launch to counters), -1 if unknown       */
+    uint32_t reserved;
+} trig_trace_rec;
+
+/* Starts recording (clearing earlier records) up to `capacity` slices;
+ * 0 stops.  trig_engine_trace_read moves up to `max` records, oldest first,
+ * into host memory `out` and sets *n_out. */
+int trig_engine_trace(uint32_t capacity);
+int trig_engine_trace_read(trig_trace_rec *out, uint32_t max, uint32_t *n_out);
+
 /* Bounded device waits.  Every wait of the tile pass (the stager waiting
  * for a free buffer, the consumers waiting for a staged tile) gives up after
  * limit_ns of the GPU's global timer (default 1 s; 0 restores it, at most

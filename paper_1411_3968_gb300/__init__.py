@@ -14,5 +14,5 @@ from ._lib import (  # noqa: F401
     Array, ASEED_DTYPE, ASTATS_DTYPE, TRIG_AFLAG_SEED_FULL, TRIG_AFLAG_WIN_FULL, TRIG_AFLAG_HIT_FULL,
     TRIG_AFLAG_TOWER_INCOMPLETE, trig_array_scratch_bytes, trig_array_select, pinned_copy,
     trig_engine_hold, trig_engine_set_staging_limit, trig_engine_fail_result_allocs, trig_set_device_wait,
-    TRIG_FLAG_TIMEOUT,
+    TRIG_FLAG_TIMEOUT, TRACE_DTYPE, trig_engine_trace, trig_engine_trace_read,
 )

@@ -38,6 +38,11 @@ WINDOW_DTYPE = np.dtype([("lo", "<i8"), ("hi", "<i8"), ("n_hits", "<u8"), ("n_tr
 STATS_DTYPE = np.dtype([("status", "<i4"), ("flags", "<u4"), ("n_hits", "<u8"), ("n_seeds", "<u8"),
                         ("n_triggers", "<u8"), ("n_windows", "<u8"), ("n_events", "<u8")])
 
+TRACE_DTYPE = np.dtype([("slice_id", "<u8"), ("batch", "<u8"), ("batch_slices", "<u4"), ("n_pmt", "<u4"),
+                        ("n_hits", "<u8"), ("status", "<i4"), ("continuation", "<u4"), ("t_submit_ns", "<i8"),
+                        ("t_queued_ns", "<i8"), ("t_launch_ns", "<i8"), ("t_stats_ns", "<i8"), ("t_done_ns", "<i8"),
+                        ("device_ms", "<f4"), ("reserved", "<u4")])
+
 ASEED_DTYPE = np.dtype([("t", "<i8"), ("pmt", "<u2"), ("tower", "<u2"), ("n_towers", "<u4")])
 ASTATS_DTYPE = np.dtype([("n_tower_triggers", "<u8"), ("n_selected", "<u8"), ("n_windows", "<u8"),
                          ("n_hits", "<u8"), ("flags", "<u4"), ("status", "<i4")])
@@ -55,6 +60,7 @@ EXPORTS = [
     "trig_autotune", "trig_detector_tile_config", "trig_batch_events_scratch_bytes", "trig_batch_run_events",
     "trig_set_events", "trig_host_alloc", "trig_host_free", "trig_array_create", "trig_array_destroy", "trig_array_scratch_bytes", "trig_array_select",
     "trig_engine_hold", "trig_engine_set_staging_limit", "trig_engine_fail_result_allocs", "trig_set_device_wait",
+    "trig_engine_trace", "trig_engine_trace_read",
 ]
 
 NOALLOC_SCRATCH_BYTES = 64 << 20
@@ -146,6 +152,8 @@ def load(path: str | None = None):
         "trig_engine_set_staging_limit": (c.c_int, [c.c_uint64]),
         "trig_engine_fail_result_allocs": (c.c_int, [c.c_uint32]),
         "trig_set_device_wait": (c.c_int, [c.c_uint64, c.c_int]),
+        "trig_engine_trace": (c.c_int, [c.c_uint32]),
+        "trig_engine_trace_read": (c.c_int, [c.c_void_p, c.c_uint32, c.POINTER(c.c_uint32)]),
         "trig_last_error": (c.c_char_p, []),
         "trig_batch_scratch_bytes": (c.c_size_t, [c.POINTER(trig_slice_dev), c.c_uint32]),
         "trig_batch_run": (c.c_int, [c.POINTER(trig_slice_dev), c.c_uint32, c.c_void_p, c.c_size_t, c.c_void_p,
@@ -382,6 +390,20 @@ def trig_engine_set_staging_limit(nbytes: int) -> None:
 def trig_engine_fail_result_allocs(n: int) -> None:
     """Failure injection: the next n result-memory requests fail (TRIG_ENOMEM results)."""
     _check(load().trig_engine_fail_result_allocs(int(n)))
+
+
+def trig_engine_trace(capacity: int) -> None:
+    """Start recording per-slice engine records (0 stops)."""
+    _check(load().trig_engine_trace(int(capacity)))
+
+
+def trig_engine_trace_read(max_records: int = 1 << 20) -> np.ndarray:
+    """The recorded slices so far (TRACE_DTYPE), oldest first; they are
+    removed from the engine's record."""
+    out = np.zeros(int(max_records), TRACE_DTYPE)
+    n = ctypes.c_uint32()
+    _check(load().trig_engine_trace_read(out.ctypes.data, len(out), ctypes.byref(n)))
+    return out[: n.value].copy()
 
 
 def trig_set_device_wait(limit_ns: int = 0, stall: bool = False) -> None:

@@ -1095,6 +1095,8 @@ struct Pending {
     size_t pmt_at = 0;
     uint64_t n_hits = 0;
     Clock::time_point t_submit;
+    Clock::time_point t_queued;         // copied to the device and queued
+    bool continuation = false;
 };
 
 // Device blocks for submitted slices, in power-of-two size classes and
@@ -1228,6 +1230,9 @@ namespace {
 struct Slot {
     cudaStream_t stream = nullptr;
     cudaEvent_t ev_stats = nullptr, ev_done = nullptr;
+    cudaEvent_t ev_launch = nullptr;                // timing events around the batch's kernels
+    uint64_t batch_id = 0;
+    Clock::time_point t_launch, t_stats;
     void *arena = nullptr;
     size_t arena_bytes = 0;
     unsigned char *bounce = nullptr;                // pinned: stats + outputs
@@ -1263,6 +1268,11 @@ struct Engine {
     int mode = 1;
     std::atomic<uint64_t> next_id{1};
     std::atomic<uint64_t> batches{0}, completed{0};
+    // per-slice trace (trig_engine_trace): records of completed slices
+    std::mutex trace_mu;
+    std::vector<trig_trace_rec> trace;
+    size_t trace_cap = 0;
+    Clock::time_point trace_t0;
     bool started = false;
     std::string fatal;
 
@@ -1272,7 +1282,7 @@ struct Engine {
         for (auto &s : slots) {
             cudaError_t e;
             if ((e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking)) ||
-                (e = cudaEventCreateWithFlags(&s.ev_stats, cudaEventDisableTiming)) ||
+                (e = cudaEventCreate(&s.ev_stats)) || (e = cudaEventCreate(&s.ev_launch)) ||
                 (e = cudaEventCreateWithFlags(&s.ev_done, cudaEventDisableTiming)))
                 return cuda_fail(e, "engine start");
         }
@@ -1441,6 +1451,8 @@ bool Engine::launch_batch_on(Slot &s, std::vector<Pending> &batch)
     cudaError_t e = cudaSuccess;
     // batches of the engine vary in size and composition from one launch
     // to the next, so they are launched directly rather than from graphs
+    s.t_launch = Clock::now();
+    cudaEventRecord(s.ev_launch, s.stream);
     int rc = any_ev ? trig_batch_run_events(dev.data(), evs.data(), n, A + L.scratch, L.scratch_bytes, s.stream, 0)
                     : trig_batch_run(dev.data(), n, A + L.scratch, L.scratch_bytes, s.stream, 0);
     if (rc) {
@@ -1462,7 +1474,7 @@ bool Engine::launch_batch_on(Slot &s, std::vector<Pending> &batch)
     s.state = 1;
     s.trig_n.assign(n, 0);
     s.win_n.assign(n, 0);
-    batches++;
+    s.batch_id = ++batches;
     return true;
 }
 
@@ -1486,6 +1498,7 @@ void Engine::fail_slot(Slot &s, cudaError_t err)
 
 void Engine::collect_stats(Slot &s)
 {
+    s.t_stats = Clock::now();
     const uint32_t n = (uint32_t)s.slices.size();
     const trig_slice_stats *st = reinterpret_cast<const trig_slice_stats *>(s.bounce);
     // per slice one pinned block sized by the actual counts: triggers,
@@ -1537,6 +1550,37 @@ void Engine::finish(Slot &s)
     const uint32_t n = (uint32_t)s.slices.size();
     const trig_slice_stats *st = reinterpret_cast<const trig_slice_stats *>(s.bounce);
     const auto now = Clock::now();
+    {
+        std::lock_guard<std::mutex> tk(trace_mu);
+        if (trace.size() < trace_cap) {
+            float dev_ms = -1.f;
+            if (cudaEventElapsedTime(&dev_ms, s.ev_launch, s.ev_stats) != cudaSuccess) {
+                (void)cudaGetLastError();
+                dev_ms = -1.f;
+            }
+            auto ns = [&](Clock::time_point t) {
+                return (int64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(t - trace_t0).count();
+            };
+            for (uint32_t i = 0; i < n && trace.size() < trace_cap; ++i) {
+                const Pending &p = s.slices[i];
+                trig_trace_rec t{};
+                t.slice_id = p.id;
+                t.batch = s.batch_id;
+                t.batch_slices = n;
+                t.n_pmt = p.det->n_pmt;
+                t.n_hits = p.n_hits;
+                t.status = s.lost[i] ? TRIG_ENOMEM : st[i].status;
+                t.continuation = p.continuation ? 1u : 0u;
+                t.t_submit_ns = ns(p.t_submit);
+                t.t_queued_ns = ns(p.t_queued);
+                t.t_launch_ns = ns(s.t_launch);
+                t.t_stats_ns = ns(s.t_stats);
+                t.t_done_ns = ns(now);
+                t.device_ms = dev_ms;
+                trace.push_back(t);
+            }
+        }
+    }
     for (uint32_t i = 0; i < n; ++i) {
         Pending &p = s.slices[i];
         trig_result *r = new_result(p.id, p.t0, s.lost[i] ? TRIG_ENOMEM : st[i].status);
@@ -1684,6 +1728,32 @@ extern "C" int trig_engine_fail_result_allocs(uint32_t n)
     return TRIG_OK;
 }
 
+extern "C" int trig_engine_trace(uint32_t capacity)
+{
+    Engine *e = engine();
+    if (!e) return TRIG_EDEVICE;
+    std::lock_guard<std::mutex> lk(e->trace_mu);
+    e->trace.clear();
+    e->trace.shrink_to_fit();
+    e->trace_cap = capacity;
+    if (capacity) e->trace.reserve(std::min<size_t>(capacity, (size_t)1 << 20));
+    e->trace_t0 = Clock::now();
+    return TRIG_OK;
+}
+
+extern "C" int trig_engine_trace_read(trig_trace_rec *out, uint32_t max, uint32_t *n_out)
+{
+    if (!n_out || (max && !out)) return fail(TRIG_EINVAL, "NULL argument");
+    Engine *e = engine();
+    if (!e) return TRIG_EDEVICE;
+    std::lock_guard<std::mutex> lk(e->trace_mu);
+    const uint32_t n = (uint32_t)std::min<size_t>(max, e->trace.size());
+    std::copy(e->trace.begin(), e->trace.begin() + n, out);
+    e->trace.erase(e->trace.begin(), e->trace.begin() + n);
+    *n_out = n;
+    return TRIG_OK;
+}
+
 extern "C" int trig_engine_stats(uint64_t *batches, uint64_t *slices)
 {
     Engine *e = engine();
@@ -1819,6 +1889,8 @@ extern "C" int trig_submit_slice(trig_detector *det, int64_t t0, const trig_hit 
     tl.have = true;
     tl.next_t0 = t0 + S;
     p.t_submit = t_entry;
+    p.t_queued = Clock::now();
+    p.continuation = is_continuation != 0;
     p.id = e->next_id++;
     {
         std::lock_guard<std::mutex> lk(p.q->mu);

@@ -91,13 +91,29 @@ __device__ __forceinline__ uint64_t global_ns()
     return t;
 }
 
+// Built with -DTRIG_PHASE_STATS, the tile kernel adds its per-phase clock
+// cycles and its waits (cycles, try_wait rounds) into device counters that
+// trig_phase_stats reads; without it the counters compile to nothing.
+#ifdef TRIG_PHASE_STATS
+__device__ unsigned long long g_phase[24];
+#define PHASE_ADD(i, v) atomicAdd(&g_phase[(i)], (unsigned long long)(v))
+#else
+#define PHASE_ADD(i, v) ((void)0)
+#endif
+enum PhaseCounter {
+    kPhTiles, kPhConsWait, kPhConsWaitRounds, kPhProdWait, kPhProdWaitRounds, kPhA, kPhB, kPhC, kPhD, kPhE,
+    kPhF, kPhG, kPhSeeds, kPhProdItem, kPhConsTotal, kPhProdTotal, kPhKeys
+};
+
 // Bounded wait: gives up after limit_ns of the GPU's global timer and
-// reports failure.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns)
+// reports failure.  *rounds (optional) counts the try_wait rounds.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns,
+                                          uint32_t *rounds = nullptr)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t_start = global_ns();
-    for (;;) {
+    for (uint32_t r = 1;; ++r) {
+        if (rounds) *rounds = r;
         if (mbar_try_wait_hint(bar, parity, 20000u)) return true;
         if (global_ns() - t_start > limit_ns) return false;
     }
@@ -956,6 +972,17 @@ __device__ __forceinline__ void count_causal(const TileCtx<CAP> &cx, const uint3
     constexpr uint32_t G = 1u << LG, NG = NC >> LG;
     const uint32_t tid = threadIdx.x, gl = tid & (G - 1u), gid = tid >> LG, P = cx.P;
     const uint32_t rounds = (ns + NG - 1) / NG;
+#ifdef TRIG_PHASE_STATS
+    uint32_t keys_seen = 0;
+    struct Flush {
+        uint32_t &k;
+        __device__ ~Flush()
+        {
+            const uint32_t w = __reduce_add_sync(0xffffffffu, k);
+            if ((threadIdx.x & 31u) == 0 && w) PHASE_ADD(kPhKeys, w);
+        }
+    } flush{keys_seen};
+#endif
     for (uint32_t r = 0; r < rounds; ++r) {
         const uint32_t k = r * NG + gid;
         uint32_t c = 0;
@@ -964,6 +991,9 @@ __device__ __forceinline__ void count_causal(const TileCtx<CAP> &cx, const uint3
             const uint32_t ts = pk_t(ks), ps = pk_p(ks);
             uint32_t j0, j1;
             seed_range<CAP>(cx, ts, ps, bsh, j0, j1);
+#ifdef TRIG_PHASE_STATS
+            keys_seen += gl == 0 ? j1 - j0 : 0u;
+#endif
             if (CHECK(12, j1, n + 1) && CHECK(13, ps, P)) {
                 const uint16_t *row_s = cx.dt_s() + (size_t)ps * P;
                 const uint16_t *row_g = cx.dt_g + (size_t)ps * P;
@@ -1019,34 +1049,51 @@ __device__ __forceinline__ uint32_t bucket_shift(uint32_t span)
 //     in its time bucket (t - tb) >> bsh; the stage buffer is then handed
 //     back to the producer (release_bar), the rest works on the keys;
 //  B. bucket offsets (exclusive scan of the counts);
-//  C. keys (and charges) scattered to bucket order, then each key ranked
-//     inside its bucket by (t, pmt, charge): the k-way merge of the PMT
-//     runs ("DAQ system of NEMO Phase II"), one key per bucket on average;
+//  C. keys (and charges) scattered to bucket order: the k-way merge of the
+//     PMT runs ("DAQ system of NEMO Phase II") down to time buckets of
+//     2^bsh ns, about one key per bucket.  Builds that need the full (t,
+//     pmt, charge) order (SORT: the extended rules, row outputs, event
+//     extraction) then rank each key inside its bucket;
 //  D. seeds ("Sorting and triggering in GPU"): a charge over q_seed, or
-//     another PMT of the same floor within tau -- each hit walks forward
-//     through the merged keys while they are within tau, so every pair is
-//     seen once, and both hits of a pair are marked; seed rule 1 and level 0
-//     of the extended builds (EXT) test each core hit instead;
-//  E. the ordered seed list; F. the causal count of every seed ("Muon
-//     trigger strategy"); G. the fired seeds, in merged order, to out.
+//     another PMT of the same floor within tau.  Each key walks forward
+//     through the keys that follow it while they can be within tau (in
+//     bucket order: to the end of the bucket holding t + tau), so every
+//     pair is seen once and both hits of a pair are marked; seed rule 1
+//     and level 0 (SORT builds) test each core hit instead;
+//  E. the seed list; F. the causal count of every seed over whole buckets
+//     of its scan range, each key tested exactly ("Muon trigger
+//     strategy"); G. the fired seeds, in (t, pmt, charge) order, to out.
 //
-// Returns the counts and c0 = the number of staged keys before the core (the
-// core is keys [c0, c1) of the merged order).  cnt and mask are zero on
-// entry and on return.
+// Returns the counts and c0 = the number of staged keys before the core.
+// cnt and mask are zero on entry and on return.
 template <int CAP, int NC, bool SMEM_DT, bool EXT, bool DENSE>
 __device__ CoreOut tile_pass(TileCtx<CAP> &cx, const uint64_t *stage, uint32_t n, int64_t tb, uint32_t span,
                              uint32_t lo_t, uint32_t hi_t, const TrigParams &tp, trig_trigger *out, bool out_at_c0,
                              int64_t dbg_rank_lo, uint64_t *release_bar)
 {
+    constexpr bool SORT = EXT;
     constexpr uint32_t NW = NC / 32;
     constexpr int PER = CAP / NC;
     const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
     const uint32_t bsh = bucket_shift<CAP>(span);
     __shared__ uint32_t s_red[NW + 1];
     __shared__ uint32_t s_below[2];
-    __shared__ uint32_t s_tot[2 * (NW + 1)];
+    __shared__ uint32_t s_tot[2 * NW];
     uint32_t *cnt = cx.cnt();
     uint32_t *mask = cx.mask();
+#ifdef TRIG_PHASE_STATS
+    long long t_ph = clock64();
+#define PHASE_MARK(i)                                   \
+    do {                                                \
+        if (tid == 0) {                                 \
+            const long long now_ = clock64();           \
+            PHASE_ADD((i), now_ - t_ph);                \
+            t_ph = now_;                                \
+        }                                               \
+    } while (0)
+#else
+#define PHASE_MARK(i) ((void)0)
+#endif
 
     // A. keys and bucket counts
     uint32_t key[PER], cs[PER];           // packed key; charge << 16 | slot in the bucket
@@ -1084,47 +1131,61 @@ __device__ CoreOut tile_pass(TileCtx<CAP> &cx, const uint64_t *stage, uint32_t n
     cons_exclusive_scan<NC>(cnt, TileLayout<CAP>::NBK, s_red);
     if (release_bar && tid == 0) mbar_arrive(release_bar);
     const uint32_t c0 = s_below[0], c1 = s_below[1];
+    PHASE_MARK(kPhA);
 
-    // C. bucket order, then the rank inside the bucket
-    uint32_t *pk_b = cx.pk_b(), *pk = cx.pk_s();
-    uint16_t *chg_b = cx.chg_b(), *chg = cx.chg_s();
-#pragma unroll
-    for (int r = 0; r < PER; ++r) {
-        if (key[r] != kPkNone) {
-            const uint32_t pos = cnt[bucket_of<CAP>(key[r] >> 12, bsh)] + (cs[r] & 0xffffu);
-            if (CHECK(22, pos, CAP)) {
-                pk_b[pos] = key[r];
-                chg_b[pos] = (uint16_t)(cs[r] >> 16);
-            }
-        }
-    }
-    cons_sync<NC>();
+    // C. bucket order (the final order of the default rule); charge seeds
+    //    of the core are marked where their keys land
+    uint32_t *pk = cx.pk_s();
+    uint16_t *chg = cx.chg_s();
+    uint32_t *pk_c = SORT ? cx.pk_b() : pk;
+    uint16_t *chg_c = SORT ? cx.chg_b() : chg;
     const bool charge_rule = !(EXT && tp.seed_rule == 1);
 #pragma unroll
     for (int r = 0; r < PER; ++r) {
-        const uint32_t k = key[r];
-        if (k == kPkNone) continue;
-        const uint32_t b = bucket_of<CAP>(k >> 12, bsh);
-        const uint32_t s0 = cnt[b], s1 = cnt[b + 1], q = cs[r] >> 16, pos = s0 + (cs[r] & 0xffffu);
-        uint32_t rk = s0;
-        for (uint32_t m = s0; m < s1; ++m) {
-            const uint32_t o = pk_b[m];
-            rk += o < k;
-            if (o == k) {                          // equal time and PMT: charge, then position
-                const uint32_t oq = chg_b[m];
-                rk += oq < q || (oq == q && m < pos);
+        if (key[r] != kPkNone) {
+            const uint32_t tr = key[r] >> 12;
+            const uint32_t pos = cnt[bucket_of<CAP>(tr, bsh)] + (cs[r] & 0xffffu);
+            if (CHECK(22, pos, CAP)) {
+                pk_c[pos] = key[r];
+                chg_c[pos] = (uint16_t)(cs[r] >> 16);
+                if (!SORT && charge_rule && (cs[r] >> 16) >= tp.q_seed && tr >= lo_t && tr < hi_t)
+                    atomicOr(&mask[pos >> 5], 1u << (pos & 31u));
             }
-        }
-        if (CHECK(23, rk, CAP)) {
-            pk[rk] = k;
-            chg[rk] = (uint16_t)q;
-            const uint32_t tr = k >> 12;
-            if (charge_rule && q >= tp.q_seed && tr >= lo_t && tr < hi_t) atomicOr(&mask[rk >> 5], 1u << (rk & 31u));
         }
     }
     cons_sync<NC>();
+    PHASE_MARK(kPhB);
+    if (SORT) {
+        // the rank inside the bucket by (t, pmt, charge), then position
+#pragma unroll
+        for (int r = 0; r < PER; ++r) {
+            const uint32_t k = key[r];
+            if (k == kPkNone) continue;
+            const uint32_t b = bucket_of<CAP>(k >> 12, bsh);
+            const uint32_t s0 = cnt[b], s1 = cnt[b + 1], q = cs[r] >> 16, pos = s0 + (cs[r] & 0xffffu);
+            uint32_t rk = s0;
+            for (uint32_t m = s0; m < s1; ++m) {
+                const uint32_t o = pk_c[m];
+                rk += o < k;
+                if (o == k) {                      // equal time and PMT: charge, then position
+                    const uint32_t oq = chg_c[m];
+                    rk += oq < q || (oq == q && m < pos);
+                }
+            }
+            if (CHECK(23, rk, CAP)) {
+                pk[rk] = k;
+                chg[rk] = (uint16_t)q;
+                const uint32_t tr = k >> 12;
+                if (charge_rule && q >= tp.q_seed && tr >= lo_t && tr < hi_t)
+                    atomicOr(&mask[rk >> 5], 1u << (rk & 31u));
+            }
+        }
+        cons_sync<NC>();
+    }
+    PHASE_MARK(kPhC);
 
-    // D. seed flags of the core keys [c0, c1)
+    // D. seed flags of the core keys [c0, c1) (in bucket order the core is
+    //    the keys whose time is in [lo_t, hi_t))
     const uint32_t P = cx.P;
     if (EXT && tp.seed_rule == 1) {
         for (uint32_t base = c0 & ~31u; base < c1; base += NC) {
@@ -1134,8 +1195,6 @@ __device__ CoreOut tile_pass(TileCtx<CAP> &cx, const uint64_t *stage, uint32_t n
             if (lane == 0 && m) atomicOr(&mask[(base >> 5) + warp], m);
         }
     } else {
-        // keys that can pair with a core key: [c0, c1) widened by tau on
-        // both sides, found by walking from the core's ends
         const uint32_t tau = tp.tau;
         const uint16_t *fl = cx.floor_s();
         for (uint32_t base = 0; base < n; base += NC) {
@@ -1146,14 +1205,19 @@ __device__ CoreOut tile_pass(TileCtx<CAP> &cx, const uint64_t *stage, uint32_t n
                 if (ti + tau >= lo_t && ti < hi_t + tau) {
                     const uint32_t pi = ki & 0xfffu;
                     const uint32_t fi = fl[pi];
-                    const bool ci = i >= c0 && i < c1;
+                    const bool ci = ti >= lo_t && ti < hi_t;
+                    // the walk ends after the keys that can be within tau:
+                    // sorted, the first later than t + tau; in bucket
+                    // order, the first past the bucket holding t + tau
+                    const uint32_t stop = SORT ? ti + tau : (bucket_of<CAP>(ti + tau, bsh) + 1) << bsh;
                     for (uint32_t j = i + 1; j < n; ++j) {
-                        const uint32_t kj = pk[j];
-                        if ((kj >> 12) - ti > tau) break;
+                        const uint32_t kj = pk[j], tj = kj >> 12;
+                        if (SORT ? tj > stop : tj >= stop) break;
                         const uint32_t pj = kj & 0xfffu;
-                        if (pj != pi && fl[pj] == fi) {
+                        const uint32_t d = tj > ti ? tj - ti : ti - tj;
+                        if (d <= tau && pj != pi && fl[pj] == fi) {
                             mine |= ci;
-                            if (j >= c0 && j < c1) atomicOr(&mask[j >> 5], 1u << (j & 31u));
+                            if (tj >= lo_t && tj < hi_t) atomicOr(&mask[j >> 5], 1u << (j & 31u));
                         }
                     }
                 }
@@ -1175,13 +1239,20 @@ __device__ CoreOut tile_pass(TileCtx<CAP> &cx, const uint64_t *stage, uint32_t n
         }
         cons_sync<NC>();
     }
+    PHASE_MARK(kPhD);
 
-    // E. ordered seed list: warp w expands a contiguous group of mask words
+    // E. ordered seed list: warp w expands a contiguous group of mask words;
+    //    each warp adds up the totals of the warps before it
     uint16_t *seed_idx = cx.seed_idx(), *seed_cnt = cx.seed_cnt();
-    const uint32_t w_lo = c0 >> 5, w_hi = (c1 + 31) >> 5;
+    // marks lie in the core: sorted, positions [c0, c1); in bucket order,
+    // the buckets of [lo_t, hi_t)
+    const uint32_t p_lo = SORT ? c0 : cnt[bucket_of<CAP>(lo_t, bsh)];
+    const uint32_t p_hi = SORT ? c1 : cnt[bucket_of<CAP>(hi_t > 0 ? hi_t - 1 : 0, bsh) + 1];
+    const uint32_t w_lo = p_lo >> 5, w_hi = (p_hi + 31) >> 5;
     const uint32_t nwords = w_hi - w_lo;
-    const uint32_t wpw = (nwords + NW - 1) / NW;          // words per warp (<= CAP / 32 / NW)
-    uint32_t *wtot = s_tot;                               // [NW + 1]
+    const uint32_t wpw = (nwords + NW - 1) / NW;          // words per warp
+    uint32_t *wtot = s_tot;                               // [NW]
+    uint32_t ns;
     {
         uint32_t pc = 0;
         for (uint32_t x = 0; x < wpw; x += 32) {
@@ -1191,14 +1262,14 @@ __device__ CoreOut tile_pass(TileCtx<CAP> &cx, const uint64_t *stage, uint32_t n
         pc = __reduce_add_sync(0xffffffffu, pc);
         if (lane == 0) wtot[warp] = pc;
         cons_sync<NC>();
-        if (warp == 0) {
-            const uint32_t v = lane < NW ? wtot[lane] : 0u;
-            const uint32_t vi = warp_incl_scan(v);
-            if (lane < NW) wtot[lane] = vi - v;
-            if (lane == NW - 1) wtot[NW] = vi;
+        uint32_t pos = 0;
+        ns = 0;
+#pragma unroll
+        for (uint32_t w2 = 0; w2 < NW; ++w2) {
+            const uint32_t v = wtot[w2];
+            pos += w2 < warp ? v : 0u;
+            ns += v;
         }
-        cons_sync<NC>();
-        uint32_t pos = wtot[warp];
         for (uint32_t x = 0; x < wpw; x += 32) {
             const uint32_t w = w_lo + warp * wpw + x + lane;
             const uint32_t m = (x + lane < wpw && w < w_hi) ? mask[w] : 0u;
@@ -1215,8 +1286,9 @@ __device__ CoreOut tile_pass(TileCtx<CAP> &cx, const uint64_t *stage, uint32_t n
             pos += __shfl_sync(0xffffffffu, incl, 31);
         }
     }
-    const uint32_t ns = wtot[NW];
     cons_sync<NC>();
+    PHASE_MARK(kPhE);
+    if (tid == 0) PHASE_ADD(kPhSeeds, ns);
 
     // F. causal count c(s) over each seed's scan range, or its distinct-PMT
     //    form (sparse batches give each seed 4 lanes, dense ones a warp)
@@ -1226,9 +1298,12 @@ __device__ CoreOut tile_pass(TileCtx<CAP> &cx, const uint64_t *stage, uint32_t n
         count_causal<CAP, NC, SMEM_DT, DENSE ? 5u : 2u>(cx, pk, n, ns, seed_idx, bsh, seed_cnt);
     }
     cons_sync<NC>();
+    PHASE_MARK(kPhF);
 
     // G. emit the fired seeds in order: warp w takes a contiguous range of
-    //    the seed list, a scan of the warp totals gives its output offset
+    //    the seed list and adds up the fired totals of the warps before it.
+    //    In bucket order a fired seed's rank also counts the fired seeds of
+    //    its bucket (adjacent in the list) with a smaller (t, pmt, charge).
     const uint32_t threshold = tp.threshold;
     const uint32_t per_w = (ns + NW - 1) / NW;
     const uint32_t k_begin = min(ns, warp * per_w), k_end = min(ns, k_begin + per_w);
@@ -1237,43 +1312,56 @@ __device__ CoreOut tile_pass(TileCtx<CAP> &cx, const uint64_t *stage, uint32_t n
         const uint32_t k = k0 + lane;
         my_f += __popc(__ballot_sync(0xffffffffu, k < k_end && seed_cnt[k] >= threshold));
     }
-    uint32_t *ftot = s_tot + (NW + 1);                    // [NW + 1]
+    uint32_t *ftot = s_tot + NW;                          // [NW]
     if (lane == 0) ftot[warp] = my_f;
     cons_sync<NC>();
-    if (warp == 0) {
-        const uint32_t v = lane < NW ? ftot[lane] : 0u;
-        const uint32_t vi = warp_incl_scan(v);
-        if (lane < NW) ftot[lane] = vi - v;
-        if (lane == NW - 1) ftot[NW] = vi;
+    uint32_t n_fired = 0, F = 0;
+#pragma unroll
+    for (uint32_t w2 = 0; w2 < NW; ++w2) {
+        const uint32_t v = ftot[w2];
+        F += w2 < warp ? v : 0u;
+        n_fired += v;
     }
-    cons_sync<NC>();
     trig_trigger *dst = out + (out_at_c0 ? c0 : 0u);
-    {
-        uint32_t F = ftot[warp];
-        for (uint32_t k0 = k_begin; k0 < k_end; k0 += 32) {
-            const uint32_t k = k0 + lane;
-            const bool fired = k < k_end && seed_cnt[k] >= threshold;
-            const uint32_t m = __ballot_sync(0xffffffffu, fired);
-            if (fired) {
-                const uint32_t i = seed_idx[k];
-                const uint32_t ks = pk[i];
-                trig_trigger tr;
-                tr.t_ns = tb + (int64_t)(ks >> 12);
-                tr.pmt = (uint16_t)(ks & 0xfffu);
-                tr.charge = chg[i];
-                tr.count = seed_cnt[k];
-                const uint32_t o_ = F + __popc(m & ((1u << lane) - 1u));
-                if (CHECK(3, o_, c1 - c0)) dst[o_] = tr;
+    for (uint32_t k0 = k_begin; k0 < k_end; k0 += 32) {
+        const uint32_t k = k0 + lane;
+        const bool fired = k < k_end && seed_cnt[k] >= threshold;
+        const uint32_t m = __ballot_sync(0xffffffffu, fired);
+        if (fired) {
+            const uint32_t i = seed_idx[k];
+            const uint32_t ks = pk[i];
+            const uint32_t q = chg[i];
+            uint32_t o_ = F + __popc(m & ((1u << lane) - 1u));
+            if (!SORT) {
+                // fired seeds of the same bucket before k that order after
+                // it, and after k that order before it
+                const uint32_t bk = bucket_of<CAP>(ks >> 12, bsh);
+                const uint64_t key_k = ((uint64_t)ks << 16) | q;
+                for (uint32_t k2 = k; k2-- > 0;) {
+                    const uint32_t i2 = seed_idx[k2];
+                    if (bucket_of<CAP>(pk[i2] >> 12, bsh) != bk) break;
+                    if (seed_cnt[k2] >= threshold && (((uint64_t)pk[i2] << 16) | chg[i2]) > key_k) --o_;
+                }
+                for (uint32_t k2 = k + 1; k2 < ns; ++k2) {
+                    const uint32_t i2 = seed_idx[k2];
+                    if (bucket_of<CAP>(pk[i2] >> 12, bsh) != bk) break;
+                    if (seed_cnt[k2] >= threshold && (((uint64_t)pk[i2] << 16) | chg[i2]) < key_k) ++o_;
+                }
             }
-            F += __popc(m);
+            trig_trigger tr;
+            tr.t_ns = tb + (int64_t)(ks >> 12);
+            tr.pmt = (uint16_t)(ks & 0xfffu);
+            tr.charge = (uint16_t)q;
+            tr.count = seed_cnt[k];
+            if (CHECK(3, o_, c1 - c0)) dst[o_] = tr;
         }
+        F += __popc(m);
     }
-    const uint32_t n_fired = ftot[NW];
-    // optional row outputs: the merged core rows (verification, and the
-    // merged stream of event extraction) and each row's causal count
-    // (verification only); rows are indexed by merged rank minus the rank
-    // of the slice's first owned hit
-    if (tp.dbg_merged) {
+    // optional row outputs (SORT builds): the merged core rows
+    // (verification, and the merged stream of event extraction) and each
+    // row's causal count (verification only); rows are indexed by merged
+    // rank minus the rank of the slice's first owned hit
+    if (SORT && tp.dbg_merged) {
         const uint64_t dbg_base = (uint64_t)(dbg_rank_lo + (int64_t)c0);
         for (uint32_t i = tid; i < c1 - c0; i += NC) {
             const uint32_t k = pk[c0 + i];
@@ -1294,6 +1382,8 @@ __device__ CoreOut tile_pass(TileCtx<CAP> &cx, const uint64_t *stage, uint32_t n
     for (uint32_t i = tid; i < (uint32_t)TileLayout<CAP>::NBK; i += NC) cnt[i] = 0;
     for (uint32_t w = w_lo + tid; w < w_hi; w += NC) mask[w] = 0;
     cons_sync<NC>();
+    PHASE_MARK(kPhG);
+#undef PHASE_MARK
     CoreOut co;
     co.n_fired = n_fired;
     co.n_seeds = ns;
@@ -1480,6 +1570,9 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 
         item = __shfl_sync(0xffffffffu, item, 0);
         for (uint32_t it = 0;; ++it) {
             const uint32_t b = it % NSTG, use = it / NSTG;
+#ifdef TRIG_PHASE_STATS
+            const long long tp0 = clock64();
+#endif
             uint32_t g = 0, P = 0, mode = 2, lo_t = 0, span = 0;
             uint64_t ra[R];
             uint32_t rl[R];
@@ -1545,7 +1638,19 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 
                 if (lane == 0) next = atomicAdd(&hdr->queue, 1u);
                 next = __shfl_sync(0xffffffffu, next, 0);
             }
+#ifdef TRIG_PHASE_STATS
+            const long long tw0 = clock64();
+            if (lane == 0) PHASE_ADD(kPhProdItem, tw0 - tp0);
+            uint32_t pr = 0;
+            const bool pwait_ok = it < NSTG || mbar_wait(&empty_bar[b], (use - 1) & 1u, wait_ns, &pr);
+            if (lane == 0) {
+                PHASE_ADD(kPhProdWait, clock64() - tw0);
+                PHASE_ADD(kPhProdWaitRounds, pr);
+            }
+            if (!pwait_ok) {
+#else
             if (it >= NSTG && !mbar_wait(&empty_bar[b], (use - 1) & 1u, wait_ns)) {
+#endif
                 if (lane == 0) atomicOr(&hdr->err, TRIG_FLAG_TIMEOUT);
                 break;
             }
@@ -1584,6 +1689,9 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 
                     dst += __shfl_sync(0xffffffffu, incl, 31);
                 }
             }
+#ifdef TRIG_PHASE_STATS
+            if (lane == 0) PHASE_ADD(kPhProdTotal, clock64() - tp0);
+#endif
             item = next;
         }
         return;
@@ -1603,7 +1711,19 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 
     __shared__ int64_t sl[4];
     for (uint32_t it = 0;; ++it) {
         const uint32_t b = it % NSTG, use = it / NSTG;
+#ifdef TRIG_PHASE_STATS
+        const long long tw0 = clock64();
+        uint32_t cr = 0;
+        const bool cwait_ok = mbar_wait(&full_bar[b], use & 1u, wait_ns, &cr);
+        if (tid == 0) {
+            PHASE_ADD(kPhConsWait, clock64() - tw0);
+            PHASE_ADD(kPhConsWaitRounds, cr);
+            PHASE_ADD(kPhTiles, 1);
+        }
+        if (!cwait_ok) {
+#else
         if (!mbar_wait(&full_bar[b], use & 1u, wait_ns)) {
+#endif
             if (tid == 0) atomicOr(&hdr->err, TRIG_FLAG_TIMEOUT);
             break;
         }
@@ -2249,6 +2369,23 @@ __global__ void k_status(const BatchHeader *__restrict__ hdr, const SliceDesc *_
     }
 }
 
+#ifdef TRIG_PHASE_STATS
+// Tile-kernel counters of the phase-statistics build (summed over blocks
+// since the last reset): read n of them into out, then optionally reset.
+extern "C" int trig_phase_stats(unsigned long long *out, int n, int reset)
+{
+    unsigned long long v[24] = {};
+    if (n > 24) n = 24;
+    if (cudaMemcpyFromSymbol(v, g_phase, sizeof v) != cudaSuccess) return -1;
+    for (int i = 0; i < n; ++i) out[i] = v[i];
+    if (reset) {
+        const unsigned long long z[24] = {};
+        if (cudaMemcpyToSymbol(g_phase, z, sizeof z) != cudaSuccess) return -1;
+    }
+    return 0;
+}
+#endif
+
 #ifdef TRIG_CHECK
 // First recorded check failure of the process (checked builds only).
 extern "C" int trig_check_record(unsigned *site, unsigned *count, unsigned long long *index,
@@ -2402,9 +2539,11 @@ cudaError_t launch_batch(BatchHeader *d_hdr, SliceDesc *d_desc, uint32_t n_slice
     mark(5);
     cudaError_t e;
     const bool smem_dt = any_smem_dt && max_pmt <= kSmemDtMaxPmt;
-    if (any_ext) {
-        // level 0, seed rule 1, distinct count: one build per shape, dt rows
-        // read through the cache
+    if (any_ext || any_events || rows) {
+        // level 0, seed rule 1, distinct count, and every batch that needs
+        // the merged rows (event extraction, row outputs): the build that
+        // puts each tile in full (t, pmt, charge) order, one per shape, dt
+        // rows read through the cache
         if (cfg.cap == 1024)
             e = launch_tile<1024, 128, false, true>(d_hdr, d_desc, max_pmt, st);
         else if (cfg.cap == 2048)

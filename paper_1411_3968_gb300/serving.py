@@ -2,12 +2,21 @@
 and go through the native engine (trig_submit_slice / trig_poll), which
 batches whatever is pending continuously.  Reports slice latency
 percentiles against the 200 ms real-time budget of a slice ("Results and
-perspectives": a TGPU must keep up with 1 s of data per second).
+perspectives": a TGPU must keep up with 1 s of data per second), the
+served hits/s, and where the latency goes (the engine's per-slice trace).
+
+Each detector replays a pool of contiguous slices: the pool's first slice
+carries both halos, every later one starts at its t0 and takes its leading
+halo from the previous slice's tail that the engine keeps on the device
+(is_continuation = 1).  A run is rate:mode:detector_seconds, where rate is
+the arrival rate in units of real time (or "sat": every slice submitted at
+once, which measures capacity) and mode is the engine's (0 plain per-slice
+launches, 1 continuous batching).
 
 The request loop and the pollers are Python threads; every call they make
 releases the GIL inside libtrig.so, where copies, batching and kernels run.
 
-    python -m paper_1411_3968_gb300.serving --rate 4 --detector-seconds 600
+    python -m paper_1411_3968_gb300.serving --pool 20 --runs 4:1:600 4:0:600 1:1:600 sat:1:60 sat:0:60
 """
 from __future__ import annotations
 
@@ -21,14 +30,14 @@ import numpy as np
 from . import _lib
 
 
-def warm_up(dets, pools, rounds: int = 2) -> None:
-    """Runs every pool slice through the engine a few times, unmeasured: a
-    server that runs continuously has its staging memory, device arenas and
-    CUDA graphs in place; this brings a fresh process to that state."""
+def warm_up(dets, pools, rounds: int = 1) -> None:
+    """Runs every pool slice through the engine, unmeasured: a server that
+    runs continuously has its staging memory and device arenas in place;
+    this brings a fresh process to that state."""
     for _ in range(rounds):
         for i, det in enumerate(dets):
-            for t0, st in pools[i]:
-                _lib.trig_submit_slice(det, t0, st.hits, st.pmt_off)
+            for (t0, st, cont) in pools[i]:
+                _submit(det, t0, st, cont)
         for i, det in enumerate(dets):
             for _ in pools[i]:
                 r = _lib.trig_poll(det, 120_000)
@@ -36,22 +45,36 @@ def warm_up(dets, pools, rounds: int = 2) -> None:
                     raise RuntimeError(f"warm-up slice failed: {None if r is None else (r.status, r.flags)}")
 
 
-def replay(dets, pools, rate_factor: float, detector_seconds: float, slice_ns: int, seed: int = 0,
-           mode: int = 1, warmup_rounds: int = 2) -> dict:
+def _submit(det, t0, st, cont) -> int:
+    deferred = 0
+    while True:
+        try:
+            _lib.trig_submit_slice(det, t0, st.hits, st.pmt_off, is_continuation=cont)
+            return deferred
+        except _lib.TrigError as e:
+            if e.code != _lib.TRIG_EAGAIN:
+                raise
+            deferred += 1
+            time.sleep(0.0005)
+
+
+def replay(dets, pools, rate_factor, detector_seconds: float, slice_ns: int, seed: int = 0, mode: int = 1,
+           warmup_rounds: int = 1) -> dict:
     """dets[i] receives pools[i][k % len(pools[i])] as its k-th slice; the
     arrival gaps of each detector are exponential with mean
-    slice_ns / rate_factor (wall clock)."""
+    slice_ns / rate_factor (wall clock), or zero for rate_factor "sat"."""
     _lib.trig_engine_set_mode(mode)
     if warmup_rounds:
         warm_up(dets, pools, warmup_rounds)
     rng = np.random.Generator(np.random.PCG64(seed))
     n_per = max(1, int(round(detector_seconds * 1e9 / slice_ns)))
-    mean_gap = slice_ns * 1e-9 / rate_factor
+    saturate = rate_factor == "sat"
+    mean_gap = 0.0 if saturate else slice_ns * 1e-9 / float(rate_factor)
     events = []
     for i in range(len(dets)):
         t = 0.0
         for k in range(n_per):
-            t += rng.exponential(mean_gap)
+            t += rng.exponential(mean_gap) if mean_gap > 0 else 0.0
             events.append((t, i, k))
     events.sort()
     arrivals = {i: [0.0] * n_per for i in range(len(dets))}
@@ -71,26 +94,21 @@ def replay(dets, pools, rate_factor: float, detector_seconds: float, slice_ns: i
     threads = [threading.Thread(target=poller, args=(i,), daemon=True) for i in range(len(dets))]
     for th in threads:
         th.start()
+    _lib.trig_engine_trace(len(events) + 16)
     t_start = time.perf_counter()
     deferred = 0
     for (t, i, k) in events:
         now = time.perf_counter() - t_start
         if t > now:
             time.sleep(t - now)
-        t0, st = pools[i][k % len(pools[i])]
+        t0, st, cont = pools[i][k % len(pools[i])]
         arrivals[i][k] = t_start + t
-        while True:
-            try:
-                _lib.trig_submit_slice(dets[i], t0, st.hits, st.pmt_off)
-                break
-            except _lib.TrigError as e:
-                if e.code != _lib.TRIG_EAGAIN:
-                    raise
-                deferred += 1
-                time.sleep(0.0005)
+        deferred += _submit(dets[i], t0, st, cont)
     for th in threads:
         th.join()
     t_end = time.perf_counter()
+    trace = _lib.trig_engine_trace_read(len(events) + 16)
+    _lib.trig_engine_trace(0)
     lat_engine, lat_e2e, per_det = [], [], []
     hits = 0
     bad = 0
@@ -107,47 +125,116 @@ def replay(dets, pools, rate_factor: float, detector_seconds: float, slice_ns: i
             le.append((received[i][k] - arrivals[i][k]) * 1e3)
         lat_e2e += le
         per_det.append({"n_pmt": int(dets[i].n_pmt), "p50_ms": _pct(le, 50), "p99_ms": _pct(le, 99),
-                        "p999_ms": _pct(le, 99.9), "slices": len(le)})
+                        "p999_ms": _pct(le, 99.9), "max_ms": max(le) if le else float("nan"), "slices": len(le)})
     wall = t_end - t_start
     return {
         "rate_factor": rate_factor,
+        "mode": mode,
         "detector_seconds": detector_seconds,
         "slices": int(sum(len(x) for x in results.values())),
         "bad_status": int(bad),
         "errors": errors,
         "wall_s": wall,
         "hits_per_s": hits / wall if wall > 0 else 0.0,
+        "detector_s_per_wall_s": len(dets) * detector_seconds / wall if wall > 0 else 0.0,
         "p50_ms": _pct(lat_e2e, 50),
         "p99_ms": _pct(lat_e2e, 99),
         "p999_ms": _pct(lat_e2e, 99.9),
+        "max_ms": max(lat_e2e) if lat_e2e else float("nan"),
         "engine_p99_ms": _pct(lat_engine, 99),
         "budget_ms": slice_ns * 1e-6,
         "deferred_submits": deferred,
         "per_detector": per_det,
+        "trace": trace_summary(trace),
     }
+
+
+def trace_summary(tr: np.ndarray) -> dict:
+    """Where a slice's time goes, from the engine's records: submit (the
+    host-to-device copy, and the resident tail's update), queue (waiting for
+    a slot and a batch), device (the batch's kernels, CUDA events), readback
+    (the results' copy back after the counters) -- percentiles of each, and
+    the same parts for the slowest 0.1 % of slices."""
+    if len(tr) == 0:
+        return {}
+    ms = 1e-6
+    parts = {
+        "submit_ms": (tr["t_queued_ns"] - tr["t_submit_ns"]) * ms,
+        "queue_ms": (tr["t_launch_ns"] - tr["t_queued_ns"]) * ms,
+        "batch_ms": (tr["t_stats_ns"] - tr["t_launch_ns"]) * ms,
+        "readback_ms": (tr["t_done_ns"] - tr["t_stats_ns"]) * ms,
+        "total_ms": (tr["t_done_ns"] - tr["t_submit_ns"]) * ms,
+    }
+    dev = tr["device_ms"][tr["device_ms"] >= 0]
+    out = {name: {"p50": _pct(v, 50), "p99": _pct(v, 99), "p999": _pct(v, 99.9)} for name, v in parts.items()}
+    out["device_ms"] = {"p50": _pct(dev, 50), "p99": _pct(dev, 99), "p999": _pct(dev, 99.9)}
+    out["batch_slices"] = {"mean": float(np.mean(tr["batch_slices"])), "max": int(np.max(tr["batch_slices"]))}
+    out["batches"] = int(len(np.unique(tr["batch"])))
+    out["continuation_share"] = float(np.mean(tr["continuation"]))
+    tot = parts["total_ms"]
+    cut = np.percentile(tot, 99.9)
+    slow = tot >= cut
+    out["slowest"] = {name: float(np.mean(v[slow])) for name, v in parts.items()}
+    out["slowest"]["n_pmt"] = sorted(set(int(x) for x in tr["n_pmt"][slow]))
+    out["slowest"]["batch_slices"] = float(np.mean(tr["batch_slices"][slow]))
+    return out
 
 
 def _pct(v, q):
     return float(np.percentile(np.asarray(v), q)) if len(v) else float("nan")
 
 
+def make_pools(detectors, rates, pool: int, par: dict, seed: int = 0):
+    """Per detector: one contiguous run of `pool` slices (with muons), cut
+    into the pool's submissions in page-locked memory -- the first with
+    both halos, the others from t0 on (continuations)."""
+    import workload
+    S = par["slice_ns"]
+    H = workload.HALO_NS
+    pools = []
+    for i, (det, rate) in enumerate(zip(detectors, rates)):
+        t_origin = workload.T_ORIGIN_NS
+        full = workload.gen_stream(det, t_origin - H, t_origin + pool * S + H, rate, n_muons=10 * pool, seed=seed,
+                                   stream=5000 + i)
+        subs = []
+        for k in range(pool):
+            t0 = t_origin + k * S
+            st = workload.cut(full, t0 - H if k == 0 else t0, t0 + S + H)
+            subs.append((t0, workload.Stream(_lib.pinned_copy(st.hits), _lib.pinned_copy(st.pmt_off)), int(k > 0)))
+        del full
+        pools.append(subs)
+    return pools
+
+
+def _parse_run(text: str):
+    rate, mode, secs = text.split(":")
+    return (rate if rate == "sat" else float(rate)), int(mode), float(secs)
+
+
 def main():
     import workload
 
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
-    ap.add_argument("--rate", type=float, default=1.0, help="arrival rate in units of real time")
-    ap.add_argument("--detector-seconds", type=float, default=20.0)
-    ap.add_argument("--pool", type=int, default=4, help="pre-generated slices per detector")
-    ap.add_argument("--mode", type=int, default=1, help="0 plain per-slice launches, 1 continuous batching")
+    ap.add_argument("--runs", nargs="+", default=["4:1:60", "4:0:60", "1:1:30", "sat:1:20", "sat:0:20"],
+                    help="rate:mode:detector_seconds per run (rate in units of real time, or sat)")
+    ap.add_argument("--pool", type=int, default=20, help="contiguous pre-generated slices per detector")
     ap.add_argument("--seed", type=int, default=0)
     args = ap.parse_args()
     par = dict(workload.DEFAULT_PARAMS)
-    wl = workload.cfg_serving_pool(seed=args.seed, slices_per_det=args.pool)
-    dets = [_lib.Detector(g.xyz_mm, g.floor_id, par) for g in wl.detectors]
-    # the slice pools sit in page-locked host memory, as a DAQ front end's buffers would
-    pools = [[(s.t0, workload.Stream(_lib.pinned_copy(s.stream.hits), _lib.pinned_copy(s.stream.pmt_off)))
-              for s in wl.submissions if s.det_index == i] for i in range(len(dets))]
-    out = replay(dets, pools, args.rate, args.detector_seconds, par["slice_ns"], args.seed, args.mode)
+    spec = [(workload.nemo_tower(), 50e3), (workload.km3_tower(), 55e3), (workload.km3_tower(), 55e3),
+            (workload.tower_array(), 55e3)]
+    t = time.perf_counter()
+    pools = make_pools([d for d, _ in spec], [r for _, r in spec], args.pool, par, args.seed)
+    gen_s = time.perf_counter() - t
+    dets = [_lib.Detector(d.xyz_mm, d.floor_id, par) for d, _ in spec]
+    runs = []
+    for k, text in enumerate(args.runs):
+        rate, mode, secs = _parse_run(text)
+        runs.append(replay(dets, pools, rate, secs, par["slice_ns"], args.seed + k, mode))
+    out = {"detectors": "32@50kHz, 84@55kHz, 84@55kHz, 2688@55kHz", "pool_slices_per_detector": args.pool,
+           "pool_generation_s": gen_s, "continuation": "every pool slice after the first", "runs": runs}
+    for d in dets:
+        d.close()
     print(json.dumps(out))
 
 

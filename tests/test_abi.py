@@ -65,12 +65,15 @@ def test_binding_struct_sizes_match_header():
           "trig_array_out": _lib.trig_array_out}
     np_types = {"trig_hit": _lib.HIT_DTYPE, "trig_trigger": _lib.TRIGGER_DTYPE, "trig_window": _lib.WINDOW_DTYPE,
                 "trig_slice_stats": _lib.STATS_DTYPE, "trig_array_seed": _lib.ASEED_DTYPE,
-                "trig_array_stats": _lib.ASTATS_DTYPE}
+                "trig_array_stats": _lib.ASTATS_DTYPE, "trig_trace_rec": _lib.TRACE_DTYPE}
     c_names = {"trig_hit": ["t_ns", "pmt", "charge", "reserved"], "trig_trigger": ["t_ns", "pmt", "charge", "count"],
                "trig_window": ["lo_ns", "hi_ns", "n_hits", "n_triggers"],
                "trig_slice_stats": ["status", "flags", "n_hits", "n_seeds", "n_triggers", "n_windows", "n_events"],
                "trig_array_seed": ["t_ns", "pmt", "tower", "n_towers"],
-               "trig_array_stats": ["n_tower_triggers", "n_selected", "n_windows", "n_hits", "flags", "status"]}
+               "trig_array_stats": ["n_tower_triggers", "n_selected", "n_windows", "n_hits", "flags", "status"],
+               "trig_trace_rec": ["slice_id", "batch", "batch_slices", "n_pmt", "n_hits", "status", "continuation",
+                                  "t_submit_ns", "t_queued_ns", "t_launch_ns", "t_stats_ns", "t_done_ns", "device_ms",
+                                  "reserved"]}
     lay = _c_layout({**{k: [f for f, _ in v._fields_] for k, v in ct.items()}, **c_names})
     for name, cls in ct.items():
         assert ctypes.sizeof(cls) == lay[name], name
