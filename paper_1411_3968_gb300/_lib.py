@@ -128,11 +128,13 @@ _lib = None
 
 
 def load(path: str | None = None):
-    """Load libtrig.so (built by __graft_entry__.build() or build.build())."""
+    """Load libtrig.so (built by __graft_entry__.build() or build.build());
+    the environment variable TRIG_LIB names another build of it (a checked
+    or instrumented one)."""
     global _lib
     if _lib is not None:
         return _lib
-    p = path or LIB_PATH
+    p = path or os.environ.get("TRIG_LIB") or LIB_PATH
     if not os.path.exists(p):
         raise ImportError(f"libtrig.so not built at {p}; run __graft_entry__.build()")
     lib = ctypes.CDLL(p)

@@ -16,9 +16,12 @@ constexpr uint32_t kSmemDtMaxPmt = 96;      // dt table lives in shared memory u
 constexpr uint32_t kWideMinPmt = 129;       // from this P on, slices are staged from a bucketed copy
 constexpr uint32_t kBktChunk = 1024;        // buckets per block of the bucket scan
 // A tile plus its halos spans less than 2^20 ns, so a hit's time within the
-// staged range and its PMT (< 2^12) pack into 32 bits.
+// staged range and its PMT (< 2^12) pack into 32 bits.  The limit keeps
+// 65536 ns (more than any dt, <= 60000 ns) between the last staged time and
+// 2^20 - 1, the time of the end keys that the causal count may read past
+// the last key.
 constexpr uint32_t kTileSpanBits = 20;
-constexpr int64_t kMaxTileSpan = ((int64_t)1 << kTileSpanBits) - 1;
+constexpr int64_t kMaxTileSpan = ((int64_t)1 << kTileSpanBits) - 65536;
 constexpr uint64_t kMaxSliceHits = 0xFFFFFFF0ull;
 
 // Detector tables resident on the device (owned by trig_detector).

@@ -685,12 +685,13 @@ struct ItemInfo {
 // Shared memory of the tile kernel, in this order: the staging buffers of
 // CAP 16-byte records (two, or one for the 2048-hit tile: its tile pass
 // hands the buffer back once it has read it, so the next tile's copy
-// overlaps the rest of the pass, and two blocks of it then fit on an SM); the tile's packed keys in merged order (+16 bytes:
-// the causal count reads 16 bytes at a time past the last key); the keys in
-// bucket order (reused as the seed list and seed counts once merged); the
-// charges in bucket order and in merged order; the bucket offsets; the seed
-// mask; the PMT tables (floor, row maximum of dt, and dt itself when the
-// detector's table fits).
+// overlaps the rest of the pass, and two blocks of it then fit on an SM);
+// the tile's packed keys in merged order (+16 bytes: four end keys that the
+// causal count's 16-byte loads may read past the last key); the keys in
+// bucket order (reused for the seed rounds' lists, then the seed list and
+// seed counts); the charges in bucket order and in merged order; the floor
+// of each merged key; the bucket offsets; the seed mask; the PMT tables
+// (floor, row maximum of dt, and dt itself when the detector's table fits).
 template <int CAP>
 struct TileLayout {
     static constexpr int NBK = CAP;                        // time buckets of the in-tile merge
@@ -699,13 +700,15 @@ struct TileLayout {
     static constexpr size_t kPkS = (size_t)CAP * 4 + 16;
     static constexpr size_t kPkB = (size_t)CAP * 4;
     static constexpr size_t kChg = (size_t)CAP * 2;
+    static constexpr size_t kFlk = (size_t)CAP * 2;
     static constexpr size_t kCnt = (size_t)(NBK + 1) * 4;
     static constexpr size_t kMask = (size_t)(CAP / 32) * 4;
     static constexpr size_t oPkS = NS * kStage;
     static constexpr size_t oPkB = oPkS + kPkS;
     static constexpr size_t oChgB = oPkB + kPkB;
     static constexpr size_t oChgS = oChgB + kChg;
-    static constexpr size_t oCnt = oChgS + kChg;
+    static constexpr size_t oFlk = oChgS + kChg;
+    static constexpr size_t oCnt = oFlk + kFlk;
     static constexpr size_t oMask = oCnt + kCnt;
     static constexpr size_t oTab = (oMask + kMask + 15) & ~(size_t)15;
     static size_t bytes(uint32_t P, bool smem_dt)
@@ -742,6 +745,9 @@ struct TileCtx {
     }
     __device__ __forceinline__ uint16_t *chg_b() const { return reinterpret_cast<uint16_t *>(g_tile_smem + L::oChgB); }
     __device__ __forceinline__ uint16_t *chg_s() const { return reinterpret_cast<uint16_t *>(g_tile_smem + L::oChgS); }
+    __device__ __forceinline__ uint16_t *flk() const { return reinterpret_cast<uint16_t *>(g_tile_smem + L::oFlk); }
+    // per-warp lists of the seed rounds (the bucket-order key region, free then)
+    __device__ __forceinline__ uint16_t *live() const { return reinterpret_cast<uint16_t *>(g_tile_smem + L::oPkB); }
     __device__ __forceinline__ uint32_t *cnt() const { return reinterpret_cast<uint32_t *>(g_tile_smem + L::oCnt); }
     __device__ __forceinline__ uint32_t *mask() const { return reinterpret_cast<uint32_t *>(g_tile_smem + L::oMask); }
     __device__ __forceinline__ uint16_t *floor_s() const { return reinterpret_cast<uint16_t *>(g_tile_smem + L::oTab); }
@@ -1004,19 +1010,19 @@ __device__ __forceinline__ void count_causal(const TileCtx<CAP> &cx, const uint3
                     const uint32_t lim = SMEM_DT ? (uint32_t)row_s[pj] : (uint32_t)__ldg(row_g + pj);
                     return (tj > ts ? tj - ts : ts - tj) <= lim;
                 };
-                // each lane takes four consecutive keys per 16-byte load (from
-                // j0 rounded down to a multiple of 4, inside the CAP-entry key
-                // array); positions outside [j0, j1) use the seed's own key,
-                // which is never looked up out of range, and are not counted
+                // each lane takes four consecutive keys per 16-byte load, from
+                // j0 rounded down to a multiple of 4.  No key outside
+                // [j0, j1) can pass: those before j0 lie in earlier buckets,
+                // more than dmax_row(p_s) >= dt before t_s, those from j1 on
+                // in later buckets, and the four end keys past the last key
+                // (time 2^20 - 1, PMT 0) are beyond any dt as well
                 uint32_t ca = 0, cb = 0, cc = 0, cd = 0;
                 for (uint32_t q = (j0 & ~3u) + 4 * gl; q < j1; q += 4 * G) {
                     const uint4 v = *reinterpret_cast<const uint4 *>(pk + q);
-                    const bool m0 = q >= j0, m1 = q + 1 >= j0 && q + 1 < j1;
-                    const bool m2 = q + 2 >= j0 && q + 2 < j1, m3 = q + 3 < j1;
-                    ca += m0 & causal(m0 ? v.x : ks);
-                    cb += m1 & causal(m1 ? v.y : ks);
-                    cc += m2 & causal(m2 ? v.z : ks);
-                    cd += m3 & causal(m3 ? v.w : ks);
+                    ca += causal(v.x);
+                    cb += causal(v.y);
+                    cc += causal(v.z);
+                    cd += causal(v.w);
                 }
                 c = ca + cb + cc + cd;
             }
@@ -1049,35 +1055,36 @@ __device__ __forceinline__ uint32_t bucket_shift(uint32_t span)
 //     in its time bucket (t - tb) >> bsh; the stage buffer is then handed
 //     back to the producer (release_bar), the rest works on the keys;
 //  B. bucket offsets (exclusive scan of the counts);
-//  C. keys (and charges) scattered to bucket order: the k-way merge of the
-//     PMT runs ("DAQ system of NEMO Phase II") down to time buckets of
-//     2^bsh ns, about one key per bucket.  Builds that need the full (t,
-//     pmt, charge) order (SORT: the extended rules, row outputs, event
-//     extraction) then rank each key inside its bucket;
-//  D. seeds ("Sorting and triggering in GPU"): a charge over q_seed, or
-//     another PMT of the same floor within tau.  Each key walks forward
-//     through the keys that follow it while they can be within tau (in
-//     bucket order: to the end of the bucket holding t + tau), so every
-//     pair is seen once and both hits of a pair are marked; seed rule 1
-//     and level 0 (SORT builds) test each core hit instead;
-//  E. the seed list; F. the causal count of every seed over whole buckets
-//     of its scan range, each key tested exactly ("Muon trigger
-//     strategy"); G. the fired seeds, in (t, pmt, charge) order, to out.
+//  C. the k-way merge of the PMT runs ("DAQ system of NEMO Phase II"):
+//     keys (and charges) scattered to their bucket, about one per bucket,
+//     then ranked inside it by (t, pmt, charge); each merged key's floor is
+//     kept beside it, and charge seeds of the core are marked;
+//  D. floor coincidences ("Sorting and triggering in GPU": another PMT of
+//     the same floor within tau) in rounds: round r checks the pair
+//     (i, i + r) of every key i still live, live meaning that keys
+//     i + 1 .. i + r - 1 all lie within tau of it; both hits of a pair are
+//     marked, every pair is checked once, and each warp keeps its own list
+//     of live keys, so its lanes stay busy.  Seed rule 1 and level 0 (EXT
+//     builds) test each core key instead;
+//  E. the ordered seed list; F. the causal count of every seed over whole
+//     buckets of its scan range, each key tested exactly ("Muon trigger
+//     strategy"); G. the fired seeds, in merged order, to out.
 //
-// Returns the counts and c0 = the number of staged keys before the core.
-// cnt and mask are zero on entry and on return.
+// Returns the counts and c0 = the number of staged keys before the core
+// (the core is keys [c0, c1) of the merged order).  cnt and mask are zero
+// on entry and on return.
 template <int CAP, int NC, bool SMEM_DT, bool EXT, bool DENSE>
 __device__ CoreOut tile_pass(TileCtx<CAP> &cx, const uint64_t *stage, uint32_t n, int64_t tb, uint32_t span,
                              uint32_t lo_t, uint32_t hi_t, const TrigParams &tp, trig_trigger *out, bool out_at_c0,
                              int64_t dbg_rank_lo, uint64_t *release_bar)
 {
-    constexpr bool SORT = EXT;
     constexpr uint32_t NW = NC / 32;
     constexpr int PER = CAP / NC;
     const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
     const uint32_t bsh = bucket_shift<CAP>(span);
+    const uint32_t tau = tp.tau;
     __shared__ uint32_t s_red[NW + 1];
-    __shared__ uint32_t s_below[2];
+    __shared__ uint32_t s_below[3];
     __shared__ uint32_t s_tot[2 * NW];
     uint32_t *cnt = cx.cnt();
     uint32_t *mask = cx.mask();
@@ -1095,9 +1102,10 @@ __device__ CoreOut tile_pass(TileCtx<CAP> &cx, const uint64_t *stage, uint32_t n
 #define PHASE_MARK(i) ((void)0)
 #endif
 
-    // A. keys and bucket counts
+    // A. keys and bucket counts; keys before the core, before its end, and
+    //    too early to pair with a core key (t + tau < lo_t)
     uint32_t key[PER], cs[PER];           // packed key; charge << 16 | slot in the bucket
-    uint32_t below_lo = 0, below_hi = 0;
+    uint32_t below_lo = 0, below_hi = 0, below_w = 0;
 #pragma unroll
     for (int r = 0; r < PER; ++r) {
         const uint32_t i = tid + r * NC;
@@ -1112,15 +1120,18 @@ __device__ CoreOut tile_pass(TileCtx<CAP> &cx, const uint64_t *stage, uint32_t n
             cs[r] = (v.z & 0xffff0000u) | slot;
             below_lo += tr < lo_t;
             below_hi += tr < hi_t;
+            below_w += tr + tau < lo_t;
         }
     }
     below_lo = __reduce_add_sync(0xffffffffu, below_lo);
     below_hi = __reduce_add_sync(0xffffffffu, below_hi);
-    if (tid == 0) s_below[0] = s_below[1] = 0;
+    below_w = __reduce_add_sync(0xffffffffu, below_w);
+    if (tid == 0) s_below[0] = s_below[1] = s_below[2] = 0;
     cons_sync<NC>();
     if (lane == 0) {
         if (below_lo) atomicAdd(&s_below[0], below_lo);
         if (below_hi) atomicAdd(&s_below[1], below_hi);
+        if (below_w) atomicAdd(&s_below[2], below_w);
     }
     // the stage buffer has been read: order those reads before the
     // producer's next bulk copy into it, then hand it back
@@ -1130,62 +1141,55 @@ __device__ CoreOut tile_pass(TileCtx<CAP> &cx, const uint64_t *stage, uint32_t n
     //    every read of the stage buffer)
     cons_exclusive_scan<NC>(cnt, TileLayout<CAP>::NBK, s_red);
     if (release_bar && tid == 0) mbar_arrive(release_bar);
-    const uint32_t c0 = s_below[0], c1 = s_below[1];
+    const uint32_t c0 = s_below[0], c1 = s_below[1], d_lo = s_below[2];
     PHASE_MARK(kPhA);
 
-    // C. bucket order (the final order of the default rule); charge seeds
-    //    of the core are marked where their keys land
-    uint32_t *pk = cx.pk_s();
-    uint16_t *chg = cx.chg_s();
-    uint32_t *pk_c = SORT ? cx.pk_b() : pk;
-    uint16_t *chg_c = SORT ? cx.chg_b() : chg;
+    // C. bucket order, then the rank inside the bucket by (t, pmt, charge),
+    //    then position
+    uint32_t *pk = cx.pk_s(), *pk_b = cx.pk_b();
+    uint16_t *chg = cx.chg_s(), *chg_b = cx.chg_b(), *flk = cx.flk();
+    const uint16_t *fl = cx.floor_s();
     const bool charge_rule = !(EXT && tp.seed_rule == 1);
 #pragma unroll
     for (int r = 0; r < PER; ++r) {
         if (key[r] != kPkNone) {
-            const uint32_t tr = key[r] >> 12;
-            const uint32_t pos = cnt[bucket_of<CAP>(tr, bsh)] + (cs[r] & 0xffffu);
+            const uint32_t pos = cnt[bucket_of<CAP>(key[r] >> 12, bsh)] + (cs[r] & 0xffffu);
             if (CHECK(22, pos, CAP)) {
-                pk_c[pos] = key[r];
-                chg_c[pos] = (uint16_t)(cs[r] >> 16);
-                if (!SORT && charge_rule && (cs[r] >> 16) >= tp.q_seed && tr >= lo_t && tr < hi_t)
-                    atomicOr(&mask[pos >> 5], 1u << (pos & 31u));
+                pk_b[pos] = key[r];
+                chg_b[pos] = (uint16_t)(cs[r] >> 16);
             }
+        }
+    }
+    if (tid < 4) pk[n + tid] = 0xfffff000u;           // end keys (time 2^20 - 1, PMT 0)
+    cons_sync<NC>();
+    PHASE_MARK(kPhB);
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+        const uint32_t k = key[r];
+        if (k == kPkNone) continue;
+        const uint32_t b = bucket_of<CAP>(k >> 12, bsh);
+        const uint32_t s0 = cnt[b], s1 = cnt[b + 1], q = cs[r] >> 16, pos = s0 + (cs[r] & 0xffffu);
+        uint32_t rk = s0;
+        for (uint32_t m = s0; m < s1; ++m) {
+            const uint32_t o = pk_b[m];
+            rk += o < k;
+            if (o == k) {                          // equal time and PMT: charge, then position
+                const uint32_t oq = chg_b[m];
+                rk += oq < q || (oq == q && m < pos);
+            }
+        }
+        if (CHECK(23, rk, CAP)) {
+            pk[rk] = k;
+            chg[rk] = (uint16_t)q;
+            flk[rk] = fl[k & 0xfffu];
+            const uint32_t tr = k >> 12;
+            if (charge_rule && q >= tp.q_seed && tr >= lo_t && tr < hi_t) atomicOr(&mask[rk >> 5], 1u << (rk & 31u));
         }
     }
     cons_sync<NC>();
-    PHASE_MARK(kPhB);
-    if (SORT) {
-        // the rank inside the bucket by (t, pmt, charge), then position
-#pragma unroll
-        for (int r = 0; r < PER; ++r) {
-            const uint32_t k = key[r];
-            if (k == kPkNone) continue;
-            const uint32_t b = bucket_of<CAP>(k >> 12, bsh);
-            const uint32_t s0 = cnt[b], s1 = cnt[b + 1], q = cs[r] >> 16, pos = s0 + (cs[r] & 0xffffu);
-            uint32_t rk = s0;
-            for (uint32_t m = s0; m < s1; ++m) {
-                const uint32_t o = pk_c[m];
-                rk += o < k;
-                if (o == k) {                      // equal time and PMT: charge, then position
-                    const uint32_t oq = chg_c[m];
-                    rk += oq < q || (oq == q && m < pos);
-                }
-            }
-            if (CHECK(23, rk, CAP)) {
-                pk[rk] = k;
-                chg[rk] = (uint16_t)q;
-                const uint32_t tr = k >> 12;
-                if (charge_rule && q >= tp.q_seed && tr >= lo_t && tr < hi_t)
-                    atomicOr(&mask[rk >> 5], 1u << (rk & 31u));
-            }
-        }
-        cons_sync<NC>();
-    }
     PHASE_MARK(kPhC);
 
-    // D. seed flags of the core keys [c0, c1) (in bucket order the core is
-    //    the keys whose time is in [lo_t, hi_t))
+    // D. seed flags of the core keys [c0, c1)
     const uint32_t P = cx.P;
     if (EXT && tp.seed_rule == 1) {
         for (uint32_t base = c0 & ~31u; base < c1; base += NC) {
@@ -1195,35 +1199,57 @@ __device__ CoreOut tile_pass(TileCtx<CAP> &cx, const uint64_t *stage, uint32_t n
             if (lane == 0 && m) atomicOr(&mask[(base >> 5) + warp], m);
         }
     } else {
-        const uint32_t tau = tp.tau;
-        const uint16_t *fl = cx.floor_s();
-        for (uint32_t base = 0; base < n; base += NC) {
-            const uint32_t i = base + tid;
-            bool mine = false;
-            if (i < n) {
-                const uint32_t ki = pk[i], ti = ki >> 12;
-                if (ti + tau >= lo_t && ti < hi_t + tau) {
-                    const uint32_t pi = ki & 0xfffu;
-                    const uint32_t fi = fl[pi];
-                    const bool ci = ti >= lo_t && ti < hi_t;
-                    // the walk ends after the keys that can be within tau:
-                    // sorted, the first later than t + tau; in bucket
-                    // order, the first past the bucket holding t + tau
-                    const uint32_t stop = SORT ? ti + tau : (bucket_of<CAP>(ti + tau, bsh) + 1) << bsh;
-                    for (uint32_t j = i + 1; j < n; ++j) {
-                        const uint32_t kj = pk[j], tj = kj >> 12;
-                        if (SORT ? tj > stop : tj >= stop) break;
-                        const uint32_t pj = kj & 0xfffu;
-                        const uint32_t d = tj > ti ? tj - ti : ti - tj;
-                        if (d <= tau && pj != pi && fl[pj] == fi) {
-                            mine |= ci;
-                            if (tj >= lo_t && tj < hi_t) atomicOr(&mask[j >> 5], 1u << (j & 31u));
+        // the keys [d_lo, c1) can pair with a core key; warp w takes a
+        // contiguous share of them
+        const uint32_t lt = (1u << lane) - 1u;
+        const uint32_t d_n = c1 > d_lo ? c1 - d_lo : 0u;
+        const uint32_t share = ((d_n + NW - 1) / NW + 31u) & ~31u;
+        const uint32_t w_begin = min(d_lo + warp * share, c1), w_end = min(w_begin + share, c1);
+        uint16_t *live = cx.live() + warp * (CAP / NW);
+        auto pair = [&](uint32_t i, uint32_t j, uint32_t ki, uint32_t kj) {
+            if ((ki & 0xfffu) != (kj & 0xfffu) && flk[i] == flk[j]) {
+                if (i >= c0 && i < c1) atomicOr(&mask[i >> 5], 1u << (i & 31u));
+                if (j >= c0 && j < c1) atomicOr(&mask[j >> 5], 1u << (j & 31u));
+            }
+        };
+        uint32_t nlive = 0;
+        for (uint32_t x = w_begin; x < w_end; x += 32) {
+            const uint32_t i = x + lane;
+            bool alive = false;
+            if (i < w_end) {                       // i + 1 <= c1 <= n: an end key at worst
+                const uint32_t ki = pk[i], kj = pk[i + 1];
+                if ((kj >> 12) - (ki >> 12) <= tau && i + 1 < n) {
+                    alive = true;
+                    pair(i, i + 1, ki, kj);
+                }
+            }
+            const uint32_t m = __ballot_sync(0xffffffffu, alive);
+            if (alive) live[nlive + __popc(m & lt)] = (uint16_t)i;
+            nlive += __popc(m);
+        }
+        for (uint32_t d = 2; nlive; ++d) {
+            uint32_t next = 0;
+            for (uint32_t x = 0; x < nlive; x += 32) {
+                bool alive = false;
+                uint32_t i = 0;
+                if (x + lane < nlive) {
+                    i = live[x + lane];
+                    const uint32_t j = i + d;
+                    if (j < n) {
+                        const uint32_t ki = pk[i], kj = pk[j];
+                        if ((kj >> 12) - (ki >> 12) <= tau) {
+                            alive = true;
+                            pair(i, j, ki, kj);
                         }
                     }
                 }
+                // the ballot orders this batch's reads of the list before
+                // the writes below (which land at or before x + 31)
+                const uint32_t m = __ballot_sync(0xffffffffu, alive);
+                if (alive) live[next + __popc(m & lt)] = (uint16_t)i;
+                next += __popc(m);
             }
-            const uint32_t m = __ballot_sync(0xffffffffu, mine);
-            if (lane == 0 && m) atomicOr(&mask[(base >> 5) + warp], m);
+            nlive = next;
         }
     }
     cons_sync<NC>();
@@ -1241,49 +1267,34 @@ __device__ CoreOut tile_pass(TileCtx<CAP> &cx, const uint64_t *stage, uint32_t n
     }
     PHASE_MARK(kPhD);
 
-    // E. ordered seed list: warp w expands a contiguous group of mask words;
-    //    each warp adds up the totals of the warps before it
+    // E. ordered seed list: thread x takes mask word w_lo + x (at most
+    //    CAP / 32 <= NC words); each word's offset adds the totals of the
+    //    warps before it
     uint16_t *seed_idx = cx.seed_idx(), *seed_cnt = cx.seed_cnt();
-    // marks lie in the core: sorted, positions [c0, c1); in bucket order,
-    // the buckets of [lo_t, hi_t)
-    const uint32_t p_lo = SORT ? c0 : cnt[bucket_of<CAP>(lo_t, bsh)];
-    const uint32_t p_hi = SORT ? c1 : cnt[bucket_of<CAP>(hi_t > 0 ? hi_t - 1 : 0, bsh) + 1];
-    const uint32_t w_lo = p_lo >> 5, w_hi = (p_hi + 31) >> 5;
+    const uint32_t w_lo = c0 >> 5, w_hi = (c1 + 31) >> 5;
     const uint32_t nwords = w_hi - w_lo;
-    const uint32_t wpw = (nwords + NW - 1) / NW;          // words per warp
+    const uint32_t nw_used = (nwords + 31) >> 5;
     uint32_t *wtot = s_tot;                               // [NW]
-    uint32_t ns;
+    uint32_t ns = 0;
     {
-        uint32_t pc = 0;
-        for (uint32_t x = 0; x < wpw; x += 32) {
-            const uint32_t w = w_lo + warp * wpw + x + lane;
-            if (x + lane < wpw && w < w_hi) pc += __popc(mask[w]);
-        }
-        pc = __reduce_add_sync(0xffffffffu, pc);
-        if (lane == 0) wtot[warp] = pc;
+        const uint32_t m = tid < nwords ? mask[w_lo + tid] : 0u;
+        const uint32_t c = __popc(m);
+        const uint32_t incl = warp < nw_used ? warp_incl_scan(c) : 0u;
+        if (warp < nw_used && lane == 31) wtot[warp] = incl;
         cons_sync<NC>();
-        uint32_t pos = 0;
-        ns = 0;
-#pragma unroll
-        for (uint32_t w2 = 0; w2 < NW; ++w2) {
+        uint32_t before = 0;
+        for (uint32_t w2 = 0; w2 < nw_used; ++w2) {
             const uint32_t v = wtot[w2];
-            pos += w2 < warp ? v : 0u;
+            before += w2 < warp ? v : 0u;
             ns += v;
         }
-        for (uint32_t x = 0; x < wpw; x += 32) {
-            const uint32_t w = w_lo + warp * wpw + x + lane;
-            const uint32_t m = (x + lane < wpw && w < w_hi) ? mask[w] : 0u;
-            const uint32_t c = __popc(m);
-            const uint32_t incl = warp_incl_scan(c);
-            uint32_t at = pos + incl - c;
-            uint32_t mm = m;
-            while (mm) {
-                const uint32_t bit = __ffs(mm) - 1;
-                mm &= mm - 1;
-                if (CHECK(2, at, CAP)) seed_idx[at] = (uint16_t)(w * 32 + bit);
-                ++at;
-            }
-            pos += __shfl_sync(0xffffffffu, incl, 31);
+        uint32_t at = before + incl - c;
+        uint32_t mm = m;
+        while (mm) {
+            const uint32_t bit = __ffs(mm) - 1;
+            mm &= mm - 1;
+            if (CHECK(2, at, CAP)) seed_idx[at] = (uint16_t)((w_lo + tid) * 32 + bit);
+            ++at;
         }
     }
     cons_sync<NC>();
@@ -1301,9 +1312,7 @@ __device__ CoreOut tile_pass(TileCtx<CAP> &cx, const uint64_t *stage, uint32_t n
     PHASE_MARK(kPhF);
 
     // G. emit the fired seeds in order: warp w takes a contiguous range of
-    //    the seed list and adds up the fired totals of the warps before it.
-    //    In bucket order a fired seed's rank also counts the fired seeds of
-    //    its bucket (adjacent in the list) with a smaller (t, pmt, charge).
+    //    the seed list and adds up the fired totals of the warps before it
     const uint32_t threshold = tp.threshold;
     const uint32_t per_w = (ns + NW - 1) / NW;
     const uint32_t k_begin = min(ns, warp * per_w), k_end = min(ns, k_begin + per_w);
@@ -1330,38 +1339,21 @@ __device__ CoreOut tile_pass(TileCtx<CAP> &cx, const uint64_t *stage, uint32_t n
         if (fired) {
             const uint32_t i = seed_idx[k];
             const uint32_t ks = pk[i];
-            const uint32_t q = chg[i];
-            uint32_t o_ = F + __popc(m & ((1u << lane) - 1u));
-            if (!SORT) {
-                // fired seeds of the same bucket before k that order after
-                // it, and after k that order before it
-                const uint32_t bk = bucket_of<CAP>(ks >> 12, bsh);
-                const uint64_t key_k = ((uint64_t)ks << 16) | q;
-                for (uint32_t k2 = k; k2-- > 0;) {
-                    const uint32_t i2 = seed_idx[k2];
-                    if (bucket_of<CAP>(pk[i2] >> 12, bsh) != bk) break;
-                    if (seed_cnt[k2] >= threshold && (((uint64_t)pk[i2] << 16) | chg[i2]) > key_k) --o_;
-                }
-                for (uint32_t k2 = k + 1; k2 < ns; ++k2) {
-                    const uint32_t i2 = seed_idx[k2];
-                    if (bucket_of<CAP>(pk[i2] >> 12, bsh) != bk) break;
-                    if (seed_cnt[k2] >= threshold && (((uint64_t)pk[i2] << 16) | chg[i2]) < key_k) ++o_;
-                }
-            }
             trig_trigger tr;
             tr.t_ns = tb + (int64_t)(ks >> 12);
             tr.pmt = (uint16_t)(ks & 0xfffu);
-            tr.charge = (uint16_t)q;
+            tr.charge = chg[i];
             tr.count = seed_cnt[k];
+            const uint32_t o_ = F + __popc(m & ((1u << lane) - 1u));
             if (CHECK(3, o_, c1 - c0)) dst[o_] = tr;
         }
         F += __popc(m);
     }
-    // optional row outputs (SORT builds): the merged core rows
-    // (verification, and the merged stream of event extraction) and each
-    // row's causal count (verification only); rows are indexed by merged
-    // rank minus the rank of the slice's first owned hit
-    if (SORT && tp.dbg_merged) {
+    // optional row outputs: the merged core rows (verification, and the
+    // merged stream of event extraction) and each row's causal count
+    // (verification only); rows are indexed by merged rank minus the rank
+    // of the slice's first owned hit
+    if (tp.dbg_merged) {
         const uint64_t dbg_base = (uint64_t)(dbg_rank_lo + (int64_t)c0);
         for (uint32_t i = tid; i < c1 - c0; i += NC) {
             const uint32_t k = pk[c0 + i];
