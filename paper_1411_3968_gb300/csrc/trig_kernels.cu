@@ -1037,6 +1037,83 @@ __device__ __forceinline__ void count_causal(const TileCtx<CAP> &cx, const uint3
     }
 }
 
+// Causal count with the work of a warp's seeds spread evenly over its
+// lanes (the default rule): warp w takes a contiguous range of the seed
+// list in batches of 32 seeds, one per lane; each lane finds its seed's
+// scan range [j0, j1) (seed_range) and the number of 4-key vectors from j0
+// rounded down to a multiple of 4.  The batch's vectors are cut into 32
+// equal contiguous chunks, one per lane; a lane walks its chunk from seed to
+// seed and adds each partial count into the seed's counter (shared
+// atomics).  No key outside [j0, j1) passes the test (see count_causal), so
+// whole vectors are tested.  tab holds the warp's batch: seed key, first
+// vector position and inclusive vector prefix.
+template <int CAP, int NC, bool SMEM_DT>
+__device__ __forceinline__ void count_flat(const TileCtx<CAP> &cx, const uint32_t *pk, uint32_t ns,
+                                           const uint16_t *seed_idx, uint32_t bsh, uint32_t *seed_c, uint2 *tab_all)
+{
+    constexpr uint32_t NW = NC / 32;
+    const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+    uint2 *tab = tab_all + warp * 32;
+    const uint32_t per_w = (ns + NW - 1) / NW;
+    const uint32_t s_begin = min(ns, warp * per_w), s_end = min(ns, s_begin + per_w);
+    for (uint32_t sb = s_begin; sb < s_end; sb += 32) {
+        const uint32_t k = sb + lane;
+        uint32_t ks = 0, a = 0, nv = 0;
+        if (k < s_end) {
+            ks = pk[seed_idx[k]];
+            uint32_t j0, j1;
+            seed_range<CAP>(cx, ks >> 12, ks & 0xfffu, bsh, j0, j1);
+            a = j0 & ~3u;
+            nv = j1 > a ? (j1 - a + 3u) >> 2 : 0u;
+            seed_c[k] = 0;
+        }
+        const uint32_t incl = warp_incl_scan(nv);
+        tab[lane] = make_uint2(ks, (a << 16) | incl);       // a < 2^12, incl < 2^16
+        const uint32_t V = __shfl_sync(0xffffffffu, incl, 31);
+        __syncwarp();
+        const uint32_t v0 = (uint32_t)(((uint64_t)V * lane) >> 5);
+        const uint32_t v1 = (uint32_t)(((uint64_t)V * (lane + 1)) >> 5);
+        // the seed of v0: the first entry whose inclusive prefix exceeds it
+        uint32_t cur = 0;
+#pragma unroll
+        for (uint32_t step = 16; step; step >>= 1) {
+            const uint32_t at = cur + step - 1;
+            if ((tab[at].y & 0xffffu) <= v0) cur += step;
+        }
+        if (v0 < v1) {
+            uint2 e = tab[cur];
+            uint32_t end_v = e.y & 0xffffu, base_v = cur ? (tab[cur - 1].y & 0xffffu) : 0u;
+            uint32_t ts = e.x >> 12, q0 = e.y >> 16;
+            const uint16_t *row_s = cx.dt_s() + (e.x & 0xfffu) * cx.P;
+            const uint16_t *row_g = cx.dt_g + (e.x & 0xfffu) * cx.P;
+            uint32_t c = 0;
+            for (uint32_t v = v0; v < v1; ++v) {
+                while (v >= end_v) {
+                    if (c) atomicAdd(&seed_c[sb + cur], c);
+                    c = 0;
+                    ++cur;
+                    e = tab[cur];
+                    base_v = end_v;
+                    end_v = e.y & 0xffffu;
+                    ts = e.x >> 12;
+                    q0 = e.y >> 16;
+                    row_s = cx.dt_s() + (e.x & 0xfffu) * cx.P;
+                    row_g = cx.dt_g + (e.x & 0xfffu) * cx.P;
+                }
+                const uint4 w = *reinterpret_cast<const uint4 *>(pk + q0 + 4u * (v - base_v));
+                auto causal = [&](uint32_t kj) -> uint32_t {
+                    const uint32_t tj = kj >> 12, pj = kj & 0xfffu;
+                    const uint32_t lim = SMEM_DT ? (uint32_t)row_s[pj] : (uint32_t)__ldg(row_g + pj);
+                    return (tj > ts ? tj - ts : ts - tj) <= lim;
+                };
+                c += causal(w.x) + causal(w.y) + causal(w.z) + causal(w.w);
+            }
+            if (c) atomicAdd(&seed_c[sb + cur], c);
+        }
+        __syncwarp();
+    }
+}
+
 // Bucket shift of a staged range of `span` ns: buckets of 2^bsh ns, NBK of
 // them cover the range.
 template <int CAP>
@@ -1056,28 +1133,30 @@ __device__ __forceinline__ uint32_t bucket_shift(uint32_t span)
 //     back to the producer (release_bar), the rest works on the keys;
 //  B. bucket offsets (exclusive scan of the counts);
 //  C. the k-way merge of the PMT runs ("DAQ system of NEMO Phase II"):
-//     keys (and charges) scattered to their bucket, about one per bucket,
-//     then ranked inside it by (t, pmt, charge); each merged key's floor is
-//     kept beside it, and charge seeds of the core are marked;
+//     keys, charges and floors scattered to their bucket, about one key per
+//     bucket.  For the default rule that bucket order is the final order;
+//     the builds with the extended rules, row outputs and event extraction
+//     (SORT) also rank each key inside its bucket by (t, pmt, charge);
 //  D. floor coincidences ("Sorting and triggering in GPU": another PMT of
-//     the same floor within tau) in rounds: round r checks the pair
-//     (i, i + r) of every key i still live, live meaning that keys
-//     i + 1 .. i + r - 1 all lie within tau of it; both hits of a pair are
-//     marked, every pair is checked once, and each warp keeps its own list
-//     of live keys, so its lanes stay busy.  Seed rule 1 and level 0 (EXT
-//     builds) test each core key instead;
+//     the same floor within tau), in rounds: round r checks the pair
+//     (i, i + r) of every key i still live.  Sorted, a key stays live while
+//     its next keys lie within tau; in bucket order, while i + r + 1 is
+//     before the end of the bucket holding t_i + tau (every key within tau
+//     after it in that order).  Every pair is checked once, both hits are
+//     marked, and each warp keeps its own list of live keys.  Seed rule 1
+//     and level 0 (SORT builds) test each core key instead;
 //  E. the ordered seed list; F. the causal count of every seed over whole
 //     buckets of its scan range, each key tested exactly ("Muon trigger
-//     strategy"); G. the fired seeds, in merged order, to out.
+//     strategy"); G. the fired seeds, in (t, pmt, charge) order, to out.
 //
-// Returns the counts and c0 = the number of staged keys before the core
-// (the core is keys [c0, c1) of the merged order).  cnt and mask are zero
-// on entry and on return.
+// Returns the counts and c0 = the number of staged keys before the core.
+// cnt and mask are zero on entry and on return.
 template <int CAP, int NC, bool SMEM_DT, bool EXT, bool DENSE>
 __device__ CoreOut tile_pass(TileCtx<CAP> &cx, const uint64_t *stage, uint32_t n, int64_t tb, uint32_t span,
                              uint32_t lo_t, uint32_t hi_t, const TrigParams &tp, trig_trigger *out, bool out_at_c0,
                              int64_t dbg_rank_lo, uint64_t *release_bar)
 {
+    constexpr bool SORT = EXT;
     constexpr uint32_t NW = NC / 32;
     constexpr int PER = CAP / NC;
     const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
@@ -1144,52 +1223,63 @@ __device__ CoreOut tile_pass(TileCtx<CAP> &cx, const uint64_t *stage, uint32_t n
     const uint32_t c0 = s_below[0], c1 = s_below[1], d_lo = s_below[2];
     PHASE_MARK(kPhA);
 
-    // C. bucket order, then the rank inside the bucket by (t, pmt, charge),
-    //    then position
-    uint32_t *pk = cx.pk_s(), *pk_b = cx.pk_b();
-    uint16_t *chg = cx.chg_s(), *chg_b = cx.chg_b(), *flk = cx.flk();
+    // C. bucket order (with each key's floor); SORT: then the rank inside
+    //    the bucket
+    uint32_t *pk = cx.pk_s();
+    uint16_t *chg = cx.chg_s(), *flk = cx.flk();
+    uint32_t *pk_c = SORT ? cx.pk_b() : pk;
+    uint16_t *chg_c = SORT ? cx.chg_b() : chg;
     const uint16_t *fl = cx.floor_s();
     const bool charge_rule = !(EXT && tp.seed_rule == 1);
 #pragma unroll
     for (int r = 0; r < PER; ++r) {
         if (key[r] != kPkNone) {
-            const uint32_t pos = cnt[bucket_of<CAP>(key[r] >> 12, bsh)] + (cs[r] & 0xffffu);
+            const uint32_t tr = key[r] >> 12;
+            const uint32_t pos = cnt[bucket_of<CAP>(tr, bsh)] + (cs[r] & 0xffffu);
             if (CHECK(22, pos, CAP)) {
-                pk_b[pos] = key[r];
-                chg_b[pos] = (uint16_t)(cs[r] >> 16);
+                pk_c[pos] = key[r];
+                chg_c[pos] = (uint16_t)(cs[r] >> 16);
+                if (!SORT) {
+                    flk[pos] = fl[key[r] & 0xfffu];
+                    if (charge_rule && (cs[r] >> 16) >= tp.q_seed && tr >= lo_t && tr < hi_t)
+                        atomicOr(&mask[pos >> 5], 1u << (pos & 31u));
+                }
             }
         }
     }
     if (tid < 4) pk[n + tid] = 0xfffff000u;           // end keys (time 2^20 - 1, PMT 0)
     cons_sync<NC>();
     PHASE_MARK(kPhB);
+    if (SORT) {
 #pragma unroll
-    for (int r = 0; r < PER; ++r) {
-        const uint32_t k = key[r];
-        if (k == kPkNone) continue;
-        const uint32_t b = bucket_of<CAP>(k >> 12, bsh);
-        const uint32_t s0 = cnt[b], s1 = cnt[b + 1], q = cs[r] >> 16, pos = s0 + (cs[r] & 0xffffu);
-        uint32_t rk = s0;
-        for (uint32_t m = s0; m < s1; ++m) {
-            const uint32_t o = pk_b[m];
-            rk += o < k;
-            if (o == k) {                          // equal time and PMT: charge, then position
-                const uint32_t oq = chg_b[m];
-                rk += oq < q || (oq == q && m < pos);
+        for (int r = 0; r < PER; ++r) {
+            const uint32_t k = key[r];
+            if (k == kPkNone) continue;
+            const uint32_t b = bucket_of<CAP>(k >> 12, bsh);
+            const uint32_t s0 = cnt[b], s1 = cnt[b + 1], q = cs[r] >> 16, pos = s0 + (cs[r] & 0xffffu);
+            uint32_t rk = s0;
+            for (uint32_t m = s0; m < s1; ++m) {
+                const uint32_t o = pk_c[m];
+                rk += o < k;
+                if (o == k) {                      // equal time and PMT: charge, then position
+                    const uint32_t oq = chg_c[m];
+                    rk += oq < q || (oq == q && m < pos);
+                }
+            }
+            if (CHECK(23, rk, CAP)) {
+                pk[rk] = k;
+                chg[rk] = (uint16_t)q;
+                flk[rk] = fl[k & 0xfffu];
+                const uint32_t tr = k >> 12;
+                if (charge_rule && q >= tp.q_seed && tr >= lo_t && tr < hi_t)
+                    atomicOr(&mask[rk >> 5], 1u << (rk & 31u));
             }
         }
-        if (CHECK(23, rk, CAP)) {
-            pk[rk] = k;
-            chg[rk] = (uint16_t)q;
-            flk[rk] = fl[k & 0xfffu];
-            const uint32_t tr = k >> 12;
-            if (charge_rule && q >= tp.q_seed && tr >= lo_t && tr < hi_t) atomicOr(&mask[rk >> 5], 1u << (rk & 31u));
-        }
+        cons_sync<NC>();
     }
-    cons_sync<NC>();
     PHASE_MARK(kPhC);
 
-    // D. seed flags of the core keys [c0, c1)
+    // D. seed flags of the core keys
     const uint32_t P = cx.P;
     if (EXT && tp.seed_rule == 1) {
         for (uint32_t base = c0 & ~31u; base < c1; base += NC) {
@@ -1199,54 +1289,76 @@ __device__ CoreOut tile_pass(TileCtx<CAP> &cx, const uint64_t *stage, uint32_t n
             if (lane == 0 && m) atomicOr(&mask[(base >> 5) + warp], m);
         }
     } else {
-        // the keys [d_lo, c1) can pair with a core key; warp w takes a
-        // contiguous share of them
+        // the keys that can pair with a core key -- sorted: [d_lo, c1); in
+        // bucket order: the buckets from t = lo_t - tau to hi_t + tau - 1 --
+        // in contiguous shares per warp; a live entry is (end << 16) | i
+        // with end the first position past i's candidates
         const uint32_t lt = (1u << lane) - 1u;
-        const uint32_t d_n = c1 > d_lo ? c1 - d_lo : 0u;
+        const uint32_t r_lo = SORT ? d_lo : cnt[bucket_of<CAP>(lo_t > tau ? lo_t - tau : 0u, bsh)];
+        const uint32_t r_hi = SORT ? c1 : cnt[bucket_of<CAP>(hi_t + tau - 1u, bsh) + 1];
+        const uint32_t d_n = r_hi > r_lo ? r_hi - r_lo : 0u;
         const uint32_t share = ((d_n + NW - 1) / NW + 31u) & ~31u;
-        const uint32_t w_begin = min(d_lo + warp * share, c1), w_end = min(w_begin + share, c1);
-        uint16_t *live = cx.live() + warp * (CAP / NW);
+        const uint32_t w_begin = min(r_lo + warp * share, r_hi), w_end = min(w_begin + share, r_hi);
+        uint32_t *live = cx.pk_b() + warp * (CAP / NW);
+        auto core = [&](uint32_t i, uint32_t ti) { return SORT ? (i >= c0 && i < c1) : (ti >= lo_t && ti < hi_t); };
         auto pair = [&](uint32_t i, uint32_t j, uint32_t ki, uint32_t kj) {
-            if ((ki & 0xfffu) != (kj & 0xfffu) && flk[i] == flk[j]) {
-                if (i >= c0 && i < c1) atomicOr(&mask[i >> 5], 1u << (i & 31u));
-                if (j >= c0 && j < c1) atomicOr(&mask[j >> 5], 1u << (j & 31u));
+            const uint32_t ti = ki >> 12, tj = kj >> 12;
+            if ((SORT || (tj > ti ? tj - ti : ti - tj) <= tau) && (ki & 0xfffu) != (kj & 0xfffu) && flk[i] == flk[j]) {
+                if (core(i, ti)) atomicOr(&mask[i >> 5], 1u << (i & 31u));
+                if (core(j, tj)) atomicOr(&mask[j >> 5], 1u << (j & 31u));
             }
         };
         uint32_t nlive = 0;
         for (uint32_t x = w_begin; x < w_end; x += 32) {
             const uint32_t i = x + lane;
             bool alive = false;
-            if (i < w_end) {                       // i + 1 <= c1 <= n: an end key at worst
-                const uint32_t ki = pk[i], kj = pk[i + 1];
-                if ((kj >> 12) - (ki >> 12) <= tau && i + 1 < n) {
-                    alive = true;
-                    pair(i, i + 1, ki, kj);
+            uint32_t end = 0;
+            if (i < w_end) {
+                const uint32_t ki = pk[i], ti = ki >> 12;
+                if (SORT) {
+                    // i + 1 <= c1 <= n: an end key at worst
+                    const uint32_t kj = pk[i + 1];
+                    if ((kj >> 12) - ti <= tau && i + 1 < n) {
+                        alive = true;
+                        pair(i, i + 1, ki, kj);
+                    }
+                } else if (ti + tau >= lo_t && ti < hi_t + tau) {
+                    end = cnt[bucket_of<CAP>(ti + tau, bsh) + 1];
+                    if (i + 1 < end) {
+                        pair(i, i + 1, ki, pk[i + 1]);
+                        alive = i + 2 < end;
+                    }
                 }
             }
             const uint32_t m = __ballot_sync(0xffffffffu, alive);
-            if (alive) live[nlive + __popc(m & lt)] = (uint16_t)i;
+            if (alive) live[nlive + __popc(m & lt)] = (end << 16) | i;
             nlive += __popc(m);
         }
         for (uint32_t d = 2; nlive; ++d) {
             uint32_t next = 0;
             for (uint32_t x = 0; x < nlive; x += 32) {
                 bool alive = false;
-                uint32_t i = 0;
+                uint32_t e = 0;
                 if (x + lane < nlive) {
-                    i = live[x + lane];
-                    const uint32_t j = i + d;
-                    if (j < n) {
-                        const uint32_t ki = pk[i], kj = pk[j];
-                        if ((kj >> 12) - (ki >> 12) <= tau) {
-                            alive = true;
-                            pair(i, j, ki, kj);
+                    e = live[x + lane];
+                    const uint32_t i = e & 0xffffu, j = i + d;
+                    if (SORT) {
+                        if (j < n) {
+                            const uint32_t ki = pk[i], kj = pk[j];
+                            if ((kj >> 12) - (ki >> 12) <= tau) {
+                                alive = true;
+                                pair(i, j, ki, kj);
+                            }
                         }
+                    } else {
+                        pair(i, j, pk[i], pk[j]);           // j < end by the list
+                        alive = j + 1 < (e >> 16);
                     }
                 }
                 // the ballot orders this batch's reads of the list before
                 // the writes below (which land at or before x + 31)
                 const uint32_t m = __ballot_sync(0xffffffffu, alive);
-                if (alive) live[next + __popc(m & lt)] = (uint16_t)i;
+                if (alive) live[next + __popc(m & lt)] = e;
                 next += __popc(m);
             }
             nlive = next;
@@ -1269,9 +1381,12 @@ __device__ CoreOut tile_pass(TileCtx<CAP> &cx, const uint64_t *stage, uint32_t n
 
     // E. ordered seed list: thread x takes mask word w_lo + x (at most
     //    CAP / 32 <= NC words); each word's offset adds the totals of the
-    //    warps before it
-    uint16_t *seed_idx = cx.seed_idx(), *seed_cnt = cx.seed_cnt();
-    const uint32_t w_lo = c0 >> 5, w_hi = (c1 + 31) >> 5;
+    //    warps before it.  Marks lie in the core: sorted, positions
+    //    [c0, c1); in bucket order, the buckets of [lo_t, hi_t)
+    uint16_t *seed_idx = SORT ? cx.seed_idx() : cx.flk();
+    const uint32_t p_lo = SORT ? c0 : cnt[bucket_of<CAP>(lo_t, bsh)];
+    const uint32_t p_hi = SORT ? c1 : cnt[bucket_of<CAP>(hi_t > 0 ? hi_t - 1 : 0, bsh) + 1];
+    const uint32_t w_lo = p_lo >> 5, w_hi = (p_hi + 31) >> 5;
     const uint32_t nwords = w_hi - w_lo;
     const uint32_t nw_used = (nwords + 31) >> 5;
     uint32_t *wtot = s_tot;                               // [NW]
@@ -1301,25 +1416,33 @@ __device__ CoreOut tile_pass(TileCtx<CAP> &cx, const uint64_t *stage, uint32_t n
     PHASE_MARK(kPhE);
     if (tid == 0) PHASE_ADD(kPhSeeds, ns);
 
-    // F. causal count c(s) over each seed's scan range, or its distinct-PMT
-    //    form (sparse batches give each seed 4 lanes, dense ones a warp)
-    if (EXT && tp.count_distinct) {
+    // F. causal count c(s) over each seed's scan range: the default rule
+    //    with each warp's work spread evenly over its lanes; SORT builds
+    //    with a group of lanes per seed, or the distinct-PMT form
+    uint16_t *seed_cnt = cx.seed_cnt();
+    uint32_t *seed_c = cx.pk_b();
+    if (!SORT) {
+        count_flat<CAP, NC, SMEM_DT>(cx, pk, ns, seed_idx, bsh, seed_c, reinterpret_cast<uint2 *>(cx.chg_b()));
+    } else if (EXT && tp.count_distinct) {
         count_distinct_pmts<CAP, NC, SMEM_DT>(cx, pk, n, ns, seed_idx, bsh, seed_cnt);
     } else {
         count_causal<CAP, NC, SMEM_DT, DENSE ? 5u : 2u>(cx, pk, n, ns, seed_idx, bsh, seed_cnt);
     }
     cons_sync<NC>();
     PHASE_MARK(kPhF);
+    auto count_of = [&](uint32_t k) -> uint32_t { return SORT ? (uint32_t)seed_cnt[k] : seed_c[k]; };
 
     // G. emit the fired seeds in order: warp w takes a contiguous range of
-    //    the seed list and adds up the fired totals of the warps before it
+    //    the seed list and adds up the fired totals of the warps before it.
+    //    In bucket order a fired seed's rank also counts the fired seeds of
+    //    its bucket (adjacent in the list) with a smaller (t, pmt, charge).
     const uint32_t threshold = tp.threshold;
     const uint32_t per_w = (ns + NW - 1) / NW;
     const uint32_t k_begin = min(ns, warp * per_w), k_end = min(ns, k_begin + per_w);
     uint32_t my_f = 0;
     for (uint32_t k0 = k_begin; k0 < k_end; k0 += 32) {
         const uint32_t k = k0 + lane;
-        my_f += __popc(__ballot_sync(0xffffffffu, k < k_end && seed_cnt[k] >= threshold));
+        my_f += __popc(__ballot_sync(0xffffffffu, k < k_end && count_of(k) >= threshold));
     }
     uint32_t *ftot = s_tot + NW;                          // [NW]
     if (lane == 0) ftot[warp] = my_f;
@@ -1334,26 +1457,44 @@ __device__ CoreOut tile_pass(TileCtx<CAP> &cx, const uint64_t *stage, uint32_t n
     trig_trigger *dst = out + (out_at_c0 ? c0 : 0u);
     for (uint32_t k0 = k_begin; k0 < k_end; k0 += 32) {
         const uint32_t k = k0 + lane;
-        const bool fired = k < k_end && seed_cnt[k] >= threshold;
+        const uint32_t cnt_k = k < k_end ? count_of(k) : 0u;
+        const bool fired = k < k_end && cnt_k >= threshold;
         const uint32_t m = __ballot_sync(0xffffffffu, fired);
         if (fired) {
             const uint32_t i = seed_idx[k];
             const uint32_t ks = pk[i];
+            const uint32_t q = chg[i];
+            uint32_t o_ = F + __popc(m & ((1u << lane) - 1u));
+            if (!SORT) {
+                // fired seeds of the same bucket before k that order after
+                // it, and after k that order before it
+                const uint32_t bk = bucket_of<CAP>(ks >> 12, bsh);
+                const uint64_t key_k = ((uint64_t)ks << 16) | q;
+                for (uint32_t k2 = k; k2-- > 0;) {
+                    const uint32_t i2 = seed_idx[k2];
+                    if (bucket_of<CAP>(pk[i2] >> 12, bsh) != bk) break;
+                    if (count_of(k2) >= threshold && (((uint64_t)pk[i2] << 16) | chg[i2]) > key_k) --o_;
+                }
+                for (uint32_t k2 = k + 1; k2 < ns; ++k2) {
+                    const uint32_t i2 = seed_idx[k2];
+                    if (bucket_of<CAP>(pk[i2] >> 12, bsh) != bk) break;
+                    if (count_of(k2) >= threshold && (((uint64_t)pk[i2] << 16) | chg[i2]) < key_k) ++o_;
+                }
+            }
             trig_trigger tr;
             tr.t_ns = tb + (int64_t)(ks >> 12);
             tr.pmt = (uint16_t)(ks & 0xfffu);
-            tr.charge = chg[i];
-            tr.count = seed_cnt[k];
-            const uint32_t o_ = F + __popc(m & ((1u << lane) - 1u));
+            tr.charge = (uint16_t)q;
+            tr.count = cnt_k;
             if (CHECK(3, o_, c1 - c0)) dst[o_] = tr;
         }
         F += __popc(m);
     }
-    // optional row outputs: the merged core rows (verification, and the
-    // merged stream of event extraction) and each row's causal count
-    // (verification only); rows are indexed by merged rank minus the rank
-    // of the slice's first owned hit
-    if (tp.dbg_merged) {
+    // optional row outputs (SORT builds): the merged core rows
+    // (verification, and the merged stream of event extraction) and each
+    // row's causal count (verification only); rows are indexed by merged
+    // rank minus the rank of the slice's first owned hit
+    if (SORT && tp.dbg_merged) {
         const uint64_t dbg_base = (uint64_t)(dbg_rank_lo + (int64_t)c0);
         for (uint32_t i = tid; i < c1 - c0; i += NC) {
             const uint32_t k = pk[c0 + i];
