@@ -130,6 +130,20 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         : "memory");
 }
 
+// Per-thread asynchronous 16-byte copy global -> shared (cp.async, through
+// L2), grouped by commit_group and awaited with wait_group.
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc)
+{
+    uint64_t g;
+    asm("cvta.to.global.u64 %0, %1;" : "=l"(g) : "l"(gsrc));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(smem_dst)), "l"(g) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 __device__ __forceinline__ void fence_proxy_async_smem()
 {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -695,7 +709,7 @@ struct ItemInfo {
 template <int CAP>
 struct TileLayout {
     static constexpr int NBK = CAP;                        // time buckets of the in-tile merge
-    static constexpr uint32_t NS = CAP == 2048 ? 1u : 2u;  // staging buffers
+    static constexpr uint32_t NS = 2;                      // staging buffers
     static constexpr size_t kStage = (size_t)CAP * 16;     // one staging buffer
     static constexpr size_t kPkS = (size_t)CAP * 4 + 16;
     static constexpr size_t kPkB = (size_t)CAP * 4;
@@ -704,9 +718,7 @@ struct TileLayout {
     static constexpr size_t kCnt = (size_t)(NBK + 1) * 4;
     static constexpr size_t kMask = (size_t)(CAP / 32) * 4;
     static constexpr size_t oPkS = NS * kStage;
-    static constexpr size_t oPkB = oPkS + kPkS;
-    static constexpr size_t oChgB = oPkB + kPkB;
-    static constexpr size_t oChgS = oChgB + kChg;
+    static constexpr size_t oChgS = oPkS + kPkS;
     static constexpr size_t oFlk = oChgS + kChg;
     static constexpr size_t oCnt = oFlk + kFlk;
     static constexpr size_t oMask = oCnt + kCnt;
@@ -737,17 +749,8 @@ struct TileCtx {
         return reinterpret_cast<uint64_t *>(g_tile_smem + (size_t)b * L::kStage);
     }
     __device__ __forceinline__ uint32_t *pk_s() const { return reinterpret_cast<uint32_t *>(g_tile_smem + L::oPkS); }
-    __device__ __forceinline__ uint32_t *pk_b() const { return reinterpret_cast<uint32_t *>(g_tile_smem + L::oPkB); }
-    __device__ __forceinline__ uint16_t *seed_idx() const { return reinterpret_cast<uint16_t *>(g_tile_smem + L::oPkB); }
-    __device__ __forceinline__ uint16_t *seed_cnt() const
-    {
-        return reinterpret_cast<uint16_t *>(g_tile_smem + L::oPkB) + CAP;
-    }
-    __device__ __forceinline__ uint16_t *chg_b() const { return reinterpret_cast<uint16_t *>(g_tile_smem + L::oChgB); }
     __device__ __forceinline__ uint16_t *chg_s() const { return reinterpret_cast<uint16_t *>(g_tile_smem + L::oChgS); }
     __device__ __forceinline__ uint16_t *flk() const { return reinterpret_cast<uint16_t *>(g_tile_smem + L::oFlk); }
-    // per-warp lists of the seed rounds (the bucket-order key region, free then)
-    __device__ __forceinline__ uint16_t *live() const { return reinterpret_cast<uint16_t *>(g_tile_smem + L::oPkB); }
     __device__ __forceinline__ uint32_t *cnt() const { return reinterpret_cast<uint32_t *>(g_tile_smem + L::oCnt); }
     __device__ __forceinline__ uint32_t *mask() const { return reinterpret_cast<uint32_t *>(g_tile_smem + L::oMask); }
     __device__ __forceinline__ uint16_t *floor_s() const { return reinterpret_cast<uint16_t *>(g_tile_smem + L::oTab); }
@@ -1037,83 +1040,6 @@ __device__ __forceinline__ void count_causal(const TileCtx<CAP> &cx, const uint3
     }
 }
 
-// Causal count with the work of a warp's seeds spread evenly over its
-// lanes (the default rule): warp w takes a contiguous range of the seed
-// list in batches of 32 seeds, one per lane; each lane finds its seed's
-// scan range [j0, j1) (seed_range) and the number of 4-key vectors from j0
-// rounded down to a multiple of 4.  The batch's vectors are cut into 32
-// equal contiguous chunks, one per lane; a lane walks its chunk from seed to
-// seed and adds each partial count into the seed's counter (shared
-// atomics).  No key outside [j0, j1) passes the test (see count_causal), so
-// whole vectors are tested.  tab holds the warp's batch: seed key, first
-// vector position and inclusive vector prefix.
-template <int CAP, int NC, bool SMEM_DT>
-__device__ __forceinline__ void count_flat(const TileCtx<CAP> &cx, const uint32_t *pk, uint32_t ns,
-                                           const uint16_t *seed_idx, uint32_t bsh, uint32_t *seed_c, uint2 *tab_all)
-{
-    constexpr uint32_t NW = NC / 32;
-    const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
-    uint2 *tab = tab_all + warp * 32;
-    const uint32_t per_w = (ns + NW - 1) / NW;
-    const uint32_t s_begin = min(ns, warp * per_w), s_end = min(ns, s_begin + per_w);
-    for (uint32_t sb = s_begin; sb < s_end; sb += 32) {
-        const uint32_t k = sb + lane;
-        uint32_t ks = 0, a = 0, nv = 0;
-        if (k < s_end) {
-            ks = pk[seed_idx[k]];
-            uint32_t j0, j1;
-            seed_range<CAP>(cx, ks >> 12, ks & 0xfffu, bsh, j0, j1);
-            a = j0 & ~3u;
-            nv = j1 > a ? (j1 - a + 3u) >> 2 : 0u;
-            seed_c[k] = 0;
-        }
-        const uint32_t incl = warp_incl_scan(nv);
-        tab[lane] = make_uint2(ks, (a << 16) | incl);       // a < 2^12, incl < 2^16
-        const uint32_t V = __shfl_sync(0xffffffffu, incl, 31);
-        __syncwarp();
-        const uint32_t v0 = (uint32_t)(((uint64_t)V * lane) >> 5);
-        const uint32_t v1 = (uint32_t)(((uint64_t)V * (lane + 1)) >> 5);
-        // the seed of v0: the first entry whose inclusive prefix exceeds it
-        uint32_t cur = 0;
-#pragma unroll
-        for (uint32_t step = 16; step; step >>= 1) {
-            const uint32_t at = cur + step - 1;
-            if ((tab[at].y & 0xffffu) <= v0) cur += step;
-        }
-        if (v0 < v1) {
-            uint2 e = tab[cur];
-            uint32_t end_v = e.y & 0xffffu, base_v = cur ? (tab[cur - 1].y & 0xffffu) : 0u;
-            uint32_t ts = e.x >> 12, q0 = e.y >> 16;
-            const uint16_t *row_s = cx.dt_s() + (e.x & 0xfffu) * cx.P;
-            const uint16_t *row_g = cx.dt_g + (e.x & 0xfffu) * cx.P;
-            uint32_t c = 0;
-            for (uint32_t v = v0; v < v1; ++v) {
-                while (v >= end_v) {
-                    if (c) atomicAdd(&seed_c[sb + cur], c);
-                    c = 0;
-                    ++cur;
-                    e = tab[cur];
-                    base_v = end_v;
-                    end_v = e.y & 0xffffu;
-                    ts = e.x >> 12;
-                    q0 = e.y >> 16;
-                    row_s = cx.dt_s() + (e.x & 0xfffu) * cx.P;
-                    row_g = cx.dt_g + (e.x & 0xfffu) * cx.P;
-                }
-                const uint4 w = *reinterpret_cast<const uint4 *>(pk + q0 + 4u * (v - base_v));
-                auto causal = [&](uint32_t kj) -> uint32_t {
-                    const uint32_t tj = kj >> 12, pj = kj & 0xfffu;
-                    const uint32_t lim = SMEM_DT ? (uint32_t)row_s[pj] : (uint32_t)__ldg(row_g + pj);
-                    return (tj > ts ? tj - ts : ts - tj) <= lim;
-                };
-                c += causal(w.x) + causal(w.y) + causal(w.z) + causal(w.w);
-            }
-            if (c) atomicAdd(&seed_c[sb + cur], c);
-        }
-        __syncwarp();
-    }
-}
-
 // Bucket shift of a staged range of `span` ns: buckets of 2^bsh ns, NBK of
 // them cover the range.
 template <int CAP>
@@ -1152,7 +1078,7 @@ __device__ __forceinline__ uint32_t bucket_shift(uint32_t span)
 // Returns the counts and c0 = the number of staged keys before the core.
 // cnt and mask are zero on entry and on return.
 template <int CAP, int NC, bool SMEM_DT, bool EXT, bool DENSE>
-__device__ CoreOut tile_pass(TileCtx<CAP> &cx, const uint64_t *stage, uint32_t n, int64_t tb, uint32_t span,
+__device__ CoreOut tile_pass(TileCtx<CAP> &cx, uint64_t *stage, uint32_t n, int64_t tb, uint32_t span,
                              uint32_t lo_t, uint32_t hi_t, const TrigParams &tp, trig_trigger *out, bool out_at_c0,
                              int64_t dbg_rank_lo, uint64_t *release_bar)
 {
@@ -1227,8 +1153,13 @@ __device__ CoreOut tile_pass(TileCtx<CAP> &cx, const uint64_t *stage, uint32_t n
     //    the bucket
     uint32_t *pk = cx.pk_s();
     uint16_t *chg = cx.chg_s(), *flk = cx.flk();
-    uint32_t *pk_c = SORT ? cx.pk_b() : pk;
-    uint16_t *chg_c = SORT ? cx.chg_b() : chg;
+    // scratch in the stage buffer, read in A only: keys and charges in
+    // bucket order (SORT), then the seed rounds' lists, the seed list and
+    // counts, the count's batch tables
+    uint32_t *pk_b = reinterpret_cast<uint32_t *>(stage);
+    uint16_t *chg_b = reinterpret_cast<uint16_t *>(reinterpret_cast<unsigned char *>(stage) + (size_t)CAP * 4);
+    uint32_t *pk_c = SORT ? pk_b : pk;
+    uint16_t *chg_c = SORT ? chg_b : chg;
     const uint16_t *fl = cx.floor_s();
     const bool charge_rule = !(EXT && tp.seed_rule == 1);
 #pragma unroll
@@ -1299,7 +1230,7 @@ __device__ CoreOut tile_pass(TileCtx<CAP> &cx, const uint64_t *stage, uint32_t n
         const uint32_t d_n = r_hi > r_lo ? r_hi - r_lo : 0u;
         const uint32_t share = ((d_n + NW - 1) / NW + 31u) & ~31u;
         const uint32_t w_begin = min(r_lo + warp * share, r_hi), w_end = min(w_begin + share, r_hi);
-        uint32_t *live = cx.pk_b() + warp * (CAP / NW);
+        uint32_t *live = pk_b + warp * (CAP / NW);
         auto core = [&](uint32_t i, uint32_t ti) { return SORT ? (i >= c0 && i < c1) : (ti >= lo_t && ti < hi_t); };
         auto pair = [&](uint32_t i, uint32_t j, uint32_t ki, uint32_t kj) {
             const uint32_t ti = ki >> 12, tj = kj >> 12;
@@ -1383,7 +1314,7 @@ __device__ CoreOut tile_pass(TileCtx<CAP> &cx, const uint64_t *stage, uint32_t n
     //    CAP / 32 <= NC words); each word's offset adds the totals of the
     //    warps before it.  Marks lie in the core: sorted, positions
     //    [c0, c1); in bucket order, the buckets of [lo_t, hi_t)
-    uint16_t *seed_idx = SORT ? cx.seed_idx() : cx.flk();
+    uint16_t *seed_idx = SORT ? reinterpret_cast<uint16_t *>(pk_b) : cx.flk();
     const uint32_t p_lo = SORT ? c0 : cnt[bucket_of<CAP>(lo_t, bsh)];
     const uint32_t p_hi = SORT ? c1 : cnt[bucket_of<CAP>(hi_t > 0 ? hi_t - 1 : 0, bsh) + 1];
     const uint32_t w_lo = p_lo >> 5, w_hi = (p_hi + 31) >> 5;
@@ -1416,21 +1347,17 @@ __device__ CoreOut tile_pass(TileCtx<CAP> &cx, const uint64_t *stage, uint32_t n
     PHASE_MARK(kPhE);
     if (tid == 0) PHASE_ADD(kPhSeeds, ns);
 
-    // F. causal count c(s) over each seed's scan range: the default rule
-    //    with each warp's work spread evenly over its lanes; SORT builds
-    //    with a group of lanes per seed, or the distinct-PMT form
-    uint16_t *seed_cnt = cx.seed_cnt();
-    uint32_t *seed_c = cx.pk_b();
-    if (!SORT) {
-        count_flat<CAP, NC, SMEM_DT>(cx, pk, ns, seed_idx, bsh, seed_c, reinterpret_cast<uint2 *>(cx.chg_b()));
-    } else if (EXT && tp.count_distinct) {
+    // F. causal count c(s) over each seed's scan range (sparse batches give
+    //    each seed 4 lanes, dense ones a warp), or its distinct-PMT form
+    uint16_t *seed_cnt = reinterpret_cast<uint16_t *>(pk_b) + CAP;
+    if (EXT && tp.count_distinct) {
         count_distinct_pmts<CAP, NC, SMEM_DT>(cx, pk, n, ns, seed_idx, bsh, seed_cnt);
     } else {
         count_causal<CAP, NC, SMEM_DT, DENSE ? 5u : 2u>(cx, pk, n, ns, seed_idx, bsh, seed_cnt);
     }
     cons_sync<NC>();
     PHASE_MARK(kPhF);
-    auto count_of = [&](uint32_t k) -> uint32_t { return SORT ? (uint32_t)seed_cnt[k] : seed_c[k]; };
+    auto count_of = [&](uint32_t k) -> uint32_t { return seed_cnt[k]; };
 
     // G. emit the fired seeds in order: warp w takes a contiguous range of
     //    the seed list and adds up the fired totals of the warps before it.
@@ -1444,16 +1371,18 @@ __device__ CoreOut tile_pass(TileCtx<CAP> &cx, const uint64_t *stage, uint32_t n
         const uint32_t k = k0 + lane;
         my_f += __popc(__ballot_sync(0xffffffffu, k < k_end && count_of(k) >= threshold));
     }
-    uint32_t *ftot = s_tot + NW;                          // [NW]
+    uint32_t *ftot = s_tot + NW;                          // [NW]: fired per warp, then their prefix
     if (lane == 0) ftot[warp] = my_f;
     cons_sync<NC>();
-    uint32_t n_fired = 0, F = 0;
-#pragma unroll
-    for (uint32_t w2 = 0; w2 < NW; ++w2) {
-        const uint32_t v = ftot[w2];
-        F += w2 < warp ? v : 0u;
-        n_fired += v;
+    if (warp == 0) {
+        const uint32_t v = lane < NW ? ftot[lane] : 0u;
+        const uint32_t vi = warp_incl_scan(v);
+        if (lane < NW) ftot[lane] = vi - v;
+        if (lane == NW - 1) s_red[0] = vi;
     }
+    cons_sync<NC>();
+    const uint32_t n_fired = s_red[0];
+    uint32_t F = ftot[warp];
     trig_trigger *dst = out + (out_at_c0 ? c0 : 0u);
     for (uint32_t k0 = k_begin; k0 < k_end; k0 += 32) {
         const uint32_t k = k0 + lane;
@@ -1657,15 +1586,56 @@ __device__ void tile_overflow(TileCtx<CAP> &cx, uint64_t *buf, const SliceDesc &
     cons_sync<NC>();
 }
 
+// The producer's plan for one work item: where its hits are, the runs to
+// copy (one per PMT of a narrow slice, at most kWideMinPmt - 1; one range of
+// the bucketed copy for a wide slice) and where each lands in the staging
+// buffer.
+constexpr uint32_t kMaxRuns = kWideMinPmt - 1;
+struct LookSlot {
+    ItemInfo info;
+    const trig_hit *src;
+    uint32_t nruns;
+    uint32_t pad;
+    uint32_t run_src[kMaxRuns];     // first hit of the run, index into src
+    uint32_t run_len[kMaxRuns];
+    uint32_t run_dst[kMaxRuns];     // its first record in the staging buffer
+};
+
+// The consumers stage an item with per-thread 16-byte copies: a warp per PMT
+// run (narrow slices) or every thread over the one range (wide slices).
+template <int NC>
+__device__ __forceinline__ void stage_item(const LookSlot &L, uint64_t *stage)
+{
+    constexpr uint32_t NW = NC / 32;
+    const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
+    if (L.info.item < 0 || L.info.mode != 0) return;
+    const uint32_t nr = L.nruns;
+    if (nr == 1) {
+        const trig_hit *src = L.src + L.run_src[0];
+        uint64_t *dst = stage + 2 * (size_t)L.run_dst[0];
+        const uint32_t len = L.run_len[0];
+        for (uint32_t e = tid; e < len; e += NC) cp_async16(dst + 2 * e, src + e);
+        return;
+    }
+    for (uint32_t r = warp; r < nr; r += NW) {
+        const uint32_t len = L.run_len[r];
+        const trig_hit *src = L.src + L.run_src[r];
+        uint64_t *dst = stage + 2 * (size_t)L.run_dst[r];
+        for (uint32_t e = lane; e < len; e += 32) cp_async16(dst + 2 * e, src + e);
+    }
+}
+
 template <int CAP, int NC, bool SMEM_DT, bool EXT, bool DENSE>
 __global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 1)) k_tile(BatchHeader *__restrict__ hdr,
                                                                           const SliceDesc *__restrict__ desc,
                                                                           uint32_t max_pmt)
 {
     constexpr uint32_t NW = NC / 32;
-    constexpr uint32_t NSTG = TileLayout<CAP>::NS;
-    __shared__ uint64_t full_bar[2], empty_bar[2];
-    __shared__ ItemInfo info[2];
+    // look_full[s]: the producer published slot s; look_empty[s]: every
+    // consumer warp has issued slot s's copies and the slot may be reused
+    __shared__ uint64_t look_full[2], look_empty[2];
+    __shared__ LookSlot look[2];
+    __shared__ ItemInfo cinfo[2];           // the consumers' copy of each staged item's plan
     __shared__ __align__(16) uint32_t red[64 + 64];
     __shared__ int64_t stk[128];
 
@@ -1676,10 +1646,10 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 
 
     const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = lane_id();
     if (tid == 0) {
-        mbar_init(&full_bar[0], 1);
-        mbar_init(&full_bar[1], 1);
-        mbar_init(&empty_bar[0], 1);
-        mbar_init(&empty_bar[1], 1);
+        mbar_init(&look_full[0], 1);
+        mbar_init(&look_full[1], 1);
+        mbar_init(&look_empty[0], NW);
+        mbar_init(&look_empty[1], NW);
         fence_mbar_init();
     }
     __syncthreads();
@@ -1688,27 +1658,26 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 
     const uint64_t wait_ns = hdr->wait_ns;
 
     if (warp == NW) {
-        // test control: stage nothing, so that the consumers' first wait
+        // test control: publish nothing, so that the consumers' first wait
         // runs out (no copy is ever in flight)
         if (hdr->stall) return;
         // ------------------------------------------------ producer warp
-        // The next item is dequeued and its per-PMT runs looked up before
-        // waiting for a free buffer, so those global loads overlap the wait.
+        // Dequeues items and looks up each one's runs; the next item is
+        // dequeued and looked up before waiting for a free slot.
         uint32_t s = 0;
         bool bad = false;
         const SliceDesc *d = nullptr;
-        constexpr int R = 4;                       // PMTs per lane kept in registers
+        constexpr int R = 4;                       // PMTs per lane (P <= 128 for narrow slices)
         uint32_t item = 0;
         if (lane == 0) item = atomicAdd(&hdr->queue, 1u);
         item = __shfl_sync(0xffffffffu, item, 0);
         for (uint32_t it = 0;; ++it) {
-            const uint32_t b = it % NSTG, use = it / NSTG;
+            const uint32_t b = it & 1u, use = it >> 1;
 #ifdef TRIG_PHASE_STATS
             const long long tp0 = clock64();
 #endif
             uint32_t g = 0, P = 0, mode = 2, lo_t = 0, span = 0;
-            uint64_t ra[R];
-            uint32_t rl[R];
+            uint32_t ra[R], rl[R];
             uint64_t tot = 0, rlo = 0;
             bool wide = false;
             if (item < n_items) {
@@ -1742,24 +1711,22 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 
                     const uint64_t *poff = d->pmt_off;
                     lo_t = d->halo;
                     span = (uint32_t)d->tile_w + 2u * d->halo;
-                    if (!bad) {
 #pragma unroll
-                        for (int r = 0; r < R; ++r) {
-                            const uint32_t p = r * 32 + lane;
-                            uint64_t a = 0, e = 0, sp_ = 0, ep_ = 0;
-                            if (p < P) {
-                                a = __ldg(elo + p);
-                                e = __ldg(ehi + p);
-                                sp_ = __ldg(poff + p);
-                                ep_ = __ldg(poff + p + 1);
-                                a = min(max(a, sp_), ep_);
-                                e = min(max(e, a), ep_);
-                            }
-                            ra[r] = a;
-                            rl[r] = (uint32_t)(e - a);
-                            tot += e - a;
-                            rlo += a - sp_;
+                    for (int r = 0; r < R; ++r) {
+                        const uint32_t p = r * 32 + lane;
+                        uint64_t a = 0, e = 0, sp_ = 0, ep_ = 0;
+                        if (!bad && p < P) {
+                            a = __ldg(elo + p);
+                            e = __ldg(ehi + p);
+                            sp_ = __ldg(poff + p);
+                            ep_ = __ldg(poff + p + 1);
+                            a = min(max(a, sp_), ep_);
+                            e = min(max(e, a), ep_);
                         }
+                        ra[r] = (uint32_t)a;
+                        rl[r] = (uint32_t)(e - a);
+                        tot += e - a;
+                        rlo += a - sp_;
                     }
                     tot = warp_sum_u64(tot);
                     rlo = warp_sum_u64(rlo);
@@ -1771,57 +1738,69 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 
                 if (lane == 0) next = atomicAdd(&hdr->queue, 1u);
                 next = __shfl_sync(0xffffffffu, next, 0);
             }
+            // lane 0 waits (bounded) for the slot and decides for the warp
 #ifdef TRIG_PHASE_STATS
             const long long tw0 = clock64();
             if (lane == 0) PHASE_ADD(kPhProdItem, tw0 - tp0);
-            uint32_t pr = 0;
-            const bool pwait_ok = it < NSTG || mbar_wait(&empty_bar[b], (use - 1) & 1u, wait_ns, &pr);
-            if (lane == 0) {
+#endif
+            uint32_t free_ok = 1;
+            if (it >= 2 && lane == 0) {
+#ifdef TRIG_PHASE_STATS
+                uint32_t pr = 0;
+                free_ok = mbar_wait(&look_empty[b], (use - 1) & 1u, wait_ns, &pr) ? 1u : 0u;
                 PHASE_ADD(kPhProdWait, clock64() - tw0);
                 PHASE_ADD(kPhProdWaitRounds, pr);
-            }
-            if (!pwait_ok) {
 #else
-            if (it >= NSTG && !mbar_wait(&empty_bar[b], (use - 1) & 1u, wait_ns)) {
+                free_ok = mbar_wait(&look_empty[b], (use - 1) & 1u, wait_ns) ? 1u : 0u;
 #endif
+            }
+            free_ok = __shfl_sync(0xffffffffu, free_ok, 0);
+            __syncwarp();
+            if (!free_ok) {
                 if (lane == 0) atomicOr(&hdr->err, TRIG_FLAG_TIMEOUT);
                 break;
             }
+            LookSlot &L = look[b];
             if (item >= n_items) {
                 if (lane == 0) {
-                    info[b].item = -1;
-                    mbar_arrive(&full_bar[b]);
+                    L.info.item = -1;
+                    mbar_arrive(&look_full[b]);
                 }
                 break;
             }
             if (lane == 0) {
-                info[b].item = (int32_t)item;
-                info[b].slice = s;
-                info[b].g = g;
-                info[b].n = (uint32_t)min(tot, (uint64_t)CAP);
-                info[b].rank_lo = (uint32_t)rlo;
-                info[b].mode = mode;
-                info[b].lo_t = lo_t;
-                info[b].span = span;
-                if (mode == 0) mbar_arrive_expect_tx(&full_bar[b], (uint32_t)tot * 16u);
-                else mbar_arrive(&full_bar[b]);
+                L.info.item = (int32_t)item;
+                L.info.slice = s;
+                L.info.g = g;
+                L.info.n = (uint32_t)min(tot, (uint64_t)CAP);
+                L.info.rank_lo = (uint32_t)rlo;
+                L.info.mode = mode;
+                L.info.lo_t = lo_t;
+                L.info.span = span;
+                L.src = wide ? d->tbuf : d->hits;
+                L.nruns = mode != 0 ? 0u : (wide ? 1u : P);
+                if (wide) {
+                    L.run_src[0] = (uint32_t)rlo;
+                    L.run_len[0] = (uint32_t)tot;
+                    L.run_dst[0] = 0;
+                }
             }
-            __syncwarp();
-            if (mode == 0 && wide) {
-                if (lane == 0 && CHECK(7, rlo + tot, d->n_hits + 1))
-                    bulk_g2s(cx.stage(b), d->tbuf + rlo, (uint32_t)tot * 16u, &full_bar[b]);
-            } else if (mode == 0) {
+            if (mode == 0 && !wide) {
                 uint32_t dst = 0;
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    const uint32_t len = rl[r];
-                    const uint64_t a = ra[r];
-                    const uint32_t incl = warp_incl_scan(len);
-                    if (len && CHECK(6, dst + incl, CAP + 1) && CHECK(7, a + len, d->n_hits + 1))
-                        bulk_g2s(cx.stage(b) + 2 * (size_t)(dst + incl - len), d->hits + a, len * 16u, &full_bar[b]);
+                    const uint32_t p = r * 32 + lane;
+                    const uint32_t incl = warp_incl_scan(rl[r]);
+                    if (p < P) {
+                        L.run_src[p] = ra[r];
+                        L.run_len[p] = rl[r];
+                        L.run_dst[p] = dst + incl - rl[r];
+                    }
                     dst += __shfl_sync(0xffffffffu, incl, 31);
                 }
             }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&look_full[b]);       // releases the slot's writes
 #ifdef TRIG_PHASE_STATS
             if (lane == 0) PHASE_ADD(kPhProdTotal, clock64() - tp0);
 #endif
@@ -1834,7 +1813,6 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 
     // the tile pass expects zero bucket counts and seed mask (and leaves them so)
     for (uint32_t i = tid; i < (uint32_t)TileLayout<CAP>::NBK; i += NC) cx.cnt()[i] = 0;
     for (uint32_t i = tid; i < (uint32_t)CAP / 32; i += NC) cx.mask()[i] = 0;
-    cons_sync<NC>();
     const SliceDesc *loaded = nullptr;
     // the slice's trigger parameters live in shared memory (written by one
     // thread when the slice changes), keeping registers for the tile phases
@@ -1842,30 +1820,53 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 
     // the loaded slice's tile width, t0, length and merged rank of its first
     // owned hit, also kept in shared memory
     __shared__ int64_t sl[4];
-    for (uint32_t it = 0;; ++it) {
-        const uint32_t b = it % NSTG, use = it / NSTG;
-#ifdef TRIG_PHASE_STATS
-        const long long tw0 = clock64();
-        uint32_t cr = 0;
-        const bool cwait_ok = mbar_wait(&full_bar[b], use & 1u, wait_ns, &cr);
+    __shared__ uint32_t s_ok;
+    // Item it+1 is staged while item it is processed: wait for its plan,
+    // issue its copies, keep a copy of the plan, hand the slot back.  One
+    // thread waits (bounded) and the barrier gives every thread its
+    // decision, so the block never splits on a timeout.
+    auto take = [&](uint32_t it) -> bool {
+        const uint32_t b = it & 1u;
         if (tid == 0) {
+#ifdef TRIG_PHASE_STATS
+            const long long tw0 = clock64();
+            uint32_t cr = 0;
+            s_ok = mbar_wait(&look_full[b], (it >> 1) & 1u, wait_ns, &cr) ? 1u : 0u;
             PHASE_ADD(kPhConsWait, clock64() - tw0);
             PHASE_ADD(kPhConsWaitRounds, cr);
-            PHASE_ADD(kPhTiles, 1);
-        }
-        if (!cwait_ok) {
 #else
-        if (!mbar_wait(&full_bar[b], use & 1u, wait_ns)) {
+            s_ok = mbar_wait(&look_full[b], (it >> 1) & 1u, wait_ns) ? 1u : 0u;
 #endif
-            if (tid == 0) atomicOr(&hdr->err, TRIG_FLAG_TIMEOUT);
+        }
+        cons_sync<NC>();
+        if (!s_ok) return false;
+        stage_item<NC>(look[b], cx.stage(b));
+        cp_async_commit();
+        if (tid == 0) cinfo[b] = look[b].info;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&look_empty[b]);
+        return true;
+    };
+    bool ok = take(0);
+    cons_sync<NC>();
+    for (uint32_t it = 0; ok; ++it) {
+        const uint32_t b = it & 1u;
+        const ItemInfo inf = cinfo[b];
+        if (inf.item < 0) break;
+        if (!take(it + 1)) {
+            ok = false;
             break;
         }
-        const ItemInfo &inf = info[b];      // stable until this buffer is released
-        if (inf.item < 0) break;
+        // this thread's copies of item it are done; after the barrier,
+        // everyone's
+        cp_async_wait<1>();
+        cons_sync<NC>();
+#ifdef TRIG_PHASE_STATS
+        if (tid == 0) PHASE_ADD(kPhTiles, 1);
+#endif
         const SliceDesc &d = desc[inf.slice];
         if (&d != loaded) {
             // (re)load the detector tables of this slice
-            cons_sync<NC>();
             const uint32_t P = d.n_pmt;
             for (uint32_t p = tid; p < P; p += NC) {
                 cx.floor_s()[p] = d.floor[p];
@@ -1892,8 +1893,6 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 
                 tp.rel = d.rel;
                 tp.dbg_merged = d.dbg_merged;
                 tp.dbg_seedcnt = d.dbg_seedcnt;
-            }
-            if (tid == 0) {
                 sl[0] = d.tile_w;
                 sl[1] = d.t0;
                 sl[2] = d.slice_ns;
@@ -1910,33 +1909,29 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 
             tile_overflow<CAP, NC, SMEM_DT, EXT, DENSE>(cx, cx.stage(b), d, tp, inf.g, red, stk);
         } else {
             const int64_t W = sl[0];
-            const uint32_t g = inf.g, n_st = inf.n, rank_lo = inf.rank_lo, span = inf.span;
-            const int64_t Bg = sl[1] + (int64_t)g * W;
+            const int64_t Bg = sl[1] + (int64_t)inf.g * W;
             const int64_t core_end = min(Bg + W, sl[1] + sl[2]);
             // the staged range starts lo_t (>= H) before the core
-            const uint32_t lo_t = inf.lo_t;
-            const int64_t tb = Bg - (int64_t)lo_t;
-            const uint32_t hi_t = lo_t + (uint32_t)(core_end - Bg);
-            // the pass hands the buffer back as soon as it has read it (inf
-            // is not read after that); the core's first hit has merged rank
-            // rank_lo + c0
-            CoreOut co = tile_pass<CAP, NC, SMEM_DT, EXT, DENSE>(cx, cx.stage(b), n_st, tb, span, lo_t, hi_t, tp,
-                                                                 d.stage + rank_lo, true,
-                                                                 (int64_t)rank_lo - sl[3], &empty_bar[b]);
-            const uint32_t tile_rank = rank_lo + co.c0;
-            if (tid == 0 && CHECK(14, (uint64_t)tile_rank + co.n_fired, d.n_hits + 1) && CHECK(15, g, d.n_tiles)) {
-                d.tile_nfired[g] = co.n_fired;
-                d.tile_rank[g] = tile_rank;
+            const int64_t tb = Bg - (int64_t)inf.lo_t;
+            const uint32_t hi_t = inf.lo_t + (uint32_t)(core_end - Bg);
+            // the core's first hit has merged rank rank_lo + c0
+            CoreOut co = tile_pass<CAP, NC, SMEM_DT, EXT, DENSE>(cx, cx.stage(b), inf.n, tb, inf.span, inf.lo_t, hi_t,
+                                                                 tp, d.stage + inf.rank_lo, true,
+                                                                 (int64_t)inf.rank_lo - sl[3], nullptr);
+            const uint32_t tile_rank = inf.rank_lo + co.c0;
+            if (tid == 0 && CHECK(14, (uint64_t)tile_rank + co.n_fired, d.n_hits + 1) && CHECK(15, inf.g, d.n_tiles)) {
+                d.tile_nfired[inf.g] = co.n_fired;
+                d.tile_rank[inf.g] = tile_rank;
                 atomicAdd(reinterpret_cast<unsigned long long *>(&d.stats->n_seeds), (unsigned long long)co.n_seeds);
             }
-            continue;
         }
-        // release the buffer to the producer: order our generic-proxy
-        // accesses before its next bulk copy into the same buffer
-        fence_proxy_async_smem();
+        // every thread is done with item it's staging buffer and plan
+        // before the next iteration stages item it + 2 into it
         cons_sync<NC>();
-        if (tid == 0) mbar_arrive(&empty_bar[b]);
     }
+    if (!ok && tid == 0) atomicOr(&hdr->err, TRIG_FLAG_TIMEOUT);
+    // no copy of this block is left in flight when it exits
+    cp_async_wait<0>();
 }
 
 // ------------------------------------------------------------------ k_scan
