@@ -462,7 +462,7 @@ __device__ __noinline__ void bounds_wide_chunk(const SliceDesc &d, uint64_t firs
 // (run starts and ends against pmt_off, neighbours from adjacent lanes), and
 // the tile edges passed between the previous hit of the PMT and this one
 // get this hit's index.
-__global__ void __launch_bounds__(kBoundsThreads, 4) k_bounds(const BatchHeader *__restrict__ hdr,
+__global__ void __launch_bounds__(kBoundsThreads, 3) k_bounds(const BatchHeader *__restrict__ hdr,
                                                            const SliceDesc *__restrict__ desc)
 {
     const uint32_t n_slices = hdr->n_slices, n_chunks = hdr->n_chunks;
@@ -525,13 +525,26 @@ __global__ void __launch_bounds__(kBoundsThreads, 4) k_bounds(const BatchHeader 
             c_t = q.t_ns;
             edges(c_t, c_lo, c_hi);
         }
+        // software-pipelined: the next group's records are loaded before
+        // this group is processed, so two groups' loads are in flight
+        trig_hit hn[kBoundsUnroll];
+#pragma unroll
+        for (int u = 0; u < kBoundsUnroll; ++u) {
+            const uint64_t li = wbase + u * 32 + lane;
+            if (li < n_hits) hn[u] = load_hit(hits + li);
+            else hn[u].t_ns = 0, hn[u].pmt = 0xffff;
+        }
         for (uint32_t k0 = 0; k0 < kBoundsPerWarp; k0 += 32 * kBoundsUnroll) {
             trig_hit h[kBoundsUnroll];
 #pragma unroll
-            for (int u = 0; u < kBoundsUnroll; ++u) {
-                const uint64_t li = wbase + k0 + u * 32 + lane;
-                if (li < n_hits) h[u] = load_hit(hits + li);
-                else h[u].t_ns = 0, h[u].pmt = 0xffff;
+            for (int u = 0; u < kBoundsUnroll; ++u) h[u] = hn[u];
+            if (k0 + 32 * kBoundsUnroll < kBoundsPerWarp) {
+#pragma unroll
+                for (int u = 0; u < kBoundsUnroll; ++u) {
+                    const uint64_t li = wbase + k0 + 32 * kBoundsUnroll + u * 32 + lane;
+                    if (li < n_hits) hn[u] = load_hit(hits + li);
+                    else hn[u].t_ns = 0, hn[u].pmt = 0xffff;
+                }
             }
 #pragma unroll
             for (int u = 0; u < kBoundsUnroll; ++u) {
@@ -1601,27 +1614,24 @@ struct LookSlot {
     uint32_t run_dst[kMaxRuns];     // its first record in the staging buffer
 };
 
-// The consumers stage an item with per-thread 16-byte copies: a warp per PMT
-// run (narrow slices) or every thread over the one range (wide slices).
+// The consumers stage an item with bulk copies (cp.async.bulk, the TMA
+// engine), one per PMT run issued by one thread each (narrow slices), or
+// one over the item's range (wide slices), all completing on `bar`; thread
+// 0 arms `bar` with the item's bytes (or just arrives when nothing is
+// copied), so the phase completes once every byte has landed.
 template <int NC>
-__device__ __forceinline__ void stage_item(const LookSlot &L, uint64_t *stage)
+__device__ __forceinline__ void stage_item(const LookSlot &L, uint64_t *stage, uint64_t *bar)
 {
-    constexpr uint32_t NW = NC / 32;
-    const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
-    if (L.info.item < 0 || L.info.mode != 0) return;
-    const uint32_t nr = L.nruns;
-    if (nr == 1) {
-        const trig_hit *src = L.src + L.run_src[0];
-        uint64_t *dst = stage + 2 * (size_t)L.run_dst[0];
-        const uint32_t len = L.run_len[0];
-        for (uint32_t e = tid; e < len; e += NC) cp_async16(dst + 2 * e, src + e);
-        return;
+    const uint32_t tid = threadIdx.x;
+    const bool copy = L.info.item >= 0 && L.info.mode == 0;
+    if (tid == 0) {
+        if (copy) mbar_arrive_expect_tx(bar, L.info.n * 16u);
+        else mbar_arrive(bar);
     }
-    for (uint32_t r = warp; r < nr; r += NW) {
+    if (!copy) return;
+    for (uint32_t r = tid; r < L.nruns; r += NC) {
         const uint32_t len = L.run_len[r];
-        const trig_hit *src = L.src + L.run_src[r];
-        uint64_t *dst = stage + 2 * (size_t)L.run_dst[r];
-        for (uint32_t e = lane; e < len; e += 32) cp_async16(dst + 2 * e, src + e);
+        if (len) bulk_g2s(stage + 2 * (size_t)L.run_dst[r], L.src + L.run_src[r], len * 16u, bar);
     }
 }
 
@@ -1633,7 +1643,8 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 
     constexpr uint32_t NW = NC / 32;
     // look_full[s]: the producer published slot s; look_empty[s]: every
     // consumer warp has issued slot s's copies and the slot may be reused
-    __shared__ uint64_t look_full[2], look_empty[2];
+    // full_bar[b]: staging buffer b holds its item
+    __shared__ uint64_t look_full[2], look_empty[2], full_bar[2];
     __shared__ LookSlot look[2];
     __shared__ ItemInfo cinfo[2];           // the consumers' copy of each staged item's plan
     __shared__ __align__(16) uint32_t red[64 + 64];
@@ -1650,6 +1661,8 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 
         mbar_init(&look_full[1], 1);
         mbar_init(&look_empty[0], NW);
         mbar_init(&look_empty[1], NW);
+        mbar_init(&full_bar[0], 1);
+        mbar_init(&full_bar[1], 1);
         fence_mbar_init();
     }
     __syncthreads();
@@ -1840,14 +1853,16 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 
         }
         cons_sync<NC>();
         if (!s_ok) return false;
-        stage_item<NC>(look[b], cx.stage(b));
-        cp_async_commit();
+        stage_item<NC>(look[b], cx.stage(b), &full_bar[b]);
         if (tid == 0) cinfo[b] = look[b].info;
         __syncwarp();
         if (lane == 0) mbar_arrive(&look_empty[b]);
         return true;
     };
+    // items [waited, taken) have copies that may still be in flight
+    uint32_t taken = 0, waited = 0;
     bool ok = take(0);
+    taken = ok ? 1u : 0u;
     cons_sync<NC>();
     for (uint32_t it = 0; ok; ++it) {
         const uint32_t b = it & 1u;
@@ -1857,10 +1872,18 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 
             ok = false;
             break;
         }
-        // this thread's copies of item it are done; after the barrier,
-        // everyone's
-        cp_async_wait<1>();
+        taken = it + 2;
+        // item it has landed: one thread waits (bounded), the barrier
+        // passes its decision on, and every thread then observes the
+        // completed phase itself
+        if (tid == 0) s_ok = mbar_wait(&full_bar[b], (it >> 1) & 1u, wait_ns) ? 1u : 0u;
         cons_sync<NC>();
+        if (!s_ok) {
+            ok = false;
+            break;
+        }
+        (void)mbar_try_wait(&full_bar[b], (it >> 1) & 1u);
+        waited = it + 1;
 #ifdef TRIG_PHASE_STATS
         if (tid == 0) PHASE_ADD(kPhTiles, 1);
 #endif
@@ -1926,12 +1949,16 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 
             }
         }
         // every thread is done with item it's staging buffer and plan
-        // before the next iteration stages item it + 2 into it
+        // (its generic accesses ordered before the next bulk copy into the
+        // buffer) before the next iteration stages item it + 2 into it
+        fence_proxy_async_smem();
         cons_sync<NC>();
     }
-    if (!ok && tid == 0) atomicOr(&hdr->err, TRIG_FLAG_TIMEOUT);
-    // no copy of this block is left in flight when it exits
-    cp_async_wait<0>();
+    if (tid == 0) {
+        if (!ok) atomicOr(&hdr->err, TRIG_FLAG_TIMEOUT);
+        // no copy of this block is left in flight when it exits (bounded)
+        for (uint32_t j = waited; j < taken; ++j) (void)mbar_wait(&full_bar[j & 1u], (j >> 1) & 1u, wait_ns);
+    }
 }
 
 // ------------------------------------------------------------------ k_scan
