@@ -130,20 +130,6 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         : "memory");
 }
 
-// Per-thread asynchronous 16-byte copy global -> shared (cp.async, through
-// L2), grouped by commit_group and awaited with wait_group.
-__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc)
-{
-    uint64_t g;
-    asm("cvta.to.global.u64 %0, %1;" : "=l"(g) : "l"(gsrc));
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(smem_dst)), "l"(g) : "memory");
-}
-
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
 __device__ __forceinline__ void fence_proxy_async_smem()
 {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -157,6 +143,22 @@ __device__ __forceinline__ void fence_mbar_init()
 __device__ __forceinline__ void named_sync(uint32_t id, uint32_t n)
 {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+// Named barrier over n threads that also ANDs a predicate across them: every
+// thread leaves with the same answer.
+__device__ __forceinline__ bool named_sync_and(uint32_t id, uint32_t n, bool p)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred q, o;\n\t"
+        "setp.ne.u32 q, %1, 0;\n\t"
+        "bar.red.and.pred o, %2, %3, q;\n\t"
+        "selp.u32 %0, 1, 0, o;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)p), "r"(id), "r"(n)
+        : "memory");
+    return r != 0;
 }
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
@@ -462,7 +464,7 @@ __device__ __noinline__ void bounds_wide_chunk(const SliceDesc &d, uint64_t firs
 // (run starts and ends against pmt_off, neighbours from adjacent lanes), and
 // the tile edges passed between the previous hit of the PMT and this one
 // get this hit's index.
-__global__ void __launch_bounds__(kBoundsThreads, 3) k_bounds(const BatchHeader *__restrict__ hdr,
+__global__ void __launch_bounds__(kBoundsThreads, 4) k_bounds(const BatchHeader *__restrict__ hdr,
                                                            const SliceDesc *__restrict__ desc)
 {
     const uint32_t n_slices = hdr->n_slices, n_chunks = hdr->n_chunks;
@@ -525,26 +527,13 @@ __global__ void __launch_bounds__(kBoundsThreads, 3) k_bounds(const BatchHeader 
             c_t = q.t_ns;
             edges(c_t, c_lo, c_hi);
         }
-        // software-pipelined: the next group's records are loaded before
-        // this group is processed, so two groups' loads are in flight
-        trig_hit hn[kBoundsUnroll];
-#pragma unroll
-        for (int u = 0; u < kBoundsUnroll; ++u) {
-            const uint64_t li = wbase + u * 32 + lane;
-            if (li < n_hits) hn[u] = load_hit(hits + li);
-            else hn[u].t_ns = 0, hn[u].pmt = 0xffff;
-        }
         for (uint32_t k0 = 0; k0 < kBoundsPerWarp; k0 += 32 * kBoundsUnroll) {
             trig_hit h[kBoundsUnroll];
 #pragma unroll
-            for (int u = 0; u < kBoundsUnroll; ++u) h[u] = hn[u];
-            if (k0 + 32 * kBoundsUnroll < kBoundsPerWarp) {
-#pragma unroll
-                for (int u = 0; u < kBoundsUnroll; ++u) {
-                    const uint64_t li = wbase + k0 + 32 * kBoundsUnroll + u * 32 + lane;
-                    if (li < n_hits) hn[u] = load_hit(hits + li);
-                    else hn[u].t_ns = 0, hn[u].pmt = 0xffff;
-                }
+            for (int u = 0; u < kBoundsUnroll; ++u) {
+                const uint64_t li = wbase + k0 + u * 32 + lane;
+                if (li < n_hits) h[u] = load_hit(hits + li);
+                else h[u].t_ns = 0, h[u].pmt = 0xffff;
             }
 #pragma unroll
             for (int u = 0; u < kBoundsUnroll; ++u) {
@@ -722,7 +711,7 @@ struct ItemInfo {
 template <int CAP>
 struct TileLayout {
     static constexpr int NBK = CAP;                        // time buckets of the in-tile merge
-    static constexpr uint32_t NS = 2;                      // staging buffers
+    static constexpr uint32_t NS = CAP == 2048 ? 1u : 2u;  // staging buffers
     static constexpr size_t kStage = (size_t)CAP * 16;     // one staging buffer
     static constexpr size_t kPkS = (size_t)CAP * 4 + 16;
     static constexpr size_t kPkB = (size_t)CAP * 4;
@@ -731,7 +720,9 @@ struct TileLayout {
     static constexpr size_t kCnt = (size_t)(NBK + 1) * 4;
     static constexpr size_t kMask = (size_t)(CAP / 32) * 4;
     static constexpr size_t oPkS = NS * kStage;
-    static constexpr size_t oChgS = oPkS + kPkS;
+    static constexpr size_t oPkB = oPkS + kPkS;
+    static constexpr size_t oChgB = oPkB + kPkB;
+    static constexpr size_t oChgS = oChgB + kChg;
     static constexpr size_t oFlk = oChgS + kChg;
     static constexpr size_t oCnt = oFlk + kFlk;
     static constexpr size_t oMask = oCnt + kCnt;
@@ -762,8 +753,17 @@ struct TileCtx {
         return reinterpret_cast<uint64_t *>(g_tile_smem + (size_t)b * L::kStage);
     }
     __device__ __forceinline__ uint32_t *pk_s() const { return reinterpret_cast<uint32_t *>(g_tile_smem + L::oPkS); }
+    __device__ __forceinline__ uint32_t *pk_b() const { return reinterpret_cast<uint32_t *>(g_tile_smem + L::oPkB); }
+    __device__ __forceinline__ uint16_t *seed_idx() const { return reinterpret_cast<uint16_t *>(g_tile_smem + L::oPkB); }
+    __device__ __forceinline__ uint16_t *seed_cnt() const
+    {
+        return reinterpret_cast<uint16_t *>(g_tile_smem + L::oPkB) + CAP;
+    }
+    __device__ __forceinline__ uint16_t *chg_b() const { return reinterpret_cast<uint16_t *>(g_tile_smem + L::oChgB); }
     __device__ __forceinline__ uint16_t *chg_s() const { return reinterpret_cast<uint16_t *>(g_tile_smem + L::oChgS); }
     __device__ __forceinline__ uint16_t *flk() const { return reinterpret_cast<uint16_t *>(g_tile_smem + L::oFlk); }
+    // per-warp lists of the seed rounds (the bucket-order key region, free then)
+    __device__ __forceinline__ uint16_t *live() const { return reinterpret_cast<uint16_t *>(g_tile_smem + L::oPkB); }
     __device__ __forceinline__ uint32_t *cnt() const { return reinterpret_cast<uint32_t *>(g_tile_smem + L::oCnt); }
     __device__ __forceinline__ uint32_t *mask() const { return reinterpret_cast<uint32_t *>(g_tile_smem + L::oMask); }
     __device__ __forceinline__ uint16_t *floor_s() const { return reinterpret_cast<uint16_t *>(g_tile_smem + L::oTab); }
@@ -1091,7 +1091,7 @@ __device__ __forceinline__ uint32_t bucket_shift(uint32_t span)
 // Returns the counts and c0 = the number of staged keys before the core.
 // cnt and mask are zero on entry and on return.
 template <int CAP, int NC, bool SMEM_DT, bool EXT, bool DENSE>
-__device__ CoreOut tile_pass(TileCtx<CAP> &cx, uint64_t *stage, uint32_t n, int64_t tb, uint32_t span,
+__device__ CoreOut tile_pass(TileCtx<CAP> &cx, const uint64_t *stage, uint32_t n, int64_t tb, uint32_t span,
                              uint32_t lo_t, uint32_t hi_t, const TrigParams &tp, trig_trigger *out, bool out_at_c0,
                              int64_t dbg_rank_lo, uint64_t *release_bar)
 {
@@ -1166,13 +1166,8 @@ __device__ CoreOut tile_pass(TileCtx<CAP> &cx, uint64_t *stage, uint32_t n, int6
     //    the bucket
     uint32_t *pk = cx.pk_s();
     uint16_t *chg = cx.chg_s(), *flk = cx.flk();
-    // scratch in the stage buffer, read in A only: keys and charges in
-    // bucket order (SORT), then the seed rounds' lists, the seed list and
-    // counts, the count's batch tables
-    uint32_t *pk_b = reinterpret_cast<uint32_t *>(stage);
-    uint16_t *chg_b = reinterpret_cast<uint16_t *>(reinterpret_cast<unsigned char *>(stage) + (size_t)CAP * 4);
-    uint32_t *pk_c = SORT ? pk_b : pk;
-    uint16_t *chg_c = SORT ? chg_b : chg;
+    uint32_t *pk_c = SORT ? cx.pk_b() : pk;
+    uint16_t *chg_c = SORT ? cx.chg_b() : chg;
     const uint16_t *fl = cx.floor_s();
     const bool charge_rule = !(EXT && tp.seed_rule == 1);
 #pragma unroll
@@ -1243,7 +1238,7 @@ __device__ CoreOut tile_pass(TileCtx<CAP> &cx, uint64_t *stage, uint32_t n, int6
         const uint32_t d_n = r_hi > r_lo ? r_hi - r_lo : 0u;
         const uint32_t share = ((d_n + NW - 1) / NW + 31u) & ~31u;
         const uint32_t w_begin = min(r_lo + warp * share, r_hi), w_end = min(w_begin + share, r_hi);
-        uint32_t *live = pk_b + warp * (CAP / NW);
+        uint32_t *live = cx.pk_b() + warp * (CAP / NW);
         auto core = [&](uint32_t i, uint32_t ti) { return SORT ? (i >= c0 && i < c1) : (ti >= lo_t && ti < hi_t); };
         auto pair = [&](uint32_t i, uint32_t j, uint32_t ki, uint32_t kj) {
             const uint32_t ti = ki >> 12, tj = kj >> 12;
@@ -1327,7 +1322,7 @@ __device__ CoreOut tile_pass(TileCtx<CAP> &cx, uint64_t *stage, uint32_t n, int6
     //    CAP / 32 <= NC words); each word's offset adds the totals of the
     //    warps before it.  Marks lie in the core: sorted, positions
     //    [c0, c1); in bucket order, the buckets of [lo_t, hi_t)
-    uint16_t *seed_idx = SORT ? reinterpret_cast<uint16_t *>(pk_b) : cx.flk();
+    uint16_t *seed_idx = SORT ? cx.seed_idx() : cx.flk();
     const uint32_t p_lo = SORT ? c0 : cnt[bucket_of<CAP>(lo_t, bsh)];
     const uint32_t p_hi = SORT ? c1 : cnt[bucket_of<CAP>(hi_t > 0 ? hi_t - 1 : 0, bsh) + 1];
     const uint32_t w_lo = p_lo >> 5, w_hi = (p_hi + 31) >> 5;
@@ -1362,7 +1357,9 @@ __device__ CoreOut tile_pass(TileCtx<CAP> &cx, uint64_t *stage, uint32_t n, int6
 
     // F. causal count c(s) over each seed's scan range (sparse batches give
     //    each seed 4 lanes, dense ones a warp), or its distinct-PMT form
-    uint16_t *seed_cnt = reinterpret_cast<uint16_t *>(pk_b) + CAP;
+    // (in bucket order the seed list sits in the floor array, so the
+    // counts take the second half of the bucket-order key region)
+    uint16_t *seed_cnt = cx.seed_cnt();
     if (EXT && tp.count_distinct) {
         count_distinct_pmts<CAP, NC, SMEM_DT>(cx, pk, n, ns, seed_idx, bsh, seed_cnt);
     } else {
@@ -1599,54 +1596,15 @@ __device__ void tile_overflow(TileCtx<CAP> &cx, uint64_t *buf, const SliceDesc &
     cons_sync<NC>();
 }
 
-// The producer's plan for one work item: where its hits are, the runs to
-// copy (one per PMT of a narrow slice, at most kWideMinPmt - 1; one range of
-// the bucketed copy for a wide slice) and where each lands in the staging
-// buffer.
-constexpr uint32_t kMaxRuns = kWideMinPmt - 1;
-struct LookSlot {
-    ItemInfo info;
-    const trig_hit *src;
-    uint32_t nruns;
-    uint32_t pad;
-    uint32_t run_src[kMaxRuns];     // first hit of the run, index into src
-    uint32_t run_len[kMaxRuns];
-    uint32_t run_dst[kMaxRuns];     // its first record in the staging buffer
-};
-
-// The consumers stage an item with bulk copies (cp.async.bulk, the TMA
-// engine), one per PMT run issued by one thread each (narrow slices), or
-// one over the item's range (wide slices), all completing on `bar`; thread
-// 0 arms `bar` with the item's bytes (or just arrives when nothing is
-// copied), so the phase completes once every byte has landed.
-template <int NC>
-__device__ __forceinline__ void stage_item(const LookSlot &L, uint64_t *stage, uint64_t *bar)
-{
-    const uint32_t tid = threadIdx.x;
-    const bool copy = L.info.item >= 0 && L.info.mode == 0;
-    if (tid == 0) {
-        if (copy) mbar_arrive_expect_tx(bar, L.info.n * 16u);
-        else mbar_arrive(bar);
-    }
-    if (!copy) return;
-    for (uint32_t r = tid; r < L.nruns; r += NC) {
-        const uint32_t len = L.run_len[r];
-        if (len) bulk_g2s(stage + 2 * (size_t)L.run_dst[r], L.src + L.run_src[r], len * 16u, bar);
-    }
-}
-
 template <int CAP, int NC, bool SMEM_DT, bool EXT, bool DENSE>
 __global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 1)) k_tile(BatchHeader *__restrict__ hdr,
                                                                           const SliceDesc *__restrict__ desc,
                                                                           uint32_t max_pmt)
 {
     constexpr uint32_t NW = NC / 32;
-    // look_full[s]: the producer published slot s; look_empty[s]: every
-    // consumer warp has issued slot s's copies and the slot may be reused
-    // full_bar[b]: staging buffer b holds its item
-    __shared__ uint64_t look_full[2], look_empty[2], full_bar[2];
-    __shared__ LookSlot look[2];
-    __shared__ ItemInfo cinfo[2];           // the consumers' copy of each staged item's plan
+    constexpr uint32_t NSTG = TileLayout<CAP>::NS;
+    __shared__ uint64_t full_bar[2], empty_bar[2];
+    __shared__ ItemInfo info[2];
     __shared__ __align__(16) uint32_t red[64 + 64];
     __shared__ int64_t stk[128];
 
@@ -1657,12 +1615,10 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 
 
     const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = lane_id();
     if (tid == 0) {
-        mbar_init(&look_full[0], 1);
-        mbar_init(&look_full[1], 1);
-        mbar_init(&look_empty[0], NW);
-        mbar_init(&look_empty[1], NW);
         mbar_init(&full_bar[0], 1);
         mbar_init(&full_bar[1], 1);
+        mbar_init(&empty_bar[0], 1);
+        mbar_init(&empty_bar[1], 1);
         fence_mbar_init();
     }
     __syncthreads();
@@ -1671,26 +1627,27 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 
     const uint64_t wait_ns = hdr->wait_ns;
 
     if (warp == NW) {
-        // test control: publish nothing, so that the consumers' first wait
+        // test control: stage nothing, so that the consumers' first wait
         // runs out (no copy is ever in flight)
         if (hdr->stall) return;
         // ------------------------------------------------ producer warp
-        // Dequeues items and looks up each one's runs; the next item is
-        // dequeued and looked up before waiting for a free slot.
+        // The next item is dequeued and its per-PMT runs looked up before
+        // waiting for a free buffer, so those global loads overlap the wait.
         uint32_t s = 0;
         bool bad = false;
         const SliceDesc *d = nullptr;
-        constexpr int R = 4;                       // PMTs per lane (P <= 128 for narrow slices)
+        constexpr int R = 4;                       // PMTs per lane kept in registers
         uint32_t item = 0;
         if (lane == 0) item = atomicAdd(&hdr->queue, 1u);
         item = __shfl_sync(0xffffffffu, item, 0);
         for (uint32_t it = 0;; ++it) {
-            const uint32_t b = it & 1u, use = it >> 1;
+            const uint32_t b = it % NSTG, use = it / NSTG;
 #ifdef TRIG_PHASE_STATS
             const long long tp0 = clock64();
 #endif
             uint32_t g = 0, P = 0, mode = 2, lo_t = 0, span = 0;
-            uint32_t ra[R], rl[R];
+            uint64_t ra[R];
+            uint32_t rl[R];
             uint64_t tot = 0, rlo = 0;
             bool wide = false;
             if (item < n_items) {
@@ -1724,22 +1681,24 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 
                     const uint64_t *poff = d->pmt_off;
                     lo_t = d->halo;
                     span = (uint32_t)d->tile_w + 2u * d->halo;
+                    if (!bad) {
 #pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        const uint32_t p = r * 32 + lane;
-                        uint64_t a = 0, e = 0, sp_ = 0, ep_ = 0;
-                        if (!bad && p < P) {
-                            a = __ldg(elo + p);
-                            e = __ldg(ehi + p);
-                            sp_ = __ldg(poff + p);
-                            ep_ = __ldg(poff + p + 1);
-                            a = min(max(a, sp_), ep_);
-                            e = min(max(e, a), ep_);
+                        for (int r = 0; r < R; ++r) {
+                            const uint32_t p = r * 32 + lane;
+                            uint64_t a = 0, e = 0, sp_ = 0, ep_ = 0;
+                            if (p < P) {
+                                a = __ldg(elo + p);
+                                e = __ldg(ehi + p);
+                                sp_ = __ldg(poff + p);
+                                ep_ = __ldg(poff + p + 1);
+                                a = min(max(a, sp_), ep_);
+                                e = min(max(e, a), ep_);
+                            }
+                            ra[r] = a;
+                            rl[r] = (uint32_t)(e - a);
+                            tot += e - a;
+                            rlo += a - sp_;
                         }
-                        ra[r] = (uint32_t)a;
-                        rl[r] = (uint32_t)(e - a);
-                        tot += e - a;
-                        rlo += a - sp_;
                     }
                     tot = warp_sum_u64(tot);
                     rlo = warp_sum_u64(rlo);
@@ -1751,20 +1710,20 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 
                 if (lane == 0) next = atomicAdd(&hdr->queue, 1u);
                 next = __shfl_sync(0xffffffffu, next, 0);
             }
-            // lane 0 waits (bounded) for the slot and decides for the warp
+            // lane 0 waits (bounded) for the buffer and decides for the warp
 #ifdef TRIG_PHASE_STATS
             const long long tw0 = clock64();
             if (lane == 0) PHASE_ADD(kPhProdItem, tw0 - tp0);
 #endif
             uint32_t free_ok = 1;
-            if (it >= 2 && lane == 0) {
+            if (it >= NSTG && lane == 0) {
 #ifdef TRIG_PHASE_STATS
                 uint32_t pr = 0;
-                free_ok = mbar_wait(&look_empty[b], (use - 1) & 1u, wait_ns, &pr) ? 1u : 0u;
+                free_ok = mbar_wait(&empty_bar[b], (use - 1) & 1u, wait_ns, &pr) ? 1u : 0u;
                 PHASE_ADD(kPhProdWait, clock64() - tw0);
                 PHASE_ADD(kPhProdWaitRounds, pr);
 #else
-                free_ok = mbar_wait(&look_empty[b], (use - 1) & 1u, wait_ns) ? 1u : 0u;
+                free_ok = mbar_wait(&empty_bar[b], (use - 1) & 1u, wait_ns) ? 1u : 0u;
 #endif
             }
             free_ok = __shfl_sync(0xffffffffu, free_ok, 0);
@@ -1773,47 +1732,41 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 
                 if (lane == 0) atomicOr(&hdr->err, TRIG_FLAG_TIMEOUT);
                 break;
             }
-            LookSlot &L = look[b];
             if (item >= n_items) {
                 if (lane == 0) {
-                    L.info.item = -1;
-                    mbar_arrive(&look_full[b]);
+                    info[b].item = -1;
+                    mbar_arrive(&full_bar[b]);
                 }
                 break;
             }
             if (lane == 0) {
-                L.info.item = (int32_t)item;
-                L.info.slice = s;
-                L.info.g = g;
-                L.info.n = (uint32_t)min(tot, (uint64_t)CAP);
-                L.info.rank_lo = (uint32_t)rlo;
-                L.info.mode = mode;
-                L.info.lo_t = lo_t;
-                L.info.span = span;
-                L.src = wide ? d->tbuf : d->hits;
-                L.nruns = mode != 0 ? 0u : (wide ? 1u : P);
-                if (wide) {
-                    L.run_src[0] = (uint32_t)rlo;
-                    L.run_len[0] = (uint32_t)tot;
-                    L.run_dst[0] = 0;
-                }
+                info[b].item = (int32_t)item;
+                info[b].slice = s;
+                info[b].g = g;
+                info[b].n = (uint32_t)min(tot, (uint64_t)CAP);
+                info[b].rank_lo = (uint32_t)rlo;
+                info[b].mode = mode;
+                info[b].lo_t = lo_t;
+                info[b].span = span;
+                if (mode == 0) mbar_arrive_expect_tx(&full_bar[b], (uint32_t)tot * 16u);
+                else mbar_arrive(&full_bar[b]);
             }
-            if (mode == 0 && !wide) {
+            __syncwarp();
+            if (mode == 0 && wide) {
+                if (lane == 0 && CHECK(7, rlo + tot, d->n_hits + 1))
+                    bulk_g2s(cx.stage(b), d->tbuf + rlo, (uint32_t)tot * 16u, &full_bar[b]);
+            } else if (mode == 0) {
                 uint32_t dst = 0;
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    const uint32_t p = r * 32 + lane;
-                    const uint32_t incl = warp_incl_scan(rl[r]);
-                    if (p < P) {
-                        L.run_src[p] = ra[r];
-                        L.run_len[p] = rl[r];
-                        L.run_dst[p] = dst + incl - rl[r];
-                    }
+                    const uint32_t len = rl[r];
+                    const uint64_t a = ra[r];
+                    const uint32_t incl = warp_incl_scan(len);
+                    if (len && CHECK(6, dst + incl, CAP + 1) && CHECK(7, a + len, d->n_hits + 1))
+                        bulk_g2s(cx.stage(b) + 2 * (size_t)(dst + incl - len), d->hits + a, len * 16u, &full_bar[b]);
                     dst += __shfl_sync(0xffffffffu, incl, 31);
                 }
             }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&look_full[b]);       // releases the slot's writes
 #ifdef TRIG_PHASE_STATS
             if (lane == 0) PHASE_ADD(kPhProdTotal, clock64() - tp0);
 #endif
@@ -1826,6 +1779,7 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 
     // the tile pass expects zero bucket counts and seed mask (and leaves them so)
     for (uint32_t i = tid; i < (uint32_t)TileLayout<CAP>::NBK; i += NC) cx.cnt()[i] = 0;
     for (uint32_t i = tid; i < (uint32_t)CAP / 32; i += NC) cx.mask()[i] = 0;
+    cons_sync<NC>();
     const SliceDesc *loaded = nullptr;
     // the slice's trigger parameters live in shared memory (written by one
     // thread when the slice changes), keeping registers for the tile phases
@@ -1833,63 +1787,32 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 
     // the loaded slice's tile width, t0, length and merged rank of its first
     // owned hit, also kept in shared memory
     __shared__ int64_t sl[4];
-    __shared__ uint32_t s_ok;
-    // Item it+1 is staged while item it is processed: wait for its plan,
-    // issue its copies, keep a copy of the plan, hand the slot back.  One
-    // thread waits (bounded) and the barrier gives every thread its
-    // decision, so the block never splits on a timeout.
-    auto take = [&](uint32_t it) -> bool {
-        const uint32_t b = it & 1u;
-        if (tid == 0) {
+    for (uint32_t it = 0;; ++it) {
+        const uint32_t b = it % NSTG, use = it / NSTG;
+        // every thread waits (bounded) for the staged tile; the barrier
+        // ANDs their results, so the block never splits on a timeout
 #ifdef TRIG_PHASE_STATS
-            const long long tw0 = clock64();
-            uint32_t cr = 0;
-            s_ok = mbar_wait(&look_full[b], (it >> 1) & 1u, wait_ns, &cr) ? 1u : 0u;
+        const long long tw0 = clock64();
+        uint32_t cr = 0;
+        const bool cwait_ok = mbar_wait(&full_bar[b], use & 1u, wait_ns, &cr);
+        if (tid == 0) {
             PHASE_ADD(kPhConsWait, clock64() - tw0);
             PHASE_ADD(kPhConsWaitRounds, cr);
+            PHASE_ADD(kPhTiles, 1);
+        }
 #else
-            s_ok = mbar_wait(&look_full[b], (it >> 1) & 1u, wait_ns) ? 1u : 0u;
+        const bool cwait_ok = mbar_wait(&full_bar[b], use & 1u, wait_ns);
 #endif
+        if (!named_sync_and(kBarCons, NC, cwait_ok)) {
+            if (tid == 0) atomicOr(&hdr->err, TRIG_FLAG_TIMEOUT);
+            break;
         }
-        cons_sync<NC>();
-        if (!s_ok) return false;
-        stage_item<NC>(look[b], cx.stage(b), &full_bar[b]);
-        if (tid == 0) cinfo[b] = look[b].info;
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&look_empty[b]);
-        return true;
-    };
-    // items [waited, taken) have copies that may still be in flight
-    uint32_t taken = 0, waited = 0;
-    bool ok = take(0);
-    taken = ok ? 1u : 0u;
-    cons_sync<NC>();
-    for (uint32_t it = 0; ok; ++it) {
-        const uint32_t b = it & 1u;
-        const ItemInfo inf = cinfo[b];
+        const ItemInfo &inf = info[b];      // stable until this buffer is released
         if (inf.item < 0) break;
-        if (!take(it + 1)) {
-            ok = false;
-            break;
-        }
-        taken = it + 2;
-        // item it has landed: one thread waits (bounded), the barrier
-        // passes its decision on, and every thread then observes the
-        // completed phase itself
-        if (tid == 0) s_ok = mbar_wait(&full_bar[b], (it >> 1) & 1u, wait_ns) ? 1u : 0u;
-        cons_sync<NC>();
-        if (!s_ok) {
-            ok = false;
-            break;
-        }
-        (void)mbar_try_wait(&full_bar[b], (it >> 1) & 1u);
-        waited = it + 1;
-#ifdef TRIG_PHASE_STATS
-        if (tid == 0) PHASE_ADD(kPhTiles, 1);
-#endif
         const SliceDesc &d = desc[inf.slice];
         if (&d != loaded) {
             // (re)load the detector tables of this slice
+            cons_sync<NC>();
             const uint32_t P = d.n_pmt;
             for (uint32_t p = tid; p < P; p += NC) {
                 cx.floor_s()[p] = d.floor[p];
@@ -1916,6 +1839,8 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 
                 tp.rel = d.rel;
                 tp.dbg_merged = d.dbg_merged;
                 tp.dbg_seedcnt = d.dbg_seedcnt;
+            }
+            if (tid == 0) {
                 sl[0] = d.tile_w;
                 sl[1] = d.t0;
                 sl[2] = d.slice_ns;
@@ -1932,32 +1857,32 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 
             tile_overflow<CAP, NC, SMEM_DT, EXT, DENSE>(cx, cx.stage(b), d, tp, inf.g, red, stk);
         } else {
             const int64_t W = sl[0];
-            const int64_t Bg = sl[1] + (int64_t)inf.g * W;
+            const uint32_t g = inf.g, n_st = inf.n, rank_lo = inf.rank_lo, span = inf.span;
+            const int64_t Bg = sl[1] + (int64_t)g * W;
             const int64_t core_end = min(Bg + W, sl[1] + sl[2]);
             // the staged range starts lo_t (>= H) before the core
-            const int64_t tb = Bg - (int64_t)inf.lo_t;
-            const uint32_t hi_t = inf.lo_t + (uint32_t)(core_end - Bg);
-            // the core's first hit has merged rank rank_lo + c0
-            CoreOut co = tile_pass<CAP, NC, SMEM_DT, EXT, DENSE>(cx, cx.stage(b), inf.n, tb, inf.span, inf.lo_t, hi_t,
-                                                                 tp, d.stage + inf.rank_lo, true,
-                                                                 (int64_t)inf.rank_lo - sl[3], nullptr);
-            const uint32_t tile_rank = inf.rank_lo + co.c0;
-            if (tid == 0 && CHECK(14, (uint64_t)tile_rank + co.n_fired, d.n_hits + 1) && CHECK(15, inf.g, d.n_tiles)) {
-                d.tile_nfired[inf.g] = co.n_fired;
-                d.tile_rank[inf.g] = tile_rank;
+            const uint32_t lo_t = inf.lo_t;
+            const int64_t tb = Bg - (int64_t)lo_t;
+            const uint32_t hi_t = lo_t + (uint32_t)(core_end - Bg);
+            // the pass hands the buffer back as soon as it has read it (inf
+            // is not read after that); the core's first hit has merged rank
+            // rank_lo + c0
+            CoreOut co = tile_pass<CAP, NC, SMEM_DT, EXT, DENSE>(cx, cx.stage(b), n_st, tb, span, lo_t, hi_t, tp,
+                                                                 d.stage + rank_lo, true,
+                                                                 (int64_t)rank_lo - sl[3], &empty_bar[b]);
+            const uint32_t tile_rank = rank_lo + co.c0;
+            if (tid == 0 && CHECK(14, (uint64_t)tile_rank + co.n_fired, d.n_hits + 1) && CHECK(15, g, d.n_tiles)) {
+                d.tile_nfired[g] = co.n_fired;
+                d.tile_rank[g] = tile_rank;
                 atomicAdd(reinterpret_cast<unsigned long long *>(&d.stats->n_seeds), (unsigned long long)co.n_seeds);
             }
+            continue;
         }
-        // every thread is done with item it's staging buffer and plan
-        // (its generic accesses ordered before the next bulk copy into the
-        // buffer) before the next iteration stages item it + 2 into it
+        // release the buffer to the producer: order our generic-proxy
+        // accesses before its next bulk copy into the same buffer
         fence_proxy_async_smem();
         cons_sync<NC>();
-    }
-    if (tid == 0) {
-        if (!ok) atomicOr(&hdr->err, TRIG_FLAG_TIMEOUT);
-        // no copy of this block is left in flight when it exits (bounded)
-        for (uint32_t j = waited; j < taken; ++j) (void)mbar_wait(&full_bar[j & 1u], (j >> 1) & 1u, wait_ns);
+        if (tid == 0) mbar_arrive(&empty_bar[b]);
     }
 }
 
