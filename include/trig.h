@@ -308,8 +308,9 @@ int trig_engine_trace_read(trig_trace_rec *out, uint32_t max, uint32_t *n_out);
  * 600 s), sets TRIG_FLAG_TIMEOUT and ends the pass; the batch's slices then
  * report TRIG_ETIMEOUT with no output, and the device stays usable.
  * stall = 1 is a test control: later batches stage no tile, so the first
- * wait of every block runs out with no copy in flight; stall = 0 ends it.
- * Applies to batches planned after the call. */
+ * wait of every block runs out with no copy in flight; stall = 0 ends it;
+ * any other value is TRIG_EINVAL.  Applies to batches planned after the
+ * call. */
 int trig_set_device_wait(uint64_t limit_ns, int stall);
 
 /* Page-locked host memory for a producer's slice buffers (the Hit
@@ -466,10 +467,10 @@ uint64_t trig_kernel_launch_count(void);
 /* Average device time per kernel of the pipeline over the runs made with
  * TRIG_RUN_TIMED since the previous call (waits for their events), in the
  * launch order k_prep, k_bounds, k_bsum, k_bscan, k_scatter, k_tile,
- * k_evhalo, k_scan, k_copy, k_wscan, k_wwrite, k_whits, k_escan (with
- * k_wrank), k_events, k_status.  k_bsum, k_bscan and k_scatter run only for
- * batches with a detector of 129 or more PMTs, k_evhalo, k_wrank, k_escan
- * and k_events only for event extraction; the others read about 0.
+ * k_evhalo, k_scan, k_copy, k_wscan, k_wwrite, k_wcount, k_escan,
+ * k_events, k_status.  k_bsum, k_bscan and k_scatter run only for batches
+ * with a detector of 129 or more PMTs, k_evhalo, k_escan and k_events only
+ * for event extraction; the others read about 0.
  * avg_ms[i] and names[i] (static strings) for i < max_kernels; returns the
  * number of kernels (15) and the number of runs in *n_runs. */
 int trig_kernel_times(double *avg_ms, const char **names, uint32_t max_kernels, uint32_t *n_runs);

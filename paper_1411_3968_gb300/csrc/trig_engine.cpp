@@ -566,6 +566,10 @@ static int plan_into(const trig_slice_dev *sl, uint32_t n, uintptr_t base, const
         off += align256((size_t)d.n_tiles * 4);
         d.stage = reinterpret_cast<trig_trigger *>(base + off);
         off += align256((size_t)x.n_hits * sizeof(trig_trigger));
+        d.wrank = reinterpret_cast<uint32_t *>(base + off);
+        off += align256((size_t)x.n_hits * 8);
+        d.win_r = reinterpret_cast<uint32_t *>(base + off);
+        off += align256((size_t)x.win_cap * 8);
         d.triggers = x.triggers;
         d.trig_cap = x.trig_cap;
         d.windows = x.windows;
@@ -1774,6 +1778,21 @@ static uint64_t host_lb(const trig_hit *h, uint64_t lo, uint64_t hi, int64_t v)
     return lo;
 }
 
+// The same for a v near the end of the run: steps of 1, 2, 4, ... back from
+// hi, then a bisection of the last step, so a tail of k hits costs about
+// 2 log2(k) reads near the run's end instead of log2(run) scattered ones.
+static uint64_t host_lb_back(const trig_hit *h, uint64_t lo, uint64_t hi, int64_t v)
+{
+    uint64_t right = hi, step = 1;
+    while (right > lo) {
+        const uint64_t left = right - std::min<uint64_t>(step, right - lo);
+        if (h[left].t_ns < v) return host_lb(h, left + 1, right, v);
+        right = left;
+        step <<= 1;
+    }
+    return lo;
+}
+
 extern "C" int trig_submit_slice(trig_detector *det, int64_t t0, const trig_hit *hits, const uint64_t *pmt_off,
                                  int is_continuation, uint64_t *slice_id_out)
 {
@@ -1850,19 +1869,19 @@ extern "C" int trig_submit_slice(trig_detector *det, int64_t t0, const trig_hit 
                             reinterpret_cast<const uint64_t *>(raw + raw_pmt_at), n, P,
                             reinterpret_cast<trig_hit *>(p.dblk), reinterpret_cast<uint64_t *>(p.dblk + p.pmt_at),
                             copy_stream);
-    if (!ce) ce = cudaStreamSynchronize(copy_stream);
-    // the next slice's leading halo: this submission's hits in
-    // [t0 + S - halo, t0 + S), PMT by PMT (a producer's unordered stream
-    // gives some sub-range; the device flags such a slice)
+    // the next slice's leading halo, found while the copy runs: this
+    // submission's hits in [t0 + S - halo, t0 + S), PMT by PMT (a producer's
+    // unordered stream gives some sub-range; the device flags such a slice)
     std::vector<uint64_t> toff(P + 1, 0);
     std::vector<trig_hit> th;
+    for (uint32_t q = 0; q < P; ++q) {
+        const uint64_t a = host_lb_back(hits, pmt_off[q], pmt_off[q + 1], t0 + S - halo);
+        const uint64_t b = host_lb_back(hits, a, pmt_off[q + 1], t0 + S);
+        th.insert(th.end(), hits + a, hits + b);
+        toff[q + 1] = th.size();
+    }
+    if (!ce) ce = cudaStreamSynchronize(copy_stream);
     if (!ce) {
-        for (uint32_t q = 0; q < P; ++q) {
-            const uint64_t a = host_lb(hits, pmt_off[q], pmt_off[q + 1], t0 + S - halo);
-            const uint64_t b = host_lb(hits, a, pmt_off[q + 1], t0 + S);
-            th.insert(th.end(), hits + a, hits + b);
-            toff[q + 1] = th.size();
-        }
         if (th.size() > tl.cap) {
             cudaFree(tl.d_hits);
             tl.d_hits = nullptr;

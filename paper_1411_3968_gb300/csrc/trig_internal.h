@@ -88,6 +88,10 @@ struct SliceDesc {
     uint32_t *bkt_part;     // [ceil(NB / kBktChunk)] sums of the counts per chunk
     trig_hit *tbuf;         // [n_hits] hits in bucket order
     trig_trigger *stage;    // [n_hits] fired seeds at their merged rank
+    uint32_t *wrank;        // [n_hits][2] beside each staged fired seed: the merged ranks of the
+                            //   first hit at or after t - win_half and of the first after t + win_half
+    uint32_t *win_r;        // [win_cap][2] a window's first-hit rank (from its first trigger)
+                            //   and its one-past-last rank (from its last trigger)
     uint32_t *tile_nfired;  // [NG]
     uint32_t *tile_rank;    // [NG] merged rank of the tile's first core hit
     uint32_t *tile_out;     // [NG] exclusive prefix of tile_nfired

@@ -18,8 +18,10 @@
 //              strategy"), and emit the fired seeds at their merged rank.
 //   k_scan / k_copy   stream compaction of the fired seeds (tile prefix sum,
 //              then a copy into the dense trigger list).
-//   k_windows  the +-3 us windows around the triggers, merged while
-//              lo_next <= hi_cur + 1, with the hit count inside each.
+//   k_wscan / k_wwrite / k_wcount   the +-3 us windows around the
+//              triggers, merged while lo_next <= hi_cur + 1, with the hit
+//              count inside each: the difference of two merged ranks the
+//              tile pass records beside each fired seed.
 //
 // Every wait on an mbarrier is bounded; a wait that gives up sets
 // TRIG_FLAG_TIMEOUT on the batch and the kernel returns.
@@ -664,7 +666,11 @@ __global__ void __launch_bounds__(kBktChunk) k_bscan(const BatchHeader *__restri
 
 // Wide slices: every hit copied to its time bucket's range of tbuf (the
 // order inside a bucket is arbitrary; the tile pass sorts).  Slices with
-// malformed input (flagged by the structure pass) are skipped.
+// malformed input (flagged by the structure pass) are skipped.  Chunks of
+// different PMTs cover the same times, so blocks that walked their chunks
+// in step would aim their fill-cursor atomics at the same buckets; each
+// chunk starts at its own offset instead (whole 256-hit rows, so the loads
+// stay coalesced).
 __global__ void __launch_bounds__(256) k_scatter(const BatchHeader *__restrict__ hdr, const SliceDesc *__restrict__ desc)
 {
     const uint32_t n_slices = hdr->n_slices, n_chunks = hdr->n_chunks;
@@ -673,9 +679,11 @@ __global__ void __launch_bounds__(256) k_scatter(const BatchHeader *__restrict__
         if (!d.wide) continue;
         if (d.stats->flags & (TRIG_FLAG_BAD_PMT | TRIG_FLAG_UNSORTED | TRIG_FLAG_OUT_OF_RANGE)) continue;
         const uint64_t first = (uint64_t)(c - d.chunk0) * kChunkHits;
+        constexpr uint32_t kRows = kChunkHits / 256;
+        const uint32_t rot = ((c * 2654435761u) >> 16) % kRows * 256;
         for (uint32_t k = threadIdx.x; k < kChunkHits; k += blockDim.x) {
-            const uint64_t li = first + k;
-            if (li >= d.n_hits) break;
+            const uint64_t li = first + (k + rot) % kChunkHits;
+            if (li >= d.n_hits) continue;
             const int4 v = *reinterpret_cast<const int4 *>(d.hits + li);
             const int64_t t = (int64_t)(((uint64_t)(uint32_t)v.y << 32) | (uint32_t)v.x);
             const uint32_t b = bkt_index(d, t);
@@ -710,7 +718,9 @@ struct ItemInfo {
 // (floor, row maximum of dt, and dt itself when the detector's table fits).
 template <int CAP>
 struct TileLayout {
-    static constexpr int NBK = CAP;                        // time buckets of the in-tile merge
+    // time buckets of the in-tile merge, at most: two per hit slot up to
+    // 2048 hits (shorter chains in the floor-coincidence rounds), one at 4096
+    static constexpr int NBK = CAP <= 2048 ? 2 * CAP : CAP;
     static constexpr uint32_t NS = CAP == 2048 ? 1u : 2u;  // staging buffers
     static constexpr size_t kStage = (size_t)CAP * 16;     // one staging buffer
     static constexpr size_t kPkS = (size_t)CAP * 4 + 16;
@@ -727,6 +737,7 @@ struct TileLayout {
     static constexpr size_t oCnt = oFlk + kFlk;
     static constexpr size_t oMask = oCnt + kCnt;
     static constexpr size_t oTab = (oMask + kMask + 15) & ~(size_t)15;
+    static_assert(oCnt % 16 == 0, "the bucket counts are read as 16-byte vectors");
     static size_t bytes(uint32_t P, bool smem_dt)
     {
         size_t b = oTab;
@@ -773,6 +784,10 @@ struct TileCtx {
 
 constexpr uint32_t kBarCons = 1;        // named barrier of the consumers
 
+// Floor coincidences in bucket order: candidates of a key checked in the
+// first pass before the rounds take over.
+constexpr uint32_t kFloorPairs = 3;
+
 template <int NC>
 __device__ __forceinline__ void cons_sync() { named_sync(kBarCons, NC); }
 
@@ -788,41 +803,52 @@ __device__ __forceinline__ uint32_t pk_p(uint32_t k) { return k & 0xfffu; }
 
 // Consumer-wide exclusive scan of cnt[0..nb), nb a multiple of NC; writes
 // the total to cnt[nb].  Scratch words red[0..NC/32].
-template <int NC>
-__device__ void cons_exclusive_scan(uint32_t *cnt, uint32_t nb, uint32_t *red)
+template <int NC, uint32_t NB>
+__device__ void cons_exclusive_scan(uint32_t *cnt, uint32_t *red)
 {
-    constexpr uint32_t NW = NC / 32;
-    const uint32_t tid = threadIdx.x, per = nb / NC;
+    constexpr uint32_t NW = NC / 32, PER = NB / NC, V = PER / 4;
+    static_assert(NB % NC == 0 && PER % 4 == 0, "each thread scans whole 16-byte vectors");
+    const uint32_t tid = threadIdx.x;
+    uint4 *c4 = reinterpret_cast<uint4 *>(cnt) + tid * V;
+    uint4 v[V];
     uint32_t local = 0;
-    for (uint32_t i = 0; i < per; ++i) local += cnt[tid * per + i];
+#pragma unroll
+    for (uint32_t i = 0; i < V; ++i) {
+        v[i] = c4[i];
+        local += v[i].x + v[i].y + v[i].z + v[i].w;
+    }
     uint32_t incl = warp_incl_scan(local);
     if (lane_id() == 31) red[tid >> 5] = incl;
     cons_sync<NC>();
     if (tid < 32) {
-        uint32_t v = tid < NW ? red[tid] : 0u;
-        uint32_t vi = warp_incl_scan(v);
-        if (tid < NW) red[tid] = vi - v;
-        if (tid == NW - 1) red[NW] = vi;
+        uint32_t w = tid < NW ? red[tid] : 0u;
+        uint32_t wi = warp_incl_scan(w);
+        if (tid < NW) red[tid] = wi - w;
+        if (tid == NW - 1) red[NW] = wi;
     }
     cons_sync<NC>();
     uint32_t run = red[tid >> 5] + incl - local;
-    for (uint32_t i = 0; i < per; ++i) {
-        uint32_t c = cnt[tid * per + i];
-        cnt[tid * per + i] = run;
-        run += c;
+#pragma unroll
+    for (uint32_t i = 0; i < V; ++i) {
+        uint4 o;
+        o.x = run;
+        o.y = o.x + v[i].x;
+        o.z = o.y + v[i].y;
+        o.w = o.z + v[i].z;
+        run = o.w + v[i].w;
+        c4[i] = o;
     }
-    if (tid == 0) cnt[nb] = red[NW];
+    if (tid == 0) cnt[NB] = red[NW];
     cons_sync<NC>();
 }
 
-// Bucket of a time relative to the tile base: t_rel >> bsh, the last bucket
-// taking everything beyond.
-template <int CAP>
+// Bucket of a time relative to the tile base: t_rel >> bsh, the last of
+// the NB buckets taking everything beyond.
+template <uint32_t NB>
 __device__ __forceinline__ uint32_t bucket_of(uint32_t t_rel, uint32_t bsh)
 {
-    constexpr uint32_t NBK = TileLayout<CAP>::NBK;
     const uint32_t b = t_rel >> bsh;
-    return b < NBK ? b : NBK - 1;
+    return b < NB ? b : NB - 1;
 }
 
 struct CoreOut {
@@ -834,7 +860,7 @@ struct CoreOut {
 // Seeds, causal counts and emission over the sorted tile keys[0..n).  The
 // core is t_rel in [H, H + core_w).  Fired seeds go to out[0..n_fired).
 struct TrigParams {
-    uint32_t H, tau, q_seed, threshold;
+    uint32_t H, tau, q_seed, threshold, win_half;
     uint32_t l0_hits, l0_window, l0_distinct;
     uint32_t seed_rule, sc_w, fc_w, afc_w, count_distinct;
     const uint8_t *rel;
@@ -878,21 +904,21 @@ __device__ __noinline__ bool coincidence_seed(const uint32_t *pk, uint32_t n, ui
 // A seed's scan range: the keys [j0, j1) of the buckets covering
 // [t_s - d, t_s + d], d its row's maximum (keys beyond fail the causal
 // test), from the sorted tile's bucket offsets.
-template <int CAP>
+template <int CAP, uint32_t NB>
 __device__ __forceinline__ void seed_range(const TileCtx<CAP> &cx, uint32_t ts, uint32_t ps, uint32_t bsh,
                                            uint32_t &j0, uint32_t &j1)
 {
     const uint32_t dm = ps < cx.P ? (uint32_t)cx.dmax_s()[ps] : 0u;
     const uint32_t *boff = cx.cnt();
-    j0 = boff[bucket_of<CAP>(ts >= dm ? ts - dm : 0u, bsh)];
-    j1 = boff[bucket_of<CAP>(ts + dm, bsh) + 1];
+    j0 = boff[bucket_of<NB>(ts >= dm ? ts - dm : 0u, bsh)];
+    j1 = boff[bucket_of<NB>(ts + dm, bsh) + 1];
 }
 
 // Distinct-PMT causal count (P <= 128): c(s) = the number of different
 // PMTs among the keys j with |t_j - t_s| <= min(dt_max[p_s][p_j], W).
 // Eight lanes per seed each collect a 128-bit PMT set over every eighth key
 // of the seed's scan range; the sets are OR-ed and counted.
-template <int CAP, int NC, bool SMEM_DT>
+template <int CAP, int NC, bool SMEM_DT, uint32_t NB>
 __device__ __noinline__ void count_distinct_pmts(const TileCtx<CAP> &cx, const uint32_t *pk, uint32_t n, uint32_t ns,
                                                  const uint16_t *seed_idx, uint32_t bsh, uint16_t *seed_cnt)
 {
@@ -906,7 +932,7 @@ __device__ __noinline__ void count_distinct_pmts(const TileCtx<CAP> &cx, const u
             const uint32_t ks = pk[seed_idx[k]];
             const uint32_t ts = pk_t(ks), ps = pk_p(ks);
             uint32_t j0, j1;
-            seed_range<CAP>(cx, ts, ps, bsh, j0, j1);
+            seed_range<CAP, NB>(cx, ts, ps, bsh, j0, j1);
             if (CHECK(12, j1, n + 1) && CHECK(13, ps, P)) {
                 const uint16_t *row_s = cx.dt_s() + (size_t)ps * P;
                 const uint16_t *row_g = cx.dt_g + (size_t)ps * P;
@@ -987,7 +1013,7 @@ __device__ __noinline__ bool level0_pass(const uint32_t *pk, uint32_t n, uint32_
 // lanes per seed,
 // seeds dealt round-robin to the groups, four independent tests per lane in
 // flight.
-template <int CAP, int NC, bool SMEM_DT, uint32_t LG>
+template <int CAP, int NC, bool SMEM_DT, uint32_t LG, uint32_t NB>
 __device__ __forceinline__ void count_causal(const TileCtx<CAP> &cx, const uint32_t *pk, uint32_t n, uint32_t ns,
                                              const uint16_t *seed_idx, uint32_t bsh, uint16_t *seed_cnt)
 {
@@ -1012,7 +1038,7 @@ __device__ __forceinline__ void count_causal(const TileCtx<CAP> &cx, const uint3
             const uint32_t ks = pk[seed_idx[k]];
             const uint32_t ts = pk_t(ks), ps = pk_p(ks);
             uint32_t j0, j1;
-            seed_range<CAP>(cx, ts, ps, bsh, j0, j1);
+            seed_range<CAP, NB>(cx, ts, ps, bsh, j0, j1);
 #ifdef TRIG_PHASE_STATS
             keys_seen += gl == 0 ? j1 - j0 : 0u;
 #endif
@@ -1053,13 +1079,32 @@ __device__ __forceinline__ void count_causal(const TileCtx<CAP> &cx, const uint3
     }
 }
 
+// A window-edge rank the tile pass could not read off its staged keys.
+constexpr uint32_t kRankUnknown = 0xffffffffu;
+
+// Staged keys with time below x (relative to the staged range's start, x
+// in [0, span]): the buckets before x's bucket, plus the keys of that bucket
+// below x.  The keys of a bucket are contiguous in bucket order and in
+// sorted order alike.
+template <uint32_t NB>
+__device__ __forceinline__ uint32_t keys_before(const uint32_t *pk, const uint32_t *cnt, uint32_t n, uint32_t x,
+                                                uint32_t bsh, uint32_t span)
+{
+    if (x >= span) return n;
+    const uint32_t b = bucket_of<NB>(x, bsh);
+    uint32_t c = cnt[b];
+    const uint32_t e = cnt[b + 1];
+    for (uint32_t m = c; m < e; ++m) c += pk_t(pk[m]) < x;
+    return c;
+}
+
 // Bucket shift of a staged range of `span` ns: buckets of 2^bsh ns, NBK of
 // them cover the range.
-template <int CAP>
+template <uint32_t NB>
 __device__ __forceinline__ uint32_t bucket_shift(uint32_t span)
 {
     const uint32_t top = span > 1 ? 32u - __clz(span - 1u) : 0u;      // bits of span - 1
-    const uint32_t nb_bits = 31u - __clz((uint32_t)TileLayout<CAP>::NBK);
+    const uint32_t nb_bits = 31u - __clz(NB);
     return top > nb_bits ? top - nb_bits : 0u;
 }
 
@@ -1092,14 +1137,17 @@ __device__ __forceinline__ uint32_t bucket_shift(uint32_t span)
 // cnt and mask are zero on entry and on return.
 template <int CAP, int NC, bool SMEM_DT, bool EXT, bool DENSE>
 __device__ CoreOut tile_pass(TileCtx<CAP> &cx, const uint64_t *stage, uint32_t n, int64_t tb, uint32_t span,
-                             uint32_t lo_t, uint32_t hi_t, const TrigParams &tp, trig_trigger *out, bool out_at_c0,
-                             int64_t dbg_rank_lo, uint64_t *release_bar)
+                             uint32_t lo_t, uint32_t hi_t, const TrigParams &tp, trig_trigger *out, uint32_t *wr,
+                             bool out_at_c0, uint32_t rank_base, int64_t dbg_rank_lo, uint64_t *release_bar)
 {
     constexpr bool SORT = EXT;
     constexpr uint32_t NW = NC / 32;
     constexpr int PER = CAP / NC;
     const uint32_t tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
-    const uint32_t bsh = bucket_shift<CAP>(span);
+    // buckets of the in-tile merge: the finer grid where it pays (the dense
+    // builds, whose long causal scans dominate, keep one bucket per slot)
+    constexpr uint32_t NB = DENSE ? (uint32_t)CAP : (uint32_t)TileLayout<CAP>::NBK;
+    const uint32_t bsh = bucket_shift<NB>(span);
     const uint32_t tau = tp.tau;
     __shared__ uint32_t s_red[NW + 1];
     __shared__ uint32_t s_below[3];
@@ -1134,7 +1182,7 @@ __device__ CoreOut tile_pass(TileCtx<CAP> &cx, const uint64_t *stage, uint32_t n
             // t - tb in 32 bits (the staged range spans less than 2^20 ns)
             const uint32_t tr = min(v.x - (uint32_t)tb, span - 1u);
             key[r] = (tr << 12) | (v.z & 0xfffu);
-            const uint32_t slot = atomicAdd(&cnt[bucket_of<CAP>(tr, bsh)], 1u);
+            const uint32_t slot = atomicAdd(&cnt[bucket_of<NB>(tr, bsh)], 1u);
             cs[r] = (v.z & 0xffff0000u) | slot;
             below_lo += tr < lo_t;
             below_hi += tr < hi_t;
@@ -1157,7 +1205,7 @@ __device__ CoreOut tile_pass(TileCtx<CAP> &cx, const uint64_t *stage, uint32_t n
 
     // B. bucket offsets (the scan's barriers also publish s_below and end
     //    every read of the stage buffer)
-    cons_exclusive_scan<NC>(cnt, TileLayout<CAP>::NBK, s_red);
+    cons_exclusive_scan<NC, NB>(cnt, s_red);
     if (release_bar && tid == 0) mbar_arrive(release_bar);
     const uint32_t c0 = s_below[0], c1 = s_below[1], d_lo = s_below[2];
     PHASE_MARK(kPhA);
@@ -1174,7 +1222,7 @@ __device__ CoreOut tile_pass(TileCtx<CAP> &cx, const uint64_t *stage, uint32_t n
     for (int r = 0; r < PER; ++r) {
         if (key[r] != kPkNone) {
             const uint32_t tr = key[r] >> 12;
-            const uint32_t pos = cnt[bucket_of<CAP>(tr, bsh)] + (cs[r] & 0xffffu);
+            const uint32_t pos = cnt[bucket_of<NB>(tr, bsh)] + (cs[r] & 0xffffu);
             if (CHECK(22, pos, CAP)) {
                 pk_c[pos] = key[r];
                 chg_c[pos] = (uint16_t)(cs[r] >> 16);
@@ -1194,7 +1242,7 @@ __device__ CoreOut tile_pass(TileCtx<CAP> &cx, const uint64_t *stage, uint32_t n
         for (int r = 0; r < PER; ++r) {
             const uint32_t k = key[r];
             if (k == kPkNone) continue;
-            const uint32_t b = bucket_of<CAP>(k >> 12, bsh);
+            const uint32_t b = bucket_of<NB>(k >> 12, bsh);
             const uint32_t s0 = cnt[b], s1 = cnt[b + 1], q = cs[r] >> 16, pos = s0 + (cs[r] & 0xffffu);
             uint32_t rk = s0;
             for (uint32_t m = s0; m < s1; ++m) {
@@ -1233,8 +1281,8 @@ __device__ CoreOut tile_pass(TileCtx<CAP> &cx, const uint64_t *stage, uint32_t n
         // in contiguous shares per warp; a live entry is (end << 16) | i
         // with end the first position past i's candidates
         const uint32_t lt = (1u << lane) - 1u;
-        const uint32_t r_lo = SORT ? d_lo : cnt[bucket_of<CAP>(lo_t > tau ? lo_t - tau : 0u, bsh)];
-        const uint32_t r_hi = SORT ? c1 : cnt[bucket_of<CAP>(hi_t + tau - 1u, bsh) + 1];
+        const uint32_t r_lo = SORT ? d_lo : cnt[bucket_of<NB>(lo_t > tau ? lo_t - tau : 0u, bsh)];
+        const uint32_t r_hi = SORT ? c1 : cnt[bucket_of<NB>(hi_t + tau - 1u, bsh) + 1];
         const uint32_t d_n = r_hi > r_lo ? r_hi - r_lo : 0u;
         const uint32_t share = ((d_n + NW - 1) / NW + 31u) & ~31u;
         const uint32_t w_begin = min(r_lo + warp * share, r_hi), w_end = min(w_begin + share, r_hi);
@@ -1262,18 +1310,20 @@ __device__ CoreOut tile_pass(TileCtx<CAP> &cx, const uint64_t *stage, uint32_t n
                         pair(i, i + 1, ki, kj);
                     }
                 } else if (ti + tau >= lo_t && ti < hi_t + tau) {
-                    end = cnt[bucket_of<CAP>(ti + tau, bsh) + 1];
-                    if (i + 1 < end) {
-                        pair(i, i + 1, ki, pk[i + 1]);
-                        alive = i + 2 < end;
-                    }
+                    // the first kFloorPairs candidates inline (most keys
+                    // have no more), the rest in the rounds below
+                    end = cnt[bucket_of<NB>(ti + tau, bsh) + 1];
+#pragma unroll
+                    for (uint32_t r = 1; r <= kFloorPairs; ++r)
+                        if (i + r < end) pair(i, i + r, ki, pk[i + r]);
+                    alive = i + kFloorPairs + 1 < end;
                 }
             }
             const uint32_t m = __ballot_sync(0xffffffffu, alive);
             if (alive) live[nlive + __popc(m & lt)] = (end << 16) | i;
             nlive += __popc(m);
         }
-        for (uint32_t d = 2; nlive; ++d) {
+        for (uint32_t d = SORT ? 2u : kFloorPairs + 1; nlive; ++d) {
             uint32_t next = 0;
             for (uint32_t x = 0; x < nlive; x += 32) {
                 bool alive = false;
@@ -1323,8 +1373,8 @@ __device__ CoreOut tile_pass(TileCtx<CAP> &cx, const uint64_t *stage, uint32_t n
     //    warps before it.  Marks lie in the core: sorted, positions
     //    [c0, c1); in bucket order, the buckets of [lo_t, hi_t)
     uint16_t *seed_idx = SORT ? cx.seed_idx() : cx.flk();
-    const uint32_t p_lo = SORT ? c0 : cnt[bucket_of<CAP>(lo_t, bsh)];
-    const uint32_t p_hi = SORT ? c1 : cnt[bucket_of<CAP>(hi_t > 0 ? hi_t - 1 : 0, bsh) + 1];
+    const uint32_t p_lo = SORT ? c0 : cnt[bucket_of<NB>(lo_t, bsh)];
+    const uint32_t p_hi = SORT ? c1 : cnt[bucket_of<NB>(hi_t > 0 ? hi_t - 1 : 0, bsh) + 1];
     const uint32_t w_lo = p_lo >> 5, w_hi = (p_hi + 31) >> 5;
     const uint32_t nwords = w_hi - w_lo;
     const uint32_t nw_used = (nwords + 31) >> 5;
@@ -1361,9 +1411,9 @@ __device__ CoreOut tile_pass(TileCtx<CAP> &cx, const uint64_t *stage, uint32_t n
     // counts take the second half of the bucket-order key region)
     uint16_t *seed_cnt = cx.seed_cnt();
     if (EXT && tp.count_distinct) {
-        count_distinct_pmts<CAP, NC, SMEM_DT>(cx, pk, n, ns, seed_idx, bsh, seed_cnt);
+        count_distinct_pmts<CAP, NC, SMEM_DT, NB>(cx, pk, n, ns, seed_idx, bsh, seed_cnt);
     } else {
-        count_causal<CAP, NC, SMEM_DT, DENSE ? 5u : 2u>(cx, pk, n, ns, seed_idx, bsh, seed_cnt);
+        count_causal<CAP, NC, SMEM_DT, DENSE ? 5u : 2u, NB>(cx, pk, n, ns, seed_idx, bsh, seed_cnt);
     }
     cons_sync<NC>();
     PHASE_MARK(kPhF);
@@ -1407,16 +1457,16 @@ __device__ CoreOut tile_pass(TileCtx<CAP> &cx, const uint64_t *stage, uint32_t n
             if (!SORT) {
                 // fired seeds of the same bucket before k that order after
                 // it, and after k that order before it
-                const uint32_t bk = bucket_of<CAP>(ks >> 12, bsh);
+                const uint32_t bk = bucket_of<NB>(ks >> 12, bsh);
                 const uint64_t key_k = ((uint64_t)ks << 16) | q;
                 for (uint32_t k2 = k; k2-- > 0;) {
                     const uint32_t i2 = seed_idx[k2];
-                    if (bucket_of<CAP>(pk[i2] >> 12, bsh) != bk) break;
+                    if (bucket_of<NB>(pk[i2] >> 12, bsh) != bk) break;
                     if (count_of(k2) >= threshold && (((uint64_t)pk[i2] << 16) | chg[i2]) > key_k) --o_;
                 }
                 for (uint32_t k2 = k + 1; k2 < ns; ++k2) {
                     const uint32_t i2 = seed_idx[k2];
-                    if (bucket_of<CAP>(pk[i2] >> 12, bsh) != bk) break;
+                    if (bucket_of<NB>(pk[i2] >> 12, bsh) != bk) break;
                     if (count_of(k2) >= threshold && (((uint64_t)pk[i2] << 16) | chg[i2]) < key_k) ++o_;
                 }
             }
@@ -1425,7 +1475,20 @@ __device__ CoreOut tile_pass(TileCtx<CAP> &cx, const uint64_t *stage, uint32_t n
             tr.pmt = (uint16_t)(ks & 0xfffu);
             tr.charge = (uint16_t)q;
             tr.count = cnt_k;
-            if (CHECK(3, o_, c1 - c0)) dst[o_] = tr;
+            if (CHECK(3, o_, c1 - c0)) {
+                dst[o_] = tr;
+                // the merged ranks of the first hit of the seed's event
+                // window [t - h, t + h] and of the first hit past it, where
+                // that bound lies in the staged range (else kRankUnknown:
+                // the window pass searches for it)
+                const uint32_t ts = ks >> 12, wh = tp.win_half;
+                const uint32_t r_lo = ts >= wh ? rank_base + keys_before<NB>(pk, cnt, n, ts - wh, bsh, span)
+                                               : kRankUnknown;
+                const uint32_t r_hi = ts + wh + 1u <= span
+                                          ? rank_base + keys_before<NB>(pk, cnt, n, ts + wh + 1u, bsh, span)
+                                          : kRankUnknown;
+                *reinterpret_cast<uint2 *>(wr + 2 * ((out_at_c0 ? c0 : 0u) + o_)) = make_uint2(r_lo, r_hi);
+            }
         }
         F += __popc(m);
     }
@@ -1451,7 +1514,9 @@ __device__ CoreOut tile_pass(TileCtx<CAP> &cx, const uint64_t *stage, uint32_t n
         }
     }
     // leave the bucket counts and the seed mask zero for the next tile
-    for (uint32_t i = tid; i < (uint32_t)TileLayout<CAP>::NBK; i += NC) cnt[i] = 0;
+    // (after every warp's last read of the offsets: the window ranks above)
+    cons_sync<NC>();
+    for (uint32_t i = tid; i < NB; i += NC) cnt[i] = 0;
     for (uint32_t w = w_lo + tid; w < w_hi; w += NC) mask[w] = 0;
     cons_sync<NC>();
     PHASE_MARK(kPhG);
@@ -1580,8 +1645,10 @@ __device__ void tile_overflow(TileCtx<CAP> &cx, uint64_t *buf, const SliceDesc &
         const uint32_t span = (uint32_t)(hi - lo) + 2 * H;
         const uint32_t fired0 = red[5];
         CoreOut co = tile_pass<CAP, NC, SMEM_DT, EXT, DENSE>(cx, buf, total, tb, span, H, H + (uint32_t)(hi - lo), tp,
-                                                             d.stage + tile_rank + fired0, false,
-                                                             (int64_t)rank_lo - (int64_t)d.dbg_rank0, nullptr);
+                                                             d.stage + tile_rank + fired0,
+                                                             d.wrank + 2 * (size_t)(tile_rank + fired0), false,
+                                                             rank_lo, (int64_t)rank_lo - (int64_t)d.dbg_rank0,
+                                                             nullptr);
         if (tid == 0) {
             red[5] = fired0 + co.n_fired;
             red[6] += co.n_seeds;
@@ -1825,6 +1892,7 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 
             loaded = &d;
             if (tid == 0) {
                 tp.H = d.halo;
+                tp.win_half = d.win_half;
                 tp.tau = d.tau;
                 tp.q_seed = d.q_seed;
                 tp.threshold = d.threshold;
@@ -1868,8 +1936,9 @@ __global__ void __launch_bounds__(NC + 32, (CAP <= 1024 ? 4 : CAP <= 2048 ? 2 : 
             // is not read after that); the core's first hit has merged rank
             // rank_lo + c0
             CoreOut co = tile_pass<CAP, NC, SMEM_DT, EXT, DENSE>(cx, cx.stage(b), n_st, tb, span, lo_t, hi_t, tp,
-                                                                 d.stage + rank_lo, true,
-                                                                 (int64_t)rank_lo - sl[3], &empty_bar[b]);
+                                                                 d.stage + rank_lo, d.wrank + 2 * (size_t)rank_lo,
+                                                                 true, rank_lo, (int64_t)rank_lo - sl[3],
+                                                                 &empty_bar[b]);
             const uint32_t tile_rank = rank_lo + co.c0;
             if (tid == 0 && CHECK(14, (uint64_t)tile_rank + co.n_fired, d.n_hits + 1) && CHECK(15, g, d.n_tiles)) {
                 d.tile_nfired[g] = co.n_fired;
@@ -2015,8 +2084,11 @@ __global__ void __launch_bounds__(1024) k_wscan(const BatchHeader *__restrict__ 
 // ---------------------------------------------------------------- k_wwrite
 
 // One warp per tile: window w of a head trigger is tile_wout[g] plus the
-// heads before it in the tile; heads write lo and the first trigger index,
-// tails (the next trigger is a head, or none follows) write hi and the last.
+// heads before it in the tile; heads write lo, the first trigger index and
+// the rank of the window's first hit, tails (the next trigger is a head, or
+// none follows) write hi, the last trigger index and the rank one past the
+// window's last hit (both ranks recorded by the tile pass beside the
+// fired seed).
 __global__ void __launch_bounds__(256) k_wwrite(const BatchHeader *__restrict__ hdr, const SliceDesc *__restrict__ desc)
 {
     if (hdr->err) return;           // the tile pass gave up: its per-tile outputs are not valid
@@ -2049,20 +2121,23 @@ __global__ void __launch_bounds__(256) k_wwrite(const BatchHeader *__restrict__ 
             }
             const uint32_t m = __ballot_sync(0xffffffffu, head);
             const uint64_t w = w_run + __popc(m & ((2u << lane) - 1u)) - 1;   // window of trigger k
+            const uint64_t at = 2 * ((uint64_t)d.tile_rank[g] + f);            // the seed's staged ranks
             if (head && w < d.win_cap) {
                 d.windows[w].lo_ns = t - h;
-                d.windows[w].n_triggers = k;        // first trigger, turned into a count by k_whits
+                d.windows[w].n_triggers = k;        // first trigger, turned into a count by k_wcount
+                if (CHECK(9, at, 2 * d.n_hits)) d.win_r[2 * w] = d.wrank[at];
             }
             if (tail && w < d.win_cap) {
                 d.windows[w].hi_ns = t + h;
-                d.windows[w].n_hits = k;            // last trigger, turned into the hit count by k_whits
+                d.windows[w].n_hits = k;            // last trigger, turned into the hit count by k_wcount
+                if (CHECK(9, at + 1, 2 * d.n_hits)) d.win_r[2 * w + 1] = d.wrank[at + 1];
             }
             w_run += __popc(m);
         }
     }
 }
 
-// ----------------------------------------------------------------- k_whits
+// ---------------------------------------------------------------- k_wcount
 
 // Hit rank of time x in PMT p's stream, narrowed by the tile edges the
 // structure pass recorded: x in tile g's core lies between the PMT's
@@ -2083,10 +2158,35 @@ __device__ __forceinline__ uint64_t rank_in_pmt(const SliceDesc &d, uint32_t p, 
     return lb_time(d.hits, lo, hi, x);
 }
 
-// Hits of the submission inside each window: sum over PMTs of the hits in
-// [lo, hi] of that PMT's stream.  A warp per window over the whole batch
-// (lanes take PMTs); the window's slice comes from a prefix over slices.
-__global__ void __launch_bounds__(256) k_whits(const BatchHeader *__restrict__ hdr, const SliceDesc *__restrict__ desc)
+// Merged rank of time x (the hits of the submission with t < x), by the
+// warp: per-PMT searches, or for a wide slice the bucket offsets plus the
+// edge bucket's hits below x.
+__device__ uint64_t warp_rank_of(const SliceDesc &d, int64_t x)
+{
+    const uint32_t lane = lane_id();
+    uint64_t r = 0;
+    if (d.wide) {
+        const uint32_t bx = bkt_index(d, x);
+        const uint32_t e0 = d.bkt_off[bx], e1 = d.bkt_off[bx + 1];
+        if (lane == 0) r = e0;
+        for (uint32_t j = e0 + lane; j < e1; j += 32) r += d.tbuf[j].t_ns < x;
+    } else {
+        for (uint32_t p = lane; p < d.n_pmt; p += 32) {
+            const uint64_t sp = d.pmt_off[p], ep = d.pmt_off[p + 1];
+            r += rank_in_pmt(d, p, x, sp, ep) - sp;
+        }
+    }
+    return warp_sum_u64(r);
+}
+
+// Each window's counts from what k_wwrite left: triggers = last - first + 1,
+// hits = (rank one past its last hit) - (rank of its first hit); event
+// slices also keep the first-hit rank.  The tile pass records both ranks
+// beside every fired seed whose window edge lies in its staged range; the
+// few others (seeds near a tile edge) are searched for here.  A warp per
+// window over the whole batch; the window's slice comes from a prefix over
+// slices.
+__global__ void __launch_bounds__(256) k_wcount(const BatchHeader *__restrict__ hdr, const SliceDesc *__restrict__ desc)
 {
     if (hdr->err) return;           // the tile pass gave up: its per-tile outputs are not valid
     __shared__ unsigned long long pre[1025];
@@ -2117,72 +2217,19 @@ __global__ void __launch_bounds__(256) k_whits(const BatchHeader *__restrict__ h
             }
             const SliceDesc &d = desc[s0 + lo];
             const uint64_t i = wi - pre[lo];
-            if (!CHECK(9, i, d.win_cap)) continue;
+            if (!CHECK(10, i, d.win_cap)) continue;
+            const uint2 r = *reinterpret_cast<const uint2 *>(d.win_r + 2 * i);
             const trig_window win = d.windows[i];
-            uint64_t cnt = 0;
-            if (d.wide) {
-                // whole buckets between the edge buckets, plus the edge
-                // buckets' hits inside [lo, hi]
-                const uint32_t bl = bkt_index(d, win.lo_ns), bh = bkt_index(d, win.hi_ns);
-                if (bl + 1 < bh && lane == 0) cnt = d.bkt_off[bh] - d.bkt_off[bl + 1];
-                const uint32_t e0 = d.bkt_off[bl], e1 = d.bkt_off[bl + 1];
-                for (uint32_t j = e0 + lane; j < e1; j += 32) {
-                    const int64_t t = d.tbuf[j].t_ns;
-                    cnt += t >= win.lo_ns && t <= win.hi_ns;
-                }
-                if (bh != bl) {
-                    const uint32_t f0 = d.bkt_off[bh], f1 = d.bkt_off[bh + 1];
-                    for (uint32_t j = f0 + lane; j < f1; j += 32) cnt += d.tbuf[j].t_ns <= win.hi_ns;
-                }
-            } else {
-                for (uint32_t p = lane; p < d.n_pmt; p += 32) {
-                    const uint64_t sp = d.pmt_off[p], ep = d.pmt_off[p + 1];
-                    cnt += rank_in_pmt(d, p, win.hi_ns + 1, sp, ep) - rank_in_pmt(d, p, win.lo_ns, sp, ep);
-                }
-            }
-            cnt = warp_sum_u64(cnt);
+            const uint64_t r_lo = r.x != kRankUnknown ? (uint64_t)r.x : warp_rank_of(d, win.lo_ns);
+            const uint64_t r_hi = r.y != kRankUnknown ? (uint64_t)r.y : warp_rank_of(d, win.hi_ns + 1);
             __syncwarp();
             if (lane == 0) {
                 d.windows[i].n_triggers = win.n_hits - win.n_triggers + 1;
-                d.windows[i].n_hits = cnt;
+                d.windows[i].n_hits = r_hi - r_lo;
+                if (d.ev && d.ev_cap) d.win_rlo[i] = (uint32_t)r_lo;
             }
         }
         __syncthreads();
-    }
-}
-
-// Event slices: each window's first merged rank (the hits with t < lo),
-// from the same narrowed per-PMT searches, or from the bucket offsets plus
-// the edge bucket of a wide slice.  A warp per window, as k_whits.
-__global__ void __launch_bounds__(256) k_wrank(const BatchHeader *__restrict__ hdr, const SliceDesc *__restrict__ desc)
-{
-    if (hdr->err) return;           // the tile pass gave up: its per-tile outputs are not valid
-    const uint32_t lane = lane_id();
-    const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint64_t nwarp = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    for (uint32_t s = 0; s < hdr->n_slices; ++s) {
-        const SliceDesc &d = desc[s];
-        if (!d.ev || d.ev_cap == 0) continue;
-        if (d.stats->flags & (TRIG_FLAG_TRIG_FULL | TRIG_FLAG_BAD_PMT | TRIG_FLAG_UNSORTED | TRIG_FLAG_OUT_OF_RANGE))
-            continue;
-        const uint64_t nw = min((unsigned long long)d.stats->n_windows, (unsigned long long)d.win_cap);
-        for (uint64_t i = gw; i < nw; i += nwarp) {
-            const int64_t lo_ns = d.windows[i].lo_ns;
-            uint64_t below = 0;
-            if (d.wide) {
-                const uint32_t bl = bkt_index(d, lo_ns);
-                const uint32_t e0 = d.bkt_off[bl], e1 = d.bkt_off[bl + 1];
-                if (lane == 0) below = e0;
-                for (uint32_t j = e0 + lane; j < e1; j += 32) below += d.tbuf[j].t_ns < lo_ns;
-            } else {
-                for (uint32_t p = lane; p < d.n_pmt; p += 32) {
-                    const uint64_t sp = d.pmt_off[p], ep = d.pmt_off[p + 1];
-                    below += rank_in_pmt(d, p, lo_ns, sp, ep) - sp;
-                }
-            }
-            below = warp_sum_u64(below);
-            if (lane == 0 && CHECK(20, i, d.win_cap)) d.win_rlo[i] = (uint32_t)below;
-        }
     }
 }
 
@@ -2583,7 +2630,7 @@ static cudaError_t launch_tile(BatchHeader *hdr, SliceDesc *desc, uint32_t max_p
 
 const char *const kKernelNames[kPipelineKernels] = {"k_prep",   "k_bounds", "k_bsum",  "k_bscan",  "k_scatter",
                                                      "k_tile",   "k_evhalo", "k_scan",  "k_copy",   "k_wscan",
-                                                     "k_wwrite", "k_whits",  "k_escan", "k_events", "k_status"};
+                                                     "k_wwrite", "k_wcount", "k_escan", "k_events", "k_status"};
 
 cudaError_t launch_batch(BatchHeader *d_hdr, SliceDesc *d_desc, uint32_t n_slices, uint32_t max_pmt,
                          bool any_smem_dt, bool any_wide, bool any_events, bool any_ext, bool dense,
@@ -2680,14 +2727,13 @@ cudaError_t launch_batch(BatchHeader *d_hdr, SliceDesc *d_desc, uint32_t n_slice
     mark(10);
     k_wwrite<<<sms * 4, 256, 0, st>>>(d_hdr, d_desc);
     mark(11);
-    k_whits<<<sms * 4, 256, 0, st>>>(d_hdr, d_desc);
+    k_wcount<<<sms * 4, 256, 0, st>>>(d_hdr, d_desc);
     mark(12);
     if (any_events) {
-        k_wrank<<<sms * 4, 256, 0, st>>>(d_hdr, d_desc);
         k_escan<<<sb, 1024, 0, st>>>(d_hdr, d_desc);
         mark(13);
         k_events<<<sms * 8, 256, 0, st>>>(d_hdr, d_desc);
-        nl += 3;
+        nl += 2;
     } else {
         mark(13);
     }

@@ -10,18 +10,24 @@ carries both halos, every later one starts at its t0 and takes its leading
 halo from the previous slice's tail that the engine keeps on the device
 (is_continuation = 1).  A run is rate:mode:detector_seconds, where rate is
 the arrival rate in units of real time (or "sat": every slice submitted at
-once, which measures capacity) and mode is the engine's (0 plain per-slice
-launches, 1 continuous batching).
+once, which measures capacity through the submitting thread's copies; or
+"burst": every slice submitted while the engine holds its launches, then
+released at once, which measures the device side's capacity with the
+copies already done) and mode is the engine's (0 plain per-slice launches,
+1 continuous batching).
 
-The request loop and the pollers are Python threads; every call they make
-releases the GIL inside libtrig.so, where copies, batching and kernels run.
+Each detector has a submitting thread and a polling thread (Python
+threads; every call they make releases the GIL inside libtrig.so, where
+copies, batching and kernels run).
 
-    python -m paper_1411_3968_gb300.serving --pool 20 --runs 4:1:600 4:0:600 1:1:600 sat:1:60 sat:0:60
+    python -m paper_1411_3968_gb300.serving --pool 20 --runs 4:1:600 4:0:600 1:1:600 1:0:600 \
+        sat:1:60 sat:0:60 burst:1:4 burst:0:4
 """
 from __future__ import annotations
 
 import argparse
 import json
+import sys
 import threading
 import time
 
@@ -68,7 +74,8 @@ def replay(dets, pools, rate_factor, detector_seconds: float, slice_ns: int, see
         warm_up(dets, pools, warmup_rounds)
     rng = np.random.Generator(np.random.PCG64(seed))
     n_per = max(1, int(round(detector_seconds * 1e9 / slice_ns)))
-    saturate = rate_factor == "sat"
+    burst = rate_factor == "burst"
+    saturate = rate_factor == "sat" or burst
     mean_gap = 0.0 if saturate else slice_ns * 1e-9 / float(rate_factor)
     events = []
     for i in range(len(dets)):
@@ -95,15 +102,55 @@ def replay(dets, pools, rate_factor, detector_seconds: float, slice_ns: int, see
     for th in threads:
         th.start()
     _lib.trig_engine_trace(len(events) + 16)
-    t_start = time.perf_counter()
     deferred = 0
-    for (t, i, k) in events:
-        now = time.perf_counter() - t_start
-        if t > now:
-            time.sleep(t - now)
-        t0, st, cont = pools[i][k % len(pools[i])]
-        arrivals[i][k] = t_start + t
-        deferred += _submit(dets[i], t0, st, cont)
+    released_early = False
+    if burst:
+        # everything staged while the engine holds; a full staging area
+        # releases the hold (the engine then drains while the rest arrive)
+        _lib.trig_engine_hold(True)
+        try:
+            for (t, i, k) in events:
+                t0, st, cont = pools[i][k % len(pools[i])]
+                if not released_early:
+                    try:
+                        _lib.trig_submit_slice(dets[i], t0, st.hits, st.pmt_off, is_continuation=cont)
+                        continue
+                    except _lib.TrigError as e:
+                        if e.code != _lib.TRIG_EAGAIN:
+                            raise
+                        released_early = True
+                        _lib.trig_engine_hold(False)
+                deferred += _submit(dets[i], t0, st, cont)
+        finally:
+            t_start = time.perf_counter()
+            _lib.trig_engine_hold(False)
+        for i in range(len(dets)):
+            arrivals[i] = [t_start] * n_per
+    else:
+        # one submitting thread per detector, as each tower's data
+        # acquisition feeds the trigger on its own: a large detector's copy
+        # does not hold back the others' submissions
+        t_start = time.perf_counter()
+        deferred_of = [0] * len(dets)
+
+        def submitter(i):
+            try:
+                for (t, _, k) in (e for e in events if e[1] == i):
+                    now = time.perf_counter() - t_start
+                    if t > now:
+                        time.sleep(t - now)
+                    t0, st, cont = pools[i][k % len(pools[i])]
+                    arrivals[i][k] = t_start + t
+                    deferred_of[i] += _submit(dets[i], t0, st, cont)
+            except Exception as err:        # noqa: BLE001
+                errors.append(f"detector {i}: submit failed: {err!r}")
+
+        subs = [threading.Thread(target=submitter, args=(i,), daemon=True) for i in range(len(dets))]
+        for th in subs:
+            th.start()
+        for th in subs:
+            th.join()
+        deferred = sum(deferred_of)
     for th in threads:
         th.join()
     t_end = time.perf_counter()
@@ -144,6 +191,7 @@ def replay(dets, pools, rate_factor, detector_seconds: float, slice_ns: int, see
         "engine_p99_ms": _pct(lat_engine, 99),
         "budget_ms": slice_ns * 1e-6,
         "deferred_submits": deferred,
+        "released_early": released_early if burst else None,
         "per_detector": per_det,
         "trace": trace_summary(trace),
     }
@@ -208,7 +256,7 @@ def make_pools(detectors, rates, pool: int, par: dict, seed: int = 0):
 
 def _parse_run(text: str):
     rate, mode, secs = text.split(":")
-    return (rate if rate == "sat" else float(rate)), int(mode), float(secs)
+    return (rate if rate in ("sat", "burst") else float(rate)), int(mode), float(secs)
 
 
 def main():
@@ -216,7 +264,7 @@ def main():
 
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--runs", nargs="+", default=["4:1:60", "4:0:60", "1:1:30", "sat:1:20", "sat:0:20"],
-                    help="rate:mode:detector_seconds per run (rate in units of real time, or sat)")
+                    help="rate:mode:detector_seconds per run (rate in units of real time, sat or burst)")
     ap.add_argument("--pool", type=int, default=20, help="contiguous pre-generated slices per detector")
     ap.add_argument("--seed", type=int, default=0)
     args = ap.parse_args()
@@ -231,6 +279,7 @@ def main():
     for k, text in enumerate(args.runs):
         rate, mode, secs = _parse_run(text)
         runs.append(replay(dets, pools, rate, secs, par["slice_ns"], args.seed + k, mode))
+        print(json.dumps(runs[-1]), file=sys.stderr, flush=True)      # progress, one line per run
     out = {"detectors": "32@50kHz, 84@55kHz, 84@55kHz, 2688@55kHz", "pool_slices_per_detector": args.pool,
            "pool_generation_s": gen_s, "continuation": "every pool slice after the first", "runs": runs}
     for d in dets:

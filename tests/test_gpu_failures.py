@@ -132,6 +132,7 @@ def test_device_wait_parameters_checked(pkg):
     lib = pkg.load()
     try:
         assert lib.trig_set_device_wait(0, 2) == pkg.TRIG_EINVAL
+        assert lib.trig_set_device_wait(0, -1) == pkg.TRIG_EINVAL
         assert lib.trig_set_device_wait(601 * 10**9, 0) == pkg.TRIG_EINVAL
         assert lib.trig_engine_hold(2) == pkg.TRIG_EINVAL
     finally:
