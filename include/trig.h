@@ -126,8 +126,8 @@ typedef struct {
     uint32_t afc_window_ns;     /* <= 60000 */
     uint32_t sc_dist_mm;
     /* 1: c(s) counts the different PMTs among the causally related hits
-     * (the distinct-PMT variant, robust to a single PMT's bursts; n_pmt
-     * must be at most 128); 0: c(s) counts hits. */
+     * (the distinct-PMT variant, robust to a single PMT's bursts; any
+     * n_pmt); 0: c(s) counts hits. */
     uint32_t count_distinct_pmts;
     uint32_t reserved;          /* 0 */
 } trig_params;

@@ -666,11 +666,7 @@ __global__ void __launch_bounds__(kBktChunk) k_bscan(const BatchHeader *__restri
 
 // Wide slices: every hit copied to its time bucket's range of tbuf (the
 // order inside a bucket is arbitrary; the tile pass sorts).  Slices with
-// malformed input (flagged by the structure pass) are skipped.  Chunks of
-// different PMTs cover the same times, so blocks that walked their chunks
-// in step would aim their fill-cursor atomics at the same buckets; each
-// chunk starts at its own offset instead (whole 256-hit rows, so the loads
-// stay coalesced).
+// malformed input (flagged by the structure pass) are skipped.
 __global__ void __launch_bounds__(256) k_scatter(const BatchHeader *__restrict__ hdr, const SliceDesc *__restrict__ desc)
 {
     const uint32_t n_slices = hdr->n_slices, n_chunks = hdr->n_chunks;
@@ -679,11 +675,9 @@ __global__ void __launch_bounds__(256) k_scatter(const BatchHeader *__restrict__
         if (!d.wide) continue;
         if (d.stats->flags & (TRIG_FLAG_BAD_PMT | TRIG_FLAG_UNSORTED | TRIG_FLAG_OUT_OF_RANGE)) continue;
         const uint64_t first = (uint64_t)(c - d.chunk0) * kChunkHits;
-        constexpr uint32_t kRows = kChunkHits / 256;
-        const uint32_t rot = ((c * 2654435761u) >> 16) % kRows * 256;
         for (uint32_t k = threadIdx.x; k < kChunkHits; k += blockDim.x) {
-            const uint64_t li = first + (k + rot) % kChunkHits;
-            if (li >= d.n_hits) continue;
+            const uint64_t li = first + k;
+            if (li >= d.n_hits) break;
             const int4 v = *reinterpret_cast<const int4 *>(d.hits + li);
             const int64_t t = (int64_t)(((uint64_t)(uint32_t)v.y << 32) | (uint32_t)v.x);
             const uint32_t b = bkt_index(d, t);
@@ -777,6 +771,15 @@ struct TileCtx {
     __device__ __forceinline__ uint16_t *live() const { return reinterpret_cast<uint16_t *>(g_tile_smem + L::oPkB); }
     __device__ __forceinline__ uint32_t *cnt() const { return reinterpret_cast<uint32_t *>(g_tile_smem + L::oCnt); }
     __device__ __forceinline__ uint32_t *mask() const { return reinterpret_cast<uint32_t *>(g_tile_smem + L::oMask); }
+    // warp w's 4096-bit PMT set of the distinct count above 128 PMTs (extended
+    // builds: the bucket-order charges and the floor keys are no longer read
+    // by then; each region holds CAP / 256 sets)
+    __device__ __forceinline__ uint32_t *pmt_set(uint32_t w) const
+    {
+        constexpr uint32_t per = (uint32_t)CAP / 256;
+        return w < per ? reinterpret_cast<uint32_t *>(g_tile_smem + L::oChgB) + 128 * w
+                       : reinterpret_cast<uint32_t *>(g_tile_smem + L::oFlk) + 128 * (w - per);
+    }
     __device__ __forceinline__ uint16_t *floor_s() const { return reinterpret_cast<uint16_t *>(g_tile_smem + L::oTab); }
     __device__ __forceinline__ uint16_t *dmax_s() const { return floor_s() + pp; }
     __device__ __forceinline__ uint16_t *dt_s() const { return floor_s() + 2 * (size_t)pp; }
@@ -914,16 +917,47 @@ __device__ __forceinline__ void seed_range(const TileCtx<CAP> &cx, uint32_t ts, 
     j1 = boff[bucket_of<NB>(ts + dm, bsh) + 1];
 }
 
-// Distinct-PMT causal count (P <= 128): c(s) = the number of different
-// PMTs among the keys j with |t_j - t_s| <= min(dt_max[p_s][p_j], W).
-// Eight lanes per seed each collect a 128-bit PMT set over every eighth key
-// of the seed's scan range; the sets are OR-ed and counted.
+// Distinct-PMT causal count: c(s) = the number of different PMTs among the
+// keys j with |t_j - t_s| <= min(dt_max[p_s][p_j], W).  Up to 128 PMTs,
+// eight lanes per seed each collect a 128-bit PMT set in registers over
+// every eighth key of the seed's scan range, and the sets are OR-ed and
+// counted; above, a warp per seed marks the PMTs in a shared-memory set.
 template <int CAP, int NC, bool SMEM_DT, uint32_t NB>
 __device__ __noinline__ void count_distinct_pmts(const TileCtx<CAP> &cx, const uint32_t *pk, uint32_t n, uint32_t ns,
                                                  const uint16_t *seed_idx, uint32_t bsh, uint16_t *seed_cnt)
 {
     constexpr uint32_t G = 8, NG = NC / G;
+    static_assert(NC / 32 <= CAP / 128, "a PMT set per consumer warp");
     const uint32_t tid = threadIdx.x, gl = tid & (G - 1u), gid = tid / G, P = cx.P;
+    if (P > 128) {
+        const uint32_t warp = tid >> 5, lane = tid & 31u, nwords = (P + 31u) >> 5;
+        uint32_t *set = cx.pmt_set(warp);
+        for (uint32_t k = warp; k < ns; k += NC / 32) {
+            for (uint32_t w = lane; w < nwords; w += 32) set[w] = 0u;
+            __syncwarp();
+            const uint32_t ks = pk[seed_idx[k]];
+            const uint32_t ts = pk_t(ks), ps = pk_p(ks);
+            uint32_t j0, j1;
+            seed_range<CAP, NB>(cx, ts, ps, bsh, j0, j1);
+            if (CHECK(12, j1, n + 1) && CHECK(13, ps, P) && CHECK(16, nwords, 129)) {
+                const uint16_t *row_s = cx.dt_s() + (size_t)ps * P;
+                const uint16_t *row_g = cx.dt_g + (size_t)ps * P;
+                for (uint32_t q = j0 + lane; q < j1; q += 32) {
+                    const uint32_t kj = pk[q], tj = pk_t(kj), pj = pk_p(kj);
+                    if (!CHECK(11, pj, P)) continue;
+                    const uint32_t lim = SMEM_DT ? (uint32_t)row_s[pj] : (uint32_t)__ldg(row_g + pj);
+                    if ((tj > ts ? tj - ts : ts - tj) <= lim) atomicOr(&set[pj >> 5], 1u << (pj & 31u));
+                }
+            }
+            __syncwarp();
+            uint32_t c = 0;
+            for (uint32_t w = lane; w < nwords; w += 32) c += __popc(set[w]);
+            c = __reduce_add_sync(0xffffffffu, c);
+            if (lane == 0) seed_cnt[k] = (uint16_t)c;
+            __syncwarp();                       // the set is read before the next seed clears it
+        }
+        return;
+    }
     const uint32_t rounds = (ns + NG - 1) / NG;
     for (uint32_t r = 0; r < rounds; ++r) {
         const uint32_t k = r * NG + gid;

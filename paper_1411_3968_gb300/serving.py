@@ -267,10 +267,13 @@ def main():
                     help="rate:mode:detector_seconds per run (rate in units of real time, sat or burst)")
     ap.add_argument("--pool", type=int, default=20, help="contiguous pre-generated slices per detector")
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--detectors", type=int, nargs="+", default=[0, 1, 2, 3],
+                    help="which of the four detectors (32, 84, 84, 2688 PMTs) take part")
     args = ap.parse_args()
     par = dict(workload.DEFAULT_PARAMS)
     spec = [(workload.nemo_tower(), 50e3), (workload.km3_tower(), 55e3), (workload.km3_tower(), 55e3),
             (workload.tower_array(), 55e3)]
+    spec = [spec[i] for i in args.detectors]
     t = time.perf_counter()
     pools = make_pools([d for d, _ in spec], [r for _, r in spec], args.pool, par, args.seed)
     gen_s = time.perf_counter() - t
@@ -280,7 +283,7 @@ def main():
         rate, mode, secs = _parse_run(text)
         runs.append(replay(dets, pools, rate, secs, par["slice_ns"], args.seed + k, mode))
         print(json.dumps(runs[-1]), file=sys.stderr, flush=True)      # progress, one line per run
-    out = {"detectors": "32@50kHz, 84@55kHz, 84@55kHz, 2688@55kHz", "pool_slices_per_detector": args.pool,
+    out = {"detectors": ", ".join(f"{d.n_pmt}@{r / 1e3:g}kHz" for d, r in spec), "pool_slices_per_detector": args.pool,
            "pool_generation_s": gen_s, "continuation": "every pool slice after the first", "runs": runs}
     for d in dets:
         d.close()

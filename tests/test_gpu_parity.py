@@ -641,9 +641,25 @@ def test_ladder_wide_detector_with_towers(pkg, params):
     d.close()
 
 
+def test_distinct_count_above_128_pmts(pkg, params):
+    """The distinct-PMT count on a 168-PMT two-tower array and on the
+    2688-PMT array (a warp per seed with a shared-memory PMT set): exact
+    against the oracle on two contiguous slices each."""
+    for g, rate, slice_ns in ((_tower_array(2, 1), 150e3, 1_000_000), (_tower_array(8, 4), 55e3, 200_000)):
+        par = dict(params, slice_ns=slice_ns, count_distinct_pmts=1)
+        t0 = workload.T_ORIGIN_NS
+        t0s = [t0, t0 + slice_ns]
+        full = workload.gen_stream(g, t0 - 3000, t0 + 2 * slice_ns + 3000, rate, n_muons=20, seed=9, stream=150)
+        d = _det(pkg, g, par)
+        _, res = _run(pkg, d, _subs_from_run(full, t0s, slice_ns))
+        ref = oracle.run(g.xyz_mm, g.floor_id, par, full.hits, t0s)
+        assert sum(len(r.triggers) for r in ref) > 0
+        for k in range(2):
+            _assert_same(res[k], ref[k], f"distinct count, {g.n_pmt} PMTs, slice {k}")
+        d.close()
+
+
 def test_rule_parameter_checks(pkg, params):
-    with pytest.raises(pkg.TrigError):
-        _det(pkg, _tower_array(2, 1), dict(params, count_distinct_pmts=1))      # > 128 PMTs
     with pytest.raises(pkg.TrigError):
         _det(pkg, workload.nemo_tower(), dict(params, seed_rule=2))
     with pytest.raises(pkg.TrigError):

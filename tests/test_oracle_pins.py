@@ -544,7 +544,7 @@ def test_ladder_and_distinct_count_match_bruteforce(case, params):
     rng = np.random.Generator(np.random.PCG64(700 + case))
     det = [workload.nemo_tower, workload.km3_tower, lambda: workload.tower_array(nx=2, ny=1)][case % 3]()
     par = dict(params, slice_ns=10_000, threshold=1, seed_rule=int(case % 2 == 0),
-               count_distinct_pmts=int(case % 4 < 2 and det.n_pmt <= 128),
+               count_distinct_pmts=int(case % 4 < 2),
                sc_window_ns=int(rng.choice([20, 60])), fc_window_ns=int(rng.choice([10, 100])),
                afc_window_ns=int(rng.choice([100, 250])), sc_dist_mm=int(rng.choice([1000, 7000])))
     t0 = 2_000_000
