@@ -140,10 +140,16 @@ struct TailState {
     std::mutex mu;                  // serialises the detector's submissions
     bool have = false;
     int64_t next_t0 = 0;            // t0 of the slice that may continue it
-    trig_hit *d_hits = nullptr;     // device, cap entries
-    uint64_t *d_off = nullptr;      // device, n_pmt + 1 offsets
-    size_t cap = 0;
-    std::vector<uint64_t> off;      // host copy of the offsets
+    // two device copies: a submission reads the current one (cur) while it
+    // writes the next slice's into the other, so one stream sync suffices
+    trig_hit *d_hits[2] = {nullptr, nullptr};   // device, cap[i] entries
+    uint64_t *d_off[2] = {nullptr, nullptr};    // device, n_pmt + 1 offsets
+    size_t cap[2] = {0, 0};
+    int cur = 0;
+    trig_hit *h_hits = nullptr;     // page-locked staging of the next tail, h_cap entries
+    uint64_t *h_off = nullptr;      // page-locked, n_pmt + 1 offsets
+    size_t h_cap = 0;
+    std::vector<uint64_t> off;      // host copy of the current offsets
 };
 
 struct trig_detector {
@@ -181,10 +187,18 @@ void count_launches(uint64_t n) { g_launches += n; }
 
 static void free_det_dev(trig_detector *d)
 {
-    cudaFree(d->tail.d_hits);
-    cudaFree(d->tail.d_off);
-    d->tail.d_hits = nullptr;
-    d->tail.d_off = nullptr;
+    for (int i = 0; i < 2; ++i) {
+        cudaFree(d->tail.d_hits[i]);
+        cudaFree(d->tail.d_off[i]);
+        d->tail.d_hits[i] = nullptr;
+        d->tail.d_off[i] = nullptr;
+        d->tail.cap[i] = 0;
+    }
+    cudaFreeHost(d->tail.h_hits);
+    cudaFreeHost(d->tail.h_off);
+    d->tail.h_hits = nullptr;
+    d->tail.h_off = nullptr;
+    d->tail.h_cap = 0;
     cudaFree(d->dev.dt);
     cudaFree(d->dev.dt_exact);
     cudaFree(d->dev.floor);
@@ -1858,43 +1872,57 @@ extern "C" int trig_submit_slice(trig_detector *det, int64_t t0, const trig_hit 
         ce = cudaStreamCreateWithFlags(&copy_stream, cudaStreamNonBlocking);
         copy_dev = e->device;
     }
+    // the next slice's leading halo: this submission's hits in
+    // [t0 + S - halo, t0 + S), PMT by PMT (a producer's unordered stream
+    // gives some sub-range; the device flags such a slice), staged in
+    // page-locked memory so that its copy is asynchronous like the slice's
+    std::vector<uint64_t> toff(P + 1, 0), tfrom(P, 0);
+    for (uint32_t q = 0; q < P; ++q) {
+        const uint64_t a = host_lb_back(hits, pmt_off[q], pmt_off[q + 1], t0 + S - halo);
+        const uint64_t b = host_lb_back(hits, a, pmt_off[q + 1], t0 + S);
+        tfrom[q] = a;
+        toff[q + 1] = toff[q] + (b - a);
+    }
+    const size_t tn = (size_t)toff[P];
+    if (!ce && tn > tl.h_cap) {
+        cudaFreeHost(tl.h_hits);
+        tl.h_hits = nullptr;
+        tl.h_cap = 0;
+        const size_t want = std::max<size_t>(tn + tn / 2, 1024);
+        ce = cudaHostAlloc(reinterpret_cast<void **>(&tl.h_hits), want * sizeof(trig_hit), cudaHostAllocPortable);
+        if (!ce) tl.h_cap = want;
+    }
+    if (!ce && !tl.h_off) ce = cudaHostAlloc(reinterpret_cast<void **>(&tl.h_off), (size_t)(P + 1) * 8,
+                                             cudaHostAllocPortable);
+    if (!ce) {
+        for (uint32_t q = 0; q < P; ++q)
+            std::memcpy(tl.h_hits + toff[q], hits + tfrom[q], (size_t)(toff[q + 1] - toff[q]) * sizeof(trig_hit));
+        std::memcpy(tl.h_off, toff.data(), (size_t)(P + 1) * 8);
+    }
+    // the new tail goes to the device copy the prepend below does not read
+    const int nx = tl.cur ^ 1;
+    if (!ce && tn > tl.cap[nx]) {
+        cudaFree(tl.d_hits[nx]);
+        tl.d_hits[nx] = nullptr;
+        tl.cap[nx] = 0;
+        const size_t want = std::max<size_t>(tn + tn / 2, 1024);
+        ce = cudaMalloc(&tl.d_hits[nx], want * sizeof(trig_hit));
+        if (!ce) tl.cap[nx] = want;
+    }
+    if (!ce && !tl.d_off[nx]) ce = cudaMalloc(&tl.d_off[nx], (size_t)(P + 1) * 8);
     unsigned char *dst = T ? raw : p.dblk;
     const size_t dst_pmt_at = T ? raw_pmt_at : p.pmt_at;
     if (!ce && n) ce = cudaMemcpyAsync(dst, hits, n * sizeof(trig_hit), cudaMemcpyHostToDevice, copy_stream);
     if (!ce) ce = cudaMemcpyAsync(dst + dst_pmt_at, pmt_off, (size_t)(P + 1) * 8, cudaMemcpyHostToDevice, copy_stream);
     if (!ce && T)
-        ce = launch_prepend(tl.d_hits, tl.d_off, T, reinterpret_cast<const trig_hit *>(raw),
+        ce = launch_prepend(tl.d_hits[tl.cur], tl.d_off[tl.cur], T, reinterpret_cast<const trig_hit *>(raw),
                             reinterpret_cast<const uint64_t *>(raw + raw_pmt_at), n, P,
                             reinterpret_cast<trig_hit *>(p.dblk), reinterpret_cast<uint64_t *>(p.dblk + p.pmt_at),
                             copy_stream);
-    // the next slice's leading halo, found while the copy runs: this
-    // submission's hits in [t0 + S - halo, t0 + S), PMT by PMT (a producer's
-    // unordered stream gives some sub-range; the device flags such a slice)
-    std::vector<uint64_t> toff(P + 1, 0);
-    std::vector<trig_hit> th;
-    for (uint32_t q = 0; q < P; ++q) {
-        const uint64_t a = host_lb_back(hits, pmt_off[q], pmt_off[q + 1], t0 + S - halo);
-        const uint64_t b = host_lb_back(hits, a, pmt_off[q + 1], t0 + S);
-        th.insert(th.end(), hits + a, hits + b);
-        toff[q + 1] = th.size();
-    }
+    if (!ce && tn)
+        ce = cudaMemcpyAsync(tl.d_hits[nx], tl.h_hits, tn * sizeof(trig_hit), cudaMemcpyHostToDevice, copy_stream);
+    if (!ce) ce = cudaMemcpyAsync(tl.d_off[nx], tl.h_off, (size_t)(P + 1) * 8, cudaMemcpyHostToDevice, copy_stream);
     if (!ce) ce = cudaStreamSynchronize(copy_stream);
-    if (!ce) {
-        if (th.size() > tl.cap) {
-            cudaFree(tl.d_hits);
-            tl.d_hits = nullptr;
-            tl.cap = 0;
-            const size_t want = std::max<size_t>(th.size() + th.size() / 2, 1024);
-            ce = cudaMalloc(&tl.d_hits, want * sizeof(trig_hit));
-            if (!ce) tl.cap = want;
-        }
-        if (!ce && !tl.d_off) ce = cudaMalloc(&tl.d_off, (size_t)(P + 1) * 8);
-        if (!ce && !th.empty())
-            ce = cudaMemcpyAsync(tl.d_hits, th.data(), th.size() * sizeof(trig_hit), cudaMemcpyHostToDevice,
-                                 copy_stream);
-        if (!ce) ce = cudaMemcpyAsync(tl.d_off, toff.data(), (size_t)(P + 1) * 8, cudaMemcpyHostToDevice, copy_stream);
-        if (!ce) ce = cudaStreamSynchronize(copy_stream);
-    }
     if (raw) e->pool.put(raw, raw_bytes);
     if (ce) {
         (void)cudaGetLastError();
@@ -1903,6 +1931,7 @@ extern "C" int trig_submit_slice(trig_detector *det, int64_t t0, const trig_hit 
         return fail(TRIG_EDEVICE, std::string("copying the slice to the device: ") + cudaGetErrorString(ce));
     }
     tl.off = std::move(toff);
+    tl.cur = nx;
     tl.have = true;
     tl.next_t0 = t0 + S;
     p.t_submit = t_entry;
