@@ -293,7 +293,9 @@ typedef struct {
     int64_t t_done_ns;          /* result delivered to trig_poll            */
     float device_ms;            /* its batch's device time (CUDA events from
                                    launch to counters), -1 if unknown       */
-    uint32_t reserved;
+    uint32_t copy_wait_us;      /* of t_queued - t_submit: the time the
+                                   submission waited for its copies to the
+                                   device after its host work (microseconds) */
 } trig_trace_rec;
 
 /* Starts recording (clearing earlier records) up to `capacity` slices;

@@ -41,7 +41,7 @@ STATS_DTYPE = np.dtype([("status", "<i4"), ("flags", "<u4"), ("n_hits", "<u8"), 
 TRACE_DTYPE = np.dtype([("slice_id", "<u8"), ("batch", "<u8"), ("batch_slices", "<u4"), ("n_pmt", "<u4"),
                         ("n_hits", "<u8"), ("status", "<i4"), ("continuation", "<u4"), ("t_submit_ns", "<i8"),
                         ("t_queued_ns", "<i8"), ("t_launch_ns", "<i8"), ("t_stats_ns", "<i8"), ("t_done_ns", "<i8"),
-                        ("device_ms", "<f4"), ("reserved", "<u4")])
+                        ("device_ms", "<f4"), ("copy_wait_us", "<u4")])
 
 ASEED_DTYPE = np.dtype([("t", "<i8"), ("pmt", "<u2"), ("tower", "<u2"), ("n_towers", "<u4")])
 ASTATS_DTYPE = np.dtype([("n_tower_triggers", "<u8"), ("n_selected", "<u8"), ("n_windows", "<u8"),

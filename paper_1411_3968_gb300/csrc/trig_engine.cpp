@@ -1112,6 +1112,7 @@ struct Pending {
     uint64_t n_hits = 0;
     Clock::time_point t_submit;
     Clock::time_point t_queued;         // copied to the device and queued
+    uint32_t copy_wait_us = 0;          // of that, waiting for the copies after the host work
     bool continuation = false;
 };
 
@@ -1593,6 +1594,7 @@ void Engine::finish(Slot &s)
                 t.t_stats_ns = ns(s.t_stats);
                 t.t_done_ns = ns(now);
                 t.device_ms = dev_ms;
+                t.copy_wait_us = p.copy_wait_us;
                 trace.push_back(t);
             }
         }
@@ -1872,10 +1874,20 @@ extern "C" int trig_submit_slice(trig_detector *det, int64_t t0, const trig_hit 
         ce = cudaStreamCreateWithFlags(&copy_stream, cudaStreamNonBlocking);
         copy_dev = e->device;
     }
-    // the next slice's leading halo: this submission's hits in
-    // [t0 + S - halo, t0 + S), PMT by PMT (a producer's unordered stream
+    unsigned char *dst = T ? raw : p.dblk;
+    const size_t dst_pmt_at = T ? raw_pmt_at : p.pmt_at;
+    if (!ce && n) ce = cudaMemcpyAsync(dst, hits, n * sizeof(trig_hit), cudaMemcpyHostToDevice, copy_stream);
+    if (!ce) ce = cudaMemcpyAsync(dst + dst_pmt_at, pmt_off, (size_t)(P + 1) * 8, cudaMemcpyHostToDevice, copy_stream);
+    if (!ce && T)
+        ce = launch_prepend(tl.d_hits[tl.cur], tl.d_off[tl.cur], T, reinterpret_cast<const trig_hit *>(raw),
+                            reinterpret_cast<const uint64_t *>(raw + raw_pmt_at), n, P,
+                            reinterpret_cast<trig_hit *>(p.dblk), reinterpret_cast<uint64_t *>(p.dblk + p.pmt_at),
+                            copy_stream);
+    // while that runs, the next slice's leading halo: this submission's hits
+    // in [t0 + S - halo, t0 + S), PMT by PMT (a producer's unordered stream
     // gives some sub-range; the device flags such a slice), staged in
     // page-locked memory so that its copy is asynchronous like the slice's
+    // and goes to the device copy the prepend above does not read
     std::vector<uint64_t> toff(P + 1, 0), tfrom(P, 0);
     for (uint32_t q = 0; q < P; ++q) {
         const uint64_t a = host_lb_back(hits, pmt_off[q], pmt_off[q + 1], t0 + S - halo);
@@ -1899,7 +1911,6 @@ extern "C" int trig_submit_slice(trig_detector *det, int64_t t0, const trig_hit 
             std::memcpy(tl.h_hits + toff[q], hits + tfrom[q], (size_t)(toff[q + 1] - toff[q]) * sizeof(trig_hit));
         std::memcpy(tl.h_off, toff.data(), (size_t)(P + 1) * 8);
     }
-    // the new tail goes to the device copy the prepend below does not read
     const int nx = tl.cur ^ 1;
     if (!ce && tn > tl.cap[nx]) {
         cudaFree(tl.d_hits[nx]);
@@ -1910,19 +1921,13 @@ extern "C" int trig_submit_slice(trig_detector *det, int64_t t0, const trig_hit 
         if (!ce) tl.cap[nx] = want;
     }
     if (!ce && !tl.d_off[nx]) ce = cudaMalloc(&tl.d_off[nx], (size_t)(P + 1) * 8);
-    unsigned char *dst = T ? raw : p.dblk;
-    const size_t dst_pmt_at = T ? raw_pmt_at : p.pmt_at;
-    if (!ce && n) ce = cudaMemcpyAsync(dst, hits, n * sizeof(trig_hit), cudaMemcpyHostToDevice, copy_stream);
-    if (!ce) ce = cudaMemcpyAsync(dst + dst_pmt_at, pmt_off, (size_t)(P + 1) * 8, cudaMemcpyHostToDevice, copy_stream);
-    if (!ce && T)
-        ce = launch_prepend(tl.d_hits[tl.cur], tl.d_off[tl.cur], T, reinterpret_cast<const trig_hit *>(raw),
-                            reinterpret_cast<const uint64_t *>(raw + raw_pmt_at), n, P,
-                            reinterpret_cast<trig_hit *>(p.dblk), reinterpret_cast<uint64_t *>(p.dblk + p.pmt_at),
-                            copy_stream);
     if (!ce && tn)
         ce = cudaMemcpyAsync(tl.d_hits[nx], tl.h_hits, tn * sizeof(trig_hit), cudaMemcpyHostToDevice, copy_stream);
     if (!ce) ce = cudaMemcpyAsync(tl.d_off[nx], tl.h_off, (size_t)(P + 1) * 8, cudaMemcpyHostToDevice, copy_stream);
+    const auto t_wait = Clock::now();
     if (!ce) ce = cudaStreamSynchronize(copy_stream);
+    p.copy_wait_us = (uint32_t)std::min<int64_t>(
+        std::chrono::duration_cast<std::chrono::microseconds>(Clock::now() - t_wait).count(), 0xffffffffLL);
     if (raw) e->pool.put(raw, raw_bytes);
     if (ce) {
         (void)cudaGetLastError();

@@ -27,6 +27,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import os
 import sys
 import threading
 import time
@@ -65,7 +66,7 @@ def _submit(det, t0, st, cont) -> int:
 
 
 def replay(dets, pools, rate_factor, detector_seconds: float, slice_ns: int, seed: int = 0, mode: int = 1,
-           warmup_rounds: int = 1) -> dict:
+           warmup_rounds: int = 1, trace_out: str | None = None) -> dict:
     """dets[i] receives pools[i][k % len(pools[i])] as its k-th slice; the
     arrival gaps of each detector are exponential with mean
     slice_ns / rate_factor (wall clock), or zero for rate_factor "sat"."""
@@ -155,6 +156,8 @@ def replay(dets, pools, rate_factor, detector_seconds: float, slice_ns: int, see
         th.join()
     t_end = time.perf_counter()
     trace = _lib.trig_engine_trace_read(len(events) + 16)
+    if trace_out:
+        np.save(trace_out, trace)           # the engine's per-slice records of this run
     _lib.trig_engine_trace(0)
     lat_engine, lat_e2e, per_det = [], [], []
     hits = 0
@@ -199,7 +202,8 @@ def replay(dets, pools, rate_factor, detector_seconds: float, slice_ns: int, see
 
 def trace_summary(tr: np.ndarray) -> dict:
     """Where a slice's time goes, from the engine's records: submit (the
-    host-to-device copy, and the resident tail's update), queue (waiting for
+    host-to-device copy, and the resident tail's update; copy_wait the part
+    spent waiting for the copies after the host work), queue (waiting for
     a slot and a batch), device (the batch's kernels, CUDA events), readback
     (the results' copy back after the counters) -- percentiles of each, and
     the same parts for the slowest 0.1 % of slices."""
@@ -208,6 +212,7 @@ def trace_summary(tr: np.ndarray) -> dict:
     ms = 1e-6
     parts = {
         "submit_ms": (tr["t_queued_ns"] - tr["t_submit_ns"]) * ms,
+        "copy_wait_ms": tr["copy_wait_us"] * 1e-3,
         "queue_ms": (tr["t_launch_ns"] - tr["t_queued_ns"]) * ms,
         "batch_ms": (tr["t_stats_ns"] - tr["t_launch_ns"]) * ms,
         "readback_ms": (tr["t_done_ns"] - tr["t_stats_ns"]) * ms,
@@ -267,6 +272,7 @@ def main():
                     help="rate:mode:detector_seconds per run (rate in units of real time, sat or burst)")
     ap.add_argument("--pool", type=int, default=20, help="contiguous pre-generated slices per detector")
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--trace-dir", default=None, help="save each run's per-slice engine trace here (run<k>.npy)")
     ap.add_argument("--detectors", type=int, nargs="+", default=[0, 1, 2, 3],
                     help="which of the four detectors (32, 84, 84, 2688 PMTs) take part")
     args = ap.parse_args()
@@ -281,7 +287,11 @@ def main():
     runs = []
     for k, text in enumerate(args.runs):
         rate, mode, secs = _parse_run(text)
-        runs.append(replay(dets, pools, rate, secs, par["slice_ns"], args.seed + k, mode))
+        out_k = None
+        if args.trace_dir:
+            os.makedirs(args.trace_dir, exist_ok=True)
+            out_k = os.path.join(args.trace_dir, f"run{k}.npy")
+        runs.append(replay(dets, pools, rate, secs, par["slice_ns"], args.seed + k, mode, trace_out=out_k))
         print(json.dumps(runs[-1]), file=sys.stderr, flush=True)      # progress, one line per run
     out = {"detectors": ", ".join(f"{d.n_pmt}@{r / 1e3:g}kHz" for d, r in spec), "pool_slices_per_detector": args.pool,
            "pool_generation_s": gen_s, "continuation": "every pool slice after the first", "runs": runs}

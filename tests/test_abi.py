@@ -73,7 +73,7 @@ def test_binding_struct_sizes_match_header():
                "trig_array_stats": ["n_tower_triggers", "n_selected", "n_windows", "n_hits", "flags", "status"],
                "trig_trace_rec": ["slice_id", "batch", "batch_slices", "n_pmt", "n_hits", "status", "continuation",
                                   "t_submit_ns", "t_queued_ns", "t_launch_ns", "t_stats_ns", "t_done_ns", "device_ms",
-                                  "reserved"]}
+                                  "copy_wait_us"]}
     lay = _c_layout({**{k: [f for f, _ in v._fields_] for k, v in ct.items()}, **c_names})
     for name, cls in ct.items():
         assert ctypes.sizeof(cls) == lay[name], name
