@@ -1783,6 +1783,36 @@ extern "C" int trig_engine_stats(uint64_t *batches, uint64_t *slices)
 
 // First index i in [lo, hi) of a time-ordered host run with hits[i].t_ns >= v
 // (for a run that is not ordered: some index in [lo, hi]).
+// A large host-to-device copy in chunks with at most two queued on the
+// stream: copies from other submitting threads queue behind two chunks, not
+// behind a whole large slice.
+static cudaError_t copy_paced(void *dst, const void *src, size_t bytes, cudaStream_t st)
+{
+    constexpr size_t kChunk = (size_t)64 << 20;
+    if (bytes <= 2 * kChunk) return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st);
+    thread_local cudaEvent_t ev[2] = {nullptr, nullptr};
+    thread_local int ev_dev = -1;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e) return e;
+    if (ev_dev != dev) {
+        for (int i = 0; i < 2; ++i) {
+            if ((e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming))) return e;
+        }
+        ev_dev = dev;
+    }
+    size_t k = 0;
+    for (size_t off = 0; off < bytes; off += kChunk, ++k) {
+        const size_t len = std::min(kChunk, bytes - off);
+        if ((e = cudaMemcpyAsync(static_cast<unsigned char *>(dst) + off, static_cast<const unsigned char *>(src) + off,
+                                 len, cudaMemcpyHostToDevice, st)))
+            return e;
+        if ((e = cudaEventRecord(ev[k & 1], st))) return e;
+        if (k >= 1 && (e = cudaEventSynchronize(ev[(k - 1) & 1]))) return e;
+    }
+    return cudaSuccess;
+}
+
 static uint64_t host_lb(const trig_hit *h, uint64_t lo, uint64_t hi, int64_t v)
 {
     while (lo < hi) {
@@ -1876,7 +1906,7 @@ extern "C" int trig_submit_slice(trig_detector *det, int64_t t0, const trig_hit 
     }
     unsigned char *dst = T ? raw : p.dblk;
     const size_t dst_pmt_at = T ? raw_pmt_at : p.pmt_at;
-    if (!ce && n) ce = cudaMemcpyAsync(dst, hits, n * sizeof(trig_hit), cudaMemcpyHostToDevice, copy_stream);
+    if (!ce && n) ce = copy_paced(dst, hits, n * sizeof(trig_hit), copy_stream);
     if (!ce) ce = cudaMemcpyAsync(dst + dst_pmt_at, pmt_off, (size_t)(P + 1) * 8, cudaMemcpyHostToDevice, copy_stream);
     if (!ce && T)
         ce = launch_prepend(tl.d_hits[tl.cur], tl.d_off[tl.cur], T, reinterpret_cast<const trig_hit *>(raw),
