@@ -1913,11 +1913,11 @@ extern "C" int trig_submit_slice(trig_detector *det, int64_t t0, const trig_hit 
                             reinterpret_cast<const uint64_t *>(raw + raw_pmt_at), n, P,
                             reinterpret_cast<trig_hit *>(p.dblk), reinterpret_cast<uint64_t *>(p.dblk + p.pmt_at),
                             copy_stream);
-    // while that runs, the next slice's leading halo: this submission's hits
-    // in [t0 + S - halo, t0 + S), PMT by PMT (a producer's unordered stream
-    // gives some sub-range; the device flags such a slice), staged in
-    // page-locked memory so that its copy is asynchronous like the slice's
-    // and goes to the device copy the prepend above does not read
+    // while the copy finishes, the next slice's leading halo: this
+    // submission's hits in [t0 + S - halo, t0 + S), PMT by PMT (a producer's
+    // unordered stream gives some sub-range; the device flags such a slice),
+    // staged in page-locked memory so that its copy is asynchronous like the
+    // slice's, and sent to the device copy the prepend above does not read
     std::vector<uint64_t> toff(P + 1, 0), tfrom(P, 0);
     for (uint32_t q = 0; q < P; ++q) {
         const uint64_t a = host_lb_back(hits, pmt_off[q], pmt_off[q + 1], t0 + S - halo);
