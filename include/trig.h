@@ -102,8 +102,8 @@ typedef struct {
      * GPU": N7TW1000 / DN7TW1000, N hits within TW, applied before the
      * seed triggers).  With l0_hits = N > 0 a seed counts only if some
      * window [a, a + TW) containing it holds at least N hits, or, with
-     * l0_distinct_pmts, hits of at least N different PMTs (then n_pmt must
-     * be at most 128).  l0_hits = 0 turns it off; TW <= 60000 ns. */
+     * l0_distinct_pmts, hits of at least N different PMTs (any n_pmt).
+     * l0_hits = 0 turns it off; TW <= 60000 ns. */
     uint32_t l0_hits;
     uint32_t l0_window_ns;
     uint32_t l0_distinct_pmts;

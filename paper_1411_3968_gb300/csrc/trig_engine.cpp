@@ -285,8 +285,6 @@ extern "C" int trig_create(const trig_geometry *g, const trig_params *params, tr
     int rc = check_params(params);
     if (rc) return rc;
     const uint32_t P = g->n_pmt;
-    if (params->l0_hits > 0 && params->l0_distinct_pmts && P > 128)
-        return fail(TRIG_EINVAL, "the distinct-PMT level 0 needs n_pmt <= 128");
     for (uint32_t i = 0; i < 3 * P; ++i)
         if (g->xyz_mm[i] > 100000000 || g->xyz_mm[i] < -100000000)
             return fail(TRIG_EINVAL, "coordinates must lie within +-1e8 mm");

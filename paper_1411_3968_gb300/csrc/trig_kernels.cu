@@ -995,7 +995,7 @@ __device__ __noinline__ void count_distinct_pmts(const TileCtx<CAP> &cx, const u
 
 // Level 0 at sorted index i: some window [t_j, t_j + TW) with
 // t_i - TW < t_j <= t_i holds at least N hits, or hits of N different PMTs
-// (P <= 128).  Only the first index of each time starts a window; every
+// (P <= 128 here; above, level0_distinct_warp).  Only the first index of each time starts a window; every
 // hit within TW of a core hit is staged (the tile halo covers TW).  The
 // distinct count slides the window back start by start, keeping per-PMT
 // counts, so it reads each hit within 2 TW once.
@@ -1039,6 +1039,46 @@ __device__ __noinline__ bool level0_pass(const uint32_t *pk, uint32_t n, uint32_
             if (--cnt[pk_p(pk[e]) & 127u] == 0) --distinct_n;
         }
         j = nj;
+    }
+}
+
+// Level 0 with distinct PMTs above 128 PMTs, by a warp: the same window
+// starts as level0_pass (each first index of a time within TW before t_i),
+// each window's PMTs marked in the warp's 4096-bit set in shared memory and
+// counted; the first window with N different PMTs ends the search.
+__device__ __noinline__ bool level0_distinct_warp(const uint32_t *pk, uint32_t n, uint32_t i, uint32_t N, uint32_t TW,
+                                                  uint32_t P, uint32_t *set)
+{
+    const uint32_t lane = lane_id(), nwords = (P + 31u) >> 5;
+    const uint32_t ts = pk_t(pk[i]);
+    uint32_t j = i;
+    while (j > 0 && pk_t(pk[j - 1]) == ts) --j;             // first index of t_i
+    for (;;) {
+        const uint32_t tj = pk_t(pk[j]);
+        for (uint32_t w = lane; w < nwords; w += 32) set[w] = 0u;
+        __syncwarp();
+        // the window [t_j, t_j + TW): keys from j on, in time order
+        for (uint32_t k0 = j; k0 < n; k0 += 32) {
+            const uint32_t k = k0 + lane;
+            bool in = false;
+            if (k < n) {
+                const uint32_t kk = pk[k], pj = pk_p(kk);
+                in = pk_t(kk) - tj < TW;
+                if (in && CHECK(27, pj, P)) atomicOr(&set[pj >> 5], 1u << (pj & 31u));
+            }
+            if (!__any_sync(0xffffffffu, in)) break;
+        }
+        __syncwarp();
+        uint32_t c = 0;
+        for (uint32_t w = lane; w < nwords; w += 32) c += __popc(set[w]);
+        c = __reduce_add_sync(0xffffffffu, c);
+        __syncwarp();                                       // the set is read before it is cleared again
+        if (c >= N) return true;
+        if (j == 0) return false;
+        const uint32_t tp = pk_t(pk[j - 1]);
+        if (ts - tp >= TW) return false;
+        for (--j; j > 0 && pk_t(pk[j - 1]) == tp; --j) {
+        }
     }
 }
 
@@ -1390,13 +1430,32 @@ __device__ CoreOut tile_pass(TileCtx<CAP> &cx, const uint64_t *stage, uint32_t n
     cons_sync<NC>();
     if (EXT && tp.l0_hits) {
         // level 0 (N hits within TW) before the seed triggers count
-        for (uint32_t base = c0 & ~31u; base < c1; base += NC) {
-            const uint32_t i = base + tid;
-            const uint32_t w = (i >= c0 && i < c1) ? mask[i >> 5] : 0u;
-            const bool drop = ((w >> (i & 31u)) & 1u) &&
-                              !level0_pass(pk, n, i, tp.l0_hits, tp.l0_window, tp.l0_distinct != 0);
-            const uint32_t m = __ballot_sync(0xffffffffu, drop);
-            if (lane == 0 && m) atomicAnd(&mask[(base >> 5) + warp], ~m);
+        if (tp.l0_distinct && P > 128) {
+            // a warp per seed, its PMT set in the bucket-order key region
+            // (free between the floor coincidences and the seed list)
+            static_assert(NC / 32 * 128 <= CAP, "a 4096-bit PMT set per consumer warp");
+            uint32_t *set = cx.pk_b() + warp * 128;
+            for (uint32_t base = (c0 & ~31u) + warp * 32; base < c1; base += NC) {
+                const uint32_t i = base + lane;
+                const uint32_t w = (i >= c0 && i < c1) ? mask[i >> 5] : 0u;
+                uint32_t cand = __ballot_sync(0xffffffffu, (w >> (i & 31u)) & 1u);
+                uint32_t drop = 0;
+                while (cand) {
+                    const uint32_t b = __ffs(cand) - 1;
+                    cand &= cand - 1;
+                    if (!level0_distinct_warp(pk, n, base + b, tp.l0_hits, tp.l0_window, P, set)) drop |= 1u << b;
+                }
+                if (lane == 0 && drop) atomicAnd(&mask[base >> 5], ~drop);
+            }
+        } else {
+            for (uint32_t base = c0 & ~31u; base < c1; base += NC) {
+                const uint32_t i = base + tid;
+                const uint32_t w = (i >= c0 && i < c1) ? mask[i >> 5] : 0u;
+                const bool drop = ((w >> (i & 31u)) & 1u) &&
+                                  !level0_pass(pk, n, i, tp.l0_hits, tp.l0_window, tp.l0_distinct != 0);
+                const uint32_t m = __ballot_sync(0xffffffffu, drop);
+                if (lane == 0 && m) atomicAnd(&mask[(base >> 5) + warp], ~m);
+            }
         }
         cons_sync<NC>();
     }

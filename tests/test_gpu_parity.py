@@ -562,9 +562,28 @@ def test_level0_wide_detector(pkg, params):
     d.close()
 
 
+def test_distinct_level0_above_128_pmts(pkg, params):
+    """DN7TW1000 (level 0 over different PMTs) on a 168-PMT two-tower array
+    and on the 2688-PMT array (a warp per seed with a shared-memory PMT set):
+    exact against the oracle on two contiguous slices each."""
+    for g, rate, slice_ns, n_req in ((_tower_array(2, 1), 300e3, 500_000, 48),
+                                     (_tower_array(8, 4), 55e3, 200_000, 150)):
+        par = dict(params, slice_ns=slice_ns, l0_hits=n_req, l0_window_ns=1000, l0_distinct_pmts=1)
+        t0 = workload.T_ORIGIN_NS
+        t0s = [t0, t0 + slice_ns]
+        full = workload.gen_stream(g, t0 - 3000, t0 + 2 * slice_ns + 3000, rate, n_muons=20, seed=10, stream=160)
+        d = _det(pkg, g, par)
+        _, res = _run(pkg, d, _subs_from_run(full, t0s, slice_ns))
+        ref = oracle.run(g.xyz_mm, g.floor_id, par, full.hits, t0s)
+        off = oracle.run(g.xyz_mm, g.floor_id, dict(par, l0_hits=0), full.hits, t0s)
+        assert sum(len(r.seeds) for r in ref) > 0
+        assert sum(len(r.seeds) for r in ref) < sum(len(r.seeds) for r in off)     # level 0 drops seeds
+        for k in range(2):
+            _assert_same(res[k], ref[k], f"distinct level 0, {g.n_pmt} PMTs, slice {k}")
+        d.close()
+
+
 def test_level0_parameter_checks(pkg, params):
-    with pytest.raises(pkg.TrigError):
-        _det(pkg, _tower_array(2, 1), dict(params, l0_hits=7, l0_distinct_pmts=1))   # > 128 PMTs
     with pytest.raises(pkg.TrigError):
         _det(pkg, workload.nemo_tower(), dict(params, l0_hits=7, l0_window_ns=0))
 

@@ -432,6 +432,32 @@ def test_level0_bruteforce_and_index_reading():
             assert idx == keep, case
 
 
+def test_distinct_level0_bruteforce_above_128_pmts():
+    """The distinct-PMT level 0 on a 168-PMT two-tower array (PMT ids above
+    128, repeats of one PMT inside a window): the oracle keeps exactly the
+    seeds whose some window holds N different PMTs."""
+    rng = np.random.Generator(np.random.PCG64(321))
+    g = workload.tower_array(nx=2, ny=1)
+    for case in range(6):
+        n_req = int(rng.integers(2, 9))
+        tw = int(rng.choice([100, 400, 1000]))
+        par = dict(workload.DEFAULT_PARAMS, slice_ns=30_000, threshold=1, l0_window_ns=tw, l0_hits=n_req,
+                   l0_distinct_pmts=1, q_seed_adc=250)
+        t0 = 10_000_000
+        n = int(rng.integers(150, 400))
+        hits = np.zeros(n, oracle.HIT_DTYPE)
+        hits["t"] = rng.integers(t0 - 3000, t0 + par["slice_ns"] + 3000, n)
+        hits["pmt"] = rng.choice(np.r_[rng.integers(0, 168, 12), rng.integers(128, 168, 6)], n)
+        hits["charge"] = rng.integers(1, 400, n)
+        off = oracle.run(g.xyz_mm, g.floor_id, dict(par, l0_hits=0), hits, [t0])[0]
+        on = oracle.run(g.xyz_mm, g.floor_id, par, hits, [t0])[0]
+        sh = oracle.merge(hits)
+        key = list(zip(sh["t"].tolist(), sh["pmt"].tolist(), sh["charge"].tolist()))
+        keep = [sd for sd in off.seeds.tolist() if _level0_brute(sh, key.index(tuple(sd[:3])), n_req, tw, 1)]
+        assert on.seeds.tolist() == keep, case
+        assert 0 < len(keep) <= len(off.seeds), case
+
+
 # ------------------------------------- coincidence ladder, distinct count
 
 def test_ladder_golden_fixture():
