@@ -499,6 +499,22 @@ def main():
                   "pipeline": {"bytes_per_hit": pipe_b, "achieved": pipe_b * n_s / (ms_s * 1e-3) / 1e9,
                                "note": "structure pass 16 B + bucket-major copy 32 B + tile pass 16 B per hit"},
                   "path": "trig_batch_run, CUDA graph replay"}
+        # DRAM traffic and issue bound of k_tile on this slice from the ncu
+        # record (profiles/k_tile_traffic.json), while the kernel source
+        # matches; the issue bound only at the captured tile shape
+        tf = _traffic_record()
+        if tf:
+            bph = tf.get("bytes_per_hit", {}).get("scaled")
+            scaled["roofline"]["traffic"] = bph * n_s if bph else None
+            wiph = tf.get("warp_inst_per_hit", {}).get("scaled")
+            shape = tf.get("shapes", {}).get("scaled", {})
+            tc = scaled["tile"]
+            mhz = (clocks or {}).get("sm_mhz")
+            if wiph and mhz and all(tc.get(k) == v for k, v in shape.items()):
+                sms = torch.cuda.get_device_properties(local).multi_processor_count
+                bound_ms = wiph * n_s / (sms * 4 * mhz * 1e6) * 1e3
+                scaled["roofline"]["issue"] = {"warp_inst_per_hit": wiph, "sm_mhz": mhz, "bound_ms": bound_ms,
+                                               "frac": bound_ms / t_ms}
         del bs, dsc
         log(f"scaled: {ms_s:.3f} ms/step, k_tile {t_ms:.3f} ms")
 
@@ -601,6 +617,18 @@ def main():
         d.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def _traffic_record():
+    """The ncu record of k_tile's DRAM bytes and instructions per hit, or
+    None when it is missing or was taken on another version of the kernel
+    source."""
+    path = os.path.join(ROOT, "profiles", "k_tile_traffic.json")
+    try:
+        tf = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    return tf if tf.get("source_hash") == _tile_source_hash() else None
 
 
 def _tile_source_hash() -> str:
